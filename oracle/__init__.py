@@ -1,0 +1,235 @@
+"""Python access to the FP64 CPU oracle (test infrastructure only).
+
+The oracle is a plain double-precision C++ evaluation of the equivariant
+interaction potential (see mlip_oracle.cpp for the definitions it writes out).
+Only the tests, the smoke check and the CPU-baseline leg of the benchmark use
+it; the library never imports, links or runs anything here.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mlip_oracle.cpp")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (OpenMP, no FMA contraction)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
+               "-o", tmp, _SRC]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i32, i64, f64 = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        L.oracle_real_sh.argtypes = [i32, P, P]
+        L.oracle_real_sh_grad.argtypes = [i32, P, P]
+        L.oracle_complex_sh.argtypes = [i32, P, P, P]
+        L.oracle_cg_complex.argtypes = [i32] * 6
+        L.oracle_cg_complex.restype = f64
+        L.oracle_real_basis_U.argtypes = [i32, P, P]
+        L.oracle_real_cg.argtypes = [i32, i32, i32, P]
+        L.oracle_paths.argtypes = [i32, i32, P]
+        L.oracle_bessel.argtypes = [i32, f64, f64]
+        L.oracle_bessel.restype = f64
+        L.oracle_envelope.argtypes = [f64, i32]
+        L.oracle_envelope.restype = f64
+        L.oracle_num_weights.argtypes = [P]
+        L.oracle_num_weights.restype = i64
+        L.oracle_model_create.argtypes = [P, P, P]
+        L.oracle_model_create.restype = P
+        L.oracle_model_free.argtypes = [P]
+        L.oracle_neighbors.argtypes = [P, i64, P, P, f64, P, P, P, i64]
+        L.oracle_neighbors.restype = i64
+        L.oracle_energy_forces.argtypes = [P, P, P, i64, P, P, P, P, P, P]
+        L.oracle_energy.argtypes = [P, P, P, i64, P, P, P, P]
+        L.oracle_energy_dual.argtypes = [P, P, P, i64, P, P, i64, i32, P, P]
+        L.oracle_tp.argtypes = [i32, i32, i32, P, P, P, P]
+        L.oracle_vv_nve.argtypes = [P, P, P, P, P, i64, P, P, f64, i64, P, P]
+        L.oracle_set_threads.argtypes = [i32]
+        L.oracle_max_threads.restype = i32
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def set_threads(n: int) -> None:
+    lib().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
+
+
+def real_sh(lmax: int, v) -> np.ndarray:
+    v = _c(v, np.float64)
+    out = np.zeros((lmax + 1) ** 2)
+    assert lib().oracle_real_sh(lmax, _p(v), _p(out)) == 0
+    return out
+
+
+def real_sh_grad(lmax: int, v) -> np.ndarray:
+    v = _c(v, np.float64)
+    out = np.zeros(((lmax + 1) ** 2, 3))
+    assert lib().oracle_real_sh_grad(lmax, _p(v), _p(out)) == 0
+    return out
+
+
+def complex_sh(l: int, v) -> np.ndarray:
+    v = _c(v, np.float64)
+    re = np.zeros(2 * l + 1); im = np.zeros(2 * l + 1)
+    lib().oracle_complex_sh(l, _p(v), _p(re), _p(im))
+    return re + 1j * im
+
+
+def cg_complex(l1, m1, l2, m2, l3, m3) -> float:
+    return float(lib().oracle_cg_complex(l1, m1, l2, m2, l3, m3))
+
+
+def real_basis_U(l: int) -> np.ndarray:
+    n = 2 * l + 1
+    re = np.zeros(n * n); im = np.zeros(n * n)
+    lib().oracle_real_basis_U(l, _p(re), _p(im))
+    return (re + 1j * im).reshape(n, n)
+
+
+def real_cg(l1: int, l2: int, l3: int) -> np.ndarray:
+    out = np.zeros((2 * l3 + 1) * (2 * l1 + 1) * (2 * l2 + 1))
+    assert lib().oracle_real_cg(l1, l2, l3, _p(out)) == 0
+    return out.reshape(2 * l3 + 1, 2 * l1 + 1, 2 * l2 + 1)
+
+
+def paths(L: int, Lsh: int = 3) -> list:
+    n = lib().oracle_paths(L, Lsh, None)
+    out = np.zeros(3 * n, dtype=np.int32)
+    lib().oracle_paths(L, Lsh, _p(out))
+    return [tuple(int(x) for x in out[3 * k:3 * k + 3]) for k in range(n)]
+
+
+def bessel(n: int, r: float, rc: float) -> float:
+    return float(lib().oracle_bessel(n, r, rc))
+
+
+def envelope(x: float, p: int = 6) -> float:
+    return float(lib().oracle_envelope(x, p))
+
+
+def tp(L: int, Lsh: int, h: np.ndarray, v, w: np.ndarray) -> np.ndarray:
+    """Feature-level tensor product for one edge; h [(L+1)^2, C], w [P, C]."""
+    h = _c(h, np.float64); w = _c(w, np.float64); v = _c(v, np.float64)
+    C = h.shape[1]
+    out = np.zeros_like(h)
+    lib().oracle_tp(L, Lsh, C, _p(h), _p(v), _p(w), _p(out))
+    return out
+
+
+def neighbors(pos, cell, pbc, rc: float):
+    """Brute-force neighbour list sorted by (recv, send, shift)."""
+    pos = _c(pos, np.float64); cell = _c(cell, np.float64); pbc = _c(pbc, np.uint8)
+    n = pos.shape[0]
+    cap = 0
+    e = lib().oracle_neighbors(_p(pos), n, _p(cell), _p(pbc), rc, None, None, None, 0)
+    if e < 0:
+        raise ValueError("singular cell")
+    recv = np.zeros(max(e, 1), np.int32); send = np.zeros(max(e, 1), np.int32)
+    shift = np.zeros((max(e, 1), 3), np.int32)
+    cap = e
+    e2 = lib().oracle_neighbors(_p(pos), n, _p(cell), _p(pbc), rc, _p(recv), _p(send), _p(shift), cap)
+    assert e2 == e
+    return recv[:e], send[:e], shift[:e]
+
+
+class Model:
+    """Oracle model built from the flat float32 weights of synth.make_weights."""
+
+    def __init__(self, spec, weights: np.ndarray):
+        self.spec = spec
+        self._hyper = _c(spec.hyper, np.int32)
+        self._dhyper = _c(spec.dhyper, np.float64)
+        nw = lib().oracle_num_weights(_p(self._hyper))
+        w = _c(weights, np.float32)
+        if w.size != nw:
+            raise ValueError(f"expected {nw} weights, got {w.size}")
+        self._w = w
+        self._h = lib().oracle_model_create(_p(self._hyper), _p(self._dhyper), _p(w))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.oracle_model_free(h)
+            self._h = None
+
+    def energy_forces(self, pos, species, cell, pbc, stress: bool = False, atom_energies: bool = False):
+        pos = _c(pos, np.float64); species = _c(species, np.int32)
+        cell = _c(cell, np.float64); pbc = _c(pbc, np.uint8)
+        n = pos.shape[0]
+        E = np.zeros(1); F = np.zeros((n, 3))
+        S = np.zeros((3, 3)) if stress else None
+        A = np.zeros(n) if atom_energies else None
+        rc = lib().oracle_energy_forces(self._h, _p(pos), _p(species), n, _p(cell), _p(pbc), _p(E), _p(F),
+                                        _p(S) if stress else None, _p(A) if atom_energies else None)
+        if rc != 0:
+            raise ValueError(f"oracle_energy_forces failed: {rc}")
+        out = {"energy": float(E[0]), "forces": F}
+        if stress:
+            out["stress"] = S
+        if atom_energies:
+            out["atom_energies"] = A
+        return out
+
+    def energy(self, pos, species, cell, pbc, atom_energies: bool = False):
+        pos = _c(pos, np.float64); species = _c(species, np.int32)
+        cell = _c(cell, np.float64); pbc = _c(pbc, np.uint8)
+        n = pos.shape[0]
+        E = np.zeros(1)
+        A = np.zeros(n) if atom_energies else None
+        rc = lib().oracle_energy(self._h, _p(pos), _p(species), n, _p(cell), _p(pbc), _p(E),
+                                 _p(A) if atom_energies else None)
+        if rc != 0:
+            raise ValueError(f"oracle_energy failed: {rc}")
+        return (float(E[0]), A) if atom_energies else float(E[0])
+
+    def energy_dual(self, pos, species, cell, pbc, atom: int, axis: int):
+        pos = _c(pos, np.float64); species = _c(species, np.int32)
+        cell = _c(cell, np.float64); pbc = _c(pbc, np.uint8)
+        E = np.zeros(1); dE = np.zeros(1)
+        rc = lib().oracle_energy_dual(self._h, _p(pos), _p(species), pos.shape[0], _p(cell), _p(pbc),
+                                      atom, axis, _p(E), _p(dE))
+        if rc != 0:
+            raise ValueError("oracle_energy_dual failed")
+        return float(E[0]), float(dE[0])
+
+    def vv_nve(self, pos, vel, species, masses, cell, pbc, dt: float, n_steps: int):
+        pos = np.array(pos, dtype=np.float64, copy=True); vel = np.array(vel, dtype=np.float64, copy=True)
+        species = _c(species, np.int32); masses = _c(masses, np.float64)
+        cell = _c(cell, np.float64); pbc = _c(pbc, np.uint8)
+        pe = np.zeros(n_steps + 1); ke = np.zeros(n_steps + 1)
+        rc = lib().oracle_vv_nve(self._h, _p(pos), _p(vel), _p(species), _p(masses), pos.shape[0], _p(cell),
+                                 _p(pbc), dt, n_steps, _p(pe), _p(ke))
+        if rc != 0:
+            raise ValueError("oracle_vv_nve failed")
+        return pos, vel, pe, ke
