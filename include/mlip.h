@@ -1,0 +1,141 @@
+/*
+ * mlip.h - C ABI of the GB300 equivariant interaction-layer library.
+ *
+ * The library evaluates an equivariant message-passing interatomic potential
+ * of the NequIP/MACE family that arxiv 2605.22698 ("mlip v2") trains and
+ * simulates (Sec. 2 "Background and related work"; Sec. 4 "Accelerating
+ * equivariant operations with e3j"; hyperparameters of Tables
+ * tbl:nequip_params and tbl:mace_params).  Energy is a per-atom readout plus
+ * per-species reference energies (Eq. multihead_readout with one head);
+ * forces are -dE/dr (the first derivative in Eq. full_hessian).  The model:
+ *
+ *   edges     all (receiver i, sender j, image S) with |r_j - r_i + S.h| < rc
+ *   x_e       r_j - r_i + S.h,  r = |x_e|,  unit vector r^ = x_e / r
+ *   Y_e       real spherical harmonics Y_{l m}(r^), l <= 3 (16 values)
+ *   b_e[n]    sqrt(2/rc) sin(n pi r/rc)/r * u(r/rc), n = 1..8, u the p = 6
+ *             polynomial envelope
+ *   w_e       W3^T silu(W2^T silu(W1^T b_e))  -> one weight per path and channel
+ *   m_i       (1/avg_num_neighbors) sum_{e: recv = i} sum_paths w_e[p][c]
+ *             sum_{m1,m2} CG^p[m3][m1][m2] h_j[l1 m1][c] Y_e[l2 m2]
+ *   update    u = m W_l per l; h_0 += silu(u_0); h_{l>0} += u_l
+ *   energy    E = sum_i (W_out[z_i] . h_i,0 + E0[z_i])
+ *
+ * Conventions (all functions):
+ *   - Return an int status: 0 = MLIP_OK, negative = error; they never abort.
+ *     mlip_last_error() gives a thread-local message for the last failure.
+ *     A sticky CUDA error is reported as MLIP_ERR_CUDA.
+ *   - Units: positions A (double, row-major [n][3]), energies eV, forces eV/A,
+ *     stress eV/A^3 (ASE sign: stress = (1/V) dE/d(strain)), time fs, mass amu.
+ *   - cell: 3 x 3 row-major doubles, rows are the lattice vectors; pbc: 3 bytes.
+ *     cell and pbc are always HOST pointers.  For a system with no periodic
+ *     axis the cell is ignored.  Positions are never wrapped.
+ *   - on_device = 0: positions, species and outputs are host pointers; the
+ *     call copies them to and from device buffers it owns.  on_device = 1: they are
+ *     device pointers on the current CUDA device.  stream: a cudaStream_t or
+ *     NULL (legacy default stream).
+ *   - The caller owns every buffer it passes.  Opaque handles are owned by the
+ *     library and released with the matching _free/_destroy.  One model handle
+ *     must not be used by two threads at the same time.
+ *   - Species are integers 0..n_species-1.
+ */
+#ifndef MLIP_H
+#define MLIP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MLIP_OK = 0,
+  MLIP_PENDING = 1,
+  MLIP_ERR_INVALID_ARG = -1,
+  MLIP_ERR_CUDA = -2,
+  MLIP_ERR_OOM = -3,
+  MLIP_ERR_BUDGET = -4,
+  MLIP_ERR_CAPACITY = -5,
+  MLIP_ERR_CELL = -6,
+  MLIP_ERR_DEGENERATE = -7,
+  MLIP_ERR_TIMEOUT = -8,
+  MLIP_ERR_DEVICE_TIMEOUT = -9,
+  MLIP_ERR_NOT_FOUND = -10
+} mlip_status;
+
+/* Precision of a model's compute path.
+ * MLIP_PREC_FP32: the plain FP32 form - every product on the FP32 ALUs, the
+ *   per-edge radial weights materialised in HBM, stored intermediates.
+ * MLIP_PREC_BF16: the fused form - radial MLP and channel mixes on tcgen05
+ *   tensor cores (BF16 inputs, FP32 accumulation in tensor memory), harmonics
+ *   and the tensor product in FP32, recomputation in the adjoint. */
+enum { MLIP_PREC_FP32 = 0, MLIP_PREC_BF16 = 1 };
+
+typedef struct mlip_model mlip_model;
+
+/* Hyperparameters.  Defaults of the paper's tables: n_basis 8 (num_rbf),
+ * hidden 64 (radial_net_n_hidden), two hidden layers, envelope p = 6,
+ * cutoff 5 A (graph_cutoff_angstrom).  Supported: channels 16 or 128 (BF16
+ * form: 128), l_max 2 or 3, sh_l_max 3, n_basis 8, hidden 32 or 64. */
+typedef struct {
+  int32_t n_species, n_layers, channels, l_max, sh_l_max, n_basis, hidden, envelope_p;
+  double cutoff;             /* rc, A */
+  double avg_num_neighbors;  /* message scale s = 1/avg_num_neighbors */
+  const double* masses;      /* n_species masses (amu), host; may be NULL (no MD) */
+} mlip_model_desc;
+
+/* Thread-local text of the last error (never NULL). */
+const char* mlip_last_error(void);
+int mlip_version(void);
+
+/* Number of float32 weights a model with this description takes, in the order
+ *   W_emb [S][C]; per layer: W1 [8][H], W2 [H][H], W3 [H][P][C], W_mix [L+1][C][C];
+ *   W_out [S][C]; E0 [S]
+ * (P = number of coupling paths (l1 <= L, l2 <= 3, l3 <= L, triangle rule,
+ * l1 + l2 + l3 even, lexicographic).  Errors: MLIP_ERR_INVALID_ARG. */
+int mlip_model_num_weights(const mlip_model_desc* desc, int64_t* n_weights);
+
+/* Create a model on the current device from host weights (copied).
+ * Errors: MLIP_ERR_INVALID_ARG (unsupported hyperparameters, wrong count),
+ * MLIP_ERR_OOM, MLIP_ERR_CUDA. */
+int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t n_weights,
+                      int precision, mlip_model** out);
+
+/* Load a parameter file: "MLIPPRM1", u32 version 1, 8 x i32 (S, T, C, L, Lsh,
+ * NB, H, p), 2 x f64 (rc, avg_num_neighbors), S x f64 masses, i64 count,
+ * count x f32 weights; little-endian.  Errors as mlip_model_create plus
+ * MLIP_ERR_NOT_FOUND (unreadable file). */
+int mlip_model_load(const char* params_path, int precision, mlip_model** out);
+
+int mlip_model_free(mlip_model* model);
+
+/* Directed neighbour list (the Graph built from a ChemicalSystem with
+ * graph_cutoff_angstrom, App. A): all (recv i, send j, S) with
+ *   d2 = (dx*dx + dy*dy) + dz*dz < cutoff^2,  dx = (x_j - x_i) + sx,
+ *   sx = (S0*h00 + S1*h10) + S2*h20 (likewise y, z), in FP64 with no fused
+ *   multiply-add,
+ * excluding i == j with S = 0; S_k = 0 on open axes.  Sorted by (recv, send,
+ * S0, S1, S2).  recv/send: int32[capacity]; shift: int8[capacity * 3].
+ * On return *n_edges holds the number of edges; if it exceeds capacity the
+ * call returns MLIP_ERR_CAPACITY and writes nothing (retry with a larger
+ * buffer).  Other errors: MLIP_ERR_CELL (singular cell with a periodic axis),
+ * MLIP_ERR_INVALID_ARG (|S| > 127, n < 0, cutoff <= 0, a receiver with more
+ * than 4096 neighbours), MLIP_ERR_CUDA. */
+int mlip_neighbors(const double* pos, int64_t n, const double cell[9], const uint8_t pbc[3],
+                   double cutoff, int32_t* recv, int32_t* send, int8_t* shift, int64_t capacity,
+                   int64_t* n_edges, int on_device, void* stream);
+
+/* Energy, forces and stress of one system.  energy: one double; forces:
+ * double[n][3] or NULL; stress: double[9] or NULL (requires pbc all true, else
+ * MLIP_ERR_CELL).  The neighbour list is built on the device inside the call.
+ * Errors: MLIP_ERR_INVALID_ARG (species out of range, n < 1), MLIP_ERR_CELL,
+ * MLIP_ERR_OOM, MLIP_ERR_CUDA.  The call synchronises the stream once (to size
+ * the edge buffers). */
+int mlip_energy_forces(mlip_model* model, const double* pos, const int32_t* species, int64_t n,
+                       const double cell[9], const uint8_t pbc[3], double* energy, double* forces,
+                       double* stress, int on_device, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLIP_H */

@@ -1,0 +1,371 @@
+// C ABI of the library: errors, workspaces, model handles, the neighbour
+// entry point and the energy/forces entry point (plain FP32 form here; the
+// fused BF16 form lives in fused_bf16.cu).
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <fstream>
+
+#include "launchers.cuh"
+
+namespace mlip {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+const char* last_error() { return g_err; }
+
+int Workspace::get(const std::string& name, size_t bytes, void** out) {
+  Buf& b = bufs[name];
+  if (b.bytes < bytes) {
+    if (b.p) {
+      cudaError_t e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) { set_error("workspace sync: %s", cudaGetErrorString(e)); return MLIP_ERR_CUDA; }
+      cudaFree(b.p);
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    size_t nb = bytes + bytes / 8;
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("workspace '%s': cudaMalloc of %zu bytes failed: %s", name.c_str(), nb, cudaGetErrorString(e));
+      b.p = nullptr;
+      return MLIP_ERR_OOM;
+    }
+    b.bytes = nb;
+  }
+  *out = b.p;
+  return MLIP_OK;
+}
+
+void Workspace::release() {
+  for (auto& kv : bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  bufs.clear();
+}
+
+int HostStage::get(size_t need, void** out) {
+  if (bytes < need) {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMallocHost(&p, need);
+    if (e != cudaSuccess) { cudaGetLastError(); set_error("pinned staging: %s", cudaGetErrorString(e)); return MLIP_ERR_OOM; }
+    bytes = need;
+  }
+  *out = p;
+  return MLIP_OK;
+}
+HostStage::~HostStage() {
+  if (p) cudaFreeHost(p);
+}
+
+static int count_paths(int L, int Lsh, int* P0) {
+  int P = 0, p0 = 0;
+  for (int l1 = 0; l1 <= L; ++l1)
+    for (int l2 = 0; l2 <= Lsh; ++l2)
+      for (int l3 = 0; l3 <= L; ++l3)
+        if (l3 >= std::abs(l1 - l2) && l3 <= l1 + l2 && (l1 + l2 + l3) % 2 == 0) {
+          ++P;
+          if (l1 == 0) ++p0;
+        }
+  if (P0) *P0 = p0;
+  return P;
+}
+
+static int64_t weights_for(const mlip_model_desc& d, int P) {
+  const int64_t S = d.n_species, C = d.channels, H = d.hidden, NB = d.n_basis, L = d.l_max;
+  return S * C + d.n_layers * (NB * H + H * H + H * P * C + (L + 1) * C * C) + S * C + S;
+}
+
+static int validate_desc(const mlip_model_desc* d, int precision) {
+  if (!d) { set_error("null model description"); return MLIP_ERR_INVALID_ARG; }
+  if (d->n_species < 1 || d->n_species > 128) { set_error("n_species %d out of range", d->n_species); return MLIP_ERR_INVALID_ARG; }
+  if (d->n_layers < 1 || d->n_layers > 8) { set_error("n_layers %d out of range", d->n_layers); return MLIP_ERR_INVALID_ARG; }
+  if (d->channels != 16 && d->channels != 32 && d->channels != 64 && d->channels != 128) {
+    set_error("channels %d unsupported (16, 32, 64, 128)", d->channels);
+    return MLIP_ERR_INVALID_ARG;
+  }
+  if (d->l_max != 2 && d->l_max != 3) { set_error("l_max %d unsupported (2, 3)", d->l_max); return MLIP_ERR_INVALID_ARG; }
+  if (d->sh_l_max != 3) { set_error("sh_l_max must be 3"); return MLIP_ERR_INVALID_ARG; }
+  if (d->n_basis != 8) { set_error("n_basis must be 8"); return MLIP_ERR_INVALID_ARG; }
+  if (d->hidden != 32 && d->hidden != 64) { set_error("hidden %d unsupported (32, 64)", d->hidden); return MLIP_ERR_INVALID_ARG; }
+  if (d->envelope_p < 1 || d->envelope_p > 16) { set_error("envelope_p %d out of range", d->envelope_p); return MLIP_ERR_INVALID_ARG; }
+  if (!(d->cutoff > 0) || !(d->avg_num_neighbors > 0)) { set_error("cutoff and avg_num_neighbors must be positive"); return MLIP_ERR_INVALID_ARG; }
+  if (precision != MLIP_PREC_FP32 && precision != MLIP_PREC_BF16) { set_error("unknown precision %d", precision); return MLIP_ERR_INVALID_ARG; }
+  if (precision == MLIP_PREC_BF16 && d->channels != 128) { set_error("the BF16 form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
+  return MLIP_OK;
+}
+
+}  // namespace mlip
+
+using namespace mlip;
+
+extern "C" {
+
+const char* mlip_last_error(void) { return last_error(); }
+int mlip_version(void) { return 1; }
+
+int mlip_model_num_weights(const mlip_model_desc* desc, int64_t* n_weights) {
+  MLIP_TRY(validate_desc(desc, MLIP_PREC_FP32));
+  *n_weights = weights_for(*desc, count_paths(desc->l_max, desc->sh_l_max, nullptr));
+  return MLIP_OK;
+}
+
+int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t n_weights, int precision,
+                      mlip_model** out) {
+  if (!out || !weights) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  *out = nullptr;
+  MLIP_TRY(validate_desc(desc, precision));
+  int P0 = 0;
+  const int P = count_paths(desc->l_max, desc->sh_l_max, &P0);
+  const int64_t need = weights_for(*desc, P);
+  if (n_weights != need) { set_error("expected %lld weights, got %lld", (long long)need, (long long)n_weights); return MLIP_ERR_INVALID_ARG; }
+  mlip_model* M = new mlip_model();
+  M->S = desc->n_species; M->T = desc->n_layers; M->C = desc->channels; M->L = desc->l_max;
+  M->Lsh = desc->sh_l_max; M->NB = desc->n_basis; M->H = desc->hidden; M->p = desc->envelope_p;
+  M->rc = desc->cutoff; M->avg_nb = desc->avg_num_neighbors;
+  M->P = P; M->P0 = P0; M->D = (M->L + 1) * (M->L + 1);
+  M->precision = precision;
+  if (desc->masses) M->masses.assign(desc->masses, desc->masses + M->S);
+  M->host_weights.assign(weights, weights + n_weights);
+  cudaGetDevice(&M->device);
+  cudaError_t e = cudaMalloc(&M->d_weights, sizeof(float) * n_weights);
+  if (e != cudaSuccess) { cudaGetLastError(); delete M; set_error("cudaMalloc weights: %s", cudaGetErrorString(e)); return MLIP_ERR_OOM; }
+  e = cudaMemcpy(M->d_weights, weights, sizeof(float) * n_weights, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(M->d_weights); delete M; set_error("copy weights: %s", cudaGetErrorString(e)); return MLIP_ERR_CUDA; }
+  const float* q = M->d_weights;
+  const int64_t S = M->S, C = M->C, H = M->H, NB = M->NB;
+  M->W_emb = q; q += S * C;
+  for (int t = 0; t < M->T; ++t) {
+    M->W1.push_back(q); q += NB * H;
+    M->W2.push_back(q); q += H * H;
+    M->W3.push_back(q); q += H * P * C;
+    M->Wmix.push_back(q); q += (int64_t)(M->L + 1) * C * C;
+  }
+  M->W_out = q; q += S * C;
+  M->E0 = q; q += S;
+  *out = M;
+  return MLIP_OK;
+}
+
+int mlip_model_load(const char* path, int precision, mlip_model** out) {
+  if (!path || !out) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  std::ifstream f(path, std::ios::binary);
+  if (!f) { set_error("cannot open '%s'", path); return MLIP_ERR_NOT_FOUND; }
+  char magic[8];
+  uint32_t version = 0;
+  int32_t hyper[8];
+  double dh[2];
+  f.read(magic, 8);
+  f.read(reinterpret_cast<char*>(&version), 4);
+  f.read(reinterpret_cast<char*>(hyper), sizeof(hyper));
+  f.read(reinterpret_cast<char*>(dh), sizeof(dh));
+  if (!f || std::memcmp(magic, "MLIPPRM1", 8) != 0 || version != 1) { set_error("'%s' is not a parameter file", path); return MLIP_ERR_INVALID_ARG; }
+  if (hyper[0] < 1 || hyper[0] > 128) { set_error("bad species count"); return MLIP_ERR_INVALID_ARG; }
+  std::vector<double> masses(hyper[0]);
+  f.read(reinterpret_cast<char*>(masses.data()), sizeof(double) * masses.size());
+  int64_t count = 0;
+  f.read(reinterpret_cast<char*>(&count), 8);
+  if (!f || count < 0 || count > (int64_t)1 << 32) { set_error("truncated parameter file"); return MLIP_ERR_INVALID_ARG; }
+  std::vector<float> w(count);
+  f.read(reinterpret_cast<char*>(w.data()), sizeof(float) * count);
+  if (!f) { set_error("truncated parameter file"); return MLIP_ERR_INVALID_ARG; }
+  mlip_model_desc d{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dh[0], dh[1], masses.data()};
+  return mlip_model_create(&d, w.data(), count, precision, out);
+}
+
+int mlip_model_free(mlip_model* M) {
+  if (!M) return MLIP_OK;
+  cudaDeviceSynchronize();
+  M->ws.release();
+  if (M->d_weights) cudaFree(M->d_weights);
+  delete M;
+  return MLIP_OK;
+}
+
+int mlip_neighbors(const double* pos, int64_t n, const double cell[9], const uint8_t pbc[3], double cutoff,
+                   int32_t* recv, int32_t* send, int8_t* shift, int64_t capacity, int64_t* n_edges,
+                   int on_device, void* stream) {
+  if (!n_edges || !cell || !pbc || (n > 0 && !pos)) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  *n_edges = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  static thread_local Workspace* ws = nullptr;
+  if (!ws) ws = new Workspace();
+  const double* d_pos = pos;
+  if (!on_device && n > 0) {
+    double* dp = nullptr;
+    MLIP_TRY(ws->get("in.pos", (size_t)3 * n, &dp));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dp, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    d_pos = dp;
+  }
+  NeighborList nl;
+  MLIP_TRY(build_neighbors(*ws, d_pos, n, cell, pbc, cutoff, false, st, &nl));
+  *n_edges = nl.E;
+  if (nl.E > capacity) { set_error("neighbour capacity %lld < %lld edges", (long long)capacity, (long long)nl.E); return MLIP_ERR_CAPACITY; }
+  if (nl.E > 0) {
+    if (!recv || !send || !shift) { set_error("null output buffer"); return MLIP_ERR_INVALID_ARG; }
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    MLIP_CUDA_TRY(cudaMemcpyAsync(recv, nl.recv, sizeof(int32_t) * nl.E, k, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(send, nl.send, sizeof(int32_t) * nl.E, k, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(shift, nl.shift, 3 * nl.E, k, st));
+  }
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  return MLIP_OK;
+}
+
+}  // extern "C"
+
+namespace mlip {
+
+__global__ void check_inputs(int n, const double* __restrict__ pos, const int* __restrict__ species, int S,
+                             int* __restrict__ flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int z = species[i];
+  if (z < 0 || z >= S) atomicOr(flag, 1);
+  if (!isfinite(pos[3 * i]) || !isfinite(pos[3 * i + 1]) || !isfinite(pos[3 * i + 2])) atomicOr(flag, 2);
+}
+
+static double cell_volume(const double* h) {
+  return std::fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+                   h[2] * (h[3] * h[7] - h[4] * h[6]));
+}
+
+int energy_forces_plain(mlip_model* M, const double* d_pos, const int* d_species, int64_t n64, const double* cell,
+                        const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+  Workspace& ws = M->ws;
+  const int n = (int)n64, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H, P = M->P, P0 = M->P0;
+  const float s = (float)(1.0 / M->avg_nb);
+  int* flag = nullptr;
+  MLIP_TRY(ws.get("chk.flag", 1, &flag));
+  MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  check_inputs<<<(n + 255) / 256, 256, 0, st>>>(n, d_pos, d_species, M->S, flag);
+  MLIP_LAUNCH_CHECK();
+  NeighborList nl;
+  MLIP_TRY(build_neighbors(ws, d_pos, n, cell, pbc, M->rc, true, st, &nl));
+  int hflag = 0;
+  MLIP_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hflag & 1) { set_error("species index out of range"); return MLIP_ERR_INVALID_ARG; }
+  if (hflag & 2) { set_error("non-finite position"); return MLIP_ERR_INVALID_ARG; }
+  const int E = (int)nl.E;
+  const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)n * D * C;
+
+  CellArg ca{};
+  ca.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
+  for (int k = 0; k < 9; ++k) ca.h[k] = ca.any_pbc ? cell[k] : 0.0;
+
+  float4 *ev = nullptr, *g = nullptr;
+  float *z2T = nullptr, *m = nullptr, *Gm = nullptr, *Ga = nullptr, *Gb = nullptr, *dw = nullptr, *dz2 = nullptr,
+        *dY = nullptr, *dr = nullptr;
+  double* atom_e = nullptr;
+  MLIP_TRY(ws.get("ef.ev", Ec, &ev));
+  MLIP_TRY(ws.get("ef.g", Ec, &g));
+  MLIP_TRY(ws.get("ef.z2T", Ec * H, &z2T));
+  MLIP_TRY(ws.get("ef.m", ND, &m));
+  MLIP_TRY(ws.get("ef.Gm", ND, &Gm));
+  MLIP_TRY(ws.get("ef.Ga", ND, &Ga));
+  MLIP_TRY(ws.get("ef.Gb", ND, &Gb));
+  MLIP_TRY(ws.get("ef.dw", Ec * P * C, &dw));
+  MLIP_TRY(ws.get("ef.dz2", Ec * H, &dz2));
+  MLIP_TRY(ws.get("ef.dY", Ec * 16, &dY));
+  MLIP_TRY(ws.get("ef.dr", Ec, &dr));
+  MLIP_TRY(ws.get("ef.atom_e", (size_t)std::max(n, 1), &atom_e));
+  std::vector<float*> h(T + 1), u0(T), w(T);
+  for (int t = 0; t <= T; ++t) MLIP_TRY(ws.get("ef.h" + std::to_string(t), ND, &h[t]));
+  for (int t = 0; t < T; ++t) {
+    MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
+    MLIP_TRY(ws.get("ef.w" + std::to_string(t), Ec * (t == 0 ? P0 : P) * C, &w[t]));
+  }
+  double* energy = d_energy;
+
+  MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st));
+  MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
+  for (int t = 0; t < T; ++t) {
+    const bool first = t == 0;
+    const int PW = first ? P0 : P;
+    MLIP_TRY(launch_radial_fwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, z2T, E, st));
+    MLIP_TRY(launch_sgemm(true, false, E, PW * C, H, z2T, E, M->W3[t], P * C, w[t], PW * C, st));
+    MLIP_TRY(launch_tp_fwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], w[t], PW, s, m, st));
+    MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
+  }
+  MLIP_TRY(launch_energy(n, C, D, d_species, M->W_out, M->E0, h[T], atom_e, energy, st));
+  if (d_forces || d_stress) {
+    MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, Ga, st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(dr, 0, Ec * sizeof(float), st));
+    for (int t = T - 1; t >= 0; --t) {
+      const bool first = t == 0;
+      const int PW = first ? P0 : P;
+      MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], Gm, st));
+      MLIP_TRY(launch_tp_bwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], Gm, w[t], PW, s, Ga, Gb, dw, dY, st));
+      MLIP_TRY(launch_sgemm(false, true, E, H, PW * C, dw, PW * C, M->W3[t], P * C, dz2, H, st));
+      MLIP_TRY(launch_radial_bwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, st));
+      std::swap(Ga, Gb);
+    }
+    MLIP_TRY(launch_edge_grad(E, ev, dY, dr, g, st));
+    double* fbuf = d_forces;
+    if (!fbuf) MLIP_TRY(ws.get("ef.fscratch", (size_t)3 * std::max(n, 1), &fbuf));
+    const double vol = ca.any_pbc ? cell_volume(cell) : 1.0;
+    MLIP_TRY(launch_forces_virial(ws, n, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, 1.0 / vol, st));
+  }
+  return MLIP_OK;
+}
+
+}  // namespace mlip
+
+extern "C" int mlip_energy_forces(mlip_model* M, const double* pos, const int32_t* species, int64_t n,
+                                  const double cell[9], const uint8_t pbc[3], double* energy, double* forces,
+                                  double* stress, int on_device, void* stream) {
+  using namespace mlip;
+  if (!M || !pos || !species || !energy || !cell || !pbc) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  if (n < 1 || n > (1LL << 28)) { set_error("atom count %lld out of range", (long long)n); return MLIP_ERR_INVALID_ARG; }
+  if (stress && !(pbc[0] && pbc[1] && pbc[2])) { set_error("stress needs a fully periodic cell"); return MLIP_ERR_CELL; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != M->device) { set_error("model lives on device %d, current device is %d", M->device, cur); return MLIP_ERR_INVALID_ARG; }
+  Workspace& ws = M->ws;
+  const double* d_pos = pos;
+  const int* d_species = species;
+  double *d_energy = energy, *d_forces = forces, *d_stress = stress;
+  if (!on_device) {
+    if (!(pbc[0] || pbc[1] || pbc[2])) { /* cell ignored */ }
+    for (int64_t i = 0; i < n; ++i)
+      if (species[i] < 0 || species[i] >= M->S) { set_error("species[%lld] = %d out of range", (long long)i, species[i]); return MLIP_ERR_INVALID_ARG; }
+    double* dp = nullptr;
+    int* dz = nullptr;
+    MLIP_TRY(ws.get("in.pos", (size_t)3 * n, &dp));
+    MLIP_TRY(ws.get("in.species", (size_t)n, &dz));
+    MLIP_TRY(ws.get("out.energy", 1, &d_energy));
+    if (forces) MLIP_TRY(ws.get("out.forces", (size_t)3 * n, &d_forces));
+    if (stress) MLIP_TRY(ws.get("out.stress", 9, &d_stress));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dp, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dz, species, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    d_pos = dp;
+    d_species = dz;
+  }
+  int rc;
+  if (M->precision == MLIP_PREC_FP32) {
+    rc = energy_forces_plain(M, d_pos, d_species, n, cell, pbc, d_energy, d_forces, d_stress, st);
+  } else {
+    rc = energy_forces_fused(M, d_pos, d_species, n, cell, pbc, d_energy, d_forces, d_stress, st);
+  }
+  if (rc != MLIP_OK) return rc;
+  if (!on_device) {
+    MLIP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (forces) MLIP_CUDA_TRY(cudaMemcpyAsync(forces, d_forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (stress) MLIP_CUDA_TRY(cudaMemcpyAsync(stress, d_stress, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+    MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  } else {
+    MLIP_CUDA_TRY(cudaGetLastError());
+  }
+  return MLIP_OK;
+}

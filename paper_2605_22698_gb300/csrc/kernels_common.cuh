@@ -1,0 +1,135 @@
+// Device helpers shared by the interaction kernels.
+#pragma once
+
+#include <type_traits>
+
+#include "mlip_internal.cuh"
+
+namespace mlip {
+
+template <int L>
+struct NodeDims {
+  static constexpr int D = (L + 1) * (L + 1);
+};
+
+// Compile-time loop: f(std::integral_constant<int, k>) for k in [B, E).
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    if constexpr (E - B == 1) {
+      f(std::integral_constant<int, B>{});
+    } else {
+      constexpr int M = B + (E - B) / 2;
+      static_for<B, M>(f);
+      static_for<M, E>(f);
+    }
+  }
+}
+
+// Paths with l1 = 0 come first in lexicographic order.
+template <int L>
+struct PathInfo {
+  using T = CGTable<L>;
+  static constexpr int P = T::P;
+  static constexpr int NNZ = T::NNZ;
+  static constexpr int P0 = L + 1;                  // (0,0,0), (0,1,1), (0,2,2)[, (0,3,3)]
+  static constexpr int NNZ0 = T::off[L + 1];        // entries of the l1 = 0 paths
+};
+
+__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + expf(-x)); }
+__device__ __forceinline__ float silu_grad_f(float x) {
+  const float s = 1.0f / (1.0f + expf(-x));
+  return s * (1.0f + x * (1.0f - s));
+}
+
+// Bessel basis times the polynomial envelope, and its r-derivative.
+//   e_n = sqrt(2/rc) sin(n pi r / rc) / r * u(r/rc)
+//   u(x) = 1 - a x^p + b x^{p+1} - c x^{p+2},  a = (p+1)(p+2)/2, b = p(p+2), c = p(p+1)/2
+template <int NB, bool GRAD>
+__device__ __forceinline__ void radial_basis(float r, float rc, int p, float* e, float* de) {
+  const float x = r / rc;
+  float u = 0.0f, du = 0.0f;
+  if (x < 1.0f) {
+    float xp = 1.0f;
+    for (int k = 0; k < p - 1; ++k) xp *= x;  // x^{p-1}
+    const float a = 0.5f * (p + 1) * (p + 2), b = (float)(p * (p + 2)), c = 0.5f * p * (p + 1);
+    const float xp0 = xp * x;                 // x^p
+    u = 1.0f - a * xp0 + b * xp0 * x - c * xp0 * x * x;
+    du = (-a * p * xp + b * (p + 1) * xp0 - c * (p + 2) * xp0 * x) / rc;
+  }
+  const float pref = sqrtf(2.0f / rc);
+  const float inv_r = 1.0f / r;
+#pragma unroll
+  for (int n = 1; n <= NB; ++n) {
+    const float k = (float)n * 3.14159265358979f / rc;
+    float sn, cs;
+    sincosf(k * r, &sn, &cs);
+    const float B = pref * sn * inv_r;
+    e[n - 1] = B * u;
+    if (GRAD) {
+      const float dB = pref * (k * cs * inv_r - sn * inv_r * inv_r);
+      de[n - 1] = dB * u + B * du;
+    }
+  }
+}
+
+// Receiver range of block b out of G, balanced by edges: [first receiver with
+// row_ptr >= b*E/G, first receiver with row_ptr >= (b+1)*E/G); the last block
+// ends at n.
+__device__ __forceinline__ int lower_bound_i32(const int* a, int n, long long v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if ((long long)a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ void block_receivers(const int* row_ptr, int n, int b, int G, int* i0, int* i1) {
+  const long long E = row_ptr[n];
+  *i0 = (b == 0) ? 0 : lower_bound_i32(row_ptr, n + 1, (E * b) / G);
+  *i1 = (b == G - 1) ? n : lower_bound_i32(row_ptr, n + 1, (E * (b + 1)) / G);
+  if (*i0 > n) *i0 = n;
+  if (*i1 > n) *i1 = n;
+}
+
+// Sum 16 values over the 32 lanes; lane l ends with the total of component l >> 1.
+__device__ __forceinline__ float warp_reduce16(const float* v) {
+  const int lane = threadIdx.x & 31;
+  float u[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const bool hi = lane & 16;
+    float send = hi ? v[k] : v[k + 8];
+    float keep = hi ? v[k + 8] : v[k];
+    u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool hi = lane & 8;
+    float send = hi ? u[k] : u[k + 4];
+    float keep = hi ? u[k + 4] : u[k];
+    u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool hi = lane & 4;
+    float send = hi ? u[k] : u[k + 2];
+    float keep = hi ? u[k + 2] : u[k];
+    u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool hi = lane & 2;
+    float send = hi ? u[0] : u[1];
+    float keep = hi ? u[1] : u[0];
+    u[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  u[0] += __shfl_xor_sync(0xffffffffu, u[0], 1);
+  return u[0];
+}
+
+struct CellArg {
+  double h[9];
+  int any_pbc;
+};
+
+}  // namespace mlip

@@ -1,0 +1,105 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "mlip.h"
+#include "sh_poly.h"
+
+namespace mlip {
+
+// ----------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+const char* last_error();
+
+#define MLIP_CUDA_TRY(expr)                                                                    \
+  do {                                                                                         \
+    cudaError_t e__ = (expr);                                                                  \
+    if (e__ != cudaSuccess) {                                                                  \
+      ::mlip::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e__), __FILE__, __LINE__); \
+      return e__ == cudaErrorMemoryAllocation ? MLIP_ERR_OOM : MLIP_ERR_CUDA;                  \
+    }                                                                                          \
+  } while (0)
+
+#define MLIP_TRY(expr)              \
+  do {                              \
+    int r__ = (expr);               \
+    if (r__ != MLIP_OK) return r__; \
+  } while (0)
+
+#define MLIP_LAUNCH_CHECK() MLIP_CUDA_TRY(cudaGetLastError())
+
+// ------------------------------------------------------- coupling tables
+template <int L>
+struct CGTable;
+#include "cg_tables.inc"
+
+// ------------------------------------------------------------ workspace
+// Grow-only named device buffers, owned by a model (or a neighbour call).
+struct Workspace {
+  struct Buf { void* p = nullptr; size_t bytes = 0; };
+  std::map<std::string, Buf> bufs;
+  int get(const std::string& name, size_t bytes, void** out);
+  template <class T>
+  int get(const std::string& name, size_t count, T** out) {
+    void* p = nullptr;
+    int rc = get(name, count * sizeof(T) + 16, &p);
+    *out = static_cast<T*>(p);
+    return rc;
+  }
+  void release();
+  ~Workspace() { release(); }
+};
+
+// Pinned host staging (grow-only).
+struct HostStage {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int get(size_t need, void** out);
+  ~HostStage();
+};
+
+// --------------------------------------------------------- neighbours
+constexpr int kMaxDegreeLimit = 4096;
+
+struct NeighborList {
+  int64_t n = 0, E = 0;
+  int32_t* row_ptr = nullptr;   // [n + 1], receiver segments
+  int32_t* recv = nullptr;      // [E]
+  int32_t* send = nullptr;      // [E]
+  int8_t* shift = nullptr;      // [E * 3]
+  int32_t* rev = nullptr;       // [E] index of the reverse edge (j <- i, -S)
+  unsigned long long* keys = nullptr;  // [E] sorted (send, S) keys per segment
+};
+
+// Builds the sorted list on the device.  Synchronises `st` once to read E.
+int build_neighbors(Workspace& ws, const double* d_pos, int64_t n, const double* cell,
+                    const uint8_t* pbc, double rc, bool want_rev, cudaStream_t st, NeighborList* out);
+
+// exclusive scan of n int32 values into out[0..n] (out[n] = total)
+int exclusive_scan_i32(Workspace& ws, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+
+}  // namespace mlip
+
+// ------------------------------------------------------------- the model
+struct mlip_model {
+  int S = 0, T = 0, C = 0, L = 0, Lsh = 3, NB = 8, H = 0, p = 6;
+  double rc = 5.0, avg_nb = 1.0;
+  int P = 0, P0 = 0, D = 0;  // paths, paths with l1 = 0, node components
+  int precision = MLIP_PREC_FP32;
+  std::vector<double> masses;
+  std::vector<float> host_weights;
+  float* d_weights = nullptr;  // one allocation
+  const float* W_emb = nullptr;
+  const float* W_out = nullptr;
+  const float* E0 = nullptr;
+  std::vector<const float*> W1, W2, W3, Wmix;
+  int device = 0;
+  mlip::Workspace ws;
+  mlip::HostStage stage;
+};

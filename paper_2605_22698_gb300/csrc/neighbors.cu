@@ -1,0 +1,484 @@
+// Cell-list neighbour build on the device (the Graph construction from a
+// ChemicalSystem with a distance cutoff, App. A of arxiv 2605.22698; the
+// paper's models use graph_cutoff_angstrom = 5 in every hyperparameter table).
+//
+// Pipeline (all FP64 geometry, integer binning):
+//   nl_frac     fractional coordinates s = r h^-1; periodic axes split into an
+//               integer image n = floor(s) and a wrapped part f = s - n;
+//               extents of open axes reduced into a bounding box
+//   nl_setup    one thread: bins per axis (each bin at least rc (1 + 1e-6) wide
+//               perpendicular to its faces), search reach, cap on bin count
+//   nl_bin      bin of each atom, counts; scan; nl_scatter atoms into bins
+//   nl_pairs    one thread per receiver: every candidate (j, S) from the bins
+//               within reach, S = q - n_j + n_i, exact test
+//                 d2 = (dx*dx + dy*dy) + dz*dz < rc^2 with dx = (x_j - x_i) + sx,
+//                 sx = (S0 h00 + S1 h10) + S2 h20, round-to-nearest, no FMA,
+//               keys (j, S) appended to a per-receiver slab
+//   scan        receiver degrees -> row_ptr
+//   nl_sort     one warp per receiver: bitonic sort of its keys in shared
+//               memory, compact write of recv / send / shift
+//   nl_rev      per edge: binary search of (i, -S) in the sender's segment
+#include <cmath>
+
+#include "mlip_internal.cuh"
+
+namespace mlip {
+namespace {
+
+struct Grid {
+  double inv[9];   // s_k = sum_a r_a inv[a][k]
+  double h[9];     // rows = lattice vectors (zero for open systems)
+  double w[3];     // perpendicular width of the cell per axis (1 for open systems)
+  double lo[3], bsz[3];
+  int pbc[3], nb[3], reach[3];
+  double rc, rc2;
+  int max_bins, maxdeg;
+  int any_pbc;
+};
+
+__device__ __forceinline__ long long dbl_order(double x) {
+  long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double order_dbl(long long b) {
+  return __longlong_as_double(b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL));
+}
+
+__global__ void nl_frac(const double* __restrict__ pos, int n, const Grid* __restrict__ g,
+                        double* __restrict__ frac, int* __restrict__ img, long long* __restrict__ bbox) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double f[3] = {0, 0, 0};
+  bool valid = i < n;
+  if (valid) {
+    const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    for (int k = 0; k < 3; ++k) {
+      double s = __dadd_rn(__dadd_rn(__dmul_rn(x, g->inv[k]), __dmul_rn(y, g->inv[3 + k])), __dmul_rn(z, g->inv[6 + k]));
+      if (g->pbc[k]) {
+        double fl = floor(s);
+        img[3 * i + k] = (int)fl;
+        f[k] = s - fl;
+      } else {
+        img[3 * i + k] = 0;
+        f[k] = s;
+      }
+      frac[3 * i + k] = f[k];
+    }
+  }
+  // bounding box of open axes
+  for (int k = 0; k < 3; ++k) {
+    long long mn = valid ? dbl_order(f[k]) : LLONG_MAX;
+    long long mx = valid ? dbl_order(f[k]) : LLONG_MIN;
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&bbox[2 * k], mn);
+      atomicMax(&bbox[2 * k + 1], mx);
+    }
+  }
+}
+
+__global__ void nl_setup(Grid* g, const long long* bbox) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double margin = 1.0 + 1e-6;
+  double ext[3];
+  for (int k = 0; k < 3; ++k) {
+    if (g->pbc[k]) {
+      g->lo[k] = 0.0;
+      ext[k] = 1.0;
+    } else {
+      double lo = order_dbl(bbox[2 * k]), hi = order_dbl(bbox[2 * k + 1]);
+      g->lo[k] = lo;
+      ext[k] = fmax(hi - lo, 1e-9);
+    }
+    double minsz = g->rc * margin / g->w[k];
+    double nbd = floor(ext[k] / minsz);
+    nbd = fmin(fmax(nbd, 1.0), 1048576.0);
+    g->nb[k] = (int)nbd;
+  }
+  // cap the bin count (keeps the bin arrays bounded); coarser bins stay correct
+  while ((long long)g->nb[0] * g->nb[1] * g->nb[2] > g->max_bins) {
+    int k = 0;
+    if (g->nb[1] > g->nb[k]) k = 1;
+    if (g->nb[2] > g->nb[k]) k = 2;
+    g->nb[k] = max(1, g->nb[k] / 2);
+  }
+  for (int k = 0; k < 3; ++k) {
+    g->bsz[k] = ext[k] / g->nb[k];
+    double span = g->bsz[k] * g->w[k];  // perpendicular width of one bin
+    int r = (int)floor(g->rc / span * margin) + 1;
+    if (!g->pbc[k]) r = min(r, g->nb[k]);
+    g->reach[k] = r;
+  }
+}
+
+__device__ __forceinline__ void bin_coords(const Grid* g, const double* f, int* b) {
+  for (int k = 0; k < 3; ++k) {
+    double t = floor((f[k] - g->lo[k]) / g->bsz[k]);
+    int bi = (int)fmin(fmax(t, 0.0), (double)(g->nb[k] - 1));
+    b[k] = bi;
+  }
+}
+
+__global__ void nl_bin(int n, const Grid* __restrict__ g, const double* __restrict__ frac,
+                       int* __restrict__ bin_of, int* __restrict__ counts) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double f[3] = {frac[3 * i], frac[3 * i + 1], frac[3 * i + 2]};
+  int b[3];
+  bin_coords(g, f, b);
+  int bin = (b[0] * g->nb[1] + b[1]) * g->nb[2] + b[2];
+  bin_of[i] = bin;
+  atomicAdd(&counts[bin], 1);
+}
+
+__global__ void nl_scatter(int n, const int* __restrict__ bin_of, const int* __restrict__ bin_start,
+                           int* __restrict__ cursor, int* __restrict__ bin_atoms) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int b = bin_of[i];
+  int slot = atomicAdd(&cursor[b], 1);
+  bin_atoms[bin_start[b] + slot] = i;
+}
+
+__device__ __forceinline__ unsigned long long make_key(int j, int s0, int s1, int s2) {
+  return ((unsigned long long)(unsigned)j << 24) | ((unsigned long long)(s0 + 128) << 16) |
+         ((unsigned long long)(s1 + 128) << 8) | (unsigned long long)(s2 + 128);
+}
+
+// flags[0]: max degree seen; flags[1]: |S| > 127 seen
+__global__ void nl_pairs(int n, const Grid* __restrict__ g, const double* __restrict__ pos,
+                         const double* __restrict__ frac, const int* __restrict__ img,
+                         const int* __restrict__ bin_start, const int* __restrict__ bin_atoms,
+                         unsigned long long* __restrict__ slab, int* __restrict__ deg, int* __restrict__ flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int maxdeg = g->maxdeg;
+  double f[3] = {frac[3 * i], frac[3 * i + 1], frac[3 * i + 2]};
+  int b[3];
+  bin_coords(g, f, b);
+  const int ni0 = img[3 * i], ni1 = img[3 * i + 1], ni2 = img[3 * i + 2];
+  const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+  const double* h = g->h;
+  const double rc2 = g->rc2;
+  int cnt = 0;
+  bool bad_shift = false;
+  for (int d0 = -g->reach[0]; d0 <= g->reach[0]; ++d0) {
+    int c0 = b[0] + d0, q0 = 0;
+    if (g->pbc[0]) { q0 = (int)floor((double)c0 / g->nb[0]); c0 -= q0 * g->nb[0]; }
+    else if (c0 < 0 || c0 >= g->nb[0]) continue;
+    for (int d1 = -g->reach[1]; d1 <= g->reach[1]; ++d1) {
+      int c1 = b[1] + d1, q1 = 0;
+      if (g->pbc[1]) { q1 = (int)floor((double)c1 / g->nb[1]); c1 -= q1 * g->nb[1]; }
+      else if (c1 < 0 || c1 >= g->nb[1]) continue;
+      for (int d2 = -g->reach[2]; d2 <= g->reach[2]; ++d2) {
+        int c2 = b[2] + d2, q2 = 0;
+        if (g->pbc[2]) { q2 = (int)floor((double)c2 / g->nb[2]); c2 -= q2 * g->nb[2]; }
+        else if (c2 < 0 || c2 >= g->nb[2]) continue;
+        const int bin = (c0 * g->nb[1] + c1) * g->nb[2] + c2;
+        const int beg = bin_start[bin], end = bin_start[bin + 1];
+        for (int t = beg; t < end; ++t) {
+          const int j = bin_atoms[t];
+          const int S0 = q0 - img[3 * j] + ni0;
+          const int S1 = q1 - img[3 * j + 1] + ni1;
+          const int S2 = q2 - img[3 * j + 2] + ni2;
+          if (j == i && S0 == 0 && S1 == 0 && S2 == 0) continue;
+          double sx = 0.0, sy = 0.0, sz = 0.0;
+          if (g->any_pbc) {
+            sx = __dadd_rn(__dadd_rn(__dmul_rn((double)S0, h[0]), __dmul_rn((double)S1, h[3])), __dmul_rn((double)S2, h[6]));
+            sy = __dadd_rn(__dadd_rn(__dmul_rn((double)S0, h[1]), __dmul_rn((double)S1, h[4])), __dmul_rn((double)S2, h[7]));
+            sz = __dadd_rn(__dadd_rn(__dmul_rn((double)S0, h[2]), __dmul_rn((double)S1, h[5])), __dmul_rn((double)S2, h[8]));
+          }
+          const double dx = __dadd_rn(__dsub_rn(pos[3 * j], xi), sx);
+          const double dy = __dadd_rn(__dsub_rn(pos[3 * j + 1], yi), sy);
+          const double dz = __dadd_rn(__dsub_rn(pos[3 * j + 2], zi), sz);
+          const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+          if (d2 < rc2) {
+            if (S0 < -127 || S0 > 127 || S1 < -127 || S1 > 127 || S2 < -127 || S2 > 127) bad_shift = true;
+            if (cnt < maxdeg) slab[(size_t)i * maxdeg + cnt] = make_key(j, S0, S1, S2);
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  deg[i] = cnt;
+  if (cnt > maxdeg) atomicMax(&flags[0], cnt);
+  if (bad_shift) atomicOr(&flags[1], 1);
+}
+
+// One warp per receiver; dynamic shared memory: warps_per_block * cap keys.
+__global__ void nl_sort(int n, int cap, const unsigned long long* __restrict__ slab, int maxdeg,
+                        const int* __restrict__ row_ptr, unsigned long long* __restrict__ keys,
+                        int* __restrict__ recv, int* __restrict__ send, int8_t* __restrict__ shift) {
+  extern __shared__ unsigned long long sk[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int i = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (i >= n) return;
+  unsigned long long* s = sk + (size_t)wib * cap;
+  const int beg = row_ptr[i], d = row_ptr[i + 1] - beg;
+  int m = 1;
+  while (m < d) m <<= 1;
+  for (int t = lane; t < m; t += 32) s[t] = t < d ? slab[(size_t)i * maxdeg + t] : ~0ULL;
+  __syncwarp();
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < m; t += 32) {
+        int ixj = t ^ j;
+        if (ixj > t) {
+          unsigned long long a = s[t], b = s[ixj];
+          bool up = (t & k) == 0;
+          if ((a > b) == up) { s[t] = b; s[ixj] = a; }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (int t = lane; t < d; t += 32) {
+    unsigned long long key = s[t];
+    keys[beg + t] = key;
+    recv[beg + t] = i;
+    send[beg + t] = (int)(key >> 24);
+    shift[3 * (beg + t) + 0] = (int8_t)((int)((key >> 16) & 0xFF) - 128);
+    shift[3 * (beg + t) + 1] = (int8_t)((int)((key >> 8) & 0xFF) - 128);
+    shift[3 * (beg + t) + 2] = (int8_t)((int)(key & 0xFF) - 128);
+  }
+}
+
+__global__ void nl_rev(const int* __restrict__ E_ptr, const int* __restrict__ row_ptr,
+                       const int* __restrict__ recv, const int* __restrict__ send,
+                       const int8_t* __restrict__ shift, const unsigned long long* __restrict__ keys,
+                       int* __restrict__ rev, int* __restrict__ flags) {
+  const int E = *E_ptr;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const int i = recv[e], j = send[e];
+    const unsigned long long want = make_key(i, -shift[3 * e], -shift[3 * e + 1], -shift[3 * e + 2]);
+    int lo = row_ptr[j], hi = row_ptr[j + 1];
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (keys[mid] < want) lo = mid + 1; else hi = mid;
+    }
+    if (lo < row_ptr[j + 1] && keys[lo] == want) rev[e] = lo;
+    else { rev[e] = e; atomicOr(&flags[2], 1); }
+  }
+}
+
+// ------------------------------------------------------------ scan
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+__device__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    int s = lane < nw ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  int off = w ? warp_sums[w - 1] : 0;
+  int res = off + x - v;
+  *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return res;
+}
+
+__global__ void scan_local(const int* __restrict__ in, int* __restrict__ out, long long n, int* __restrict__ bsum) {
+  __shared__ int ws[32];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  int v[kScanItems], s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    s += v[k];
+  }
+  int tot;
+  int ex = block_exclusive_scan(s, ws, &tot);
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void scan_blocks(int* __restrict__ bsum, int nb, int* __restrict__ total_out) {
+  __shared__ int ws[32];
+  int carry = 0;
+  for (int base = 0; base < nb; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int v = i < nb ? bsum[i] : 0;
+    int tot;
+    int ex = block_exclusive_scan(v, ws, &tot);
+    if (i < nb) bsum[i] = ex + carry;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void scan_add(int* __restrict__ out, long long n, const int* __restrict__ bsum) {
+  const long long base = (long long)blockIdx.x * kScanTile;
+  const int add = bsum[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x)
+    if (base + k < n) out[base + k] += add;
+}
+
+}  // namespace
+
+int exclusive_scan_i32(Workspace& ws, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
+  int nb = (int)((n + kScanTile - 1) / kScanTile);
+  if (nb < 1) nb = 1;
+  int* bsum = nullptr;
+  MLIP_TRY(ws.get("scan.bsum", (size_t)nb, &bsum));
+  scan_local<<<nb, kScanThreads, 0, st>>>(in, out, n, bsum);
+  scan_blocks<<<1, 1024, 0, st>>>(bsum, nb, out + n);
+  scan_add<<<nb, kScanThreads, 0, st>>>(out, n, bsum);
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+static bool invert3(const double* h, double* inv, double* det_out) {
+  double det = h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
+               h[2] * (h[3] * h[7] - h[4] * h[6]);
+  *det_out = det;
+  if (!(std::fabs(det) > 1e-12)) return false;
+  double id = 1.0 / det;
+  inv[0] = (h[4] * h[8] - h[5] * h[7]) * id;
+  inv[1] = (h[2] * h[7] - h[1] * h[8]) * id;
+  inv[2] = (h[1] * h[5] - h[2] * h[4]) * id;
+  inv[3] = (h[5] * h[6] - h[3] * h[8]) * id;
+  inv[4] = (h[0] * h[8] - h[2] * h[6]) * id;
+  inv[5] = (h[2] * h[3] - h[0] * h[5]) * id;
+  inv[6] = (h[3] * h[7] - h[4] * h[6]) * id;
+  inv[7] = (h[1] * h[6] - h[0] * h[7]) * id;
+  inv[8] = (h[0] * h[4] - h[1] * h[3]) * id;
+  return true;
+}
+
+int build_neighbors(Workspace& ws, const double* d_pos, int64_t n64, const double* cell,
+                    const uint8_t* pbc, double rc, bool want_rev, cudaStream_t st, NeighborList* out) {
+  if (n64 < 0 || n64 > (1LL << 30)) { set_error("neighbors: bad atom count %lld", (long long)n64); return MLIP_ERR_INVALID_ARG; }
+  if (!(rc > 0)) { set_error("neighbors: cutoff must be positive"); return MLIP_ERR_INVALID_ARG; }
+  const int n = (int)n64;
+  out->n = n;
+  Grid hg{};
+  hg.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
+  if (hg.any_pbc) {
+    double det;
+    if (!invert3(cell, hg.inv, &det)) { set_error("neighbors: singular cell with a periodic axis"); return MLIP_ERR_CELL; }
+    for (int k = 0; k < 9; ++k) hg.h[k] = cell[k];
+    for (int k = 0; k < 3; ++k) {
+      // width = 1 / |column k of h^-1|
+      double c2 = hg.inv[k] * hg.inv[k] + hg.inv[3 + k] * hg.inv[3 + k] + hg.inv[6 + k] * hg.inv[6 + k];
+      hg.w[k] = 1.0 / std::sqrt(c2);
+      hg.pbc[k] = pbc[k] ? 1 : 0;
+    }
+  } else {
+    for (int k = 0; k < 9; ++k) { hg.inv[k] = (k % 4 == 0) ? 1.0 : 0.0; hg.h[k] = 0.0; }
+    for (int k = 0; k < 3; ++k) { hg.w[k] = 1.0; hg.pbc[k] = 0; }
+  }
+  hg.rc = rc;
+  hg.rc2 = rc * rc;
+  hg.max_bins = (int)std::min<int64_t>(std::max<int64_t>(64, 4 * (int64_t)n), 1 << 24);
+
+  Grid* dg = nullptr;
+  double* frac = nullptr;
+  int *img = nullptr, *bin_of = nullptr, *counts = nullptr, *bin_start = nullptr, *cursor = nullptr,
+      *bin_atoms = nullptr, *deg = nullptr, *flags = nullptr;
+  long long* bbox = nullptr;
+  const int nn = std::max(n, 1);
+  MLIP_TRY(ws.get("nl.grid", 1, &dg));
+  MLIP_TRY(ws.get("nl.frac", (size_t)3 * nn, &frac));
+  MLIP_TRY(ws.get("nl.img", (size_t)3 * nn, &img));
+  MLIP_TRY(ws.get("nl.bin_of", (size_t)nn, &bin_of));
+  MLIP_TRY(ws.get("nl.counts", (size_t)hg.max_bins + 1, &counts));
+  MLIP_TRY(ws.get("nl.bin_start", (size_t)hg.max_bins + 1, &bin_start));
+  MLIP_TRY(ws.get("nl.cursor", (size_t)hg.max_bins + 1, &cursor));
+  MLIP_TRY(ws.get("nl.bin_atoms", (size_t)nn, &bin_atoms));
+  MLIP_TRY(ws.get("nl.deg", (size_t)nn, &deg));
+  MLIP_TRY(ws.get("nl.flags", 4, &flags));
+  MLIP_TRY(ws.get("nl.bbox", 6, &bbox));
+  MLIP_TRY(ws.get("nl.row_ptr", (size_t)nn + 1, &out->row_ptr));
+
+  int maxdeg = 256;
+  const int threads = 128;
+  const int blocks = (n + threads - 1) / threads;
+  for (int attempt = 0; attempt < 6; ++attempt) {
+    hg.maxdeg = maxdeg;
+    long long bb_init[6] = {LLONG_MAX, LLONG_MIN, LLONG_MAX, LLONG_MIN, LLONG_MAX, LLONG_MIN};
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dg, &hg, sizeof(Grid), cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(bbox, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(counts, 0, ((size_t)hg.max_bins + 1) * sizeof(int), st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(cursor, 0, ((size_t)hg.max_bins + 1) * sizeof(int), st));
+    if (n > 0) {
+      nl_frac<<<blocks, threads, 0, st>>>(d_pos, n, dg, frac, img, bbox);
+      nl_setup<<<1, 1, 0, st>>>(dg, bbox);
+      nl_bin<<<blocks, threads, 0, st>>>(n, dg, frac, bin_of, counts);
+    } else {
+      nl_setup<<<1, 1, 0, st>>>(dg, bbox);
+    }
+    MLIP_LAUNCH_CHECK();
+    MLIP_TRY(exclusive_scan_i32(ws, counts, bin_start, hg.max_bins, st));
+    unsigned long long* slab = nullptr;
+    MLIP_TRY(ws.get("nl.slab", (size_t)nn * maxdeg, &slab));
+    if (n > 0) {
+      nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms);
+      nl_pairs<<<blocks, threads, 0, st>>>(n, dg, d_pos, frac, img, bin_start, bin_atoms, slab, deg, flags);
+      MLIP_LAUNCH_CHECK();
+    }
+    MLIP_TRY(exclusive_scan_i32(ws, deg, out->row_ptr, n, st));
+    int hflags[4];
+    int E32 = 0;
+    MLIP_CUDA_TRY(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(&E32, out->row_ptr + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hflags[1]) { set_error("neighbors: image index beyond +-127"); return MLIP_ERR_INVALID_ARG; }
+    if (hflags[0] > maxdeg) {
+      if (hflags[0] > kMaxDegreeLimit) {
+        set_error("neighbors: a receiver has %d neighbours (limit %d)", hflags[0], kMaxDegreeLimit);
+        return MLIP_ERR_INVALID_ARG;
+      }
+      while (maxdeg < hflags[0]) maxdeg *= 2;
+      continue;
+    }
+    out->E = E32;
+    const size_t Ecap = (size_t)std::max(E32, 1);
+    MLIP_TRY(ws.get("nl.keys", Ecap, &out->keys));
+    MLIP_TRY(ws.get("nl.recv", Ecap, &out->recv));
+    MLIP_TRY(ws.get("nl.send", Ecap, &out->send));
+    MLIP_TRY(ws.get("nl.shift", 3 * Ecap, &out->shift));
+    if (n > 0) {
+      int cap = 32;
+      while (cap < maxdeg) cap <<= 1;
+      const int wpb = 4;
+      size_t smem = (size_t)wpb * cap * sizeof(unsigned long long);
+      if (smem > 48 * 1024)
+        MLIP_CUDA_TRY(cudaFuncSetAttribute(nl_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      nl_sort<<<(n + wpb - 1) / wpb, 32 * wpb, smem, st>>>(n, cap, slab, maxdeg, out->row_ptr, out->keys,
+                                                          out->recv, out->send, out->shift);
+      MLIP_LAUNCH_CHECK();
+    }
+    if (want_rev) {
+      MLIP_TRY(ws.get("nl.rev", Ecap, &out->rev));
+      if (E32 > 0) {
+        nl_rev<<<std::min((E32 + 255) / 256, 4096), 256, 0, st>>>(out->row_ptr + n, out->row_ptr, out->recv,
+                                                                   out->send, out->shift, out->keys, out->rev, flags);
+        MLIP_LAUNCH_CHECK();
+      }
+    }
+    return MLIP_OK;
+  }
+  set_error("neighbors: degree capacity retries exhausted");
+  return MLIP_ERR_CAPACITY;
+}
+
+}  // namespace mlip

@@ -1,0 +1,177 @@
+// Node-level and reduction kernels shared by both compute forms:
+// species embedding, readout and FP64 energy sum, dE/dh^T initialisation,
+// edge gradients from dE/dY and dE/dr, forces and virial in FP64.
+#include <algorithm>
+
+#include "kernels_common.cuh"
+
+namespace mlip {
+namespace {
+
+// h^0: scalars from the species embedding, l > 0 zero.
+__global__ void embed(int n, int C, int D, const int* __restrict__ species, const float* __restrict__ W_emb,
+                      float* __restrict__ h) {
+  const size_t total = (size_t)n * D * C;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(k % C);
+    const size_t rest = k / C;
+    const int d = (int)(rest % D);
+    const int i = (int)(rest / D);
+    h[k] = d == 0 ? W_emb[(size_t)species[i] * C + c] : 0.0f;
+  }
+}
+
+// dE/dh^T: W_out[z_i] on the scalars, zero elsewhere.
+__global__ void grad_init(int n, int C, int D, const int* __restrict__ species, const float* __restrict__ W_out,
+                          float* __restrict__ G) {
+  const size_t total = (size_t)n * D * C;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(k % C);
+    const size_t rest = k / C;
+    const int d = (int)(rest % D);
+    const int i = (int)(rest / D);
+    G[k] = d == 0 ? W_out[(size_t)species[i] * C + c] : 0.0f;
+  }
+}
+
+// E_i = sum_c W_out[z_i][c] h_i,0[c] + E0[z_i]  (one warp per atom, FP32 dot, FP64 result)
+__global__ void readout(int n, int C, int D, const int* __restrict__ species, const float* __restrict__ W_out,
+                        const float* __restrict__ E0, const float* __restrict__ h, double* __restrict__ atom_e) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const int z = species[i];
+  float acc = 0.0f;
+  for (int c = lane; c < C; c += 32) acc = fmaf(W_out[(size_t)z * C + c], h[(size_t)i * D * C + c], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) atom_e[i] = (double)acc + (double)E0[z];
+}
+
+// Deterministic FP64 sum of n values (one block).
+__global__ void sum_f64(int n, const double* __restrict__ x, double* __restrict__ out) {
+  __shared__ double part[32];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) acc += x[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) *out = v;
+  }
+}
+
+// g_e = dr r^ + (1/r)(I - r^ r^T) grad(Y . dY)
+__global__ void edge_grad(int E, const float4* __restrict__ ev, const float* __restrict__ dY,
+                          const float* __restrict__ dr, float4* __restrict__ g) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const float4 v = ev[e];
+    const float ir = 1.0f / v.w;
+    const float x = v.x * ir, y = v.y * ir, z = v.z * ir;
+    float d[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) d[k] = dY[(size_t)e * 16 + k];
+    float gx, gy, gz;
+    sh3_vjp<float>(x, y, z, d, gx, gy, gz);
+    const float rad = gx * x + gy * y + gz * z;
+    gx = (gx - rad * x) * ir;
+    gy = (gy - rad * y) * ir;
+    gz = (gz - rad * z) * ir;
+    const float dre = dr[e];
+    g[e] = make_float4(gx + dre * x, gy + dre * y, gz + dre * z, 0.0f);
+  }
+}
+
+// F_i = sum_{e in seg(i)} (g_e - g_rev(e)) in FP64; per-block virial partials
+// sum_e x_e (x) g_e (FP64).
+__global__ void forces_virial(int n, const int* __restrict__ row_ptr, const int* __restrict__ rev,
+                              const float4* __restrict__ g, const float4* __restrict__ ev,
+                              double* __restrict__ forces, double* __restrict__ vir_part) {
+  __shared__ double part[9][32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (i < n) {
+    double f0 = 0, f1 = 0, f2 = 0;
+    for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const float4 a = g[e], b = g[rev[e]], x = ev[e];
+      f0 += (double)a.x - (double)b.x;
+      f1 += (double)a.y - (double)b.y;
+      f2 += (double)a.z - (double)b.z;
+      const double xe[3] = {x.x, x.y, x.z}, ge[3] = {a.x, a.y, a.z};
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[3 * p + q] += xe[p] * ge[q];
+    }
+    forces[3 * i] = f0;
+    forces[3 * i + 1] = f1;
+    forces[3 * i + 2] = f2;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) part[k][w] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double s = 0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += part[threadIdx.x][ww];
+    vir_part[(size_t)blockIdx.x * 9 + threadIdx.x] = s;
+  }
+}
+
+__global__ void virial_finish(int nb, const double* __restrict__ vir_part, double inv_vol, double* __restrict__ stress) {
+  const int k = threadIdx.x;
+  if (k >= 9) return;
+  double s = 0;
+  for (int b = 0; b < nb; ++b) s += vir_part[(size_t)b * 9 + k];
+  stress[k] = s * inv_vol;
+}
+
+}  // namespace
+
+int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  embed<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_emb, h);
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  grad_init<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_out, G);
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+int launch_energy(int n, int C, int D, const int* species, const float* W_out, const float* E0, const float* h,
+                  double* atom_e, double* energy, cudaStream_t st) {
+  if (n > 0) readout<<<(n + 7) / 8, 256, 0, st>>>(n, C, D, species, W_out, E0, h, atom_e);
+  sum_f64<<<1, 1024, 0, st>>>(n, atom_e, energy);
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, float4* g, cudaStream_t st) {
+  if (E <= 0) return MLIP_OK;
+  edge_grad<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, dY, dr, g);
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+int launch_forces_virial(Workspace& ws, int n, const int* row_ptr, const int* rev, const float4* g,
+                         const float4* ev, double* forces, double* stress, double inv_vol, cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  const int nb = (n + 127) / 128;
+  double* part = nullptr;
+  MLIP_TRY(ws.get("fv.part", (size_t)nb * 9, &part));
+  forces_virial<<<nb, 128, 0, st>>>(n, row_ptr, rev, g, ev, forces, part);
+  if (stress) virial_finish<<<1, 32, 0, st>>>(nb, part, inv_vol, stress);
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+}  // namespace mlip
