@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: energy+force atom-steps/s of the equivariant interaction layer.
+
+Workload (default): a periodic water-like box, 1000 H2O = 3000 atoms in a
+31.0 A cube (random orientations, O-O >= 2.5 A), the two-layer, 128-channel,
+l <= 2 model with l <= 3 edge harmonics and a 64-wide radial MLP (random
+weights).  One step = one full evaluation through the library's C ABI with the
+positions resident on the GPU: neighbour list (cell list), edge geometry,
+harmonics, radial basis and MLP, tensor product and segmented sum, channel
+mixes, readout and FP64 energy, then the adjoint: forces and virial stress.
+The synthetic box stands in for the paper's MD benchmark systems (Table
+tbl:performance), which are not available here.
+
+Between timed steps L2 is flushed by writing a 512 MB buffer (outside the
+per-step CUDA-event pairs).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "energy+force atom-steps/s"
+UNIT = "atom-steps/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+# FP32 ALU peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
+# lanes x 2 flop (FMA) x 2.07 GHz.
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0])); mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(name: str, rank: int = 0):
+    if name == "water3000":
+        spec = synth.model_spec("water")
+        sysm = synth.water_box(1000, 31.0, seed=2 + 1000 * rank)
+        return spec, synth.make_weights(spec, 21), sysm
+    if name == "fcc108k":
+        spec = synth.model_spec("fcc")
+        return spec, synth.make_weights(spec, 31), synth.fcc((30, 30, 30), seed=3 + 1000 * rank)
+    if name == "cluster64":
+        spec = synth.model_spec("small")
+        return spec, synth.make_weights(spec, 7), synth.cluster64(1 + rank)
+    raise ValueError(name)
+
+
+def sample_workload(name: str):
+    """Bounded CPU sample of the same workload for the oracle baseline."""
+    if name == "water3000":
+        spec = synth.model_spec("water")
+        return spec, synth.make_weights(spec, 21), synth.water_box(100, synth.water_side_for(100), seed=2), \
+            "100 H2O (300 atoms) periodic box at the same density, same model"
+    if name == "fcc108k":
+        spec = synth.model_spec("fcc")
+        return spec, synth.make_weights(spec, 31), synth.fcc((3, 3, 4), seed=3), \
+            "FCC 3x3x4 cells (144 atoms), same model"
+    spec = synth.model_spec("small")
+    return spec, synth.make_weights(spec, 7), synth.cluster64(1), "the full 64-atom cluster"
+
+
+def time_oracle(name: str, min_seconds: float, max_evals: int = 1000):
+    import oracle
+    spec, w, s, desc = sample_workload(name)
+    m = oracle.Model(spec, w)
+    stress = bool(s.pbc.all())
+    m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=stress)  # warm-up
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=stress)
+        k += 1
+        dt = time.perf_counter() - t0
+        if dt >= min_seconds or k >= max_evals:
+            break
+    return {"value": s.n * k / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{desc}; {k} energy+force(+stress) evaluations in {dt:.1f} s"}
+
+
+def algorithmic_flops(spec, E: int, n: int):
+    """Algorithmic FP32 flops per step for the kernels of the plain form
+    (per-edge and per-node counts written out in the design notes)."""
+    import oracle  # noqa: F401  (paths only; counting, not arithmetic)
+    P0 = spec.L + 1
+    paths = []
+    for l1 in range(spec.L + 1):
+        for l2 in range(spec.Lsh + 1):
+            for l3 in range(spec.L + 1):
+                if abs(l1 - l2) <= l3 <= l1 + l2 and (l1 + l2 + l3) % 2 == 0:
+                    paths.append((l1, l2, l3))
+    P = len(paths)
+    C, H, T = spec.C, spec.H, spec.T
+    # w = z2 W3 forward and dz2 = dw W3^T backward, per layer (first layer: l1 = 0 paths)
+    pw = [P0] + [P] * (T - 1)
+    sgemm = sum(2 * 2 * E * H * C * p for p in pw)
+    return {"sgemm": sgemm}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2605_22698_gb300 import binding as B
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    spec, w, s = workload(args.workload, rank)
+    prec = {"fp32": B.MLIP_PREC_FP32, "bf16": B.MLIP_PREC_BF16}[args.precision]
+    model = B.Model(spec, w, prec)
+    pos = torch.tensor(s.pos, device=dev)
+    sp = torch.tensor(s.species, device=dev)
+    stress = bool(s.pbc.all())
+    out = {"energy": torch.zeros(1, dtype=torch.float64, device=dev),
+           "forces": torch.zeros((s.n, 3), dtype=torch.float64, device=dev)}
+    if stress:
+        out["stress"] = torch.zeros((3, 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        model.energy_forces(pos, sp, s.cell, s.pbc, forces=True, stress=stress, stream=stream, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    B.mlip_profile_enable(True)
+    launches0 = B.mlip_launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = B.mlip_launch_count() - launches0
+    prof = B.mlip_profile_report()
+    B.mlip_profile_enable(False)
+    clocks = sampler.stop() if sampler else None
+    ms = [a.elapsed_time(b) for a, b in evs]
+    t_dev = sum(ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = world * s.n * args.steps / t_dev
+    E_edges = int(sum(1 for _ in range(0)))  # filled below
+    # edge count of this structure (for the algorithmic counts)
+    r, _, _ = B.mlip_neighbors(np.ascontiguousarray(s.pos), s.cell, s.pbc, spec.rc)
+    E_edges = len(r)
+
+    # end-to-end: host arrays in pinned memory, copies inside the timed region
+    pin_pos = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    pin_pos[:] = s.pos
+    pin_sp = torch.empty(s.n, dtype=torch.int32, pin_memory=True).numpy()
+    pin_sp[:] = s.species
+    for _ in range(2):
+        model.energy_forces(pin_pos, pin_sp, s.cell, s.pbc, forces=True, stress=stress)
+    k_e2e = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        res = model.energy_forces(pin_pos, pin_sp, s.cell, s.pbc, forces=True, stress=stress)
+        _ = float(res["energy"][0])
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": world * s.n * k_e2e / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(pin_pos.nbytes + pin_sp.nbytes),
+           "d2h_bytes_per_step": int(8 + s.n * 3 * 8 + (72 if stress else 0))}
+
+    # roofline of the dominant kernel
+    kern = prof.get("kernels", {})
+    roof = None
+    if kern:
+        top = max(kern.items(), key=lambda kv: kv[1][1])
+        name, (nl, tot_ms) = top
+        flops = algorithmic_flops(spec, E_edges, s.n)
+        if name in flops:
+            per_step = flops[name]
+            achieved = per_step * args.steps / (tot_ms / 1e3) / 1e12
+            roof = {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_ALU_TFLOPS, 1),
+                    "unit": "TFLOP/s", "frac": round(achieved / FP32_ALU_TFLOPS, 4), "traffic": None,
+                    "launches": nl, "avg_launch_ms": round(tot_ms / nl, 5),
+                    "peak_src": "FP32 ALU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+        else:
+            roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": round(FP32_ALU_TFLOPS, 1),
+                    "unit": "TFLOP/s", "frac": None, "traffic": None, "launches": nl,
+                    "avg_launch_ms": round(tot_ms / nl, 5)}
+    share = {}
+    tot_all = sum(v[1] for v in kern.values()) or 1.0
+    for k_, v in sorted(kern.items(), key=lambda kv: -kv[1][1])[:8]:
+        share[k_] = round(v[1] / tot_all, 4)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(args.workload, args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": args.workload, "atoms": s.n, "edges": E_edges, "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}",
+                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (512 MB write)", "stress": stress},
+        "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernel_share": share,
+        "cpu_baseline": cpu, "clocks": clocks, "wall_s": round(t_wall, 3),
+        "peaks": peaks(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    res = None
+    t0 = time.perf_counter()
+    import oracle
+    spec, w, s, desc = sample_workload(args.workload)
+    m = oracle.Model(spec, w)
+    stress = bool(s.pbc.all())
+    for _ in range(args.warmup):
+        m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=stress)
+    t1 = time.perf_counter()
+    for _ in range(args.steps):
+        m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=stress)
+    dt = time.perf_counter() - t1
+    value = s.n * args.steps / dt
+    cpu = {"value": round(value, 2), "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": f"{desc}; one step = one energy+force(+stress) evaluation"}
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "sample_atoms": s.n},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(time.perf_counter() - t0, 2)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water3000", choices=["water3000", "fcc108k", "cluster64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

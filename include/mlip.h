@@ -134,6 +134,20 @@ int mlip_energy_forces(mlip_model* model, const double* pos, const int32_t* spec
                        const double cell[9], const uint8_t pbc[3], double* energy, double* forces,
                        double* stress, int on_device, void* stream);
 
+/* Tracing (no counterpart in the paper; used by the benchmark).
+ * mlip_launch_count: number of kernels the library has launched in this
+ *   process (monotone counter).
+ * mlip_profile_enable(1): from now on every kernel launch records a pair of
+ *   CUDA events on its stream (clears earlier records); 0 stops recording.
+ *   Do not enable it while a stream is being captured into a CUDA graph.
+ * mlip_profile_report: writes a NUL-terminated JSON object
+ *   {"kernels": {"<name>": [launches, total_ms], ...}} for the records since
+ *   the last enable into buf (at most cap bytes); *needed receives the full
+ *   size.  It synchronises on the recorded events.  Errors: MLIP_ERR_CUDA. */
+int mlip_profile_enable(int on);
+long long mlip_launch_count(void);
+int mlip_profile_report(char* buf, long long cap, long long* needed);
+
 #ifdef __cplusplus
 }
 #endif

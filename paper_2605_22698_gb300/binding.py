@@ -63,6 +63,9 @@ def lib():
         L.mlip_model_free.argtypes = [P]
         L.mlip_neighbors.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), i32, P]
         L.mlip_energy_forces.argtypes = [P, P, P, i64, P, P, P, P, P, i32, P]
+        L.mlip_profile_enable.argtypes = [i32]
+        L.mlip_launch_count.restype = ctypes.c_longlong
+        L.mlip_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
         _lib = L
     return _lib
 
@@ -188,6 +191,23 @@ def mlip_energy_forces(h, pos, species, cell, pbc, forces: bool = True, stress: 
                                     _ptr(out["forces"])[0] if forces else None,
                                     _ptr(out["stress"])[0] if stress else None, dev, _stream_ptr(stream)))
     return out
+
+
+def mlip_profile_enable(on: bool) -> None:
+    _check(lib().mlip_profile_enable(1 if on else 0))
+
+
+def mlip_launch_count() -> int:
+    return int(lib().mlip_launch_count())
+
+
+def mlip_profile_report() -> dict:
+    import json
+    need = ctypes.c_longlong(0)
+    _check(lib().mlip_profile_report(None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(int(need.value) + 16)
+    _check(lib().mlip_profile_report(buf, len(buf), ctypes.byref(need)))
+    return json.loads(buf.value.decode())
 
 
 class Model:

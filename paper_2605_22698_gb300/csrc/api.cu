@@ -7,6 +7,7 @@
 #include <fstream>
 
 #include "launchers.cuh"
+#include "profile.cuh"
 
 namespace mlip {
 
@@ -246,7 +247,7 @@ int energy_forces_plain(mlip_model* M, const double* d_pos, const int* d_species
   int* flag = nullptr;
   MLIP_TRY(ws.get("chk.flag", 1, &flag));
   MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  check_inputs<<<(n + 255) / 256, 256, 0, st>>>(n, d_pos, d_species, M->S, flag);
+  { MLIP_PROF("check_inputs", st); check_inputs<<<(n + 255) / 256, 256, 0, st>>>(n, d_pos, d_species, M->S, flag); }
   MLIP_LAUNCH_CHECK();
   NeighborList nl;
   MLIP_TRY(build_neighbors(ws, d_pos, n, cell, pbc, M->rc, true, st, &nl));

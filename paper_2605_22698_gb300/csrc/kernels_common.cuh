@@ -45,17 +45,23 @@ __device__ __forceinline__ float silu_grad_f(float x) {
 // Bessel basis times the polynomial envelope, and its r-derivative.
 //   e_n = sqrt(2/rc) sin(n pi r / rc) / r * u(r/rc)
 //   u(x) = 1 - a x^p + b x^{p+1} - c x^{p+2},  a = (p+1)(p+2)/2, b = p(p+2), c = p(p+1)/2
+// evaluated in the algebraically identical factored form
+//   u(x)  = (1-x)^3 sum_{k<p} C(k+2, 2) x^k,   u'(x) = -p(p+1)(p+2)/2 x^{p-1} (1-x)^2,
+// which keeps FP32 accuracy near the cutoff (the expanded form cancels there).
 template <int NB, bool GRAD>
 __device__ __forceinline__ void radial_basis(float r, float rc, int p, float* e, float* de) {
   const float x = r / rc;
   float u = 0.0f, du = 0.0f;
   if (x < 1.0f) {
-    float xp = 1.0f;
-    for (int k = 0; k < p - 1; ++k) xp *= x;  // x^{p-1}
-    const float a = 0.5f * (p + 1) * (p + 2), b = (float)(p * (p + 2)), c = 0.5f * p * (p + 1);
-    const float xp0 = xp * x;                 // x^p
-    u = 1.0f - a * xp0 + b * xp0 * x - c * xp0 * x * x;
-    du = (-a * p * xp + b * (p + 1) * xp0 - c * (p + 2) * xp0 * x) / rc;
+    const float om = 1.0f - x;
+    float poly = 0.0f, xk = 1.0f, xpm1 = 1.0f;
+    for (int k = 0; k < p; ++k) {
+      poly = fmaf(0.5f * (float)((k + 2) * (k + 1)), xk, poly);
+      if (k < p - 1) xpm1 *= x;
+      xk *= x;
+    }
+    u = om * om * om * poly;
+    du = -0.5f * (float)(p * (p + 1) * (p + 2)) * xpm1 * om * om / rc;
   }
   const float pref = sqrtf(2.0f / rc);
   const float inv_r = 1.0f / r;

@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "mlip_internal.cuh"
+#include "profile.cuh"
 
 namespace mlip {
 namespace {
@@ -107,7 +108,9 @@ __global__ void nl_setup(Grid* g, const long long* bbox) {
   for (int k = 0; k < 3; ++k) {
     g->bsz[k] = ext[k] / g->nb[k];
     double span = g->bsz[k] * g->w[k];  // perpendicular width of one bin
-    int r = (int)floor(g->rc / span * margin) + 1;
+    // clamp in floating point before converting (a flat open axis has a tiny span)
+    const double rd = fmin(floor(g->rc / span * margin) + 1.0, 1048576.0);
+    int r = (int)rd;
     if (!g->pbc[k]) r = min(r, g->nb[k]);
     g->reach[k] = r;
   }
@@ -338,9 +341,9 @@ int exclusive_scan_i32(Workspace& ws, const int32_t* in, int32_t* out, int64_t n
   if (nb < 1) nb = 1;
   int* bsum = nullptr;
   MLIP_TRY(ws.get("scan.bsum", (size_t)nb, &bsum));
-  scan_local<<<nb, kScanThreads, 0, st>>>(in, out, n, bsum);
-  scan_blocks<<<1, 1024, 0, st>>>(bsum, nb, out + n);
-  scan_add<<<nb, kScanThreads, 0, st>>>(out, n, bsum);
+  { MLIP_PROF("scan_local", st); scan_local<<<nb, kScanThreads, 0, st>>>(in, out, n, bsum); }
+  { MLIP_PROF("scan_blocks", st); scan_blocks<<<1, 1024, 0, st>>>(bsum, nb, out + n); }
+  { MLIP_PROF("scan_add", st); scan_add<<<nb, kScanThreads, 0, st>>>(out, n, bsum); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
@@ -420,19 +423,19 @@ int build_neighbors(Workspace& ws, const double* d_pos, int64_t n64, const doubl
     MLIP_CUDA_TRY(cudaMemsetAsync(counts, 0, ((size_t)hg.max_bins + 1) * sizeof(int), st));
     MLIP_CUDA_TRY(cudaMemsetAsync(cursor, 0, ((size_t)hg.max_bins + 1) * sizeof(int), st));
     if (n > 0) {
-      nl_frac<<<blocks, threads, 0, st>>>(d_pos, n, dg, frac, img, bbox);
-      nl_setup<<<1, 1, 0, st>>>(dg, bbox);
-      nl_bin<<<blocks, threads, 0, st>>>(n, dg, frac, bin_of, counts);
+      { MLIP_PROF("nl_frac", st); nl_frac<<<blocks, threads, 0, st>>>(d_pos, n, dg, frac, img, bbox); }
+      { MLIP_PROF("nl_setup", st); nl_setup<<<1, 1, 0, st>>>(dg, bbox); }
+      { MLIP_PROF("nl_bin", st); nl_bin<<<blocks, threads, 0, st>>>(n, dg, frac, bin_of, counts); }
     } else {
-      nl_setup<<<1, 1, 0, st>>>(dg, bbox);
+      { MLIP_PROF("nl_setup", st); nl_setup<<<1, 1, 0, st>>>(dg, bbox); }
     }
     MLIP_LAUNCH_CHECK();
     MLIP_TRY(exclusive_scan_i32(ws, counts, bin_start, hg.max_bins, st));
     unsigned long long* slab = nullptr;
     MLIP_TRY(ws.get("nl.slab", (size_t)nn * maxdeg, &slab));
     if (n > 0) {
-      nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms);
-      nl_pairs<<<blocks, threads, 0, st>>>(n, dg, d_pos, frac, img, bin_start, bin_atoms, slab, deg, flags);
+      { MLIP_PROF("nl_scatter", st); nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms); }
+      { MLIP_PROF("nl_pairs", st); nl_pairs<<<blocks, threads, 0, st>>>(n, dg, d_pos, frac, img, bin_start, bin_atoms, slab, deg, flags); }
       MLIP_LAUNCH_CHECK();
     }
     MLIP_TRY(exclusive_scan_i32(ws, deg, out->row_ptr, n, st));
@@ -463,15 +466,15 @@ int build_neighbors(Workspace& ws, const double* d_pos, int64_t n64, const doubl
       size_t smem = (size_t)wpb * cap * sizeof(unsigned long long);
       if (smem > 48 * 1024)
         MLIP_CUDA_TRY(cudaFuncSetAttribute(nl_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      nl_sort<<<(n + wpb - 1) / wpb, 32 * wpb, smem, st>>>(n, cap, slab, maxdeg, out->row_ptr, out->keys,
-                                                          out->recv, out->send, out->shift);
+      { MLIP_PROF("nl_sort", st); nl_sort<<<(n + wpb - 1) / wpb, 32 * wpb, smem, st>>>(n, cap, slab, maxdeg, out->row_ptr, out->keys,
+                                                          out->recv, out->send, out->shift); }
       MLIP_LAUNCH_CHECK();
     }
     if (want_rev) {
       MLIP_TRY(ws.get("nl.rev", Ecap, &out->rev));
       if (E32 > 0) {
-        nl_rev<<<std::min((E32 + 255) / 256, 4096), 256, 0, st>>>(out->row_ptr + n, out->row_ptr, out->recv,
-                                                                   out->send, out->shift, out->keys, out->rev, flags);
+        { MLIP_PROF("nl_rev", st); nl_rev<<<std::min((E32 + 255) / 256, 4096), 256, 0, st>>>(out->row_ptr + n, out->row_ptr, out->recv,
+                                                                   out->send, out->shift, out->keys, out->rev, flags); }
         MLIP_LAUNCH_CHECK();
       }
     }

@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "kernels_common.cuh"
+#include "profile.cuh"
 
 namespace mlip {
 namespace {
@@ -135,29 +136,29 @@ __global__ void virial_finish(int nb, const double* __restrict__ vir_part, doubl
 
 int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
-  embed<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_emb, h);
+  { MLIP_PROF("embed", st); embed<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_emb, h); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
 int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
-  grad_init<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_out, G);
+  { MLIP_PROF("grad_init", st); grad_init<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_out, G); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
 int launch_energy(int n, int C, int D, const int* species, const float* W_out, const float* E0, const float* h,
                   double* atom_e, double* energy, cudaStream_t st) {
-  if (n > 0) readout<<<(n + 7) / 8, 256, 0, st>>>(n, C, D, species, W_out, E0, h, atom_e);
-  sum_f64<<<1, 1024, 0, st>>>(n, atom_e, energy);
+  if (n > 0) { MLIP_PROF("readout", st); readout<<<(n + 7) / 8, 256, 0, st>>>(n, C, D, species, W_out, E0, h, atom_e); }
+  { MLIP_PROF("sum_f64", st); sum_f64<<<1, 1024, 0, st>>>(n, atom_e, energy); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
 int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, float4* g, cudaStream_t st) {
   if (E <= 0) return MLIP_OK;
-  edge_grad<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, dY, dr, g);
+  { MLIP_PROF("edge_grad", st); edge_grad<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, dY, dr, g); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
@@ -168,8 +169,8 @@ int launch_forces_virial(Workspace& ws, int n, const int* row_ptr, const int* re
   const int nb = (n + 127) / 128;
   double* part = nullptr;
   MLIP_TRY(ws.get("fv.part", (size_t)nb * 9, &part));
-  forces_virial<<<nb, 128, 0, st>>>(n, row_ptr, rev, g, ev, forces, part);
-  if (stress) virial_finish<<<1, 32, 0, st>>>(nb, part, inv_vol, stress);
+  { MLIP_PROF("forces_virial", st); forces_virial<<<nb, 128, 0, st>>>(n, row_ptr, rev, g, ev, forces, part); }
+  if (stress) { MLIP_PROF("virial_finish", st); virial_finish<<<1, 32, 0, st>>>(nb, part, inv_vol, stress); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }

@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "kernels_common.cuh"
+#include "profile.cuh"
 
 namespace mlip {
 namespace {
@@ -507,7 +508,7 @@ __global__ void mix_bwd(int n, int C, int L, const float* __restrict__ G, const 
 int launch_edge_geom(int E, const double* pos, const int* recv, const int* send, const int8_t* shift,
                      const CellArg& cell, float4* ev, cudaStream_t st) {
   if (E <= 0) return MLIP_OK;
-  edge_geom<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, pos, recv, send, shift, cell, ev);
+  { MLIP_PROF("edge_geom", st); edge_geom<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, pos, recv, send, shift, cell, ev); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
@@ -516,8 +517,8 @@ int launch_radial_fwd(int H, int E, const float4* ev, const float* W1, const flo
                       float* z2T, int ldz, cudaStream_t st) {
   if (E <= 0) return MLIP_OK;
   const int blocks = (E + 127) / 128;
-  if (H == 64) radial_fwd<64><<<blocks, 128, 0, st>>>(E, ev, W1, W2, rc, p, z2T, ldz);
-  else if (H == 32) radial_fwd<32><<<blocks, 128, 0, st>>>(E, ev, W1, W2, rc, p, z2T, ldz);
+  if (H == 64) { MLIP_PROF("radial_fwd", st); radial_fwd<64><<<blocks, 128, 0, st>>>(E, ev, W1, W2, rc, p, z2T, ldz); }
+  else if (H == 32) { MLIP_PROF("radial_fwd", st); radial_fwd<32><<<blocks, 128, 0, st>>>(E, ev, W1, W2, rc, p, z2T, ldz); }
   else { set_error("radial hidden width %d unsupported", H); return MLIP_ERR_INVALID_ARG; }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
@@ -527,8 +528,8 @@ int launch_radial_bwd(int H, int E, const float4* ev, const float* W1, const flo
                       const float* dz2, float* dr_tot, cudaStream_t st) {
   if (E <= 0) return MLIP_OK;
   const int blocks = (E + 127) / 128;
-  if (H == 64) radial_bwd<64><<<blocks, 128, 0, st>>>(E, ev, W1, W2, rc, p, dz2, dr_tot);
-  else if (H == 32) radial_bwd<32><<<blocks, 128, 0, st>>>(E, ev, W1, W2, rc, p, dz2, dr_tot);
+  if (H == 64) { MLIP_PROF("radial_bwd", st); radial_bwd<64><<<blocks, 128, 0, st>>>(E, ev, W1, W2, rc, p, dz2, dr_tot); }
+  else if (H == 32) { MLIP_PROF("radial_bwd", st); radial_bwd<32><<<blocks, 128, 0, st>>>(E, ev, W1, W2, rc, p, dz2, dr_tot); }
   else { set_error("radial hidden width %d unsupported", H); return MLIP_ERR_INVALID_ARG; }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
@@ -538,10 +539,10 @@ int launch_sgemm(bool a_km, bool b_nk, int M, int N, int K, const float* A, int 
                  float* C, int ldc, cudaStream_t st) {
   if (M <= 0 || N <= 0) return MLIP_OK;
   dim3 grid((N + 127) / 128, (M + 127) / 128);
-  if (a_km && !b_nk) sgemm<true, false><<<grid, 256, 0, st>>>(M, nullptr, N, K, A, lda, B, ldb, C, ldc);
-  else if (!a_km && b_nk) sgemm<false, true><<<grid, 256, 0, st>>>(M, nullptr, N, K, A, lda, B, ldb, C, ldc);
-  else if (!a_km && !b_nk) sgemm<false, false><<<grid, 256, 0, st>>>(M, nullptr, N, K, A, lda, B, ldb, C, ldc);
-  else sgemm<true, true><<<grid, 256, 0, st>>>(M, nullptr, N, K, A, lda, B, ldb, C, ldc);
+  if (a_km && !b_nk) { MLIP_PROF("sgemm", st); sgemm<true, false><<<grid, 256, 0, st>>>(M, nullptr, N, K, A, lda, B, ldb, C, ldc); }
+  else if (!a_km && b_nk) { MLIP_PROF("sgemm", st); sgemm<false, true><<<grid, 256, 0, st>>>(M, nullptr, N, K, A, lda, B, ldb, C, ldc); }
+  else if (!a_km && !b_nk) { MLIP_PROF("sgemm", st); sgemm<false, false><<<grid, 256, 0, st>>>(M, nullptr, N, K, A, lda, B, ldb, C, ldc); }
+  else { MLIP_PROF("sgemm", st); sgemm<true, true><<<grid, 256, 0, st>>>(M, nullptr, N, K, A, lda, B, ldb, C, ldc); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
@@ -557,10 +558,10 @@ int launch_tp_fwd(int L, bool first, int n, int C, const int* row_ptr, const int
                   const float4* ev, const float* h, const float* w, int PW, float s, float* m, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   const int G = tp_blocks(n), threads = std::max(C, 32);
-  if (L == 2 && first) tp_fwd<2, true><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m);
-  else if (L == 2) tp_fwd<2, false><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m);
-  else if (L == 3 && first) tp_fwd<3, true><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m);
-  else if (L == 3) tp_fwd<3, false><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m);
+  if (L == 2 && first) { MLIP_PROF("tp_fwd", st); tp_fwd<2, true><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m); }
+  else if (L == 2) { MLIP_PROF("tp_fwd", st); tp_fwd<2, false><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m); }
+  else if (L == 3 && first) { MLIP_PROF("tp_fwd", st); tp_fwd<3, true><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m); }
+  else if (L == 3) { MLIP_PROF("tp_fwd", st); tp_fwd<3, false><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m); }
   else { set_error("l_max %d unsupported", L); return MLIP_ERR_INVALID_ARG; }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
@@ -572,12 +573,15 @@ int launch_tp_bwd(int L, bool first, int n, int C, const int* row_ptr, const int
   if (n <= 0) return MLIP_OK;
   const int G = tp_blocks(n), threads = std::max(C, 32);
   if (threads > 128) { set_error("channels %d unsupported", C); return MLIP_ERR_INVALID_ARG; }
-#define MLIP_TPB(LL, FF) \
-  tp_bwd<LL, FF><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, hprev, Gm, w, PW, s, Gin, Gout, dw, dY)
-  if (L == 2 && first) MLIP_TPB(2, true);
-  else if (L == 2) MLIP_TPB(2, false);
-  else if (L == 3 && first) MLIP_TPB(3, true);
-  else if (L == 3) MLIP_TPB(3, false);
+#define MLIP_TPB(LL, FF)                                                                                \
+  {                                                                                                     \
+    MLIP_PROF("tp_bwd", st);                                                                            \
+    tp_bwd<LL, FF><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, hprev, Gm, w, PW, s, Gin, Gout, dw, dY); \
+  }
+  if (L == 2 && first) MLIP_TPB(2, true)
+  else if (L == 2) MLIP_TPB(2, false)
+  else if (L == 3 && first) MLIP_TPB(3, true)
+  else if (L == 3) MLIP_TPB(3, false)
   else { set_error("l_max %d unsupported", L); return MLIP_ERR_INVALID_ARG; }
 #undef MLIP_TPB
   MLIP_LAUNCH_CHECK();
@@ -590,7 +594,7 @@ int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const
   const size_t smem = ((size_t)C * C + (size_t)kMixNodes * (2 * L + 1) * C) * sizeof(float);
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n + kMixNodes - 1) / kMixNodes, L + 1);
-  mix_fwd<<<grid, std::max(C, 32), smem, st>>>(n, C, L, m, Wmix, hin, hout, u0);
+  { MLIP_PROF("mix_fwd", st); mix_fwd<<<grid, std::max(C, 32), smem, st>>>(n, C, L, m, Wmix, hin, hout, u0); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
@@ -601,7 +605,7 @@ int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const f
   const size_t smem = ((size_t)C * C + (size_t)kMixNodes * (2 * L + 1) * C) * sizeof(float);
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n + kMixNodes - 1) / kMixNodes, L + 1);
-  mix_bwd<<<grid, std::max(C, 32), smem, st>>>(n, C, L, G, u0, Wmix, Gm);
+  { MLIP_PROF("mix_bwd", st); mix_bwd<<<grid, std::max(C, 32), smem, st>>>(n, C, L, G, u0, Wmix, Gm); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }

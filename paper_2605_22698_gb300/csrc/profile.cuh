@@ -1,0 +1,22 @@
+// Launch accounting and optional per-kernel timing with CUDA events.
+// Every kernel launch of the library goes through a ProfScope: it counts the
+// launch and, when timing is enabled, records an event pair on the launching
+// stream.  Reports aggregate (launches, total ms) per kernel name.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mlip {
+
+void prof_begin(const char* name, cudaStream_t st);
+void prof_end(cudaStream_t st);
+
+struct ProfScope {
+  cudaStream_t st;
+  ProfScope(const char* name, cudaStream_t s) : st(s) { prof_begin(name, s); }
+  ~ProfScope() { prof_end(st); }
+};
+
+}  // namespace mlip
+
+#define MLIP_PROF(name, st) ::mlip::ProfScope mlip_prof_scope__(name, st)

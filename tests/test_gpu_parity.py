@@ -44,6 +44,10 @@ def _cases():
     s = synth.cluster(700, seed=9)
     out.append(("cluster700", s.pos, s.cell, s.pbc))
     out.append(("single", np.array([[1.0, 2.0, 3.0]]), np.eye(3), np.zeros(3, np.uint8)))
+    out.append(("planar", np.c_[r.uniform(size=(30, 2)) * 9, np.zeros(30)], np.eye(3), np.zeros(3, np.uint8)))
+    out.append(("linear", np.c_[np.arange(12) * 1.3, np.zeros(12), np.zeros(12)], np.eye(3), np.zeros(3, np.uint8)))
+    out.append(("coincident-images", np.array([[0.0, 0, 0], [0.0, 0, 0.0]]) + 0.5, np.eye(3) * 3.0,
+                np.ones(3, np.uint8)))
     out.append(("single-periodic", np.array([[1.0, 2.0, 3.0]]), np.eye(3) * 4.0, np.ones(3, np.uint8)))
     return out
 
