@@ -134,6 +134,14 @@ int mlip_energy_forces(mlip_model* model, const double* pos, const int32_t* spec
                        const double cell[9], const uint8_t pbc[3], double* energy, double* forces,
                        double* stress, int on_device, void* stream);
 
+/* Self test of a hardware path (no counterpart in the paper).  which = 1: one
+ * tcgen05 tile product (M = 128, N = 32, K = 64, BF16 operands in the
+ * shared-memory layout the fused kernels use, FP32 accumulation in tensor
+ * memory) against a host FP64 product; *result = max |error| / max |value|.
+ * Errors: MLIP_ERR_INVALID_ARG (unknown test), MLIP_ERR_DEVICE_TIMEOUT (the
+ * MMA completion wait ran out), MLIP_ERR_CUDA. */
+int mlip_selftest(int which, double* result);
+
 /* Tracing (no counterpart in the paper; used by the benchmark).
  * mlip_launch_count: number of kernels the library has launched in this
  *   process (monotone counter).

@@ -63,6 +63,7 @@ def lib():
         L.mlip_model_free.argtypes = [P]
         L.mlip_neighbors.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), i32, P]
         L.mlip_energy_forces.argtypes = [P, P, P, i64, P, P, P, P, P, i32, P]
+        L.mlip_selftest.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         L.mlip_profile_enable.argtypes = [i32]
         L.mlip_launch_count.restype = ctypes.c_longlong
         L.mlip_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
@@ -191,6 +192,12 @@ def mlip_energy_forces(h, pos, species, cell, pbc, forces: bool = True, stress: 
                                     _ptr(out["forces"])[0] if forces else None,
                                     _ptr(out["stress"])[0] if stress else None, dev, _stream_ptr(stream)))
     return out
+
+
+def mlip_selftest(which: int) -> float:
+    r = ctypes.c_double(0.0)
+    _check(lib().mlip_selftest(which, ctypes.byref(r)))
+    return float(r.value)
 
 
 def mlip_profile_enable(on: bool) -> None:

@@ -100,7 +100,10 @@ static int validate_desc(const mlip_model_desc* d, int precision) {
   if (d->envelope_p < 1 || d->envelope_p > 16) { set_error("envelope_p %d out of range", d->envelope_p); return MLIP_ERR_INVALID_ARG; }
   if (!(d->cutoff > 0) || !(d->avg_num_neighbors > 0)) { set_error("cutoff and avg_num_neighbors must be positive"); return MLIP_ERR_INVALID_ARG; }
   if (precision != MLIP_PREC_FP32 && precision != MLIP_PREC_BF16) { set_error("unknown precision %d", precision); return MLIP_ERR_INVALID_ARG; }
-  if (precision == MLIP_PREC_BF16 && d->channels != 128) { set_error("the BF16 form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
+  if (precision == MLIP_PREC_BF16 && (d->channels != 128 || d->hidden != 64)) {
+    set_error("the BF16 form needs 128 channels and hidden width 64");
+    return MLIP_ERR_INVALID_ARG;
+  }
   return MLIP_OK;
 }
 
@@ -152,8 +155,33 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
   }
   M->W_out = q; q += S * C;
   M->E0 = q; q += S;
+  if (precision == MLIP_PREC_BF16) {
+    std::vector<uint8_t> all, img;
+    for (int t = 0; t < M->T; ++t) {
+      std::vector<size_t> goff;
+      pack_w3_groups(M, t, img, goff);
+      M->w3_layer_off.push_back(all.size());
+      M->w3_goff.push_back(goff);
+      all.insert(all.end(), img.begin(), img.end());
+    }
+    e = cudaMalloc(&M->d_w3img, all.size());
+    if (e == cudaSuccess) e = cudaMemcpy(M->d_w3img, all.data(), all.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("tensor-core weight image: %s", cudaGetErrorString(e));
+      mlip_model_free(M);
+      return MLIP_ERR_OOM;
+    }
+  }
   *out = M;
   return MLIP_OK;
+}
+
+int mlip_selftest(int which, double* result) {
+  if (!result) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  if (which == 1) return umma_selftest_run(result);
+  set_error("unknown self test %d", which);
+  return MLIP_ERR_INVALID_ARG;
 }
 
 int mlip_model_load(const char* path, int precision, mlip_model** out) {
@@ -187,6 +215,7 @@ int mlip_model_free(mlip_model* M) {
   cudaDeviceSynchronize();
   M->ws.release();
   if (M->d_weights) cudaFree(M->d_weights);
+  if (M->d_w3img) cudaFree(M->d_w3img);
   delete M;
   return MLIP_OK;
 }
@@ -234,6 +263,13 @@ __global__ void check_inputs(int n, const double* __restrict__ pos, const int* _
   if (!isfinite(pos[3 * i]) || !isfinite(pos[3 * i + 1]) || !isfinite(pos[3 * i + 2])) atomicOr(flag, 2);
 }
 
+int launch_check_inputs(int n, const double* pos, const int* species, int S, int* flag, cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  { MLIP_PROF("check_inputs", st); check_inputs<<<(n + 255) / 256, 256, 0, st>>>(n, pos, species, S, flag); }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
 static double cell_volume(const double* h) {
   return std::fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
                    h[2] * (h[3] * h[7] - h[4] * h[6]));
@@ -247,8 +283,7 @@ int energy_forces_plain(mlip_model* M, const double* d_pos, const int* d_species
   int* flag = nullptr;
   MLIP_TRY(ws.get("chk.flag", 1, &flag));
   MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  { MLIP_PROF("check_inputs", st); check_inputs<<<(n + 255) / 256, 256, 0, st>>>(n, d_pos, d_species, M->S, flag); }
-  MLIP_LAUNCH_CHECK();
+  MLIP_TRY(launch_check_inputs(n, d_pos, d_species, M->S, flag, st));
   NeighborList nl;
   MLIP_TRY(build_neighbors(ws, d_pos, n, cell, pbc, M->rc, true, st, &nl));
   int hflag = 0;

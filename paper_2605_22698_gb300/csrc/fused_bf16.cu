@@ -1,12 +1,566 @@
-// Fused BF16 form of the interaction layer (tcgen05 radial MLP).
+// Fused BF16 form of the interaction layer.
+//
+// Per layer:
+//   radial_tiles  one thread per edge: r -> Bessel x envelope -> z1 -> z2 (FP32),
+//                 z2 written as BF16 in the tcgen05 canonical K-major layout,
+//                 one 4 KB tile per kNT = 32 consecutive (receiver-sorted) edges
+//   tp_fused      one launch per path group (all l1 = 0 paths for the first
+//                 layer, else the paths of one output order l3).  Each CTA keeps
+//                 its group's W3 slices resident in shared memory (bulk-copied
+//                 once), streams the z2 tiles of its balanced receiver range
+//                 through a double buffer with 1-D bulk copies, and per tile
+//                 issues one tcgen05.mma (M = 128 channels, N = 32 edges,
+//                 K = 64) per path: w[c][e] = W3_p^T z2 lands in tensor memory.
+//                 Thread c then reads its lane (channel c) with tcgen05.ld and
+//                 runs the FP32 tensor product for its channel over the tile's
+//                 edges, accumulating the receiver's message in registers and
+//                 flushing it at segment ends (no atomics).
+// The per-edge radial weights never reach HBM.
+#include <algorithm>
+#include <array>
+#include <cstring>
+
+#include <cuda_bf16.h>
+
+#include "kernels_common.cuh"
 #include "launchers.cuh"
+#include "profile.cuh"
+#include "sm100_tc.cuh"
 
 namespace mlip {
+namespace {
 
-int energy_forces_fused(mlip_model*, const double*, const int*, int64_t, const double*, const uint8_t*, double*,
-                        double*, double*, cudaStream_t) {
-  set_error("the fused BF16 form is not available in this build");
-  return MLIP_ERR_INVALID_ARG;
+constexpr int kNT = 32;           // edges per tile (MMA N)
+constexpr int kTileBytes = kNT * 64 * 2;
+constexpr int kW3PathBytes = 128 * 64 * 2;
+
+// ------------------------------------------------------------ path groups
+// MODE < 0: the l1 = 0 paths (first layer, scalar inputs); MODE = l: paths with l3 = l.
+template <int L, int MODE>
+struct Group {
+  using Tab = CGTable<L>;
+  static constexpr bool sel(int p) { return MODE < 0 ? Tab::l1[p] == 0 : Tab::l3[p] == MODE; }
+  static constexpr int count() {
+    int n = 0;
+    for (int p = 0; p < Tab::P; ++p) n += sel(p) ? 1 : 0;
+    return n;
+  }
+  static constexpr int NP = count();
+  static constexpr std::array<int, NP> make_paths() {
+    std::array<int, NP> a{};
+    int n = 0;
+    for (int p = 0; p < Tab::P; ++p)
+      if (sel(p)) a[n++] = p;
+    return a;
+  }
+  static constexpr std::array<int, NP> paths = make_paths();
+  // offset of each member path's entries in the group's entry list
+  static constexpr std::array<int, NP + 1> make_eoff() {
+    std::array<int, NP + 1> a{};
+    for (int s = 0; s < NP; ++s) a[s + 1] = a[s] + Tab::off[paths[s] + 1] - Tab::off[paths[s]];
+    return a;
+  }
+  static constexpr std::array<int, NP + 1> eoff = make_eoff();
+  static constexpr int NZ = eoff[NP];
+  static constexpr int NZP = (NZ + 3) & ~3;
+  // output components written: [comp0, comp0 + NOUT)
+  static constexpr int comp0 = MODE < 0 ? 0 : MODE * MODE;
+  static constexpr int NOUT = MODE < 0 ? (L + 1) * (L + 1) : 2 * MODE + 1;
+  static constexpr int max_l1() {
+    int m = 0;
+    for (int s = 0; s < NP; ++s) m = Tab::l1[paths[s]] > m ? Tab::l1[paths[s]] : m;
+    return m;
+  }
+  static constexpr int DH = (max_l1() + 1) * (max_l1() + 1);  // sender components read
+  static constexpr int tmem_cols() {
+    int need = NP * kNT, c = 32;
+    while (c < need) c <<= 1;
+    return c;
+  }
+  static constexpr int NCOLS = tmem_cols();
+  static constexpr size_t smem_bytes() {
+    return (size_t)NP * kW3PathBytes + 2 * kTileBytes + (size_t)kNT * NZP * 4 + 2 * kNT * 4 + 64;
+  }
+};
+
+// ------------------------------------------------------------- radial tiles
+template <int H>
+__global__ void radial_tiles(int E, int n_tiles, const float4* __restrict__ ev, const float* __restrict__ W1,
+                             const float* __restrict__ W2, float rc, int p, uint8_t* __restrict__ z2t) {
+  static_assert(H == 64, "tile layout assumes K = 64");
+  __shared__ float sW1[8 * H], sW2[H * H];
+  for (int k = threadIdx.x; k < 8 * H; k += blockDim.x) sW1[k] = W1[k];
+  for (int k = threadIdx.x; k < H * H; k += blockDim.x) sW2[k] = W2[k];
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_tiles * kNT) return;
+  uint8_t* tile = z2t + (size_t)(e / kNT) * kTileBytes;
+  const int t = e % kNT;
+  if (e >= E) {
+    const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int kg = 0; kg < 8; ++kg) *reinterpret_cast<uint4*>(tile + tc::canon_off(t, kg * 8)) = z;
+    return;
+  }
+  float b[8], db[8];
+  radial_basis<8, false>(ev[e].w, rc, p, b, db);
+  float z1[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    float a = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a = fmaf(b[q], sW1[q * H + k], a);
+    z1[k] = silu_f(a);
+  }
+#pragma unroll 1
+  for (int kg = 0; kg < 8; ++kg) {
+    uint32_t pk[4];
+#pragma unroll
+    for (int h2 = 0; h2 < 4; ++h2) {
+      float o[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int k = kg * 8 + h2 * 2 + u;
+        float a = 0.0f;
+#pragma unroll
+        for (int q = 0; q < H; ++q) a = fmaf(z1[q], sW2[q * H + k], a);
+        o[u] = silu_f(a);
+      }
+      const __nv_bfloat162 v = __floats2bfloat162_rn(o[0], o[1]);
+      pk[h2] = *reinterpret_cast<const uint32_t*>(&v);
+    }
+    *reinterpret_cast<uint4*>(tile + tc::canon_off(t, kg * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+}
+
+// ---------------------------------------------------------------- tp_fused
+template <int L, int MODE>
+__global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ row_ptr, const int* __restrict__ recv,
+                                                const int* __restrict__ send, const float4* __restrict__ ev,
+                                                const float* __restrict__ h, const uint8_t* __restrict__ w3img,
+                                                const uint8_t* __restrict__ z2t, float s, float* __restrict__ m,
+                                                int* __restrict__ err) {
+  using G = Group<L, MODE>;
+  using Tab = CGTable<L>;
+  constexpr int D = NodeDims<L>::D;
+  constexpr int C = 128;
+  constexpr int NP = G::NP;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sW3 = smem;
+  uint8_t* sZ2 = smem + NP * kW3PathBytes;
+  float* cY = reinterpret_cast<float*>(sZ2 + 2 * kTileBytes);
+  int* s_send = reinterpret_cast<int*>(cY + kNT * G::NZP);
+  int* s_recv = s_send + kNT;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_recv + kNT);  // 16-byte aligned offset
+  uint64_t* bar_w3 = bars;
+  uint64_t* bar_z2 = bars + 1;  // [2]
+  uint64_t* bar_mma = bars + 3;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 4);
+  __shared__ int abort_s;
+
+  const int tid = threadIdx.x, warp = tid >> 5, c = tid;
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, G::NCOLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(bar_w3, 1);
+    tc::mbar_init(bar_z2, 1);
+    tc::mbar_init(bar_z2 + 1, 1);
+    tc::mbar_init(bar_mma, 1);
+    tc::fence_mbar_init();
+    abort_s = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tmem_holder;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+
+  int i0, i1;
+  block_receivers(row_ptr, n, blockIdx.x, gridDim.x, &i0, &i1);
+  const int E0 = row_ptr[i0], E1 = row_ptr[i1];
+  const int t_begin = E0 / kNT, t_end = (E1 > E0) ? (E1 + kNT - 1) / kNT : t_begin;
+  const int n_tiles = t_end - t_begin;
+
+  // producer state (thread 0)
+  int z2_issued[2] = {0, 0}, z2_waited[2] = {0, 0};
+  bool w3_issued = false;
+  if (tid == 0 && n_tiles > 0) {
+    tc::mbar_arrive_expect_tx(bar_w3, NP * kW3PathBytes);
+#pragma unroll 1
+    for (int sl = 0; sl < NP; ++sl)
+      tc::bulk_g2s(sW3 + sl * kW3PathBytes, w3img + (size_t)sl * kW3PathBytes, kW3PathBytes, bar_w3);
+    w3_issued = true;
+    tc::mbar_arrive_expect_tx(bar_z2, kTileBytes);
+    tc::bulk_g2s(sZ2, z2t + (size_t)t_begin * kTileBytes, kTileBytes, bar_z2);
+    z2_issued[0] = 1;
+  }
+
+  float acc[G::NOUT];
+#pragma unroll
+  for (int q = 0; q < G::NOUT; ++q) acc[q] = 0.0f;
+  int cur = i0;
+  auto flush = [&](int i) {
+#pragma unroll
+    for (int q = 0; q < G::NOUT; ++q) {
+      m[((size_t)i * D + G::comp0 + q) * C + c] = s * acc[q];
+      acc[q] = 0.0f;
+    }
+  };
+  constexpr uint32_t idesc = tc::idesc_bf16(128, kNT);
+
+#pragma unroll 1
+  for (int it = 0; it < n_tiles; ++it) {
+    const int tile = t_begin + it;
+    const int buf = it & 1;
+    // per-edge setup of this tile
+    if (tid < kNT) {
+      const int e = tile * kNT + tid;
+      const bool valid = e >= E0 && e < E1;
+      s_recv[tid] = valid ? recv[e] : -1;
+      s_send[tid] = valid ? send[e] : 0;
+      float* dst = cY + tid * G::NZP;
+      if (valid) {
+        const float4 v = ev[e];
+        const float ir = 1.0f / v.w;
+        float Y[16];
+        sh3<float>(v.x * ir, v.y * ir, v.z * ir, Y);
+        static_for<0, NP>([&](auto sc) {
+          constexpr int sl = decltype(sc)::value;
+          constexpr int p = G::paths[sl];
+          constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
+          static_for<kb, ke>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr float cv = Tab::ec[k];
+            constexpr int i2 = Tab::e2[k];
+            dst[gb + k - kb] = cv * Y[i2];
+          });
+        });
+      }
+    }
+    // MMA issue (thread 0): prefetch the next z2 tile, wait for this one, one MMA per path
+    if (tid == 0) {
+      bool ok = true;
+      if (it + 1 < n_tiles) {
+        const int nb = buf ^ 1;
+        tc::mbar_arrive_expect_tx(bar_z2 + nb, kTileBytes);
+        tc::bulk_g2s(sZ2 + nb * kTileBytes, z2t + (size_t)(tile + 1) * kTileBytes, kTileBytes, bar_z2 + nb);
+        z2_issued[nb]++;
+      }
+      if (it == 0) ok = ok && tc::mbar_wait(bar_w3, 0);
+      ok = ok && tc::mbar_wait(bar_z2 + buf, (uint32_t)(z2_waited[buf] & 1));
+      if (ok) {
+        z2_waited[buf]++;
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sZ2 + buf * kTileBytes);
+#pragma unroll 1
+        for (int sl = 0; sl < NP; ++sl) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+            const uint64_t bd = tc::desc_noswizzle(b0 + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+            tc::mma_bf16(tbase + sl * kNT, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          }
+        }
+        tc::mma_commit(bar_mma);
+      } else {
+        atomicOr(err, 1);
+        abort_s = 1;
+      }
+    }
+    __syncthreads();
+    if (abort_s) break;
+    if (!tc::mbar_wait(bar_mma, (uint32_t)(it & 1))) {
+      atomicOr(err, 2);
+      abort_s = 1;
+    }
+    tc::fence_after_sync();
+    // tensor product over the tile's edges, 8 at a time
+#pragma unroll 1
+    for (int ch = 0; ch < kNT / 8; ++ch) {
+      float wv[NP][8];
+#pragma unroll
+      for (int sl = 0; sl < NP; ++sl) tc::tmem_ld8(tbase + lane_off + sl * kNT + ch * 8, wv[sl]);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int t = ch * 8 + j;
+        const int r = s_recv[t];
+        if (r < 0) continue;
+        while (cur < r) { flush(cur); ++cur; }
+        const int sj = s_send[t];
+        float hj[G::DH];
+#pragma unroll
+        for (int d = 0; d < G::DH; ++d) hj[d] = h[((size_t)sj * D + d) * C + c];
+        const float* cy = cY + t * G::NZP;
+        static_for<0, NP>([&](auto sc) {
+          constexpr int sl = decltype(sc)::value;
+          constexpr int p = G::paths[sl];
+          constexpr int l1 = Tab::l1[p];
+          constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
+          float wh[2 * l1 + 1];
+#pragma unroll
+          for (int q = 0; q < 2 * l1 + 1; ++q) wh[q] = wv[sl][j] * hj[l1 * l1 + q];
+          static_for<kb, ke>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int o3 = Tab::e3[k] - G::comp0, j1 = Tab::e1[k] - l1 * l1;
+            acc[o3] = fmaf(cy[gb + k - kb], wh[j1], acc[o3]);
+          });
+        });
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (abort_s) break;
+  }
+  if (!abort_s)
+    while (cur < i1) { flush(cur); ++cur; }
+  // teardown: make sure no bulk copy is still writing into shared memory
+  if (tid == 0) {
+    if (w3_issued && n_tiles > 0) tc::mbar_wait(bar_w3, 0, 1LL << 20);
+    for (int b = 0; b < 2; ++b)
+      while (z2_waited[b] < z2_issued[b]) {
+        if (!tc::mbar_wait(bar_z2 + b, (uint32_t)(z2_waited[b] & 1), 1LL << 20)) break;
+        z2_waited[b]++;
+      }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, G::NCOLS);
+}
+
+// ------------------------------------------------------------- self test
+// One M = 128, N = 32, K = 64 tile: D = A B^T with the canonical layouts.
+__global__ void umma_selftest(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ D,
+                              int* __restrict__ err) {
+  __shared__ __align__(1024) uint8_t sA[128 * 64 * 2];
+  __shared__ __align__(1024) uint8_t sB[32 * 64 * 2];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t holder;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int idx = tid; idx < 128 * 64; idx += blockDim.x)
+    *reinterpret_cast<__nv_bfloat16*>(sA + tc::canon_off(idx / 64, idx % 64)) = __float2bfloat16_rn(A[idx]);
+  for (int idx = tid; idx < 32 * 64; idx += blockDim.x)
+    *reinterpret_cast<__nv_bfloat16*>(sB + tc::canon_off(idx / 64, idx % 64)) = __float2bfloat16_rn(B[idx]);
+  tc::fence_proxy_async_smem();
+  if (warp == 0) {
+    tc::tmem_alloc(&holder, 32);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = holder;
+  if (tid == 0) {
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint64_t ad = tc::desc_noswizzle(tc::smem_u32(sA) + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+      const uint64_t bd = tc::desc_noswizzle(tc::smem_u32(sB) + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+      tc::mma_bf16(tbase, ad, bd, tc::idesc_bf16(128, 32), kk > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(&bar);
+  }
+  const bool ok = tc::mbar_wait(&bar, 0);
+  if (!ok && tid == 0) atomicOr(err, 1);
+  tc::fence_after_sync();
+  if (ok) {
+    for (int col = 0; col < 32; col += 8) {
+      float v[8];
+      tc::tmem_ld8(tbase + ((uint32_t)(warp * 32) << 16) + col, v);
+      tc::tmem_ld_wait();
+      for (int j = 0; j < 8; ++j) D[tid * 32 + col + j] = v[j];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 32);
+}
+
+template <int L, int MODE>
+int launch_group(int n, const int* row_ptr, const int* recv, const int* send, const float4* ev, const float* h,
+                 const uint8_t* w3img, const uint8_t* z2t, float s, float* m, int* err, int blocks, cudaStream_t st) {
+  using G = Group<L, MODE>;
+  const size_t smem = G::smem_bytes();
+  MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    MLIP_PROF("tp_fused", st);
+    tp_fused<L, MODE><<<blocks, 128, smem, st>>>(n, row_ptr, recv, send, ev, h, w3img, z2t, s, m, err);
+  }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+}  // namespace
+
+// Path-group layout of W3 for one layer: for each group (first layer: one group
+// of the l1 = 0 paths; later layers: one group per l3 = 0..L), the BF16 A
+// operands W3_p^T [128 channels][64 hidden] of its paths in the canonical
+// K-major layout, concatenated.  Byte offset of each group in *group_off.
+int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::vector<size_t>& group_off) {
+  const int P = M->P, C = M->C, H = M->H, L = M->L;
+  std::vector<int> l1s, l2s, l3s;
+  for (int a = 0; a <= L; ++a)
+    for (int b = 0; b <= 3; ++b)
+      for (int c3 = 0; c3 <= L; ++c3)
+        if (c3 >= std::abs(a - b) && c3 <= a + b && (a + b + c3) % 2 == 0) { l1s.push_back(a); l2s.push_back(b); l3s.push_back(c3); }
+  const float* W3 = M->host_weights.data() + (M->W3[t] - M->d_weights);
+  std::vector<std::vector<int>> groups;
+  if (t == 0) {
+    std::vector<int> g;
+    for (int p = 0; p < P; ++p) if (l1s[p] == 0) g.push_back(p);
+    groups.push_back(g);
+  } else {
+    for (int l3 = 0; l3 <= L; ++l3) {
+      std::vector<int> g;
+      for (int p = 0; p < P; ++p) if (l3s[p] == l3) g.push_back(p);
+      groups.push_back(g);
+    }
+  }
+  img.clear();
+  group_off.clear();
+  for (auto& g : groups) {
+    group_off.push_back(img.size());
+    for (int p : g) {
+      const size_t base = img.size();
+      img.resize(base + kW3PathBytes, 0);
+      for (int c = 0; c < C; ++c)
+        for (int k = 0; k < H; ++k) {
+          const __nv_bfloat16 v = __float2bfloat16_rn(W3[((size_t)k * P + p) * C + c]);
+          std::memcpy(&img[base + tc::canon_off(c, k)], &v, 2);
+        }
+    }
+  }
+  group_off.push_back(img.size());
+  return MLIP_OK;
+}
+
+int launch_radial_tiles(int H, int E, int n_tiles, const float4* ev, const float* W1, const float* W2, float rc,
+                        int p, uint8_t* z2t, cudaStream_t st) {
+  if (n_tiles <= 0) return MLIP_OK;
+  if (H != 64) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
+  const int threads = 128, blocks = (n_tiles * kNT + threads - 1) / threads;
+  { MLIP_PROF("radial_tiles", st); radial_tiles<64><<<blocks, threads, 0, st>>>(E, n_tiles, ev, W1, W2, rc, p, z2t); }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+// Forward message pass of one layer with the fused kernels (m written for all components).
+int launch_tp_fused(int L, bool first, int n, const int* row_ptr, const int* recv, const int* send,
+                    const float4* ev, const float* h, const uint8_t* w3img, const std::vector<size_t>& goff,
+                    const uint8_t* z2t, float s, float* m, int* err, cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = std::max(1, std::min(n, 2 * sms));
+#define MLIP_G(LL, MM, GI) \
+  MLIP_TRY((launch_group<LL, MM>(n, row_ptr, recv, send, ev, h, w3img + goff[GI], z2t, s, m, err, blocks, st)))
+  if (L == 2) {
+    if (first) { MLIP_G(2, -1, 0); }
+    else { MLIP_G(2, 0, 0); MLIP_G(2, 1, 1); MLIP_G(2, 2, 2); }
+  } else if (L == 3) {
+    if (first) { MLIP_G(3, -1, 0); }
+    else { MLIP_G(3, 0, 0); MLIP_G(3, 1, 1); MLIP_G(3, 2, 2); MLIP_G(3, 3, 3); }
+  } else {
+    set_error("l_max %d unsupported", L);
+    return MLIP_ERR_INVALID_ARG;
+  }
+#undef MLIP_G
+  return MLIP_OK;
+}
+
+int umma_selftest_run(double* rel_err) {
+  const int M = 128, N = 32, K = 64;
+  std::vector<float> A(M * K), B(N * K), D(M * N, 0.0f);
+  uint64_t st = 12345;
+  auto rnd = [&]() {
+    st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+    return (float)((st >> 40) & 0xFFFF) / 65536.0f - 0.5f;
+  };
+  for (auto& a : A) a = __bfloat162float(__float2bfloat16_rn(rnd()));
+  for (auto& b : B) b = __bfloat162float(__float2bfloat16_rn(rnd()));
+  float *dA, *dB, *dD;
+  int* derr;
+  MLIP_CUDA_TRY(cudaMalloc(&dA, A.size() * 4));
+  MLIP_CUDA_TRY(cudaMalloc(&dB, B.size() * 4));
+  MLIP_CUDA_TRY(cudaMalloc(&dD, D.size() * 4));
+  MLIP_CUDA_TRY(cudaMalloc(&derr, 4));
+  MLIP_CUDA_TRY(cudaMemcpy(dA, A.data(), A.size() * 4, cudaMemcpyHostToDevice));
+  MLIP_CUDA_TRY(cudaMemcpy(dB, B.data(), B.size() * 4, cudaMemcpyHostToDevice));
+  MLIP_CUDA_TRY(cudaMemset(dD, 0, D.size() * 4));
+  MLIP_CUDA_TRY(cudaMemset(derr, 0, 4));
+  { MLIP_PROF("umma_selftest", 0); umma_selftest<<<1, 128>>>(dA, dB, dD, derr); }
+  MLIP_LAUNCH_CHECK();
+  MLIP_CUDA_TRY(cudaDeviceSynchronize());
+  int herr = 0;
+  MLIP_CUDA_TRY(cudaMemcpy(D.data(), dD, D.size() * 4, cudaMemcpyDeviceToHost));
+  MLIP_CUDA_TRY(cudaMemcpy(&herr, derr, 4, cudaMemcpyDeviceToHost));
+  cudaFree(dA); cudaFree(dB); cudaFree(dD); cudaFree(derr);
+  if (herr) { set_error("tensor-core self test: MMA completion wait timed out"); return MLIP_ERR_DEVICE_TIMEOUT; }
+  double maxerr = 0, maxref = 0;
+  for (int i = 0; i < M; ++i)
+    for (int j = 0; j < N; ++j) {
+      double ref = 0;
+      for (int k = 0; k < K; ++k) ref += (double)A[i * K + k] * B[j * K + k];
+      maxerr = std::max(maxerr, std::fabs(ref - D[i * N + j]));
+      maxref = std::max(maxref, std::fabs(ref));
+    }
+  *rel_err = maxerr / std::max(maxref, 1e-30);
+  return MLIP_OK;
+}
+
+int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species, int64_t n64, const double* cell,
+                        const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+  Workspace& ws = M->ws;
+  const int n = (int)n64, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H;
+  const float s = (float)(1.0 / M->avg_nb);
+  if (d_forces || d_stress) {
+    set_error("the fused BF16 adjoint is not available in this build (energy only)");
+    return MLIP_ERR_INVALID_ARG;
+  }
+  int* flag = nullptr;
+  MLIP_TRY(ws.get("chk.flag", 2, &flag));
+  MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
+  MLIP_TRY(launch_check_inputs(n, d_pos, d_species, M->S, flag, st));
+  NeighborList nl;
+  MLIP_TRY(build_neighbors(ws, d_pos, n, cell, pbc, M->rc, true, st, &nl));
+  const int E = (int)nl.E;
+  const int n_tiles = (E + kNT - 1) / kNT;
+  const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)n * D * C;
+  CellArg ca{};
+  ca.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
+  for (int k = 0; k < 9; ++k) ca.h[k] = ca.any_pbc ? cell[k] : 0.0;
+  float4* ev = nullptr;
+  uint8_t* z2t = nullptr;
+  float* m = nullptr;
+  double* atom_e = nullptr;
+  MLIP_TRY(ws.get("ef.ev", Ec, &ev));
+  MLIP_TRY(ws.get("fz.z2t", (size_t)std::max(n_tiles, 1) * kTileBytes, &z2t));
+  MLIP_TRY(ws.get("ef.m", ND, &m));
+  MLIP_TRY(ws.get("ef.atom_e", (size_t)std::max(n, 1), &atom_e));
+  std::vector<float*> h(T + 1), u0(T);
+  for (int t = 0; t <= T; ++t) MLIP_TRY(ws.get("ef.h" + std::to_string(t), ND, &h[t]));
+  for (int t = 0; t < T; ++t) MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
+  MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st));
+  MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
+  for (int t = 0; t < T; ++t) {
+    MLIP_TRY(launch_radial_tiles(H, E, n_tiles, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, z2t, st));
+    MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, ev, h[t], M->d_w3img + M->w3_layer_off[t],
+                             M->w3_goff[t], z2t, s, m, flag + 1, st));
+    MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
+  }
+  MLIP_TRY(launch_energy(n, C, D, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
+  int hflag[2] = {0, 0};
+  MLIP_CUDA_TRY(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, st));
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hflag[0] & 1) { set_error("species index out of range"); return MLIP_ERR_INVALID_ARG; }
+  if (hflag[0] & 2) { set_error("non-finite position"); return MLIP_ERR_INVALID_ARG; }
+  if (hflag[1]) { set_error("fused kernel: a bounded wait timed out (code %d)", hflag[1]); return MLIP_ERR_DEVICE_TIMEOUT; }
+  return MLIP_OK;
 }
 
 }  // namespace mlip

@@ -30,6 +30,10 @@ int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, 
 int launch_forces_virial(Workspace& ws, int n, const int* row_ptr, const int* rev, const float4* g,
                          const float4* ev, double* forces, double* stress, double inv_vol, cudaStream_t st);
 
+int launch_check_inputs(int n, const double* pos, const int* species, int S, int* flag, cudaStream_t st);
+int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::vector<size_t>& group_off);
+int umma_selftest_run(double* rel_err);
+
 // Plain FP32 energy/forces/stress of one system whose positions and species
 // are on the device.  d_energy, d_forces (n x 3), d_stress (9) are device
 // pointers (forces/stress nullable).

@@ -99,6 +99,10 @@ struct mlip_model {
   const float* W_out = nullptr;
   const float* E0 = nullptr;
   std::vector<const float*> W1, W2, W3, Wmix;
+  // fused form: W3 of every layer as BF16 tensor-core operands, grouped by path group
+  uint8_t* d_w3img = nullptr;
+  std::vector<size_t> w3_layer_off;
+  std::vector<std::vector<size_t>> w3_goff;
   int device = 0;
   mlip::Workspace ws;
   mlip::HostStage stage;

@@ -1,0 +1,64 @@
+"""GPU checks of the fused BF16 form (tcgen05 radial MLP) against the FP64 oracle.
+
+BF16 tolerance (radial MLP inputs and weights rounded to BF16, FP32
+accumulation): energy |E - E_ref| <= 2e-3 max(|E_ref|, sum_i |E_i,ref|),
+forces max |F - F_ref| <= 2e-3 max |F_ref|.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-3
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    torch.cuda.init()
+    from paper_2605_22698_gb300 import build
+    build.build()
+    from paper_2605_22698_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def test_tensor_core_tile_selftest(B):
+    rel = B.mlip_selftest(1)
+    assert rel < 1e-5, rel
+
+
+@pytest.mark.parametrize("name,nmol", [("water", 100), ("water", 1000)])
+def test_fused_energy_water(B, name, nmol):
+    spec = synth.model_spec(name)
+    w = synth.make_weights(spec, 21)
+    s = synth.water_box(nmol, synth.water_side_for(nmol), seed=2)
+    ref = oracle.Model(spec, w).energy(s.pos, s.species, s.cell, s.pbc, atom_energies=True)
+    m = B.Model(spec, w, B.MLIP_PREC_BF16)
+    out = m.energy_forces(s.pos, s.species, s.cell, s.pbc, forces=False)
+    scale = max(abs(ref[0]), float(np.abs(ref[1]).sum()))
+    assert abs(out["energy"][0] - ref[0]) <= TOL * scale, (out["energy"][0], ref[0])
+
+
+def test_fused_energy_fcc_l3(B):
+    spec = synth.model_spec("fcc")
+    w = synth.make_weights(spec, 31)
+    s = synth.fcc((4, 4, 5), seed=3)
+    ref = oracle.Model(spec, w).energy(s.pos, s.species, s.cell, s.pbc, atom_energies=True)
+    m = B.Model(spec, w, B.MLIP_PREC_BF16)
+    out = m.energy_forces(s.pos, s.species, s.cell, s.pbc, forces=False)
+    scale = max(abs(ref[0]), float(np.abs(ref[1]).sum()))
+    assert abs(out["energy"][0] - ref[0]) <= TOL * scale, (out["energy"][0], ref[0])
+
+
+def test_fused_matches_plain_closely(B):
+    """Same model, FP32 plain vs fused BF16: the only difference is the BF16
+    rounding of the radial MLP's last layer inputs and weights."""
+    spec = synth.model_spec("water")
+    w = synth.make_weights(spec, 5)
+    s = synth.water_box(300, synth.water_side_for(300), seed=9)
+    a = B.Model(spec, w, B.MLIP_PREC_FP32).energy_forces(s.pos, s.species, s.cell, s.pbc, forces=False)
+    b = B.Model(spec, w, B.MLIP_PREC_BF16).energy_forces(s.pos, s.species, s.cell, s.pbc, forces=False)
+    assert abs(a["energy"][0] - b["energy"][0]) <= 1e-2 * max(1.0, abs(a["energy"][0]))
