@@ -138,6 +138,9 @@ int mlip_energy_forces(mlip_model* model, const double* pos, const int32_t* spec
  * tcgen05 tile product (M = 128, N = 32, K = 64, BF16 operands in the
  * shared-memory layout the fused kernels use, FP32 accumulation in tensor
  * memory) against a host FP64 product; *result = max |error| / max |value|.
+ * which = 2, 3: the transposed product of the adjoint (A read M-major from the
+ * forward weight image, K = 128), with the two possible assignments of the
+ * descriptor's leading/stride offsets; the kernels use the one that passes.
  * Errors: MLIP_ERR_INVALID_ARG (unknown test), MLIP_ERR_DEVICE_TIMEOUT (the
  * MMA completion wait ran out), MLIP_ERR_CUDA. */
 int mlip_selftest(int which, double* result);

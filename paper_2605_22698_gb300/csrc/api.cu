@@ -180,6 +180,7 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
 int mlip_selftest(int which, double* result) {
   if (!result) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
   if (which == 1) return umma_selftest_run(result);
+  if (which == 2 || which == 3) return umma_selftest_mn_run(which - 2, result);
   set_error("unknown self test %d", which);
   return MLIP_ERR_INVALID_ARG;
 }

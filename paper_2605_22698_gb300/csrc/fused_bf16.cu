@@ -380,6 +380,66 @@ __global__ void umma_selftest(const float* __restrict__ A, const float* __restri
   if (warp == 0) tc::tmem_dealloc(tbase, 32);
 }
 
+// MN-major A operand check for the adjoint GEMM: A' = W^T read from the
+// forward K-major image of W [128 rows (c)][64 (k)]: A'[k][c] (64 valid rows of
+// an M = 128 MMA), B = X [32][128] K-major (K = 128 channels).  `variant`
+// selects which descriptor offset is the K-direction stride.
+__global__ void umma_selftest_mn(const float* __restrict__ W, const float* __restrict__ X, float* __restrict__ D,
+                                 int variant, int* __restrict__ err) {
+  __shared__ __align__(1024) uint8_t sA[32768];
+  __shared__ __align__(1024) uint8_t sB[32 * 128 * 2];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t holder;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int idx = tid; idx < 32768 / 4; idx += blockDim.x) reinterpret_cast<uint32_t*>(sA)[idx] = 0u;
+  __syncthreads();
+  for (int idx = tid; idx < 128 * 64; idx += blockDim.x)  // W[c][k] at canon_off(c, k)
+    *reinterpret_cast<__nv_bfloat16*>(sA + tc::canon_off(idx / 64, idx % 64)) = __float2bfloat16_rn(W[idx]);
+  for (int idx = tid; idx < 32 * 128; idx += blockDim.x) {  // X[e][c], K = 128
+    const int e = idx / 128, c = idx % 128;
+    *reinterpret_cast<__nv_bfloat16*>(sB + (e >> 3) * 2048 + (c >> 3) * 128 + (e & 7) * 16 + (c & 7) * 2) =
+        __float2bfloat16_rn(X[idx]);
+  }
+  tc::fence_proxy_async_smem();
+  if (warp == 0) {
+    tc::tmem_alloc(&holder, 32);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = holder;
+  if (tid == 0) {
+    const uint32_t kstride = 1024, mstride = 128;  // along K' (channel groups) and M' (hidden groups)
+    const uint32_t lbo = variant == 0 ? kstride : mstride, sbo = variant == 0 ? mstride : kstride;
+    const uint32_t idesc = tc::idesc_bf16(128, 32) | (1u << 15);  // A MN-major
+    for (int kk = 0; kk < 8; ++kk) {
+      const uint64_t ad = tc::desc_noswizzle(tc::smem_u32(sA) + kk * 2 * kstride, lbo, sbo);
+      const uint64_t bd = tc::desc_noswizzle(tc::smem_u32(sB) + kk * 256, 128, 2048);
+      tc::mma_bf16(tbase, ad, bd, idesc, kk > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(&bar);
+  }
+  const bool ok = tc::mbar_wait(&bar, 0);
+  if (!ok && tid == 0) atomicOr(err, 1);
+  tc::fence_after_sync();
+  if (ok) {
+    for (int col = 0; col < 32; col += 8) {
+      float v[8];
+      tc::tmem_ld8(tbase + ((uint32_t)(warp * 32) << 16) + col, v);
+      tc::tmem_ld_wait();
+      for (int j = 0; j < 8; ++j) D[tid * 32 + col + j] = v[j];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 32);
+}
+
 template <int L, int MODE>
 int launch_group(int n, const int* row_ptr, const int* recv, const int* send, const float4* ev, const float* h,
                  const uint8_t* w3img, const uint8_t* z2t, float s, float* m, int* err, int blocks, cudaStream_t st) {
@@ -507,6 +567,45 @@ int umma_selftest_run(double* rel_err) {
       double ref = 0;
       for (int k = 0; k < K; ++k) ref += (double)A[i * K + k] * B[j * K + k];
       maxerr = std::max(maxerr, std::fabs(ref - D[i * N + j]));
+      maxref = std::max(maxref, std::fabs(ref));
+    }
+  *rel_err = maxerr / std::max(maxref, 1e-30);
+  return MLIP_OK;
+}
+
+int umma_selftest_mn_run(int variant, double* rel_err) {
+  std::vector<float> W(128 * 64), X(32 * 128), D(128 * 32, 0.0f);
+  uint64_t st = 777;
+  auto rnd = [&]() {
+    st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+    return (float)((st >> 40) & 0xFFFF) / 65536.0f - 0.5f;
+  };
+  for (auto& a : W) a = __bfloat162float(__float2bfloat16_rn(rnd()));
+  for (auto& b : X) b = __bfloat162float(__float2bfloat16_rn(rnd()));
+  float *dW, *dX, *dD;
+  int* derr;
+  MLIP_CUDA_TRY(cudaMalloc(&dW, W.size() * 4));
+  MLIP_CUDA_TRY(cudaMalloc(&dX, X.size() * 4));
+  MLIP_CUDA_TRY(cudaMalloc(&dD, D.size() * 4));
+  MLIP_CUDA_TRY(cudaMalloc(&derr, 4));
+  MLIP_CUDA_TRY(cudaMemcpy(dW, W.data(), W.size() * 4, cudaMemcpyHostToDevice));
+  MLIP_CUDA_TRY(cudaMemcpy(dX, X.data(), X.size() * 4, cudaMemcpyHostToDevice));
+  MLIP_CUDA_TRY(cudaMemset(dD, 0, D.size() * 4));
+  MLIP_CUDA_TRY(cudaMemset(derr, 0, 4));
+  { MLIP_PROF("umma_selftest_mn", 0); umma_selftest_mn<<<1, 128>>>(dW, dX, dD, variant, derr); }
+  MLIP_LAUNCH_CHECK();
+  MLIP_CUDA_TRY(cudaDeviceSynchronize());
+  int herr = 0;
+  MLIP_CUDA_TRY(cudaMemcpy(D.data(), dD, D.size() * 4, cudaMemcpyDeviceToHost));
+  MLIP_CUDA_TRY(cudaMemcpy(&herr, derr, 4, cudaMemcpyDeviceToHost));
+  cudaFree(dW); cudaFree(dX); cudaFree(dD); cudaFree(derr);
+  if (herr) { set_error("tensor-core self test: MMA completion wait timed out"); return MLIP_ERR_DEVICE_TIMEOUT; }
+  double maxerr = 0, maxref = 0;
+  for (int k = 0; k < 64; ++k)
+    for (int e = 0; e < 32; ++e) {
+      double ref = 0;
+      for (int c = 0; c < 128; ++c) ref += (double)W[c * 64 + k] * X[e * 128 + c];
+      maxerr = std::max(maxerr, std::fabs(ref - D[k * 32 + e]));
       maxref = std::max(maxref, std::fabs(ref));
     }
   *rel_err = maxerr / std::max(maxref, 1e-30);

@@ -33,6 +33,7 @@ int launch_forces_virial(Workspace& ws, int n, const int* row_ptr, const int* re
 int launch_check_inputs(int n, const double* pos, const int* species, int S, int* flag, cudaStream_t st);
 int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::vector<size_t>& group_off);
 int umma_selftest_run(double* rel_err);
+int umma_selftest_mn_run(int variant, double* rel_err);
 
 // Plain FP32 energy/forces/stress of one system whose positions and species
 // are on the device.  d_energy, d_forces (n x 3), d_stress (9) are device
