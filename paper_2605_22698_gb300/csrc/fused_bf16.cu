@@ -18,6 +18,7 @@
 // The per-edge radial weights never reach HBM.
 #include <algorithm>
 #include <array>
+#include <cmath>
 #include <cstring>
 
 #include <cuda_bf16.h>
@@ -330,6 +331,362 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
   if (warp == 0) tc::tmem_dealloc(tbase, G::NCOLS);
 }
 
+// ------------------------------------------------------------ tp_fused_bwd
+// Adjoint of one layer for one path group.  Per tile of kNT receiver-sorted
+// edges: (1) w = W3_p^T z2 recomputed on the tensor cores into tensor memory;
+// (2) thread c (channel c), per edge e = (j <- i):
+//       G^{t-1}_j[l1 m1] += s w[p] (-1)^{l2} C Y[l2 m2] Gm_i[l3 m3]        (reverse edge)
+//       T_p[m2] = sum C h_i[l1 m1] Gt_j[l3 m3],   Gt = s Gm_j
+//       dE/dw_e[p] = sum_m2 Y[l2 m2] T_p[m2]   -> BF16 operand tile in shared memory
+//       dE/dY_e[l2 m2] += sum_c w[p] T_p[m2]   (channel sum: warp butterfly + shared memory)
+// (3) dE/dz2[k][e] = sum_{p,c} W3[k][p][c] dE/dw_e[p][c]: a second MMA with A
+// read M-major from the same resident W3 image (rows 64..127 of that M = 128
+// product are unused), accumulated into dz2[e][k].  Group kernels of one layer
+// run one after another on the stream, so G^{t-1}, dY and dz2 are updated
+// with plain read-modify-writes (the first group writes G^{t-1} = G^t + ...).
+constexpr bool kMnLboIsK = true;  // descriptor assignment checked by mlip_selftest(2 / 3)
+
+template <int L, int MODE>
+struct BwdLayout {
+  using G = Group<L, MODE>;
+  static constexpr int NP = G::NP;
+  static constexpr bool FIRST = MODE < 0;
+  static constexpr int B2_BYTES = kNT * NP * 128 * 2;
+  static constexpr int NZP = FIRST ? 4 : G::NZP;
+  static constexpr int tmem_cols() {
+    int need = (NP + 1) * kNT, c = 32;
+    while (c < need) c <<= 1;
+    return c;
+  }
+  static constexpr int NCOLS = tmem_cols();
+  static constexpr size_t smem_bytes() {
+    return (size_t)NP * kW3PathBytes + 2 * kTileBytes + B2_BYTES + (size_t)kNT * NZP * 4 + kNT * 16 * 4 +
+           4 * kNT * 16 * 4 + 2 * kNT * 4 + 64;
+  }
+};
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict__ row_ptr,
+                                                    const int* __restrict__ recv, const int* __restrict__ send,
+                                                    const float4* __restrict__ ev, const float* __restrict__ hprev,
+                                                    const float* __restrict__ Gm, const uint8_t* __restrict__ w3img,
+                                                    const uint8_t* __restrict__ z2t, float s,
+                                                    const float* __restrict__ Gin, float* __restrict__ Gout,
+                                                    int first_group, float* __restrict__ dY, float* __restrict__ dz2,
+                                                    int* __restrict__ err) {
+  using G = Group<L, MODE>;
+  using BL = BwdLayout<L, MODE>;
+  using Tab = CGTable<L>;
+  constexpr int D = NodeDims<L>::D;
+  constexpr int C = 128;
+  constexpr int NP = G::NP;
+  constexpr bool FIRST = BL::FIRST;
+  constexpr int NZP = BL::NZP;
+  constexpr int SBO2 = NP * 2048;  // B' operand: K' = NP * 128 channels
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sW3 = smem;
+  uint8_t* sZ2 = sW3 + NP * kW3PathBytes;
+  uint8_t* sB2 = sZ2 + 2 * kTileBytes;
+  float* cY = reinterpret_cast<float*>(sB2 + BL::B2_BYTES);
+  float* sY = cY + kNT * NZP;
+  float* red = sY + kNT * 16;  // [4][kNT][16]
+  int* s_send = reinterpret_cast<int*>(red + 4 * kNT * 16);
+  int* s_recv = s_send + kNT;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(s_recv + kNT);
+  uint64_t* bar_w3 = bars;
+  uint64_t* bar_z2 = bars + 1;  // [2]
+  uint64_t* bar_mma = bars + 3;
+  uint64_t* bar_mma2 = bars + 4;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 5);
+  __shared__ int abort_s;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, c = tid;
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, BL::NCOLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(bar_w3, 1);
+    tc::mbar_init(bar_z2, 1);
+    tc::mbar_init(bar_z2 + 1, 1);
+    tc::mbar_init(bar_mma, 1);
+    tc::mbar_init(bar_mma2, 1);
+    tc::fence_mbar_init();
+    abort_s = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tmem_holder;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t dcol = NP * kNT;  // columns of dE/dz2 in tensor memory
+
+  int i0, i1;
+  block_receivers(row_ptr, n, blockIdx.x, gridDim.x, &i0, &i1);
+  const int E0 = row_ptr[i0], E1 = row_ptr[i1];
+  const int t_begin = E0 / kNT, t_end = (E1 > E0) ? (E1 + kNT - 1) / kNT : t_begin;
+  const int n_tiles = t_end - t_begin;
+
+  int z2_issued[2] = {0, 0}, z2_waited[2] = {0, 0};
+  bool w3_issued = false;
+  if (tid == 0 && n_tiles > 0) {
+    tc::mbar_arrive_expect_tx(bar_w3, NP * kW3PathBytes);
+#pragma unroll 1
+    for (int sl = 0; sl < NP; ++sl)
+      tc::bulk_g2s(sW3 + sl * kW3PathBytes, w3img + (size_t)sl * kW3PathBytes, kW3PathBytes, bar_w3);
+    w3_issued = true;
+    tc::mbar_arrive_expect_tx(bar_z2, kTileBytes);
+    tc::bulk_g2s(sZ2, z2t + (size_t)t_begin * kTileBytes, kTileBytes, bar_z2);
+    z2_issued[0] = 1;
+  }
+
+  float Gacc[D], Gt[G::NOUT];
+#pragma unroll
+  for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < G::NOUT; ++q) Gt[q] = 0.0f;
+  int cur = i0 - 1;
+  auto flush = [&](int i) {
+    if (!FIRST) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const size_t o = ((size_t)i * D + d) * C + c;
+        Gout[o] = (first_group ? Gin[o] : Gout[o]) + Gacc[d];
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
+  };
+  auto enter = [&](int i) {
+#pragma unroll
+    for (int q = 0; q < G::NOUT; ++q) Gt[q] = s * Gm[((size_t)i * D + G::comp0 + q) * C + c];
+  };
+  auto advance = [&](int r) {
+    while (cur < r) {
+      if (cur >= i0) flush(cur);
+      ++cur;
+      if (cur < i1) enter(cur);
+    }
+  };
+  constexpr uint32_t idesc1 = tc::idesc_bf16(128, kNT);
+  constexpr uint32_t idesc2 = tc::idesc_bf16(128, kNT) | (1u << 15);  // A M-major
+
+#pragma unroll 1
+  for (int it = 0; it < n_tiles; ++it) {
+    const int tile = t_begin + it;
+    const int buf = it & 1;
+    if (tid < kNT) {
+      const int e = tile * kNT + tid;
+      const bool valid = e >= E0 && e < E1;
+      s_recv[tid] = valid ? recv[e] : -1;
+      s_send[tid] = valid ? send[e] : 0;
+      if (valid) {
+        const float4 v = ev[e];
+        const float ir = 1.0f / v.w;
+        float Y[16];
+        sh3<float>(v.x * ir, v.y * ir, v.z * ir, Y);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) sY[tid * 16 + k] = Y[k];
+        if constexpr (!FIRST) {
+          float* dst = cY + tid * NZP;
+          static_for<0, NP>([&](auto sc) {
+            constexpr int sl = decltype(sc)::value;
+            constexpr int p = G::paths[sl];
+            constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
+            static_for<kb, ke>([&](auto kc) {
+              constexpr int k = decltype(kc)::value;
+              constexpr float cv = ((Tab::l2[p] & 1) ? -1.0f : 1.0f) * Tab::ec[k];
+              constexpr int i2 = Tab::e2[k];
+              dst[gb + k - kb] = cv * Y[i2];
+            });
+          });
+        }
+      }
+    }
+    if (tid == 0) {
+      bool ok = true;
+      if (it + 1 < n_tiles) {
+        const int nb = buf ^ 1;
+        tc::mbar_arrive_expect_tx(bar_z2 + nb, kTileBytes);
+        tc::bulk_g2s(sZ2 + nb * kTileBytes, z2t + (size_t)(tile + 1) * kTileBytes, kTileBytes, bar_z2 + nb);
+        z2_issued[nb]++;
+      }
+      if (it == 0) ok = ok && tc::mbar_wait(bar_w3, 0);
+      ok = ok && tc::mbar_wait(bar_z2 + buf, (uint32_t)(z2_waited[buf] & 1));
+      if (ok) {
+        z2_waited[buf]++;
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sZ2 + buf * kTileBytes);
+#pragma unroll 1
+        for (int sl = 0; sl < NP; ++sl)
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+            const uint64_t bd = tc::desc_noswizzle(b0 + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+            tc::mma_bf16(tbase + sl * kNT, ad, bd, idesc1, kk > 0 ? 1u : 0u);
+          }
+        tc::mma_commit(bar_mma);
+      } else {
+        atomicOr(err, 4);
+        abort_s = 1;
+      }
+    }
+    __syncthreads();
+    if (abort_s) break;
+    if (!tc::mbar_wait(bar_mma, (uint32_t)(it & 1))) {
+      atomicOr(err, 8);
+      abort_s = 1;
+    }
+    tc::fence_after_sync();
+#pragma unroll 1
+    for (int ch = 0; ch < kNT / 8; ++ch) {
+      float wv[NP][8];
+#pragma unroll
+      for (int sl = 0; sl < NP; ++sl) tc::tmem_ld8(tbase + lane_off + sl * kNT + ch * 8, wv[sl]);
+      tc::tmem_ld_wait();
+#pragma unroll 1
+      for (int j = 0; j < 8; ++j) {
+        const int t = ch * 8 + j;
+        const int r = s_recv[t];
+        float dYp[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dYp[k] = 0.0f;
+        float wsel[NP];
+#pragma unroll
+        for (int sl = 0; sl < NP; ++sl) {
+          float x = wv[sl][0];
+#pragma unroll
+          for (int q = 1; q < 8; ++q) x = (j == q) ? wv[sl][q] : x;
+          wsel[sl] = x;
+        }
+        if (r >= 0) {
+          advance(r);
+          const int si = s_send[t];
+          float hi[G::DH];
+#pragma unroll
+          for (int d = 0; d < G::DH; ++d) hi[d] = hprev[((size_t)si * D + d) * C + c];
+          float Y[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
+          float Gi[G::NOUT];
+          if constexpr (!FIRST) {
+#pragma unroll
+            for (int q = 0; q < G::NOUT; ++q) Gi[q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
+          }
+          const float* cy = cY + t * NZP;
+          static_for<0, NP>([&](auto sc) {
+            constexpr int sl = decltype(sc)::value;
+            constexpr int p = G::paths[sl];
+            constexpr int l2 = Tab::l2[p], l3 = Tab::l3[p];
+            constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
+            const float wp = wsel[sl];
+            if constexpr (!FIRST) {
+              float wg[2 * l3 + 1];
+#pragma unroll
+              for (int q = 0; q < 2 * l3 + 1; ++q) wg[q] = s * wp * Gi[l3 * l3 + q - G::comp0];
+              static_for<kb, ke>([&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                constexpr int i1 = Tab::e1[k], j3 = Tab::e3[k] - l3 * l3;
+                Gacc[i1] = fmaf(cy[gb + k - kb], wg[j3], Gacc[i1]);
+              });
+            }
+            float Tp[2 * l2 + 1];
+#pragma unroll
+            for (int q = 0; q < 2 * l2 + 1; ++q) Tp[q] = 0.0f;
+            static_for<kb, ke>([&](auto kc) {
+              constexpr int k = decltype(kc)::value;
+              constexpr int j2 = Tab::e2[k] - l2 * l2, i1 = Tab::e1[k], o3 = Tab::e3[k] - G::comp0;
+              constexpr float cv = Tab::ec[k];
+              Tp[j2] = fmaf(cv, hi[i1] * Gt[o3], Tp[j2]);
+            });
+            float dwp = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 2 * l2 + 1; ++q) {
+              dwp = fmaf(Y[l2 * l2 + q], Tp[q], dwp);
+              dYp[l2 * l2 + q] = fmaf(wp, Tp[q], dYp[l2 * l2 + q]);
+            }
+            const int kidx = sl * 128 + c;
+            *reinterpret_cast<__nv_bfloat16*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) =
+                __float2bfloat16_rn(dwp);
+          });
+        } else {
+          // edge outside this block's range: zero operand row
+#pragma unroll
+          for (int sl = 0; sl < NP; ++sl) {
+            const int kidx = sl * 128 + c;
+            *reinterpret_cast<__nv_bfloat16*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) =
+                __float2bfloat16_rn(0.0f);
+          }
+        }
+        const float tot = warp_reduce16(dYp);
+        if ((lane & 1) == 0) red[(warp * kNT + t) * 16 + (lane >> 1)] = tot;
+      }
+    }
+    // second product: dE/dz2 = W3 dE/dw over this tile
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sB2);
+      const uint32_t kstride = 1024, mstride = 128;
+      const uint32_t lbo = kMnLboIsK ? kstride : mstride, sbo = kMnLboIsK ? mstride : kstride;
+#pragma unroll 1
+      for (int sl = 0; sl < NP; ++sl)
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 2 * kstride, lbo, sbo);
+          const uint64_t bd = tc::desc_noswizzle(b0 + sl * 2048 + kk * 256, 128, SBO2);
+          tc::mma_bf16(tbase + dcol, ad, bd, idesc2, (sl | kk) ? 1u : 0u);
+        }
+      tc::mma_commit(bar_mma2);
+    }
+    // channel sums of dE/dY while the product runs
+    for (int q = tid; q < kNT * 16; q += blockDim.x) {
+      const int t = q >> 4, k = q & 15;
+      const int e = tile * kNT + t;
+      if (e >= E0 && e < E1) {
+        const float v = red[(0 * kNT + t) * 16 + k] + red[(1 * kNT + t) * 16 + k] + red[(2 * kNT + t) * 16 + k] +
+                        red[(3 * kNT + t) * 16 + k];
+        dY[(size_t)e * 16 + k] += v;
+      }
+    }
+    if (!tc::mbar_wait(bar_mma2, (uint32_t)(it & 1))) {
+      atomicOr(err, 16);
+      abort_s = 1;
+    }
+    tc::fence_after_sync();
+    if (warp < 2) {  // lanes 0..63 hold hidden units k = 0..63
+#pragma unroll 1
+      for (int ch = 0; ch < kNT / 8; ++ch) {
+        float v[8];
+        tc::tmem_ld8(tbase + lane_off + dcol + ch * 8, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int e = tile * kNT + ch * 8 + j;
+          if (e >= E0 && e < E1) dz2[(size_t)e * 64 + tid] += v[j];
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (abort_s) break;
+  }
+  if (!abort_s) advance(i1);
+  if (tid == 0) {
+    if (w3_issued && n_tiles > 0) tc::mbar_wait(bar_w3, 0, 1LL << 20);
+    for (int b = 0; b < 2; ++b)
+      while (z2_waited[b] < z2_issued[b]) {
+        if (!tc::mbar_wait(bar_z2 + b, (uint32_t)(z2_waited[b] & 1), 1LL << 20)) break;
+        z2_waited[b]++;
+      }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, BL::NCOLS);
+}
+
 // ------------------------------------------------------------- self test
 // One M = 128, N = 32, K = 64 tile: D = A B^T with the canonical layouts.
 __global__ void umma_selftest(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ D,
@@ -454,6 +811,23 @@ int launch_group(int n, const int* row_ptr, const int* recv, const int* send, co
   return MLIP_OK;
 }
 
+template <int L, int MODE>
+int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send, const float4* ev,
+                     const float* hprev, const float* Gm, const uint8_t* w3img, const uint8_t* z2t, float s,
+                     const float* Gin, float* Gout, int first_group, float* dY, float* dz2, int* err, int blocks,
+                     cudaStream_t st) {
+  using BL = BwdLayout<L, MODE>;
+  const size_t smem = BL::smem_bytes();
+  MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused_bwd<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    MLIP_PROF("tp_fused_bwd", st);
+    tp_fused_bwd<L, MODE><<<blocks, 128, smem, st>>>(n, row_ptr, recv, send, ev, hprev, Gm, w3img, z2t, s, Gin,
+                                                    Gout, first_group, dY, dz2, err);
+  }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
 }  // namespace
 
 // Path-group layout of W3 for one layer: for each group (first layer: one group
@@ -530,6 +904,33 @@ int launch_tp_fused(int L, bool first, int n, const int* row_ptr, const int* rec
     return MLIP_ERR_INVALID_ARG;
   }
 #undef MLIP_G
+  return MLIP_OK;
+}
+
+// Adjoint message pass of one layer with the fused kernels (all groups in order).
+int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int* recv, const int* send,
+                        const float4* ev, const float* hprev, const float* Gm, const uint8_t* w3img,
+                        const std::vector<size_t>& goff, const uint8_t* z2t, float s, const float* Gin, float* Gout,
+                        float* dY, float* dz2, int* err, cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = std::max(1, std::min(n, sms));
+#define MLIP_GB(LL, MM, GI) \
+  MLIP_TRY((launch_group_bwd<LL, MM>(n, row_ptr, recv, send, ev, hprev, Gm, w3img + goff[GI], z2t, s, Gin, Gout, \
+                                     GI == 0, dY, dz2, err, blocks, st)))
+  if (L == 2) {
+    if (first) { MLIP_GB(2, -1, 0); }
+    else { MLIP_GB(2, 0, 0); MLIP_GB(2, 1, 1); MLIP_GB(2, 2, 2); }
+  } else if (L == 3) {
+    if (first) { MLIP_GB(3, -1, 0); }
+    else { MLIP_GB(3, 0, 0); MLIP_GB(3, 1, 1); MLIP_GB(3, 2, 2); MLIP_GB(3, 3, 3); }
+  } else {
+    set_error("l_max %d unsupported", L);
+    return MLIP_ERR_INVALID_ARG;
+  }
+#undef MLIP_GB
   return MLIP_OK;
 }
 
@@ -617,10 +1018,6 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
   Workspace& ws = M->ws;
   const int n = (int)n64, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H;
   const float s = (float)(1.0 / M->avg_nb);
-  if (d_forces || d_stress) {
-    set_error("the fused BF16 adjoint is not available in this build (energy only)");
-    return MLIP_ERR_INVALID_ARG;
-  }
   int* flag = nullptr;
   MLIP_TRY(ws.get("chk.flag", 2, &flag));
   MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
@@ -633,26 +1030,57 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
   CellArg ca{};
   ca.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
   for (int k = 0; k < 9; ++k) ca.h[k] = ca.any_pbc ? cell[k] : 0.0;
-  float4* ev = nullptr;
-  uint8_t* z2t = nullptr;
-  float* m = nullptr;
+  float4 *ev = nullptr, *g = nullptr;
+  float *m = nullptr, *Gm = nullptr, *Ga = nullptr, *Gb = nullptr, *dY = nullptr, *dr = nullptr, *dz2 = nullptr;
   double* atom_e = nullptr;
   MLIP_TRY(ws.get("ef.ev", Ec, &ev));
-  MLIP_TRY(ws.get("fz.z2t", (size_t)std::max(n_tiles, 1) * kTileBytes, &z2t));
   MLIP_TRY(ws.get("ef.m", ND, &m));
   MLIP_TRY(ws.get("ef.atom_e", (size_t)std::max(n, 1), &atom_e));
   std::vector<float*> h(T + 1), u0(T);
+  std::vector<uint8_t*> z2t(T);
   for (int t = 0; t <= T; ++t) MLIP_TRY(ws.get("ef.h" + std::to_string(t), ND, &h[t]));
-  for (int t = 0; t < T; ++t) MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
+  for (int t = 0; t < T; ++t) {
+    MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
+    MLIP_TRY(ws.get("fz.z2t" + std::to_string(t), (size_t)std::max(n_tiles, 1) * kTileBytes, &z2t[t]));
+  }
   MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st));
   MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
   for (int t = 0; t < T; ++t) {
-    MLIP_TRY(launch_radial_tiles(H, E, n_tiles, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, z2t, st));
+    MLIP_TRY(launch_radial_tiles(H, E, n_tiles, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, z2t[t], st));
     MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, ev, h[t], M->d_w3img + M->w3_layer_off[t],
-                             M->w3_goff[t], z2t, s, m, flag + 1, st));
+                             M->w3_goff[t], z2t[t], s, m, flag + 1, st));
     MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
   }
   MLIP_TRY(launch_energy(n, C, D, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
+  if (d_forces || d_stress) {
+    MLIP_TRY(ws.get("ef.g", Ec, &g));
+    MLIP_TRY(ws.get("ef.Gm", ND, &Gm));
+    MLIP_TRY(ws.get("ef.Ga", ND, &Ga));
+    MLIP_TRY(ws.get("ef.Gb", ND, &Gb));
+    MLIP_TRY(ws.get("ef.dY", Ec * 16, &dY));
+    MLIP_TRY(ws.get("ef.dr", Ec, &dr));
+    MLIP_TRY(ws.get("fz.dz2", Ec * 64, &dz2));
+    MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, Ga, st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(dr, 0, Ec * sizeof(float), st));
+    for (int t = T - 1; t >= 0; --t) {
+      MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], Gm, st));
+      MLIP_CUDA_TRY(cudaMemsetAsync(dz2, 0, Ec * 64 * sizeof(float), st));
+      MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, ev, h[t], Gm,
+                                   M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, Ga, Gb, dY, dz2,
+                                   flag + 1, st));
+      MLIP_TRY(launch_radial_bwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, st));
+      std::swap(Ga, Gb);
+    }
+    MLIP_TRY(launch_edge_grad(E, ev, dY, dr, g, st));
+    double* fbuf = d_forces;
+    if (!fbuf) MLIP_TRY(ws.get("ef.fscratch", (size_t)3 * std::max(n, 1), &fbuf));
+    const double vol = ca.any_pbc ? std::fabs(cell[0] * (cell[4] * cell[8] - cell[5] * cell[7]) -
+                                              cell[1] * (cell[3] * cell[8] - cell[5] * cell[6]) +
+                                              cell[2] * (cell[3] * cell[7] - cell[4] * cell[6]))
+                                  : 1.0;
+    MLIP_TRY(launch_forces_virial(ws, n, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, 1.0 / vol, st));
+  }
   int hflag[2] = {0, 0};
   MLIP_CUDA_TRY(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, st));
   MLIP_CUDA_TRY(cudaStreamSynchronize(st));
