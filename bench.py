@@ -153,23 +153,62 @@ def time_oracle(name: str, min_seconds: float, max_evals: int = 1000):
             "sample": f"{desc}; {k} energy+force(+stress) evaluations in {dt:.1f} s"}
 
 
-def algorithmic_flops(spec, E: int, n: int):
-    """Algorithmic FP32 flops per step for the kernels of the plain form
-    (per-edge and per-node counts written out in the design notes)."""
-    import oracle  # noqa: F401  (paths only; counting, not arithmetic)
-    P0 = spec.L + 1
-    paths = []
+# Nonzero real Clebsch-Gordan entries of each coupling path (l1, l2, l3),
+# natural parity, l2 <= 3: a property of the paths (counted once from the
+# coupling tables), used for the algorithmic flop counts below.
+CG_NNZ = {
+    (0, 0, 0): 1, (0, 1, 1): 3, (0, 2, 2): 5, (0, 3, 3): 7, (1, 0, 1): 3, (1, 1, 0): 3, (1, 1, 2): 11,
+    (1, 2, 1): 11, (1, 2, 3): 21, (1, 3, 2): 21, (2, 0, 2): 5, (2, 1, 1): 11, (2, 1, 3): 21, (2, 2, 0): 5,
+    (2, 2, 2): 25, (2, 3, 1): 21, (2, 3, 3): 41, (3, 0, 3): 7, (3, 1, 2): 21, (3, 2, 1): 21, (3, 2, 3): 41,
+    (3, 3, 0): 7, (3, 3, 2): 41,
+}
+
+
+def model_paths(spec):
+    out = []
     for l1 in range(spec.L + 1):
         for l2 in range(spec.Lsh + 1):
             for l3 in range(spec.L + 1):
                 if abs(l1 - l2) <= l3 <= l1 + l2 and (l1 + l2 + l3) % 2 == 0:
-                    paths.append((l1, l2, l3))
-    P = len(paths)
+                    out.append((l1, l2, l3))
+    return out
+
+
+def tp_flops_per_edge_channel(spec, first: bool, backward: bool) -> int:
+    """FP32 flops of the tensor product per edge and channel.
+    forward:  per path (2 l1 + 1) products w h, then 2 flops per CG entry;
+    backward: dE/dh (not first layer): 2 (2 l3 + 1) products s w Gm + 2 per entry;
+              T_p: 3 per entry (h Gt product, FMA with the coefficient);
+              dE/dw and dE/dY: 2 (2 l2 + 1) each."""
+    tot = 0
+    for (l1, l2, l3) in model_paths(spec):
+        if first and l1 != 0:
+            continue
+        nz = CG_NNZ[(l1, l2, l3)]
+        if not backward:
+            tot += (2 * l1 + 1) + 2 * nz
+        else:
+            if not first:
+                tot += 2 * (2 * l3 + 1) + 2 * nz
+            tot += 3 * nz + 4 * (2 * l2 + 1)
+    return tot
+
+
+def algorithmic_flops(spec, E: int, n: int):
+    """Algorithmic flops per step per kernel name (edge counts x per-edge work)."""
+    P0 = spec.L + 1
+    P = len(model_paths(spec))
     C, H, T = spec.C, spec.H, spec.T
-    # w = z2 W3 forward and dz2 = dw W3^T backward, per layer (first layer: l1 = 0 paths)
     pw = [P0] + [P] * (T - 1)
-    sgemm = sum(2 * 2 * E * H * C * p for p in pw)
-    return {"sgemm": sgemm}
+    fwd_tp = sum(tp_flops_per_edge_channel(spec, t == 0, False) for t in range(T)) * E * C
+    bwd_tp = sum(tp_flops_per_edge_channel(spec, t == 0, True) for t in range(T)) * E * C
+    mlp_out = sum(2 * E * H * C * p for p in pw)          # w = z2 W3 (one product)
+    return {
+        "sgemm": 2 * mlp_out,                              # forward w and backward dz2 (plain form)
+        "tp_fwd": fwd_tp, "tp_bwd": bwd_tp,
+        "tp_fused": fwd_tp, "tp_fused_bwd": bwd_tp,        # FP32 ALU work; the MMAs run on the tensor pipe
+        "tensor_fused": mlp_out, "tensor_fused_bwd": 2 * mlp_out,
+    }
 
 
 def run_ours(args, rank, world):
@@ -178,7 +217,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda", torch.cuda.current_device())
     spec, w, s = workload(args.workload, rank)
-    prec = {"fp32": B.MLIP_PREC_FP32, "bf16": B.MLIP_PREC_BF16}[args.precision]
+    prec = {"fp32": B.MLIP_PREC_FP32, "bf16": B.MLIP_PREC_BF16, "f16": B.MLIP_PREC_F16}[args.precision]
     model = B.Model(spec, w, prec)
     pos = torch.tensor(s.pos, device=dev)
     sp = torch.tensor(s.species, device=dev)
@@ -262,7 +301,12 @@ def run_ours(args, rank, world):
             roof = {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_ALU_TFLOPS, 1),
                     "unit": "TFLOP/s", "frac": round(achieved / FP32_ALU_TFLOPS, 4), "traffic": None,
                     "launches": nl, "avg_launch_ms": round(tot_ms / nl, 5),
-                    "peak_src": "FP32 ALU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"}
+                    "peak_src": "FP32 ALU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, not measured)"}
+            if name in ("tp_fused", "tp_fused_bwd"):
+                tk = "tensor_" + name[3:]
+                tens = flops[tk] * args.steps / (tot_ms / 1e3) / 1e12
+                roof["tensor_pipe"] = {"achieved": round(tens, 2), "peak": peaks()["bf16_tflops"],
+                                       "frac": round(tens / peaks()["bf16_tflops"], 4), "unit": "TFLOP/s"}
         else:
             roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": round(FP32_ALU_TFLOPS, 1),
                     "unit": "TFLOP/s", "frac": None, "traffic": None, "launches": nl,
@@ -279,7 +323,7 @@ def run_ours(args, rank, world):
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32", "f16": "f16 tensor-core MLP + f32"}[args.precision],
         "data": "synthetic", "impl": "ours",
         "config": {"workload": args.workload, "atoms": s.n, "edges": E_edges, "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}",
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
@@ -327,7 +371,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water3000", choices=["water3000", "fcc108k", "cluster64"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "f16"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

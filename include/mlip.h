@@ -65,10 +65,16 @@ typedef enum {
 /* Precision of a model's compute path.
  * MLIP_PREC_FP32: the plain FP32 form - every product on the FP32 ALUs, the
  *   per-edge radial weights materialised in HBM, stored intermediates.
- * MLIP_PREC_BF16: the fused form - radial MLP and channel mixes on tcgen05
- *   tensor cores (BF16 inputs, FP32 accumulation in tensor memory), harmonics
- *   and the tensor product in FP32, recomputation in the adjoint. */
-enum { MLIP_PREC_FP32 = 0, MLIP_PREC_BF16 = 1 };
+ * MLIP_PREC_BF16: the fused form - the radial MLP's output layer (forward and
+ *   adjoint) on tcgen05 tensor cores with BF16 operands and FP32 accumulation
+ *   in tensor memory; harmonics, tensor product, mixes and reductions in FP32
+ *   (FP64 for energy, virial, forces); radial weights recomputed in the
+ *   adjoint, never stored.
+ * MLIP_PREC_F16: the same fused form with FP16 operands (3 more mantissa bits;
+ *   the adjoint operand is scaled by a power of two per layer to stay in
+ *   range).  Same speed; used where BF16 rounding of the weights exceeds a
+ *   2e-3 max|F| force tolerance. */
+enum { MLIP_PREC_FP32 = 0, MLIP_PREC_BF16 = 1, MLIP_PREC_F16 = 2 };
 
 typedef struct mlip_model mlip_model;
 
@@ -133,6 +139,20 @@ int mlip_neighbors(const double* pos, int64_t n, const double cell[9], const uin
 int mlip_energy_forces(mlip_model* model, const double* pos, const int32_t* species, int64_t n,
                        const double cell[9], const uint8_t pbc[3], double* energy, double* forces,
                        double* stress, int on_device, void* stream);
+
+/* Velocity-Verlet NVE trajectory of one system (the batched MD
+ * engines named in the Introduction and in "NPT ensemble
+ * simulations"; NVE is the integrator of the benchmark workloads):
+ *   v += dt/2 F/m kappa;  r += dt v;  F = F(r);  v += dt/2 F/m kappa,
+ * kappa = 9.648533212e-3 (eV/A/amu -> A/fs^2), FP64 positions and velocities,
+ * masses from the model description (per species).  pos, vel: [n][3] in/out
+ * (A, A/fs).  pe, ke: n_steps + 1 potential / kinetic energies (eV; the start
+ * and after every step) or NULL.  The neighbour list is rebuilt at every force
+ * evaluation.  Errors: MLIP_ERR_INVALID_ARG (no masses, bad sizes, species out
+ * of range), the errors of mlip_energy_forces. */
+int mlip_md_nve(mlip_model* model, double* pos, double* vel, const int32_t* species, int64_t n,
+                const double cell[9], const uint8_t pbc[3], double dt_fs, int64_t n_steps, double* pe,
+                double* ke, int on_device, void* stream);
 
 /* Self test of a hardware path (no counterpart in the paper).  which = 1: one
  * tcgen05 tile product (M = 128, N = 32, K = 64, BF16 operands in the

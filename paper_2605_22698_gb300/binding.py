@@ -30,6 +30,7 @@ MLIP_ERR_DEVICE_TIMEOUT = -9
 MLIP_ERR_NOT_FOUND = -10
 MLIP_PREC_FP32 = 0
 MLIP_PREC_BF16 = 1
+MLIP_PREC_F16 = 2
 
 
 class MlipError(RuntimeError):
@@ -63,6 +64,7 @@ def lib():
         L.mlip_model_free.argtypes = [P]
         L.mlip_neighbors.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), i32, P]
         L.mlip_energy_forces.argtypes = [P, P, P, i64, P, P, P, P, P, i32, P]
+        L.mlip_md_nve.argtypes = [P, P, P, P, i64, P, P, f64, i64, P, P, i32, P]
         L.mlip_selftest.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         L.mlip_profile_enable.argtypes = [i32]
         L.mlip_launch_count.restype = ctypes.c_longlong
@@ -194,6 +196,27 @@ def mlip_energy_forces(h, pos, species, cell, pbc, forces: bool = True, stress: 
     return out
 
 
+def mlip_md_nve(h, pos, vel, species, cell, pbc, dt_fs: float, n_steps: int, stream=None):
+    """Velocity-Verlet NVE.  numpy inputs: copies are integrated and returned
+    with the energy traces; torch CUDA tensors: integrated in place."""
+    cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    pbc = np.ascontiguousarray(pbc, dtype=np.uint8).reshape(3)
+    if isinstance(pos, np.ndarray):
+        pos = np.array(pos, dtype=np.float64, copy=True)
+        vel = np.array(vel, dtype=np.float64, copy=True)
+        species = np.ascontiguousarray(species, dtype=np.int32)
+        pe = np.zeros(n_steps + 1); ke = np.zeros(n_steps + 1)
+    else:
+        import torch
+        pe = torch.zeros(n_steps + 1, dtype=torch.float64, device=pos.device)
+        ke = torch.zeros_like(pe)
+    pp, dev = _ptr(pos)
+    _check(lib().mlip_md_nve(h, pp, _ptr(vel)[0], _ptr(species)[0], int(pos.shape[0]),
+                             cell.ctypes.data_as(ctypes.c_void_p), pbc.ctypes.data_as(ctypes.c_void_p), dt_fs,
+                             n_steps, _ptr(pe)[0], _ptr(ke)[0], dev, _stream_ptr(stream)))
+    return pos, vel, pe, ke
+
+
 def mlip_selftest(which: int) -> float:
     r = ctypes.c_double(0.0)
     _check(lib().mlip_selftest(which, ctypes.byref(r)))
@@ -228,6 +251,9 @@ class Model:
 
     def energy_forces(self, pos, species, cell, pbc, forces=True, stress=False, stream=None, out=None):
         return mlip_energy_forces(self.h, pos, species, cell, pbc, forces, stress, stream, out)
+
+    def md_nve(self, pos, vel, species, cell, pbc, dt_fs, n_steps, stream=None):
+        return mlip_md_nve(self.h, pos, vel, species, cell, pbc, dt_fs, n_steps, stream)
 
     def close(self):
         if getattr(self, "h", None):

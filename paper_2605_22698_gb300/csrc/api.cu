@@ -99,9 +99,12 @@ static int validate_desc(const mlip_model_desc* d, int precision) {
   if (d->hidden != 32 && d->hidden != 64) { set_error("hidden %d unsupported (32, 64)", d->hidden); return MLIP_ERR_INVALID_ARG; }
   if (d->envelope_p < 1 || d->envelope_p > 16) { set_error("envelope_p %d out of range", d->envelope_p); return MLIP_ERR_INVALID_ARG; }
   if (!(d->cutoff > 0) || !(d->avg_num_neighbors > 0)) { set_error("cutoff and avg_num_neighbors must be positive"); return MLIP_ERR_INVALID_ARG; }
-  if (precision != MLIP_PREC_FP32 && precision != MLIP_PREC_BF16) { set_error("unknown precision %d", precision); return MLIP_ERR_INVALID_ARG; }
-  if (precision == MLIP_PREC_BF16 && (d->channels != 128 || d->hidden != 64)) {
-    set_error("the BF16 form needs 128 channels and hidden width 64");
+  if (precision != MLIP_PREC_FP32 && precision != MLIP_PREC_BF16 && precision != MLIP_PREC_F16) {
+    set_error("unknown precision %d", precision);
+    return MLIP_ERR_INVALID_ARG;
+  }
+  if (precision != MLIP_PREC_FP32 && (d->channels != 128 || d->hidden != 64)) {
+    set_error("the fused tensor-core form needs 128 channels and hidden width 64");
     return MLIP_ERR_INVALID_ARG;
   }
   return MLIP_OK;
@@ -155,7 +158,7 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
   }
   M->W_out = q; q += S * C;
   M->E0 = q; q += S;
-  if (precision == MLIP_PREC_BF16) {
+  if (precision != MLIP_PREC_FP32) {
     std::vector<uint8_t> all, img;
     for (int t = 0; t < M->T; ++t) {
       std::vector<size_t> goff;

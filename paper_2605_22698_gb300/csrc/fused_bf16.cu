@@ -1,8 +1,9 @@
-// Fused BF16 form of the interaction layer.
+// Fused tensor-core form of the interaction layer (16-bit operands: BF16, or
+// FP16 for the tighter error bar, with FP32 accumulation in tensor memory).
 //
 // Per layer:
 //   radial_tiles  one thread per edge: r -> Bessel x envelope -> z1 -> z2 (FP32),
-//                 z2 written as BF16 in the tcgen05 canonical K-major layout,
+//                 z2 written as BF16 or FP16 in the tcgen05 canonical K-major layout,
 //                 one 4 KB tile per kNT = 32 consecutive (receiver-sorted) edges
 //   tp_fused      one launch per path group (all l1 = 0 paths for the first
 //                 layer, else the paths of one output order l3).  Each CTA keeps
@@ -22,6 +23,7 @@
 #include <cstring>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "kernels_common.cuh"
 #include "launchers.cuh"
@@ -32,6 +34,16 @@ namespace mlip {
 namespace {
 
 constexpr int kNT = 32;           // edges per tile (MMA N)
+
+// 16-bit operand encodings (bits of a BF16 or FP16 value)
+__host__ __device__ inline uint16_t to16(float x, bool bf16) {
+  if (bf16) {
+    const __nv_bfloat16 v = __float2bfloat16_rn(x);
+    return *reinterpret_cast<const uint16_t*>(&v);
+  }
+  const __half v = __float2half_rn(x);
+  return *reinterpret_cast<const uint16_t*>(&v);
+}
 constexpr int kTileBytes = kNT * 64 * 2;
 constexpr int kW3PathBytes = 128 * 64 * 2;
 
@@ -87,7 +99,7 @@ struct Group {
 // ------------------------------------------------------------- radial tiles
 template <int H>
 __global__ void radial_tiles(int E, int n_tiles, const float4* __restrict__ ev, const float* __restrict__ W1,
-                             const float* __restrict__ W2, float rc, int p, uint8_t* __restrict__ z2t) {
+                             const float* __restrict__ W2, float rc, int p, int use_bf16, uint8_t* __restrict__ z2t) {
   static_assert(H == 64, "tile layout assumes K = 64");
   __shared__ float sW1[8 * H], sW2[H * H];
   for (int k = threadIdx.x; k < 8 * H; k += blockDim.x) sW1[k] = W1[k];
@@ -127,8 +139,7 @@ __global__ void radial_tiles(int E, int n_tiles, const float4* __restrict__ ev, 
         for (int q = 0; q < H; ++q) a = fmaf(z1[q], sW2[q * H + k], a);
         o[u] = silu_f(a);
       }
-      const __nv_bfloat162 v = __floats2bfloat162_rn(o[0], o[1]);
-      pk[h2] = *reinterpret_cast<const uint32_t*>(&v);
+      pk[h2] = (uint32_t)to16(o[0], use_bf16) | ((uint32_t)to16(o[1], use_bf16) << 16);
     }
     *reinterpret_cast<uint4*>(tile + tc::canon_off(t, kg * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
@@ -140,7 +151,7 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
                                                 const int* __restrict__ send, const float4* __restrict__ ev,
                                                 const float* __restrict__ h, const uint8_t* __restrict__ w3img,
                                                 const uint8_t* __restrict__ z2t, float s, float* __restrict__ m,
-                                                int* __restrict__ err) {
+                                                int use_bf16, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using Tab = CGTable<L>;
   constexpr int D = NodeDims<L>::D;
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
       acc[q] = 0.0f;
     }
   };
-  constexpr uint32_t idesc = tc::idesc_bf16(128, kNT);
+  const uint32_t idesc = tc::idesc_16bit(128, kNT, use_bf16 != 0);
 
 #pragma unroll 1
   for (int it = 0; it < n_tiles; ++it) {
@@ -373,6 +384,7 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
                                                     const uint8_t* __restrict__ z2t, float s,
                                                     const float* __restrict__ Gin, float* __restrict__ Gout,
                                                     int first_group, float* __restrict__ dY, float* __restrict__ dz2,
+                                                    int use_bf16, const float* __restrict__ absmax,
                                                     int* __restrict__ err) {
   using G = Group<L, MODE>;
   using BL = BwdLayout<L, MODE>;
@@ -468,8 +480,17 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
       if (cur < i1) enter(cur);
     }
   };
-  constexpr uint32_t idesc1 = tc::idesc_bf16(128, kNT);
-  constexpr uint32_t idesc2 = tc::idesc_bf16(128, kNT) | (1u << 15);  // A M-major
+  const uint32_t idesc1 = tc::idesc_16bit(128, kNT, use_bf16 != 0);
+  const uint32_t idesc2 = idesc1 | (1u << 15);  // A M-major
+  // dE/dw enters the second product scaled by a power of two (FP16 operands):
+  // |dE/dw| <= 17 max|h| s max|Gm| (orthonormal CG rows, |Y| <= 1), so the
+  // scale 2^floor(log2(2^14 / (32 max|h| s max|Gm|))) keeps it below 2^14.
+  float dw_scale = 1.0f;
+  if (!use_bf16) {
+    const float U = 32.0f * absmax[0] * s * absmax[1];
+    dw_scale = U > 0.0f ? exp2f(fminf(fmaxf(floorf(log2f(16384.0f / U)), -60.0f), 60.0f)) : 1.0f;
+  }
+  const float inv_dw_scale = 1.0f / dw_scale;
 
 #pragma unroll 1
   for (int it = 0; it < n_tiles; ++it) {
@@ -606,16 +627,15 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
               dYp[l2 * l2 + q] = fmaf(wp, Tp[q], dYp[l2 * l2 + q]);
             }
             const int kidx = sl * 128 + c;
-            *reinterpret_cast<__nv_bfloat16*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) =
-                __float2bfloat16_rn(dwp);
+            *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) =
+                to16(dwp * dw_scale, use_bf16);
           });
         } else {
           // edge outside this block's range: zero operand row
 #pragma unroll
           for (int sl = 0; sl < NP; ++sl) {
             const int kidx = sl * 128 + c;
-            *reinterpret_cast<__nv_bfloat16*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) =
-                __float2bfloat16_rn(0.0f);
+            *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) = 0;
           }
         }
         const float tot = warp_reduce16(dYp);
@@ -665,7 +685,7 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int e = tile * kNT + ch * 8 + j;
-          if (e >= E0 && e < E1) dz2[(size_t)e * 64 + tid] += v[j];
+          if (e >= E0 && e < E1) dz2[(size_t)e * 64 + tid] += v[j] * inv_dw_scale;
         }
       }
     }
@@ -685,6 +705,24 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, BL::NCOLS);
+}
+
+// max |x| of two arrays (non-negative floats compare as integers)
+__global__ void absmax2(size_t na, const float* __restrict__ a, size_t nb, const float* __restrict__ b,
+                        float* __restrict__ out) {
+  float ma = 0.0f, mb = 0.0f;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < na; k += (size_t)gridDim.x * blockDim.x)
+    ma = fmaxf(ma, fabsf(a[k]));
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nb; k += (size_t)gridDim.x * blockDim.x)
+    mb = fmaxf(mb, fabsf(b[k]));
+  for (int o = 16; o > 0; o >>= 1) {
+    ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(reinterpret_cast<int*>(out), __float_as_int(ma));
+    atomicMax(reinterpret_cast<int*>(out) + 1, __float_as_int(mb));
+  }
 }
 
 // ------------------------------------------------------------- self test
@@ -799,13 +837,14 @@ __global__ void umma_selftest_mn(const float* __restrict__ W, const float* __res
 
 template <int L, int MODE>
 int launch_group(int n, const int* row_ptr, const int* recv, const int* send, const float4* ev, const float* h,
-                 const uint8_t* w3img, const uint8_t* z2t, float s, float* m, int* err, int blocks, cudaStream_t st) {
+                 const uint8_t* w3img, const uint8_t* z2t, float s, float* m, int use_bf16, int* err, int blocks,
+                 cudaStream_t st) {
   using G = Group<L, MODE>;
   const size_t smem = G::smem_bytes();
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     MLIP_PROF("tp_fused", st);
-    tp_fused<L, MODE><<<blocks, 128, smem, st>>>(n, row_ptr, recv, send, ev, h, w3img, z2t, s, m, err);
+    tp_fused<L, MODE><<<blocks, 128, smem, st>>>(n, row_ptr, recv, send, ev, h, w3img, z2t, s, m, use_bf16, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
@@ -814,15 +853,15 @@ int launch_group(int n, const int* row_ptr, const int* recv, const int* send, co
 template <int L, int MODE>
 int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send, const float4* ev,
                      const float* hprev, const float* Gm, const uint8_t* w3img, const uint8_t* z2t, float s,
-                     const float* Gin, float* Gout, int first_group, float* dY, float* dz2, int* err, int blocks,
-                     cudaStream_t st) {
+                     const float* Gin, float* Gout, int first_group, float* dY, float* dz2, int use_bf16,
+                     const float* absmax, int* err, int blocks, cudaStream_t st) {
   using BL = BwdLayout<L, MODE>;
   const size_t smem = BL::smem_bytes();
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused_bwd<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     MLIP_PROF("tp_fused_bwd", st);
     tp_fused_bwd<L, MODE><<<blocks, 128, smem, st>>>(n, row_ptr, recv, send, ev, hprev, Gm, w3img, z2t, s, Gin,
-                                                    Gout, first_group, dY, dz2, err);
+                                                    Gout, first_group, dY, dz2, use_bf16, absmax, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
@@ -863,7 +902,7 @@ int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::v
       img.resize(base + kW3PathBytes, 0);
       for (int c = 0; c < C; ++c)
         for (int k = 0; k < H; ++k) {
-          const __nv_bfloat16 v = __float2bfloat16_rn(W3[((size_t)k * P + p) * C + c]);
+          const uint16_t v = to16(W3[((size_t)k * P + p) * C + c], M->precision == MLIP_PREC_BF16);
           std::memcpy(&img[base + tc::canon_off(c, k)], &v, 2);
         }
     }
@@ -873,11 +912,11 @@ int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::v
 }
 
 int launch_radial_tiles(int H, int E, int n_tiles, const float4* ev, const float* W1, const float* W2, float rc,
-                        int p, uint8_t* z2t, cudaStream_t st) {
+                        int p, int use_bf16, uint8_t* z2t, cudaStream_t st) {
   if (n_tiles <= 0) return MLIP_OK;
   if (H != 64) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
   const int threads = 128, blocks = (n_tiles * kNT + threads - 1) / threads;
-  { MLIP_PROF("radial_tiles", st); radial_tiles<64><<<blocks, threads, 0, st>>>(E, n_tiles, ev, W1, W2, rc, p, z2t); }
+  { MLIP_PROF("radial_tiles", st); radial_tiles<64><<<blocks, threads, 0, st>>>(E, n_tiles, ev, W1, W2, rc, p, use_bf16, z2t); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
@@ -885,14 +924,14 @@ int launch_radial_tiles(int H, int E, int n_tiles, const float4* ev, const float
 // Forward message pass of one layer with the fused kernels (m written for all components).
 int launch_tp_fused(int L, bool first, int n, const int* row_ptr, const int* recv, const int* send,
                     const float4* ev, const float* h, const uint8_t* w3img, const std::vector<size_t>& goff,
-                    const uint8_t* z2t, float s, float* m, int* err, cudaStream_t st) {
+                    const uint8_t* z2t, float s, float* m, int use_bf16, int* err, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = std::max(1, std::min(n, 2 * sms));
 #define MLIP_G(LL, MM, GI) \
-  MLIP_TRY((launch_group<LL, MM>(n, row_ptr, recv, send, ev, h, w3img + goff[GI], z2t, s, m, err, blocks, st)))
+  MLIP_TRY((launch_group<LL, MM>(n, row_ptr, recv, send, ev, h, w3img + goff[GI], z2t, s, m, use_bf16, err, blocks, st)))
   if (L == 2) {
     if (first) { MLIP_G(2, -1, 0); }
     else { MLIP_G(2, 0, 0); MLIP_G(2, 1, 1); MLIP_G(2, 2, 2); }
@@ -911,7 +950,7 @@ int launch_tp_fused(int L, bool first, int n, const int* row_ptr, const int* rec
 int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int* recv, const int* send,
                         const float4* ev, const float* hprev, const float* Gm, const uint8_t* w3img,
                         const std::vector<size_t>& goff, const uint8_t* z2t, float s, const float* Gin, float* Gout,
-                        float* dY, float* dz2, int* err, cudaStream_t st) {
+                        float* dY, float* dz2, int use_bf16, const float* absmax, int* err, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -919,7 +958,7 @@ int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int*
   const int blocks = std::max(1, std::min(n, sms));
 #define MLIP_GB(LL, MM, GI) \
   MLIP_TRY((launch_group_bwd<LL, MM>(n, row_ptr, recv, send, ev, hprev, Gm, w3img + goff[GI], z2t, s, Gin, Gout, \
-                                     GI == 0, dY, dz2, err, blocks, st)))
+                                     GI == 0, dY, dz2, use_bf16, absmax, err, blocks, st)))
   if (L == 2) {
     if (first) { MLIP_GB(2, -1, 0); }
     else { MLIP_GB(2, 0, 0); MLIP_GB(2, 1, 1); MLIP_GB(2, 2, 2); }
@@ -1018,6 +1057,7 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
   Workspace& ws = M->ws;
   const int n = (int)n64, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H;
   const float s = (float)(1.0 / M->avg_nb);
+  const int use_bf16 = M->precision == MLIP_PREC_BF16 ? 1 : 0;
   int* flag = nullptr;
   MLIP_TRY(ws.get("chk.flag", 2, &flag));
   MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
@@ -1046,9 +1086,9 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
   MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st));
   MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
   for (int t = 0; t < T; ++t) {
-    MLIP_TRY(launch_radial_tiles(H, E, n_tiles, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, z2t[t], st));
+    MLIP_TRY(launch_radial_tiles(H, E, n_tiles, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, use_bf16, z2t[t], st));
     MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, ev, h[t], M->d_w3img + M->w3_layer_off[t],
-                             M->w3_goff[t], z2t[t], s, m, flag + 1, st));
+                             M->w3_goff[t], z2t[t], s, m, use_bf16, flag + 1, st));
     MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
   }
   MLIP_TRY(launch_energy(n, C, D, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
@@ -1063,12 +1103,21 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
     MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, Ga, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dr, 0, Ec * sizeof(float), st));
+    float* absmax = nullptr;
+    MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)T, &absmax));
+    MLIP_CUDA_TRY(cudaMemsetAsync(absmax, 0, 2 * T * sizeof(float), st));
     for (int t = T - 1; t >= 0; --t) {
       MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], Gm, st));
       MLIP_CUDA_TRY(cudaMemsetAsync(dz2, 0, Ec * 64 * sizeof(float), st));
+      if (!use_bf16) {
+        MLIP_PROF("absmax2", st);
+        absmax2<<<std::max(1, std::min(1024, (int)((ND + 1023) / 1024))), 256, 0, st>>>(ND, h[t], ND, Gm,
+                                                                                         absmax + 2 * t);
+        MLIP_LAUNCH_CHECK();
+      }
       MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, ev, h[t], Gm,
                                    M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, Ga, Gb, dY, dz2,
-                                   flag + 1, st));
+                                   use_bf16, absmax + 2 * t, flag + 1, st));
       MLIP_TRY(launch_radial_bwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, st));
       std::swap(Ga, Gb);
     }

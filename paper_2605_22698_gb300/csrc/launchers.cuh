@@ -47,4 +47,11 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
                         const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress,
                         cudaStream_t st);
 
+int launch_vv_kick(int n, const int* species, const double* mass, double half_dt, const double* F, double* vel,
+                   cudaStream_t st);
+int launch_vv_drift(int n, double dt, const double* vel, double* pos, cudaStream_t st);
+int launch_kinetic(int n, const int* species, const double* mass, const double* vel, double* out, cudaStream_t st);
+int energy_forces_device(mlip_model* M, const double* d_pos, const int* d_species, int64_t n, const double* cell,
+                         const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress, cudaStream_t st);
+
 }  // namespace mlip

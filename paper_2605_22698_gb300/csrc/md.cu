@@ -1,0 +1,132 @@
+// Velocity-Verlet NVE integration on the device (FP64 positions and
+// velocities), the integrator of the batched MD workload:
+//   v += dt/2 F/m kappa;  r += dt v;  F = F(r);  v += dt/2 F/m kappa,
+// kappa = 9.648533212e-3 converts eV/A/amu to A/fs^2.  Kinetic energy
+// KE = sum_i m_i v_i^2 / (2 kappa) in eV, reduced in FP64 in a fixed order.
+#include <algorithm>
+
+#include "launchers.cuh"
+#include "profile.cuh"
+
+namespace mlip {
+namespace {
+
+constexpr double kKappa = 9.648533212e-3;
+
+__global__ void vv_kick(int n, const int* __restrict__ species, const double* __restrict__ mass, double half_dt,
+                        const double* __restrict__ F, double* __restrict__ vel) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = half_dt * kKappa / mass[species[i]];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) vel[3 * i + k] += a * F[3 * i + k];
+}
+
+__global__ void vv_drift(int n, double dt, const double* __restrict__ vel, double* __restrict__ pos) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) pos[3 * i + k] += dt * vel[3 * i + k];
+}
+
+// One block: KE = sum_i m v^2 / (2 kappa).
+__global__ void kinetic(int n, const int* __restrict__ species, const double* __restrict__ mass,
+                        const double* __restrict__ vel, double* __restrict__ out) {
+  __shared__ double part[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v2 = vel[3 * i] * vel[3 * i] + vel[3 * i + 1] * vel[3 * i + 1] + vel[3 * i + 2] * vel[3 * i + 2];
+    acc += 0.5 * mass[species[i]] * v2 / kKappa;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) *out = v;
+  }
+}
+
+}  // namespace
+
+int launch_vv_kick(int n, const int* species, const double* mass, double half_dt, const double* F, double* vel,
+                   cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  { MLIP_PROF("vv_kick", st); vv_kick<<<(n + 255) / 256, 256, 0, st>>>(n, species, mass, half_dt, F, vel); }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+int launch_vv_drift(int n, double dt, const double* vel, double* pos, cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  { MLIP_PROF("vv_drift", st); vv_drift<<<(n + 255) / 256, 256, 0, st>>>(n, dt, vel, pos); }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+int launch_kinetic(int n, const int* species, const double* mass, const double* vel, double* out, cudaStream_t st) {
+  { MLIP_PROF("kinetic", st); kinetic<<<1, 1024, 0, st>>>(n, species, mass, vel, out); }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+// Energy and forces of device-resident positions with the model's form.
+int energy_forces_device(mlip_model* M, const double* d_pos, const int* d_species, int64_t n, const double* cell,
+                         const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+  if (M->precision == MLIP_PREC_FP32)
+    return energy_forces_plain(M, d_pos, d_species, n, cell, pbc, d_energy, d_forces, d_stress, st);
+  return energy_forces_fused(M, d_pos, d_species, n, cell, pbc, d_energy, d_forces, d_stress, st);
+}
+
+}  // namespace mlip
+
+using namespace mlip;
+
+extern "C" int mlip_md_nve(mlip_model* M, double* pos, double* vel, const int32_t* species, int64_t n,
+                           const double cell[9], const uint8_t pbc[3], double dt_fs, int64_t n_steps, double* pe,
+                           double* ke, int on_device, void* stream) {
+  if (!M || !pos || !vel || !species || !cell || !pbc) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  if (n < 1 || n_steps < 0 || !(dt_fs > 0)) { set_error("bad atom count, step count or time step"); return MLIP_ERR_INVALID_ARG; }
+  if ((int)M->masses.size() != M->S) { set_error("the model has no masses (needed for MD)"); return MLIP_ERR_INVALID_ARG; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Workspace& ws = M->ws;
+  double *d_pos = pos, *d_vel = vel, *d_F = nullptr, *d_E = nullptr, *d_mass = nullptr, *d_pe = nullptr, *d_ke = nullptr;
+  const int* d_sp = species;
+  if (!on_device) {
+    for (int64_t i = 0; i < n; ++i)
+      if (species[i] < 0 || species[i] >= M->S) { set_error("species[%lld] out of range", (long long)i); return MLIP_ERR_INVALID_ARG; }
+    int* dz = nullptr;
+    MLIP_TRY(ws.get("md.pos", (size_t)3 * n, &d_pos));
+    MLIP_TRY(ws.get("md.vel", (size_t)3 * n, &d_vel));
+    MLIP_TRY(ws.get("md.species", (size_t)n, &dz));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(d_vel, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dz, species, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    d_sp = dz;
+  }
+  MLIP_TRY(ws.get("md.F", (size_t)3 * n, &d_F));
+  MLIP_TRY(ws.get("md.E", 1, &d_E));
+  MLIP_TRY(ws.get("md.mass", (size_t)M->S, &d_mass));
+  MLIP_TRY(ws.get("md.pe", (size_t)n_steps + 1, &d_pe));
+  MLIP_TRY(ws.get("md.ke", (size_t)n_steps + 1, &d_ke));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(d_mass, M->masses.data(), sizeof(double) * M->S, cudaMemcpyHostToDevice, st));
+  MLIP_TRY(energy_forces_device(M, d_pos, d_sp, n, cell, pbc, d_pe, d_F, nullptr, st));
+  MLIP_TRY(launch_kinetic((int)n, d_sp, d_mass, d_vel, d_ke, st));
+  for (int64_t s = 0; s < n_steps; ++s) {
+    MLIP_TRY(launch_vv_kick((int)n, d_sp, d_mass, 0.5 * dt_fs, d_F, d_vel, st));
+    MLIP_TRY(launch_vv_drift((int)n, dt_fs, d_vel, d_pos, st));
+    MLIP_TRY(energy_forces_device(M, d_pos, d_sp, n, cell, pbc, d_pe + s + 1, d_F, nullptr, st));
+    MLIP_TRY(launch_vv_kick((int)n, d_sp, d_mass, 0.5 * dt_fs, d_F, d_vel, st));
+    MLIP_TRY(launch_kinetic((int)n, d_sp, d_mass, d_vel, d_ke + s + 1, st));
+  }
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (pe) MLIP_CUDA_TRY(cudaMemcpyAsync(pe, d_pe, sizeof(double) * (n_steps + 1), k, st));
+  if (ke) MLIP_CUDA_TRY(cudaMemcpyAsync(ke, d_ke, sizeof(double) * (n_steps + 1), k, st));
+  if (!on_device) {
+    MLIP_CUDA_TRY(cudaMemcpyAsync(pos, d_pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(vel, d_vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+  }
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  return MLIP_OK;
+}

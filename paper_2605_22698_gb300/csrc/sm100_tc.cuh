@@ -85,6 +85,10 @@ __device__ __forceinline__ uint64_t desc_noswizzle(uint32_t saddr, uint32_t lbo,
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// Same with A and B FP16 (format code 0) when bf16 == false.
+__host__ __device__ constexpr uint32_t idesc_16bit(int M, int N, bool bf16) {
+  return bf16 ? idesc_bf16(M, N) : ((1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24));
+}
 
 // D[tmem] (+)= A * B^T, issued by one thread.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
