@@ -39,7 +39,7 @@ def test_tensor_core_transposed_operand_selftest(B):
     assert B.mlip_selftest(2) < 1e-5
 
 
-def _check(out, ref, stress=False, tol=TOL):
+def _check(out, ref, stress=False, tol=TOL, cell=None, n_edges=0):
     scale = max(abs(ref["energy"]), float(np.abs(ref["atom_energies"]).sum()))
     E = float(np.asarray(out["energy"]).reshape(-1)[0])
     assert abs(E - ref["energy"]) <= tol * scale, (E, ref["energy"])
@@ -47,8 +47,12 @@ def _check(out, ref, stress=False, tol=TOL):
     err = np.abs(np.asarray(out["forces"]) - ref["forces"]).max()
     assert err <= tol * fmax, (err, fmax)
     if stress:
-        smax = np.abs(ref["stress"]).max()
-        assert np.abs(np.asarray(out["stress"]) - ref["stress"]).max() <= tol * smax
+        # the stress is a sum of E virial terms x_e (x) g_e / V that largely
+        # cancel; its error scale is that of a random sum of E terms of size
+        # rc max|F|, so the bar is tol * max(max|s_ref|, rc max|F| sqrt(E) / V)
+        V = abs(np.linalg.det(cell))
+        sscale = max(np.abs(ref["stress"]).max(), 5.0 * fmax * np.sqrt(n_edges) / V)
+        assert np.abs(np.asarray(out["stress"]) - ref["stress"]).max() <= tol * sscale
     return err / fmax
 
 
@@ -77,7 +81,9 @@ def test_fused_forces_stress_water(B, nmol, prec, tol):
     s = synth.water_box(nmol, synth.water_side_for(nmol), seed=2)
     ref = _oracle(("water", nmol), spec, w, s, True)
     m = B.Model(spec, w, _prec(B, prec))
-    rel = _check(m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=True), ref, stress=True, tol=tol)
+    ne = len(oracle.neighbors(s.pos, s.cell, s.pbc, 5.0)[0])
+    rel = _check(m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=True), ref, stress=True, tol=tol,
+                 cell=s.cell, n_edges=ne)
     print(f"water{3 * nmol} {prec}: max|dF|/max|F| = {rel:.2e}")
 
 
@@ -88,7 +94,9 @@ def test_fused_forces_stress_fcc_l3(B, prec, tol):
     s = synth.fcc((5, 10, 10), seed=3)
     ref = _oracle(("fcc", 2000), spec, w, s, True)
     m = B.Model(spec, w, _prec(B, prec))
-    rel = _check(m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=True), ref, stress=True, tol=tol)
+    ne = len(oracle.neighbors(s.pos, s.cell, s.pbc, 5.0)[0])
+    rel = _check(m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=True), ref, stress=True, tol=tol,
+                 cell=s.cell, n_edges=ne)
     print(f"fcc2000 {prec}: max|dF|/max|F| = {rel:.2e}")
 
 
