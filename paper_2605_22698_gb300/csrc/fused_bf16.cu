@@ -145,32 +145,178 @@ __global__ void radial_tiles(int E, int n_tiles, const float4* __restrict__ ev, 
   }
 }
 
+// ------------------------------------------------------------ warp sets
+// A CTA runs kWS warp sets of 4 warps (128 threads, one per channel and TMEM
+// lane).  All warp sets walk the same edges; the group's paths are split
+// between them (greedy by flop cost), and their per-receiver partial sums are
+// combined through shared memory at receiver boundaries.
+constexpr int kWS = 2;
+constexpr int kThreads = 128 * kWS;
+
+__device__ __forceinline__ void ws_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
+
+template <int L, int MODE, bool BWD>
+struct Split {
+  using G = Group<L, MODE>;
+  using Tab = CGTable<L>;
+  static constexpr int NP = G::NP;
+  static constexpr int cost(int p) {
+    const int nz = Tab::off[p + 1] - Tab::off[p];
+    const int l1 = Tab::l1[p], l2 = Tab::l2[p], l3 = Tab::l3[p];
+    if (!BWD) return (2 * l1 + 1) + 2 * nz;
+    return (MODE < 0 ? 0 : 2 * (2 * l3 + 1) + 2 * nz) + 3 * nz + 4 * (2 * l2 + 1);
+  }
+  static constexpr std::array<int, NP> make() {
+    std::array<int, NP> ws{};
+    std::array<bool, NP> done{};
+    int load[kWS] = {};
+    for (int it = 0; it < NP; ++it) {
+      int best = -1;
+      for (int s = 0; s < NP; ++s)
+        if (!done[s] && (best < 0 || cost(G::paths[s]) > cost(G::paths[best]))) best = s;
+      int w = 0;
+      for (int k = 1; k < kWS; ++k)
+        if (load[k] < load[w]) w = k;
+      ws[best] = w;
+      load[w] += cost(G::paths[best]);
+      done[best] = true;
+    }
+    return ws;
+  }
+  static constexpr std::array<int, NP> ws = make();
+  // sender components read by warp set W (max l1 of its paths)
+  static constexpr int dh(int W) {
+    int m = -1;
+    for (int s = 0; s < NP; ++s)
+      if (ws[s] == W && Tab::l1[G::paths[s]] > m) m = Tab::l1[G::paths[s]];
+    return m < 0 ? 1 : (m + 1) * (m + 1);
+  }
+};
+
 // ---------------------------------------------------------------- tp_fused
 template <int L, int MODE>
-__global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ row_ptr, const int* __restrict__ recv,
-                                                const int* __restrict__ send, const float4* __restrict__ ev,
-                                                const float* __restrict__ h, const uint8_t* __restrict__ w3img,
-                                                const uint8_t* __restrict__ z2t, float s, float* __restrict__ m,
-                                                int use_bf16, int* __restrict__ err) {
+struct FwdLayout {
   using G = Group<L, MODE>;
+  static constexpr int NP = G::NP;
+  static constexpr size_t off_z2 = (size_t)NP * kW3PathBytes;
+  static constexpr size_t off_cy = off_z2 + 2 * kTileBytes;
+  static constexpr size_t off_idx = off_cy + (size_t)kNT * G::NZP * 4;
+  static constexpr size_t off_comb = off_idx + 2 * kNT * 4;
+  static constexpr size_t off_bar = off_comb + (size_t)2 * G::NOUT * 128 * 4;
+  static constexpr size_t bytes = off_bar + 64;
+};
+
+template <int L, int MODE, int W>
+__device__ __forceinline__ void fwd_edge(const float (&wv)[Group<L, MODE>::NP][8], int j, const float* hj,
+                                         const float* cy, float* acc) {
+  using G = Group<L, MODE>;
+  using S = Split<L, MODE, false>;
+  using Tab = CGTable<L>;
+  static_for<0, G::NP>([&](auto sc) {
+    constexpr int sl = decltype(sc)::value;
+    if constexpr (S::ws[sl] == W) {
+      constexpr int p = G::paths[sl];
+      constexpr int l1 = Tab::l1[p];
+      constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
+      float wh[2 * l1 + 1];
+#pragma unroll
+      for (int q = 0; q < 2 * l1 + 1; ++q) wh[q] = wv[sl][j] * hj[l1 * l1 + q];
+      static_for<kb, ke>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        constexpr int o3 = Tab::e3[k] - G::comp0, j1 = Tab::e1[k] - l1 * l1;
+        acc[o3] = fmaf(cy[gb + k - kb], wh[j1], acc[o3]);
+      });
+    }
+  });
+}
+
+template <int L, int MODE, int W>
+__device__ __forceinline__ void fwd_tile_ws(int tile, const int* s_send, const int* s_recv, const float* cY,
+                                            uint32_t taddr0, const float* __restrict__ h, int& cur, float* acc,
+                                            float* comb, int& par, float* __restrict__ m, float s) {
+  using G = Group<L, MODE>;
+  using S = Split<L, MODE, false>;
+  constexpr int D = NodeDims<L>::D;
+  constexpr int C = 128;
+  constexpr int DH = S::dh(W);
+  const int c = threadIdx.x & 127;
+  auto flush = [&](int i) {
+    float* cb = comb + par * G::NOUT * 128;
+    if (W != 0) {
+#pragma unroll
+      for (int q = 0; q < G::NOUT; ++q) cb[q * 128 + c] = acc[q];
+    }
+    ws_barrier();
+    if (W == 0) {
+#pragma unroll
+      for (int q = 0; q < G::NOUT; ++q) m[((size_t)i * D + G::comp0 + q) * C + c] = s * (acc[q] + cb[q * 128 + c]);
+    }
+#pragma unroll
+    for (int q = 0; q < G::NOUT; ++q) acc[q] = 0.0f;
+    par ^= 1;
+  };
+#pragma unroll 1
+  for (int ch = 0; ch < kNT / 8; ++ch) {
+    float wv[G::NP][8];
+    static_for<0, G::NP>([&](auto sc) {
+      constexpr int sl = decltype(sc)::value;
+      if constexpr (S::ws[sl] == W) tc::tmem_ld8(taddr0 + sl * kNT + ch * 8, wv[sl]);
+    });
+    tc::tmem_ld_wait();
+    float hn[DH];
+    {
+      const int sj = s_send[ch * 8];
+#pragma unroll
+      for (int d = 0; d < DH; ++d) hn[d] = h[((size_t)sj * D + d) * C + c];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int t = ch * 8 + j;
+      float hj[DH];
+#pragma unroll
+      for (int d = 0; d < DH; ++d) hj[d] = hn[d];
+      if (j < 7) {
+        const int sj = s_send[t + 1];
+#pragma unroll
+        for (int d = 0; d < DH; ++d) hn[d] = h[((size_t)sj * D + d) * C + c];
+      }
+      const int r = s_recv[t];
+      if (r < 0) continue;
+      while (cur < r) { flush(cur); ++cur; }
+      fwd_edge<L, MODE, W>(wv, j, hj, cY + t * G::NZP, acc);
+    }
+  }
+  (void)tile;
+}
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restrict__ row_ptr,
+                                                     const int* __restrict__ recv, const int* __restrict__ send,
+                                                     const float4* __restrict__ ev, const float* __restrict__ h,
+                                                     const uint8_t* __restrict__ w3img,
+                                                     const uint8_t* __restrict__ z2t, float s, float* __restrict__ m,
+                                                     int use_bf16, int* __restrict__ err) {
+  using G = Group<L, MODE>;
+  using FL = FwdLayout<L, MODE>;
   using Tab = CGTable<L>;
   constexpr int D = NodeDims<L>::D;
   constexpr int C = 128;
   constexpr int NP = G::NP;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sW3 = smem;
-  uint8_t* sZ2 = smem + NP * kW3PathBytes;
-  float* cY = reinterpret_cast<float*>(sZ2 + 2 * kTileBytes);
-  int* s_send = reinterpret_cast<int*>(cY + kNT * G::NZP);
+  uint8_t* sZ2 = smem + FL::off_z2;
+  float* cY = reinterpret_cast<float*>(smem + FL::off_cy);
+  int* s_send = reinterpret_cast<int*>(smem + FL::off_idx);
   int* s_recv = s_send + kNT;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_recv + kNT);  // 16-byte aligned offset
+  float* comb = reinterpret_cast<float*>(smem + FL::off_comb);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + FL::off_bar);
   uint64_t* bar_w3 = bars;
   uint64_t* bar_z2 = bars + 1;  // [2]
   uint64_t* bar_mma = bars + 3;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 4);
   __shared__ int abort_s;
 
-  const int tid = threadIdx.x, warp = tid >> 5, c = tid;
+  const int tid = threadIdx.x, warp = tid >> 5, c = tid & 127, wsid = warp >> 2;
   if (warp == 0) {
     tc::tmem_alloc(tmem_holder, G::NCOLS);
     tc::tmem_relinquish();
@@ -187,7 +333,7 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tmem_holder;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t taddr0 = tbase + ((uint32_t)((warp & 3) * 32) << 16);
 
   int i0, i1;
   block_receivers(row_ptr, n, blockIdx.x, gridDim.x, &i0, &i1);
@@ -195,7 +341,6 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
   const int t_begin = E0 / kNT, t_end = (E1 > E0) ? (E1 + kNT - 1) / kNT : t_begin;
   const int n_tiles = t_end - t_begin;
 
-  // producer state (thread 0)
   int z2_issued[2] = {0, 0}, z2_waited[2] = {0, 0};
   bool w3_issued = false;
   if (tid == 0 && n_tiles > 0) {
@@ -212,21 +357,13 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
   float acc[G::NOUT];
 #pragma unroll
   for (int q = 0; q < G::NOUT; ++q) acc[q] = 0.0f;
-  int cur = i0;
-  auto flush = [&](int i) {
-#pragma unroll
-    for (int q = 0; q < G::NOUT; ++q) {
-      m[((size_t)i * D + G::comp0 + q) * C + c] = s * acc[q];
-      acc[q] = 0.0f;
-    }
-  };
+  int cur = i0, par = 0;
   const uint32_t idesc = tc::idesc_16bit(128, kNT, use_bf16 != 0);
 
 #pragma unroll 1
   for (int it = 0; it < n_tiles; ++it) {
     const int tile = t_begin + it;
     const int buf = it & 1;
-    // per-edge setup of this tile
     if (tid < kNT) {
       const int e = tile * kNT + tid;
       const bool valid = e >= E0 && e < E1;
@@ -251,7 +388,6 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
         });
       }
     }
-    // MMA issue (thread 0): prefetch the next z2 tile, wait for this one, one MMA per path
     if (tid == 0) {
       bool ok = true;
       if (it + 1 < n_tiles) {
@@ -267,14 +403,13 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
         tc::fence_after_sync();
         const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sZ2 + buf * kTileBytes);
 #pragma unroll 1
-        for (int sl = 0; sl < NP; ++sl) {
+        for (int sl = 0; sl < NP; ++sl)
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
             const uint64_t bd = tc::desc_noswizzle(b0 + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
             tc::mma_bf16(tbase + sl * kNT, ad, bd, idesc, kk > 0 ? 1u : 0u);
           }
-        }
         tc::mma_commit(bar_mma);
       } else {
         atomicOr(err, 1);
@@ -288,47 +423,32 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
       abort_s = 1;
     }
     tc::fence_after_sync();
-    // tensor product over the tile's edges, 8 at a time
-#pragma unroll 1
-    for (int ch = 0; ch < kNT / 8; ++ch) {
-      float wv[NP][8];
-#pragma unroll
-      for (int sl = 0; sl < NP; ++sl) tc::tmem_ld8(tbase + lane_off + sl * kNT + ch * 8, wv[sl]);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int t = ch * 8 + j;
-        const int r = s_recv[t];
-        if (r < 0) continue;
-        while (cur < r) { flush(cur); ++cur; }
-        const int sj = s_send[t];
-        float hj[G::DH];
-#pragma unroll
-        for (int d = 0; d < G::DH; ++d) hj[d] = h[((size_t)sj * D + d) * C + c];
-        const float* cy = cY + t * G::NZP;
-        static_for<0, NP>([&](auto sc) {
-          constexpr int sl = decltype(sc)::value;
-          constexpr int p = G::paths[sl];
-          constexpr int l1 = Tab::l1[p];
-          constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
-          float wh[2 * l1 + 1];
-#pragma unroll
-          for (int q = 0; q < 2 * l1 + 1; ++q) wh[q] = wv[sl][j] * hj[l1 * l1 + q];
-          static_for<kb, ke>([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            constexpr int o3 = Tab::e3[k] - G::comp0, j1 = Tab::e1[k] - l1 * l1;
-            acc[o3] = fmaf(cy[gb + k - kb], wh[j1], acc[o3]);
-          });
-        });
-      }
-    }
+    if (wsid == 0) fwd_tile_ws<L, MODE, 0>(tile, s_send, s_recv, cY, taddr0, h, cur, acc, comb, par, m, s);
+    else fwd_tile_ws<L, MODE, 1>(tile, s_send, s_recv, cY, taddr0, h, cur, acc, comb, par, m, s);
     tc::fence_before_sync();
     __syncthreads();
     if (abort_s) break;
   }
-  if (!abort_s)
-    while (cur < i1) { flush(cur); ++cur; }
-  // teardown: make sure no bulk copy is still writing into shared memory
+  if (!abort_s) {
+    // receivers after the last edge (zero degree) and the last open segment
+    while (cur < i1) {
+      float* cb = comb + par * G::NOUT * 128;
+      if (wsid != 0) {
+#pragma unroll
+        for (int q = 0; q < G::NOUT; ++q) cb[q * 128 + c] = acc[q];
+      }
+      ws_barrier();
+      if (wsid == 0) {
+#pragma unroll
+        for (int q = 0; q < G::NOUT; ++q)
+          m[((size_t)cur * D + G::comp0 + q) * C + c] = s * (acc[q] + cb[q * 128 + c]);
+      }
+#pragma unroll
+      for (int q = 0; q < G::NOUT; ++q) acc[q] = 0.0f;
+      par ^= 1;
+      ++cur;
+    }
+  }
   if (tid == 0) {
     if (w3_issued && n_tiles > 0) tc::mbar_wait(bar_w3, 0, 1LL << 20);
     for (int b = 0; b < 2; ++b)
@@ -345,10 +465,10 @@ __global__ void __launch_bounds__(128) tp_fused(int n, const int* __restrict__ r
 // ------------------------------------------------------------ tp_fused_bwd
 // Adjoint of one layer for one path group.  Per tile of kNT receiver-sorted
 // edges: (1) w = W3_p^T z2 recomputed on the tensor cores into tensor memory;
-// (2) thread c (channel c), per edge e = (j <- i):
+// (2) per edge e = (j <- i) and channel c (paths split between the warp sets):
 //       G^{t-1}_j[l1 m1] += s w[p] (-1)^{l2} C Y[l2 m2] Gm_i[l3 m3]        (reverse edge)
 //       T_p[m2] = sum C h_i[l1 m1] Gt_j[l3 m3],   Gt = s Gm_j
-//       dE/dw_e[p] = sum_m2 Y[l2 m2] T_p[m2]   -> BF16 operand tile in shared memory
+//       dE/dw_e[p] = sum_m2 Y[l2 m2] T_p[m2]   -> 16-bit operand tile in shared memory
 //       dE/dY_e[l2 m2] += sum_c w[p] T_p[m2]   (channel sum: warp butterfly + shared memory)
 // (3) dE/dz2[k][e] = sum_{p,c} W3[k][p][c] dE/dw_e[p][c]: a second MMA with A
 // read M-major from the same resident W3 image (rows 64..127 of that M = 128
@@ -362,6 +482,7 @@ struct BwdLayout {
   using G = Group<L, MODE>;
   static constexpr int NP = G::NP;
   static constexpr bool FIRST = MODE < 0;
+  static constexpr int D = NodeDims<L>::D;
   static constexpr int B2_BYTES = kNT * NP * 128 * 2;
   static constexpr int NZP = FIRST ? 4 : G::NZP;
   static constexpr int tmem_cols() {
@@ -370,41 +491,207 @@ struct BwdLayout {
     return c;
   }
   static constexpr int NCOLS = tmem_cols();
-  static constexpr size_t smem_bytes() {
-    return (size_t)NP * kW3PathBytes + 2 * kTileBytes + B2_BYTES + (size_t)kNT * NZP * 4 + kNT * 16 * 4 +
-           4 * kNT * 16 * 4 + 2 * kNT * 4 + 64;
-  }
+  static constexpr size_t off_z2 = (size_t)NP * kW3PathBytes;
+  static constexpr size_t off_b2 = off_z2 + 2 * kTileBytes;
+  static constexpr size_t off_cy = off_b2 + B2_BYTES;
+  static constexpr size_t off_y = off_cy + (size_t)kNT * NZP * 4;
+  static constexpr size_t off_red = off_y + kNT * 16 * 4;
+  static constexpr size_t off_idx = off_red + (size_t)(4 * kWS) * kNT * 16 * 4;
+  static constexpr size_t off_comb = off_idx + 2 * kNT * 4;
+  static constexpr size_t off_bar = off_comb + (FIRST ? 0 : (size_t)2 * D * 128 * 4);
+  static constexpr size_t bytes = off_bar + 64;
+  static_assert(bytes <= 232448, "shared memory of the adjoint kernel exceeds the per-block limit");
 };
 
+template <int L, int MODE, int W>
+__device__ __forceinline__ void bwd_edge(const float (&wv)[Group<L, MODE>::NP][8], int j, int t, const float* hi,
+                                         const float* Gi, const float* Gt, const float* Y, const float* cy, float s,
+                                         float dw_scale, int use_bf16, uint8_t* sB2, float* Gacc, float* dYp) {
+  using G = Group<L, MODE>;
+  using S = Split<L, MODE, true>;
+  using Tab = CGTable<L>;
+  constexpr bool FIRST = MODE < 0;
+  constexpr int SBO2 = G::NP * 2048;
+  const int c = threadIdx.x & 127;
+  static_for<0, G::NP>([&](auto sc) {
+    constexpr int sl = decltype(sc)::value;
+    if constexpr (S::ws[sl] == W) {
+      constexpr int p = G::paths[sl];
+      constexpr int l2 = Tab::l2[p], l3 = Tab::l3[p];
+      constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
+      const float wp = wv[sl][j];
+      if constexpr (!FIRST) {
+        float wg[2 * l3 + 1];
+#pragma unroll
+        for (int q = 0; q < 2 * l3 + 1; ++q) wg[q] = s * wp * Gi[l3 * l3 + q - G::comp0];
+        static_for<kb, ke>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          constexpr int i1 = Tab::e1[k], j3 = Tab::e3[k] - l3 * l3;
+          Gacc[i1] = fmaf(cy[gb + k - kb], wg[j3], Gacc[i1]);
+        });
+      }
+      float Tp[2 * l2 + 1];
+#pragma unroll
+      for (int q = 0; q < 2 * l2 + 1; ++q) Tp[q] = 0.0f;
+      static_for<kb, ke>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        constexpr int j2 = Tab::e2[k] - l2 * l2, i1 = Tab::e1[k], o3 = Tab::e3[k] - G::comp0;
+        constexpr float cv = Tab::ec[k];
+        Tp[j2] = fmaf(cv, hi[i1] * Gt[o3], Tp[j2]);
+      });
+      float dwp = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 2 * l2 + 1; ++q) {
+        dwp = fmaf(Y[l2 * l2 + q], Tp[q], dwp);
+        dYp[l2 * l2 + q] = fmaf(wp, Tp[q], dYp[l2 * l2 + q]);
+      }
+      const int kidx = sl * 128 + c;
+      *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) =
+          to16(dwp * dw_scale, use_bf16);
+    }
+  });
+}
+
+template <int L, int MODE, int W>
+__device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, const int* s_recv, const float* sY,
+                                            const float* cY, uint32_t taddr0, const float* __restrict__ hprev,
+                                            const float* __restrict__ Gm, const float* __restrict__ Gin,
+                                            float* __restrict__ Gout, int first_group, int& cur, float* Gacc,
+                                            float* Gt, float* comb, int& par, float* red, uint8_t* sB2, float s,
+                                            float dw_scale, int use_bf16) {
+  using G = Group<L, MODE>;
+  using S = Split<L, MODE, true>;
+  using BL = BwdLayout<L, MODE>;
+  constexpr int D = NodeDims<L>::D;
+  constexpr int C = 128;
+  constexpr bool FIRST = MODE < 0;
+  constexpr int DH = S::dh(W);
+  constexpr int SBO2 = G::NP * 2048;
+  const int c = threadIdx.x & 127, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto flush = [&](int i) {
+    if constexpr (!FIRST) {
+      float* cb = comb + par * D * 128;
+      if (W != 0) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) cb[d * 128 + c] = Gacc[d];
+      }
+      ws_barrier();
+      if (W == 0) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const size_t o = ((size_t)i * D + d) * C + c;
+          Gout[o] = (first_group ? Gin[o] : Gout[o]) + Gacc[d] + cb[d * 128 + c];
+        }
+      }
+      par ^= 1;
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
+  };
+  auto enter = [&](int i) {
+#pragma unroll
+    for (int q = 0; q < G::NOUT; ++q) Gt[q] = s * Gm[((size_t)i * D + G::comp0 + q) * C + c];
+  };
+  auto advance = [&](int r) {
+    while (cur < r) {
+      if (cur >= i0) flush(cur);
+      ++cur;
+      if (cur < i1) enter(cur);
+    }
+  };
+#pragma unroll 1
+  for (int ch = 0; ch < kNT / 8; ++ch) {
+    float wv[G::NP][8];
+    static_for<0, G::NP>([&](auto sc) {
+      constexpr int sl = decltype(sc)::value;
+      if constexpr (S::ws[sl] == W) tc::tmem_ld8(taddr0 + sl * kNT + ch * 8, wv[sl]);
+    });
+    tc::tmem_ld_wait();
+    float hn[DH], gn[FIRST ? 1 : G::NOUT];
+    {
+      const int si = s_send[ch * 8];
+#pragma unroll
+      for (int d = 0; d < DH; ++d) hn[d] = hprev[((size_t)si * D + d) * C + c];
+      if constexpr (!FIRST) {
+#pragma unroll
+        for (int q = 0; q < G::NOUT; ++q) gn[q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int t = ch * 8 + j;
+      float hi[DH], Gi[FIRST ? 1 : G::NOUT];
+#pragma unroll
+      for (int d = 0; d < DH; ++d) hi[d] = hn[d];
+      if constexpr (!FIRST) {
+#pragma unroll
+        for (int q = 0; q < G::NOUT; ++q) Gi[q] = gn[q];
+      }
+      if (j < 7) {
+        const int si = s_send[t + 1];
+#pragma unroll
+        for (int d = 0; d < DH; ++d) hn[d] = hprev[((size_t)si * D + d) * C + c];
+        if constexpr (!FIRST) {
+#pragma unroll
+          for (int q = 0; q < G::NOUT; ++q) gn[q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
+        }
+      }
+      const int r = s_recv[t];
+      float dYp[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) dYp[k] = 0.0f;
+      if (r >= 0) {
+        advance(r);
+        float Y[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
+        bwd_edge<L, MODE, W>(wv, j, t, hi, Gi, Gt, Y, cY + t * BL::NZP, s, dw_scale, use_bf16, sB2, Gacc, dYp);
+      } else {
+        static_for<0, G::NP>([&](auto sc) {
+          constexpr int sl = decltype(sc)::value;
+          if constexpr (S::ws[sl] == W) {
+            const int kidx = sl * 128 + c;
+            *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) = 0;
+          }
+        });
+      }
+      const float tot = warp_reduce16(dYp);
+      if ((lane & 1) == 0) red[(warp * kNT + t) * 16 + (lane >> 1)] = tot;
+    }
+  }
+}
+
 template <int L, int MODE>
-__global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict__ row_ptr,
-                                                    const int* __restrict__ recv, const int* __restrict__ send,
-                                                    const float4* __restrict__ ev, const float* __restrict__ hprev,
-                                                    const float* __restrict__ Gm, const uint8_t* __restrict__ w3img,
-                                                    const uint8_t* __restrict__ z2t, float s,
-                                                    const float* __restrict__ Gin, float* __restrict__ Gout,
-                                                    int first_group, float* __restrict__ dY, float* __restrict__ dz2,
-                                                    int use_bf16, const float* __restrict__ absmax,
-                                                    int* __restrict__ err) {
+__global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __restrict__ row_ptr,
+                                                         const int* __restrict__ recv, const int* __restrict__ send,
+                                                         const float4* __restrict__ ev,
+                                                         const float* __restrict__ hprev,
+                                                         const float* __restrict__ Gm,
+                                                         const uint8_t* __restrict__ w3img,
+                                                         const uint8_t* __restrict__ z2t, float s,
+                                                         const float* __restrict__ Gin, float* __restrict__ Gout,
+                                                         int first_group, float* __restrict__ dY,
+                                                         float* __restrict__ dz2, int use_bf16,
+                                                         const float* __restrict__ absmax, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using BL = BwdLayout<L, MODE>;
   using Tab = CGTable<L>;
   constexpr int D = NodeDims<L>::D;
-  constexpr int C = 128;
   constexpr int NP = G::NP;
   constexpr bool FIRST = BL::FIRST;
   constexpr int NZP = BL::NZP;
   constexpr int SBO2 = NP * 2048;  // B' operand: K' = NP * 128 channels
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sW3 = smem;
-  uint8_t* sZ2 = sW3 + NP * kW3PathBytes;
-  uint8_t* sB2 = sZ2 + 2 * kTileBytes;
-  float* cY = reinterpret_cast<float*>(sB2 + BL::B2_BYTES);
-  float* sY = cY + kNT * NZP;
-  float* red = sY + kNT * 16;  // [4][kNT][16]
-  int* s_send = reinterpret_cast<int*>(red + 4 * kNT * 16);
+  uint8_t* sZ2 = smem + BL::off_z2;
+  uint8_t* sB2 = smem + BL::off_b2;
+  float* cY = reinterpret_cast<float*>(smem + BL::off_cy);
+  float* sY = reinterpret_cast<float*>(smem + BL::off_y);
+  float* red = reinterpret_cast<float*>(smem + BL::off_red);  // [4 kWS][kNT][16]
+  int* s_send = reinterpret_cast<int*>(smem + BL::off_idx);
   int* s_recv = s_send + kNT;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_recv + kNT);
+  float* comb = reinterpret_cast<float*>(smem + BL::off_comb);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BL::off_bar);
   uint64_t* bar_w3 = bars;
   uint64_t* bar_z2 = bars + 1;  // [2]
   uint64_t* bar_mma = bars + 3;
@@ -412,7 +699,7 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 5);
   __shared__ int abort_s;
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, c = tid;
+  const int tid = threadIdx.x, warp = tid >> 5, wsid = warp >> 2;
   if (warp == 0) {
     tc::tmem_alloc(tmem_holder, BL::NCOLS);
     tc::tmem_relinquish();
@@ -430,7 +717,7 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tmem_holder;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const uint32_t taddr0 = tbase + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t dcol = NP * kNT;  // columns of dE/dz2 in tensor memory
 
   int i0, i1;
@@ -457,29 +744,7 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
   for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
 #pragma unroll
   for (int q = 0; q < G::NOUT; ++q) Gt[q] = 0.0f;
-  int cur = i0 - 1;
-  auto flush = [&](int i) {
-    if (!FIRST) {
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const size_t o = ((size_t)i * D + d) * C + c;
-        Gout[o] = (first_group ? Gin[o] : Gout[o]) + Gacc[d];
-      }
-    }
-#pragma unroll
-    for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
-  };
-  auto enter = [&](int i) {
-#pragma unroll
-    for (int q = 0; q < G::NOUT; ++q) Gt[q] = s * Gm[((size_t)i * D + G::comp0 + q) * C + c];
-  };
-  auto advance = [&](int r) {
-    while (cur < r) {
-      if (cur >= i0) flush(cur);
-      ++cur;
-      if (cur < i1) enter(cur);
-    }
-  };
+  int cur = i0 - 1, par = 0;
   const uint32_t idesc1 = tc::idesc_16bit(128, kNT, use_bf16 != 0);
   const uint32_t idesc2 = idesc1 | (1u << 15);  // A M-major
   // dE/dw enters the second product scaled by a power of two (FP16 operands):
@@ -559,89 +824,12 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
       abort_s = 1;
     }
     tc::fence_after_sync();
-#pragma unroll 1
-    for (int ch = 0; ch < kNT / 8; ++ch) {
-      float wv[NP][8];
-#pragma unroll
-      for (int sl = 0; sl < NP; ++sl) tc::tmem_ld8(tbase + lane_off + sl * kNT + ch * 8, wv[sl]);
-      tc::tmem_ld_wait();
-#pragma unroll 1
-      for (int j = 0; j < 8; ++j) {
-        const int t = ch * 8 + j;
-        const int r = s_recv[t];
-        float dYp[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) dYp[k] = 0.0f;
-        float wsel[NP];
-#pragma unroll
-        for (int sl = 0; sl < NP; ++sl) {
-          float x = wv[sl][0];
-#pragma unroll
-          for (int q = 1; q < 8; ++q) x = (j == q) ? wv[sl][q] : x;
-          wsel[sl] = x;
-        }
-        if (r >= 0) {
-          advance(r);
-          const int si = s_send[t];
-          float hi[G::DH];
-#pragma unroll
-          for (int d = 0; d < G::DH; ++d) hi[d] = hprev[((size_t)si * D + d) * C + c];
-          float Y[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
-          float Gi[G::NOUT];
-          if constexpr (!FIRST) {
-#pragma unroll
-            for (int q = 0; q < G::NOUT; ++q) Gi[q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
-          }
-          const float* cy = cY + t * NZP;
-          static_for<0, NP>([&](auto sc) {
-            constexpr int sl = decltype(sc)::value;
-            constexpr int p = G::paths[sl];
-            constexpr int l2 = Tab::l2[p], l3 = Tab::l3[p];
-            constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
-            const float wp = wsel[sl];
-            if constexpr (!FIRST) {
-              float wg[2 * l3 + 1];
-#pragma unroll
-              for (int q = 0; q < 2 * l3 + 1; ++q) wg[q] = s * wp * Gi[l3 * l3 + q - G::comp0];
-              static_for<kb, ke>([&](auto kc) {
-                constexpr int k = decltype(kc)::value;
-                constexpr int i1 = Tab::e1[k], j3 = Tab::e3[k] - l3 * l3;
-                Gacc[i1] = fmaf(cy[gb + k - kb], wg[j3], Gacc[i1]);
-              });
-            }
-            float Tp[2 * l2 + 1];
-#pragma unroll
-            for (int q = 0; q < 2 * l2 + 1; ++q) Tp[q] = 0.0f;
-            static_for<kb, ke>([&](auto kc) {
-              constexpr int k = decltype(kc)::value;
-              constexpr int j2 = Tab::e2[k] - l2 * l2, i1 = Tab::e1[k], o3 = Tab::e3[k] - G::comp0;
-              constexpr float cv = Tab::ec[k];
-              Tp[j2] = fmaf(cv, hi[i1] * Gt[o3], Tp[j2]);
-            });
-            float dwp = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 2 * l2 + 1; ++q) {
-              dwp = fmaf(Y[l2 * l2 + q], Tp[q], dwp);
-              dYp[l2 * l2 + q] = fmaf(wp, Tp[q], dYp[l2 * l2 + q]);
-            }
-            const int kidx = sl * 128 + c;
-            *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) =
-                to16(dwp * dw_scale, use_bf16);
-          });
-        } else {
-          // edge outside this block's range: zero operand row
-#pragma unroll
-          for (int sl = 0; sl < NP; ++sl) {
-            const int kidx = sl * 128 + c;
-            *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) = 0;
-          }
-        }
-        const float tot = warp_reduce16(dYp);
-        if ((lane & 1) == 0) red[(warp * kNT + t) * 16 + (lane >> 1)] = tot;
-      }
-    }
+    if (wsid == 0)
+      bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, Gin, Gout, first_group, cur, Gacc,
+                              Gt, comb, par, red, sB2, s, dw_scale, use_bf16);
+    else
+      bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, Gin, Gout, first_group, cur, Gacc,
+                              Gt, comb, par, red, sB2, s, dw_scale, use_bf16);
     // second product: dE/dz2 = W3 dE/dw over this tile
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -666,8 +854,9 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
       const int t = q >> 4, k = q & 15;
       const int e = tile * kNT + t;
       if (e >= E0 && e < E1) {
-        const float v = red[(0 * kNT + t) * 16 + k] + red[(1 * kNT + t) * 16 + k] + red[(2 * kNT + t) * 16 + k] +
-                        red[(3 * kNT + t) * 16 + k];
+        float v = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 4 * kWS; ++w) v += red[(w * kNT + t) * 16 + k];
         dY[(size_t)e * 16 + k] += v;
       }
     }
@@ -680,7 +869,7 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
 #pragma unroll 1
       for (int ch = 0; ch < kNT / 8; ++ch) {
         float v[8];
-        tc::tmem_ld8(tbase + lane_off + dcol + ch * 8, v);
+        tc::tmem_ld8(taddr0 + dcol + ch * 8, v);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -693,7 +882,33 @@ __global__ void __launch_bounds__(128) tp_fused_bwd(int n, const int* __restrict
     __syncthreads();
     if (abort_s) break;
   }
-  if (!abort_s) advance(i1);
+  if (!abort_s) {
+    // remaining receivers of the range (uniform across warp sets)
+    const int c = tid & 127;
+    while (cur < i1) {
+      if (cur >= i0) {
+        if constexpr (!FIRST) {
+          float* cb = comb + par * D * 128;
+          if (wsid != 0) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) cb[d * 128 + c] = Gacc[d];
+          }
+          ws_barrier();
+          if (wsid == 0) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              const size_t o = ((size_t)cur * D + d) * 128 + c;
+              Gout[o] = (first_group ? Gin[o] : Gout[o]) + Gacc[d] + cb[d * 128 + c];
+            }
+          }
+          par ^= 1;
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
+      }
+      ++cur;
+    }
+  }
   if (tid == 0) {
     if (w3_issued && n_tiles > 0) tc::mbar_wait(bar_w3, 0, 1LL << 20);
     for (int b = 0; b < 2; ++b)
@@ -839,12 +1054,11 @@ template <int L, int MODE>
 int launch_group(int n, const int* row_ptr, const int* recv, const int* send, const float4* ev, const float* h,
                  const uint8_t* w3img, const uint8_t* z2t, float s, float* m, int use_bf16, int* err, int blocks,
                  cudaStream_t st) {
-  using G = Group<L, MODE>;
-  const size_t smem = G::smem_bytes();
+  const size_t smem = FwdLayout<L, MODE>::bytes;
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     MLIP_PROF("tp_fused", st);
-    tp_fused<L, MODE><<<blocks, 128, smem, st>>>(n, row_ptr, recv, send, ev, h, w3img, z2t, s, m, use_bf16, err);
+    tp_fused<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, ev, h, w3img, z2t, s, m, use_bf16, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
@@ -856,11 +1070,11 @@ int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send
                      const float* Gin, float* Gout, int first_group, float* dY, float* dz2, int use_bf16,
                      const float* absmax, int* err, int blocks, cudaStream_t st) {
   using BL = BwdLayout<L, MODE>;
-  const size_t smem = BL::smem_bytes();
+  const size_t smem = BL::bytes;
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused_bwd<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     MLIP_PROF("tp_fused_bwd", st);
-    tp_fused_bwd<L, MODE><<<blocks, 128, smem, st>>>(n, row_ptr, recv, send, ev, hprev, Gm, w3img, z2t, s, Gin,
+    tp_fused_bwd<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, ev, hprev, Gm, w3img, z2t, s, Gin,
                                                     Gout, first_group, dY, dz2, use_bf16, absmax, err);
   }
   MLIP_LAUNCH_CHECK();
