@@ -204,6 +204,7 @@ struct FwdLayout {
   static constexpr size_t off_comb = off_idx + 2 * kNT * 4;
   static constexpr size_t off_bar = off_comb + (size_t)2 * G::NOUT * 128 * 4;
   static constexpr size_t bytes = off_bar + 64;
+  static_assert(bytes <= 232448 - 1024, "shared memory of the forward kernel exceeds the per-block limit");
 };
 
 template <int L, int MODE, int W>
@@ -498,9 +499,9 @@ struct BwdLayout {
   static constexpr size_t off_red = off_y + kNT * 16 * 4;
   static constexpr size_t off_idx = off_red + (size_t)(4 * kWS) * kNT * 16 * 4;
   static constexpr size_t off_comb = off_idx + 2 * kNT * 4;
-  static constexpr size_t off_bar = off_comb + (FIRST ? 0 : (size_t)2 * D * 128 * 4);
+  static constexpr size_t off_bar = off_comb + (FIRST ? 0 : (size_t)D * 128 * 4);
   static constexpr size_t bytes = off_bar + 64;
-  static_assert(bytes <= 232448, "shared memory of the adjoint kernel exceeds the per-block limit");
+  static_assert(bytes <= 232448 - 1024, "shared memory of the adjoint kernel exceeds the per-block limit");
 };
 
 template <int L, int MODE, int W>
@@ -570,7 +571,7 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
   const int c = threadIdx.x & 127, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto flush = [&](int i) {
     if constexpr (!FIRST) {
-      float* cb = comb + par * D * 128;
+      float* cb = comb;  // single buffer: written, barrier, read, barrier
       if (W != 0) {
 #pragma unroll
         for (int d = 0; d < D; ++d) cb[d * 128 + c] = Gacc[d];
@@ -583,6 +584,7 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
           Gout[o] = (first_group ? Gin[o] : Gout[o]) + Gacc[d] + cb[d * 128 + c];
         }
       }
+      ws_barrier();
       par ^= 1;
     }
 #pragma unroll
@@ -888,7 +890,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
     while (cur < i1) {
       if (cur >= i0) {
         if constexpr (!FIRST) {
-          float* cb = comb + par * D * 128;
+          float* cb = comb;
           if (wsid != 0) {
 #pragma unroll
             for (int d = 0; d < D; ++d) cb[d * 128 + c] = Gacc[d];
@@ -901,6 +903,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
               Gout[o] = (first_group ? Gin[o] : Gout[o]) + Gacc[d] + cb[d * 128 + c];
             }
           }
+          ws_barrier();
           par ^= 1;
         }
 #pragma unroll

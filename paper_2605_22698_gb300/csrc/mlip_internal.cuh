@@ -21,6 +21,7 @@ const char* last_error();
   do {                                                                                         \
     cudaError_t e__ = (expr);                                                                  \
     if (e__ != cudaSuccess) {                                                                  \
+      cudaGetLastError(); /* clear a non-sticky error so later calls are not blamed */          \
       ::mlip::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e__), __FILE__, __LINE__); \
       return e__ == cudaErrorMemoryAllocation ? MLIP_ERR_OOM : MLIP_ERR_CUDA;                  \
     }                                                                                          \

@@ -9,7 +9,7 @@
 //   nl_setup    one thread: bins per axis (each bin at least rc (1 + 1e-6) wide
 //               perpendicular to its faces), search reach, cap on bin count
 //   nl_bin      bin of each atom, counts; scan; nl_scatter atoms into bins
-//   nl_pairs    one thread per receiver: every candidate (j, S) from the bins
+//   nl_pairs    one warp per receiver: every candidate (j, S) from the bins
 //               within reach, S = q - n_j + n_i, exact test
 //                 d2 = (dx*dx + dy*dy) + dz*dz < rc^2 with dx = (x_j - x_i) + sx,
 //                 sx = (S0 h00 + S1 h10) + S2 h20, round-to-nearest, no FMA,
@@ -151,11 +151,17 @@ __device__ __forceinline__ unsigned long long make_key(int j, int s0, int s1, in
 }
 
 // flags[0]: max degree seen; flags[1]: |S| > 127 seen
-__global__ void nl_pairs(int n, const Grid* __restrict__ g, const double* __restrict__ pos,
-                         const double* __restrict__ frac, const int* __restrict__ img,
-                         const int* __restrict__ bin_start, const int* __restrict__ bin_atoms,
-                         unsigned long long* __restrict__ slab, int* __restrict__ deg, int* __restrict__ flags) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per receiver: the candidate bins within reach are taken 32 at a
+// time, their atom counts prefix-summed across the lanes, and the flattened
+// candidate list walked by all lanes at once (each lane finds its bin by a
+// binary search over the prefix with shuffles).  Matches are compacted with a
+// ballot into the receiver's slab (order irrelevant: nl_sort orders them).
+__global__ void nl_pairs_warp(int n, const Grid* __restrict__ g, const double* __restrict__ pos,
+                              const double* __restrict__ frac, const int* __restrict__ img,
+                              const int* __restrict__ bin_start, const int* __restrict__ bin_atoms,
+                              unsigned long long* __restrict__ slab, int* __restrict__ deg, int* __restrict__ flags) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
   const int maxdeg = g->maxdeg;
   double f[3] = {frac[3 * i], frac[3 * i + 1], frac[3 * i + 2]};
@@ -165,28 +171,59 @@ __global__ void nl_pairs(int n, const Grid* __restrict__ g, const double* __rest
   const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
   const double* h = g->h;
   const double rc2 = g->rc2;
+  const int r0 = g->reach[0], r1 = g->reach[1], r2 = g->reach[2];
+  const int w0 = 2 * r0 + 1, w1 = 2 * r1 + 1, w2 = 2 * r2 + 1;
+  const int nbins = w0 * w1 * w2;
   int cnt = 0;
   bool bad_shift = false;
-  for (int d0 = -g->reach[0]; d0 <= g->reach[0]; ++d0) {
-    int c0 = b[0] + d0, q0 = 0;
-    if (g->pbc[0]) { q0 = (int)floor((double)c0 / g->nb[0]); c0 -= q0 * g->nb[0]; }
-    else if (c0 < 0 || c0 >= g->nb[0]) continue;
-    for (int d1 = -g->reach[1]; d1 <= g->reach[1]; ++d1) {
-      int c1 = b[1] + d1, q1 = 0;
-      if (g->pbc[1]) { q1 = (int)floor((double)c1 / g->nb[1]); c1 -= q1 * g->nb[1]; }
-      else if (c1 < 0 || c1 >= g->nb[1]) continue;
-      for (int d2 = -g->reach[2]; d2 <= g->reach[2]; ++d2) {
-        int c2 = b[2] + d2, q2 = 0;
-        if (g->pbc[2]) { q2 = (int)floor((double)c2 / g->nb[2]); c2 -= q2 * g->nb[2]; }
-        else if (c2 < 0 || c2 >= g->nb[2]) continue;
+  for (int base = 0; base < nbins; base += 32) {
+    // this lane's bin
+    const int bidx = base + lane;
+    int beg = 0, len = 0, q0 = 0, q1 = 0, q2 = 0;
+    if (bidx < nbins) {
+      const int d2 = bidx % w2 - r2, d1 = (bidx / w2) % w1 - r1, d0 = bidx / (w2 * w1) - r0;
+      int c0 = b[0] + d0, c1 = b[1] + d1, c2 = b[2] + d2;
+      bool ok = true;
+      if (g->pbc[0]) { q0 = (int)floor((double)c0 / g->nb[0]); c0 -= q0 * g->nb[0]; } else ok = ok && c0 >= 0 && c0 < g->nb[0];
+      if (g->pbc[1]) { q1 = (int)floor((double)c1 / g->nb[1]); c1 -= q1 * g->nb[1]; } else ok = ok && c1 >= 0 && c1 < g->nb[1];
+      if (g->pbc[2]) { q2 = (int)floor((double)c2 / g->nb[2]); c2 -= q2 * g->nb[2]; } else ok = ok && c2 >= 0 && c2 < g->nb[2];
+      if (ok) {
         const int bin = (c0 * g->nb[1] + c1) * g->nb[2] + c2;
-        const int beg = bin_start[bin], end = bin_start[bin + 1];
-        for (int t = beg; t < end; ++t) {
-          const int j = bin_atoms[t];
-          const int S0 = q0 - img[3 * j] + ni0;
-          const int S1 = q1 - img[3 * j + 1] + ni1;
-          const int S2 = q2 - img[3 * j + 2] + ni2;
-          if (j == i && S0 == 0 && S1 == 0 && S2 == 0) continue;
+        beg = bin_start[bin];
+        len = bin_start[bin + 1] - beg;
+      }
+    }
+    int incl = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int fb = 0; fb < total; fb += 32) {
+      const int fidx = fb + lane;
+      const bool act = fidx < total;
+      // smallest k with incl[k] > fidx
+      int lo = 0, hi = 31;
+#pragma unroll
+      for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const int v = __shfl_sync(0xffffffffu, incl, mid);
+        if (v > fidx) hi = mid; else lo = mid + 1;
+      }
+      const int k = lo;
+      const int kbeg = __shfl_sync(0xffffffffu, beg, k);
+      const int klen = __shfl_sync(0xffffffffu, len, k);
+      const int kinc = __shfl_sync(0xffffffffu, incl, k);
+      const int kq0 = __shfl_sync(0xffffffffu, q0, k), kq1 = __shfl_sync(0xffffffffu, q1, k),
+                kq2 = __shfl_sync(0xffffffffu, q2, k);
+      bool hit = false;
+      unsigned long long key = 0;
+      if (act) {
+        const int j = bin_atoms[kbeg + fidx - (kinc - klen)];
+        const int S0 = kq0 - img[3 * j] + ni0;
+        const int S1 = kq1 - img[3 * j + 1] + ni1;
+        const int S2 = kq2 - img[3 * j + 2] + ni2;
+        if (!(j == i && S0 == 0 && S1 == 0 && S2 == 0)) {
           double sx = 0.0, sy = 0.0, sz = 0.0;
           if (g->any_pbc) {
             sx = __dadd_rn(__dadd_rn(__dmul_rn((double)S0, h[0]), __dmul_rn((double)S1, h[3])), __dmul_rn((double)S2, h[6]));
@@ -198,17 +235,25 @@ __global__ void nl_pairs(int n, const Grid* __restrict__ g, const double* __rest
           const double dz = __dadd_rn(__dsub_rn(pos[3 * j + 2], zi), sz);
           const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
           if (d2 < rc2) {
+            hit = true;
             if (S0 < -127 || S0 > 127 || S1 < -127 || S1 > 127 || S2 < -127 || S2 > 127) bad_shift = true;
-            if (cnt < maxdeg) slab[(size_t)i * maxdeg + cnt] = make_key(j, S0, S1, S2);
-            ++cnt;
+            key = make_key(j, S0, S1, S2);
           }
         }
       }
+      const unsigned mask = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int slot = cnt + __popc(mask & ((1u << lane) - 1u));
+        if (slot < maxdeg) slab[(size_t)i * maxdeg + slot] = key;
+      }
+      cnt += __popc(mask);
     }
   }
-  deg[i] = cnt;
-  if (cnt > maxdeg) atomicMax(&flags[0], cnt);
-  if (bad_shift) atomicOr(&flags[1], 1);
+  if (lane == 0) {
+    deg[i] = cnt;
+    if (cnt > maxdeg) atomicMax(&flags[0], cnt);
+  }
+  if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicOr(&flags[1], 1);
 }
 
 // One warp per receiver; dynamic shared memory: warps_per_block * cap keys.
@@ -435,7 +480,7 @@ int build_neighbors(Workspace& ws, const double* d_pos, int64_t n64, const doubl
     MLIP_TRY(ws.get("nl.slab", (size_t)nn * maxdeg, &slab));
     if (n > 0) {
       { MLIP_PROF("nl_scatter", st); nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms); }
-      { MLIP_PROF("nl_pairs", st); nl_pairs<<<blocks, threads, 0, st>>>(n, dg, d_pos, frac, img, bin_start, bin_atoms, slab, deg, flags); }
+      { MLIP_PROF("nl_pairs", st); nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, d_pos, frac, img, bin_start, bin_atoms, slab, deg, flags); }
       MLIP_LAUNCH_CHECK();
     }
     MLIP_TRY(exclusive_scan_i32(ws, deg, out->row_ptr, n, st));

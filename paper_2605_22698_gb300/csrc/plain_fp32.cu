@@ -432,8 +432,86 @@ __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int*
 }
 
 // ----------------------------------------------------------- channel mixing
-// u = m W_l for the 2l+1 rows of every node; h_out = h_in + (l == 0 ? silu(u) : u);
-// u0 keeps the l = 0 pre-activation.  grid = (node tiles, L+1); W_l in shared memory.
+// Per order l, the (2l+1) N rows of node components times W_l (C x C), as a
+// tiled FP32 GEMM: 64 rows x 128 output channels per block, K = C = 128 staged
+// in shared memory, 8 x 8 outputs per thread.  Row r of order l is node
+// r / (2l+1), component l^2 + r % (2l+1).
+//   forward:  u = m W_l;  h_out = h_in + (l == 0 ? silu(u) : u);  u0 keeps u (l = 0)
+//   backward: Gm = Gu W_l^T,  Gu = G silu'(u0) (l = 0) or G
+constexpr int kMixRows = 64;
+template <bool BWD>
+__global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __restrict__ X,
+                                                const float* __restrict__ Wmix, const float* __restrict__ hin,
+                                                float* __restrict__ out, float* __restrict__ u0,
+                                                const float* __restrict__ u0_in) {
+  constexpr int C = 128;
+  extern __shared__ __align__(16) float sm[];
+  float* Ws = sm;                   // [k][n]  (forward W_l[k][n]; backward W_l[n][k])
+  float* As = sm + C * C;           // [k][row]
+  const int l = blockIdx.y, R = 2 * l + 1, D = (L + 1) * (L + 1);
+  const int rows = n * R;
+  const int row0 = blockIdx.x * kMixRows;
+  if (row0 >= rows) return;
+  const float* Wl = Wmix + (size_t)l * C * C;
+  for (int k = threadIdx.x; k < C * C; k += blockDim.x) {
+    const int a = k / C, b = k % C;
+    if (!BWD) Ws[k] = Wl[k];
+    else Ws[b * C + a] = Wl[k];     // Ws[k'][n'] = W[n'][k']
+  }
+  for (int k = threadIdx.x; k < kMixRows * C; k += blockDim.x) {
+    const int rr = k / C, cc = k % C, r = row0 + rr;
+    float v = 0.0f;
+    if (r < rows) {
+      const int nd = r / R, mm = r % R;
+      v = X[((size_t)nd * D + l * l + mm) * C + cc];
+      if (BWD && l == 0) v *= silu_grad_f(u0_in[(size_t)nd * C + cc]);
+    }
+    As[cc * kMixRows + rr] = v;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 column groups x 8 row groups
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < C; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(&As[k * kMixRows + ty * 8]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&As[k * kMixRows + ty * 8 + 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&Ws[k * C + tx * 4]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Ws[k * C + 64 + tx * 4]);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = row0 + ty * 8 + i;
+    if (r >= rows) continue;
+    const int nd = r / R, mm = r % R;
+    const size_t base = ((size_t)nd * D + l * l + mm) * C;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int cc = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
+      const float u = acc[i][j];
+      if (BWD) {
+        out[base + cc] = u;
+      } else if (l == 0) {
+        u0[(size_t)nd * C + cc] = u;
+        out[base + cc] = hin[base + cc] + silu_f(u);
+      } else {
+        out[base + cc] = hin[base + cc] + u;
+      }
+    }
+  }
+}
+
+// Mixes for other channel counts (the 16-channel model): one thread per output
+// channel, W_l in shared memory.
 constexpr int kMixNodes = 8;
 __global__ void mix_fwd(int n, int C, int L, const float* __restrict__ m, const float* __restrict__ Wmix,
                         const float* __restrict__ hin, float* __restrict__ hout, float* __restrict__ u0) {
@@ -467,7 +545,6 @@ __global__ void mix_fwd(int n, int C, int L, const float* __restrict__ m, const 
   }
 }
 
-// Gm[c] = sum_c' W_l[c][c'] Gu[c'],  Gu = G * silu'(u0) (l = 0) or G.
 __global__ void mix_bwd(int n, int C, int L, const float* __restrict__ G, const float* __restrict__ u0,
                         const float* __restrict__ Wmix, float* __restrict__ Gm) {
   extern __shared__ float smem[];
@@ -591,6 +668,14 @@ int launch_tp_bwd(int L, bool first, int n, int C, const int* row_ptr, const int
 int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const float* hin, float* hout,
                    float* u0, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
+  if (C == 128) {
+    const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
+    MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
+    { MLIP_PROF("mix_fwd", st); mix_gemm<false><<<grid, 128, smem, st>>>(n, L, m, Wmix, hin, hout, u0, nullptr); }
+    MLIP_LAUNCH_CHECK();
+    return MLIP_OK;
+  }
   const size_t smem = ((size_t)C * C + (size_t)kMixNodes * (2 * L + 1) * C) * sizeof(float);
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n + kMixNodes - 1) / kMixNodes, L + 1);
@@ -602,6 +687,14 @@ int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const
 int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, float* Gm,
                    cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
+  if (C == 128) {
+    const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
+    MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
+    { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, G, Wmix, nullptr, Gm, nullptr, u0); }
+    MLIP_LAUNCH_CHECK();
+    return MLIP_OK;
+  }
   const size_t smem = ((size_t)C * C + (size_t)kMixNodes * (2 * L + 1) * C) * sizeof(float);
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n + kMixNodes - 1) / kMixNodes, L + 1);
