@@ -101,7 +101,7 @@ template <int H>
 __global__ void radial_tiles(int E, int n_tiles, const float4* __restrict__ ev, const float* __restrict__ W1,
                              const float* __restrict__ W2, float rc, int p, int use_bf16, uint8_t* __restrict__ z2t) {
   static_assert(H == 64, "tile layout assumes K = 64");
-  __shared__ float sW1[8 * H], sW2[H * H];
+  __shared__ __align__(16) float sW1[8 * H], sW2[H * H];
   for (int k = threadIdx.x; k < 8 * H; k += blockDim.x) sW1[k] = W1[k];
   for (int k = threadIdx.x; k < H * H; k += blockDim.x) sW2[k] = W2[k];
   __syncthreads();
@@ -125,21 +125,30 @@ __global__ void radial_tiles(int E, int n_tiles, const float4* __restrict__ ev, 
     for (int q = 0; q < 8; ++q) a = fmaf(b[q], sW1[q * H + k], a);
     z1[k] = silu_f(a);
   }
-#pragma unroll 1
+  // z2 = silu(z1 W2): all H outputs at once, one 16-byte load of a W2 row feeds four FMAs
+  float a2[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) a2[k] = 0.0f;
+#pragma unroll 4
+  for (int q = 0; q < H; ++q) {
+    const float zq = z1[q];
+    const float4* w4 = reinterpret_cast<const float4*>(sW2 + q * H);
+#pragma unroll
+    for (int k4 = 0; k4 < H / 4; ++k4) {
+      const float4 w = w4[k4];
+      a2[4 * k4] = fmaf(zq, w.x, a2[4 * k4]);
+      a2[4 * k4 + 1] = fmaf(zq, w.y, a2[4 * k4 + 1]);
+      a2[4 * k4 + 2] = fmaf(zq, w.z, a2[4 * k4 + 2]);
+      a2[4 * k4 + 3] = fmaf(zq, w.w, a2[4 * k4 + 3]);
+    }
+  }
+#pragma unroll
   for (int kg = 0; kg < 8; ++kg) {
     uint32_t pk[4];
 #pragma unroll
     for (int h2 = 0; h2 < 4; ++h2) {
-      float o[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int k = kg * 8 + h2 * 2 + u;
-        float a = 0.0f;
-#pragma unroll
-        for (int q = 0; q < H; ++q) a = fmaf(z1[q], sW2[q * H + k], a);
-        o[u] = silu_f(a);
-      }
-      pk[h2] = (uint32_t)to16(o[0], use_bf16) | ((uint32_t)to16(o[1], use_bf16) << 16);
+      const int k = kg * 8 + h2 * 2;
+      pk[h2] = (uint32_t)to16(silu_f(a2[k]), use_bf16) | ((uint32_t)to16(silu_f(a2[k + 1]), use_bf16) << 16);
     }
     *reinterpret_cast<uint4*>(tile + tc::canon_off(t, kg * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
@@ -148,12 +157,11 @@ __global__ void radial_tiles(int E, int n_tiles, const float4* __restrict__ ev, 
 // ------------------------------------------------------------ warp sets
 // A CTA runs kWS warp sets of 4 warps (128 threads, one per channel and TMEM
 // lane).  All warp sets walk the same edges; the group's paths are split
-// between them (greedy by flop cost), and their per-receiver partial sums are
-// combined through shared memory at receiver boundaries.
+// between them (greedy by flop cost), and every warp set writes its partial
+// sums to an output buffer of its own (the next mix adds the buffers), so the
+// warp sets never wait for each other inside a tile.
 constexpr int kWS = 2;
 constexpr int kThreads = 128 * kWS;
-
-__device__ __forceinline__ void ws_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
 
 template <int L, int MODE, bool BWD>
 struct Split {
@@ -193,6 +201,78 @@ struct Split {
   }
 };
 
+// Per-CTA copy of the group's CG entries for the per-tile products c * Y:
+// coefficient (with the reverse-edge sign (-1)^l2 when SIGNED) and Y index.
+template <int L, int MODE, bool SIGNED>
+__device__ __forceinline__ void load_group_table(float* tab_c, uint8_t* tab_y) {
+  using G = Group<L, MODE>;
+  using Tab = CGTable<L>;
+  const int tid = threadIdx.x;
+  static_for<0, G::NP>([&](auto sc) {
+    constexpr int sl = decltype(sc)::value;
+    constexpr int p = G::paths[sl];
+    constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
+    static_for<kb, ke>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      constexpr float cv = ((SIGNED && (Tab::l2[p] & 1)) ? -1.0f : 1.0f) * Tab::ec[k];
+      constexpr int i2 = Tab::e2[k];
+      if (tid == gb + k - kb) {
+        tab_c[gb + k - kb] = cv;
+        tab_y[gb + k - kb] = (uint8_t)i2;
+      }
+    });
+  });
+}
+
+// Per tile: receiver/sender ids and harmonics (threads < kNT), then the
+// products cY[t][k] = c_k Y_t[i2_k] by all threads.
+template <int NZ, int NZP>
+__device__ __forceinline__ void tile_setup(int tile, int E0, int E1, const int* __restrict__ recv,
+                                           const int* __restrict__ send, const float* __restrict__ Yg, int* s_recv,
+                                           int* s_send, float* sY, float* cY, const float* tab_c,
+                                           const uint8_t* tab_y) {
+  const int tid = threadIdx.x;
+  if (tid < kNT) {
+    const int e = tile * kNT + tid;
+    const bool valid = e >= E0 && e < E1;
+    s_recv[tid] = valid ? recv[e] : -1;
+    s_send[tid] = valid ? send[e] : 0;
+  }
+  for (int q = tid; q < kNT * 4; q += blockDim.x) {  // 16 floats per edge as float4
+    const int t = q >> 2, e = tile * kNT + t;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e >= E0 && e < E1) v = reinterpret_cast<const float4*>(Yg)[(size_t)e * 4 + (q & 3)];
+    reinterpret_cast<float4*>(sY)[q] = v;
+  }
+  __syncthreads();
+  if (NZ > 0) {
+    for (int q = tid; q < kNT * NZ; q += blockDim.x) {
+      const int t = q / NZ, k = q - t * NZ;
+      cY[t * NZP + k] = tab_c[k] * sY[t * 16 + tab_y[k]];
+    }
+  }
+}
+
+// Real harmonics of every edge direction, Y[e][16] (once per evaluation).
+__global__ void edge_sh(int E, const float4* __restrict__ ev, float* __restrict__ Yg) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    const float4 v = ev[e];
+    const float ir = 1.0f / v.w;
+    float Y[16];
+    sh3<float>(v.x * ir, v.y * ir, v.z * ir, Y);
+    float4* dst = reinterpret_cast<float4*>(Yg + (size_t)e * 16);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = make_float4(Y[4 * q], Y[4 * q + 1], Y[4 * q + 2], Y[4 * q + 3]);
+  }
+}
+
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
+  uint32_t r0, r1;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr));
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+}
+
 // ---------------------------------------------------------------- tp_fused
 template <int L, int MODE>
 struct FwdLayout {
@@ -200,16 +280,17 @@ struct FwdLayout {
   static constexpr int NP = G::NP;
   static constexpr size_t off_z2 = (size_t)NP * kW3PathBytes;
   static constexpr size_t off_cy = off_z2 + 2 * kTileBytes;
-  static constexpr size_t off_idx = off_cy + (size_t)kNT * G::NZP * 4;
-  static constexpr size_t off_comb = off_idx + 2 * kNT * 4;
-  static constexpr size_t off_bar = off_comb + (size_t)2 * G::NOUT * 128 * 4;
+  static constexpr size_t off_y = off_cy + (size_t)kNT * G::NZP * 4;
+  static constexpr size_t off_tab = off_y + kNT * 16 * 4;
+  static constexpr size_t off_taby = off_tab + (size_t)G::NZP * 4;
+  static constexpr size_t off_idx = off_taby + (((size_t)G::NZP + 15) & ~(size_t)15);
+  static constexpr size_t off_bar = off_idx + 2 * kNT * 4;
   static constexpr size_t bytes = off_bar + 64;
   static_assert(bytes <= 232448 - 1024, "shared memory of the forward kernel exceeds the per-block limit");
 };
 
 template <int L, int MODE, int W>
-__device__ __forceinline__ void fwd_edge(const float (&wv)[Group<L, MODE>::NP][8], int j, const float* hj,
-                                         const float* cy, float* acc) {
+__device__ __forceinline__ void fwd_edge(const float* wv, const float* hj, const float* cy, float* acc) {
   using G = Group<L, MODE>;
   using S = Split<L, MODE, false>;
   using Tab = CGTable<L>;
@@ -221,7 +302,7 @@ __device__ __forceinline__ void fwd_edge(const float (&wv)[Group<L, MODE>::NP][8
       constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
       float wh[2 * l1 + 1];
 #pragma unroll
-      for (int q = 0; q < 2 * l1 + 1; ++q) wh[q] = wv[sl][j] * hj[l1 * l1 + q];
+      for (int q = 0; q < 2 * l1 + 1; ++q) wh[q] = wv[sl] * hj[l1 * l1 + q];
       static_for<kb, ke>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
         constexpr int o3 = Tab::e3[k] - G::comp0, j1 = Tab::e1[k] - l1 * l1;
@@ -231,75 +312,76 @@ __device__ __forceinline__ void fwd_edge(const float (&wv)[Group<L, MODE>::NP][8
   });
 }
 
+// One warp set over one tile: 2-edge chunks, sender features prefetched one
+// chunk ahead, partial messages flushed (times s) into this warp set's buffer.
 template <int L, int MODE, int W>
-__device__ __forceinline__ void fwd_tile_ws(int tile, const int* s_send, const int* s_recv, const float* cY,
-                                            uint32_t taddr0, const float* __restrict__ h, int& cur, float* acc,
-                                            float* comb, int& par, float* __restrict__ m, float s) {
+__device__ __forceinline__ void fwd_tile_ws(const int* s_send, const int* s_recv, const float* cY, uint32_t taddr0,
+                                            const float* __restrict__ h, int& cur, float* acc,
+                                            float* __restrict__ mW, float s) {
   using G = Group<L, MODE>;
   using S = Split<L, MODE, false>;
   constexpr int D = NodeDims<L>::D;
   constexpr int C = 128;
   constexpr int DH = S::dh(W);
   const int c = threadIdx.x & 127;
-  auto flush = [&](int i) {
-    float* cb = comb + par * G::NOUT * 128;
-    if (W != 0) {
+  float hn[2][DH];
 #pragma unroll
-      for (int q = 0; q < G::NOUT; ++q) cb[q * 128 + c] = acc[q];
-    }
-    ws_barrier();
-    if (W == 0) {
+  for (int j = 0; j < 2; ++j) {
+    const int sj = s_send[j];
 #pragma unroll
-      for (int q = 0; q < G::NOUT; ++q) m[((size_t)i * D + G::comp0 + q) * C + c] = s * (acc[q] + cb[q * 128 + c]);
-    }
-#pragma unroll
-    for (int q = 0; q < G::NOUT; ++q) acc[q] = 0.0f;
-    par ^= 1;
-  };
+    for (int d = 0; d < DH; ++d) hn[j][d] = h[((size_t)sj * D + d) * C + c];
+  }
 #pragma unroll 1
-  for (int ch = 0; ch < kNT / 8; ++ch) {
-    float wv[G::NP][8];
+  for (int ch = 0; ch < kNT / 2; ++ch) {
+    float wv2[G::NP][2];
     static_for<0, G::NP>([&](auto sc) {
       constexpr int sl = decltype(sc)::value;
-      if constexpr (S::ws[sl] == W) tc::tmem_ld8(taddr0 + sl * kNT + ch * 8, wv[sl]);
+      if constexpr (S::ws[sl] == W) tmem_ld2(taddr0 + sl * kNT + ch * 2, wv2[sl]);
     });
     tc::tmem_ld_wait();
-    float hn[DH];
-    {
-      const int sj = s_send[ch * 8];
+    float hc[2][DH];
 #pragma unroll
-      for (int d = 0; d < DH; ++d) hn[d] = h[((size_t)sj * D + d) * C + c];
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int d = 0; d < DH; ++d) hc[j][d] = hn[j][d];
+    if (ch + 1 < kNT / 2) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int sj = s_send[2 * ch + 2 + j];
+#pragma unroll
+        for (int d = 0; d < DH; ++d) hn[j][d] = h[((size_t)sj * D + d) * C + c];
+      }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int t = ch * 8 + j;
-      float hj[DH];
-#pragma unroll
-      for (int d = 0; d < DH; ++d) hj[d] = hn[d];
-      if (j < 7) {
-        const int sj = s_send[t + 1];
-#pragma unroll
-        for (int d = 0; d < DH; ++d) hn[d] = h[((size_t)sj * D + d) * C + c];
-      }
+    for (int j = 0; j < 2; ++j) {
+      const int t = 2 * ch + j;
       const int r = s_recv[t];
       if (r < 0) continue;
-      while (cur < r) { flush(cur); ++cur; }
-      fwd_edge<L, MODE, W>(wv, j, hj, cY + t * G::NZP, acc);
+      while (cur < r) {
+#pragma unroll
+        for (int q = 0; q < G::NOUT; ++q) {
+          mW[((size_t)cur * D + G::comp0 + q) * C + c] = s * acc[q];
+          acc[q] = 0.0f;
+        }
+        ++cur;
+      }
+      float wv[G::NP];
+#pragma unroll
+      for (int sl = 0; sl < G::NP; ++sl) wv[sl] = wv2[sl][j];
+      fwd_edge<L, MODE, W>(wv, hc[j], cY + t * G::NZP, acc);
     }
   }
-  (void)tile;
 }
 
 template <int L, int MODE>
 __global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restrict__ row_ptr,
                                                      const int* __restrict__ recv, const int* __restrict__ send,
-                                                     const float4* __restrict__ ev, const float* __restrict__ h,
+                                                     const float* __restrict__ Yg, const float* __restrict__ h,
                                                      const uint8_t* __restrict__ w3img,
-                                                     const uint8_t* __restrict__ z2t, float s, float* __restrict__ m,
-                                                     int use_bf16, int* __restrict__ err) {
+                                                     const uint8_t* __restrict__ z2t, float s, float* __restrict__ mA,
+                                                     float* __restrict__ mB, int use_bf16, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using FL = FwdLayout<L, MODE>;
-  using Tab = CGTable<L>;
   constexpr int D = NodeDims<L>::D;
   constexpr int C = 128;
   constexpr int NP = G::NP;
@@ -307,9 +389,11 @@ __global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restric
   uint8_t* sW3 = smem;
   uint8_t* sZ2 = smem + FL::off_z2;
   float* cY = reinterpret_cast<float*>(smem + FL::off_cy);
+  float* sY = reinterpret_cast<float*>(smem + FL::off_y);
+  float* tab_c = reinterpret_cast<float*>(smem + FL::off_tab);
+  uint8_t* tab_y = smem + FL::off_taby;
   int* s_send = reinterpret_cast<int*>(smem + FL::off_idx);
   int* s_recv = s_send + kNT;
-  float* comb = reinterpret_cast<float*>(smem + FL::off_comb);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + FL::off_bar);
   uint64_t* bar_w3 = bars;
   uint64_t* bar_z2 = bars + 1;  // [2]
@@ -318,6 +402,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restric
   __shared__ int abort_s;
 
   const int tid = threadIdx.x, warp = tid >> 5, c = tid & 127, wsid = warp >> 2;
+  float* mW = wsid == 0 ? mA : mB;
   if (warp == 0) {
     tc::tmem_alloc(tmem_holder, G::NCOLS);
     tc::tmem_relinquish();
@@ -330,6 +415,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restric
     tc::fence_mbar_init();
     abort_s = 0;
   }
+  load_group_table<L, MODE, false>(tab_c, tab_y);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -358,37 +444,13 @@ __global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restric
   float acc[G::NOUT];
 #pragma unroll
   for (int q = 0; q < G::NOUT; ++q) acc[q] = 0.0f;
-  int cur = i0, par = 0;
+  int cur = i0;
   const uint32_t idesc = tc::idesc_16bit(128, kNT, use_bf16 != 0);
 
 #pragma unroll 1
   for (int it = 0; it < n_tiles; ++it) {
     const int tile = t_begin + it;
     const int buf = it & 1;
-    if (tid < kNT) {
-      const int e = tile * kNT + tid;
-      const bool valid = e >= E0 && e < E1;
-      s_recv[tid] = valid ? recv[e] : -1;
-      s_send[tid] = valid ? send[e] : 0;
-      float* dst = cY + tid * G::NZP;
-      if (valid) {
-        const float4 v = ev[e];
-        const float ir = 1.0f / v.w;
-        float Y[16];
-        sh3<float>(v.x * ir, v.y * ir, v.z * ir, Y);
-        static_for<0, NP>([&](auto sc) {
-          constexpr int sl = decltype(sc)::value;
-          constexpr int p = G::paths[sl];
-          constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
-          static_for<kb, ke>([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            constexpr float cv = Tab::ec[k];
-            constexpr int i2 = Tab::e2[k];
-            dst[gb + k - kb] = cv * Y[i2];
-          });
-        });
-      }
-    }
     if (tid == 0) {
       bool ok = true;
       if (it + 1 < n_tiles) {
@@ -417,6 +479,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restric
         abort_s = 1;
       }
     }
+    tile_setup<G::NZ, G::NZP>(tile, E0, E1, recv, send, Yg, s_recv, s_send, sY, cY, tab_c, tab_y);
     __syncthreads();
     if (abort_s) break;
     if (!tc::mbar_wait(bar_mma, (uint32_t)(it & 1))) {
@@ -424,29 +487,19 @@ __global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restric
       abort_s = 1;
     }
     tc::fence_after_sync();
-    if (wsid == 0) fwd_tile_ws<L, MODE, 0>(tile, s_send, s_recv, cY, taddr0, h, cur, acc, comb, par, m, s);
-    else fwd_tile_ws<L, MODE, 1>(tile, s_send, s_recv, cY, taddr0, h, cur, acc, comb, par, m, s);
+    if (wsid == 0) fwd_tile_ws<L, MODE, 0>(s_send, s_recv, cY, taddr0, h, cur, acc, mW, s);
+    else fwd_tile_ws<L, MODE, 1>(s_send, s_recv, cY, taddr0, h, cur, acc, mW, s);
     tc::fence_before_sync();
     __syncthreads();
     if (abort_s) break;
   }
   if (!abort_s) {
-    // receivers after the last edge (zero degree) and the last open segment
     while (cur < i1) {
-      float* cb = comb + par * G::NOUT * 128;
-      if (wsid != 0) {
 #pragma unroll
-        for (int q = 0; q < G::NOUT; ++q) cb[q * 128 + c] = acc[q];
+      for (int q = 0; q < G::NOUT; ++q) {
+        mW[((size_t)cur * D + G::comp0 + q) * C + c] = s * acc[q];
+        acc[q] = 0.0f;
       }
-      ws_barrier();
-      if (wsid == 0) {
-#pragma unroll
-        for (int q = 0; q < G::NOUT; ++q)
-          m[((size_t)cur * D + G::comp0 + q) * C + c] = s * (acc[q] + cb[q * 128 + c]);
-      }
-#pragma unroll
-      for (int q = 0; q < G::NOUT; ++q) acc[q] = 0.0f;
-      par ^= 1;
       ++cur;
     }
   }
@@ -475,7 +528,8 @@ __global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restric
 // read M-major from the same resident W3 image (rows 64..127 of that M = 128
 // product are unused), accumulated into dz2[e][k].  Group kernels of one layer
 // run one after another on the stream, so G^{t-1}, dY and dz2 are updated
-// with plain read-modify-writes (the first group writes G^{t-1} = G^t + ...).
+// with plain read-modify-writes; G^{t-1} is kept as two buffers (one per warp
+// set), the first group initialising them from G^t.
 constexpr bool kMnLboIsK = true;  // descriptor assignment checked by mlip_selftest(2 / 3)
 
 template <int L, int MODE>
@@ -485,6 +539,7 @@ struct BwdLayout {
   static constexpr bool FIRST = MODE < 0;
   static constexpr int D = NodeDims<L>::D;
   static constexpr int B2_BYTES = kNT * NP * 128 * 2;
+  static constexpr int NZ = FIRST ? 0 : G::NZ;
   static constexpr int NZP = FIRST ? 4 : G::NZP;
   static constexpr int tmem_cols() {
     int need = (NP + 1) * kNT, c = 32;
@@ -497,17 +552,18 @@ struct BwdLayout {
   static constexpr size_t off_cy = off_b2 + B2_BYTES;
   static constexpr size_t off_y = off_cy + (size_t)kNT * NZP * 4;
   static constexpr size_t off_red = off_y + kNT * 16 * 4;
-  static constexpr size_t off_idx = off_red + (size_t)(4 * kWS) * kNT * 16 * 4;
-  static constexpr size_t off_comb = off_idx + 2 * kNT * 4;
-  static constexpr size_t off_bar = off_comb + (FIRST ? 0 : (size_t)D * 128 * 4);
+  static constexpr size_t off_tab = off_red + (size_t)(4 * kWS) * kNT * 16 * 4;
+  static constexpr size_t off_taby = off_tab + (size_t)NZP * 4;
+  static constexpr size_t off_idx = off_taby + (((size_t)NZP + 15) & ~(size_t)15);
+  static constexpr size_t off_bar = off_idx + 2 * kNT * 4;
   static constexpr size_t bytes = off_bar + 64;
   static_assert(bytes <= 232448 - 1024, "shared memory of the adjoint kernel exceeds the per-block limit");
 };
 
 template <int L, int MODE, int W>
-__device__ __forceinline__ void bwd_edge(const float (&wv)[Group<L, MODE>::NP][8], int j, int t, const float* hi,
-                                         const float* Gi, const float* Gt, const float* Y, const float* cy, float s,
-                                         float dw_scale, int use_bf16, uint8_t* sB2, float* Gacc, float* dYp) {
+__device__ __forceinline__ void bwd_edge(const float* wv, int t, const float* hi, const float* Gi, const float* Gt,
+                                         const float* Y, const float* cy, float s, float dw_scale, int use_bf16,
+                                         uint8_t* sB2, float* Gacc, float* dYp) {
   using G = Group<L, MODE>;
   using S = Split<L, MODE, true>;
   using Tab = CGTable<L>;
@@ -520,7 +576,7 @@ __device__ __forceinline__ void bwd_edge(const float (&wv)[Group<L, MODE>::NP][8
       constexpr int p = G::paths[sl];
       constexpr int l2 = Tab::l2[p], l3 = Tab::l3[p];
       constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
-      const float wp = wv[sl][j];
+      const float wp = wv[sl];
       if constexpr (!FIRST) {
         float wg[2 * l3 + 1];
 #pragma unroll
@@ -556,10 +612,10 @@ __device__ __forceinline__ void bwd_edge(const float (&wv)[Group<L, MODE>::NP][8
 template <int L, int MODE, int W>
 __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, const int* s_recv, const float* sY,
                                             const float* cY, uint32_t taddr0, const float* __restrict__ hprev,
-                                            const float* __restrict__ Gm, const float* __restrict__ Gin,
-                                            float* __restrict__ Gout, int first_group, int& cur, float* Gacc,
-                                            float* Gt, float* comb, int& par, float* red, uint8_t* sB2, float s,
-                                            float dw_scale, int use_bf16) {
+                                            const float* __restrict__ Gm, const float* __restrict__ GinA,
+                                            const float* __restrict__ GinB, float* __restrict__ GoutW,
+                                            int first_group, int& cur, float* Gacc, float* Gt, float* red,
+                                            uint8_t* sB2, float s, float dw_scale, int use_bf16) {
   using G = Group<L, MODE>;
   using S = Split<L, MODE, true>;
   using BL = BwdLayout<L, MODE>;
@@ -567,25 +623,19 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
   constexpr int C = 128;
   constexpr bool FIRST = MODE < 0;
   constexpr int DH = S::dh(W);
+  constexpr int NG = FIRST ? 1 : G::NOUT;
   constexpr int SBO2 = G::NP * 2048;
   const int c = threadIdx.x & 127, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   auto flush = [&](int i) {
     if constexpr (!FIRST) {
-      float* cb = comb;  // single buffer: written, barrier, read, barrier
-      if (W != 0) {
 #pragma unroll
-        for (int d = 0; d < D; ++d) cb[d * 128 + c] = Gacc[d];
+      for (int d = 0; d < D; ++d) {
+        const size_t o = ((size_t)i * D + d) * C + c;
+        float base;
+        if (W == 0) base = first_group ? GinA[o] + GinB[o] : GoutW[o];
+        else base = first_group ? 0.0f : GoutW[o];
+        GoutW[o] = base + Gacc[d];
       }
-      ws_barrier();
-      if (W == 0) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const size_t o = ((size_t)i * D + d) * C + c;
-          Gout[o] = (first_group ? Gin[o] : Gout[o]) + Gacc[d] + cb[d * 128 + c];
-        }
-      }
-      ws_barrier();
-      par ^= 1;
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
@@ -601,43 +651,48 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
       if (cur < i1) enter(cur);
     }
   };
+  float hn[2][DH], gn[2][NG];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int si = s_send[j];
+#pragma unroll
+    for (int d = 0; d < DH; ++d) hn[j][d] = hprev[((size_t)si * D + d) * C + c];
+    if constexpr (!FIRST) {
+#pragma unroll
+      for (int q = 0; q < NG; ++q) gn[j][q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
+    }
+  }
 #pragma unroll 1
-  for (int ch = 0; ch < kNT / 8; ++ch) {
-    float wv[G::NP][8];
+  for (int ch = 0; ch < kNT / 2; ++ch) {
+    float wv2[G::NP][2];
     static_for<0, G::NP>([&](auto sc) {
       constexpr int sl = decltype(sc)::value;
-      if constexpr (S::ws[sl] == W) tc::tmem_ld8(taddr0 + sl * kNT + ch * 8, wv[sl]);
+      if constexpr (S::ws[sl] == W) tmem_ld2(taddr0 + sl * kNT + ch * 2, wv2[sl]);
     });
     tc::tmem_ld_wait();
-    float hn[DH], gn[FIRST ? 1 : G::NOUT];
-    {
-      const int si = s_send[ch * 8];
+    float hc[2][DH], gc[2][NG];
 #pragma unroll
-      for (int d = 0; d < DH; ++d) hn[d] = hprev[((size_t)si * D + d) * C + c];
-      if constexpr (!FIRST) {
+    for (int j = 0; j < 2; ++j) {
 #pragma unroll
-        for (int q = 0; q < G::NOUT; ++q) gn[q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
+      for (int d = 0; d < DH; ++d) hc[j][d] = hn[j][d];
+#pragma unroll
+      for (int q = 0; q < NG; ++q) gc[j][q] = FIRST ? 0.0f : gn[j][q];
+    }
+    if (ch + 1 < kNT / 2) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int si = s_send[2 * ch + 2 + j];
+#pragma unroll
+        for (int d = 0; d < DH; ++d) hn[j][d] = hprev[((size_t)si * D + d) * C + c];
+        if constexpr (!FIRST) {
+#pragma unroll
+          for (int q = 0; q < NG; ++q) gn[j][q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
+        }
       }
     }
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int t = ch * 8 + j;
-      float hi[DH], Gi[FIRST ? 1 : G::NOUT];
-#pragma unroll
-      for (int d = 0; d < DH; ++d) hi[d] = hn[d];
-      if constexpr (!FIRST) {
-#pragma unroll
-        for (int q = 0; q < G::NOUT; ++q) Gi[q] = gn[q];
-      }
-      if (j < 7) {
-        const int si = s_send[t + 1];
-#pragma unroll
-        for (int d = 0; d < DH; ++d) hn[d] = hprev[((size_t)si * D + d) * C + c];
-        if constexpr (!FIRST) {
-#pragma unroll
-          for (int q = 0; q < G::NOUT; ++q) gn[q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
-        }
-      }
+    for (int j = 0; j < 2; ++j) {
+      const int t = 2 * ch + j;
       const int r = s_recv[t];
       float dYp[16];
 #pragma unroll
@@ -647,7 +702,10 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
         float Y[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
-        bwd_edge<L, MODE, W>(wv, j, t, hi, Gi, Gt, Y, cY + t * BL::NZP, s, dw_scale, use_bf16, sB2, Gacc, dYp);
+        float wv[G::NP];
+#pragma unroll
+        for (int sl = 0; sl < G::NP; ++sl) wv[sl] = wv2[sl][j];
+        bwd_edge<L, MODE, W>(wv, t, hc[j], gc[j], Gt, Y, cY + t * BL::NZP, s, dw_scale, use_bf16, sB2, Gacc, dYp);
       } else {
         static_for<0, G::NP>([&](auto sc) {
           constexpr int sl = decltype(sc)::value;
@@ -666,22 +724,21 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
 template <int L, int MODE>
 __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __restrict__ row_ptr,
                                                          const int* __restrict__ recv, const int* __restrict__ send,
-                                                         const float4* __restrict__ ev,
+                                                         const float* __restrict__ Yg,
                                                          const float* __restrict__ hprev,
                                                          const float* __restrict__ Gm,
                                                          const uint8_t* __restrict__ w3img,
                                                          const uint8_t* __restrict__ z2t, float s,
-                                                         const float* __restrict__ Gin, float* __restrict__ Gout,
+                                                         const float* __restrict__ GinA, const float* __restrict__ GinB,
+                                                         float* __restrict__ GoutA, float* __restrict__ GoutB,
                                                          int first_group, float* __restrict__ dY,
                                                          float* __restrict__ dz2, int use_bf16,
                                                          const float* __restrict__ absmax, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using BL = BwdLayout<L, MODE>;
-  using Tab = CGTable<L>;
   constexpr int D = NodeDims<L>::D;
   constexpr int NP = G::NP;
   constexpr bool FIRST = BL::FIRST;
-  constexpr int NZP = BL::NZP;
   constexpr int SBO2 = NP * 2048;  // B' operand: K' = NP * 128 channels
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sW3 = smem;
@@ -690,9 +747,10 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
   float* cY = reinterpret_cast<float*>(smem + BL::off_cy);
   float* sY = reinterpret_cast<float*>(smem + BL::off_y);
   float* red = reinterpret_cast<float*>(smem + BL::off_red);  // [4 kWS][kNT][16]
+  float* tab_c = reinterpret_cast<float*>(smem + BL::off_tab);
+  uint8_t* tab_y = smem + BL::off_taby;
   int* s_send = reinterpret_cast<int*>(smem + BL::off_idx);
   int* s_recv = s_send + kNT;
-  float* comb = reinterpret_cast<float*>(smem + BL::off_comb);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BL::off_bar);
   uint64_t* bar_w3 = bars;
   uint64_t* bar_z2 = bars + 1;  // [2]
@@ -701,7 +759,8 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 5);
   __shared__ int abort_s;
 
-  const int tid = threadIdx.x, warp = tid >> 5, wsid = warp >> 2;
+  const int tid = threadIdx.x, warp = tid >> 5, wsid = warp >> 2, c = tid & 127;
+  float* GoutW = wsid == 0 ? GoutA : GoutB;
   if (warp == 0) {
     tc::tmem_alloc(tmem_holder, BL::NCOLS);
     tc::tmem_relinquish();
@@ -715,6 +774,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
     tc::fence_mbar_init();
     abort_s = 0;
   }
+  if constexpr (!FIRST) load_group_table<L, MODE, true>(tab_c, tab_y);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -746,7 +806,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
   for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
 #pragma unroll
   for (int q = 0; q < G::NOUT; ++q) Gt[q] = 0.0f;
-  int cur = i0 - 1, par = 0;
+  int cur = i0 - 1;
   const uint32_t idesc1 = tc::idesc_16bit(128, kNT, use_bf16 != 0);
   const uint32_t idesc2 = idesc1 | (1u << 15);  // A M-major
   // dE/dw enters the second product scaled by a power of two (FP16 operands):
@@ -763,34 +823,6 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
   for (int it = 0; it < n_tiles; ++it) {
     const int tile = t_begin + it;
     const int buf = it & 1;
-    if (tid < kNT) {
-      const int e = tile * kNT + tid;
-      const bool valid = e >= E0 && e < E1;
-      s_recv[tid] = valid ? recv[e] : -1;
-      s_send[tid] = valid ? send[e] : 0;
-      if (valid) {
-        const float4 v = ev[e];
-        const float ir = 1.0f / v.w;
-        float Y[16];
-        sh3<float>(v.x * ir, v.y * ir, v.z * ir, Y);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) sY[tid * 16 + k] = Y[k];
-        if constexpr (!FIRST) {
-          float* dst = cY + tid * NZP;
-          static_for<0, NP>([&](auto sc) {
-            constexpr int sl = decltype(sc)::value;
-            constexpr int p = G::paths[sl];
-            constexpr int kb = Tab::off[p], ke = Tab::off[p + 1], gb = G::eoff[sl];
-            static_for<kb, ke>([&](auto kc) {
-              constexpr int k = decltype(kc)::value;
-              constexpr float cv = ((Tab::l2[p] & 1) ? -1.0f : 1.0f) * Tab::ec[k];
-              constexpr int i2 = Tab::e2[k];
-              dst[gb + k - kb] = cv * Y[i2];
-            });
-          });
-        }
-      }
-    }
     if (tid == 0) {
       bool ok = true;
       if (it + 1 < n_tiles) {
@@ -819,6 +851,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
         abort_s = 1;
       }
     }
+    tile_setup<BL::NZ, BL::NZP>(tile, E0, E1, recv, send, Yg, s_recv, s_send, sY, cY, tab_c, tab_y);
     __syncthreads();
     if (abort_s) break;
     if (!tc::mbar_wait(bar_mma, (uint32_t)(it & 1))) {
@@ -827,11 +860,11 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
     }
     tc::fence_after_sync();
     if (wsid == 0)
-      bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, Gin, Gout, first_group, cur, Gacc,
-                              Gt, comb, par, red, sB2, s, dw_scale, use_bf16);
+      bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
+                              cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
     else
-      bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, Gin, Gout, first_group, cur, Gacc,
-                              Gt, comb, par, red, sB2, s, dw_scale, use_bf16);
+      bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
+                              cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
     // second product: dE/dz2 = W3 dE/dw over this tile
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
@@ -885,30 +918,20 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
     if (abort_s) break;
   }
   if (!abort_s) {
-    // remaining receivers of the range (uniform across warp sets)
-    const int c = tid & 127;
+    // remaining receivers of the range
     while (cur < i1) {
-      if (cur >= i0) {
-        if constexpr (!FIRST) {
-          float* cb = comb;
-          if (wsid != 0) {
+      if (cur >= i0 && !FIRST) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) cb[d * 128 + c] = Gacc[d];
-          }
-          ws_barrier();
-          if (wsid == 0) {
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-              const size_t o = ((size_t)cur * D + d) * 128 + c;
-              Gout[o] = (first_group ? Gin[o] : Gout[o]) + Gacc[d] + cb[d * 128 + c];
-            }
-          }
-          ws_barrier();
-          par ^= 1;
+        for (int d = 0; d < D; ++d) {
+          const size_t o = ((size_t)cur * D + d) * 128 + c;
+          float base;
+          if (wsid == 0) base = first_group ? GinA[o] + GinB[o] : GoutW[o];
+          else base = first_group ? 0.0f : GoutW[o];
+          GoutW[o] = base + Gacc[d];
         }
-#pragma unroll
-        for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
       }
+#pragma unroll
+      for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
       ++cur;
     }
   }
@@ -1054,31 +1077,33 @@ __global__ void umma_selftest_mn(const float* __restrict__ W, const float* __res
 }
 
 template <int L, int MODE>
-int launch_group(int n, const int* row_ptr, const int* recv, const int* send, const float4* ev, const float* h,
-                 const uint8_t* w3img, const uint8_t* z2t, float s, float* m, int use_bf16, int* err, int blocks,
-                 cudaStream_t st) {
+int launch_group(int n, const int* row_ptr, const int* recv, const int* send, const float* Yg, const float* h,
+                 const uint8_t* w3img, const uint8_t* z2t, float s, float* mA, float* mB, int use_bf16, int* err,
+                 int blocks, cudaStream_t st) {
   const size_t smem = FwdLayout<L, MODE>::bytes;
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     MLIP_PROF("tp_fused", st);
-    tp_fused<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, ev, h, w3img, z2t, s, m, use_bf16, err);
+    tp_fused<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, h, w3img, z2t, s, mA, mB, use_bf16,
+                                                      err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
 template <int L, int MODE>
-int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send, const float4* ev,
+int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send, const float* Yg,
                      const float* hprev, const float* Gm, const uint8_t* w3img, const uint8_t* z2t, float s,
-                     const float* Gin, float* Gout, int first_group, float* dY, float* dz2, int use_bf16,
-                     const float* absmax, int* err, int blocks, cudaStream_t st) {
+                     const float* GinA, const float* GinB, float* GoutA, float* GoutB, int first_group, float* dY,
+                     float* dz2, int use_bf16, const float* absmax, int* err, int blocks, cudaStream_t st) {
   using BL = BwdLayout<L, MODE>;
   const size_t smem = BL::bytes;
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused_bwd<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     MLIP_PROF("tp_fused_bwd", st);
-    tp_fused_bwd<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, ev, hprev, Gm, w3img, z2t, s, Gin,
-                                                    Gout, first_group, dY, dz2, use_bf16, absmax, err);
+    tp_fused_bwd<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img, z2t, s, GinA,
+                                                          GinB, GoutA, GoutB, first_group, dY, dz2, use_bf16, absmax,
+                                                          err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
@@ -1138,17 +1163,19 @@ int launch_radial_tiles(int H, int E, int n_tiles, const float4* ev, const float
   return MLIP_OK;
 }
 
-// Forward message pass of one layer with the fused kernels (m written for all components).
+// Forward message pass of one layer with the fused kernels: m = mA + mB (one
+// buffer per warp set), every component written.
 int launch_tp_fused(int L, bool first, int n, const int* row_ptr, const int* recv, const int* send,
-                    const float4* ev, const float* h, const uint8_t* w3img, const std::vector<size_t>& goff,
-                    const uint8_t* z2t, float s, float* m, int use_bf16, int* err, cudaStream_t st) {
+                    const float* Yg, const float* h, const uint8_t* w3img, const std::vector<size_t>& goff,
+                    const uint8_t* z2t, float s, float* mA, float* mB, int use_bf16, int* err, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = std::max(1, std::min(n, 2 * sms));
 #define MLIP_G(LL, MM, GI) \
-  MLIP_TRY((launch_group<LL, MM>(n, row_ptr, recv, send, ev, h, w3img + goff[GI], z2t, s, m, use_bf16, err, blocks, st)))
+  MLIP_TRY((launch_group<LL, MM>(n, row_ptr, recv, send, Yg, h, w3img + goff[GI], z2t, s, mA, mB, use_bf16, err, \
+                                 blocks, st)))
   if (L == 2) {
     if (first) { MLIP_G(2, -1, 0); }
     else { MLIP_G(2, 0, 0); MLIP_G(2, 1, 1); MLIP_G(2, 2, 2); }
@@ -1163,19 +1190,21 @@ int launch_tp_fused(int L, bool first, int n, const int* row_ptr, const int* rec
   return MLIP_OK;
 }
 
-// Adjoint message pass of one layer with the fused kernels (all groups in order).
+// Adjoint message pass of one layer with the fused kernels (all groups in
+// order); G^{t-1} = GoutA + GoutB.
 int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int* recv, const int* send,
-                        const float4* ev, const float* hprev, const float* Gm, const uint8_t* w3img,
-                        const std::vector<size_t>& goff, const uint8_t* z2t, float s, const float* Gin, float* Gout,
-                        float* dY, float* dz2, int use_bf16, const float* absmax, int* err, cudaStream_t st) {
+                        const float* Yg, const float* hprev, const float* Gm, const uint8_t* w3img,
+                        const std::vector<size_t>& goff, const uint8_t* z2t, float s, const float* GinA,
+                        const float* GinB, float* GoutA, float* GoutB, float* dY, float* dz2, int use_bf16,
+                        const float* absmax, int* err, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = std::max(1, std::min(n, sms));
-#define MLIP_GB(LL, MM, GI) \
-  MLIP_TRY((launch_group_bwd<LL, MM>(n, row_ptr, recv, send, ev, hprev, Gm, w3img + goff[GI], z2t, s, Gin, Gout, \
-                                     GI == 0, dY, dz2, use_bf16, absmax, err, blocks, st)))
+#define MLIP_GB(LL, MM, GI)                                                                                  \
+  MLIP_TRY((launch_group_bwd<LL, MM>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img + goff[GI], z2t, s, GinA, GinB, \
+                                     GoutA, GoutB, GI == 0, dY, dz2, use_bf16, absmax, err, blocks, st)))
   if (L == 2) {
     if (first) { MLIP_GB(2, -1, 0); }
     else { MLIP_GB(2, 0, 0); MLIP_GB(2, 1, 1); MLIP_GB(2, 2, 2); }
@@ -1288,10 +1317,13 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
   ca.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
   for (int k = 0; k < 9; ++k) ca.h[k] = ca.any_pbc ? cell[k] : 0.0;
   float4 *ev = nullptr, *g = nullptr;
-  float *m = nullptr, *Gm = nullptr, *Ga = nullptr, *Gb = nullptr, *dY = nullptr, *dr = nullptr, *dz2 = nullptr;
+  float *mA = nullptr, *mB = nullptr, *Yg = nullptr, *Gm = nullptr, *dY = nullptr, *dr = nullptr, *dz2 = nullptr;
+  float *GaA = nullptr, *GaB = nullptr, *GbA = nullptr, *GbB = nullptr;
   double* atom_e = nullptr;
   MLIP_TRY(ws.get("ef.ev", Ec, &ev));
-  MLIP_TRY(ws.get("ef.m", ND, &m));
+  MLIP_TRY(ws.get("fz.Y", Ec * 16, &Yg));
+  MLIP_TRY(ws.get("ef.m", ND, &mA));
+  MLIP_TRY(ws.get("fz.m2", ND, &mB));
   MLIP_TRY(ws.get("ef.atom_e", (size_t)std::max(n, 1), &atom_e));
   std::vector<float*> h(T + 1), u0(T);
   std::vector<uint8_t*> z2t(T);
@@ -1301,30 +1333,38 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
     MLIP_TRY(ws.get("fz.z2t" + std::to_string(t), (size_t)std::max(n_tiles, 1) * kTileBytes, &z2t[t]));
   }
   MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st));
+  if (E > 0) {
+    MLIP_PROF("edge_sh", st);
+    edge_sh<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, Yg);
+    MLIP_LAUNCH_CHECK();
+  }
   MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
   for (int t = 0; t < T; ++t) {
     MLIP_TRY(launch_radial_tiles(H, E, n_tiles, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, use_bf16, z2t[t], st));
-    MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, ev, h[t], M->d_w3img + M->w3_layer_off[t],
-                             M->w3_goff[t], z2t[t], s, m, use_bf16, flag + 1, st));
-    MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
+    MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], M->d_w3img + M->w3_layer_off[t],
+                             M->w3_goff[t], z2t[t], s, mA, mB, use_bf16, flag + 1, st));
+    MLIP_TRY(launch_mix_fwd2(n, C, L, mA, mB, M->Wmix[t], h[t], h[t + 1], u0[t], st));
   }
   MLIP_TRY(launch_energy(n, C, D, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
   if (d_forces || d_stress) {
     MLIP_TRY(ws.get("ef.g", Ec, &g));
     MLIP_TRY(ws.get("ef.Gm", ND, &Gm));
-    MLIP_TRY(ws.get("ef.Ga", ND, &Ga));
-    MLIP_TRY(ws.get("ef.Gb", ND, &Gb));
+    MLIP_TRY(ws.get("ef.Ga", ND, &GaA));
+    MLIP_TRY(ws.get("fz.Ga2", ND, &GaB));
+    MLIP_TRY(ws.get("ef.Gb", ND, &GbA));
+    MLIP_TRY(ws.get("fz.Gb2", ND, &GbB));
     MLIP_TRY(ws.get("ef.dY", Ec * 16, &dY));
     MLIP_TRY(ws.get("ef.dr", Ec, &dr));
     MLIP_TRY(ws.get("fz.dz2", Ec * 64, &dz2));
-    MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, Ga, st));
+    MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, GaA, st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(GaB, 0, ND * sizeof(float), st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dr, 0, Ec * sizeof(float), st));
     float* absmax = nullptr;
     MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)T, &absmax));
     MLIP_CUDA_TRY(cudaMemsetAsync(absmax, 0, 2 * T * sizeof(float), st));
     for (int t = T - 1; t >= 0; --t) {
-      MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], Gm, st));
+      MLIP_TRY(launch_mix_bwd2(n, C, L, GaA, GaB, u0[t], M->Wmix[t], Gm, st));
       MLIP_CUDA_TRY(cudaMemsetAsync(dz2, 0, Ec * 64 * sizeof(float), st));
       if (!use_bf16) {
         MLIP_PROF("absmax2", st);
@@ -1332,11 +1372,12 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
                                                                                          absmax + 2 * t);
         MLIP_LAUNCH_CHECK();
       }
-      MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, ev, h[t], Gm,
-                                   M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, Ga, Gb, dY, dz2,
-                                   use_bf16, absmax + 2 * t, flag + 1, st));
+      MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], Gm,
+                                   M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, GaA, GaB, GbA, GbB, dY,
+                                   dz2, use_bf16, absmax + 2 * t, flag + 1, st));
       MLIP_TRY(launch_radial_bwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, st));
-      std::swap(Ga, Gb);
+      std::swap(GaA, GbA);
+      std::swap(GaB, GbB);
     }
     MLIP_TRY(launch_edge_grad(E, ev, dY, dr, g, st));
     double* fbuf = d_forces;

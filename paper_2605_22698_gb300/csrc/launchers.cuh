@@ -22,6 +22,10 @@ int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const
                    float* u0, cudaStream_t st);
 int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, float* Gm,
                    cudaStream_t st);
+int launch_mix_fwd2(int n, int C, int L, const float* mA, const float* mB, const float* Wmix, const float* hin,
+                    float* hout, float* u0, cudaStream_t st);
+int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const float* u0, const float* Wmix,
+                    float* Gm, cudaStream_t st);
 int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st);
 int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st);
 int launch_energy(int n, int C, int D, const int* species, const float* W_out, const float* E0, const float* h,

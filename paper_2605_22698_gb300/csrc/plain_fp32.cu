@@ -83,7 +83,7 @@ template <int H>
 __global__ void radial_bwd(int E, const float4* __restrict__ ev, const float* __restrict__ W1,
                            const float* __restrict__ W2, float rc, int p, const float* __restrict__ dz2,
                            float* __restrict__ dr_tot) {
-  __shared__ float sW1[8 * H], sW2[H * H];
+  __shared__ __align__(16) float sW1[8 * H], sW2[H * H];
   for (int k = threadIdx.x; k < 8 * H; k += blockDim.x) sW1[k] = W1[k];
   for (int k = threadIdx.x; k < H * H; k += blockDim.x) sW2[k] = W2[k];
   __syncthreads();
@@ -104,12 +104,22 @@ __global__ void radial_bwd(int E, const float4* __restrict__ ev, const float* __
   }
   float da2[H];
 #pragma unroll
-  for (int q = 0; q < H; ++q) {
-    float a = 0.0f;
+  for (int q = 0; q < H; ++q) da2[q] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < H; ++k) {  // a2 = z1 W2, one 16-byte row load per four FMAs
+    const float zk = z1[k];
+    const float4* w4 = reinterpret_cast<const float4*>(sW2 + k * H);
 #pragma unroll
-    for (int k = 0; k < H; ++k) a = fmaf(z1[k], sW2[k * H + q], a);
-    da2[q] = dz2[(size_t)e * H + q] * silu_grad_f(a);
+    for (int q4 = 0; q4 < H / 4; ++q4) {
+      const float4 w = w4[q4];
+      da2[4 * q4] = fmaf(zk, w.x, da2[4 * q4]);
+      da2[4 * q4 + 1] = fmaf(zk, w.y, da2[4 * q4 + 1]);
+      da2[4 * q4 + 2] = fmaf(zk, w.z, da2[4 * q4 + 2]);
+      da2[4 * q4 + 3] = fmaf(zk, w.w, da2[4 * q4 + 3]);
+    }
   }
+#pragma unroll
+  for (int q = 0; q < H; ++q) da2[q] = dz2[(size_t)e * H + q] * silu_grad_f(da2[q]);
   float dr = 0.0f;
 #pragma unroll 4
   for (int k = 0; k < H; ++k) {
@@ -120,8 +130,15 @@ __global__ void radial_bwd(int E, const float4* __restrict__ ev, const float* __
       bd = fmaf(sW1[n * H + k], db[n], bd);
     }
     float dz1 = 0.0f;
+    const float4* w4 = reinterpret_cast<const float4*>(sW2 + k * H);
 #pragma unroll
-    for (int q = 0; q < H; ++q) dz1 = fmaf(sW2[k * H + q], da2[q], dz1);
+    for (int q4 = 0; q4 < H / 4; ++q4) {
+      const float4 w = w4[q4];
+      dz1 = fmaf(w.x, da2[4 * q4], dz1);
+      dz1 = fmaf(w.y, da2[4 * q4 + 1], dz1);
+      dz1 = fmaf(w.z, da2[4 * q4 + 2], dz1);
+      dz1 = fmaf(w.w, da2[4 * q4 + 3], dz1);
+    }
     dr = fmaf(dz1 * silu_grad_f(a), bd, dr);
   }
   dr_tot[e] += dr;
@@ -438,10 +455,12 @@ __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int*
 // r / (2l+1), component l^2 + r % (2l+1).
 //   forward:  u = m W_l;  h_out = h_in + (l == 0 ? silu(u) : u);  u0 keeps u (l = 0)
 //   backward: Gm = Gu W_l^T,  Gu = G silu'(u0) (l = 0) or G
+// The input is X + X2 when X2 is given (the fused kernels' two partial buffers).
 constexpr int kMixRows = 64;
 template <bool BWD>
 __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __restrict__ X,
-                                                const float* __restrict__ Wmix, const float* __restrict__ hin,
+                                                const float* __restrict__ X2, const float* __restrict__ Wmix,
+                                                const float* __restrict__ hin,
                                                 float* __restrict__ out, float* __restrict__ u0,
                                                 const float* __restrict__ u0_in) {
   constexpr int C = 128;
@@ -463,7 +482,9 @@ __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __res
     float v = 0.0f;
     if (r < rows) {
       const int nd = r / R, mm = r % R;
-      v = X[((size_t)nd * D + l * l + mm) * C + cc];
+      const size_t o = ((size_t)nd * D + l * l + mm) * C + cc;
+      v = X[o];
+      if (X2) v += X2[o];
       if (BWD && l == 0) v *= silu_grad_f(u0_in[(size_t)nd * C + cc]);
     }
     As[cc * kMixRows + rr] = v;
@@ -672,7 +693,7 @@ int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const
     const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
-    { MLIP_PROF("mix_fwd", st); mix_gemm<false><<<grid, 128, smem, st>>>(n, L, m, Wmix, hin, hout, u0, nullptr); }
+    { MLIP_PROF("mix_fwd", st); mix_gemm<false><<<grid, 128, smem, st>>>(n, L, m, nullptr, Wmix, hin, hout, u0, nullptr); }
     MLIP_LAUNCH_CHECK();
     return MLIP_OK;
   }
@@ -691,7 +712,7 @@ int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const f
     const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
-    { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, G, Wmix, nullptr, Gm, nullptr, u0); }
+    { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, G, nullptr, Wmix, nullptr, Gm, nullptr, u0); }
     MLIP_LAUNCH_CHECK();
     return MLIP_OK;
   }
@@ -699,6 +720,30 @@ int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const f
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n + kMixNodes - 1) / kMixNodes, L + 1);
   { MLIP_PROF("mix_bwd", st); mix_bwd<<<grid, std::max(C, 32), smem, st>>>(n, C, L, G, u0, Wmix, Gm); }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+int launch_mix_fwd2(int n, int C, int L, const float* mA, const float* mB, const float* Wmix, const float* hin,
+                    float* hout, float* u0, cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  if (C != 128) { set_error("the fused form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
+  const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
+  MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
+  { MLIP_PROF("mix_fwd", st); mix_gemm<false><<<grid, 128, smem, st>>>(n, L, mA, mB, Wmix, hin, hout, u0, nullptr); }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const float* u0, const float* Wmix,
+                    float* Gm, cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  if (C != 128) { set_error("the fused form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
+  const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
+  MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
+  { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, GA, GB, Wmix, nullptr, Gm, nullptr, u0); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
