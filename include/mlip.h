@@ -130,6 +130,29 @@ int mlip_neighbors(const double* pos, int64_t n, const double cell[9], const uin
                    double cutoff, int32_t* recv, int32_t* send, int8_t* shift, int64_t capacity,
                    int64_t* n_edges, int on_device, void* stream);
 
+/* Allocation-free neighbour list (the paper has no counterpart; it is an
+ * interface for callers that cannot allocate device memory).  Some callers
+ * cannot call cudaMalloc: an application that fixes its device-memory budget
+ * up front and forbids later growth, a latency-critical loop that must not
+ * take the implicit device synchronisation of cudaMalloc/cudaFree, or a
+ * plug-in running inside another framework's memory pool.  This call computes
+ * the same list as mlip_neighbors (same definition, order and bit-identical
+ * output) but allocates nothing: its scratch is one file-scope device array
+ * of 32 MiB, kept by every GPU that loads the library until the process exits.
+ *   pos: DEVICE pointer [n][3]; recv, send: DEVICE int32[capacity]; shift:
+ *   DEVICE int8[capacity * 3]; cell, pbc: host; stream: cudaStream_t or NULL.
+ * Limits: n <= 12288 atoms and at most 256 neighbours per receiver; larger
+ * inputs return MLIP_ERR_INVALID_ARG (atoms) or MLIP_ERR_CAPACITY (degree)
+ * with a message naming the limit.  *n_edges and MLIP_ERR_CAPACITY behave as
+ * in mlip_neighbors.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) for that device; make that first call before
+ * any stream capture.  All calls share the one array: calls that overlap on
+ * the GPU (two streams, two threads) race and must be serialised by the
+ * caller.  The call synchronises the stream (to read the edge count). */
+int mlip_neighbors_noalloc(const double* pos, int64_t n, const double cell[9], const uint8_t pbc[3],
+                           double cutoff, int32_t* recv, int32_t* send, int8_t* shift, int64_t capacity,
+                           int64_t* n_edges, void* stream);
+
 /* Energy, forces and stress of one system.  energy: one double; forces:
  * double[n][3] or NULL; stress: double[9] or NULL (requires pbc all true, else
  * MLIP_ERR_CELL).  The neighbour list is built on the device inside the call.

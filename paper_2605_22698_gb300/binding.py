@@ -64,6 +64,7 @@ def lib():
         L.mlip_model_free.argtypes = [P]
         L.mlip_neighbors.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), i32, P]
         L.mlip_energy_forces.argtypes = [P, P, P, i64, P, P, P, P, P, i32, P]
+        L.mlip_neighbors_noalloc.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), P]
         L.mlip_md_nve.argtypes = [P, P, P, P, i64, P, P, f64, i64, P, P, i32, P]
         L.mlip_selftest.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         L.mlip_profile_enable.argtypes = [i32]
@@ -162,6 +163,18 @@ def mlip_neighbors(pos, cell, pbc, cutoff: float, capacity: int = 0, stream=None
                                 dev, st))
     E = int(ne.value)
     return recv[:E], send[:E], shift[:E]
+
+
+def mlip_neighbors_noalloc(pos, cell, pbc, cutoff: float, recv, send, shift, stream=None) -> int:
+    """Allocation-free neighbour list into caller-provided device tensors
+    (recv/send int32 [cap], shift int8 [cap, 3]); returns the edge count."""
+    cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    pbc = np.ascontiguousarray(pbc, dtype=np.uint8).reshape(3)
+    ne = ctypes.c_int64(0)
+    _check(lib().mlip_neighbors_noalloc(_ptr(pos)[0], int(pos.shape[0]), cell.ctypes.data_as(ctypes.c_void_p),
+                                        pbc.ctypes.data_as(ctypes.c_void_p), cutoff, _ptr(recv)[0], _ptr(send)[0],
+                                        _ptr(shift)[0], int(recv.shape[0]), ctypes.byref(ne), _stream_ptr(stream)))
+    return int(ne.value)
 
 
 def mlip_energy_forces(h, pos, species, cell, pbc, forces: bool = True, stress: bool = False, stream=None,

@@ -18,7 +18,9 @@
 //   nl_sort     one warp per receiver: bitonic sort of its keys in shared
 //               memory, compact write of recv / send / shift
 //   nl_rev      per edge: binary search of (i, -S) in the sender's segment
+#include <climits>
 #include <cmath>
+#include <mutex>
 
 #include "mlip_internal.cuh"
 #include "profile.cuh"
@@ -530,3 +532,222 @@ int build_neighbors(Workspace& ws, const double* d_pos, int64_t n64, const doubl
 }
 
 }  // namespace mlip
+
+// ------------------------------------------------------------------------
+// Allocation-free variant of the neighbour build.
+//
+// Some callers cannot call cudaMalloc: code that runs while its process holds
+// a fixed device-memory budget (a host application that partitions HBM up
+// front and forbids later growth), code on a latency-critical path where the
+// implicit device synchronisation of cudaMalloc/cudaFree is not acceptable,
+// and plug-ins called from inside another framework's memory pool that must
+// not allocate behind the pool's back.  mlip_neighbors_noalloc serves them:
+// every scratch buffer lives in one file-scope __device__ array of fixed size
+// that each GPU loading the library keeps until the process exits, and the
+// caller passes the inputs and outputs in device memory.
+namespace mlip {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB per device
+constexpr int kNoAllocMaxAtoms = 12288;
+constexpr int kNoAllocMaxDegree = 256;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[256] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code only sees a host-side stand-in for the symbol).
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256) {
+    cudaGetLastError();
+    set_error("neighbors (no-alloc): no current CUDA device");
+    return MLIP_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      set_error("neighbors (no-alloc): cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return MLIP_ERR_CUDA;
+    }
+    g_noalloc_base[dev] = p;
+  }
+  *out = g_noalloc_base[dev];
+  return MLIP_OK;
+}
+
+// Bump allocator over the scratch array (256-byte aligned pieces).
+struct Carve {
+  unsigned char* base;
+  size_t off, cap;
+  template <class T>
+  T* take(size_t count) {
+    const size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+    if (off + bytes > cap) return nullptr;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+// nl_sort without the key output (the caller's edge arrays only).
+__global__ void nl_sort_out(int n, int cap, const unsigned long long* __restrict__ slab, int maxdeg,
+                            const int* __restrict__ row_ptr, int* __restrict__ recv, int* __restrict__ send,
+                            int8_t* __restrict__ shift) {
+  extern __shared__ unsigned long long sk[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int i = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (i >= n) return;
+  unsigned long long* s = sk + (size_t)wib * cap;
+  const int beg = row_ptr[i], d = row_ptr[i + 1] - beg;
+  int m = 1;
+  while (m < d) m <<= 1;
+  for (int t = lane; t < m; t += 32) s[t] = t < d ? slab[(size_t)i * maxdeg + t] : ~0ULL;
+  __syncwarp();
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < m; t += 32) {
+        int ixj = t ^ j;
+        if (ixj > t) {
+          unsigned long long a = s[t], b = s[ixj];
+          bool up = (t & k) == 0;
+          if ((a > b) == up) { s[t] = b; s[ixj] = a; }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (int t = lane; t < d; t += 32) {
+    const unsigned long long key = s[t];
+    recv[beg + t] = i;
+    send[beg + t] = (int)(key >> 24);
+    shift[3 * (beg + t) + 0] = (int8_t)((int)((key >> 16) & 0xFF) - 128);
+    shift[3 * (beg + t) + 1] = (int8_t)((int)((key >> 8) & 0xFF) - 128);
+    shift[3 * (beg + t) + 2] = (int8_t)((int)(key & 0xFF) - 128);
+  }
+}
+
+int scan_fixed(const int32_t* in, int32_t* out, int64_t n, int* bsum, cudaStream_t st) {
+  int nb = (int)((n + kScanTile - 1) / kScanTile);
+  if (nb < 1) nb = 1;
+  scan_local<<<nb, kScanThreads, 0, st>>>(in, out, n, bsum);
+  scan_blocks<<<1, 1024, 0, st>>>(bsum, nb, out + n);
+  scan_add<<<nb, kScanThreads, 0, st>>>(out, n, bsum);
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+}  // namespace
+}  // namespace mlip
+
+extern "C" int mlip_neighbors_noalloc(const double* pos, int64_t n64, const double cell[9], const uint8_t pbc[3],
+                                      double cutoff, int32_t* recv, int32_t* send, int8_t* shift, int64_t capacity,
+                                      int64_t* n_edges, void* stream) {
+  using namespace mlip;
+  if (!n_edges || !cell || !pbc || (n64 > 0 && !pos)) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  *n_edges = 0;
+  if (n64 < 0 || n64 > kNoAllocMaxAtoms) {
+    set_error("neighbors (no-alloc): %lld atoms; this entry point handles at most %d (use mlip_neighbors)",
+              (long long)n64, kNoAllocMaxAtoms);
+    return MLIP_ERR_INVALID_ARG;
+  }
+  if (!(cutoff > 0)) { set_error("neighbors (no-alloc): cutoff must be positive"); return MLIP_ERR_INVALID_ARG; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = (int)n64;
+  void* base = nullptr;
+  MLIP_TRY(noalloc_scratch(&base));
+
+  Grid hg{};
+  hg.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
+  if (hg.any_pbc) {
+    double det;
+    if (!invert3(cell, hg.inv, &det)) { set_error("neighbors (no-alloc): singular cell with a periodic axis"); return MLIP_ERR_CELL; }
+    for (int k = 0; k < 9; ++k) hg.h[k] = cell[k];
+    for (int k = 0; k < 3; ++k) {
+      const double c2 = hg.inv[k] * hg.inv[k] + hg.inv[3 + k] * hg.inv[3 + k] + hg.inv[6 + k] * hg.inv[6 + k];
+      hg.w[k] = 1.0 / std::sqrt(c2);
+      hg.pbc[k] = pbc[k] ? 1 : 0;
+    }
+  } else {
+    for (int k = 0; k < 9; ++k) { hg.inv[k] = (k % 4 == 0) ? 1.0 : 0.0; hg.h[k] = 0.0; }
+    for (int k = 0; k < 3; ++k) { hg.w[k] = 1.0; hg.pbc[k] = 0; }
+  }
+  hg.rc = cutoff;
+  hg.rc2 = cutoff * cutoff;
+  hg.max_bins = std::max(64, 4 * n);
+  hg.maxdeg = kNoAllocMaxDegree;
+
+  const size_t nn = (size_t)std::max(n, 1);
+  Carve cv{static_cast<unsigned char*>(base), 0, kNoAllocScratchBytes};
+  Grid* dg = cv.take<Grid>(1);
+  double* frac = cv.take<double>(3 * nn);
+  int* img = cv.take<int>(3 * nn);
+  int* bin_of = cv.take<int>(nn);
+  int* counts = cv.take<int>((size_t)hg.max_bins + 1);
+  int* bin_start = cv.take<int>((size_t)hg.max_bins + 1);
+  int* cursor = cv.take<int>((size_t)hg.max_bins + 1);
+  int* bin_atoms = cv.take<int>(nn);
+  int* deg = cv.take<int>(nn);
+  int* flags = cv.take<int>(4);
+  long long* bbox = cv.take<long long>(6);
+  int* row_ptr = cv.take<int>(nn + 1);
+  int* bsum = cv.take<int>((size_t)std::max<int64_t>(hg.max_bins, nn) / kScanTile + 2);
+  unsigned long long* slab = cv.take<unsigned long long>(nn * kNoAllocMaxDegree);
+  if (!slab) { set_error("neighbors (no-alloc): scratch layout exceeds %zu bytes", kNoAllocScratchBytes); return MLIP_ERR_CAPACITY; }
+
+  // the array keeps the last call's contents: clear what must start at zero
+  const long long bb_init[6] = {LLONG_MAX, LLONG_MIN, LLONG_MAX, LLONG_MIN, LLONG_MAX, LLONG_MIN};
+  MLIP_CUDA_TRY(cudaMemcpyAsync(dg, &hg, sizeof(Grid), cudaMemcpyHostToDevice, st));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(bbox, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, st));
+  MLIP_CUDA_TRY(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+  MLIP_CUDA_TRY(cudaMemsetAsync(counts, 0, ((size_t)hg.max_bins + 1) * sizeof(int), st));
+  MLIP_CUDA_TRY(cudaMemsetAsync(cursor, 0, ((size_t)hg.max_bins + 1) * sizeof(int), st));
+  const int threads = 128, blocks = (n + threads - 1) / threads;
+  if (n > 0) {
+    nl_frac<<<blocks, threads, 0, st>>>(pos, n, dg, frac, img, bbox);
+    nl_setup<<<1, 1, 0, st>>>(dg, bbox);
+    nl_bin<<<blocks, threads, 0, st>>>(n, dg, frac, bin_of, counts);
+  } else {
+    nl_setup<<<1, 1, 0, st>>>(dg, bbox);
+  }
+  MLIP_LAUNCH_CHECK();
+  MLIP_TRY(scan_fixed(counts, bin_start, hg.max_bins, bsum, st));
+  if (n > 0) {
+    nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms);
+    nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, pos, frac, img, bin_start, bin_atoms, slab, deg, flags);
+    MLIP_LAUNCH_CHECK();
+  }
+  MLIP_TRY(scan_fixed(deg, row_ptr, n, bsum, st));
+  int hflags[4] = {0, 0, 0, 0};
+  int E32 = 0;
+  MLIP_CUDA_TRY(cudaMemcpyAsync(hflags, flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(&E32, row_ptr + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hflags[1]) { set_error("neighbors (no-alloc): image index beyond +-127"); return MLIP_ERR_INVALID_ARG; }
+  if (hflags[0] > kNoAllocMaxDegree) {
+    set_error("neighbors (no-alloc): a receiver has %d neighbours (this entry point handles at most %d)", hflags[0],
+              kNoAllocMaxDegree);
+    return MLIP_ERR_CAPACITY;
+  }
+  *n_edges = E32;
+  if (E32 > capacity) {
+    set_error("neighbour capacity %lld < %d edges", (long long)capacity, E32);
+    return MLIP_ERR_CAPACITY;
+  }
+  if (n > 0 && E32 > 0) {
+    if (!recv || !send || !shift) { set_error("null output buffer"); return MLIP_ERR_INVALID_ARG; }
+    const int wpb = 4, cap = kNoAllocMaxDegree;
+    const size_t smem = (size_t)wpb * cap * sizeof(unsigned long long);
+    nl_sort_out<<<(n + wpb - 1) / wpb, 32 * wpb, smem, st>>>(n, cap, slab, kNoAllocMaxDegree, row_ptr, recv, send,
+                                                            shift);
+    MLIP_LAUNCH_CHECK();
+  }
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  return MLIP_OK;
+}
