@@ -266,6 +266,26 @@ __global__ void edge_sh(int E, const float4* __restrict__ ev, float* __restrict_
   }
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(taddr));
+  v[0] = __uint_as_float(r0); v[1] = __uint_as_float(r1); v[2] = __uint_as_float(r2); v[3] = __uint_as_float(r3);
+}
+template <int CH>
+__device__ __forceinline__ void tmem_ldn(uint32_t taddr, float* v);
+template <>
+__device__ __forceinline__ void tmem_ldn<4>(uint32_t taddr, float* v) { tmem_ld4(taddr, v); }
+template <>
+__device__ __forceinline__ void tmem_ldn<8>(uint32_t taddr, float* v) { tc::tmem_ld8(taddr, v); }
+
+// Edges per chunk of the per-warp-set loop: the sender gathers of the next
+// chunk are issued before the current chunk is computed, so light groups
+// (little work per edge) take longer chunks.
+template <int WORK>
+constexpr int chunk_edges() { return WORK <= 8 ? 8 : 4; }
+
 __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
   uint32_t r0, r1;
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr));
@@ -323,38 +343,39 @@ __device__ __forceinline__ void fwd_tile_ws(const int* s_send, const int* s_recv
   constexpr int D = NodeDims<L>::D;
   constexpr int C = 128;
   constexpr int DH = S::dh(W);
+  constexpr int CH = chunk_edges<DH>();
   const int c = threadIdx.x & 127;
-  float hn[2][DH];
+  float hn[CH][DH];
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < CH; ++j) {
     const int sj = s_send[j];
 #pragma unroll
     for (int d = 0; d < DH; ++d) hn[j][d] = h[((size_t)sj * D + d) * C + c];
   }
 #pragma unroll 1
-  for (int ch = 0; ch < kNT / 2; ++ch) {
-    float wv2[G::NP][2];
+  for (int ch = 0; ch < kNT / CH; ++ch) {
+    float wvc[G::NP][CH];
     static_for<0, G::NP>([&](auto sc) {
       constexpr int sl = decltype(sc)::value;
-      if constexpr (S::ws[sl] == W) tmem_ld2(taddr0 + sl * kNT + ch * 2, wv2[sl]);
+      if constexpr (S::ws[sl] == W) tmem_ldn<CH>(taddr0 + sl * kNT + ch * CH, wvc[sl]);
     });
     tc::tmem_ld_wait();
-    float hc[2][DH];
+    float hc[CH][DH];
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+    for (int j = 0; j < CH; ++j)
 #pragma unroll
       for (int d = 0; d < DH; ++d) hc[j][d] = hn[j][d];
-    if (ch + 1 < kNT / 2) {
+    if (ch + 1 < kNT / CH) {
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int sj = s_send[2 * ch + 2 + j];
+      for (int j = 0; j < CH; ++j) {
+        const int sj = s_send[CH * ch + CH + j];
 #pragma unroll
         for (int d = 0; d < DH; ++d) hn[j][d] = h[((size_t)sj * D + d) * C + c];
       }
     }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int t = 2 * ch + j;
+    for (int j = 0; j < CH; ++j) {
+      const int t = CH * ch + j;
       const int r = s_recv[t];
       if (r < 0) continue;
       while (cur < r) {
@@ -367,7 +388,7 @@ __device__ __forceinline__ void fwd_tile_ws(const int* s_send, const int* s_recv
       }
       float wv[G::NP];
 #pragma unroll
-      for (int sl = 0; sl < G::NP; ++sl) wv[sl] = wv2[sl][j];
+      for (int sl = 0; sl < G::NP; ++sl) wv[sl] = wvc[sl][j];
       fwd_edge<L, MODE, W>(wv, hc[j], cY + t * G::NZP, acc);
     }
   }
@@ -651,9 +672,10 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
       if (cur < i1) enter(cur);
     }
   };
-  float hn[2][DH], gn[2][NG];
+  constexpr int CH = chunk_edges<DH + (FIRST ? 0 : NG)>();
+  float hn[CH][DH], gn[CH][NG];
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
+  for (int j = 0; j < CH; ++j) {
     const int si = s_send[j];
 #pragma unroll
     for (int d = 0; d < DH; ++d) hn[j][d] = hprev[((size_t)si * D + d) * C + c];
@@ -663,25 +685,25 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
     }
   }
 #pragma unroll 1
-  for (int ch = 0; ch < kNT / 2; ++ch) {
-    float wv2[G::NP][2];
+  for (int ch = 0; ch < kNT / CH; ++ch) {
+    float wvc[G::NP][CH];
     static_for<0, G::NP>([&](auto sc) {
       constexpr int sl = decltype(sc)::value;
-      if constexpr (S::ws[sl] == W) tmem_ld2(taddr0 + sl * kNT + ch * 2, wv2[sl]);
+      if constexpr (S::ws[sl] == W) tmem_ldn<CH>(taddr0 + sl * kNT + ch * CH, wvc[sl]);
     });
     tc::tmem_ld_wait();
-    float hc[2][DH], gc[2][NG];
+    float hc[CH][DH], gc[CH][NG];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < CH; ++j) {
 #pragma unroll
       for (int d = 0; d < DH; ++d) hc[j][d] = hn[j][d];
 #pragma unroll
       for (int q = 0; q < NG; ++q) gc[j][q] = FIRST ? 0.0f : gn[j][q];
     }
-    if (ch + 1 < kNT / 2) {
+    if (ch + 1 < kNT / CH) {
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int si = s_send[2 * ch + 2 + j];
+      for (int j = 0; j < CH; ++j) {
+        const int si = s_send[CH * ch + CH + j];
 #pragma unroll
         for (int d = 0; d < DH; ++d) hn[j][d] = hprev[((size_t)si * D + d) * C + c];
         if constexpr (!FIRST) {
@@ -691,8 +713,8 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
       }
     }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int t = 2 * ch + j;
+    for (int j = 0; j < CH; ++j) {
+      const int t = CH * ch + j;
       const int r = s_recv[t];
       float dYp[16];
 #pragma unroll
@@ -704,7 +726,7 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
         for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
         float wv[G::NP];
 #pragma unroll
-        for (int sl = 0; sl < G::NP; ++sl) wv[sl] = wv2[sl][j];
+        for (int sl = 0; sl < G::NP; ++sl) wv[sl] = wvc[sl][j];
         bwd_edge<L, MODE, W>(wv, t, hc[j], gc[j], Gt, Y, cY + t * BL::NZP, s, dw_scale, use_bf16, sB2, Gacc, dYp);
       } else {
         static_for<0, G::NP>([&](auto sc) {
@@ -1076,12 +1098,25 @@ __global__ void umma_selftest_mn(const float* __restrict__ W, const float* __res
   if (warp == 0) tc::tmem_dealloc(tbase, 32);
 }
 
+// CTAs of a fused kernel resident per SM: the occupancy limit (registers,
+// shared memory) capped by tensor memory (512 columns per SM) and at 2.
+template <class K>
+int resident_ctas(K kernel, size_t smem, int ncols) {
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  return std::max(1, std::min({occ, 512 / ncols, 2}));
+}
+
 template <int L, int MODE>
 int launch_group(int n, const int* row_ptr, const int* recv, const int* send, const float* Yg, const float* h,
                  const uint8_t* w3img, const uint8_t* z2t, float s, float* mA, float* mB, int use_bf16, int* err,
-                 int blocks, cudaStream_t st) {
+                 int blocks, cudaStream_t st) {  // blocks: SM count
   const size_t smem = FwdLayout<L, MODE>::bytes;
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  blocks = std::min(n, blocks * resident_ctas(tp_fused<L, MODE>, smem, Group<L, MODE>::NCOLS));
   {
     MLIP_PROF("tp_fused", st);
     tp_fused<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, h, w3img, z2t, s, mA, mB, use_bf16,
@@ -1099,6 +1134,7 @@ int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send
   using BL = BwdLayout<L, MODE>;
   const size_t smem = BL::bytes;
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused_bwd<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  blocks = std::min(n, blocks * resident_ctas(tp_fused_bwd<L, MODE>, smem, BL::NCOLS));
   {
     MLIP_PROF("tp_fused_bwd", st);
     tp_fused_bwd<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img, z2t, s, GinA,
@@ -1172,7 +1208,7 @@ int launch_tp_fused(int L, bool first, int n, const int* row_ptr, const int* rec
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks = std::max(1, std::min(n, 2 * sms));
+  const int blocks = sms;
 #define MLIP_G(LL, MM, GI) \
   MLIP_TRY((launch_group<LL, MM>(n, row_ptr, recv, send, Yg, h, w3img + goff[GI], z2t, s, mA, mB, use_bf16, err, \
                                  blocks, st)))
@@ -1201,7 +1237,7 @@ int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int*
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int blocks = std::max(1, std::min(n, sms));
+  const int blocks = sms;
 #define MLIP_GB(LL, MM, GI)                                                                                  \
   MLIP_TRY((launch_group_bwd<LL, MM>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img + goff[GI], z2t, s, GinA, GinB, \
                                      GoutA, GoutB, GI == 0, dY, dz2, use_bf16, absmax, err, blocks, st)))
