@@ -192,6 +192,26 @@ struct Split {
     return ws;
   }
   static constexpr std::array<int, NP> ws = make();
+  // harmonic components l2 m2 touched by warp set W (bit mask over 16)
+  static constexpr int ymask(int W) {
+    int m = 0;
+    for (int s = 0; s < NP; ++s)
+      if (ws[s] == W) {
+        const int l2 = Tab::l2[G::paths[s]];
+        for (int q = 0; q < 2 * l2 + 1; ++q) m |= 1 << (l2 * l2 + q);
+      }
+    return m;
+  }
+  static constexpr int nyv(int W) { return __builtin_popcount(ymask(W)); }
+  // edges packed into one 16-value channel butterfly
+  static constexpr int ypack(int W) { return nyv(W) <= 4 ? 4 : (nyv(W) <= 8 ? 2 : 1); }
+  static constexpr std::array<int, 16> ylist(int W) {
+    std::array<int, 16> a{};
+    int n = 0;
+    for (int k = 0; k < 16; ++k)
+      if (ymask(W) >> k & 1) a[n++] = k;
+    return a;
+  }
   // sender components read by warp set W (max l1 of its paths)
   static constexpr int dh(int W) {
     int m = -1;
@@ -652,10 +672,8 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const size_t o = ((size_t)i * D + d) * C + c;
-        float base;
-        if (W == 0) base = first_group ? GinA[o] + GinB[o] : GoutW[o];
-        else base = first_group ? 0.0f : GoutW[o];
-        GoutW[o] = base + Gacc[d];
+        if (!first_group) atomicAdd(&GoutW[o], Gacc[d]);
+        else GoutW[o] = (W == 0 ? GinA[o] + GinB[o] : 0.0f) + Gacc[d];
       }
     }
 #pragma unroll
@@ -673,6 +691,14 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
     }
   };
   constexpr int CH = chunk_edges<DH + (FIRST ? 0 : NG)>();
+  static_assert(CH % S::ypack(W) == 0, "edge packing must divide the chunk");
+  float pv[16];
+  int yl_rt[16];
+  {
+    constexpr std::array<int, 16> yl = S::ylist(W);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) yl_rt[k] = yl[k];
+  }
   float hn[CH][DH], gn[CH][NG];
 #pragma unroll
   for (int j = 0; j < CH; ++j) {
@@ -712,8 +738,8 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
         }
       }
     }
-#pragma unroll
-    for (int j = 0; j < CH; ++j) {
+    static_for<0, CH>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
       const int t = CH * ch + j;
       const int r = s_recv[t];
       float dYp[16];
@@ -737,9 +763,18 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
           }
         });
       }
-      const float tot = warp_reduce16(dYp);
-      if ((lane & 1) == 0) red[(warp * kNT + t) * 16 + (lane >> 1)] = tot;
-    }
+      // channel sums of this edge's dE/dY components, several edges per butterfly
+      constexpr int PK = S::ypack(W), NVP = 16 / PK, NV = S::nyv(W);
+      constexpr std::array<int, 16> yl = S::ylist(W);
+      constexpr int slot = j % PK;
+#pragma unroll
+      for (int i = 0; i < NVP; ++i) pv[slot * NVP + i] = i < NV ? dYp[yl[i < NV ? i : 0]] : 0.0f;
+      if constexpr (slot == PK - 1) {
+        const float tot = warp_reduce16(pv);
+        const int v = lane >> 1, vi = v % NVP, te = t - (PK - 1) + v / NVP;
+        if ((lane & 1) == 0 && vi < NV) red[(warp * kNT + te) * 16 + yl_rt[vi]] = tot;
+      }
+    });
   }
 }
 
@@ -907,14 +942,24 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
       tc::mma_commit(bar_mma2);
     }
     // channel sums of dE/dY while the product runs
-    for (int q = tid; q < kNT * 16; q += blockDim.x) {
-      const int t = q >> 4, k = q & 15;
-      const int e = tile * kNT + t;
-      if (e >= E0 && e < E1) {
-        float v = 0.0f;
+    {
+      using S = Split<L, MODE, true>;
+      constexpr int m0 = S::ymask(0), m1 = S::ymask(1);
+      for (int q = tid; q < kNT * 16; q += blockDim.x) {
+        const int t = q >> 4, k = q & 15;
+        const int e = tile * kNT + t;
+        if (e >= E0 && e < E1 && ((m0 | m1) >> k & 1)) {
+          float v = 0.0f;
+          if (m0 >> k & 1) {
 #pragma unroll
-        for (int w = 0; w < 4 * kWS; ++w) v += red[(w * kNT + t) * 16 + k];
-        dY[(size_t)e * 16 + k] += v;
+            for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
+          }
+          if (m1 >> k & 1) {
+#pragma unroll
+            for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
+          }
+          atomicAdd(&dY[(size_t)e * 16 + k], v);  // one add per kernel and address: deterministic
+        }
       }
     }
     if (!tc::mbar_wait(bar_mma2, (uint32_t)(it & 1))) {
@@ -931,7 +976,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int e = tile * kNT + ch * 8 + j;
-          if (e >= E0 && e < E1) dz2[(size_t)e * 64 + tid] += v[j] * inv_dw_scale;
+          if (e >= E0 && e < E1) atomicAdd(&dz2[(size_t)e * 64 + tid], v[j] * inv_dw_scale);
         }
       }
     }
@@ -946,10 +991,8 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
 #pragma unroll
         for (int d = 0; d < D; ++d) {
           const size_t o = ((size_t)cur * D + d) * 128 + c;
-          float base;
-          if (wsid == 0) base = first_group ? GinA[o] + GinB[o] : GoutW[o];
-          else base = first_group ? 0.0f : GoutW[o];
-          GoutW[o] = base + Gacc[d];
+          if (!first_group) atomicAdd(&GoutW[o], Gacc[d]);
+          else GoutW[o] = (wsid == 0 ? GinA[o] + GinB[o] : 0.0f) + Gacc[d];
         }
       }
 #pragma unroll
@@ -1098,16 +1141,18 @@ __global__ void umma_selftest_mn(const float* __restrict__ W, const float* __res
   if (warp == 0) tc::tmem_dealloc(tbase, 32);
 }
 
-// CTAs of a fused kernel resident per SM: the occupancy limit (registers,
-// shared memory) capped by tensor memory (512 columns per SM) and at 2.
+// CTAs of a fused kernel resident per SM: limited by registers (64K per SM),
+// shared memory (228 KB per SM, 1 KB reserved per CTA) and tensor memory (512
+// columns per SM); at most 2.
 template <class K>
 int resident_ctas(K kernel, size_t smem, int ncols) {
-  int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem) != cudaSuccess) {
-    cudaGetLastError();
-    occ = 1;
-  }
-  return std::max(1, std::min({occ, 512 / ncols, 2}));
+  cudaFuncAttributes fa{};
+  int regs = 255;
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess) regs = fa.numRegs;
+  else cudaGetLastError();
+  const int by_regs = 65536 / std::max(1, ((regs + 7) & ~7) * kThreads);
+  const int by_smem = (int)((228 * 1024) / (smem + 1024 + fa.sharedSizeBytes));
+  return std::max(1, std::min({by_regs, by_smem, 512 / ncols, 2}));
 }
 
 template <int L, int MODE>
