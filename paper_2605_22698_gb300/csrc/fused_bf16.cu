@@ -778,6 +778,129 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
   }
 }
 
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+  return __uint_as_float(r);
+}
+
+// Heavy groups: one copy of the per-edge body in a runtime loop over the
+// tile's edges (keeps the hot loop inside the instruction cache); the sender
+// gathers run kPF edges ahead in a rotating register window.
+constexpr int kPF = 4;
+template <int L, int MODE, int W>
+__device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_send, const int* s_recv,
+                                                 const float* sY, const float* cY, uint32_t taddr0,
+                                                 const float* __restrict__ hprev, const float* __restrict__ Gm,
+                                                 const float* __restrict__ GinA, const float* __restrict__ GinB,
+                                                 float* __restrict__ GoutW, int first_group, int& cur, float* Gacc,
+                                                 float* Gt, float* red, uint8_t* sB2, float s, float dw_scale,
+                                                 int use_bf16) {
+  using G = Group<L, MODE>;
+  using S = Split<L, MODE, true>;
+  using BL = BwdLayout<L, MODE>;
+  constexpr int D = NodeDims<L>::D;
+  constexpr int C = 128;
+  constexpr bool FIRST = MODE < 0;
+  constexpr int DH = S::dh(W);
+  constexpr int NG = FIRST ? 1 : G::NOUT;
+  constexpr int SBO2 = G::NP * 2048;
+  constexpr int PK = S::ypack(W), NVP = 16 / PK, NV = S::nyv(W);
+  constexpr std::array<int, 16> yl = S::ylist(W);
+  const int c = threadIdx.x & 127, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int yl_rt[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) yl_rt[k] = yl[k];
+  auto flush = [&](int i) {
+    if constexpr (!FIRST) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const size_t o = ((size_t)i * D + d) * C + c;
+        if (!first_group) atomicAdd(&GoutW[o], Gacc[d]);
+        else GoutW[o] = (W == 0 ? GinA[o] + GinB[o] : 0.0f) + Gacc[d];
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
+  };
+  auto enter = [&](int i) {
+#pragma unroll
+    for (int q = 0; q < G::NOUT; ++q) Gt[q] = s * Gm[((size_t)i * D + G::comp0 + q) * C + c];
+  };
+  auto advance = [&](int r) {
+    while (cur < r) {
+      if (cur >= i0) flush(cur);
+      ++cur;
+      if (cur < i1) enter(cur);
+    }
+  };
+  auto gather = [&](int t, float* hv, float* gv) {
+    const int si = s_send[t];
+#pragma unroll
+    for (int d = 0; d < DH; ++d) hv[d] = hprev[((size_t)si * D + d) * C + c];
+    if constexpr (!FIRST) {
+#pragma unroll
+      for (int q = 0; q < NG; ++q) gv[q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
+    }
+  };
+  float hw[kPF][DH], gw[kPF][NG];
+#pragma unroll
+  for (int k = 0; k < kPF; ++k) gather(k, hw[k], gw[k]);
+  float pv[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) pv[i] = 0.0f;
+#pragma unroll 1
+  for (int t = 0; t < kNT; ++t) {
+    float wv[G::NP];
+    static_for<0, G::NP>([&](auto sc) {
+      constexpr int sl = decltype(sc)::value;
+      if constexpr (S::ws[sl] == W) wv[sl] = tmem_ld1(taddr0 + sl * kNT + t);
+    });
+    tc::tmem_ld_wait();
+    float hc[DH], gc[NG];
+#pragma unroll
+    for (int d = 0; d < DH; ++d) hc[d] = hw[0][d];
+#pragma unroll
+    for (int q = 0; q < NG; ++q) gc[q] = FIRST ? 0.0f : gw[0][q];
+#pragma unroll
+    for (int k = 0; k + 1 < kPF; ++k) {
+#pragma unroll
+      for (int d = 0; d < DH; ++d) hw[k][d] = hw[k + 1][d];
+#pragma unroll
+      for (int q = 0; q < NG; ++q) gw[k][q] = gw[k + 1][q];
+    }
+    gather(t + kPF < kNT ? t + kPF : kNT - 1, hw[kPF - 1], gw[kPF - 1]);
+    const int r = s_recv[t];
+    float dYp[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) dYp[k] = 0.0f;
+    if (r >= 0) {
+      advance(r);
+      float Y[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
+      bwd_edge<L, MODE, W>(wv, t, hc, gc, Gt, Y, cY + t * BL::NZP, s, dw_scale, use_bf16, sB2, Gacc, dYp);
+    } else {
+      static_for<0, G::NP>([&](auto sc) {
+        constexpr int sl = decltype(sc)::value;
+        if constexpr (S::ws[sl] == W) {
+          const int kidx = sl * 128 + c;
+          *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) = 0;
+        }
+      });
+    }
+#pragma unroll
+    for (int i = 0; i < NVP * (PK - 1); ++i) pv[i] = pv[i + NVP];
+#pragma unroll
+    for (int i = 0; i < NVP; ++i) pv[NVP * (PK - 1) + i] = i < NV ? dYp[yl[i < NV ? i : 0]] : 0.0f;
+    if ((t % PK) == PK - 1) {
+      const float tot = warp_reduce16(pv);
+      const int v = lane >> 1, vi = v % NVP, te = t - (PK - 1) + v / NVP;
+      if ((lane & 1) == 0 && vi < NV) red[(warp * kNT + te) * 16 + yl_rt[vi]] = tot;
+    }
+  }
+}
+
 template <int L, int MODE>
 __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __restrict__ row_ptr,
                                                          const int* __restrict__ recv, const int* __restrict__ send,
@@ -916,12 +1039,25 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
       abort_s = 1;
     }
     tc::fence_after_sync();
-    if (wsid == 0)
-      bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
-                              cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
-    else
-      bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
-                              cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
+    {
+      using S = Split<L, MODE, true>;
+      constexpr bool heavy0 = S::dh(0) + (FIRST ? 0 : G::NOUT) > 8, heavy1 = S::dh(1) + (FIRST ? 0 : G::NOUT) > 8;
+      if (wsid == 0) {
+        if constexpr (heavy0)
+          bwd_tile_ws_roll<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW,
+                                       first_group, cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
+        else
+          bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
+                                  cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
+      } else {
+        if constexpr (heavy1)
+          bwd_tile_ws_roll<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW,
+                                       first_group, cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
+        else
+          bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
+                                  cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
+      }
+    }
     // second product: dE/dz2 = W3 dE/dw over this tile
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
