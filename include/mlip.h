@@ -163,6 +163,24 @@ int mlip_energy_forces(mlip_model* model, const double* pos, const int32_t* spec
                        const double cell[9], const uint8_t pbc[3], double* energy, double* forces,
                        double* stress, int on_device, void* stream);
 
+/* Energy, forces and stress of a batch of independent systems in one call
+ * (the batched inference of the Introduction): the systems are evaluated
+ * together as one graph, the disjoint union of their neighbour graphs, so
+ * many small systems fill the GPU like one large one.  System s owns atoms
+ * [atom_off[s], atom_off[s+1]) of pos (double[n][3]) and species (int32[n]),
+ * n = atom_off[n_systems]; cells: double[n_systems][9] (lattice rows), pbc:
+ * uint8[n_systems][3].  energy: double[n_systems]; forces: double[n][3] or
+ * NULL; stress: double[n_systems][9] or NULL (every system fully periodic,
+ * else MLIP_ERR_CELL).  atom_off, cells and pbc are host arrays; pos, species
+ * and the outputs are host or device arrays per on_device.  Every system must
+ * have at least one atom.  A system's energy, forces and stress do not depend
+ * on the other systems of the batch (per-system sums run over chunks counted
+ * from the system's own first atom, and the 16-bit operand scale is chosen per
+ * system).  Errors as mlip_energy_forces. */
+int mlip_energy_forces_batch(mlip_model* model, int32_t n_systems, const int64_t* atom_off, const double* pos,
+                             const int32_t* species, const double* cells, const uint8_t* pbc, double* energy,
+                             double* forces, double* stress, int on_device, void* stream);
+
 /* Velocity-Verlet NVE trajectory of one system (the batched MD
  * engines named in the Introduction and in "NPT ensemble
  * simulations"; NVE is the integrator of the benchmark workloads):
@@ -176,6 +194,110 @@ int mlip_energy_forces(mlip_model* model, const double* pos, const int32_t* spec
 int mlip_md_nve(mlip_model* model, double* pos, double* vel, const int32_t* species, int64_t n,
                 const double cell[9], const uint8_t pbc[3], double dt_fs, int64_t n_steps, double* pe,
                 double* ke, int on_device, void* stream);
+
+/* ------------------------------------------------------------- serving
+ * Continuous batching of independent requests (the paper's batched
+ * inference and MD serving, Introduction and "NPT ensemble simulations"):
+ * a worker thread owns one CUDA stream and, at every iteration, evaluates
+ * all running requests together as one graph (mlip_energy_forces_batch).
+ * An energy+forces request runs for one iteration; an NVE request runs for
+ * n_steps + 1 (the start and one per velocity-Verlet step).  After every
+ * iteration finished requests leave the batch and queued requests join it
+ * (first in, first out) while the batch stays within max_slots requests and
+ * the device-memory budget.  A request's results do not depend on the other
+ * requests it shared batches with.
+ *
+ * Ownership: the server uses the model exclusively while it exists (do not
+ * call other functions on the model meanwhile; free the model after
+ * mlip_serve_destroy).  Submit copies the inputs.  Result arrays belong to
+ * the server and stay valid until mlip_serve_release of that id (or
+ * destroy).  submit, poll, wait, release and stats may be called from any
+ * thread. */
+typedef struct mlip_server mlip_server;
+
+enum { MLIP_REQ_ENERGY_FORCES = 0, MLIP_REQ_NVE = 1 };
+
+typedef struct {
+  int64_t hbm_budget_bytes;   /* device memory for batches (estimated per atom and
+                                 edge); 0: 80 % of the free memory at create */
+  int32_t max_slots;          /* most requests in one batch; 0: 512 */
+  int32_t n_buckets;          /* size classes of the latency statistics, 0..8 */
+  int64_t bucket_edges[8];    /* ascending upper atom counts of the classes (the
+                                 last class takes every larger request) */
+  int64_t device_poll_limit_us; /* longest host wait (microseconds) for one
+                                 iteration's results; exceeded: the batch's
+                                 requests fail with MLIP_ERR_DEVICE_TIMEOUT and
+                                 the server admits nothing more.  0: no limit */
+} mlip_serve_config;
+
+typedef struct {
+  int32_t kind;               /* MLIP_REQ_ENERGY_FORCES or MLIP_REQ_NVE */
+  int32_t want_stress;        /* energy+forces: also the stress (fully periodic cell) */
+  int64_t n;                  /* atoms, >= 1 */
+  const double* pos;          /* host [n][3], A */
+  const int32_t* species;     /* host [n], 0..n_species-1 */
+  double cell[9];             /* lattice rows (ignored without a periodic axis) */
+  uint8_t pbc[3];
+  const double* vel;          /* NVE: host [n][3] A/fs, or NULL: Maxwell-Boltzmann at
+                                 temperature_K from seed (SplitMix64 normals by
+                                 Box-Muller, centre-of-mass velocity removed) */
+  double temperature_K;
+  uint64_t seed;
+  int64_t n_steps;            /* NVE: velocity-Verlet steps, >= 0 */
+  double dt_fs;               /* NVE: time step (fs), > 0 */
+} mlip_request;
+
+typedef struct {
+  int32_t status;             /* MLIP_OK or the error that ended this request */
+  int32_t kind;
+  int64_t n, n_steps;
+  double energy;              /* energy (NVE: potential energy at the end) */
+  double stress[9];           /* when requested */
+  const double* forces;       /* [n][3] (NVE: at the end) */
+  const double* pos;          /* NVE: final positions [n][3]; NULL otherwise */
+  const double* vel;          /* NVE: final velocities [n][3] */
+  const double* pe;           /* NVE: potential energy at the start and after every step [n_steps + 1] */
+  const double* ke;           /* NVE: kinetic energy, same points */
+  double t_arrive, t_admit, t_done;  /* seconds on the server's clock (0 = create) */
+} mlip_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, rejected, queued, running;
+  int64_t iterations;         /* batched force evaluations */
+  int64_t atom_evals;         /* sum over iterations of the atoms evaluated */
+  double elapsed_s;           /* server clock now */
+  double busy_s;              /* worker time inside iterations */
+  double atom_steps_per_s;    /* atom_evals / busy_s */
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* t_done - t_arrive of completed requests */
+  double mean_batch_atoms, mean_batch_requests;
+  int64_t device_bytes;       /* device memory held by the server and the model's workspace */
+  int32_t n_buckets;
+  int64_t bucket_count[9];
+  double bucket_p50_ms[9], bucket_p99_ms[9];
+} mlip_serve_statistics;
+
+/* Starts the worker.  Errors: MLIP_ERR_INVALID_ARG (bad config: max_slots < 0,
+ * n_buckets outside 0..8, edges not ascending), MLIP_ERR_CUDA. */
+int mlip_serve_create(mlip_model* model, const mlip_serve_config* config, mlip_server** out);
+/* Validates and copies a request and queues it; *id identifies it.  Errors:
+ * MLIP_ERR_INVALID_ARG (sizes, species, non-finite input, NVE without masses),
+ * MLIP_ERR_CELL (stress without a fully periodic cell, singular cell),
+ * MLIP_ERR_BUDGET (the request alone exceeds the memory budget),
+ * MLIP_ERR_DEVICE_TIMEOUT (the server stopped after a device timeout). */
+int mlip_serve_submit(mlip_server* server, const mlip_request* req, uint64_t* id);
+/* MLIP_OK and *out filled when the request has ended (out->status tells how);
+ * MLIP_PENDING while it is queued or running; MLIP_ERR_NOT_FOUND for an
+ * unknown or released id. */
+int mlip_serve_poll(mlip_server* server, uint64_t id, mlip_result* out);
+/* As poll, but waits up to timeout_ms (< 0: no limit) for the end; returns
+ * MLIP_ERR_TIMEOUT if the request is still pending then. */
+int mlip_serve_wait(mlip_server* server, uint64_t id, int64_t timeout_ms, mlip_result* out);
+/* Frees an ended request's results (MLIP_PENDING if it has not ended). */
+int mlip_serve_release(mlip_server* server, uint64_t id);
+int mlip_serve_stats(mlip_server* server, mlip_serve_statistics* out);
+/* Stops admitting, finishes the running iteration, fails queued and running
+ * requests with MLIP_ERR_TIMEOUT, joins the worker and frees the server. */
+int mlip_serve_destroy(mlip_server* server);
 
 /* Self test of a hardware path (no counterpart in the paper).  which = 1: one
  * tcgen05 tile product (M = 128, N = 32, K = 64, BF16 operands in the

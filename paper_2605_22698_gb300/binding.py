@@ -64,6 +64,7 @@ def lib():
         L.mlip_model_free.argtypes = [P]
         L.mlip_neighbors.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), i32, P]
         L.mlip_energy_forces.argtypes = [P, P, P, i64, P, P, P, P, P, i32, P]
+        L.mlip_energy_forces_batch.argtypes = [P, i32, P, P, P, P, P, P, P, P, i32, P]
         L.mlip_neighbors_noalloc.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), P]
         L.mlip_md_nve.argtypes = [P, P, P, P, i64, P, P, f64, i64, P, P, i32, P]
         L.mlip_selftest.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
@@ -209,6 +210,29 @@ def mlip_energy_forces(h, pos, species, cell, pbc, forces: bool = True, stress: 
     return out
 
 
+def mlip_energy_forces_batch(h, systems, forces: bool = True, stress: bool = False, stream=None):
+    """Batch of host systems [(pos [n,3], species [n], cell [3,3], pbc [3]), ...]
+    evaluated in one call.  Returns (energy [n_sys], forces list, stress [n_sys,3,3])."""
+    ns = len(systems)
+    off = np.zeros(ns + 1, dtype=np.int64)
+    for k, (p, _, _, _) in enumerate(systems):
+        off[k + 1] = off[k] + int(np.asarray(p).shape[0])
+    pos = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64).reshape(-1, 3) for p, _, _, _ in systems]))
+    sp = np.ascontiguousarray(np.concatenate([np.asarray(z, dtype=np.int32).reshape(-1) for _, z, _, _ in systems]))
+    cells = np.ascontiguousarray(np.stack([np.asarray(c, dtype=np.float64).reshape(9) for _, _, c, _ in systems]))
+    pbcs = np.ascontiguousarray(np.stack([np.asarray(b, dtype=np.uint8).reshape(3) for _, _, _, b in systems]))
+    energy = np.zeros(ns)
+    F = np.zeros((int(off[-1]), 3)) if forces else None
+    S = np.zeros((ns, 3, 3)) if stress else None
+    _check(lib().mlip_energy_forces_batch(h, ns, off.ctypes.data_as(ctypes.c_void_p), _ptr(pos)[0], _ptr(sp)[0],
+                                          cells.ctypes.data_as(ctypes.c_void_p),
+                                          pbcs.ctypes.data_as(ctypes.c_void_p), _ptr(energy)[0],
+                                          _ptr(F)[0] if forces else None, _ptr(S)[0] if stress else None, 0,
+                                          _stream_ptr(stream)))
+    Fl = [F[off[k]:off[k + 1]] for k in range(ns)] if forces else None
+    return energy, Fl, S
+
+
 def mlip_md_nve(h, pos, vel, species, cell, pbc, dt_fs: float, n_steps: int, stream=None):
     """Velocity-Verlet NVE.  numpy inputs: copies are integrated and returned
     with the energy traces; torch CUDA tensors: integrated in place."""
@@ -265,12 +289,190 @@ class Model:
     def energy_forces(self, pos, species, cell, pbc, forces=True, stress=False, stream=None, out=None):
         return mlip_energy_forces(self.h, pos, species, cell, pbc, forces, stress, stream, out)
 
+    def energy_forces_batch(self, systems, forces=True, stress=False, stream=None):
+        return mlip_energy_forces_batch(self.h, systems, forces, stress, stream)
+
     def md_nve(self, pos, vel, species, cell, pbc, dt_fs, n_steps, stream=None):
         return mlip_md_nve(self.h, pos, vel, species, cell, pbc, dt_fs, n_steps, stream)
 
     def close(self):
         if getattr(self, "h", None):
             mlip_model_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+MLIP_REQ_ENERGY_FORCES = 0
+MLIP_REQ_NVE = 1
+
+
+class mlip_serve_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
+                ("bucket_edges", ctypes.c_int64 * 8), ("device_poll_limit_us", ctypes.c_int64)]
+
+
+class mlip_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("want_stress", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("pos", ctypes.c_void_p), ("species", ctypes.c_void_p), ("cell", ctypes.c_double * 9),
+                ("pbc", ctypes.c_uint8 * 3), ("vel", ctypes.c_void_p), ("temperature_K", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("n_steps", ctypes.c_int64), ("dt_fs", ctypes.c_double)]
+
+
+class mlip_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("n_steps", ctypes.c_int64), ("energy", ctypes.c_double), ("stress", ctypes.c_double * 9),
+                ("forces", ctypes.POINTER(ctypes.c_double)), ("pos", ctypes.POINTER(ctypes.c_double)),
+                ("vel", ctypes.POINTER(ctypes.c_double)), ("pe", ctypes.POINTER(ctypes.c_double)),
+                ("ke", ctypes.POINTER(ctypes.c_double)), ("t_arrive", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class mlip_serve_statistics(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("iterations", ctypes.c_int64), ("atom_evals", ctypes.c_int64), ("elapsed_s", ctypes.c_double),
+                ("busy_s", ctypes.c_double), ("atom_steps_per_s", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("mean_batch_atoms", ctypes.c_double), ("mean_batch_requests", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("n_buckets", ctypes.c_int32),
+                ("bucket_count", ctypes.c_int64 * 9), ("bucket_p50_ms", ctypes.c_double * 9),
+                ("bucket_p99_ms", ctypes.c_double * 9)]
+
+
+def _serve_lib():
+    L = lib()
+    if not getattr(L, "_serve_types", False):
+        P = ctypes.c_void_p
+        L.mlip_serve_create.argtypes = [P, ctypes.POINTER(mlip_serve_config), ctypes.POINTER(P)]
+        L.mlip_serve_submit.argtypes = [P, ctypes.POINTER(mlip_request), ctypes.POINTER(ctypes.c_uint64)]
+        L.mlip_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(mlip_result)]
+        L.mlip_serve_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(mlip_result)]
+        L.mlip_serve_release.argtypes = [P, ctypes.c_uint64]
+        L.mlip_serve_stats.argtypes = [P, ctypes.POINTER(mlip_serve_statistics)]
+        L.mlip_serve_destroy.argtypes = [P]
+        L._serve_types = True
+    return L
+
+
+def mlip_serve_create(h, hbm_budget_bytes: int = 0, max_slots: int = 0, bucket_edges=(),
+                      device_poll_limit_us: int = 0):
+    c = mlip_serve_config()
+    c.hbm_budget_bytes = int(hbm_budget_bytes)
+    c.max_slots = int(max_slots)
+    c.n_buckets = len(bucket_edges)
+    for k, e in enumerate(bucket_edges):
+        c.bucket_edges[k] = int(e)
+    c.device_poll_limit_us = int(device_poll_limit_us)
+    out = ctypes.c_void_p()
+    _check(_serve_lib().mlip_serve_create(h, ctypes.byref(c), ctypes.byref(out)))
+    return out
+
+
+def mlip_serve_submit(srv, kind, pos, species, cell=None, pbc=(0, 0, 0), want_stress=False, vel=None,
+                      temperature_K=300.0, seed=0, n_steps=0, dt_fs=0.5) -> int:
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    species = np.ascontiguousarray(species, dtype=np.int32).reshape(-1)
+    q = mlip_request()
+    q.kind = int(kind)
+    q.want_stress = 1 if want_stress else 0
+    q.n = int(pos.shape[0])
+    q.pos = pos.ctypes.data
+    q.species = species.ctypes.data
+    cell = np.eye(3) if cell is None else np.asarray(cell, dtype=np.float64)
+    for k, v in enumerate(cell.reshape(9)):
+        q.cell[k] = float(v)
+    for k, v in enumerate(np.asarray(pbc).reshape(3)):
+        q.pbc[k] = int(v)
+    if vel is not None:
+        vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
+        q.vel = vel.ctypes.data
+    q.temperature_K = float(temperature_K)
+    q.seed = int(seed)
+    q.n_steps = int(n_steps)
+    q.dt_fs = float(dt_fs)
+    rid = ctypes.c_uint64(0)
+    _check(_serve_lib().mlip_serve_submit(srv, ctypes.byref(q), ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def _result_dict(r: mlip_result) -> dict:
+    n, ns = int(r.n), int(r.n_steps)
+    d = {"status": int(r.status), "kind": int(r.kind), "n": n, "n_steps": ns, "energy": float(r.energy),
+         "stress": np.array(r.stress[:]).reshape(3, 3), "t_arrive": r.t_arrive, "t_admit": r.t_admit,
+         "t_done": r.t_done}
+
+    def arr(p, count, shape):
+        return np.ctypeslib.as_array(p, shape=(count,)).copy().reshape(shape) if p else None
+    d["forces"] = arr(r.forces, 3 * n, (n, 3))
+    d["pos"] = arr(r.pos, 3 * n, (n, 3))
+    d["vel"] = arr(r.vel, 3 * n, (n, 3))
+    d["pe"] = arr(r.pe, ns + 1, (ns + 1,))
+    d["ke"] = arr(r.ke, ns + 1, (ns + 1,))
+    return d
+
+
+def mlip_serve_poll(srv, rid: int):
+    r = mlip_result()
+    rc = _check(_serve_lib().mlip_serve_poll(srv, rid, ctypes.byref(r)))
+    return None if rc == MLIP_PENDING else _result_dict(r)
+
+
+def mlip_serve_wait(srv, rid: int, timeout_ms: int = -1):
+    r = mlip_result()
+    _check(_serve_lib().mlip_serve_wait(srv, rid, int(timeout_ms), ctypes.byref(r)))
+    return _result_dict(r)
+
+
+def mlip_serve_release(srv, rid: int) -> int:
+    return _check(_serve_lib().mlip_serve_release(srv, rid))
+
+
+def mlip_serve_stats(srv) -> dict:
+    s = mlip_serve_statistics()
+    _check(_serve_lib().mlip_serve_stats(srv, ctypes.byref(s)))
+    d = {k: getattr(s, k) for k, _ in mlip_serve_statistics._fields_ if not k.startswith("bucket_")}
+    nb = int(s.n_buckets) + 1
+    d["bucket_count"] = list(s.bucket_count[:nb])
+    d["bucket_p50_ms"] = list(s.bucket_p50_ms[:nb])
+    d["bucket_p99_ms"] = list(s.bucket_p99_ms[:nb])
+    return d
+
+
+def mlip_serve_destroy(srv) -> None:
+    _check(_serve_lib().mlip_serve_destroy(srv))
+
+
+class Server:
+    """Owning wrapper of a server handle (the model must outlive it)."""
+
+    def __init__(self, model: "Model", **cfg):
+        self.model = model
+        self.h = mlip_serve_create(model.h, **cfg)
+
+    def submit(self, kind, pos, species, **kw) -> int:
+        return mlip_serve_submit(self.h, kind, pos, species, **kw)
+
+    def poll(self, rid):
+        return mlip_serve_poll(self.h, rid)
+
+    def wait(self, rid, timeout_ms=-1):
+        return mlip_serve_wait(self.h, rid, timeout_ms)
+
+    def release(self, rid):
+        return mlip_serve_release(self.h, rid)
+
+    def stats(self):
+        return mlip_serve_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mlip_serve_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -274,33 +274,27 @@ int launch_check_inputs(int n, const double* pos, const int* species, int S, int
   return MLIP_OK;
 }
 
-static double cell_volume(const double* h) {
-  return std::fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
-                   h[2] * (h[3] * h[7] - h[4] * h[6]));
-}
 
-int energy_forces_plain(mlip_model* M, const double* d_pos, const int* d_species, int64_t n64, const double* cell,
-                        const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
   Workspace& ws = M->ws;
-  const int n = (int)n64, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H, P = M->P, P0 = M->P0;
+  const int n = (int)b.n, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H, P = M->P, P0 = M->P0;
   const float s = (float)(1.0 / M->avg_nb);
   int* flag = nullptr;
   MLIP_TRY(ws.get("chk.flag", 1, &flag));
   MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
   MLIP_TRY(launch_check_inputs(n, d_pos, d_species, M->S, flag, st));
   NeighborList nl;
-  MLIP_TRY(build_neighbors(ws, d_pos, n, cell, pbc, M->rc, true, st, &nl));
+  MLIP_TRY(build_neighbors_batch(ws, d_pos, b, M->rc, true, st, &nl));
   int hflag = 0;
   MLIP_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   MLIP_CUDA_TRY(cudaStreamSynchronize(st));
   if (hflag & 1) { set_error("species index out of range"); return MLIP_ERR_INVALID_ARG; }
   if (hflag & 2) { set_error("non-finite position"); return MLIP_ERR_INVALID_ARG; }
   const int E = (int)nl.E;
-  const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)n * D * C;
+  const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)std::max(n, 1) * D * C;
 
-  CellArg ca{};
-  ca.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
-  for (int k = 0; k < 9; ++k) ca.h[k] = ca.any_pbc ? cell[k] : 0.0;
+  CellArg ca{b.d_cell, b.d_sys_of, b.any_pbc() ? 1 : 0};
 
   float4 *ev = nullptr, *g = nullptr;
   float *z2T = nullptr, *m = nullptr, *Gm = nullptr, *Ga = nullptr, *Gb = nullptr, *dw = nullptr, *dz2 = nullptr,
@@ -336,7 +330,7 @@ int energy_forces_plain(mlip_model* M, const double* d_pos, const int* d_species
     MLIP_TRY(launch_tp_fwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], w[t], PW, s, m, st));
     MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
   }
-  MLIP_TRY(launch_energy(n, C, D, d_species, M->W_out, M->E0, h[T], atom_e, energy, st));
+  MLIP_TRY(launch_energy(ws, b, C, D, d_species, M->W_out, M->E0, h[T], atom_e, energy, st));
   if (d_forces || d_stress) {
     MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, Ga, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
@@ -353,10 +347,15 @@ int energy_forces_plain(mlip_model* M, const double* d_pos, const int* d_species
     MLIP_TRY(launch_edge_grad(E, ev, dY, dr, g, st));
     double* fbuf = d_forces;
     if (!fbuf) MLIP_TRY(ws.get("ef.fscratch", (size_t)3 * std::max(n, 1), &fbuf));
-    const double vol = ca.any_pbc ? cell_volume(cell) : 1.0;
-    MLIP_TRY(launch_forces_virial(ws, n, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, 1.0 / vol, st));
+    MLIP_TRY(launch_forces_virial(ws, b, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, st));
   }
   return MLIP_OK;
+}
+
+int evaluate(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b, double* d_energy,
+             double* d_forces, double* d_stress, cudaStream_t st) {
+  if (M->precision == MLIP_PREC_FP32) return evaluate_plain(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st);
+  return evaluate_fused(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st);
 }
 
 }  // namespace mlip
@@ -392,17 +391,72 @@ extern "C" int mlip_energy_forces(mlip_model* M, const double* pos, const int32_
     d_pos = dp;
     d_species = dz;
   }
-  int rc;
-  if (M->precision == MLIP_PREC_FP32) {
-    rc = energy_forces_plain(M, d_pos, d_species, n, cell, pbc, d_energy, d_forces, d_stress, st);
-  } else {
-    rc = energy_forces_fused(M, d_pos, d_species, n, cell, pbc, d_energy, d_forces, d_stress, st);
-  }
-  if (rc != MLIP_OK) return rc;
+  SystemBatch b;
+  single_system(b, n, cell, pbc);
+  MLIP_TRY(upload_batch(ws, M->stage, b, st));
+  MLIP_TRY(evaluate(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st));
   if (!on_device) {
     MLIP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (forces) MLIP_CUDA_TRY(cudaMemcpyAsync(forces, d_forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     if (stress) MLIP_CUDA_TRY(cudaMemcpyAsync(stress, d_stress, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+    MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  } else {
+    MLIP_CUDA_TRY(cudaGetLastError());
+  }
+  return MLIP_OK;
+}
+
+extern "C" int mlip_energy_forces_batch(mlip_model* M, int32_t n_systems, const int64_t* atom_off, const double* pos,
+                                        const int32_t* species, const double* cells, const uint8_t* pbc,
+                                        double* energy, double* forces, double* stress, int on_device,
+                                        void* stream) {
+  using namespace mlip;
+  if (!M || !atom_off || !pos || !species || !cells || !pbc || !energy) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  if (n_systems < 1 || n_systems > (1 << 20)) { set_error("system count %d out of range", n_systems); return MLIP_ERR_INVALID_ARG; }
+  if (atom_off[0] != 0) { set_error("atom_off[0] must be 0"); return MLIP_ERR_INVALID_ARG; }
+  for (int s = 0; s < n_systems; ++s) {
+    if (atom_off[s + 1] <= atom_off[s]) { set_error("system %d has no atoms (atom_off must increase)", s); return MLIP_ERR_INVALID_ARG; }
+    if (stress && !(pbc[3 * s] && pbc[3 * s + 1] && pbc[3 * s + 2])) {
+      set_error("stress needs a fully periodic cell (system %d)", s);
+      return MLIP_ERR_CELL;
+    }
+  }
+  const int64_t n = atom_off[n_systems];
+  if (n > (1LL << 28)) { set_error("atom count %lld out of range", (long long)n); return MLIP_ERR_INVALID_ARG; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != M->device) { set_error("model lives on device %d, current device is %d", M->device, cur); return MLIP_ERR_INVALID_ARG; }
+  Workspace& ws = M->ws;
+  const double* d_pos = pos;
+  const int* d_species = species;
+  double *d_energy = energy, *d_forces = forces, *d_stress = stress;
+  if (!on_device) {
+    for (int64_t i = 0; i < n; ++i)
+      if (species[i] < 0 || species[i] >= M->S) { set_error("species[%lld] = %d out of range", (long long)i, species[i]); return MLIP_ERR_INVALID_ARG; }
+    double* dp = nullptr;
+    int* dz = nullptr;
+    MLIP_TRY(ws.get("in.pos", (size_t)3 * n, &dp));
+    MLIP_TRY(ws.get("in.species", (size_t)n, &dz));
+    MLIP_TRY(ws.get("out.energy", (size_t)n_systems, &d_energy));
+    if (forces) MLIP_TRY(ws.get("out.forces", (size_t)3 * n, &d_forces));
+    if (stress) MLIP_TRY(ws.get("out.stress", (size_t)9 * n_systems, &d_stress));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dp, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dz, species, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    d_pos = dp;
+    d_species = dz;
+  }
+  SystemBatch b;
+  b.nsys = n_systems;
+  b.atom_off.assign(atom_off, atom_off + n_systems + 1);
+  b.cell.assign(cells, cells + 9 * (size_t)n_systems);
+  b.pbc.assign(pbc, pbc + 3 * (size_t)n_systems);
+  MLIP_TRY(upload_batch(ws, M->stage, b, st));
+  MLIP_TRY(evaluate(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st));
+  if (!on_device) {
+    MLIP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double) * n_systems, cudaMemcpyDeviceToHost, st));
+    if (forces) MLIP_CUDA_TRY(cudaMemcpyAsync(forces, d_forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (stress) MLIP_CUDA_TRY(cudaMemcpyAsync(stress, d_stress, sizeof(double) * 9 * n_systems, cudaMemcpyDeviceToHost, st));
     MLIP_CUDA_TRY(cudaStreamSynchronize(st));
   } else {
     MLIP_CUDA_TRY(cudaGetLastError());

@@ -656,7 +656,7 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
                                             const float* __restrict__ Gm, const float* __restrict__ GinA,
                                             const float* __restrict__ GinB, float* __restrict__ GoutW,
                                             int first_group, int& cur, float* Gacc, float* Gt, float* red,
-                                            uint8_t* sB2, float s, float dw_scale, int use_bf16) {
+                                            uint8_t* sB2, float s, const float* dws, int use_bf16) {
   using G = Group<L, MODE>;
   using S = Split<L, MODE, true>;
   using BL = BwdLayout<L, MODE>;
@@ -753,7 +753,7 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
         float wv[G::NP];
 #pragma unroll
         for (int sl = 0; sl < G::NP; ++sl) wv[sl] = wvc[sl][j];
-        bwd_edge<L, MODE, W>(wv, t, hc[j], gc[j], Gt, Y, cY + t * BL::NZP, s, dw_scale, use_bf16, sB2, Gacc, dYp);
+        bwd_edge<L, MODE, W>(wv, t, hc[j], gc[j], Gt, Y, cY + t * BL::NZP, s, dws[t], use_bf16, sB2, Gacc, dYp);
       } else {
         static_for<0, G::NP>([&](auto sc) {
           constexpr int sl = decltype(sc)::value;
@@ -794,7 +794,7 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
                                                  const float* __restrict__ hprev, const float* __restrict__ Gm,
                                                  const float* __restrict__ GinA, const float* __restrict__ GinB,
                                                  float* __restrict__ GoutW, int first_group, int& cur, float* Gacc,
-                                                 float* Gt, float* red, uint8_t* sB2, float s, float dw_scale,
+                                                 float* Gt, float* red, uint8_t* sB2, float s, const float* dws,
                                                  int use_bf16) {
   using G = Group<L, MODE>;
   using S = Split<L, MODE, true>;
@@ -879,7 +879,7 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
       float Y[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
-      bwd_edge<L, MODE, W>(wv, t, hc, gc, Gt, Y, cY + t * BL::NZP, s, dw_scale, use_bf16, sB2, Gacc, dYp);
+      bwd_edge<L, MODE, W>(wv, t, hc, gc, Gt, Y, cY + t * BL::NZP, s, dws[t], use_bf16, sB2, Gacc, dYp);
     } else {
       static_for<0, G::NP>([&](auto sc) {
         constexpr int sl = decltype(sc)::value;
@@ -913,6 +913,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
                                                          float* __restrict__ GoutA, float* __restrict__ GoutB,
                                                          int first_group, float* __restrict__ dY,
                                                          float* __restrict__ dz2, int use_bf16,
+                                                         const int* __restrict__ sys_of,
                                                          const float* __restrict__ absmax, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using BL = BwdLayout<L, MODE>;
@@ -938,6 +939,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
   uint64_t* bar_mma2 = bars + 4;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 5);
   __shared__ int abort_s;
+  __shared__ float s_dws[kNT];  // per-edge scale of dE/dw in the second product
 
   const int tid = threadIdx.x, warp = tid >> 5, wsid = warp >> 2, c = tid & 127;
   float* GoutW = wsid == 0 ? GoutA : GoutB;
@@ -989,15 +991,6 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
   int cur = i0 - 1;
   const uint32_t idesc1 = tc::idesc_16bit(128, kNT, use_bf16 != 0);
   const uint32_t idesc2 = idesc1 | (1u << 15);  // A M-major
-  // dE/dw enters the second product scaled by a power of two (FP16 operands):
-  // |dE/dw| <= 17 max|h| s max|Gm| (orthonormal CG rows, |Y| <= 1), so the
-  // scale 2^floor(log2(2^14 / (32 max|h| s max|Gm|))) keeps it below 2^14.
-  float dw_scale = 1.0f;
-  if (!use_bf16) {
-    const float U = 32.0f * absmax[0] * s * absmax[1];
-    dw_scale = U > 0.0f ? exp2f(fminf(fmaxf(floorf(log2f(16384.0f / U)), -60.0f), 60.0f)) : 1.0f;
-  }
-  const float inv_dw_scale = 1.0f / dw_scale;
 
 #pragma unroll 1
   for (int it = 0; it < n_tiles; ++it) {
@@ -1031,6 +1024,20 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
         abort_s = 1;
       }
     }
+    if (tid < kNT) {
+      // dE/dw enters the second product scaled by a power of two (FP16
+      // operands), chosen per system from its own maxima:
+      // |dE/dw| <= 17 max|h| s max|Gm| (orthonormal CG rows, |Y| <= 1), so the
+      // scale 2^floor(log2(2^14 / (32 max|h| s max|Gm|))) keeps it below 2^14.
+      const int e = tile * kNT + tid;
+      float sc = 1.0f;
+      if (!use_bf16 && e >= E0 && e < E1) {
+        const int sy = sys_of ? sys_of[recv[e]] : 0;
+        const float U = 32.0f * absmax[2 * sy] * s * absmax[2 * sy + 1];
+        sc = U > 0.0f ? exp2f(fminf(fmaxf(floorf(log2f(16384.0f / U)), -60.0f), 60.0f)) : 1.0f;
+      }
+      s_dws[tid] = sc;
+    }
     tile_setup<BL::NZ, BL::NZP>(tile, E0, E1, recv, send, Yg, s_recv, s_send, sY, cY, tab_c, tab_y);
     __syncthreads();
     if (abort_s) break;
@@ -1045,17 +1052,17 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
       if (wsid == 0) {
         if constexpr (heavy0)
           bwd_tile_ws_roll<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW,
-                                       first_group, cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
+                                       first_group, cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
         else
           bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
-                                  cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
+                                  cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
       } else {
         if constexpr (heavy1)
           bwd_tile_ws_roll<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW,
-                                       first_group, cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
+                                       first_group, cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
         else
           bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
-                                  cur, Gacc, Gt, red, sB2, s, dw_scale, use_bf16);
+                                  cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
       }
     }
     // second product: dE/dz2 = W3 dE/dw over this tile
@@ -1112,7 +1119,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int e = tile * kNT + ch * 8 + j;
-          if (e >= E0 && e < E1) atomicAdd(&dz2[(size_t)e * 64 + tid], v[j] * inv_dw_scale);
+          if (e >= E0 && e < E1) atomicAdd(&dz2[(size_t)e * 64 + tid], v[j] / s_dws[ch * 8 + j]);
         }
       }
     }
@@ -1147,24 +1154,6 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, BL::NCOLS);
-}
-
-// max |x| of two arrays (non-negative floats compare as integers)
-__global__ void absmax2(size_t na, const float* __restrict__ a, size_t nb, const float* __restrict__ b,
-                        float* __restrict__ out) {
-  float ma = 0.0f, mb = 0.0f;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < na; k += (size_t)gridDim.x * blockDim.x)
-    ma = fmaxf(ma, fabsf(a[k]));
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nb; k += (size_t)gridDim.x * blockDim.x)
-    mb = fmaxf(mb, fabsf(b[k]));
-  for (int o = 16; o > 0; o >>= 1) {
-    ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-    mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(reinterpret_cast<int*>(out), __float_as_int(ma));
-    atomicMax(reinterpret_cast<int*>(out) + 1, __float_as_int(mb));
-  }
 }
 
 // ------------------------------------------------------------- self test
@@ -1311,7 +1300,8 @@ template <int L, int MODE>
 int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send, const float* Yg,
                      const float* hprev, const float* Gm, const uint8_t* w3img, const uint8_t* z2t, float s,
                      const float* GinA, const float* GinB, float* GoutA, float* GoutB, int first_group, float* dY,
-                     float* dz2, int use_bf16, const float* absmax, int* err, int blocks, cudaStream_t st) {
+                     float* dz2, int use_bf16, const int* sys_of, const float* absmax, int* err, int blocks,
+                     cudaStream_t st) {
   using BL = BwdLayout<L, MODE>;
   const size_t smem = BL::bytes;
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused_bwd<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1319,7 +1309,8 @@ int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send
   {
     MLIP_PROF("tp_fused_bwd", st);
     tp_fused_bwd<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img, z2t, s, GinA,
-                                                          GinB, GoutA, GoutB, first_group, dY, dz2, use_bf16, absmax,
+                                                          GinB, GoutA, GoutB, first_group, dY, dz2, use_bf16, sys_of,
+                                                          absmax,
                                                           err);
   }
   MLIP_LAUNCH_CHECK();
@@ -1413,7 +1404,7 @@ int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int*
                         const float* Yg, const float* hprev, const float* Gm, const uint8_t* w3img,
                         const std::vector<size_t>& goff, const uint8_t* z2t, float s, const float* GinA,
                         const float* GinB, float* GoutA, float* GoutB, float* dY, float* dz2, int use_bf16,
-                        const float* absmax, int* err, cudaStream_t st) {
+                        const int* sys_of, const float* absmax, int* err, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -1421,7 +1412,7 @@ int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int*
   const int blocks = sms;
 #define MLIP_GB(LL, MM, GI)                                                                                  \
   MLIP_TRY((launch_group_bwd<LL, MM>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img + goff[GI], z2t, s, GinA, GinB, \
-                                     GoutA, GoutB, GI == 0, dY, dz2, use_bf16, absmax, err, blocks, st)))
+                                     GoutA, GoutB, GI == 0, dY, dz2, use_bf16, sys_of, absmax, err, blocks, st)))
   if (L == 2) {
     if (first) { MLIP_GB(2, -1, 0); }
     else { MLIP_GB(2, 0, 0); MLIP_GB(2, 1, 1); MLIP_GB(2, 2, 2); }
@@ -1515,10 +1506,10 @@ int umma_selftest_mn_run(int variant, double* rel_err) {
   return MLIP_OK;
 }
 
-int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species, int64_t n64, const double* cell,
-                        const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
   Workspace& ws = M->ws;
-  const int n = (int)n64, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H;
+  const int n = (int)b.n, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H;
   const float s = (float)(1.0 / M->avg_nb);
   const int use_bf16 = M->precision == MLIP_PREC_BF16 ? 1 : 0;
   int* flag = nullptr;
@@ -1526,13 +1517,11 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
   MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
   MLIP_TRY(launch_check_inputs(n, d_pos, d_species, M->S, flag, st));
   NeighborList nl;
-  MLIP_TRY(build_neighbors(ws, d_pos, n, cell, pbc, M->rc, true, st, &nl));
+  MLIP_TRY(build_neighbors_batch(ws, d_pos, b, M->rc, true, st, &nl));
   const int E = (int)nl.E;
   const int n_tiles = (E + kNT - 1) / kNT;
-  const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)n * D * C;
-  CellArg ca{};
-  ca.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
-  for (int k = 0; k < 9; ++k) ca.h[k] = ca.any_pbc ? cell[k] : 0.0;
+  const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)std::max(n, 1) * D * C;
+  CellArg ca{b.d_cell, b.d_sys_of, b.any_pbc() ? 1 : 0};
   float4 *ev = nullptr, *g = nullptr;
   float *mA = nullptr, *mB = nullptr, *Yg = nullptr, *Gm = nullptr, *dY = nullptr, *dr = nullptr, *dz2 = nullptr;
   float *GaA = nullptr, *GaB = nullptr, *GbA = nullptr, *GbB = nullptr;
@@ -1562,7 +1551,7 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
                              M->w3_goff[t], z2t[t], s, mA, mB, use_bf16, flag + 1, st));
     MLIP_TRY(launch_mix_fwd2(n, C, L, mA, mB, M->Wmix[t], h[t], h[t + 1], u0[t], st));
   }
-  MLIP_TRY(launch_energy(n, C, D, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
+  MLIP_TRY(launch_energy(ws, b, C, D, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
   if (d_forces || d_stress) {
     MLIP_TRY(ws.get("ef.g", Ec, &g));
     MLIP_TRY(ws.get("ef.Gm", ND, &Gm));
@@ -1577,21 +1566,15 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
     MLIP_CUDA_TRY(cudaMemsetAsync(GaB, 0, ND * sizeof(float), st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dr, 0, Ec * sizeof(float), st));
-    float* absmax = nullptr;
-    MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)T, &absmax));
-    MLIP_CUDA_TRY(cudaMemsetAsync(absmax, 0, 2 * T * sizeof(float), st));
+    float* absmax = nullptr;  // per system: max |h^t|, max |dE/dm|
+    MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)b.nsys, &absmax));
     for (int t = T - 1; t >= 0; --t) {
       MLIP_TRY(launch_mix_bwd2(n, C, L, GaA, GaB, u0[t], M->Wmix[t], Gm, st));
       MLIP_CUDA_TRY(cudaMemsetAsync(dz2, 0, Ec * 64 * sizeof(float), st));
-      if (!use_bf16) {
-        MLIP_PROF("absmax2", st);
-        absmax2<<<std::max(1, std::min(1024, (int)((ND + 1023) / 1024))), 256, 0, st>>>(ND, h[t], ND, Gm,
-                                                                                         absmax + 2 * t);
-        MLIP_LAUNCH_CHECK();
-      }
+      if (!use_bf16) MLIP_TRY(launch_seg_absmax2(b, D * C, h[t], Gm, absmax, st));
       MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], Gm,
                                    M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, GaA, GaB, GbA, GbB, dY,
-                                   dz2, use_bf16, absmax + 2 * t, flag + 1, st));
+                                   dz2, use_bf16, b.d_sys_of, absmax, flag + 1, st));
       MLIP_TRY(launch_radial_bwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, st));
       std::swap(GaA, GbA);
       std::swap(GaB, GbB);
@@ -1599,11 +1582,7 @@ int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species
     MLIP_TRY(launch_edge_grad(E, ev, dY, dr, g, st));
     double* fbuf = d_forces;
     if (!fbuf) MLIP_TRY(ws.get("ef.fscratch", (size_t)3 * std::max(n, 1), &fbuf));
-    const double vol = ca.any_pbc ? std::fabs(cell[0] * (cell[4] * cell[8] - cell[5] * cell[7]) -
-                                              cell[1] * (cell[3] * cell[8] - cell[5] * cell[6]) +
-                                              cell[2] * (cell[3] * cell[7] - cell[4] * cell[6]))
-                                  : 1.0;
-    MLIP_TRY(launch_forces_virial(ws, n, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, 1.0 / vol, st));
+    MLIP_TRY(launch_forces_virial(ws, b, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, st));
   }
   int hflag[2] = {0, 0};
   MLIP_CUDA_TRY(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, st));

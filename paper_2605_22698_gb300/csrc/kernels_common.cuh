@@ -133,8 +133,12 @@ __device__ __forceinline__ float warp_reduce16(const float* v) {
   return u[0];
 }
 
+// Lattice rows of every system of a batch on the device ([nsys][9], zero rows
+// for systems without a periodic axis) and the system of each atom (nullptr
+// for a batch of one).
 struct CellArg {
-  double h[9];
+  const double* cells;
+  const int* sys_of;
   int any_pbc;
 };
 

@@ -28,34 +28,46 @@ int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const
                     float* Gm, cudaStream_t st);
 int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st);
 int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st);
-int launch_energy(int n, int C, int D, const int* species, const float* W_out, const float* E0, const float* h,
-                  double* atom_e, double* energy, cudaStream_t st);
+// per-system energies energy[nsys] (FP64)
+int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, const int* species, const float* W_out,
+                  const float* E0, const float* h, double* atom_e, double* energy, cudaStream_t st);
 int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, float4* g, cudaStream_t st);
-int launch_forces_virial(Workspace& ws, int n, const int* row_ptr, const int* rev, const float4* g,
-                         const float4* ev, double* forces, double* stress, double inv_vol, cudaStream_t st);
+// forces[n][3]; stress[nsys][9] = virial / V per system (zero rows for systems
+// without a fully periodic cell), nullable
+int launch_forces_virial(Workspace& ws, const SystemBatch& b, const int* row_ptr, const int* rev, const float4* g,
+                         const float4* ev, double* forces, double* stress, cudaStream_t st);
+// out[s][k] = sum over the atoms of system s of v[i][k] (K = 1 or 9), times 1/V_s if scale_inv_vol
+int launch_seg_sum(Workspace& ws, const SystemBatch& b, int K, const double* v, bool scale_inv_vol, double* out,
+                   cudaStream_t st);
+// out[2s], out[2s+1] = max |a|, max |b| over the rows (row floats per atom) of system s
+int launch_seg_absmax2(const SystemBatch& b, int row, const float* a, const float* bb, float* out, cudaStream_t st);
 
 int launch_check_inputs(int n, const double* pos, const int* species, int S, int* flag, cudaStream_t st);
 int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::vector<size_t>& group_off);
 int umma_selftest_run(double* rel_err);
 int umma_selftest_mn_run(int variant, double* rel_err);
 
-// Plain FP32 energy/forces/stress of one system whose positions and species
-// are on the device.  d_energy, d_forces (n x 3), d_stress (9) are device
-// pointers (forces/stress nullable).
-int energy_forces_plain(mlip_model* M, const double* d_pos, const int* d_species, int64_t n, const double* cell,
-                        const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress,
-                        cudaStream_t st);
+// Energy, forces and stress of a batch of systems whose positions and species
+// are on the device (concatenated).  d_energy [nsys], d_forces [n][3] and
+// d_stress [nsys][9] are device pointers (forces and stress nullable).  The
+// batch must have been uploaded.
+int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st);
+// Fused 16-bit form (tcgen05 radial MLP and path products), same contract.
+int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st);
+// The model's form.
+int evaluate(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b, double* d_energy,
+             double* d_forces, double* d_stress, cudaStream_t st);
 
-// Fused BF16 form (tcgen05 radial MLP), same contract as energy_forces_plain.
-int energy_forces_fused(mlip_model* M, const double* d_pos, const int* d_species, int64_t n, const double* cell,
-                        const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress,
-                        cudaStream_t st);
-
-int launch_vv_kick(int n, const int* species, const double* mass, double half_dt, const double* F, double* vel,
-                   cudaStream_t st);
-int launch_vv_drift(int n, double dt, const double* vel, double* pos, cudaStream_t st);
-int launch_kinetic(int n, const int* species, const double* mass, const double* vel, double* out, cudaStream_t st);
-int energy_forces_device(mlip_model* M, const double* d_pos, const int* d_species, int64_t n, const double* cell,
-                         const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress, cudaStream_t st);
+// Velocity Verlet on a batch: systems with active[s] != 0 move with their own
+// time step dt[s] (fs); the others are left as they are.
+int launch_vv_kick(const SystemBatch& b, const int* species, const double* mass, const double* dt,
+                   const int* active, const double* F, double* vel, cudaStream_t st);
+int launch_vv_drift(const SystemBatch& b, const double* dt, const int* active, const double* vel, double* pos,
+                    cudaStream_t st);
+// ke[s] = sum over system s of m v^2 / (2 kappa)  (eV)
+int launch_kinetic(Workspace& ws, const SystemBatch& b, const int* species, const double* mass, const double* vel,
+                   double* ke, cudaStream_t st);
 
 }  // namespace mlip

@@ -13,70 +13,69 @@ namespace {
 
 constexpr double kKappa = 9.648533212e-3;
 
-__global__ void vv_kick(int n, const int* __restrict__ species, const double* __restrict__ mass, double half_dt,
-                        const double* __restrict__ F, double* __restrict__ vel) {
+// System of atom i (sys_of == nullptr: one system).
+__device__ __forceinline__ int sys_index(const int* sys_of, int i) { return sys_of ? sys_of[i] : 0; }
+
+__global__ void vv_kick(int n, const int* __restrict__ sys_of, const int* __restrict__ species,
+                        const double* __restrict__ mass, const double* __restrict__ dt,
+                        const int* __restrict__ active, const double* __restrict__ F, double* __restrict__ vel) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double a = half_dt * kKappa / mass[species[i]];
+  const int s = sys_index(sys_of, i);
+  if (active && !active[s]) return;
+  const double a = 0.5 * dt[s] * kKappa / mass[species[i]];
 #pragma unroll
   for (int k = 0; k < 3; ++k) vel[3 * i + k] += a * F[3 * i + k];
 }
 
-__global__ void vv_drift(int n, double dt, const double* __restrict__ vel, double* __restrict__ pos) {
+__global__ void vv_drift(int n, const int* __restrict__ sys_of, const double* __restrict__ dt,
+                         const int* __restrict__ active, const double* __restrict__ vel, double* __restrict__ pos) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int s = sys_index(sys_of, i);
+  if (active && !active[s]) return;
+  const double h = dt[s];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) pos[3 * i + k] += dt * vel[3 * i + k];
+  for (int k = 0; k < 3; ++k) pos[3 * i + k] += h * vel[3 * i + k];
 }
 
-// One block: KE = sum_i m v^2 / (2 kappa).
-__global__ void kinetic(int n, const int* __restrict__ species, const double* __restrict__ mass,
-                        const double* __restrict__ vel, double* __restrict__ out) {
-  __shared__ double part[32];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double v2 = vel[3 * i] * vel[3 * i] + vel[3 * i + 1] * vel[3 * i + 1] + vel[3 * i + 2] * vel[3 * i + 2];
-    acc += 0.5 * mass[species[i]] * v2 / kKappa;
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) *out = v;
-  }
+// ke_atom[i] = m_i v_i^2 / (2 kappa)
+__global__ void kinetic_atoms(int n, const int* __restrict__ species, const double* __restrict__ mass,
+                              const double* __restrict__ vel, double* __restrict__ ke_atom) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v2 = vel[3 * i] * vel[3 * i] + vel[3 * i + 1] * vel[3 * i + 1] + vel[3 * i + 2] * vel[3 * i + 2];
+  ke_atom[i] = 0.5 * mass[species[i]] * v2 / kKappa;
 }
 
 }  // namespace
 
-int launch_vv_kick(int n, const int* species, const double* mass, double half_dt, const double* F, double* vel,
-                   cudaStream_t st) {
+int launch_vv_kick(const SystemBatch& b, const int* species, const double* mass, const double* dt,
+                   const int* active, const double* F, double* vel, cudaStream_t st) {
+  const int n = (int)b.n;
   if (n <= 0) return MLIP_OK;
-  { MLIP_PROF("vv_kick", st); vv_kick<<<(n + 255) / 256, 256, 0, st>>>(n, species, mass, half_dt, F, vel); }
+  { MLIP_PROF("vv_kick", st); vv_kick<<<(n + 255) / 256, 256, 0, st>>>(n, b.d_sys_of, species, mass, dt, active, F, vel); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
-int launch_vv_drift(int n, double dt, const double* vel, double* pos, cudaStream_t st) {
+int launch_vv_drift(const SystemBatch& b, const double* dt, const int* active, const double* vel, double* pos,
+                    cudaStream_t st) {
+  const int n = (int)b.n;
   if (n <= 0) return MLIP_OK;
-  { MLIP_PROF("vv_drift", st); vv_drift<<<(n + 255) / 256, 256, 0, st>>>(n, dt, vel, pos); }
+  { MLIP_PROF("vv_drift", st); vv_drift<<<(n + 255) / 256, 256, 0, st>>>(n, b.d_sys_of, dt, active, vel, pos); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
-int launch_kinetic(int n, const int* species, const double* mass, const double* vel, double* out, cudaStream_t st) {
-  { MLIP_PROF("kinetic", st); kinetic<<<1, 1024, 0, st>>>(n, species, mass, vel, out); }
+int launch_kinetic(Workspace& ws, const SystemBatch& b, const int* species, const double* mass, const double* vel,
+                   double* ke, cudaStream_t st) {
+  const int n = (int)b.n;
+  double* ke_atom = nullptr;
+  MLIP_TRY(ws.get("md.ke_atom", (size_t)std::max(n, 1), &ke_atom));
+  if (n > 0) { MLIP_PROF("kinetic", st); kinetic_atoms<<<(n + 255) / 256, 256, 0, st>>>(n, species, mass, vel, ke_atom); }
   MLIP_LAUNCH_CHECK();
-  return MLIP_OK;
-}
-
-// Energy and forces of device-resident positions with the model's form.
-int energy_forces_device(mlip_model* M, const double* d_pos, const int* d_species, int64_t n, const double* cell,
-                         const uint8_t* pbc, double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
-  if (M->precision == MLIP_PREC_FP32)
-    return energy_forces_plain(M, d_pos, d_species, n, cell, pbc, d_energy, d_forces, d_stress, st);
-  return energy_forces_fused(M, d_pos, d_species, n, cell, pbc, d_energy, d_forces, d_stress, st);
+  return launch_seg_sum(ws, b, 1, ke_atom, false, ke, st);
 }
 
 }  // namespace mlip
@@ -105,20 +104,26 @@ extern "C" int mlip_md_nve(mlip_model* M, double* pos, double* vel, const int32_
     MLIP_CUDA_TRY(cudaMemcpyAsync(dz, species, sizeof(int) * n, cudaMemcpyHostToDevice, st));
     d_sp = dz;
   }
+  double* d_dt = nullptr;
   MLIP_TRY(ws.get("md.F", (size_t)3 * n, &d_F));
   MLIP_TRY(ws.get("md.E", 1, &d_E));
   MLIP_TRY(ws.get("md.mass", (size_t)M->S, &d_mass));
+  MLIP_TRY(ws.get("md.dt", 1, &d_dt));
   MLIP_TRY(ws.get("md.pe", (size_t)n_steps + 1, &d_pe));
   MLIP_TRY(ws.get("md.ke", (size_t)n_steps + 1, &d_ke));
   MLIP_CUDA_TRY(cudaMemcpyAsync(d_mass, M->masses.data(), sizeof(double) * M->S, cudaMemcpyHostToDevice, st));
-  MLIP_TRY(energy_forces_device(M, d_pos, d_sp, n, cell, pbc, d_pe, d_F, nullptr, st));
-  MLIP_TRY(launch_kinetic((int)n, d_sp, d_mass, d_vel, d_ke, st));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(d_dt, &dt_fs, sizeof(double), cudaMemcpyHostToDevice, st));
+  SystemBatch b;
+  single_system(b, n, cell, pbc);
+  MLIP_TRY(upload_batch(ws, M->stage, b, st));
+  MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe, d_F, nullptr, st));
+  MLIP_TRY(launch_kinetic(ws, b, d_sp, d_mass, d_vel, d_ke, st));
   for (int64_t s = 0; s < n_steps; ++s) {
-    MLIP_TRY(launch_vv_kick((int)n, d_sp, d_mass, 0.5 * dt_fs, d_F, d_vel, st));
-    MLIP_TRY(launch_vv_drift((int)n, dt_fs, d_vel, d_pos, st));
-    MLIP_TRY(energy_forces_device(M, d_pos, d_sp, n, cell, pbc, d_pe + s + 1, d_F, nullptr, st));
-    MLIP_TRY(launch_vv_kick((int)n, d_sp, d_mass, 0.5 * dt_fs, d_F, d_vel, st));
-    MLIP_TRY(launch_kinetic((int)n, d_sp, d_mass, d_vel, d_ke + s + 1, st));
+    MLIP_TRY(launch_vv_kick(b, d_sp, d_mass, d_dt, nullptr, d_F, d_vel, st));
+    MLIP_TRY(launch_vv_drift(b, d_dt, nullptr, d_vel, d_pos, st));
+    MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe + s + 1, d_F, nullptr, st));
+    MLIP_TRY(launch_vv_kick(b, d_sp, d_mass, d_dt, nullptr, d_F, d_vel, st));
+    MLIP_TRY(launch_kinetic(ws, b, d_sp, d_mass, d_vel, d_ke + s + 1, st));
   }
   const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (pe) MLIP_CUDA_TRY(cudaMemcpyAsync(pe, d_pe, sizeof(double) * (n_steps + 1), k, st));

@@ -82,6 +82,48 @@ struct NeighborList {
 int build_neighbors(Workspace& ws, const double* d_pos, int64_t n, const double* cell,
                     const uint8_t* pbc, double rc, bool want_rev, cudaStream_t st, NeighborList* out);
 
+// ----------------------------------------------------- batches of systems
+// Independent systems evaluated together as one graph: the disjoint union of
+// their neighbour graphs (no edge joins two systems).  Atoms of system s are
+// [atom_off[s], atom_off[s+1]) of the concatenated arrays.  Every per-system
+// reduction (energy, virial, kinetic energy) runs over fixed chunks counted
+// from the system's first atom, so a system's results do not depend on the
+// other systems of its batch.
+constexpr int kSegChunk = 1024;  // atoms per reduction chunk
+
+struct SystemBatch {
+  int nsys = 0;
+  int64_t n = 0;                      // total atoms
+  std::vector<int64_t> atom_off;      // [nsys + 1]
+  std::vector<double> cell;           // [nsys * 9] lattice rows
+  std::vector<uint8_t> pbc;           // [nsys * 3]
+  std::vector<int> chunk;             // [nchunk * 3]: system, first atom, end atom
+  std::vector<int> sys_chunk_off;     // [nsys + 1]: chunks of system s
+  // device copies (upload_batch)
+  int* d_sys_of = nullptr;            // [n] system of each atom
+  int* d_atom_off = nullptr;          // [nsys + 1]
+  double* d_cell = nullptr;           // [nsys * 9], zero rows for systems with no periodic axis
+  double* d_inv_vol = nullptr;        // [nsys], 1/V for fully periodic systems, else 0
+  int* d_chunk = nullptr;             // [nchunk * 3]
+  int* d_sys_chunk_off = nullptr;     // [nsys + 1]
+  int nchunk() const { return (int)(chunk.size() / 3); }
+  bool any_pbc() const {
+    for (uint8_t v : pbc)
+      if (v) return true;
+    return false;
+  }
+};
+
+// Fills the host tables of a batch (offsets, cells, pbc must be set) and
+// copies them to the device through the model's pinned staging.
+int upload_batch(Workspace& ws, HostStage& stage, SystemBatch& b, cudaStream_t st);
+// One system as a batch of one.
+void single_system(SystemBatch& b, int64_t n, const double* cell, const uint8_t* pbc);
+
+// Neighbour list of the disjoint union.  `b` must have been uploaded.
+int build_neighbors_batch(Workspace& ws, const double* d_pos, const SystemBatch& b, double rc, bool want_rev,
+                          cudaStream_t st, NeighborList* out);
+
 // exclusive scan of n int32 values into out[0..n] (out[n] = total)
 int exclusive_scan_i32(Workspace& ws, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
 

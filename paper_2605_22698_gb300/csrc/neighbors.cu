@@ -37,7 +37,13 @@ struct Grid {
   double rc, rc2;
   int max_bins, maxdeg;
   int any_pbc;
+  int bin_off;     // first bin of this system in the batch's bin arrays
 };
+
+// Grid of atom i: one per system of a batch (sys_of == nullptr: one system).
+__device__ __forceinline__ const Grid* grid_of(const Grid* g, const int* sys_of, int i) {
+  return sys_of ? g + sys_of[i] : g;
+}
 
 __device__ __forceinline__ long long dbl_order(double x) {
   long long b = __double_as_longlong(x);
@@ -47,12 +53,16 @@ __device__ __forceinline__ double order_dbl(long long b) {
   return __longlong_as_double(b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL));
 }
 
-__global__ void nl_frac(const double* __restrict__ pos, int n, const Grid* __restrict__ g,
-                        double* __restrict__ frac, int* __restrict__ img, long long* __restrict__ bbox) {
+__global__ void nl_frac(const double* __restrict__ pos, int n, const Grid* __restrict__ grids,
+                        const int* __restrict__ sys_of, double* __restrict__ frac, int* __restrict__ img,
+                        long long* __restrict__ bbox) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double f[3] = {0, 0, 0};
   bool valid = i < n;
+  int sys = 0;
   if (valid) {
+    if (sys_of) sys = sys_of[i];
+    const Grid* g = grids + sys;
     const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
     for (int k = 0; k < 3; ++k) {
       double s = __dadd_rn(__dadd_rn(__dmul_rn(x, g->inv[k]), __dmul_rn(y, g->inv[3 + k])), __dmul_rn(z, g->inv[6 + k]));
@@ -67,23 +77,35 @@ __global__ void nl_frac(const double* __restrict__ pos, int n, const Grid* __res
       frac[3 * i + k] = f[k];
     }
   }
-  // bounding box of open axes
+  // bounding box of open axes, per system: one atomic per warp when the
+  // warp's atoms all belong to one system, else one per atom
+  const int s0 = __shfl_sync(0xffffffffu, sys, 0);
+  const bool uniform = __all_sync(0xffffffffu, !valid || sys == s0);
   for (int k = 0; k < 3; ++k) {
     long long mn = valid ? dbl_order(f[k]) : LLONG_MAX;
     long long mx = valid ? dbl_order(f[k]) : LLONG_MIN;
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicMin(&bbox[2 * k], mn);
-      atomicMax(&bbox[2 * k + 1], mx);
+    if (uniform) {
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        atomicMin(&bbox[6 * s0 + 2 * k], mn);
+        atomicMax(&bbox[6 * s0 + 2 * k + 1], mx);
+      }
+    } else if (valid) {
+      atomicMin(&bbox[6 * sys + 2 * k], mn);
+      atomicMax(&bbox[6 * sys + 2 * k + 1], mx);
     }
   }
 }
 
-__global__ void nl_setup(Grid* g, const long long* bbox) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One thread per system.
+__global__ void nl_setup(Grid* grids, int nsys, const long long* bbox_all) {
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= nsys) return;
+  Grid* g = grids + sys;
+  const long long* bbox = bbox_all + 6 * sys;
   const double margin = 1.0 + 1e-6;
   double ext[3];
   for (int k = 0; k < 3; ++k) {
@@ -126,14 +148,15 @@ __device__ __forceinline__ void bin_coords(const Grid* g, const double* f, int* 
   }
 }
 
-__global__ void nl_bin(int n, const Grid* __restrict__ g, const double* __restrict__ frac,
-                       int* __restrict__ bin_of, int* __restrict__ counts) {
+__global__ void nl_bin(int n, const Grid* __restrict__ grids, const int* __restrict__ sys_of,
+                       const double* __restrict__ frac, int* __restrict__ bin_of, int* __restrict__ counts) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const Grid* g = grid_of(grids, sys_of, i);
   double f[3] = {frac[3 * i], frac[3 * i + 1], frac[3 * i + 2]};
   int b[3];
   bin_coords(g, f, b);
-  int bin = (b[0] * g->nb[1] + b[1]) * g->nb[2] + b[2];
+  int bin = g->bin_off + (b[0] * g->nb[1] + b[1]) * g->nb[2] + b[2];
   bin_of[i] = bin;
   atomicAdd(&counts[bin], 1);
 }
@@ -158,13 +181,15 @@ __device__ __forceinline__ unsigned long long make_key(int j, int s0, int s1, in
 // candidate list walked by all lanes at once (each lane finds its bin by a
 // binary search over the prefix with shuffles).  Matches are compacted with a
 // ballot into the receiver's slab (order irrelevant: nl_sort orders them).
-__global__ void nl_pairs_warp(int n, const Grid* __restrict__ g, const double* __restrict__ pos,
+__global__ void nl_pairs_warp(int n, const Grid* __restrict__ grids, const int* __restrict__ sys_of,
+                              const double* __restrict__ pos,
                               const double* __restrict__ frac, const int* __restrict__ img,
                               const int* __restrict__ bin_start, const int* __restrict__ bin_atoms,
                               unsigned long long* __restrict__ slab, int* __restrict__ deg, int* __restrict__ flags) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
+  const Grid* g = grid_of(grids, sys_of, i);
   const int maxdeg = g->maxdeg;
   double f[3] = {frac[3 * i], frac[3 * i + 1], frac[3 * i + 2]};
   int b[3];
@@ -190,7 +215,7 @@ __global__ void nl_pairs_warp(int n, const Grid* __restrict__ g, const double* _
       if (g->pbc[1]) { q1 = (int)floor((double)c1 / g->nb[1]); c1 -= q1 * g->nb[1]; } else ok = ok && c1 >= 0 && c1 < g->nb[1];
       if (g->pbc[2]) { q2 = (int)floor((double)c2 / g->nb[2]); c2 -= q2 * g->nb[2]; } else ok = ok && c2 >= 0 && c2 < g->nb[2];
       if (ok) {
-        const int bin = (c0 * g->nb[1] + c1) * g->nb[2] + c2;
+        const int bin = g->bin_off + (c0 * g->nb[1] + c1) * g->nb[2] + c2;
         beg = bin_start[bin];
         len = bin_start[bin + 1] - beg;
       }
@@ -413,31 +438,56 @@ static bool invert3(const double* h, double* inv, double* det_out) {
   return true;
 }
 
-int build_neighbors(Workspace& ws, const double* d_pos, int64_t n64, const double* cell,
-                    const uint8_t* pbc, double rc, bool want_rev, cudaStream_t st, NeighborList* out) {
-  if (n64 < 0 || n64 > (1LL << 30)) { set_error("neighbors: bad atom count %lld", (long long)n64); return MLIP_ERR_INVALID_ARG; }
-  if (!(rc > 0)) { set_error("neighbors: cutoff must be positive"); return MLIP_ERR_INVALID_ARG; }
-  const int n = (int)n64;
-  out->n = n;
-  Grid hg{};
-  hg.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
-  if (hg.any_pbc) {
+// Cell geometry of one system: inverse, lattice rows, perpendicular widths.
+static int make_grid(const double* cell, const uint8_t* pbc, double rc, int64_t n_atoms, Grid* hg) {
+  *hg = Grid{};
+  hg->any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
+  if (hg->any_pbc) {
     double det;
-    if (!invert3(cell, hg.inv, &det)) { set_error("neighbors: singular cell with a periodic axis"); return MLIP_ERR_CELL; }
-    for (int k = 0; k < 9; ++k) hg.h[k] = cell[k];
+    if (!invert3(cell, hg->inv, &det)) { set_error("neighbors: singular cell with a periodic axis"); return MLIP_ERR_CELL; }
+    for (int k = 0; k < 9; ++k) hg->h[k] = cell[k];
     for (int k = 0; k < 3; ++k) {
       // width = 1 / |column k of h^-1|
-      double c2 = hg.inv[k] * hg.inv[k] + hg.inv[3 + k] * hg.inv[3 + k] + hg.inv[6 + k] * hg.inv[6 + k];
-      hg.w[k] = 1.0 / std::sqrt(c2);
-      hg.pbc[k] = pbc[k] ? 1 : 0;
+      double c2 = hg->inv[k] * hg->inv[k] + hg->inv[3 + k] * hg->inv[3 + k] + hg->inv[6 + k] * hg->inv[6 + k];
+      hg->w[k] = 1.0 / std::sqrt(c2);
+      hg->pbc[k] = pbc[k] ? 1 : 0;
     }
   } else {
-    for (int k = 0; k < 9; ++k) { hg.inv[k] = (k % 4 == 0) ? 1.0 : 0.0; hg.h[k] = 0.0; }
-    for (int k = 0; k < 3; ++k) { hg.w[k] = 1.0; hg.pbc[k] = 0; }
+    for (int k = 0; k < 9; ++k) { hg->inv[k] = (k % 4 == 0) ? 1.0 : 0.0; hg->h[k] = 0.0; }
+    for (int k = 0; k < 3; ++k) { hg->w[k] = 1.0; hg->pbc[k] = 0; }
   }
-  hg.rc = rc;
-  hg.rc2 = rc * rc;
-  hg.max_bins = (int)std::min<int64_t>(std::max<int64_t>(64, 4 * (int64_t)n), 1 << 24);
+  hg->rc = rc;
+  hg->rc2 = rc * rc;
+  hg->max_bins = (int)std::min<int64_t>(std::max<int64_t>(64, 4 * n_atoms), 1 << 24);
+  return MLIP_OK;
+}
+
+int build_neighbors(Workspace& ws, const double* d_pos, int64_t n64, const double* cell,
+                    const uint8_t* pbc, double rc, bool want_rev, cudaStream_t st, NeighborList* out) {
+  SystemBatch b;
+  single_system(b, n64, cell, pbc);
+  b.d_sys_of = nullptr;  // one system: no per-atom table needed
+  return build_neighbors_batch(ws, d_pos, b, rc, want_rev, st, out);
+}
+
+int build_neighbors_batch(Workspace& ws, const double* d_pos, const SystemBatch& b, double rc, bool want_rev,
+                          cudaStream_t st, NeighborList* out) {
+  const int64_t n64 = b.n;
+  if (n64 < 0 || n64 > (1LL << 30)) { set_error("neighbors: bad atom count %lld", (long long)n64); return MLIP_ERR_INVALID_ARG; }
+  if (!(rc > 0)) { set_error("neighbors: cutoff must be positive"); return MLIP_ERR_INVALID_ARG; }
+  if (b.nsys < 1) { set_error("neighbors: empty batch"); return MLIP_ERR_INVALID_ARG; }
+  if (b.nsys > 1 && !b.d_sys_of && n64 > 0) { set_error("neighbors: batch not uploaded"); return MLIP_ERR_INVALID_ARG; }
+  const int n = (int)n64, nsys = b.nsys;
+  out->n = n;
+  std::vector<Grid> hg(nsys);
+  int64_t total_bins = 0;
+  for (int s = 0; s < nsys; ++s) {
+    MLIP_TRY(make_grid(&b.cell[9 * s], &b.pbc[3 * s], rc, b.atom_off[s + 1] - b.atom_off[s], &hg[s]));
+    hg[s].bin_off = (int)total_bins;
+    total_bins += hg[s].max_bins;
+  }
+  if (total_bins > (1LL << 30)) { set_error("neighbors: batch too large (%lld bins)", (long long)total_bins); return MLIP_ERR_INVALID_ARG; }
+  const int nbins = (int)total_bins;
 
   Grid* dg = nullptr;
   double* frac = nullptr;
@@ -445,44 +495,45 @@ int build_neighbors(Workspace& ws, const double* d_pos, int64_t n64, const doubl
       *bin_atoms = nullptr, *deg = nullptr, *flags = nullptr;
   long long* bbox = nullptr;
   const int nn = std::max(n, 1);
-  MLIP_TRY(ws.get("nl.grid", 1, &dg));
+  MLIP_TRY(ws.get("nl.grid", (size_t)nsys, &dg));
   MLIP_TRY(ws.get("nl.frac", (size_t)3 * nn, &frac));
   MLIP_TRY(ws.get("nl.img", (size_t)3 * nn, &img));
   MLIP_TRY(ws.get("nl.bin_of", (size_t)nn, &bin_of));
-  MLIP_TRY(ws.get("nl.counts", (size_t)hg.max_bins + 1, &counts));
-  MLIP_TRY(ws.get("nl.bin_start", (size_t)hg.max_bins + 1, &bin_start));
-  MLIP_TRY(ws.get("nl.cursor", (size_t)hg.max_bins + 1, &cursor));
+  MLIP_TRY(ws.get("nl.counts", (size_t)nbins + 1, &counts));
+  MLIP_TRY(ws.get("nl.bin_start", (size_t)nbins + 1, &bin_start));
+  MLIP_TRY(ws.get("nl.cursor", (size_t)nbins + 1, &cursor));
   MLIP_TRY(ws.get("nl.bin_atoms", (size_t)nn, &bin_atoms));
   MLIP_TRY(ws.get("nl.deg", (size_t)nn, &deg));
   MLIP_TRY(ws.get("nl.flags", 4, &flags));
-  MLIP_TRY(ws.get("nl.bbox", 6, &bbox));
+  MLIP_TRY(ws.get("nl.bbox", (size_t)6 * nsys, &bbox));
   MLIP_TRY(ws.get("nl.row_ptr", (size_t)nn + 1, &out->row_ptr));
+  std::vector<long long> bb_init(6 * (size_t)nsys);
+  for (int s = 0; s < nsys; ++s)
+    for (int k = 0; k < 3; ++k) {
+      bb_init[6 * s + 2 * k] = LLONG_MAX;
+      bb_init[6 * s + 2 * k + 1] = LLONG_MIN;
+    }
 
   int maxdeg = 256;
   const int threads = 128;
   const int blocks = (n + threads - 1) / threads;
   for (int attempt = 0; attempt < 6; ++attempt) {
-    hg.maxdeg = maxdeg;
-    long long bb_init[6] = {LLONG_MAX, LLONG_MIN, LLONG_MAX, LLONG_MIN, LLONG_MAX, LLONG_MIN};
-    MLIP_CUDA_TRY(cudaMemcpyAsync(dg, &hg, sizeof(Grid), cudaMemcpyHostToDevice, st));
-    MLIP_CUDA_TRY(cudaMemcpyAsync(bbox, bb_init, sizeof(bb_init), cudaMemcpyHostToDevice, st));
+    for (auto& g : hg) g.maxdeg = maxdeg;
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dg, hg.data(), sizeof(Grid) * nsys, cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(bbox, bb_init.data(), sizeof(long long) * bb_init.size(), cudaMemcpyHostToDevice, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
-    MLIP_CUDA_TRY(cudaMemsetAsync(counts, 0, ((size_t)hg.max_bins + 1) * sizeof(int), st));
-    MLIP_CUDA_TRY(cudaMemsetAsync(cursor, 0, ((size_t)hg.max_bins + 1) * sizeof(int), st));
-    if (n > 0) {
-      { MLIP_PROF("nl_frac", st); nl_frac<<<blocks, threads, 0, st>>>(d_pos, n, dg, frac, img, bbox); }
-      { MLIP_PROF("nl_setup", st); nl_setup<<<1, 1, 0, st>>>(dg, bbox); }
-      { MLIP_PROF("nl_bin", st); nl_bin<<<blocks, threads, 0, st>>>(n, dg, frac, bin_of, counts); }
-    } else {
-      { MLIP_PROF("nl_setup", st); nl_setup<<<1, 1, 0, st>>>(dg, bbox); }
-    }
+    MLIP_CUDA_TRY(cudaMemsetAsync(counts, 0, ((size_t)nbins + 1) * sizeof(int), st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(cursor, 0, ((size_t)nbins + 1) * sizeof(int), st));
+    if (n > 0) { MLIP_PROF("nl_frac", st); nl_frac<<<blocks, threads, 0, st>>>(d_pos, n, dg, b.d_sys_of, frac, img, bbox); }
+    { MLIP_PROF("nl_setup", st); nl_setup<<<(nsys + 127) / 128, 128, 0, st>>>(dg, nsys, bbox); }
+    if (n > 0) { MLIP_PROF("nl_bin", st); nl_bin<<<blocks, threads, 0, st>>>(n, dg, b.d_sys_of, frac, bin_of, counts); }
     MLIP_LAUNCH_CHECK();
-    MLIP_TRY(exclusive_scan_i32(ws, counts, bin_start, hg.max_bins, st));
+    MLIP_TRY(exclusive_scan_i32(ws, counts, bin_start, nbins, st));
     unsigned long long* slab = nullptr;
     MLIP_TRY(ws.get("nl.slab", (size_t)nn * maxdeg, &slab));
     if (n > 0) {
       { MLIP_PROF("nl_scatter", st); nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms); }
-      { MLIP_PROF("nl_pairs", st); nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, d_pos, frac, img, bin_start, bin_atoms, slab, deg, flags); }
+      { MLIP_PROF("nl_pairs", st); nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, b.d_sys_of, d_pos, frac, img, bin_start, bin_atoms, slab, deg, flags); }
       MLIP_LAUNCH_CHECK();
     }
     MLIP_TRY(exclusive_scan_i32(ws, deg, out->row_ptr, n, st));
@@ -664,24 +715,10 @@ extern "C" int mlip_neighbors_noalloc(const double* pos, int64_t n64, const doub
   MLIP_TRY(noalloc_scratch(&base));
 
   Grid hg{};
-  hg.any_pbc = (pbc[0] || pbc[1] || pbc[2]) ? 1 : 0;
-  if (hg.any_pbc) {
-    double det;
-    if (!invert3(cell, hg.inv, &det)) { set_error("neighbors (no-alloc): singular cell with a periodic axis"); return MLIP_ERR_CELL; }
-    for (int k = 0; k < 9; ++k) hg.h[k] = cell[k];
-    for (int k = 0; k < 3; ++k) {
-      const double c2 = hg.inv[k] * hg.inv[k] + hg.inv[3 + k] * hg.inv[3 + k] + hg.inv[6 + k] * hg.inv[6 + k];
-      hg.w[k] = 1.0 / std::sqrt(c2);
-      hg.pbc[k] = pbc[k] ? 1 : 0;
-    }
-  } else {
-    for (int k = 0; k < 9; ++k) { hg.inv[k] = (k % 4 == 0) ? 1.0 : 0.0; hg.h[k] = 0.0; }
-    for (int k = 0; k < 3; ++k) { hg.w[k] = 1.0; hg.pbc[k] = 0; }
-  }
-  hg.rc = cutoff;
-  hg.rc2 = cutoff * cutoff;
+  MLIP_TRY(make_grid(cell, pbc, cutoff, n, &hg));
   hg.max_bins = std::max(64, 4 * n);
   hg.maxdeg = kNoAllocMaxDegree;
+  hg.bin_off = 0;
 
   const size_t nn = (size_t)std::max(n, 1);
   Carve cv{static_cast<unsigned char*>(base), 0, kNoAllocScratchBytes};
@@ -710,17 +747,18 @@ extern "C" int mlip_neighbors_noalloc(const double* pos, int64_t n64, const doub
   MLIP_CUDA_TRY(cudaMemsetAsync(cursor, 0, ((size_t)hg.max_bins + 1) * sizeof(int), st));
   const int threads = 128, blocks = (n + threads - 1) / threads;
   if (n > 0) {
-    nl_frac<<<blocks, threads, 0, st>>>(pos, n, dg, frac, img, bbox);
-    nl_setup<<<1, 1, 0, st>>>(dg, bbox);
-    nl_bin<<<blocks, threads, 0, st>>>(n, dg, frac, bin_of, counts);
+    nl_frac<<<blocks, threads, 0, st>>>(pos, n, dg, nullptr, frac, img, bbox);
+    nl_setup<<<1, 32, 0, st>>>(dg, 1, bbox);
+    nl_bin<<<blocks, threads, 0, st>>>(n, dg, nullptr, frac, bin_of, counts);
   } else {
-    nl_setup<<<1, 1, 0, st>>>(dg, bbox);
+    nl_setup<<<1, 32, 0, st>>>(dg, 1, bbox);
   }
   MLIP_LAUNCH_CHECK();
   MLIP_TRY(scan_fixed(counts, bin_start, hg.max_bins, bsum, st));
   if (n > 0) {
     nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms);
-    nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, pos, frac, img, bin_start, bin_atoms, slab, deg, flags);
+    nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, nullptr, pos, frac, img, bin_start, bin_atoms, slab, deg,
+                                               flags);
     MLIP_LAUNCH_CHECK();
   }
   MLIP_TRY(scan_fixed(deg, row_ptr, n, bsum, st));

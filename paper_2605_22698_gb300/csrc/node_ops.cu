@@ -3,7 +3,7 @@
 // edge gradients from dE/dY and dE/dr, forces and virial in FP64.
 #include <algorithm>
 
-#include "kernels_common.cuh"
+#include "launchers.cuh"
 #include "profile.cuh"
 
 namespace mlip {
@@ -48,21 +48,6 @@ __global__ void readout(int n, int C, int D, const int* __restrict__ species, co
   if (lane == 0) atom_e[i] = (double)acc + (double)E0[z];
 }
 
-// Deterministic FP64 sum of n values (one block).
-__global__ void sum_f64(int n, const double* __restrict__ x, double* __restrict__ out) {
-  __shared__ double part[32];
-  double acc = 0.0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) acc += x[k];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) *out = v;
-  }
-}
-
 // g_e = dr r^ + (1/r)(I - r^ r^T) grad(Y . dY)
 __global__ void edge_grad(int E, const float4* __restrict__ ev, const float* __restrict__ dY,
                           const float* __restrict__ dr, float4* __restrict__ g) {
@@ -84,52 +69,33 @@ __global__ void edge_grad(int E, const float4* __restrict__ ev, const float* __r
   }
 }
 
-// F_i = sum_{e in seg(i)} (g_e - g_rev(e)) in FP64; per-block virial partials
-// sum_e x_e (x) g_e (FP64).
+// F_i = sum_{e in seg(i)} (g_e - g_rev(e)) in FP64; per-atom virial
+// sum_{e in seg(i)} x_e (x) g_e (FP64) when vir is not null.
 __global__ void forces_virial(int n, const int* __restrict__ row_ptr, const int* __restrict__ rev,
                               const float4* __restrict__ g, const float4* __restrict__ ev,
-                              double* __restrict__ forces, double* __restrict__ vir_part) {
-  __shared__ double part[9][32];
+                              double* __restrict__ forces, double* __restrict__ vir) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
   double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  if (i < n) {
-    double f0 = 0, f1 = 0, f2 = 0;
-    for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-      const float4 a = g[e], b = g[rev[e]], x = ev[e];
-      f0 += (double)a.x - (double)b.x;
-      f1 += (double)a.y - (double)b.y;
-      f2 += (double)a.z - (double)b.z;
-      const double xe[3] = {x.x, x.y, x.z}, ge[3] = {a.x, a.y, a.z};
+  double f0 = 0, f1 = 0, f2 = 0;
+  for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+    const float4 a = g[e], b = g[rev[e]], x = ev[e];
+    f0 += (double)a.x - (double)b.x;
+    f1 += (double)a.y - (double)b.y;
+    f2 += (double)a.z - (double)b.z;
+    const double xe[3] = {x.x, x.y, x.z}, ge[3] = {a.x, a.y, a.z};
 #pragma unroll
-      for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) v[3 * p + q] += xe[p] * ge[q];
-    }
-    forces[3 * i] = f0;
-    forces[3 * i + 1] = f1;
-    forces[3 * i + 2] = f2;
+      for (int q = 0; q < 3; ++q) v[3 * p + q] += xe[p] * ge[q];
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  forces[3 * i] = f0;
+  forces[3 * i + 1] = f1;
+  forces[3 * i + 2] = f2;
+  if (vir) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    double x = v[k];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) part[k][w] = x;
+    for (int k = 0; k < 9; ++k) vir[(size_t)i * 9 + k] = v[k];
   }
-  __syncthreads();
-  if (threadIdx.x < 9) {
-    double s = 0;
-    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) s += part[threadIdx.x][ww];
-    vir_part[(size_t)blockIdx.x * 9 + threadIdx.x] = s;
-  }
-}
-
-__global__ void virial_finish(int nb, const double* __restrict__ vir_part, double inv_vol, double* __restrict__ stress) {
-  const int k = threadIdx.x;
-  if (k >= 9) return;
-  double s = 0;
-  for (int b = 0; b < nb; ++b) s += vir_part[(size_t)b * 9 + k];
-  stress[k] = s * inv_vol;
 }
 
 }  // namespace
@@ -148,12 +114,12 @@ int launch_grad_init(int n, int C, int D, const int* species, const float* W_out
   return MLIP_OK;
 }
 
-int launch_energy(int n, int C, int D, const int* species, const float* W_out, const float* E0, const float* h,
-                  double* atom_e, double* energy, cudaStream_t st) {
+int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, const int* species, const float* W_out,
+                  const float* E0, const float* h, double* atom_e, double* energy, cudaStream_t st) {
+  const int n = (int)b.n;
   if (n > 0) { MLIP_PROF("readout", st); readout<<<(n + 7) / 8, 256, 0, st>>>(n, C, D, species, W_out, E0, h, atom_e); }
-  { MLIP_PROF("sum_f64", st); sum_f64<<<1, 1024, 0, st>>>(n, atom_e, energy); }
   MLIP_LAUNCH_CHECK();
-  return MLIP_OK;
+  return launch_seg_sum(ws, b, 1, atom_e, false, energy, st);
 }
 
 int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, float4* g, cudaStream_t st) {
@@ -163,15 +129,17 @@ int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, 
   return MLIP_OK;
 }
 
-int launch_forces_virial(Workspace& ws, int n, const int* row_ptr, const int* rev, const float4* g,
-                         const float4* ev, double* forces, double* stress, double inv_vol, cudaStream_t st) {
-  if (n <= 0) return MLIP_OK;
-  const int nb = (n + 127) / 128;
-  double* part = nullptr;
-  MLIP_TRY(ws.get("fv.part", (size_t)nb * 9, &part));
-  { MLIP_PROF("forces_virial", st); forces_virial<<<nb, 128, 0, st>>>(n, row_ptr, rev, g, ev, forces, part); }
-  if (stress) { MLIP_PROF("virial_finish", st); virial_finish<<<1, 32, 0, st>>>(nb, part, inv_vol, stress); }
-  MLIP_LAUNCH_CHECK();
+int launch_forces_virial(Workspace& ws, const SystemBatch& b, const int* row_ptr, const int* rev, const float4* g,
+                         const float4* ev, double* forces, double* stress, cudaStream_t st) {
+  const int n = (int)b.n;
+  double* vir = nullptr;
+  if (stress) MLIP_TRY(ws.get("fv.vir", (size_t)std::max(n, 1) * 9, &vir));
+  if (n > 0) {
+    MLIP_PROF("forces_virial", st);
+    forces_virial<<<(n + 127) / 128, 128, 0, st>>>(n, row_ptr, rev, g, ev, forces, vir);
+    MLIP_LAUNCH_CHECK();
+  }
+  if (stress) MLIP_TRY(launch_seg_sum(ws, b, 9, vir, true, stress, st));
   return MLIP_OK;
 }
 

@@ -50,3 +50,41 @@ def test_params_file_roundtrip_layout(tmp_path):
     assert raw[:8] == b"MLIPPRM1"
     tail = np.frombuffer(raw[-4 * w.size:], dtype="<f4")
     np.testing.assert_array_equal(tail, w)
+
+
+_LAYOUT_C = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "mlip.h"
+#define F(T, m) printf(#T " " #m " %zu\n", offsetof(T, m));
+#define Z(T) printf(#T " sizeof %zu\n", sizeof(T));
+int main(void) {
+  F(mlip_model_desc, cutoff) F(mlip_model_desc, masses) Z(mlip_model_desc)
+  F(mlip_serve_config, max_slots) F(mlip_serve_config, bucket_edges) F(mlip_serve_config, device_poll_limit_us)
+  Z(mlip_serve_config)
+  F(mlip_request, n) F(mlip_request, pos) F(mlip_request, cell) F(mlip_request, pbc) F(mlip_request, vel)
+  F(mlip_request, seed) F(mlip_request, dt_fs) Z(mlip_request)
+  F(mlip_result, energy) F(mlip_result, stress) F(mlip_result, forces) F(mlip_result, ke) F(mlip_result, t_done)
+  Z(mlip_result)
+  F(mlip_serve_statistics, elapsed_s) F(mlip_serve_statistics, device_bytes) F(mlip_serve_statistics, n_buckets)
+  F(mlip_serve_statistics, bucket_count) F(mlip_serve_statistics, bucket_p99_ms) Z(mlip_serve_statistics)
+  return 0;
+}
+"""
+
+
+def test_struct_layouts_match_the_header(lib, tmp_path):
+    """The binding's ctypes structures have the C header's offsets and sizes."""
+    import os
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text(_LAYOUT_C)
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    for line in out.strip().splitlines():
+        tname, field, val = line.split()
+        T = getattr(lib, tname)
+        got = ctypes.sizeof(T) if field == "sizeof" else getattr(T, field).offset
+        assert got == int(val), (tname, field, got, val)

@@ -1,0 +1,187 @@
+"""GPU checks of the serving engine (continuous batching).
+
+Every request's result must equal the single-system call on its own (alone vs
+in a mix), bit for bit: the batch evaluation is independent of the other
+systems in it, and the velocity-Verlet updates are per atom.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    torch.cuda.init()
+    from paper_2605_22698_gb300 import build
+    build.build()
+    from paper_2605_22698_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _model(B, prec):
+    spec = synth.model_spec("water")
+    w = synth.make_weights(spec, 21)
+    p = {"fp32": B.MLIP_PREC_FP32, "f16": B.MLIP_PREC_F16}[prec]
+    return B.Model(spec, w, p), spec
+
+
+def _mix():
+    """Open clusters of the serving size mix plus one periodic box."""
+    out = []
+    for n, seed in [(40, 1), (230, 2), (8, 3), (900, 4), (120, 5), (2000, 6)]:
+        s = synth.cluster(n, seed=seed)
+        out.append(s)
+    out.append(synth.water_box(100, synth.water_side_for(100), seed=2))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16"])
+def test_energy_forces_requests_match_single_calls(B, prec):
+    m, _ = _model(B, prec)
+    ref_model, _ = _model(B, prec)
+    systems = _mix()
+    srv = B.Server(m, max_slots=64)
+    ids = []
+    for k, s in enumerate(systems):
+        ids.append(srv.submit(B.MLIP_REQ_ENERGY_FORCES, s.pos, s.species, cell=s.cell, pbc=s.pbc,
+                              want_stress=bool(s.pbc.all())))
+    res = [srv.wait(i, 60000) for i in ids]
+    st = srv.stats()
+    srv.close()
+    for s, r in zip(systems, res):
+        assert r["status"] == 0
+        one = ref_model.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=bool(s.pbc.all()))
+        assert r["energy"] == one["energy"][0]
+        assert np.array_equal(r["forces"], one["forces"])
+        if s.pbc.all():
+            assert np.array_equal(r["stress"], one["stress"])
+        assert r["t_arrive"] <= r["t_admit"] <= r["t_done"]
+    assert st["completed"] == len(systems) and st["failed"] == 0
+    assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16"])
+def test_nve_requests_match_single_trajectories(B, prec):
+    """NVE requests of different lengths and time steps, mixed with energy+forces
+    requests that come and go: each trajectory equals mlip_md_nve alone."""
+    m, spec = _model(B, prec)
+    ref_model, _ = _model(B, prec)
+    systems = _mix()[:5]
+    masses = np.asarray(spec.masses)
+    srv = B.Server(m, max_slots=16)
+    nve = []
+    for k, s in enumerate(systems[:3]):
+        v = synth.maxwell_boltzmann(masses[s.species], 300.0, seed=10 + k)
+        steps, dt = [6, 3, 9][k], [0.5, 0.25, 0.5][k]
+        nve.append((s, v, steps, dt, srv.submit(B.MLIP_REQ_NVE, s.pos, s.species, cell=s.cell, pbc=s.pbc,
+                                                 vel=v, n_steps=steps, dt_fs=dt)))
+    ef = [srv.submit(B.MLIP_REQ_ENERGY_FORCES, s.pos, s.species, cell=s.cell, pbc=s.pbc) for s in systems[3:]]
+    for s, v, steps, dt, rid in nve:
+        r = srv.wait(rid, 120000)
+        assert r["status"] == 0
+        pos, vel, pe, ke = ref_model.md_nve(s.pos, v, s.species, s.cell, s.pbc, dt, steps)
+        assert np.array_equal(r["pe"], pe) and np.array_equal(r["ke"], ke)
+        assert np.array_equal(r["pos"], pos) and np.array_equal(r["vel"], vel)
+    for rid in ef:
+        assert srv.wait(rid, 60000)["status"] == 0
+    st = srv.stats()
+    srv.close()
+    assert st["iterations"] >= 10  # the longest run takes n_steps + 1 = 10 evaluations
+    assert st["mean_batch_requests"] > 1.0
+
+
+def test_maxwell_boltzmann_velocities(B):
+    """vel = NULL: velocities from SplitMix64 normals by Box-Muller with the
+    centre-of-mass velocity removed (the same recipe as synth.maxwell_boltzmann)."""
+    m, spec = _model(B, "fp32")
+    s = synth.cluster(50, seed=8)
+    srv = B.Server(m)
+    rid = srv.submit(B.MLIP_REQ_NVE, s.pos, s.species, temperature_K=450.0, seed=77, n_steps=0, dt_fs=0.5)
+    r = srv.wait(rid, 60000)
+    srv.close()
+    ref = synth.maxwell_boltzmann(np.asarray(spec.masses)[s.species], 450.0, seed=77)
+    assert np.abs(r["vel"] - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert np.array_equal(r["pos"], s.pos)
+    assert len(r["pe"]) == 1
+
+
+def test_budget_slots_and_lifecycle(B):
+    m, _ = _model(B, "f16")
+    systems = _mix()[:4]
+    # a budget of 200 MB holds under 2000 atoms of this model: 4000 are rejected
+    srv = B.Server(m, hbm_budget_bytes=200 << 20, max_slots=2, bucket_edges=(100, 1000))
+    big = synth.cluster(4000, seed=9)
+    with pytest.raises(B.MlipError) as e:
+        srv.submit(B.MLIP_REQ_ENERGY_FORCES, big.pos, big.species)
+    assert e.value.code == B.MLIP_ERR_BUDGET
+    ids = [srv.submit(B.MLIP_REQ_ENERGY_FORCES, s.pos, s.species) for s in systems]
+    long_id = srv.submit(B.MLIP_REQ_NVE, systems[1].pos, systems[1].species, n_steps=1000, dt_fs=0.5, seed=3)
+    for i in ids:
+        assert srv.wait(i, 60000)["status"] == 0
+    with pytest.raises(B.MlipError) as e:  # still running
+        srv.wait(long_id, 0)
+    assert e.value.code == B.MLIP_ERR_TIMEOUT
+    assert srv.release(long_id) == B.MLIP_PENDING
+    r = srv.wait(long_id, 300000)
+    assert r["status"] == 0 and len(r["pe"]) == 1001
+    assert srv.release(long_id) == 0
+    with pytest.raises(B.MlipError) as e:
+        srv.poll(long_id)
+    assert e.value.code == B.MLIP_ERR_NOT_FOUND
+    st = srv.stats()
+    srv.close()
+    assert st["rejected"] == 1 and st["completed"] == 5
+    assert st["mean_batch_requests"] <= 2.0
+    assert sum(st["bucket_count"]) == 5 and len(st["bucket_count"]) == 3
+
+
+def test_invalid_requests(B):
+    m, _ = _model(B, "fp32")
+    s = synth.cluster(30, seed=1)
+    srv = B.Server(m)
+    bad = s.species.copy()
+    bad[3] = 7
+    for kw, code in [(dict(species=bad), B.MLIP_ERR_INVALID_ARG),
+                     (dict(want_stress=True), B.MLIP_ERR_CELL)]:
+        args = dict(pos=s.pos, species=s.species)
+        args.update(kw)
+        with pytest.raises(B.MlipError) as e:
+            srv.submit(B.MLIP_REQ_ENERGY_FORCES, args.pop("pos"), args.pop("species"), **args)
+        assert e.value.code == code
+    p = s.pos.copy()
+    p[0, 0] = np.nan
+    with pytest.raises(B.MlipError) as e:
+        srv.submit(B.MLIP_REQ_ENERGY_FORCES, p, s.species)
+    assert e.value.code == B.MLIP_ERR_INVALID_ARG
+    with pytest.raises(B.MlipError) as e:
+        srv.submit(B.MLIP_REQ_NVE, s.pos, s.species, n_steps=5, dt_fs=-1.0)
+    assert e.value.code == B.MLIP_ERR_INVALID_ARG
+    rid = srv.submit(B.MLIP_REQ_ENERGY_FORCES, s.pos, s.species)
+    assert srv.wait(rid, 60000)["status"] == 0
+    srv.close()
+
+
+def test_host_wait_limit_stops_the_server(B):
+    """device_poll_limit_us bounds the host's wait for an iteration; a limit of
+    1 us runs out (a host-side timeout, the GPU work itself completes): the
+    requests fail with MLIP_ERR_DEVICE_TIMEOUT and the server admits nothing."""
+    m, _ = _model(B, "fp32")
+    s = synth.cluster(1500, seed=4)
+    srv = B.Server(m, device_poll_limit_us=1)
+    rid = srv.submit(B.MLIP_REQ_NVE, s.pos, s.species, n_steps=50, dt_fs=0.5, seed=1)
+    r = srv.wait(rid, 120000)
+    assert r["status"] == B.MLIP_ERR_DEVICE_TIMEOUT
+    with pytest.raises(B.MlipError) as e:
+        srv.submit(B.MLIP_REQ_ENERGY_FORCES, s.pos, s.species)
+    assert e.value.code == B.MLIP_ERR_DEVICE_TIMEOUT
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == 1
+    # the model is usable again once the server is gone
+    out = m.energy_forces(s.pos, s.species, s.cell, s.pbc)
+    assert np.isfinite(out["energy"][0])
