@@ -131,6 +131,10 @@ def sample_workload(name: str):
         spec = synth.model_spec("fcc")
         return spec, synth.make_weights(spec, 31), synth.fcc((3, 3, 4), seed=3), \
             "FCC 3x3x4 cells (144 atoms), same model"
+    if name == "serve":
+        spec = synth.model_spec("water")
+        return spec, synth.make_weights(spec, 21), synth.cluster(200, seed=4), \
+            "one 200-atom open cluster (the median request size) energy+forces, same model"
     spec = synth.model_spec("small")
     return spec, synth.make_weights(spec, 7), synth.cluster64(1), "the full 64-atom cluster"
 
@@ -266,7 +270,6 @@ def run_ours(args, rank, world):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_dev = float(tt.item())
     value = world * s.n * args.steps / t_dev
-    E_edges = int(sum(1 for _ in range(0)))  # filled below
     # edge count of this structure (for the algorithmic counts)
     r, _, _ = B.mlip_neighbors(np.ascontiguousarray(s.pos), s.cell, s.pbc, spec.rc)
     E_edges = len(r)
@@ -316,6 +319,28 @@ def run_ours(args, rank, world):
     for k_, v in sorted(kern.items(), key=lambda kv: -kv[1][1])[:8]:
         share[k_] = round(v[1] / tot_all, 4)
 
+    # the plain FP32 form on the same workload, reported beside the headline form
+    plain = None
+    if args.precision != "fp32" and not args.no_plain:
+        pm = B.Model(spec, w, B.MLIP_PREC_FP32)
+
+        def pstep():
+            pm.energy_forces(pos, sp, s.cell, s.pbc, forces=True, stress=stress, stream=stream, out=out)
+        for _ in range(3):
+            pstep()
+        kp = max(5, args.steps // 4)
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kp)]
+        for k in range(kp):
+            flush.zero_()
+            pev[k][0].record(stream)
+            pstep()
+            pev[k][1].record(stream)
+        torch.cuda.synchronize()
+        tp = sum(a.elapsed_time(b) for a, b in pev) / 1e3
+        plain = {"precision": "fp32", "value": round(world * s.n * kp / tp, 1), "unit": UNIT, "steps": kp,
+                 "ms_per_step": round(1e3 * tp / kp, 4)}
+        pm.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(args.workload, args.cpu_seconds)
@@ -329,8 +354,112 @@ def run_ours(args, rank, world):
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (512 MB write)", "stress": stress},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernel_share": share,
+        "plain_fp32": plain,
         "cpu_baseline": cpu, "clocks": clocks, "wall_s": round(t_wall, 3),
         "peaks": peaks(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serve_requests(n_requests: int, seed: int, rate: float):
+    """The serving mix: Poisson arrivals, N = floor(exp U(ln 8, ln 5000)) atoms
+    in an open cube at 0.1 atoms/A^3 (d_min 0.9 A, 4 species), 70 % energy+forces,
+    30 % 100-step NVE at dt 0.5 fs from Maxwell-Boltzmann velocities at 300 K."""
+    reqs = synth.serving_stream(n_requests, rate_per_s=rate, seed=seed)
+    systems = [synth.cluster(r.n, seed=r.seed) for r in reqs]
+    return reqs, systems
+
+
+def run_serve(args, rank, world):
+    import torch
+    from paper_2605_22698_gb300 import binding as B
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    spec = synth.model_spec("water")
+    w = synth.make_weights(spec, 21)
+    prec = {"fp32": B.MLIP_PREC_FP32, "bf16": B.MLIP_PREC_BF16, "f16": B.MLIP_PREC_F16}[args.precision]
+    model = B.Model(spec, w, prec)
+    R = args.requests
+    edges = (100, 1000)
+
+    def submit(srv, r, sy):
+        if r.kind == 1:
+            return srv.submit(B.MLIP_REQ_NVE, sy.pos, sy.species, n_steps=r.n_steps, dt_fs=r.dt_fs,
+                              temperature_K=r.temperature_K, seed=r.seed)
+        return srv.submit(B.MLIP_REQ_ENERGY_FORCES, sy.pos, sy.species)
+
+    def atom_evals(reqs):
+        return sum(r.n * (r.n_steps + 1 if r.kind == 1 else 1) for r in reqs)
+
+    # warm-up: a few requests through a throw-away server (workspace growth)
+    reqs, systems = serve_requests(min(R, 16), 100 + rank, 1.0)
+    srv = B.Server(model, bucket_edges=edges)
+    for i in [submit(srv, r, sy) for r, sy in zip(reqs, systems)]:
+        srv.wait(i)
+    srv.close()
+
+    # phase 1: saturated (every request queued at once)
+    reqs, systems = serve_requests(R, 4 + rank, 1.0)
+    srv = B.Server(model, bucket_edges=edges)
+    l0 = B.mlip_launch_count()
+    t0 = time.perf_counter()
+    ids = [submit(srv, r, sy) for r, sy in zip(reqs, systems)]
+    for i in ids:
+        assert srv.wait(i)["status"] == 0
+    t_sat = time.perf_counter() - t0
+    launches = B.mlip_launch_count() - l0
+    st_sat = srv.stats()
+    srv.close()
+    ae = atom_evals(reqs)
+    sat_rps = R / t_sat
+
+    # phase 2: open loop at 0.7x the saturated request rate
+    lam = 0.7 * sat_rps
+    reqs2, systems2 = serve_requests(R, 5 + rank, lam)
+    srv = B.Server(model, bucket_edges=edges)
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ids2 = []
+    t0 = time.perf_counter()
+    for r, sy in zip(reqs2, systems2):
+        dt = r.t_arrive - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        ids2.append(submit(srv, r, sy))
+    res2 = [srv.wait(i) for i in ids2]
+    t_open = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    clocks = sampler.stop() if sampler else None
+    assert all(r["status"] == 0 for r in res2)
+    ae2 = atom_evals(reqs2)
+    line = {
+        "metric": METRIC, "value": round(world * ae / t_sat, 1), "unit": UNIT, "n_gpus": world, "steps": R,
+        "warmup": 16, "ms_per_step": round(1e3 * t_sat / R, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32",
+                                       "f16": "f16 tensor-core MLP + f32"}[args.precision],
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": "serve", "requests": R, "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}",
+                   "precision": args.precision, "mix": "70% E+F, 30% 100-step NVE; N = exp U(ln 8, ln 5000)",
+                   "step": "one request (value: atom-evaluations/s with every request queued at once)",
+                   "l2": "inputs change every iteration (no flush)"},
+        "latency": {"rate_per_s": round(lam, 2), "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
+                    "mean_ms": round(st["mean_ms"], 2), "max_ms": round(st["max_ms"], 2),
+                    "throughput_atom_steps_per_s": round(ae2 / t_open, 1),
+                    "buckets_atoms": ["<=100", "101-1000", ">1000"],
+                    "bucket_p50_ms": [round(x, 2) for x in st["bucket_p50_ms"]],
+                    "bucket_p99_ms": [round(x, 2) for x in st["bucket_p99_ms"]],
+                    "mean_batch_atoms": round(st["mean_batch_atoms"], 1),
+                    "mean_batch_requests": round(st["mean_batch_requests"], 2)},
+        "saturated": {"requests_per_s": round(sat_rps, 2), "p50_ms": round(st_sat["p50_ms"], 2),
+                      "p99_ms": round(st_sat["p99_ms"], 2), "busy_atom_steps_per_s": round(st_sat["atom_steps_per_s"], 1),
+                      "iterations": st_sat["iterations"], "mean_batch_atoms": round(st_sat["mean_batch_atoms"], 1)},
+        "e2e": {"value": round(world * ae / t_sat, 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(sy.n * 28 for sy in systems) / R),
+                "d2h_bytes_per_step": int(sum(sy.n * 24 * (3 if r.kind == 1 else 1) + 16 * (r.n_steps + 1)
+                                              for r, sy in zip(reqs, systems)) / R)},
+        "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -367,11 +496,13 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="water3000", choices=["water3000", "fcc108k", "cluster64"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "f16"])
+    ap.add_argument("--workload", default="water3000", choices=["water3000", "fcc108k", "cluster64", "serve"])
+    ap.add_argument("--precision", default="f16", choices=["fp32", "bf16", "f16"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form beside the headline")
+    ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -385,7 +516,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    run_ours(args, rank, world)
+    if args.workload == "serve":
+        run_serve(args, rank, world)
+    else:
+        run_ours(args, rank, world)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
