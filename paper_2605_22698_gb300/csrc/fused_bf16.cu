@@ -246,17 +246,26 @@ __device__ __forceinline__ void load_group_table(float* tab_c, uint8_t* tab_y) {
 
 // Per tile: receiver/sender ids and harmonics (threads < kNT), then the
 // products cY[t][k] = c_k Y_t[i2_k] by all threads.
+// With s_dws (adjoint): s_dws[t], s_dws[kNT + t] = the scale of edge t's
+// system and its inverse (dws2[system], see dw_scales).
 template <int NZ, int NZP>
 __device__ __forceinline__ void tile_setup(int tile, int E0, int E1, const int* __restrict__ recv,
                                            const int* __restrict__ send, const float* __restrict__ Yg, int* s_recv,
                                            int* s_send, float* sY, float* cY, const float* tab_c,
-                                           const uint8_t* tab_y) {
+                                           const uint8_t* tab_y, const int* __restrict__ sys_of = nullptr,
+                                           const float2* __restrict__ dws2 = nullptr, float* s_dws = nullptr) {
   const int tid = threadIdx.x;
   if (tid < kNT) {
     const int e = tile * kNT + tid;
     const bool valid = e >= E0 && e < E1;
-    s_recv[tid] = valid ? recv[e] : -1;
+    const int r = valid ? recv[e] : -1;
+    s_recv[tid] = r;
     s_send[tid] = valid ? send[e] : 0;
+    if (s_dws) {
+      const float2 v = valid ? dws2[sys_of ? sys_of[r] : 0] : make_float2(1.0f, 1.0f);
+      s_dws[tid] = v.x;
+      s_dws[kNT + tid] = v.y;
+    }
   }
   for (int q = tid; q < kNT * 4; q += blockDim.x) {  // 16 floats per edge as float4
     const int t = q >> 2, e = tile * kNT + t;
@@ -914,7 +923,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
                                                          int first_group, float* __restrict__ dY,
                                                          float* __restrict__ dz2, int use_bf16,
                                                          const int* __restrict__ sys_of,
-                                                         const float* __restrict__ absmax, int* __restrict__ err) {
+                                                         const float2* __restrict__ dws2, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using BL = BwdLayout<L, MODE>;
   constexpr int D = NodeDims<L>::D;
@@ -939,7 +948,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
   uint64_t* bar_mma2 = bars + 4;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 5);
   __shared__ int abort_s;
-  __shared__ float s_dws[kNT];  // per-edge scale of dE/dw in the second product
+  __shared__ float s_dws[2 * kNT];  // per-edge scale of dE/dw in the second product, and its inverse
 
   const int tid = threadIdx.x, warp = tid >> 5, wsid = warp >> 2, c = tid & 127;
   float* GoutW = wsid == 0 ? GoutA : GoutB;
@@ -1024,21 +1033,8 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
         abort_s = 1;
       }
     }
-    if (tid < kNT) {
-      // dE/dw enters the second product scaled by a power of two (FP16
-      // operands), chosen per system from its own maxima:
-      // |dE/dw| <= 17 max|h| s max|Gm| (orthonormal CG rows, |Y| <= 1), so the
-      // scale 2^floor(log2(2^14 / (32 max|h| s max|Gm|))) keeps it below 2^14.
-      const int e = tile * kNT + tid;
-      float sc = 1.0f;
-      if (!use_bf16 && e >= E0 && e < E1) {
-        const int sy = sys_of ? sys_of[recv[e]] : 0;
-        const float U = 32.0f * absmax[2 * sy] * s * absmax[2 * sy + 1];
-        sc = U > 0.0f ? exp2f(fminf(fmaxf(floorf(log2f(16384.0f / U)), -60.0f), 60.0f)) : 1.0f;
-      }
-      s_dws[tid] = sc;
-    }
-    tile_setup<BL::NZ, BL::NZP>(tile, E0, E1, recv, send, Yg, s_recv, s_send, sY, cY, tab_c, tab_y);
+    tile_setup<BL::NZ, BL::NZP>(tile, E0, E1, recv, send, Yg, s_recv, s_send, sY, cY, tab_c, tab_y, sys_of, dws2,
+                                s_dws);
     __syncthreads();
     if (abort_s) break;
     if (!tc::mbar_wait(bar_mma, (uint32_t)(it & 1))) {
@@ -1119,7 +1115,7 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int e = tile * kNT + ch * 8 + j;
-          if (e >= E0 && e < E1) atomicAdd(&dz2[(size_t)e * 64 + tid], v[j] / s_dws[ch * 8 + j]);
+          if (e >= E0 && e < E1) atomicAdd(&dz2[(size_t)e * 64 + tid], v[j] * s_dws[kNT + ch * 8 + j]);
         }
       }
     }
@@ -1154,6 +1150,22 @@ __global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __res
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, BL::NCOLS);
+}
+
+// Per-system scale of dE/dw in the adjoint's second product (FP16 operands)
+// and its inverse: |dE/dw| <= 17 max|h| s max|Gm| (orthonormal CG rows,
+// |Y| <= 1), so the power of two 2^floor(log2(2^14 / (32 max|h| s max|Gm|)))
+// keeps the scaled values below 2^14.  BF16 operands: no scale.
+__global__ void dw_scales(int nsys, const float* __restrict__ absmax, float s, int use_bf16,
+                          float2* __restrict__ dws2) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nsys) return;
+  float sc = 1.0f;
+  if (!use_bf16) {
+    const float U = 32.0f * absmax[2 * q] * s * absmax[2 * q + 1];
+    sc = U > 0.0f ? exp2f(fminf(fmaxf(floorf(log2f(16384.0f / U)), -60.0f), 60.0f)) : 1.0f;
+  }
+  dws2[q] = make_float2(sc, 1.0f / sc);  // powers of two: the inverse is exact
 }
 
 // ------------------------------------------------------------- self test
@@ -1300,7 +1312,7 @@ template <int L, int MODE>
 int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send, const float* Yg,
                      const float* hprev, const float* Gm, const uint8_t* w3img, const uint8_t* z2t, float s,
                      const float* GinA, const float* GinB, float* GoutA, float* GoutB, int first_group, float* dY,
-                     float* dz2, int use_bf16, const int* sys_of, const float* absmax, int* err, int blocks,
+                     float* dz2, int use_bf16, const int* sys_of, const float2* dws2, int* err, int blocks,
                      cudaStream_t st) {
   using BL = BwdLayout<L, MODE>;
   const size_t smem = BL::bytes;
@@ -1310,7 +1322,7 @@ int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send
     MLIP_PROF("tp_fused_bwd", st);
     tp_fused_bwd<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img, z2t, s, GinA,
                                                           GinB, GoutA, GoutB, first_group, dY, dz2, use_bf16, sys_of,
-                                                          absmax,
+                                                          dws2,
                                                           err);
   }
   MLIP_LAUNCH_CHECK();
@@ -1404,7 +1416,7 @@ int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int*
                         const float* Yg, const float* hprev, const float* Gm, const uint8_t* w3img,
                         const std::vector<size_t>& goff, const uint8_t* z2t, float s, const float* GinA,
                         const float* GinB, float* GoutA, float* GoutB, float* dY, float* dz2, int use_bf16,
-                        const int* sys_of, const float* absmax, int* err, cudaStream_t st) {
+                        const int* sys_of, const float2* dws2, int* err, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -1412,7 +1424,7 @@ int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int*
   const int blocks = sms;
 #define MLIP_GB(LL, MM, GI)                                                                                  \
   MLIP_TRY((launch_group_bwd<LL, MM>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img + goff[GI], z2t, s, GinA, GinB, \
-                                     GoutA, GoutB, GI == 0, dY, dz2, use_bf16, sys_of, absmax, err, blocks, st)))
+                                     GoutA, GoutB, GI == 0, dY, dz2, use_bf16, sys_of, dws2, err, blocks, st)))
   if (L == 2) {
     if (first) { MLIP_GB(2, -1, 0); }
     else { MLIP_GB(2, 0, 0); MLIP_GB(2, 1, 1); MLIP_GB(2, 2, 2); }
@@ -1567,14 +1579,21 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
     MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dr, 0, Ec * sizeof(float), st));
     float* absmax = nullptr;  // per system: max |h^t|, max |dE/dm|
+    float2* dws2 = nullptr;   // per system: scale of dE/dw and its inverse
     MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)b.nsys, &absmax));
+    MLIP_TRY(ws.get("fz.dws2", (size_t)b.nsys, &dws2));
     for (int t = T - 1; t >= 0; --t) {
       MLIP_TRY(launch_mix_bwd2(n, C, L, GaA, GaB, u0[t], M->Wmix[t], Gm, st));
       MLIP_CUDA_TRY(cudaMemsetAsync(dz2, 0, Ec * 64 * sizeof(float), st));
       if (!use_bf16) MLIP_TRY(launch_seg_absmax2(b, D * C, h[t], Gm, absmax, st));
+      {
+        MLIP_PROF("dw_scales", st);
+        dw_scales<<<(b.nsys + 127) / 128, 128, 0, st>>>(b.nsys, absmax, s, use_bf16, dws2);
+        MLIP_LAUNCH_CHECK();
+      }
       MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], Gm,
                                    M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, GaA, GaB, GbA, GbB, dY,
-                                   dz2, use_bf16, b.d_sys_of, absmax, flag + 1, st));
+                                   dz2, use_bf16, b.d_sys_of, dws2, flag + 1, st));
       MLIP_TRY(launch_radial_bwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, st));
       std::swap(GaA, GbA);
       std::swap(GaB, GbB);
