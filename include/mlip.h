@@ -195,6 +195,17 @@ int mlip_md_nve(mlip_model* model, double* pos, double* vel, const int32_t* spec
                 const double cell[9], const uint8_t pbc[3], double dt_fs, int64_t n_steps, double* pe,
                 double* ke, int on_device, void* stream);
 
+/* Velocity-Verlet NVE trajectories of a batch of independent systems (the
+ * replicas of a batched MD run) advanced together: every step evaluates all
+ * systems as one graph (see mlip_energy_forces_batch) with the same time step.
+ * atom_off, cells, pbc as in mlip_energy_forces_batch (host arrays); pos, vel:
+ * [n][3] in/out; species [n]; pe, ke: [n_steps + 1][n_systems] (row k: after
+ * step k) or NULL.  Each system's trajectory equals mlip_md_nve on that system
+ * alone.  Errors as mlip_md_nve. */
+int mlip_md_nve_batch(mlip_model* model, int32_t n_systems, const int64_t* atom_off, double* pos, double* vel,
+                      const int32_t* species, const double* cells, const uint8_t* pbc, double dt_fs,
+                      int64_t n_steps, double* pe, double* ke, int on_device, void* stream);
+
 /* ------------------------------------------------------------- serving
  * Continuous batching of independent requests (the paper's batched
  * inference and MD serving, Introduction and "NPT ensemble simulations"):

@@ -67,6 +67,7 @@ def lib():
         L.mlip_energy_forces_batch.argtypes = [P, i32, P, P, P, P, P, P, P, P, i32, P]
         L.mlip_neighbors_noalloc.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), P]
         L.mlip_md_nve.argtypes = [P, P, P, P, i64, P, P, f64, i64, P, P, i32, P]
+        L.mlip_md_nve_batch.argtypes = [P, i32, P, P, P, P, P, P, f64, i64, P, P, i32, P]
         L.mlip_selftest.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         L.mlip_profile_enable.argtypes = [i32]
         L.mlip_launch_count.restype = ctypes.c_longlong
@@ -254,6 +255,31 @@ def mlip_md_nve(h, pos, vel, species, cell, pbc, dt_fs: float, n_steps: int, str
     return pos, vel, pe, ke
 
 
+def mlip_md_nve_batch(h, atom_off, pos, vel, species, cells, pbc, dt_fs: float, n_steps: int, stream=None):
+    """Velocity-Verlet NVE of a batch of systems (atoms of system s are
+    atom_off[s]:atom_off[s+1] of the concatenated arrays).  numpy inputs: copies
+    are integrated and returned; torch CUDA tensors: integrated in place.
+    Returns (pos, vel, pe [n_steps+1, n_sys], ke [n_steps+1, n_sys])."""
+    off = np.ascontiguousarray(atom_off, dtype=np.int64)
+    ns = len(off) - 1
+    cells = np.ascontiguousarray(cells, dtype=np.float64).reshape(ns, 9)
+    pbc = np.ascontiguousarray(pbc, dtype=np.uint8).reshape(ns, 3)
+    if isinstance(pos, np.ndarray):
+        pos = np.array(pos, dtype=np.float64, copy=True)
+        vel = np.array(vel, dtype=np.float64, copy=True)
+        species = np.ascontiguousarray(species, dtype=np.int32)
+        pe = np.zeros((n_steps + 1, ns)); ke = np.zeros((n_steps + 1, ns))
+    else:
+        import torch
+        pe = torch.zeros((n_steps + 1, ns), dtype=torch.float64, device=pos.device)
+        ke = torch.zeros_like(pe)
+    pp, dev = _ptr(pos)
+    _check(lib().mlip_md_nve_batch(h, ns, off.ctypes.data_as(ctypes.c_void_p), pp, _ptr(vel)[0], _ptr(species)[0],
+                                   cells.ctypes.data_as(ctypes.c_void_p), pbc.ctypes.data_as(ctypes.c_void_p),
+                                   dt_fs, n_steps, _ptr(pe)[0], _ptr(ke)[0], dev, _stream_ptr(stream)))
+    return pos, vel, pe, ke
+
+
 def mlip_selftest(which: int) -> float:
     r = ctypes.c_double(0.0)
     _check(lib().mlip_selftest(which, ctypes.byref(r)))
@@ -294,6 +320,9 @@ class Model:
 
     def md_nve(self, pos, vel, species, cell, pbc, dt_fs, n_steps, stream=None):
         return mlip_md_nve(self.h, pos, vel, species, cell, pbc, dt_fs, n_steps, stream)
+
+    def md_nve_batch(self, atom_off, pos, vel, species, cells, pbc, dt_fs, n_steps, stream=None):
+        return mlip_md_nve_batch(self.h, atom_off, pos, vel, species, cells, pbc, dt_fs, n_steps, stream)
 
     def close(self):
         if getattr(self, "h", None):

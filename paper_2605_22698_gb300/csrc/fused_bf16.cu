@@ -814,7 +814,9 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
   constexpr int DH = S::dh(W);
   constexpr int NG = FIRST ? 1 : G::NOUT;
   constexpr int SBO2 = G::NP * 2048;
-  constexpr int PK = S::ypack(W), NVP = 16 / PK, NV = S::nyv(W);
+  // dE/dY: the NV components of PK consecutive edges packed into one 32-value
+  // channel butterfly (PK = floor(32 / NV); the tile's last group may be short)
+  constexpr int NV = S::nyv(W), PK = 32 / NV;
   constexpr std::array<int, 16> yl = S::ylist(W);
   const int c = threadIdx.x & 127, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int yl_rt[16];
@@ -855,9 +857,9 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
   float hw[kPF][DH], gw[kPF][NG];
 #pragma unroll
   for (int k = 0; k < kPF; ++k) gather(k, hw[k], gw[k]);
-  float pv[16];
+  float pv[32];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) pv[i] = 0.0f;
+  for (int i = 0; i < 32; ++i) pv[i] = 0.0f;
 #pragma unroll 1
   for (int t = 0; t < kNT; ++t) {
     float wv[G::NP];
@@ -899,13 +901,16 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
       });
     }
 #pragma unroll
-    for (int i = 0; i < NVP * (PK - 1); ++i) pv[i] = pv[i + NVP];
+    for (int i = 0; i < NV * (PK - 1); ++i) pv[i] = pv[i + NV];
 #pragma unroll
-    for (int i = 0; i < NVP; ++i) pv[NVP * (PK - 1) + i] = i < NV ? dYp[yl[i < NV ? i : 0]] : 0.0f;
-    if ((t % PK) == PK - 1) {
-      const float tot = warp_reduce16(pv);
-      const int v = lane >> 1, vi = v % NVP, te = t - (PK - 1) + v / NVP;
-      if ((lane & 1) == 0 && vi < NV) red[(warp * kNT + te) * 16 + yl_rt[vi]] = tot;
+    for (int i = 0; i < NV; ++i) pv[NV * (PK - 1) + i] = dYp[yl[i]];
+    const int slot = t % PK;
+    if (slot == PK - 1 || t == kNT - 1) {
+      const float tot = warp_reduce32(pv);
+      // lane v holds the total of value v: edge t - (PK - 1) + v / NV, component v % NV;
+      // slots older than this group's first edge were written by the previous group
+      const int te = t - (PK - 1) + lane / NV, vi = lane % NV;
+      if (lane < PK * NV && te >= t - slot) red[(warp * kNT + te) * 16 + yl_rt[vi]] = tot;
     }
   }
 }

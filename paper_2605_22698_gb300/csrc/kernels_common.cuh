@@ -133,6 +133,30 @@ __device__ __forceinline__ float warp_reduce16(const float* v) {
   return u[0];
 }
 
+// Sum 32 values over the 32 lanes; lane l ends with the total of value l.
+__device__ __forceinline__ float warp_reduce32(const float* v) {
+  const int lane = threadIdx.x & 31;
+  float u[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const bool hi = lane & 16;
+    const float send = hi ? v[k] : v[k + 16];
+    const float keep = hi ? v[k + 16] : v[k];
+    u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int w = 8; w >= 1; w >>= 1) {
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const bool hi = lane & w;
+      const float send = hi ? u[k] : u[k + w];
+      const float keep = hi ? u[k + w] : u[k];
+      u[k] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return u[0];
+}
+
 // Lattice rows of every system of a batch on the device ([nsys][9], zero rows
 // for systems without a periodic axis) and the system of each atom (nullptr
 // for a batch of one).

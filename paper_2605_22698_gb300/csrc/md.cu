@@ -135,3 +135,67 @@ extern "C" int mlip_md_nve(mlip_model* M, double* pos, double* vel, const int32_
   MLIP_CUDA_TRY(cudaStreamSynchronize(st));
   return MLIP_OK;
 }
+
+extern "C" int mlip_md_nve_batch(mlip_model* M, int32_t n_systems, const int64_t* atom_off, double* pos, double* vel,
+                                 const int32_t* species, const double* cells, const uint8_t* pbc, double dt_fs,
+                                 int64_t n_steps, double* pe, double* ke, int on_device, void* stream) {
+  if (!M || !atom_off || !pos || !vel || !species || !cells || !pbc) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  if (n_systems < 1 || n_systems > (1 << 20)) { set_error("system count %d out of range", n_systems); return MLIP_ERR_INVALID_ARG; }
+  if (n_steps < 0 || !(dt_fs > 0)) { set_error("bad step count or time step"); return MLIP_ERR_INVALID_ARG; }
+  if ((int)M->masses.size() != M->S) { set_error("the model has no masses (needed for MD)"); return MLIP_ERR_INVALID_ARG; }
+  if (atom_off[0] != 0) { set_error("atom_off[0] must be 0"); return MLIP_ERR_INVALID_ARG; }
+  for (int s = 0; s < n_systems; ++s)
+    if (atom_off[s + 1] <= atom_off[s]) { set_error("system %d has no atoms (atom_off must increase)", s); return MLIP_ERR_INVALID_ARG; }
+  const int64_t n = atom_off[n_systems];
+  if (n > (1LL << 28)) { set_error("atom count %lld out of range", (long long)n); return MLIP_ERR_INVALID_ARG; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Workspace& ws = M->ws;
+  double *d_pos = pos, *d_vel = vel, *d_F = nullptr, *d_mass = nullptr, *d_pe = nullptr, *d_ke = nullptr,
+         *d_dt = nullptr;
+  const int* d_sp = species;
+  if (!on_device) {
+    for (int64_t i = 0; i < n; ++i)
+      if (species[i] < 0 || species[i] >= M->S) { set_error("species[%lld] out of range", (long long)i); return MLIP_ERR_INVALID_ARG; }
+    int* dz = nullptr;
+    MLIP_TRY(ws.get("md.pos", (size_t)3 * n, &d_pos));
+    MLIP_TRY(ws.get("md.vel", (size_t)3 * n, &d_vel));
+    MLIP_TRY(ws.get("md.species", (size_t)n, &dz));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(d_vel, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dz, species, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    d_sp = dz;
+  }
+  const size_t traces = (size_t)(n_steps + 1) * n_systems;
+  MLIP_TRY(ws.get("md.F", (size_t)3 * n, &d_F));
+  MLIP_TRY(ws.get("md.mass", (size_t)M->S, &d_mass));
+  MLIP_TRY(ws.get("md.dt", (size_t)n_systems, &d_dt));
+  MLIP_TRY(ws.get("md.pe", traces, &d_pe));
+  MLIP_TRY(ws.get("md.ke", traces, &d_ke));
+  std::vector<double> hdt((size_t)n_systems, dt_fs);
+  MLIP_CUDA_TRY(cudaMemcpyAsync(d_mass, M->masses.data(), sizeof(double) * M->S, cudaMemcpyHostToDevice, st));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(d_dt, hdt.data(), sizeof(double) * n_systems, cudaMemcpyHostToDevice, st));
+  SystemBatch b;
+  b.nsys = n_systems;
+  b.atom_off.assign(atom_off, atom_off + n_systems + 1);
+  b.cell.assign(cells, cells + 9 * (size_t)n_systems);
+  b.pbc.assign(pbc, pbc + 3 * (size_t)n_systems);
+  MLIP_TRY(upload_batch(ws, M->stage, b, st));
+  MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe, d_F, nullptr, st));
+  MLIP_TRY(launch_kinetic(ws, b, d_sp, d_mass, d_vel, d_ke, st));
+  for (int64_t s = 0; s < n_steps; ++s) {
+    MLIP_TRY(launch_vv_kick(b, d_sp, d_mass, d_dt, nullptr, d_F, d_vel, st));
+    MLIP_TRY(launch_vv_drift(b, d_dt, nullptr, d_vel, d_pos, st));
+    MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe + (s + 1) * n_systems, d_F, nullptr, st));
+    MLIP_TRY(launch_vv_kick(b, d_sp, d_mass, d_dt, nullptr, d_F, d_vel, st));
+    MLIP_TRY(launch_kinetic(ws, b, d_sp, d_mass, d_vel, d_ke + (s + 1) * n_systems, st));
+  }
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (pe) MLIP_CUDA_TRY(cudaMemcpyAsync(pe, d_pe, sizeof(double) * traces, k, st));
+  if (ke) MLIP_CUDA_TRY(cudaMemcpyAsync(ke, d_ke, sizeof(double) * traces, k, st));
+  if (!on_device) {
+    MLIP_CUDA_TRY(cudaMemcpyAsync(pos, d_pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(vel, d_vel, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+  }
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  return MLIP_OK;
+}

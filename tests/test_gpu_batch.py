@@ -100,3 +100,24 @@ def test_batch_errors(B):
     # the model stays usable after the errors
     E, F, _ = m.energy_forces_batch(systems)
     assert np.isfinite(E).all()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "f16"])
+def test_batched_md_equals_single_trajectories(B, prec):
+    """Replicas advanced together (mlip_md_nve_batch) follow the trajectories
+    each one follows alone (mlip_md_nve), bit for bit."""
+    m, spec, _ = _model(B, prec)
+    masses = np.asarray(spec.masses)
+    reps = [synth.water_box(60, synth.water_side_for(60), seed=30 + k) for k in range(3)]
+    vels = [synth.maxwell_boltzmann(masses[r.species], 300.0, seed=40 + k) for k, r in enumerate(reps)]
+    off = np.cumsum([0] + [r.n for r in reps])
+    pos = np.concatenate([r.pos for r in reps])
+    vel = np.concatenate(vels)
+    sp = np.concatenate([r.species for r in reps])
+    cells = np.stack([r.cell for r in reps])
+    pbc = np.stack([r.pbc for r in reps])
+    P, V, PE, KE = m.md_nve_batch(off, pos, vel, sp, cells, pbc, 0.5, 8)
+    for k, r in enumerate(reps):
+        p1, v1, pe1, ke1 = m.md_nve(r.pos, vels[k], r.species, r.cell, r.pbc, 0.5, 8)
+        assert np.array_equal(P[off[k]:off[k + 1]], p1) and np.array_equal(V[off[k]:off[k + 1]], v1)
+        assert np.array_equal(PE[:, k], pe1) and np.array_equal(KE[:, k], ke1)
