@@ -67,10 +67,11 @@ struct Group {
     return a;
   }
   static constexpr std::array<int, NP> paths = make_paths();
-  // offset of each member path's entries in the group's entry list
+  // offset of each member path's entries in the group's entry list; every
+  // path starts on a multiple of 4 (16-byte vector loads), padding entries zero
   static constexpr std::array<int, NP + 1> make_eoff() {
     std::array<int, NP + 1> a{};
-    for (int s = 0; s < NP; ++s) a[s + 1] = a[s] + Tab::off[paths[s] + 1] - Tab::off[paths[s]];
+    for (int s = 0; s < NP; ++s) a[s + 1] = a[s] + ((Tab::off[paths[s] + 1] - Tab::off[paths[s]] + 3) & ~3);
     return a;
   }
   static constexpr std::array<int, NP + 1> eoff = make_eoff();
@@ -241,6 +242,10 @@ __device__ __forceinline__ void load_group_table(float* tab_c, uint8_t* tab_y) {
         tab_y[gb + k - kb] = (uint8_t)i2;
       }
     });
+    if (tid >= gb + (ke - kb) && tid < G::eoff[sl + 1]) {  // padding up to the next path
+      tab_c[tid] = 0.0f;
+      tab_y[tid] = 0;
+    }
   });
 }
 
@@ -323,6 +328,10 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
 }
 
 // ---------------------------------------------------------------- tp_fused
+// CTAs of a fused kernel that fit on one SM by shared memory (at most 2):
+// the register budget per thread follows from it (128 for 2, 255 for 1).
+constexpr int ctas_per_sm(size_t smem_bytes) { return (smem_bytes + 2048) * 2 <= 232448 ? 2 : 1; }
+
 template <int L, int MODE>
 struct FwdLayout {
   using G = Group<L, MODE>;
@@ -338,6 +347,19 @@ struct FwdLayout {
   static_assert(bytes <= 232448 - 1024, "shared memory of the forward kernel exceeds the per-block limit");
 };
 
+// N 16-byte shared-memory loads into v[4N] (src 16-byte aligned).
+template <int N>
+__device__ __forceinline__ void load4(const float* src, float* v) {
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    const float4 x = reinterpret_cast<const float4*>(src)[q];
+    v[4 * q] = x.x;
+    v[4 * q + 1] = x.y;
+    v[4 * q + 2] = x.z;
+    v[4 * q + 3] = x.w;
+  }
+}
+
 template <int L, int MODE, int W>
 __device__ __forceinline__ void fwd_edge(const float* wv, const float* hj, const float* cy, float* acc) {
   using G = Group<L, MODE>;
@@ -352,10 +374,12 @@ __device__ __forceinline__ void fwd_edge(const float* wv, const float* hj, const
       float wh[2 * l1 + 1];
 #pragma unroll
       for (int q = 0; q < 2 * l1 + 1; ++q) wh[q] = wv[sl] * hj[l1 * l1 + q];
+      float c4[(ke - kb + 3) & ~3];
+      load4<(ke - kb + 3) / 4>(cy + gb, c4);
       static_for<kb, ke>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
         constexpr int o3 = Tab::e3[k] - G::comp0, j1 = Tab::e1[k] - l1 * l1;
-        acc[o3] = fmaf(cy[gb + k - kb], wh[j1], acc[o3]);
+        acc[o3] = fmaf(c4[k - kb], wh[j1], acc[o3]);
       });
     }
   });
@@ -424,7 +448,7 @@ __device__ __forceinline__ void fwd_tile_ws(const int* s_send, const int* s_recv
 }
 
 template <int L, int MODE>
-__global__ void __launch_bounds__(kThreads) tp_fused(int n, const int* __restrict__ row_ptr,
+__global__ void __launch_bounds__(kThreads, ctas_per_sm(FwdLayout<L, MODE>::bytes)) tp_fused(int n, const int* __restrict__ row_ptr,
                                                      const int* __restrict__ recv, const int* __restrict__ send,
                                                      const float* __restrict__ Yg, const float* __restrict__ h,
                                                      const uint8_t* __restrict__ w3img,
@@ -631,10 +655,12 @@ __device__ __forceinline__ void bwd_edge(const float* wv, int t, const float* hi
         float wg[2 * l3 + 1];
 #pragma unroll
         for (int q = 0; q < 2 * l3 + 1; ++q) wg[q] = s * wp * Gi[l3 * l3 + q - G::comp0];
+        float c4[(ke - kb + 3) & ~3];
+        load4<(ke - kb + 3) / 4>(cy + gb, c4);
         static_for<kb, ke>([&](auto kc) {
           constexpr int k = decltype(kc)::value;
           constexpr int i1 = Tab::e1[k], j3 = Tab::e3[k] - l3 * l3;
-          Gacc[i1] = fmaf(cy[gb + k - kb], wg[j3], Gacc[i1]);
+          Gacc[i1] = fmaf(c4[k - kb], wg[j3], Gacc[i1]);
         });
       }
       float Tp[2 * l2 + 1];
@@ -702,11 +728,14 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
   constexpr int CH = chunk_edges<DH + (FIRST ? 0 : NG)>();
   static_assert(CH % S::ypack(W) == 0, "edge packing must divide the chunk");
   float pv[16];
-  int yl_rt[16];
+  // the harmonic component this lane pair reduces (fixed for the thread; -1: none)
+  int my_comp = -1;
   {
     constexpr std::array<int, 16> yl = S::ylist(W);
+    constexpr int NVP = 16 / S::ypack(W), NV = S::nyv(W);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) yl_rt[k] = yl[k];
+    for (int k = 0; k < NV; ++k)
+      if (((lane >> 1) % NVP) == k) my_comp = yl[k];
   }
   float hn[CH][DH], gn[CH][NG];
 #pragma unroll
@@ -757,8 +786,7 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
       if (r >= 0) {
         advance(r);
         float Y[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
+        load4<4>(sY + t * 16, Y);
         float wv[G::NP];
 #pragma unroll
         for (int sl = 0; sl < G::NP; ++sl) wv[sl] = wvc[sl][j];
@@ -780,8 +808,8 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
       for (int i = 0; i < NVP; ++i) pv[slot * NVP + i] = i < NV ? dYp[yl[i < NV ? i : 0]] : 0.0f;
       if constexpr (slot == PK - 1) {
         const float tot = warp_reduce16(pv);
-        const int v = lane >> 1, vi = v % NVP, te = t - (PK - 1) + v / NVP;
-        if ((lane & 1) == 0 && vi < NV) red[(warp * kNT + te) * 16 + yl_rt[vi]] = tot;
+        const int te = t - (PK - 1) + (lane >> 1) / NVP;
+        if ((lane & 1) == 0 && my_comp >= 0) red[(warp * kNT + te) * 16 + my_comp] = tot;
       }
     });
   }
@@ -854,33 +882,10 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
       for (int q = 0; q < NG; ++q) gv[q] = Gm[((size_t)si * D + G::comp0 + q) * C + c];
     }
   };
-  float hw[kPF][DH], gw[kPF][NG];
-#pragma unroll
-  for (int k = 0; k < kPF; ++k) gather(k, hw[k], gw[k]);
   float pv[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) pv[i] = 0.0f;
-#pragma unroll 1
-  for (int t = 0; t < kNT; ++t) {
-    float wv[G::NP];
-    static_for<0, G::NP>([&](auto sc) {
-      constexpr int sl = decltype(sc)::value;
-      if constexpr (S::ws[sl] == W) wv[sl] = tmem_ld1(taddr0 + sl * kNT + t);
-    });
-    tc::tmem_ld_wait();
-    float hc[DH], gc[NG];
-#pragma unroll
-    for (int d = 0; d < DH; ++d) hc[d] = hw[0][d];
-#pragma unroll
-    for (int q = 0; q < NG; ++q) gc[q] = FIRST ? 0.0f : gw[0][q];
-#pragma unroll
-    for (int k = 0; k + 1 < kPF; ++k) {
-#pragma unroll
-      for (int d = 0; d < DH; ++d) hw[k][d] = hw[k + 1][d];
-#pragma unroll
-      for (int q = 0; q < NG; ++q) gw[k][q] = gw[k + 1][q];
-    }
-    gather(t + kPF < kNT ? t + kPF : kNT - 1, hw[kPF - 1], gw[kPF - 1]);
+  auto edge = [&](int t, const float* hc, const float* gc, const float* wv) {
     const int r = s_recv[t];
     float dYp[16];
 #pragma unroll
@@ -888,8 +893,7 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
     if (r >= 0) {
       advance(r);
       float Y[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
+      load4<4>(sY + t * 16, Y);
       bwd_edge<L, MODE, W>(wv, t, hc, gc, Gt, Y, cY + t * BL::NZP, s, dws[t], use_bf16, sB2, Gacc, dYp);
     } else {
       static_for<0, G::NP>([&](auto sc) {
@@ -912,11 +916,36 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
       const int te = t - (PK - 1) + lane / NV, vi = lane % NV;
       if (lane < PK * NV && te >= t - slot) red[(warp * kNT + te) * 16 + yl_rt[vi]] = tot;
     }
+  };
+  // edges in pairs with two register buffers: the sender rows of the next
+  // pair's edge load while the other edge of this pair is computed
+  float hA[DH], gA[NG], hB[DH], gB[NG];
+#pragma unroll
+  for (int q = 0; q < NG; ++q) gA[q] = gB[q] = 0.0f;
+  gather(0, hA, gA);
+  gather(1, hB, gB);
+#pragma unroll 1
+  for (int t = 0; t < kNT; t += 2) {
+    float w2[G::NP][2], wA[G::NP], wB[G::NP];
+    static_for<0, G::NP>([&](auto sc) {
+      constexpr int sl = decltype(sc)::value;
+      if constexpr (S::ws[sl] == W) tmem_ld2(taddr0 + sl * kNT + t, w2[sl]);
+    });
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int sl = 0; sl < G::NP; ++sl) {
+      wA[sl] = w2[sl][0];
+      wB[sl] = w2[sl][1];
+    }
+    edge(t, hA, gA, wA);
+    if (t + 2 < kNT) gather(t + 2, hA, gA);
+    edge(t + 1, hB, gB, wB);
+    if (t + 3 < kNT) gather(t + 3, hB, gB);
   }
 }
 
 template <int L, int MODE>
-__global__ void __launch_bounds__(kThreads) tp_fused_bwd(int n, const int* __restrict__ row_ptr,
+__global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::bytes)) tp_fused_bwd(int n, const int* __restrict__ row_ptr,
                                                          const int* __restrict__ recv, const int* __restrict__ send,
                                                          const float* __restrict__ Yg,
                                                          const float* __restrict__ hprev,
