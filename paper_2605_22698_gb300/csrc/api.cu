@@ -158,6 +158,25 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
   }
   M->W_out = q; q += S * C;
   M->E0 = q; q += S;
+  {  // W_l^T of every layer and order, for the adjoint of the mixes
+    const size_t per = (size_t)(M->L + 1) * C * C;
+    std::vector<float> wt(per * M->T);
+    for (int t = 0; t < M->T; ++t) {
+      const float* w = M->host_weights.data() + (M->Wmix[t] - M->d_weights);
+      for (int l = 0; l <= M->L; ++l)
+        for (int64_t a = 0; a < C; ++a)
+          for (int64_t b = 0; b < C; ++b) wt[t * per + l * C * C + b * C + a] = w[l * C * C + a * C + b];
+    }
+    e = cudaMalloc(&M->d_wmixT, sizeof(float) * wt.size());
+    if (e == cudaSuccess) e = cudaMemcpy(M->d_wmixT, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("transposed mix weights: %s", cudaGetErrorString(e));
+      mlip_model_free(M);
+      return MLIP_ERR_OOM;
+    }
+    for (int t = 0; t < M->T; ++t) M->WmixT.push_back(M->d_wmixT + t * per);
+  }
   if (precision != MLIP_PREC_FP32) {
     std::vector<uint8_t> all, img;
     for (int t = 0; t < M->T; ++t) {
@@ -220,6 +239,7 @@ int mlip_model_free(mlip_model* M) {
   M->ws.release();
   if (M->d_weights) cudaFree(M->d_weights);
   if (M->d_w3img) cudaFree(M->d_w3img);
+  if (M->d_wmixT) cudaFree(M->d_wmixT);
   delete M;
   return MLIP_OK;
 }
@@ -338,7 +358,7 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
     for (int t = T - 1; t >= 0; --t) {
       const bool first = t == 0;
       const int PW = first ? P0 : P;
-      MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], Gm, st));
+      MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], M->WmixT[t], Gm, st));
       MLIP_TRY(launch_tp_bwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], Gm, w[t], PW, s, Ga, Gb, dw, dY, st));
       MLIP_TRY(launch_sgemm(false, true, E, H, PW * C, dw, PW * C, M->W3[t], P * C, dz2, H, st));
       MLIP_TRY(launch_radial_bwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, st));

@@ -1617,7 +1617,7 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
     MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)b.nsys, &absmax));
     MLIP_TRY(ws.get("fz.dws2", (size_t)b.nsys, &dws2));
     for (int t = T - 1; t >= 0; --t) {
-      MLIP_TRY(launch_mix_bwd2(n, C, L, GaA, GaB, u0[t], M->Wmix[t], Gm, st));
+      MLIP_TRY(launch_mix_bwd2(n, C, L, GaA, GaB, u0[t], M->WmixT[t], Gm, st));
       MLIP_CUDA_TRY(cudaMemsetAsync(dz2, 0, Ec * 64 * sizeof(float), st));
       if (!use_bf16) MLIP_TRY(launch_seg_absmax2(b, D * C, h[t], Gm, absmax, st));
       {

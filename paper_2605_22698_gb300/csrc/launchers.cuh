@@ -20,11 +20,11 @@ int launch_tp_bwd(int L, bool first, int n, int C, const int* row_ptr, const int
                   const float* Gin, float* Gout, float* dw, float* dY, cudaStream_t st);
 int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const float* hin, float* hout,
                    float* u0, cudaStream_t st);
-int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, float* Gm,
-                   cudaStream_t st);
+int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, const float* WmixT,
+                   float* Gm, cudaStream_t st);
 int launch_mix_fwd2(int n, int C, int L, const float* mA, const float* mB, const float* Wmix, const float* hin,
                     float* hout, float* u0, cudaStream_t st);
-int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const float* u0, const float* Wmix,
+int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const float* u0, const float* WmixT,
                     float* Gm, cudaStream_t st);
 int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st);
 int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st);

@@ -142,6 +142,8 @@ struct mlip_model {
   const float* W_out = nullptr;
   const float* E0 = nullptr;
   std::vector<const float*> W1, W2, W3, Wmix;
+  float* d_wmixT = nullptr;            // channel-mix weights transposed, per layer and order
+  std::vector<const float*> WmixT;
   // fused form: W3 of every layer as BF16 tensor-core operands, grouped by path group
   uint8_t* d_w3img = nullptr;
   std::vector<size_t> w3_layer_off;

@@ -458,10 +458,15 @@ __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int*
 //   forward:  u = m W_l;  h_out = h_in + (l == 0 ? silu(u) : u);  u0 keeps u (l = 0)
 //   backward: Gm = Gu W_l^T,  Gu = G silu'(u0) (l = 0) or G
 // The input is X + X2 when X2 is given (the fused kernels' two partial buffers).
+// Wg is W_l (forward) or W_l^T (backward), both read row-major [k][n].  The
+// A tile is staged k-major with the row index XOR-swizzled by (k & 7) << 2 so
+// that both the staging stores and the 16-byte row-group loads avoid bank
+// conflicts beyond 4 ways.
 constexpr int kMixRows = 64;
+__device__ __forceinline__ int mix_swz(int k, int r) { return k * kMixRows + (r ^ ((k & 7) << 2)); }
 template <bool BWD>
 __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __restrict__ X,
-                                                const float* __restrict__ X2, const float* __restrict__ Wmix,
+                                                const float* __restrict__ X2, const float* __restrict__ Wg,
                                                 const float* __restrict__ hin,
                                                 float* __restrict__ out, float* __restrict__ u0,
                                                 const float* __restrict__ u0_in) {
@@ -473,12 +478,8 @@ __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __res
   const int rows = n * R;
   const int row0 = blockIdx.x * kMixRows;
   if (row0 >= rows) return;
-  const float* Wl = Wmix + (size_t)l * C * C;
-  for (int k = threadIdx.x; k < C * C; k += blockDim.x) {
-    const int a = k / C, b = k % C;
-    if (!BWD) Ws[k] = Wl[k];
-    else Ws[b * C + a] = Wl[k];     // Ws[k'][n'] = W[n'][k']
-  }
+  const float4* Wl4 = reinterpret_cast<const float4*>(Wg + (size_t)l * C * C);
+  for (int k = threadIdx.x; k < C * C / 4; k += blockDim.x) reinterpret_cast<float4*>(Ws)[k] = Wl4[k];
   for (int k = threadIdx.x; k < kMixRows * C; k += blockDim.x) {
     const int rr = k / C, cc = k % C, r = row0 + rr;
     float v = 0.0f;
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __res
       if (X2) v += X2[o];
       if (BWD && l == 0) v *= silu_grad_f(u0_in[(size_t)nd * C + cc]);
     }
-    As[cc * kMixRows + rr] = v;
+    As[mix_swz(cc, rr)] = v;
   }
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 column groups x 8 row groups
@@ -500,8 +501,8 @@ __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __res
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
 #pragma unroll 4
   for (int k = 0; k < C; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(&As[k * kMixRows + ty * 8]);
-    const float4 a1 = *reinterpret_cast<const float4*>(&As[k * kMixRows + ty * 8 + 4]);
+    const float4 a0 = *reinterpret_cast<const float4*>(&As[mix_swz(k, ty * 8)]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&As[mix_swz(k, ty * 8 + 4)]);
     const float4 b0 = *reinterpret_cast<const float4*>(&Ws[k * C + tx * 4]);
     const float4 b1 = *reinterpret_cast<const float4*>(&Ws[k * C + 64 + tx * 4]);
     const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
@@ -707,14 +708,14 @@ int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const
   return MLIP_OK;
 }
 
-int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, float* Gm,
-                   cudaStream_t st) {
+int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, const float* WmixT,
+                   float* Gm, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   if (C == 128) {
     const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
-    { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, G, nullptr, Wmix, nullptr, Gm, nullptr, u0); }
+    { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, G, nullptr, WmixT, nullptr, Gm, nullptr, u0); }
     MLIP_LAUNCH_CHECK();
     return MLIP_OK;
   }
@@ -738,14 +739,14 @@ int launch_mix_fwd2(int n, int C, int L, const float* mA, const float* mB, const
   return MLIP_OK;
 }
 
-int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const float* u0, const float* Wmix,
+int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const float* u0, const float* WmixT,
                     float* Gm, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   if (C != 128) { set_error("the fused form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
   const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
-  { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, GA, GB, Wmix, nullptr, Gm, nullptr, u0); }
+  { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, GA, GB, WmixT, nullptr, Gm, nullptr, u0); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
