@@ -458,39 +458,58 @@ __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int*
 //   forward:  u = m W_l;  h_out = h_in + (l == 0 ? silu(u) : u);  u0 keeps u (l = 0)
 //   backward: Gm = Gu W_l^T,  Gu = G silu'(u0) (l = 0) or G
 // The input is X + X2 when X2 is given (the fused kernels' two partial buffers).
-// Wg is W_l (forward) or W_l^T (backward), both read row-major [k][n].  The
-// A tile is staged k-major with the row index XOR-swizzled by (k & 7) << 2 so
-// that both the staging stores and the 16-byte row-group loads avoid bank
-// conflicts beyond 4 ways.
+// Wg is W_l (forward) or W_l^T (backward), both read row-major [k][n].  All
+// global traffic is in 16-byte vectors with every load of a thread issued
+// before its first use; the A tile is kept row-major (rows padded to 132
+// floats) and read four k at a time.
 constexpr int kMixRows = 64;
-__device__ __forceinline__ int mix_swz(int k, int r) { return k * kMixRows + (r ^ ((k & 7) << 2)); }
+constexpr int kMixAS = 132;  // A tile row stride (floats)
 template <bool BWD>
 __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __restrict__ X,
                                                 const float* __restrict__ X2, const float* __restrict__ Wg,
                                                 const float* __restrict__ hin,
                                                 float* __restrict__ out, float* __restrict__ u0,
                                                 const float* __restrict__ u0_in) {
-  constexpr int C = 128;
+  constexpr int C = 128, C4 = C / 4;
   extern __shared__ __align__(16) float sm[];
-  float* Ws = sm;                   // [k][n]  (forward W_l[k][n]; backward W_l[n][k])
-  float* As = sm + C * C;           // [k][row]
+  float* Ws = sm;                   // [k][n]
+  float* As = sm + C * C;           // [row][k], stride kMixAS
   const int l = blockIdx.y, R = 2 * l + 1, D = (L + 1) * (L + 1);
   const int rows = n * R;
   const int row0 = blockIdx.x * kMixRows;
   if (row0 >= rows) return;
   const float4* Wl4 = reinterpret_cast<const float4*>(Wg + (size_t)l * C * C);
-  for (int k = threadIdx.x; k < C * C / 4; k += blockDim.x) reinterpret_cast<float4*>(Ws)[k] = Wl4[k];
-  for (int k = threadIdx.x; k < kMixRows * C; k += blockDim.x) {
-    const int rr = k / C, cc = k % C, r = row0 + rr;
-    float v = 0.0f;
+  const float4* X4 = reinterpret_cast<const float4*>(X);
+  const float4* X24 = reinterpret_cast<const float4*>(X2);
+  const float4* U4 = reinterpret_cast<const float4*>(u0_in);
+  // A tile: 64 rows x 32 float4, 16 per thread, loads first
+  constexpr int NA = kMixRows * C4 / 128;
+  float4 va[NA];
+#pragma unroll
+  for (int u = 0; u < NA; ++u) {
+    const int q = threadIdx.x + u * 128, rr = q / C4, c4 = q % C4, r = row0 + rr;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (r < rows) {
       const int nd = r / R, mm = r % R;
-      const size_t o = ((size_t)nd * D + l * l + mm) * C + cc;
-      v = X[o];
-      if (X2) v += X2[o];
-      if (BWD && l == 0) v *= silu_grad_f(u0_in[(size_t)nd * C + cc]);
+      const size_t o = ((size_t)nd * D + l * l + mm) * C4 + c4;
+      v = X4[o];
+      if (X2) {
+        const float4 w = X24[o];
+        v.x += w.x; v.y += w.y; v.z += w.z; v.w += w.w;
+      }
+      if (BWD && l == 0) {
+        const float4 uu = U4[(size_t)nd * C4 + c4];
+        v.x *= silu_grad_f(uu.x); v.y *= silu_grad_f(uu.y); v.z *= silu_grad_f(uu.z); v.w *= silu_grad_f(uu.w);
+      }
     }
-    As[mix_swz(cc, rr)] = v;
+    va[u] = v;
+  }
+#pragma unroll 8
+  for (int k = threadIdx.x; k < C * C4; k += blockDim.x) reinterpret_cast<float4*>(Ws)[k] = Wl4[k];
+#pragma unroll
+  for (int u = 0; u < NA; ++u) {
+    const int q = threadIdx.x + u * 128, rr = q / C4, c4 = q % C4;
+    *reinterpret_cast<float4*>(&As[rr * kMixAS + 4 * c4]) = va[u];
   }
   __syncthreads();
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 column groups x 8 row groups
@@ -499,36 +518,57 @@ __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __res
   for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-#pragma unroll 4
-  for (int k = 0; k < C; ++k) {
-    const float4 a0 = *reinterpret_cast<const float4*>(&As[mix_swz(k, ty * 8)]);
-    const float4 a1 = *reinterpret_cast<const float4*>(&As[mix_swz(k, ty * 8 + 4)]);
-    const float4 b0 = *reinterpret_cast<const float4*>(&Ws[k * C + tx * 4]);
-    const float4 b1 = *reinterpret_cast<const float4*>(&Ws[k * C + 64 + tx * 4]);
-    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll 1
+  for (int k0 = 0; k0 < C; k0 += 4) {
+    float4 a[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) a[i] = *reinterpret_cast<const float4*>(&As[(ty * 8 + i) * kMixAS + k0]);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    for (int kk = 0; kk < 4; ++kk) {
+      const float4 b0 = *reinterpret_cast<const float4*>(&Ws[(k0 + kk) * C + tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Ws[(k0 + kk) * C + 64 + tx * 4]);
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float ai = kk == 0 ? a[i].x : kk == 1 ? a[i].y : kk == 2 ? a[i].z : a[i].w;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ai, b[j], acc[i][j]);
+      }
+    }
+  }
+  // epilogue: two float4 column groups per row (channels tx*4.. and 64+tx*4..)
+  float4 hv[8][2];
+  if (!BWD) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = row0 + ty * 8 + i;
+      hv[i][0] = hv[i][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < rows) {
+        const int nd = r / R, mm = r % R;
+        const float4* h4 = reinterpret_cast<const float4*>(hin + ((size_t)nd * D + l * l + mm) * C);
+        hv[i][0] = h4[tx];
+        hv[i][1] = h4[16 + tx];
+      }
+    }
   }
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int r = row0 + ty * 8 + i;
     if (r >= rows) continue;
     const int nd = r / R, mm = r % R;
-    const size_t base = ((size_t)nd * D + l * l + mm) * C;
+    float4* o4 = reinterpret_cast<float4*>(out + ((size_t)nd * D + l * l + mm) * C);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int cc = (j < 4) ? tx * 4 + j : 64 + tx * 4 + (j - 4);
-      const float u = acc[i][j];
+    for (int g = 0; g < 2; ++g) {
+      float4 u = make_float4(acc[i][4 * g], acc[i][4 * g + 1], acc[i][4 * g + 2], acc[i][4 * g + 3]);
       if (BWD) {
-        out[base + cc] = u;
+        o4[16 * g + tx] = u;
       } else if (l == 0) {
-        u0[(size_t)nd * C + cc] = u;
-        out[base + cc] = hin[base + cc] + silu_f(u);
+        reinterpret_cast<float4*>(u0 + (size_t)nd * C)[16 * g + tx] = u;
+        const float4 h = hv[i][g];
+        o4[16 * g + tx] = make_float4(h.x + silu_f(u.x), h.y + silu_f(u.y), h.z + silu_f(u.z), h.w + silu_f(u.w));
       } else {
-        out[base + cc] = hin[base + cc] + u;
+        const float4 h = hv[i][g];
+        o4[16 * g + tx] = make_float4(h.x + u.x, h.y + u.y, h.z + u.z, h.w + u.w);
       }
     }
   }
@@ -693,7 +733,7 @@ int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const
                    float* u0, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   if (C == 128) {
-    const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
+    const size_t smem = (size_t)(128 * 128 + kMixRows * kMixAS) * sizeof(float);
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
     { MLIP_PROF("mix_fwd", st); mix_gemm<false><<<grid, 128, smem, st>>>(n, L, m, nullptr, Wmix, hin, hout, u0, nullptr); }
@@ -712,7 +752,7 @@ int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const f
                    float* Gm, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   if (C == 128) {
-    const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
+    const size_t smem = (size_t)(128 * 128 + kMixRows * kMixAS) * sizeof(float);
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
     { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, G, nullptr, WmixT, nullptr, Gm, nullptr, u0); }
@@ -731,7 +771,7 @@ int launch_mix_fwd2(int n, int C, int L, const float* mA, const float* mB, const
                     float* hout, float* u0, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   if (C != 128) { set_error("the fused form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
-  const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
+  const size_t smem = (size_t)(128 * 128 + kMixRows * kMixAS) * sizeof(float);
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
   { MLIP_PROF("mix_fwd", st); mix_gemm<false><<<grid, 128, smem, st>>>(n, L, mA, mB, Wmix, hin, hout, u0, nullptr); }
@@ -743,7 +783,7 @@ int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const
                     float* Gm, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   if (C != 128) { set_error("the fused form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
-  const size_t smem = (size_t)(128 * 128 + kMixRows * 128) * sizeof(float);
+  const size_t smem = (size_t)(128 * 128 + kMixRows * kMixAS) * sizeof(float);
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
   { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, GA, GB, WmixT, nullptr, Gm, nullptr, u0); }
