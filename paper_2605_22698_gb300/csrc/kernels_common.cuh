@@ -36,9 +36,13 @@ struct PathInfo {
   static constexpr int NNZ0 = T::off[L + 1];        // entries of the l1 = 0 paths
 };
 
-__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + expf(-x)); }
+// SiLU and its derivative through the logistic sigmoid 1 / (1 + exp(-x)),
+// with the fast divide (2 ulp) instead of the IEEE one: exp(-x) overflowing to
+// infinity gives sigmoid 0, as it should.
+__device__ __forceinline__ float sigmoid_f(float x) { return __fdividef(1.0f, 1.0f + expf(-x)); }
+__device__ __forceinline__ float silu_f(float x) { return x * sigmoid_f(x); }
 __device__ __forceinline__ float silu_grad_f(float x) {
-  const float s = 1.0f / (1.0f + expf(-x));
+  const float s = sigmoid_f(x);
   return s * (1.0f + x * (1.0f - s));
 }
 

@@ -42,6 +42,13 @@ int launch_seg_sum(Workspace& ws, const SystemBatch& b, int K, const double* v, 
 // out[2s], out[2s+1] = max |a|, max |b| over the rows (row floats per atom) of system s
 int launch_seg_absmax2(const SystemBatch& b, int row, const float* a, const float* bb, float* out, cudaStream_t st);
 
+// Radial MLP of the fused form on the tensor cores (H = 64): z2 operand tiles,
+// and dE/dr accumulated from dE/dz2.  err receives the bounded-wait flags.
+int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float* W1, const float* W2, float rc,
+                     int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st);
+int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const float* W2, float rc, int p,
+                         const float* dz2, float* dr_tot, int* err, cudaStream_t st);
+
 int launch_check_inputs(int n, const double* pos, const int* species, int S, int* flag, cudaStream_t st);
 int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::vector<size_t>& group_off);
 int umma_selftest_run(double* rel_err);

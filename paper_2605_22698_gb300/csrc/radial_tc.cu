@@ -1,0 +1,425 @@
+// Radial MLP of the fused form with its 64 x 64 hidden layer on the tensor
+// cores (tcgen05.mma kind::f16, FP16 operands, FP32 accumulation in tensor
+// memory), for H = 64.
+//
+// The radial network of every edge e is  z1 = silu(e_n W1),  z2 = silu(z1 W2)
+// (Bessel basis e_n times the envelope, bias-free layers).  A CTA of 128
+// threads takes 128 edges at a time, one edge per thread (and per tensor-memory
+// lane):
+//   forward  (radial_tc):      z1 in FP32 on the ALUs, each row scaled by a
+//       power of two so that its largest entry lies in [2^13, 2^14) and written
+//       as the FP16 A operand; one MMA chain (M = 128 edges, N = 64, K = 64)
+//       against W2^T; the row of a2 = z1 W2 is read back, unscaled exactly,
+//       and z2 = silu(a2) is written as the 16-bit operand tile of the
+//       message kernels (4 KB per 32 edges, canonical K-major layout).
+//   adjoint  (radial_bwd_tc):  the same product for a2, then
+//       da2 = dE/dz2 * silu'(a2) (scaled per row likewise), a second MMA chain
+//       dz1 = da2 W2^T against W2, and per edge
+//       dE/dr += sum_k dz1_k silu'(a1_k) (W1 de/dr)_k  with a1 recomputed.
+// The power-of-two row scales keep FP16 away from overflow and underflow and
+// are removed exactly after the product.  Each FP32 operand x is split into
+// x_hi = fp16(x) and x_lo = fp16(x - x_hi) and the product is taken as
+// A_hi B_hi + A_lo B_hi + A_hi B_lo (three MMA chains into one accumulator),
+// which keeps about 21 significant bits: the layer stays at FP32-level
+// accuracy while its flops run on the tensor pipe.
+#include <algorithm>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "kernels_common.cuh"
+#include "launchers.cuh"
+#include "profile.cuh"
+#include "sm100_tc.cuh"
+
+namespace mlip {
+namespace {
+
+constexpr int kRH = 64;          // hidden width
+constexpr int kRM = 128;         // edges per MMA tile (M)
+constexpr int kZ2Tile = 32;      // edges per z2 operand tile of the message kernels
+constexpr int kAOpBytes = kRM * kRH * 2;   // 16 KB
+constexpr int kBOpBytes = kRH * kRH * 2;   // 8 KB
+
+__device__ __forceinline__ uint16_t f16_bits(float x) {
+  const __half v = __float2half_rn(x);
+  return *reinterpret_cast<const uint16_t*>(&v);
+}
+__device__ __forceinline__ uint16_t z2_bits(float x, int use_bf16) {
+  if (use_bf16) {
+    const __nv_bfloat16 v = __float2bfloat16_rn(x);
+    return *reinterpret_cast<const uint16_t*>(&v);
+  }
+  return f16_bits(x);
+}
+
+// 2^k with max|row| * 2^k in [2^13, 2^14) (1 for an all-zero row).
+__device__ __forceinline__ float row_scale(float amax) {
+  if (!(amax > 0.0f)) return 1.0f;
+  const int ex = ilogbf(amax);  // amax in [2^ex, 2^(ex+1))
+  return exp2f((float)max(-100, min(100, 13 - ex)));
+}
+
+__device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo) {
+  const __half h = __float2half_rn(x);
+  hi = *reinterpret_cast<const uint16_t*>(&h);
+  lo = f16_bits(x - __half2float(h));
+}
+
+// Writes an FP32 row (times sc) as the FP16 A operand row `r` of the hi and lo
+// tiles (canonical layout, K = 64).
+__device__ __forceinline__ void put_row(uint8_t* Ahi, uint8_t* Alo, int r, const float* v, float sc) {
+#pragma unroll
+  for (int kg = 0; kg < 8; ++kg) {
+    uint32_t ph[4], pl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint16_t h0, l0, h1, l1;
+      split16(v[kg * 8 + 2 * q] * sc, h0, l0);
+      split16(v[kg * 8 + 2 * q + 1] * sc, h1, l1);
+      ph[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+      pl[q] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+    }
+    *reinterpret_cast<uint4*>(Ahi + tc::canon_off(r, kg * 8)) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    *reinterpret_cast<uint4*>(Alo + tc::canon_off(r, kg * 8)) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+  }
+}
+
+// B operand [n][k] = W[k][n] (transpose = true) or W[n][k] times sc, FP16
+// hi and lo tiles, canonical layout.
+__device__ __forceinline__ void load_b(uint8_t* Bhi, uint8_t* Blo, const float* __restrict__ W, bool transpose,
+                                       float sc) {
+  for (int q = threadIdx.x; q < kRH * kRH; q += blockDim.x) {
+    const int n = q / kRH, k = q % kRH;
+    const float w = (transpose ? W[k * kRH + n] : W[n * kRH + k]) * sc;
+    uint16_t h, l;
+    split16(w, h, l);
+    *reinterpret_cast<uint16_t*>(Bhi + tc::canon_off(n, k)) = h;
+    *reinterpret_cast<uint16_t*>(Blo + tc::canon_off(n, k)) = l;
+  }
+}
+
+// Power-of-two scale of W (max |W| * scale in [2^13, 2^14)), all threads.
+__device__ __forceinline__ float weight_scale(const float* __restrict__ W, float* red) {
+  float m = 0.0f;
+  for (int q = threadIdx.x; q < kRH * kRH; q += blockDim.x) m = fmaxf(m, fabsf(W[q]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  float t = 0.0f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+  __syncthreads();
+  return row_scale(t);
+}
+
+// Issues D = A_hi B_hi + A_lo B_hi + A_hi B_lo over K = 64 (12 MMAs of K = 16)
+// and commits to `bar`.
+__device__ __forceinline__ void mma_tile(uint32_t dtm, const uint8_t* Ahi, const uint8_t* Alo, const uint8_t* Bhi,
+                                         const uint8_t* Blo, uint64_t* bar) {
+  const uint32_t idesc = tc::idesc_16bit(kRM, kRH, false);
+  const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+  const uint32_t as[3] = {ah, al, ah}, bs[3] = {bh, bh, bl};
+#pragma unroll
+  for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint64_t ad = tc::desc_noswizzle(as[pass] + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+      const uint64_t bd = tc::desc_noswizzle(bs[pass] + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+      tc::mma_bf16(dtm, ad, bd, idesc, (pass | kk) ? 1u : 0u);
+    }
+  tc::mma_commit(bar);
+}
+
+// Reads this thread's 64 accumulator columns (its lane) into v, times inv.
+__device__ __forceinline__ void get_row(uint32_t taddr, float* v, float inv) {
+#pragma unroll
+  for (int c = 0; c < kRH / 8; ++c) tc::tmem_ld8(taddr + c * 8, v + c * 8);
+  tc::tmem_ld_wait();
+#pragma unroll
+  for (int k = 0; k < kRH; ++k) v[k] *= inv;
+}
+
+__device__ __forceinline__ void z1_row(float r, float rc, int p, const float* sW1, float* z1, float* b, float* db,
+                                       bool grad) {
+  if (grad) radial_basis<8, true>(r, rc, p, b, db);
+  else radial_basis<8, false>(r, rc, p, b, db);
+#pragma unroll
+  for (int k = 0; k < kRH; ++k) {
+    float a = 0.0f;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) a = fmaf(b[n], sW1[n * kRH + k], a);
+    z1[k] = silu_f(a);
+  }
+}
+
+__device__ __forceinline__ float absmax64(const float* v) {
+  float m = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kRH; ++k) m = fmaxf(m, fabsf(v[k]));
+  return m;
+}
+
+// ------------------------------------------------------------- forward
+__global__ void __launch_bounds__(kRM, 4) radial_tc(int E, int n_tiles32, const float4* __restrict__ ev,
+                                                 const float* __restrict__ W1, const float* __restrict__ W2,
+                                                 float rc, int p, int use_bf16, uint8_t* __restrict__ z2t,
+                                                 int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sAh = smem;
+  uint8_t* sAl = smem + kAOpBytes;
+  uint8_t* sBh = smem + 2 * kAOpBytes;
+  uint8_t* sBl = sBh + kBOpBytes;
+  __shared__ __align__(16) float sW1[8 * kRH];
+  __shared__ float red[4];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_s;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, kRH);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    abort_s = 0;
+  }
+  for (int q = tid; q < 8 * kRH; q += blockDim.x) sW1[q] = W1[q];
+  const float wsc = weight_scale(W2, red);
+  load_b(sBh, sBl, W2, true, wsc);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16);
+  const int n_edges = n_tiles32 * kZ2Tile;  // z2 rows to write (E rounded up to 32)
+  uint32_t phase = 0;
+  int issued = 0, done = 0;  // products issued / seen complete (thread 0)
+#pragma unroll 1
+  for (int base = blockIdx.x * kRM; base < n_edges; base += gridDim.x * kRM) {
+    const int e = base + tid;
+    float z[kRH], b[8], db[8];
+    float sc = 1.0f;
+    if (e < E) {
+      z1_row(ev[e].w, rc, p, sW1, z, b, db, false);
+      sc = row_scale(absmax64(z));
+    } else {
+#pragma unroll
+      for (int k = 0; k < kRH; ++k) z[k] = 0.0f;
+    }
+    put_row(sAh, sAl, tid, z, sc);
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      mma_tile(tmem_base, sAh, sAl, sBh, sBl, &bar);
+      ++issued;
+    }
+    if (!tc::mbar_wait(&bar, phase)) {
+      atomicOr(err, 32);
+      abort_s = 1;
+    } else if (tid == 0) {
+      ++done;
+    }
+    phase ^= 1;
+    tc::fence_after_sync();
+    get_row(taddr, z, 1.0f / (sc * wsc));
+    if (e < n_edges) {
+      uint8_t* tile = z2t + (size_t)(e / kZ2Tile) * (kZ2Tile * kRH * 2);
+      const int t = e % kZ2Tile;
+#pragma unroll
+      for (int kg = 0; kg < 8; ++kg) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int k = kg * 8 + 2 * q;
+          const float v0 = e < E ? silu_f(z[k]) : 0.0f, v1 = e < E ? silu_f(z[k + 1]) : 0.0f;
+          pk[q] = (uint32_t)z2_bits(v0, use_bf16) | ((uint32_t)z2_bits(v1, use_bf16) << 16);
+        }
+        *reinterpret_cast<uint4*>(tile + tc::canon_off(t, kg * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // the next tile rewrites sA and the accumulator
+    tc::fence_after_sync();
+    if (abort_s) break;
+  }
+  if (tid == 0 && issued > done) tc::mbar_wait(&bar, done & 1, 1LL << 20);  // the product in flight, bounded
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem_base, kRH);
+}
+
+// ------------------------------------------------------------- adjoint
+__global__ void __launch_bounds__(kRM, 3) radial_bwd_tc(int E, const float4* __restrict__ ev,
+                                                     const float* __restrict__ W1, const float* __restrict__ W2,
+                                                     float rc, int p, const float* __restrict__ dz2,
+                                                     float* __restrict__ dr_tot, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sAh = smem;
+  uint8_t* sAl = smem + kAOpBytes;
+  uint8_t* sBth = smem + 2 * kAOpBytes;   // W2^T: a2 = z1 W2
+  uint8_t* sBtl = sBth + kBOpBytes;
+  uint8_t* sBnh = sBtl + kBOpBytes;       // W2:   dz1 = da2 W2^T
+  uint8_t* sBnl = sBnh + kBOpBytes;
+  __shared__ __align__(16) float sW1[8 * kRH];
+  __shared__ float red[4];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_s;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 2 * kRH);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    abort_s = 0;
+  }
+  for (int q = tid; q < 8 * kRH; q += blockDim.x) sW1[q] = W1[q];
+  const float wsc = weight_scale(W2, red);
+  load_b(sBth, sBtl, W2, true, wsc);
+  load_b(sBnh, sBnl, W2, false, wsc);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16);
+  uint32_t phase = 0;
+  int issued = 0, done = 0;
+#pragma unroll 1
+  for (int base = blockIdx.x * kRM; base < E; base += gridDim.x * kRM) {
+    const int e = base + tid;
+    const bool live = e < E;
+    float z[kRH], t[kRH], b[8], db[8];
+    float sc1 = 1.0f;
+    if (live) {
+      z1_row(ev[e].w, rc, p, sW1, z, b, db, true);
+      sc1 = row_scale(absmax64(z));
+    } else {
+#pragma unroll
+      for (int k = 0; k < kRH; ++k) z[k] = 0.0f;
+#pragma unroll
+      for (int n = 0; n < 8; ++n) b[n] = db[n] = 0.0f;
+    }
+    put_row(sAh, sAl, tid, z, sc1);
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      mma_tile(tmem_base, sAh, sAl, sBth, sBtl, &bar);
+      ++issued;
+    }
+    if (!tc::mbar_wait(&bar, phase)) {
+      atomicOr(err, 64);
+      abort_s = 1;
+    } else if (tid == 0) {
+      ++done;
+    }
+    phase ^= 1;
+    tc::fence_after_sync();
+    get_row(taddr, t, 1.0f / (sc1 * wsc));  // a2
+    // da2 = dE/dz2 silu'(a2)
+    if (live) {
+      const float4* g4 = reinterpret_cast<const float4*>(dz2 + (size_t)e * kRH);
+#pragma unroll
+      for (int q4 = 0; q4 < kRH / 4; ++q4) {
+        const float4 g = g4[q4];
+        t[4 * q4] = g.x * silu_grad_f(t[4 * q4]);
+        t[4 * q4 + 1] = g.y * silu_grad_f(t[4 * q4 + 1]);
+        t[4 * q4 + 2] = g.z * silu_grad_f(t[4 * q4 + 2]);
+        t[4 * q4 + 3] = g.w * silu_grad_f(t[4 * q4 + 3]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kRH; ++k) t[k] = 0.0f;
+    }
+    const float sc2 = row_scale(absmax64(t));
+    tc::fence_before_sync();
+    __syncthreads();  // every row of the first product is consumed before sA is rewritten
+    tc::fence_after_sync();
+    put_row(sAh, sAl, tid, t, sc2);
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      mma_tile(tmem_base + kRH, sAh, sAl, sBnh, sBnl, &bar);
+      ++issued;
+    }
+    if (!tc::mbar_wait(&bar, phase)) {
+      atomicOr(err, 64);
+      abort_s = 1;
+    } else if (tid == 0) {
+      ++done;
+    }
+    phase ^= 1;
+    tc::fence_after_sync();
+    get_row(taddr + kRH, z, 1.0f / (sc2 * wsc));  // dz1
+    if (live) {
+      float dr = 0.0f;
+#pragma unroll
+      for (int k = 0; k < kRH; ++k) {
+        float a = 0.0f, bd = 0.0f;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) {
+          a = fmaf(b[n], sW1[n * kRH + k], a);
+          bd = fmaf(sW1[n * kRH + k], db[n], bd);
+        }
+        dr = fmaf(z[k] * silu_grad_f(a), bd, dr);
+      }
+      dr_tot[e] += dr;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (abort_s) break;
+  }
+  if (tid == 0 && issued > done) tc::mbar_wait(&bar, done & 1, 1LL << 20);  // the product in flight, bounded
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem_base, 2 * kRH);
+}
+
+}  // namespace
+
+// Persistent grids: CTAs per SM bounded by tensor memory (512 columns) and 8.
+static int radial_grid(int tiles, int cols) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, std::min(tiles, sms * std::min(8, 512 / cols)));
+}
+
+int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float* W1, const float* W2, float rc,
+                     int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st) {
+  if (n_tiles32 <= 0) return MLIP_OK;
+  if (H != kRH) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
+  const int tiles = (n_tiles32 * kZ2Tile + kRM - 1) / kRM;
+  const int smem = 2 * kAOpBytes + 2 * kBOpBytes;
+  MLIP_CUDA_TRY(cudaFuncSetAttribute(radial_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  {
+    MLIP_PROF("radial_tc", st);
+    radial_tc<<<radial_grid(tiles, kRH), kRM, smem, st>>>(E, n_tiles32, ev, W1, W2, rc, p, use_bf16, z2t, err);
+  }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const float* W2, float rc, int p,
+                         const float* dz2, float* dr_tot, int* err, cudaStream_t st) {
+  if (E <= 0) return MLIP_OK;
+  if (H != kRH) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
+  const int tiles = (E + kRM - 1) / kRM;
+  const int smem = 2 * kAOpBytes + 4 * kBOpBytes;
+  MLIP_CUDA_TRY(cudaFuncSetAttribute(radial_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  {
+    MLIP_PROF("radial_bwd_tc", st);
+    radial_bwd_tc<<<radial_grid(tiles, 2 * kRH), kRM, smem, st>>>(E, ev, W1, W2, rc, p, dz2, dr_tot, err);
+  }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+}  // namespace mlip
