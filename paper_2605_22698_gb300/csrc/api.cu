@@ -186,6 +186,33 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
       M->w3_goff.push_back(goff);
       all.insert(all.end(), img.begin(), img.end());
     }
+    {  // split FP16 images of the mix weights
+      std::vector<uint8_t> imgs, f, b;
+      std::vector<float> scales, sc;
+      const size_t per = (size_t)(M->L + 1) * 2 * 128 * 128 * 2;
+      for (int t = 0; t < M->T; ++t) {
+        pack_mix_images(M->host_weights.data() + (M->Wmix[t] - M->d_weights), M->L, f, b, sc);
+        imgs.insert(imgs.end(), f.begin(), f.end());
+        imgs.insert(imgs.end(), b.begin(), b.end());
+        scales.insert(scales.end(), sc.begin(), sc.end());
+      }
+      cudaError_t e2 = cudaMalloc(&M->d_miximg, imgs.size());
+      if (e2 == cudaSuccess) e2 = cudaMemcpy(M->d_miximg, imgs.data(), imgs.size(), cudaMemcpyHostToDevice);
+      if (e2 == cudaSuccess) e2 = cudaMalloc(&M->d_mixscale, sizeof(float) * scales.size());
+      if (e2 == cudaSuccess)
+        e2 = cudaMemcpy(M->d_mixscale, scales.data(), sizeof(float) * scales.size(), cudaMemcpyHostToDevice);
+      if (e2 != cudaSuccess) {
+        cudaGetLastError();
+        set_error("tensor-core mix weight images: %s", cudaGetErrorString(e2));
+        mlip_model_free(M);
+        return MLIP_ERR_OOM;
+      }
+      for (int t = 0; t < M->T; ++t) {
+        M->mix_fwd_img.push_back(M->d_miximg + (2 * t) * per);
+        M->mix_bwd_img.push_back(M->d_miximg + (2 * t + 1) * per);
+        M->mix_scale.push_back(M->d_mixscale + (size_t)t * (M->L + 1));
+      }
+    }
     e = cudaMalloc(&M->d_w3img, all.size());
     if (e == cudaSuccess) e = cudaMemcpy(M->d_w3img, all.data(), all.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -240,6 +267,8 @@ int mlip_model_free(mlip_model* M) {
   if (M->d_weights) cudaFree(M->d_weights);
   if (M->d_w3img) cudaFree(M->d_w3img);
   if (M->d_wmixT) cudaFree(M->d_wmixT);
+  if (M->d_miximg) cudaFree(M->d_miximg);
+  if (M->d_mixscale) cudaFree(M->d_mixscale);
   delete M;
   return MLIP_OK;
 }

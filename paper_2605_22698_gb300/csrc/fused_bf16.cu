@@ -1596,7 +1596,8 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
                               st));
     MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], M->d_w3img + M->w3_layer_off[t],
                              M->w3_goff[t], z2t[t], s, mA, mB, use_bf16, flag + 1, st));
-    MLIP_TRY(launch_mix_fwd2(n, C, L, mA, mB, M->Wmix[t], h[t], h[t + 1], u0[t], st));
+    MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
+                           nullptr, flag + 1, st));
   }
   MLIP_TRY(launch_energy(ws, b, C, D, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
   if (d_forces || d_stress) {
@@ -1618,7 +1619,8 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
     MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)b.nsys, &absmax));
     MLIP_TRY(ws.get("fz.dws2", (size_t)b.nsys, &dws2));
     for (int t = T - 1; t >= 0; --t) {
-      MLIP_TRY(launch_mix_bwd2(n, C, L, GaA, GaB, u0[t], M->WmixT[t], Gm, st));
+      MLIP_TRY(launch_mix_tc(true, n, C, L, GaA, GaB, M->mix_bwd_img[t], M->mix_scale[t], nullptr, Gm, nullptr,
+                             u0[t], flag + 1, st));
       MLIP_CUDA_TRY(cudaMemsetAsync(dz2, 0, Ec * 64 * sizeof(float), st));
       if (!use_bf16) MLIP_TRY(launch_seg_absmax2(b, D * C, h[t], Gm, absmax, st));
       {

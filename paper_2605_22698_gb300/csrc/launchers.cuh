@@ -22,10 +22,6 @@ int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const
                    float* u0, cudaStream_t st);
 int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, const float* WmixT,
                    float* Gm, cudaStream_t st);
-int launch_mix_fwd2(int n, int C, int L, const float* mA, const float* mB, const float* Wmix, const float* hin,
-                    float* hout, float* u0, cudaStream_t st);
-int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const float* u0, const float* WmixT,
-                    float* Gm, cudaStream_t st);
 int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st);
 int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st);
 // per-system energies energy[nsys] (FP64)
@@ -48,6 +44,14 @@ int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float*
                      int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st);
 int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const float* W2, float rc, int p,
                          const float* dz2, float* dr_tot, int* err, cudaStream_t st);
+
+// Channel mixes of the fused form on the tensor cores (C = 128): X (+ X2) times
+// the split weight images of one layer (pack_mix_images), forward or adjoint.
+void pack_mix_images(const float* W, int L, std::vector<uint8_t>& fwd, std::vector<uint8_t>& bwd,
+                     std::vector<float>& scale);
+int launch_mix_tc(bool bwd, int n, int C, int L, const float* X, const float* X2, const uint8_t* wimg,
+                  const float* wscale, const float* hin, float* out, float* u0, const float* u0_in, int* err,
+                  cudaStream_t st);
 
 int launch_check_inputs(int n, const double* pos, const int* species, int S, int* flag, cudaStream_t st);
 int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::vector<size_t>& group_off);

@@ -1,0 +1,262 @@
+// Per-irrep channel mixes of the fused form on the tensor cores.
+//
+// For every order l the (2l+1) N rows of node components are multiplied by
+// the C x C weight W_l (C = 128):
+//   forward:  u = m W_l;  h_out = h_in + (l == 0 ? silu(u) : u);  u0 keeps u (l = 0)
+//   adjoint:  dE/dm = Gu W_l^T,  Gu = dE/dh silu'(u0) (l = 0) or dE/dh
+// where m (or dE/dh) arrives as the sum of the two partial buffers of the
+// message kernels.  One CTA takes 128 rows of one order: thread r loads row r,
+// scales it by a power of two (largest entry in [2^13, 2^14)) and writes it
+// split into FP16 hi and lo parts as the A operand (M = 128, K = 128); the
+// B operand is the model's pre-split image of W_l^T (forward) or W_l
+// (adjoint), bulk-copied once per CTA; the product A_hi B_hi + A_lo B_hi +
+// A_hi B_lo (three tcgen05 MMA chains, FP32 accumulation, N = 128) keeps about
+// 21 significant bits.  Thread r then reads its accumulator row back from
+// tensor memory, removes both scales exactly and applies the update.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda_fp16.h>
+
+#include "kernels_common.cuh"
+#include "launchers.cuh"
+#include "profile.cuh"
+#include "sm100_tc.cuh"
+
+namespace mlip {
+namespace {
+
+constexpr int kMC = 128;                      // channels
+constexpr int kMM = 128;                      // rows per CTA (MMA M)
+constexpr int kMOp = kMM * kMC * 2;           // one 16-bit 128 x 128 operand: 32 KB
+constexpr uint32_t kMLBO = 128, kMSBO = 2048; // K-adjacent / row-group-adjacent core matrices
+
+__host__ __device__ constexpr uint32_t canon128(int r, int k) {
+  return (uint32_t)((r >> 3) * kMSBO + (k >> 3) * kMLBO + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint16_t h16(float x) {
+  const __half v = __float2half_rn(x);
+  return *reinterpret_cast<const uint16_t*>(&v);
+}
+
+__device__ __forceinline__ float pow2_scale(float amax) {
+  if (!(amax > 0.0f)) return 1.0f;
+  return exp2f((float)max(-100, min(100, 13 - ilogbf(amax))));
+}
+
+// smem: A_hi, A_lo, B_hi, B_lo (32 KB each), then the barriers
+template <bool BWD>
+__global__ void __launch_bounds__(kMM) mix_tc(int n, int L, const float* __restrict__ X, const float* __restrict__ X2,
+                                              const uint8_t* __restrict__ wimg, const float* __restrict__ wscale,
+                                              const float* __restrict__ hin, float* __restrict__ out,
+                                              float* __restrict__ u0, const float* __restrict__ u0_in,
+                                              int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sAh = smem;
+  uint8_t* sAl = smem + kMOp;
+  uint8_t* sBh = smem + 2 * kMOp;
+  uint8_t* sBl = smem + 3 * kMOp;
+  __shared__ __align__(8) uint64_t bar_w, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_s;
+  const int l = blockIdx.y, R = 2 * l + 1, D = (L + 1) * (L + 1);
+  const int rows = n * R, row0 = blockIdx.x * kMM;
+  if (row0 >= rows) return;  // uniform over the CTA
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, kMC);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&bar_w, 1);
+    tc::mbar_init(&bar_mma, 1);
+    tc::fence_mbar_init();
+    abort_s = 0;
+  }
+  __syncthreads();
+  // weight image of this order: hi then lo, 32 KB each, one bulk copy each
+  const uint8_t* wl = wimg + (size_t)l * 2 * kMOp;
+  if (tid == 0) {
+    tc::mbar_arrive_expect_tx(&bar_w, 2 * kMOp);
+    tc::bulk_g2s(sBh, wl, kMOp, &bar_w);
+    tc::bulk_g2s(sBl, wl + kMOp, kMOp, &bar_w);
+  }
+  // this thread's row, scaled and split
+  const int r = row0 + tid;
+  const bool live = r < rows;
+  const int nd = live ? r / R : 0, mm = live ? r % R : 0;
+  const size_t base = ((size_t)nd * D + l * l + mm) * kMC;
+  float v[kMC];
+  if (live) {
+    const float4* x4 = reinterpret_cast<const float4*>(X + base);
+#pragma unroll
+    for (int q = 0; q < kMC / 4; ++q) {
+      float4 a = x4[q];
+      if (X2) {
+        const float4 b = reinterpret_cast<const float4*>(X2 + base)[q];
+        a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
+      }
+      if (BWD && l == 0) {
+        const float4 u = reinterpret_cast<const float4*>(u0_in + (size_t)nd * kMC)[q];
+        a.x *= silu_grad_f(u.x); a.y *= silu_grad_f(u.y); a.z *= silu_grad_f(u.z); a.w *= silu_grad_f(u.w);
+      }
+      v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kMC; ++k) v[k] = 0.0f;
+  }
+  float amax = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kMC; ++k) amax = fmaxf(amax, fabsf(v[k]));
+  const float sc = pow2_scale(amax);
+#pragma unroll
+  for (int kg = 0; kg < kMC / 8; ++kg) {
+    uint32_t ph[4], pl[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint16_t hh[2], ll[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const float x = v[kg * 8 + 2 * q + j] * sc;
+        const __half h = __float2half_rn(x);
+        hh[j] = *reinterpret_cast<const uint16_t*>(&h);
+        ll[j] = h16(x - __half2float(h));
+      }
+      ph[q] = (uint32_t)hh[0] | ((uint32_t)hh[1] << 16);
+      pl[q] = (uint32_t)ll[0] | ((uint32_t)ll[1] << 16);
+    }
+    *reinterpret_cast<uint4*>(sAh + canon128(tid, kg * 8)) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    *reinterpret_cast<uint4*>(sAl + canon128(tid, kg * 8)) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+  }
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  bool issued = false;
+  if (tid == 0) {
+    if (tc::mbar_wait(&bar_w, 0)) {
+      tc::fence_after_sync();
+      const uint32_t idesc = tc::idesc_16bit(kMM, kMC, false);
+      const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+      const uint32_t as[3] = {ah, al, ah}, bs[3] = {bh, bh, bl};
+#pragma unroll 1
+      for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+        for (int kk = 0; kk < kMC / 16; ++kk) {
+          const uint64_t ad = tc::desc_noswizzle(as[pass] + kk * 256, kMLBO, kMSBO);
+          const uint64_t bd = tc::desc_noswizzle(bs[pass] + kk * 256, kMLBO, kMSBO);
+          tc::mma_bf16(tmem_base, ad, bd, idesc, (pass | kk) ? 1u : 0u);
+        }
+      tc::mma_commit(&bar_mma);
+      issued = true;
+    } else {
+      atomicOr(err, 128);
+      abort_s = 1;
+    }
+  }
+  __syncthreads();
+  if (!abort_s) {
+    if (!tc::mbar_wait(&bar_mma, 0)) {
+      atomicOr(err, 128);
+      abort_s = 1;
+    }
+  }
+  __syncthreads();  // abort_s is uniform from here on
+  tc::fence_after_sync();
+  if (!abort_s) {  // every warp reads its lanes (tcgen05.ld is warp-collective)
+    const float inv = 1.0f / (sc * wscale[l]);
+    const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16);
+    float4* o4 = reinterpret_cast<float4*>(out + base);
+    const float4* h4 = reinterpret_cast<const float4*>(hin + base);
+    float4* u4 = reinterpret_cast<float4*>(u0 + (size_t)nd * kMC);
+#pragma unroll 1
+    for (int c0 = 0; c0 < kMC; c0 += 32) {
+      float w[32];
+#pragma unroll
+      for (int c = 0; c < 32; c += 8) tc::tmem_ld8(taddr + c0 + c, w + c);
+      tc::tmem_ld_wait();
+      if (!live) continue;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float4 u = make_float4(w[4 * q] * inv, w[4 * q + 1] * inv, w[4 * q + 2] * inv, w[4 * q + 3] * inv);
+        const int i4 = c0 / 4 + q;
+        if (BWD) {
+          o4[i4] = u;
+        } else {
+          const float4 h = h4[i4];
+          if (l == 0) {
+            u4[i4] = u;
+            o4[i4] = make_float4(h.x + silu_f(u.x), h.y + silu_f(u.y), h.z + silu_f(u.z), h.w + silu_f(u.w));
+          } else {
+            o4[i4] = make_float4(h.x + u.x, h.y + u.y, h.z + u.z, h.w + u.w);
+          }
+        }
+      }
+    }
+  }
+  if (tid == 0) {
+    if (abort_s && issued) tc::mbar_wait(&bar_mma, 0, 1LL << 20);  // the product in flight, bounded
+    if (abort_s && !issued) tc::mbar_wait(&bar_w, 0, 1LL << 20);   // the weight copies in flight
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem_base, kMC);
+}
+
+}  // namespace
+
+// Split FP16 images of the mix weights of one layer: per order l, for the
+// forward B[n][k] = W_l[k][n] and for the adjoint B[n][k] = W_l[n][k], each as
+// hi (32 KB) then lo (32 KB) in the canonical layout, times a power-of-two
+// scale per order (scale[l]).  fwd/bwd receive (L+1) * 64 KB each.
+void pack_mix_images(const float* W, int L, std::vector<uint8_t>& fwd, std::vector<uint8_t>& bwd,
+                     std::vector<float>& scale) {
+  const int C = kMC;
+  fwd.assign((size_t)(L + 1) * 2 * kMOp, 0);
+  bwd.assign((size_t)(L + 1) * 2 * kMOp, 0);
+  scale.assign(L + 1, 1.0f);
+  for (int l = 0; l <= L; ++l) {
+    const float* Wl = W + (size_t)l * C * C;
+    float amax = 0.0f;
+    for (int q = 0; q < C * C; ++q) amax = std::max(amax, std::fabs(Wl[q]));
+    const float sc = amax > 0.0f ? std::ldexp(1.0f, 13 - std::ilogb(amax)) : 1.0f;
+    scale[l] = sc;
+    for (int n = 0; n < C; ++n)
+      for (int k = 0; k < C; ++k) {
+        for (int which = 0; which < 2; ++which) {
+          const float x = (which == 0 ? Wl[k * C + n] : Wl[n * C + k]) * sc;
+          const __half h = __float2half_rn(x);
+          const __half lo = __float2half_rn(x - __half2float(h));
+          std::vector<uint8_t>& img = which == 0 ? fwd : bwd;
+          uint8_t* o = img.data() + (size_t)l * 2 * kMOp + canon128(n, k);
+          std::memcpy(o, &h, 2);
+          std::memcpy(o + kMOp, &lo, 2);
+        }
+      }
+  }
+}
+
+int launch_mix_tc(bool bwd, int n, int C, int L, const float* X, const float* X2, const uint8_t* wimg,
+                  const float* wscale, const float* hin, float* out, float* u0, const float* u0_in, int* err,
+                  cudaStream_t st) {
+  if (n <= 0) return MLIP_OK;
+  if (C != kMC) { set_error("the fused form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
+  const int smem = 4 * kMOp;
+  dim3 grid((n * (2 * L + 1) + kMM - 1) / kMM, L + 1);
+  if (bwd) {
+    MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MLIP_PROF("mix_tc_bwd", st);
+    mix_tc<true><<<grid, kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err);
+  } else {
+    MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MLIP_PROF("mix_tc", st);
+    mix_tc<false><<<grid, kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err);
+  }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
+}  // namespace mlip

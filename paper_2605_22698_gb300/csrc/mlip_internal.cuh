@@ -144,6 +144,12 @@ struct mlip_model {
   std::vector<const float*> W1, W2, W3, Wmix;
   float* d_wmixT = nullptr;            // channel-mix weights transposed, per layer and order
   std::vector<const float*> WmixT;
+  // fused form: split FP16 tensor-core images of the mix weights per layer
+  // (forward and adjoint, (L+1) x 64 KB each) and their per-order scales
+  uint8_t* d_miximg = nullptr;
+  float* d_mixscale = nullptr;
+  std::vector<const uint8_t*> mix_fwd_img, mix_bwd_img;
+  std::vector<const float*> mix_scale;
   // fused form: W3 of every layer as BF16 tensor-core operands, grouped by path group
   uint8_t* d_w3img = nullptr;
   std::vector<size_t> w3_layer_off;

@@ -767,28 +767,4 @@ int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const f
   return MLIP_OK;
 }
 
-int launch_mix_fwd2(int n, int C, int L, const float* mA, const float* mB, const float* Wmix, const float* hin,
-                    float* hout, float* u0, cudaStream_t st) {
-  if (n <= 0) return MLIP_OK;
-  if (C != 128) { set_error("the fused form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
-  const size_t smem = (size_t)(128 * 128 + kMixRows * kMixAS) * sizeof(float);
-  MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
-  { MLIP_PROF("mix_fwd", st); mix_gemm<false><<<grid, 128, smem, st>>>(n, L, mA, mB, Wmix, hin, hout, u0, nullptr); }
-  MLIP_LAUNCH_CHECK();
-  return MLIP_OK;
-}
-
-int launch_mix_bwd2(int n, int C, int L, const float* GA, const float* GB, const float* u0, const float* WmixT,
-                    float* Gm, cudaStream_t st) {
-  if (n <= 0) return MLIP_OK;
-  if (C != 128) { set_error("the fused form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
-  const size_t smem = (size_t)(128 * 128 + kMixRows * kMixAS) * sizeof(float);
-  MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
-  { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, GA, GB, WmixT, nullptr, Gm, nullptr, u0); }
-  MLIP_LAUNCH_CHECK();
-  return MLIP_OK;
-}
-
 }  // namespace mlip
