@@ -48,6 +48,11 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the same code (profiles/tp_fused_bwd_water3000.md: mean over the
+# four path-group launches of one evaluation), keyed by (workload, precision).
+NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): 147.7e6}
+
 # FP32 ALU peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
 # lanes x 2 flop (FMA) x 2.07 GHz.
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -306,7 +311,8 @@ def run_ours(args, rank, world):
             per_step = flops[name]
             achieved = per_step * args.steps / (tot_ms / 1e3) / 1e12
             roof = {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_ALU_TFLOPS, 1),
-                    "unit": "TFLOP/s", "frac": round(achieved / FP32_ALU_TFLOPS, 4), "traffic": None,
+                    "unit": "TFLOP/s", "frac": round(achieved / FP32_ALU_TFLOPS, 4),
+                    "traffic": NCU_TRAFFIC.get((args.workload, args.precision, name)),
                     "launches": nl, "avg_launch_ms": round(tot_ms / nl, 5),
                     "peak_src": "FP32 ALU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, not measured)"}
             if name in ("tp_fused", "tp_fused_bwd"):
