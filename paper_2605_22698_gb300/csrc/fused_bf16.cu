@@ -1186,6 +1186,370 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
   if (warp == 0) tc::tmem_dealloc(tbase, BL::NCOLS);
 }
 
+
+// ------------------------------------------------- tp_fused_bwd, pipelined
+// Groups that hold one CTA per SM run a warp-specialised form of the same
+// adjoint: warps 0..7 are the two warp sets of the per-edge work; warps 8 and
+// 9 prepare each tile one ahead (receiver/sender ids, harmonics, per-system
+// scales, c*Y products, and the first product w = W3^T z2 into one of two
+// tensor-memory buffers) and drain it one behind (dE/dz2 from the second
+// product's accumulator, which sits in tensor-memory lanes 0..63 that warps 8
+// and 9 can read).  Tile buffers alternate by tile parity b:
+//   full[b]   64 producer arrivals + the first product's commit
+//   mma2[b]   the second product's commit; consumer thread 0 issues it after
+//             the consumers' named barrier, so it also marks the buffer consumed.
+// The producer prepares tile it + 1 before it drains tile it, and prepares a
+// buffer only after draining the tile that last used it.
+constexpr int kWSConsumers = 256, kWSProducers = 64, kWSThreads = kWSConsumers + kWSProducers;
+
+template <int L, int MODE>
+struct BwdLayoutWS {
+  using G = Group<L, MODE>;
+  static constexpr int NP = G::NP;
+  static constexpr bool FIRST = MODE < 0;
+  static constexpr int B2_BYTES = kNT * NP * 128 * 2;
+  static constexpr int NZ = FIRST ? 0 : G::NZ;
+  static constexpr int NZP = FIRST ? 4 : G::NZP;
+  static constexpr int tmem_cols() {
+    int need = 2 * (NP + 1) * kNT, c = 32;
+    while (c < need) c <<= 1;
+    return c;
+  }
+  static constexpr int NCOLS = tmem_cols();
+  static constexpr size_t rest = 2 * kTileBytes + (size_t)2 * kNT * NZP * 4 + 2 * kNT * 16 * 4 + 8 * kNT * 16 * 4 +
+                                 (size_t)NZP * 4 + (((size_t)NZP + 15) & ~(size_t)15) + 4 * kNT * 4 + 4 * kNT * 4 + 128;
+  static constexpr int NB2 = (size_t)NP * kW3PathBytes + rest + 2 * (size_t)B2_BYTES <= 231424 ? 2 : 1;
+  static constexpr size_t off_z2 = (size_t)NP * kW3PathBytes;
+  static constexpr size_t off_b2 = off_z2 + 2 * kTileBytes;
+  static constexpr size_t off_cy = off_b2 + (size_t)NB2 * B2_BYTES;   // [2][kNT][NZP]
+  static constexpr size_t off_y = off_cy + (size_t)2 * kNT * NZP * 4; // [2][kNT][16]
+  static constexpr size_t off_red = off_y + 2 * kNT * 16 * 4;         // [8 warps][kNT][16]
+  static constexpr size_t off_tab = off_red + 8 * kNT * 16 * 4;
+  static constexpr size_t off_taby = off_tab + (size_t)NZP * 4;
+  static constexpr size_t off_idx = off_taby + (((size_t)NZP + 15) & ~(size_t)15);  // [2][send kNT, recv kNT]
+  static constexpr size_t off_dws = off_idx + 4 * kNT * 4;                          // [2][scale kNT, inverse kNT]
+  static constexpr size_t off_bar = off_dws + 4 * kNT * 4;
+  static constexpr size_t bytes = off_bar + 128;
+  // groups whose buffers do not fit keep the single-role kernel
+  static constexpr bool fits = bytes <= 232448 - 1024 && NCOLS <= 512;
+};
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(kWSThreads, 1)
+    tp_fused_bwd_ws(int n, const int* __restrict__ row_ptr, const int* __restrict__ recv,
+                    const int* __restrict__ send, const float* __restrict__ Yg, const float* __restrict__ hprev,
+                    const float* __restrict__ Gm, const uint8_t* __restrict__ w3img, const uint8_t* __restrict__ z2t,
+                    float s, const float* __restrict__ GinA, const float* __restrict__ GinB,
+                    float* __restrict__ GoutA, float* __restrict__ GoutB, int first_group, float* __restrict__ dY,
+                    float* __restrict__ dz2, int use_bf16, const int* __restrict__ sys_of,
+                    const float2* __restrict__ dws2, int* __restrict__ err) {
+  using G = Group<L, MODE>;
+  using BL = BwdLayoutWS<L, MODE>;
+  static_assert(BL::fits, "shared or tensor memory of the pipelined adjoint kernel exceeds the per-SM limits");
+  constexpr int D = NodeDims<L>::D;
+  constexpr int NP = G::NP;
+  constexpr bool FIRST = BL::FIRST;
+  constexpr int NZ = BL::NZ, NZP = BL::NZP;
+  constexpr int SBO2 = NP * 2048;  // B' operand: K' = NP * 128 channels
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sW3 = smem;
+  uint8_t* sZ2 = smem + BL::off_z2;
+  uint8_t* sB2base = smem + BL::off_b2;
+  float* cYb = reinterpret_cast<float*>(smem + BL::off_cy);
+  float* sYb = reinterpret_cast<float*>(smem + BL::off_y);
+  float* red = reinterpret_cast<float*>(smem + BL::off_red);
+  float* tab_c = reinterpret_cast<float*>(smem + BL::off_tab);
+  uint8_t* tab_y = smem + BL::off_taby;
+  int* idxb = reinterpret_cast<int*>(smem + BL::off_idx);
+  float* dwsb = reinterpret_cast<float*>(smem + BL::off_dws);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BL::off_bar);
+  uint64_t* bar_w3 = bars;
+  uint64_t* bar_z2 = bars + 1;    // [2]
+  uint64_t* bar_full = bars + 3;  // [2]
+  uint64_t* bar_mma2 = bars + 5;  // [2]
+  uint64_t* bar_fin = bars + 7;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 8);
+  __shared__ volatile int abort_s;
+  __shared__ int abort_c;  // consumers' copy, written by consumer thread 0 before their barrier
+  __shared__ int abort_p;  // producers' copy, written by the elected producer before theirs
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, BL::NCOLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(bar_w3, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(bar_z2 + b, 1);
+      tc::mbar_init(bar_full + b, kWSProducers + 1);
+      tc::mbar_init(bar_mma2 + b, 1);
+    }
+    tc::mbar_init(bar_fin, 2);
+    tc::fence_mbar_init();
+    abort_s = 0;
+    abort_c = 0;
+    abort_p = 0;
+  }
+  if constexpr (!FIRST) load_group_table<L, MODE, true>(tab_c, tab_y);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tmem_holder;
+  const uint32_t wcol0 = 0, wcol1 = NP * kNT, dcol0 = 2 * NP * kNT, dcol1 = 2 * NP * kNT + kNT;
+
+  int i0, i1;
+  block_receivers(row_ptr, n, blockIdx.x, gridDim.x, &i0, &i1);
+  const int E0 = row_ptr[i0], E1 = row_ptr[i1];
+  const int t_begin = E0 / kNT, t_end = (E1 > E0) ? (E1 + kNT - 1) / kNT : t_begin;
+  const int n_tiles = t_end - t_begin;
+  const uint32_t idesc1 = tc::idesc_16bit(128, kNT, use_bf16 != 0);
+  const uint32_t idesc2 = idesc1 | (1u << 15);  // A M-major
+
+  if (warp >= 8) {
+    // ---------------------------------------------------------- producers
+    const int pt = tid - kWSConsumers;  // 0..63
+    const bool elect = pt == 0;
+    int z2_issued[2] = {0, 0}, z2_waited[2] = {0, 0};
+    bool w3_waited = false;
+    if (elect && n_tiles > 0) {
+      tc::mbar_arrive_expect_tx(bar_w3, NP * kW3PathBytes);
+#pragma unroll 1
+      for (int sl = 0; sl < NP; ++sl)
+        tc::bulk_g2s(sW3 + sl * kW3PathBytes, w3img + (size_t)sl * kW3PathBytes, kW3PathBytes, bar_w3);
+    }
+    // tile it into buffer b = it & 1
+    auto setup = [&](int it) {
+      const int b = it & 1, tile = t_begin + it;
+      int* s_send = idxb + b * 2 * kNT;
+      int* s_recv = s_send + kNT;
+      float* s_dws = dwsb + b * 2 * kNT;
+      float* sY = sYb + b * kNT * 16;
+      float* cY = cYb + b * kNT * NZP;
+      if (elect) {
+        tc::mbar_arrive_expect_tx(bar_z2 + b, kTileBytes);
+        tc::bulk_g2s(sZ2 + b * kTileBytes, z2t + (size_t)tile * kTileBytes, kTileBytes, bar_z2 + b);
+        z2_issued[b]++;
+      }
+      if (pt < kNT) {
+        const int e = tile * kNT + pt;
+        const bool valid = e >= E0 && e < E1;
+        const int r = valid ? recv[e] : -1;
+        s_recv[pt] = r;
+        s_send[pt] = valid ? send[e] : 0;
+        const float2 v = valid ? dws2[sys_of ? sys_of[r] : 0] : make_float2(1.0f, 1.0f);
+        s_dws[pt] = v.x;
+        s_dws[kNT + pt] = v.y;
+      }
+      for (int q = pt; q < kNT * 4; q += kWSProducers) {
+        const int t = q >> 2, e = tile * kNT + t;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e >= E0 && e < E1) v = reinterpret_cast<const float4*>(Yg)[(size_t)e * 4 + (q & 3)];
+        reinterpret_cast<float4*>(sY)[q] = v;
+      }
+      tc::named_bar(1, kWSProducers);
+      if constexpr (NZ > 0) {
+        for (int q = pt; q < kNT * NZ; q += kWSProducers) {
+          const int t = q / NZ, k = q - t * NZ;
+          cY[t * NZP + k] = tab_c[k] * sY[t * 16 + tab_y[k]];
+        }
+      }
+      if (elect) {
+        bool ok = true;
+        if (!w3_waited) ok = w3_waited = tc::mbar_wait(bar_w3, 0);
+        ok = ok && tc::mbar_wait(bar_z2 + b, (uint32_t)(z2_waited[b] & 1));
+        if (ok) {
+          z2_waited[b]++;
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sZ2 + b * kTileBytes);
+          const uint32_t wcol = b ? wcol1 : wcol0;
+#pragma unroll 1
+          for (int sl = 0; sl < NP; ++sl)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+              const uint64_t bd = tc::desc_noswizzle(b0 + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+              tc::mma_bf16(tbase + wcol + sl * kNT, ad, bd, idesc1, kk > 0 ? 1u : 0u);
+            }
+          tc::mma_commit(bar_full + b);
+        } else {
+          atomicOr(err, 4);
+          abort_s = 1;
+          tc::mbar_arrive(bar_full + b);  // completes the phase so the consumers see the abort
+        }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(bar_full + b);
+    };
+    // dE/dz2 of tile it from the second product (lanes 0..63 = hidden units)
+    // (a failed wait only raises the abort; the warp-collective tensor-memory
+    // loads still run on every lane, and the loop stops at the next uniform check)
+    auto drain = [&](int it) {
+      const int b = it & 1, tile = t_begin + it;
+      const float* s_dws = dwsb + b * 2 * kNT;
+      if (!tc::mbar_wait(bar_mma2 + b, (uint32_t)((it >> 1) & 1))) {
+        atomicOr(err, 16);
+        abort_s = 1;
+      }
+      tc::fence_after_sync();
+      const uint32_t taddr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (b ? dcol1 : dcol0);
+#pragma unroll 1
+      for (int ch = 0; ch < kNT / 8; ++ch) {
+        float v[8];
+        tc::tmem_ld8(taddr + ch * 8, v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int e = tile * kNT + ch * 8 + j;
+          if (e >= E0 && e < E1) atomicAdd(&dz2[(size_t)e * 64 + pt], v[j] * s_dws[kNT + ch * 8 + j]);
+        }
+      }
+      tc::fence_before_sync();
+    };
+    // the same decision for all producer threads (named barriers must not diverge)
+    auto stop = [&]() -> bool {
+      if (elect) abort_p = abort_s;
+      tc::named_bar(1, kWSProducers);
+      const bool st = abort_p != 0;
+      tc::named_bar(1, kWSProducers);
+      return st;
+    };
+    if (n_tiles > 0) setup(0);
+#pragma unroll 1
+    for (int it = 0; it < n_tiles; ++it) {
+      if (stop()) break;
+      if (it + 1 < n_tiles) setup(it + 1);  // its buffer was drained at it - 1
+      drain(it);
+    }
+    if (elect) {
+      for (int b = 0; b < 2; ++b)
+        while (z2_waited[b] < z2_issued[b]) {
+          if (!tc::mbar_wait(bar_z2 + b, (uint32_t)(z2_waited[b] & 1), 1LL << 20)) break;
+          z2_waited[b]++;
+        }
+      if (n_tiles > 0 && !w3_waited) tc::mbar_wait(bar_w3, 0, 1LL << 20);
+      tc::mma_commit(bar_fin);  // every first product issued by this thread
+    }
+  } else {
+    // ---------------------------------------------------------- consumers
+    using S = Split<L, MODE, true>;
+    constexpr bool heavy0 = S::dh(0) + (FIRST ? 0 : G::NOUT) > 8, heavy1 = S::dh(1) + (FIRST ? 0 : G::NOUT) > 8;
+    const int wsid = warp >> 2, c = tid & 127;
+    float* GoutW = wsid == 0 ? GoutA : GoutB;
+    const uint32_t taddr0 = tbase + ((uint32_t)((warp & 3) * 32) << 16);
+    float Gacc[D], Gt[G::NOUT];
+#pragma unroll
+    for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < G::NOUT; ++q) Gt[q] = 0.0f;
+    int cur = i0 - 1;
+#pragma unroll 1
+    for (int it = 0; it < n_tiles; ++it) {
+      const int b = it & 1, tile = t_begin + it;
+      if (!tc::mbar_wait(bar_full + b, (uint32_t)((it >> 1) & 1))) {
+        atomicOr(err, 8);
+        abort_s = 1;
+      }
+      if constexpr (BL::NB2 == 1) {  // one dE/dw tile: the previous second product must have read it
+        if (it > 0 && !tc::mbar_wait(bar_mma2 + ((it - 1) & 1), (uint32_t)(((it - 1) >> 1) & 1))) {
+          atomicOr(err, 16);
+          abort_s = 1;
+        }
+      }
+      if (tid == 0) abort_c = abort_s;
+      tc::named_bar(2, kWSConsumers);
+      if (abort_c) break;
+      tc::fence_after_sync();
+      const int* s_send = idxb + b * 2 * kNT;
+      const int* s_recv = s_send + kNT;
+      const float* sY = sYb + b * kNT * 16;
+      const float* cY = cYb + b * kNT * NZP;
+      const float* s_dws = dwsb + b * 2 * kNT;
+      uint8_t* sB2 = sB2base + (BL::NB2 == 2 ? b : 0) * BL::B2_BYTES;
+      const uint32_t tw = taddr0 + (b ? wcol1 : wcol0);
+      if (wsid == 0) {
+        if constexpr (heavy0)
+          bwd_tile_ws_roll<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group,
+                                       cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
+        else
+          bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group, cur,
+                                  Gacc, Gt, red, sB2, s, s_dws, use_bf16);
+      } else {
+        if constexpr (heavy1)
+          bwd_tile_ws_roll<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group,
+                                       cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
+        else
+          bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group, cur,
+                                  Gacc, Gt, red, sB2, s, s_dws, use_bf16);
+      }
+      // second product: dE/dz2 = W3 dE/dw over this tile, drained by the producers
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      tc::named_bar(2, kWSConsumers);
+      if (tid == 0) {
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sB2);
+        const uint32_t kstride = 1024, mstride = 128;
+        const uint32_t lbo = kMnLboIsK ? kstride : mstride, sbo = kMnLboIsK ? mstride : kstride;
+        const uint32_t dcol = b ? dcol1 : dcol0;
+#pragma unroll 1
+        for (int sl = 0; sl < NP; ++sl)
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 2 * kstride, lbo, sbo);
+            const uint64_t bd = tc::desc_noswizzle(b0 + sl * 2048 + kk * 256, 128, SBO2);
+            tc::mma_bf16(tbase + dcol, ad, bd, idesc2, (sl | kk) ? 1u : 0u);
+          }
+        tc::mma_commit(bar_mma2 + b);
+      }
+      // channel sums of dE/dY
+      {
+        constexpr int m0 = S::ymask(0), m1 = S::ymask(1);
+        for (int q = tid; q < kNT * 16; q += kWSConsumers) {
+          const int t = q >> 4, k = q & 15;
+          const int e = tile * kNT + t;
+          if (e >= E0 && e < E1 && ((m0 | m1) >> k & 1)) {
+            float v = 0.0f;
+            if (m0 >> k & 1) {
+#pragma unroll
+              for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
+            }
+            if (m1 >> k & 1) {
+#pragma unroll
+              for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
+            }
+            atomicAdd(&dY[(size_t)e * 16 + k], v);  // one add per kernel and address: deterministic
+          }
+        }
+      }
+      tc::named_bar(2, kWSConsumers);  // the reduction buffer is read before the next tile writes it
+    }
+    if (!abort_c) {
+      // remaining receivers of the range
+      while (cur < i1) {
+        if (cur >= i0 && !FIRST) {
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            const size_t o = ((size_t)cur * D + d) * 128 + c;
+            if (!first_group) atomicAdd(&GoutW[o], Gacc[d]);
+            else GoutW[o] = (wsid == 0 ? GinA[o] + GinB[o] : 0.0f) + Gacc[d];
+          }
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) Gacc[d] = 0.0f;
+        ++cur;
+      }
+    }
+    if (tid == 0) tc::mma_commit(bar_fin);  // every second product issued by this thread
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid == 0) tc::mbar_wait(bar_fin, 0, 1LL << 20);  // no product in flight, bounded
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tbase, BL::NCOLS);
+}
+
 // Per-system scale of dE/dw in the adjoint's second product (FP16 operands)
 // and its inverse: |dE/dw| <= 17 max|h| s max|Gm| (orthonormal CG rows,
 // |Y| <= 1), so the power of two 2^floor(log2(2^14 / (32 max|h| s max|Gm|)))
@@ -1349,6 +1713,21 @@ int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send
                      float* dz2, int use_bf16, const int* sys_of, const float2* dws2, int* err, int blocks,
                      cudaStream_t st) {
   using BL = BwdLayout<L, MODE>;
+  if constexpr (ctas_per_sm(BL::bytes) == 1 && BwdLayoutWS<L, MODE>::fits) {  // one CTA per SM: pipelined
+    using BW = BwdLayoutWS<L, MODE>;
+    const size_t smem = BW::bytes;
+    MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused_bwd_ws<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    blocks = std::min(n, blocks);
+    {
+      MLIP_PROF("tp_fused_bwd", st);
+      tp_fused_bwd_ws<L, MODE><<<blocks, kWSThreads, smem, st>>>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img, z2t,
+                                                                  s, GinA, GinB, GoutA, GoutB, first_group, dY, dz2,
+                                                                  use_bf16, sys_of, dws2, err);
+    }
+    MLIP_LAUNCH_CHECK();
+    return MLIP_OK;
+  }
   const size_t smem = BL::bytes;
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused_bwd<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   blocks = std::min(n, blocks * resident_ctas(tp_fused_bwd<L, MODE>, smem, BL::NCOLS));
