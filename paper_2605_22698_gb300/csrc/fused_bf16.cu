@@ -1189,17 +1189,20 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
 
 // ------------------------------------------------- tp_fused_bwd, pipelined
 // Groups that hold one CTA per SM run a warp-specialised form of the same
-// adjoint: warps 0..7 are the two warp sets of the per-edge work; warps 8 and
+// adjoint: warps 0..7 (two warp sets) do only the per-edge work; warps 8 and
 // 9 prepare each tile one ahead (receiver/sender ids, harmonics, per-system
-// scales, c*Y products, and the first product w = W3^T z2 into one of two
-// tensor-memory buffers) and drain it one behind (dE/dz2 from the second
-// product's accumulator, which sits in tensor-memory lanes 0..63 that warps 8
-// and 9 can read).  Tile buffers alternate by tile parity b:
+// scales, c*Y products, the first product w = W3^T z2 into one of two
+// tensor-memory buffers) and finish it one behind (the second product
+// dE/dz2 = W3 dE/dw, the channel sums of dE/dY, and dE/dz2 read back from
+// tensor-memory lanes 0..63, which warps 8 and 9 can read).  Tile buffers
+// alternate by tile parity b; mbarriers order the roles:
 //   full[b]   64 producer arrivals + the first product's commit
-//   mma2[b]   the second product's commit; consumer thread 0 issues it after
-//             the consumers' named barrier, so it also marks the buffer consumed.
-// The producer prepares tile it + 1 before it drains tile it, and prepares a
-// buffer only after draining the tile that last used it.
+//   done[b]   256 consumer arrivals: the tile's dE/dw and dE/dY partials are written
+//   mma2[b]   the second product's commit
+// The producer prepares tile it + 1 before it finishes tile it, and prepares a
+// buffer only after finishing the tile that last used it.  Long waits of the
+// producers sleep between polls so that they leave the issue slots to the
+// consumers.
 constexpr int kWSConsumers = 256, kWSProducers = 64, kWSThreads = kWSConsumers + kWSProducers;
 
 template <int L, int MODE>
@@ -1216,15 +1219,15 @@ struct BwdLayoutWS {
     return c;
   }
   static constexpr int NCOLS = tmem_cols();
-  static constexpr size_t rest = 2 * kTileBytes + (size_t)2 * kNT * NZP * 4 + 2 * kNT * 16 * 4 + 8 * kNT * 16 * 4 +
+  static constexpr size_t rest = 2 * kTileBytes + (size_t)2 * kNT * NZP * 4 + 2 * kNT * 16 * 4 + 16 * kNT * 16 * 4 +
                                  (size_t)NZP * 4 + (((size_t)NZP + 15) & ~(size_t)15) + 4 * kNT * 4 + 4 * kNT * 4 + 128;
   static constexpr int NB2 = (size_t)NP * kW3PathBytes + rest + 2 * (size_t)B2_BYTES <= 231424 ? 2 : 1;
   static constexpr size_t off_z2 = (size_t)NP * kW3PathBytes;
   static constexpr size_t off_b2 = off_z2 + 2 * kTileBytes;
   static constexpr size_t off_cy = off_b2 + (size_t)NB2 * B2_BYTES;   // [2][kNT][NZP]
   static constexpr size_t off_y = off_cy + (size_t)2 * kNT * NZP * 4; // [2][kNT][16]
-  static constexpr size_t off_red = off_y + 2 * kNT * 16 * 4;         // [8 warps][kNT][16]
-  static constexpr size_t off_tab = off_red + 8 * kNT * 16 * 4;
+  static constexpr size_t off_red = off_y + 2 * kNT * 16 * 4;         // [2][8 warps][kNT][16]
+  static constexpr size_t off_tab = off_red + 16 * kNT * 16 * 4;
   static constexpr size_t off_taby = off_tab + (size_t)NZP * 4;
   static constexpr size_t off_idx = off_taby + (((size_t)NZP + 15) & ~(size_t)15);  // [2][send kNT, recv kNT]
   static constexpr size_t off_dws = off_idx + 4 * kNT * 4;                          // [2][scale kNT, inverse kNT]
@@ -1257,7 +1260,7 @@ __global__ void __launch_bounds__(kWSThreads, 1)
   uint8_t* sB2base = smem + BL::off_b2;
   float* cYb = reinterpret_cast<float*>(smem + BL::off_cy);
   float* sYb = reinterpret_cast<float*>(smem + BL::off_y);
-  float* red = reinterpret_cast<float*>(smem + BL::off_red);
+  float* redb = reinterpret_cast<float*>(smem + BL::off_red);
   float* tab_c = reinterpret_cast<float*>(smem + BL::off_tab);
   uint8_t* tab_y = smem + BL::off_taby;
   int* idxb = reinterpret_cast<int*>(smem + BL::off_idx);
@@ -1267,11 +1270,11 @@ __global__ void __launch_bounds__(kWSThreads, 1)
   uint64_t* bar_z2 = bars + 1;    // [2]
   uint64_t* bar_full = bars + 3;  // [2]
   uint64_t* bar_mma2 = bars + 5;  // [2]
-  uint64_t* bar_fin = bars + 7;
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 8);
+  uint64_t* bar_done = bars + 7;  // [2]
+  uint64_t* bar_fin = bars + 9;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 10);
   __shared__ volatile int abort_s;
-  __shared__ int abort_c;  // consumers' copy, written by consumer thread 0 before their barrier
-  __shared__ int abort_p;  // producers' copy, written by the elected producer before theirs
+  __shared__ int abort_p;  // producers' copy, written by the elected producer before their barrier
 
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
@@ -1284,11 +1287,11 @@ __global__ void __launch_bounds__(kWSThreads, 1)
       tc::mbar_init(bar_z2 + b, 1);
       tc::mbar_init(bar_full + b, kWSProducers + 1);
       tc::mbar_init(bar_mma2 + b, 1);
+      tc::mbar_init(bar_done + b, kWSConsumers);
     }
-    tc::mbar_init(bar_fin, 2);
+    tc::mbar_init(bar_fin, 1);
     tc::fence_mbar_init();
     abort_s = 0;
-    abort_c = 0;
     abort_p = 0;
   }
   if constexpr (!FIRST) load_group_table<L, MODE, true>(tab_c, tab_y);
@@ -1381,18 +1384,61 @@ __global__ void __launch_bounds__(kWSThreads, 1)
       tc::fence_before_sync();
       tc::mbar_arrive(bar_full + b);
     };
-    // dE/dz2 of tile it from the second product (lanes 0..63 = hidden units)
-    // (a failed wait only raises the abort; the warp-collective tensor-memory
-    // loads still run on every lane, and the loop stops at the next uniform check)
+    // tile it after the consumers: the second product, the channel sums of
+    // dE/dY, and dE/dz2 read back (lanes 0..63 = hidden units).  A failed wait
+    // only raises the abort; the warp-collective tensor-memory loads still run
+    // on every lane, and the loop stops at the next uniform check.
     auto drain = [&](int it) {
       const int b = it & 1, tile = t_begin + it;
       const float* s_dws = dwsb + b * 2 * kNT;
-      if (!tc::mbar_wait(bar_mma2 + b, (uint32_t)((it >> 1) & 1))) {
+      const float* red = redb + b * 8 * kNT * 16;
+      const uint32_t dcol = b ? dcol1 : dcol0;
+      if (!tc::mbar_wait_sleep(bar_done + b, (uint32_t)((it >> 1) & 1))) {
+        atomicOr(err, 8);
+        abort_s = 1;
+      }
+      tc::fence_after_sync();
+      if (elect) {
+        const uint8_t* sB2 = sB2base + (BL::NB2 == 2 ? b : 0) * BL::B2_BYTES;
+        const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sB2);
+        const uint32_t kstride = 1024, mstride = 128;
+        const uint32_t lbo = kMnLboIsK ? kstride : mstride, sbo = kMnLboIsK ? mstride : kstride;
+#pragma unroll 1
+        for (int sl = 0; sl < NP; ++sl)
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 2 * kstride, lbo, sbo);
+            const uint64_t bd = tc::desc_noswizzle(b0 + sl * 2048 + kk * 256, 128, SBO2);
+            tc::mma_bf16(tbase + dcol, ad, bd, idesc2, (sl | kk) ? 1u : 0u);
+          }
+        tc::mma_commit(bar_mma2 + b);
+      }
+      {  // channel sums of dE/dY while the product runs
+        using S = Split<L, MODE, true>;
+        constexpr int m0 = S::ymask(0), m1 = S::ymask(1);
+        for (int q = pt; q < kNT * 16; q += kWSProducers) {
+          const int t = q >> 4, k = q & 15;
+          const int e = tile * kNT + t;
+          if (e >= E0 && e < E1 && ((m0 | m1) >> k & 1)) {
+            float v = 0.0f;
+            if (m0 >> k & 1) {
+#pragma unroll
+              for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
+            }
+            if (m1 >> k & 1) {
+#pragma unroll
+              for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
+            }
+            atomicAdd(&dY[(size_t)e * 16 + k], v);  // one add per kernel and address: deterministic
+          }
+        }
+      }
+      if (!tc::mbar_wait_sleep(bar_mma2 + b, (uint32_t)((it >> 1) & 1))) {
         atomicOr(err, 16);
         abort_s = 1;
       }
       tc::fence_after_sync();
-      const uint32_t taddr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (b ? dcol1 : dcol0);
+      const uint32_t taddr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + dcol;
 #pragma unroll 1
       for (int ch = 0; ch < kNT / 8; ++ch) {
         float v[8];
@@ -1428,7 +1474,7 @@ __global__ void __launch_bounds__(kWSThreads, 1)
           z2_waited[b]++;
         }
       if (n_tiles > 0 && !w3_waited) tc::mbar_wait(bar_w3, 0, 1LL << 20);
-      tc::mma_commit(bar_fin);  // every first product issued by this thread
+      tc::mma_commit(bar_fin);  // every product issued by this thread
     }
   } else {
     // ---------------------------------------------------------- consumers
@@ -1443,28 +1489,35 @@ __global__ void __launch_bounds__(kWSThreads, 1)
 #pragma unroll
     for (int q = 0; q < G::NOUT; ++q) Gt[q] = 0.0f;
     int cur = i0 - 1;
+    bool aborted = false;
 #pragma unroll 1
     for (int it = 0; it < n_tiles; ++it) {
-      const int b = it & 1, tile = t_begin + it;
+      const int b = it & 1;
+      if (abort_s) {
+        aborted = true;
+        break;
+      }
       if (!tc::mbar_wait(bar_full + b, (uint32_t)((it >> 1) & 1))) {
         atomicOr(err, 8);
         abort_s = 1;
+        aborted = true;
+        break;
       }
       if constexpr (BL::NB2 == 1) {  // one dE/dw tile: the previous second product must have read it
         if (it > 0 && !tc::mbar_wait(bar_mma2 + ((it - 1) & 1), (uint32_t)(((it - 1) >> 1) & 1))) {
           atomicOr(err, 16);
           abort_s = 1;
+          aborted = true;
+          break;
         }
       }
-      if (tid == 0) abort_c = abort_s;
-      tc::named_bar(2, kWSConsumers);
-      if (abort_c) break;
       tc::fence_after_sync();
       const int* s_send = idxb + b * 2 * kNT;
       const int* s_recv = s_send + kNT;
       const float* sY = sYb + b * kNT * 16;
       const float* cY = cYb + b * kNT * NZP;
       const float* s_dws = dwsb + b * 2 * kNT;
+      float* red = redb + b * 8 * kNT * 16;
       uint8_t* sB2 = sB2base + (BL::NB2 == 2 ? b : 0) * BL::B2_BYTES;
       const uint32_t tw = taddr0 + (b ? wcol1 : wcol0);
       if (wsid == 0) {
@@ -1482,49 +1535,12 @@ __global__ void __launch_bounds__(kWSThreads, 1)
           bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group, cur,
                                   Gacc, Gt, red, sB2, s, s_dws, use_bf16);
       }
-      // second product: dE/dz2 = W3 dE/dw over this tile, drained by the producers
+      // dE/dw (for the second product) and the dE/dY partials are written
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
-      tc::named_bar(2, kWSConsumers);
-      if (tid == 0) {
-        tc::fence_after_sync();
-        const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sB2);
-        const uint32_t kstride = 1024, mstride = 128;
-        const uint32_t lbo = kMnLboIsK ? kstride : mstride, sbo = kMnLboIsK ? mstride : kstride;
-        const uint32_t dcol = b ? dcol1 : dcol0;
-#pragma unroll 1
-        for (int sl = 0; sl < NP; ++sl)
-#pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 2 * kstride, lbo, sbo);
-            const uint64_t bd = tc::desc_noswizzle(b0 + sl * 2048 + kk * 256, 128, SBO2);
-            tc::mma_bf16(tbase + dcol, ad, bd, idesc2, (sl | kk) ? 1u : 0u);
-          }
-        tc::mma_commit(bar_mma2 + b);
-      }
-      // channel sums of dE/dY
-      {
-        constexpr int m0 = S::ymask(0), m1 = S::ymask(1);
-        for (int q = tid; q < kNT * 16; q += kWSConsumers) {
-          const int t = q >> 4, k = q & 15;
-          const int e = tile * kNT + t;
-          if (e >= E0 && e < E1 && ((m0 | m1) >> k & 1)) {
-            float v = 0.0f;
-            if (m0 >> k & 1) {
-#pragma unroll
-              for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
-            }
-            if (m1 >> k & 1) {
-#pragma unroll
-              for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
-            }
-            atomicAdd(&dY[(size_t)e * 16 + k], v);  // one add per kernel and address: deterministic
-          }
-        }
-      }
-      tc::named_bar(2, kWSConsumers);  // the reduction buffer is read before the next tile writes it
+      tc::mbar_arrive(bar_done + b);
     }
-    if (!abort_c) {
+    if (!aborted) {
       // remaining receivers of the range
       while (cur < i1) {
         if (cur >= i0 && !FIRST) {
@@ -1540,7 +1556,6 @@ __global__ void __launch_bounds__(kWSThreads, 1)
         ++cur;
       }
     }
-    if (tid == 0) tc::mma_commit(bar_fin);  // every second product issued by this thread
   }
   tc::fence_before_sync();
   __syncthreads();
