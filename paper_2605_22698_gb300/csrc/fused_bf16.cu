@@ -157,12 +157,41 @@ __global__ void radial_tiles(int E, int n_tiles, const float4* __restrict__ ev, 
 
 // ------------------------------------------------------------ warp sets
 // A CTA runs kWS warp sets of 4 warps (128 threads, one per channel and TMEM
-// lane).  All warp sets walk the same edges; the group's paths are split
-// between them (greedy by flop cost), and every warp set writes its partial
-// sums to an output buffer of its own (the next mix adds the buffers), so the
-// warp sets never wait for each other inside a tile.
+// lane).  Every warp set writes its partial sums to an output buffer of its
+// own (the next mix adds the buffers), so the warp sets never wait for each
+// other inside a tile.
 constexpr int kWS = 2;
 constexpr int kThreads = 128 * kWS;
+// Work split between the two warp sets of a CTA: every set runs all of the
+// group's paths (one copy of the per-edge code for both sets, each edge's
+// sender rows gathered once) on its own edges of the tile.  An edge belongs to
+// set (its position within its receiver's edge segment) & 1: a receiver's
+// edges alternate between the sets, so each set's share of a receiver, and the
+// order in which it is summed, do not depend on where tile boundaries fall
+// (a system's results do not depend on the other systems of its batch).
+constexpr bool kEdgeSplit = true;
+
+// Per-tile edge lists of the two sets, built by one warp (lane t = edge slot t).
+__device__ __forceinline__ void build_lists(int t, bool valid, int par, int* s_list, int* s_cnt) {
+  const unsigned lt = (1u << t) - 1u;
+  const unsigned m0 = __ballot_sync(0xffffffffu, valid && par == 0);
+  const unsigned m1 = __ballot_sync(0xffffffffu, valid && par == 1);
+  if (valid) {
+    if (par == 0) s_list[__popc(m0 & lt)] = t;
+    else s_list[kNT + __popc(m1 & lt)] = t;
+  }
+  if (t == 0) {
+    s_cnt[0] = __popc(m0);
+    s_cnt[1] = __popc(m1);
+  }
+}
+
+// (position of edge e within its receiver's segment) & 1, once per evaluation
+__global__ void edge_parity(int E, const int* __restrict__ row_ptr, const int* __restrict__ recv,
+                            uint8_t* __restrict__ par) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+    par[e] = (uint8_t)((e - row_ptr[recv[e]]) & 1);
+}
 
 template <int L, int MODE, bool BWD>
 struct Split {
@@ -177,6 +206,7 @@ struct Split {
   }
   static constexpr std::array<int, NP> make() {
     std::array<int, NP> ws{};
+    if (kEdgeSplit) return ws;  // every warp set runs every path, on its own edges
     std::array<bool, NP> done{};
     int load[kWS] = {};
     for (int it = 0; it < NP; ++it) {
@@ -257,15 +287,19 @@ template <int NZ, int NZP>
 __device__ __forceinline__ void tile_setup(int tile, int E0, int E1, const int* __restrict__ recv,
                                            const int* __restrict__ send, const float* __restrict__ Yg, int* s_recv,
                                            int* s_send, float* sY, float* cY, const float* tab_c,
-                                           const uint8_t* tab_y, const int* __restrict__ sys_of = nullptr,
+                                           const uint8_t* tab_y, const uint8_t* __restrict__ epar, int* s_list,
+                                           int* s_cnt, int* s_own, const int* __restrict__ sys_of = nullptr,
                                            const float2* __restrict__ dws2 = nullptr, float* s_dws = nullptr) {
   const int tid = threadIdx.x;
   if (tid < kNT) {
     const int e = tile * kNT + tid;
     const bool valid = e >= E0 && e < E1;
     const int r = valid ? recv[e] : -1;
+    const int par = valid ? epar[e] : 0;
     s_recv[tid] = r;
     s_send[tid] = valid ? send[e] : 0;
+    if (s_own) s_own[tid] = valid ? par : -1;
+    build_lists(tid, valid, par, s_list, s_cnt);
     if (s_dws) {
       const float2 v = valid ? dws2[sys_of ? sys_of[r] : 0] : make_float2(1.0f, 1.0f);
       s_dws[tid] = v.x;
@@ -319,6 +353,12 @@ __device__ __forceinline__ void tmem_ldn<8>(uint32_t taddr, float* v) { tc::tmem
 // (little work per edge) take longer chunks.
 template <int WORK>
 constexpr int chunk_edges() { return WORK <= 8 ? 8 : 4; }
+
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+  return __uint_as_float(r);
+}
 
 __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float* v) {
   uint32_t r0, r1;
@@ -390,7 +430,7 @@ __device__ __forceinline__ void fwd_edge(const float* wv, const float* hj, const
 template <int L, int MODE, int W>
 __device__ __forceinline__ void fwd_tile_ws(const int* s_send, const int* s_recv, const float* cY, uint32_t taddr0,
                                             const float* __restrict__ h, int& cur, float* acc,
-                                            float* __restrict__ mW, float s) {
+                                            float* __restrict__ mW, float s, const int* list, int cnt) {
   using G = Group<L, MODE>;
   using S = Split<L, MODE, false>;
   constexpr int D = NodeDims<L>::D;
@@ -398,39 +438,45 @@ __device__ __forceinline__ void fwd_tile_ws(const int* s_send, const int* s_recv
   constexpr int DH = S::dh(W);
   constexpr int CH = chunk_edges<DH>();
   const int c = threadIdx.x & 127;
+  if (cnt <= 0) return;  // uniform over the warp set
+  auto slot = [&](int i) { return list[i < cnt ? i : cnt - 1]; };
   float hn[CH][DH];
 #pragma unroll
   for (int j = 0; j < CH; ++j) {
-    const int sj = s_send[j];
+    const int sj = s_send[slot(j)];
 #pragma unroll
     for (int d = 0; d < DH; ++d) hn[j][d] = h[((size_t)sj * D + d) * C + c];
   }
 #pragma unroll 1
-  for (int ch = 0; ch < kNT / CH; ++ch) {
+  for (int base = 0; base < cnt; base += CH) {
     float wvc[G::NP][CH];
-    static_for<0, G::NP>([&](auto sc) {
-      constexpr int sl = decltype(sc)::value;
-      if constexpr (S::ws[sl] == W) tmem_ldn<CH>(taddr0 + sl * kNT + ch * CH, wvc[sl]);
-    });
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int t = slot(base + j);
+      static_for<0, G::NP>([&](auto sc) {
+        constexpr int sl = decltype(sc)::value;
+        if constexpr (S::ws[sl] == W) wvc[sl][j] = tmem_ld1(taddr0 + sl * kNT + t);
+      });
+    }
     tc::tmem_ld_wait();
     float hc[CH][DH];
 #pragma unroll
     for (int j = 0; j < CH; ++j)
 #pragma unroll
       for (int d = 0; d < DH; ++d) hc[j][d] = hn[j][d];
-    if (ch + 1 < kNT / CH) {
+    if (base + CH < cnt) {
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
-        const int sj = s_send[CH * ch + CH + j];
+        const int sj = s_send[slot(base + CH + j)];
 #pragma unroll
         for (int d = 0; d < DH; ++d) hn[j][d] = h[((size_t)sj * D + d) * C + c];
       }
     }
 #pragma unroll
     for (int j = 0; j < CH; ++j) {
-      const int t = CH * ch + j;
+      if (base + j >= cnt) break;
+      const int t = list[base + j];
       const int r = s_recv[t];
-      if (r < 0) continue;
       while (cur < r) {
 #pragma unroll
         for (int q = 0; q < G::NOUT; ++q) {
@@ -453,7 +499,8 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(FwdLayout<L, MODE>::byte
                                                      const float* __restrict__ Yg, const float* __restrict__ h,
                                                      const uint8_t* __restrict__ w3img,
                                                      const uint8_t* __restrict__ z2t, float s, float* __restrict__ mA,
-                                                     float* __restrict__ mB, int use_bf16, int* __restrict__ err) {
+                                                     float* __restrict__ mB, int use_bf16,
+                                                     const uint8_t* __restrict__ epar, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using FL = FwdLayout<L, MODE>;
   constexpr int D = NodeDims<L>::D;
@@ -474,6 +521,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(FwdLayout<L, MODE>::byte
   uint64_t* bar_mma = bars + 3;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 4);
   __shared__ int abort_s;
+  __shared__ int s_list[2 * kNT], s_cnt[2];  // the warp sets' edges of the tile
 
   const int tid = threadIdx.x, warp = tid >> 5, c = tid & 127, wsid = warp >> 2;
   float* mW = wsid == 0 ? mA : mB;
@@ -553,7 +601,8 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(FwdLayout<L, MODE>::byte
         abort_s = 1;
       }
     }
-    tile_setup<G::NZ, G::NZP>(tile, E0, E1, recv, send, Yg, s_recv, s_send, sY, cY, tab_c, tab_y);
+    tile_setup<G::NZ, G::NZP>(tile, E0, E1, recv, send, Yg, s_recv, s_send, sY, cY, tab_c, tab_y, epar, s_list, s_cnt,
+                              nullptr);
     __syncthreads();
     if (abort_s) break;
     if (!tc::mbar_wait(bar_mma, (uint32_t)(it & 1))) {
@@ -561,8 +610,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(FwdLayout<L, MODE>::byte
       abort_s = 1;
     }
     tc::fence_after_sync();
-    if (wsid == 0) fwd_tile_ws<L, MODE, 0>(s_send, s_recv, cY, taddr0, h, cur, acc, mW, s);
-    else fwd_tile_ws<L, MODE, 1>(s_send, s_recv, cY, taddr0, h, cur, acc, mW, s);
+    fwd_tile_ws<L, MODE, 0>(s_send, s_recv, cY, taddr0, h, cur, acc, mW, s, s_list + wsid * kNT, s_cnt[wsid]);
     tc::fence_before_sync();
     __syncthreads();
     if (abort_s) break;
@@ -691,7 +739,8 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
                                             const float* __restrict__ Gm, const float* __restrict__ GinA,
                                             const float* __restrict__ GinB, float* __restrict__ GoutW,
                                             int first_group, int& cur, float* Gacc, float* Gt, float* red,
-                                            uint8_t* sB2, float s, const float* dws, int use_bf16) {
+                                            uint8_t* sB2, float s, const float* dws, int use_bf16, int wsid,
+                                            const int* list, int cnt) {
   using G = Group<L, MODE>;
   using S = Split<L, MODE, true>;
   using BL = BwdLayout<L, MODE>;
@@ -708,7 +757,7 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
       for (int d = 0; d < D; ++d) {
         const size_t o = ((size_t)i * D + d) * C + c;
         if (!first_group) atomicAdd(&GoutW[o], Gacc[d]);
-        else GoutW[o] = (W == 0 ? GinA[o] + GinB[o] : 0.0f) + Gacc[d];
+        else GoutW[o] = (wsid == 0 ? GinA[o] + GinB[o] : 0.0f) + Gacc[d];
       }
     }
 #pragma unroll
@@ -737,10 +786,12 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
     for (int k = 0; k < NV; ++k)
       if (((lane >> 1) % NVP) == k) my_comp = yl[k];
   }
+  if (cnt <= 0) return;  // uniform over the warp set
+  auto lslot = [&](int i) { return list[i < cnt ? i : cnt - 1]; };
   float hn[CH][DH], gn[CH][NG];
 #pragma unroll
   for (int j = 0; j < CH; ++j) {
-    const int si = s_send[j];
+    const int si = s_send[lslot(j)];
 #pragma unroll
     for (int d = 0; d < DH; ++d) hn[j][d] = hprev[((size_t)si * D + d) * C + c];
     if constexpr (!FIRST) {
@@ -749,12 +800,16 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
     }
   }
 #pragma unroll 1
-  for (int ch = 0; ch < kNT / CH; ++ch) {
+  for (int base = 0; base < cnt; base += CH) {
     float wvc[G::NP][CH];
-    static_for<0, G::NP>([&](auto sc) {
-      constexpr int sl = decltype(sc)::value;
-      if constexpr (S::ws[sl] == W) tmem_ldn<CH>(taddr0 + sl * kNT + ch * CH, wvc[sl]);
-    });
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int t = lslot(base + j);
+      static_for<0, G::NP>([&](auto sc) {
+        constexpr int sl = decltype(sc)::value;
+        if constexpr (S::ws[sl] == W) wvc[sl][j] = tmem_ld1(taddr0 + sl * kNT + t);
+      });
+    }
     tc::tmem_ld_wait();
     float hc[CH][DH], gc[CH][NG];
 #pragma unroll
@@ -764,10 +819,10 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
 #pragma unroll
       for (int q = 0; q < NG; ++q) gc[j][q] = FIRST ? 0.0f : gn[j][q];
     }
-    if (ch + 1 < kNT / CH) {
+    if (base + CH < cnt) {
 #pragma unroll
       for (int j = 0; j < CH; ++j) {
-        const int si = s_send[CH * ch + CH + j];
+        const int si = s_send[lslot(base + CH + j)];
 #pragma unroll
         for (int d = 0; d < DH; ++d) hn[j][d] = hprev[((size_t)si * D + d) * C + c];
         if constexpr (!FIRST) {
@@ -778,8 +833,9 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
     }
     static_for<0, CH>([&](auto jc) {
       constexpr int j = decltype(jc)::value;
-      const int t = CH * ch + j;
-      const int r = s_recv[t];
+      const bool live = base + j < cnt;
+      const int t = lslot(base + j);
+      const int r = live ? s_recv[t] : -1;
       float dYp[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) dYp[k] = 0.0f;
@@ -791,14 +847,6 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
 #pragma unroll
         for (int sl = 0; sl < G::NP; ++sl) wv[sl] = wvc[sl][j];
         bwd_edge<L, MODE, W>(wv, t, hc[j], gc[j], Gt, Y, cY + t * BL::NZP, s, dws[t], use_bf16, sB2, Gacc, dYp);
-      } else {
-        static_for<0, G::NP>([&](auto sc) {
-          constexpr int sl = decltype(sc)::value;
-          if constexpr (S::ws[sl] == W) {
-            const int kidx = sl * 128 + c;
-            *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) = 0;
-          }
-        });
       }
       // channel sums of this edge's dE/dY components, several edges per butterfly
       constexpr int PK = S::ypack(W), NVP = 16 / PK, NV = S::nyv(W);
@@ -808,18 +856,13 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
       for (int i = 0; i < NVP; ++i) pv[slot * NVP + i] = i < NV ? dYp[yl[i < NV ? i : 0]] : 0.0f;
       if constexpr (slot == PK - 1) {
         const float tot = warp_reduce16(pv);
-        const int te = t - (PK - 1) + (lane >> 1) / NVP;
-        if ((lane & 1) == 0 && my_comp >= 0) red[(warp * kNT + te) * 16 + my_comp] = tot;
+        const int ie = base + j - (PK - 1) + (lane >> 1) / NVP;  // list entry of this lane pair's value
+        if ((lane & 1) == 0 && my_comp >= 0 && ie < cnt) red[(warp * kNT + list[ie]) * 16 + my_comp] = tot;
       }
     });
   }
 }
 
-__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
-  uint32_t r;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-  return __uint_as_float(r);
-}
 
 // Heavy groups: one copy of the per-edge body in a runtime loop over the
 // tile's edges (keeps the hot loop inside the instruction cache); the sender
@@ -832,7 +875,7 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
                                                  const float* __restrict__ GinA, const float* __restrict__ GinB,
                                                  float* __restrict__ GoutW, int first_group, int& cur, float* Gacc,
                                                  float* Gt, float* red, uint8_t* sB2, float s, const float* dws,
-                                                 int use_bf16) {
+                                                 int use_bf16, int wsid, const int* list, int cnt) {
   using G = Group<L, MODE>;
   using S = Split<L, MODE, true>;
   using BL = BwdLayout<L, MODE>;
@@ -856,7 +899,7 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
       for (int d = 0; d < D; ++d) {
         const size_t o = ((size_t)i * D + d) * C + c;
         if (!first_group) atomicAdd(&GoutW[o], Gacc[d]);
-        else GoutW[o] = (W == 0 ? GinA[o] + GinB[o] : 0.0f) + Gacc[d];
+        else GoutW[o] = (wsid == 0 ? GinA[o] + GinB[o] : 0.0f) + Gacc[d];
       }
     }
 #pragma unroll
@@ -885,7 +928,8 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
   float pv[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) pv[i] = 0.0f;
-  auto edge = [&](int t, const float* hc, const float* gc, const float* wv) {
+  // list entry i (edge slot t) of this warp set
+  auto edge = [&](int i, int t, const float* hc, const float* gc, const float* wv) {
     const int r = s_recv[t];
     float dYp[16];
 #pragma unroll
@@ -895,52 +939,47 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
       float Y[16];
       load4<4>(sY + t * 16, Y);
       bwd_edge<L, MODE, W>(wv, t, hc, gc, Gt, Y, cY + t * BL::NZP, s, dws[t], use_bf16, sB2, Gacc, dYp);
-    } else {
-      static_for<0, G::NP>([&](auto sc) {
-        constexpr int sl = decltype(sc)::value;
-        if constexpr (S::ws[sl] == W) {
-          const int kidx = sl * 128 + c;
-          *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) = 0;
-        }
-      });
     }
 #pragma unroll
-    for (int i = 0; i < NV * (PK - 1); ++i) pv[i] = pv[i + NV];
+    for (int q = 0; q < NV * (PK - 1); ++q) pv[q] = pv[q + NV];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) pv[NV * (PK - 1) + i] = dYp[yl[i]];
-    const int slot = t % PK;
-    if (slot == PK - 1 || t == kNT - 1) {
+    for (int q = 0; q < NV; ++q) pv[NV * (PK - 1) + q] = dYp[yl[q]];
+    const int slot = i % PK;
+    if (slot == PK - 1 || i == cnt - 1) {
       const float tot = warp_reduce32(pv);
-      // lane v holds the total of value v: edge t - (PK - 1) + v / NV, component v % NV;
-      // slots older than this group's first edge were written by the previous group
-      const int te = t - (PK - 1) + lane / NV, vi = lane % NV;
-      if (lane < PK * NV && te >= t - slot) red[(warp * kNT + te) * 16 + yl_rt[vi]] = tot;
+      // lane v holds the total of value v: list entry i - (PK - 1) + v / NV, component v % NV;
+      // entries older than this group's first were written by the previous group
+      const int ie = i - (PK - 1) + lane / NV;
+      if (lane < PK * NV && ie >= i - slot) red[(warp * kNT + list[ie]) * 16 + yl_rt[lane % NV]] = tot;
     }
   };
-  // edges in pairs with two register buffers: the sender rows of the next
-  // pair's edge load while the other edge of this pair is computed
+  // list entries in pairs with two register buffers: the sender rows of the
+  // next pair's entry load while the other entry of this pair is computed
+  if (cnt <= 0) return;  // uniform over the warp set
+  auto lslot = [&](int i) { return list[i < cnt ? i : cnt - 1]; };
   float hA[DH], gA[NG], hB[DH], gB[NG];
 #pragma unroll
   for (int q = 0; q < NG; ++q) gA[q] = gB[q] = 0.0f;
-  gather(0, hA, gA);
-  gather(1, hB, gB);
+  gather(lslot(0), hA, gA);
+  gather(lslot(1), hB, gB);
 #pragma unroll 1
-  for (int t = 0; t < kNT; t += 2) {
-    float w2[G::NP][2], wA[G::NP], wB[G::NP];
+  for (int i = 0; i < cnt; i += 2) {
+    const int tA = list[i], tB = lslot(i + 1);
+    float wA[G::NP], wB[G::NP];
     static_for<0, G::NP>([&](auto sc) {
       constexpr int sl = decltype(sc)::value;
-      if constexpr (S::ws[sl] == W) tmem_ld2(taddr0 + sl * kNT + t, w2[sl]);
+      if constexpr (S::ws[sl] == W) {
+        wA[sl] = tmem_ld1(taddr0 + sl * kNT + tA);
+        wB[sl] = tmem_ld1(taddr0 + sl * kNT + tB);
+      }
     });
     tc::tmem_ld_wait();
-#pragma unroll
-    for (int sl = 0; sl < G::NP; ++sl) {
-      wA[sl] = w2[sl][0];
-      wB[sl] = w2[sl][1];
+    edge(i, tA, hA, gA, wA);
+    if (i + 2 < cnt) gather(list[i + 2], hA, gA);
+    if (i + 1 < cnt) {
+      edge(i + 1, tB, hB, gB, wB);
+      if (i + 3 < cnt) gather(list[i + 3], hB, gB);
     }
-    edge(t, hA, gA, wA);
-    if (t + 2 < kNT) gather(t + 2, hA, gA);
-    edge(t + 1, hB, gB, wB);
-    if (t + 3 < kNT) gather(t + 3, hB, gB);
   }
 }
 
@@ -957,7 +996,8 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
                                                          int first_group, float* __restrict__ dY,
                                                          float* __restrict__ dz2, int use_bf16,
                                                          const int* __restrict__ sys_of,
-                                                         const float2* __restrict__ dws2, int* __restrict__ err) {
+                                                         const float2* __restrict__ dws2,
+                                                         const uint8_t* __restrict__ epar, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using BL = BwdLayout<L, MODE>;
   constexpr int D = NodeDims<L>::D;
@@ -983,6 +1023,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 5);
   __shared__ int abort_s;
   __shared__ float s_dws[2 * kNT];  // per-edge scale of dE/dw in the second product, and its inverse
+  __shared__ int s_list[2 * kNT], s_cnt[2], s_own[kNT];  // the warp sets' edges of the tile
 
   const int tid = threadIdx.x, warp = tid >> 5, wsid = warp >> 2, c = tid & 127;
   float* GoutW = wsid == 0 ? GoutA : GoutB;
@@ -1067,8 +1108,8 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
         abort_s = 1;
       }
     }
-    tile_setup<BL::NZ, BL::NZP>(tile, E0, E1, recv, send, Yg, s_recv, s_send, sY, cY, tab_c, tab_y, sys_of, dws2,
-                                s_dws);
+    tile_setup<BL::NZ, BL::NZP>(tile, E0, E1, recv, send, Yg, s_recv, s_send, sY, cY, tab_c, tab_y, epar, s_list,
+                                s_cnt, s_own, sys_of, dws2, s_dws);
     __syncthreads();
     if (abort_s) break;
     if (!tc::mbar_wait(bar_mma, (uint32_t)(it & 1))) {
@@ -1079,21 +1120,14 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
     {
       using S = Split<L, MODE, true>;
       constexpr bool heavy0 = S::dh(0) + (FIRST ? 0 : G::NOUT) > 8, heavy1 = S::dh(1) + (FIRST ? 0 : G::NOUT) > 8;
-      if (wsid == 0) {
-        if constexpr (heavy0)
-          bwd_tile_ws_roll<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW,
-                                       first_group, cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
-        else
-          bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
-                                  cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
-      } else {
-        if constexpr (heavy1)
-          bwd_tile_ws_roll<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW,
-                                       first_group, cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
-        else
-          bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
-                                  cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
-      }
+      const int* lst = s_list + wsid * kNT;
+      const int cnt = s_cnt[wsid];
+      if constexpr (heavy0)
+        bwd_tile_ws_roll<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW,
+                                       first_group, cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16, wsid, lst, cnt);
+      else
+        bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, taddr0, hprev, Gm, GinA, GinB, GoutW, first_group,
+                                  cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16, wsid, lst, cnt);
     }
     // second product: dE/dz2 = W3 dE/dw over this tile
     tc::fence_proxy_async_smem();
@@ -1123,13 +1157,19 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
         const int e = tile * kNT + t;
         if (e >= E0 && e < E1 && ((m0 | m1) >> k & 1)) {
           float v = 0.0f;
-          if (m0 >> k & 1) {
+          if (kEdgeSplit) {  // the four warps of the set that owns edge t
+            const int w0 = s_own[t] * 4;
 #pragma unroll
-            for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
-          }
-          if (m1 >> k & 1) {
+            for (int w = 0; w < 4; ++w) v += red[((w0 + w) * kNT + t) * 16 + k];
+          } else {
+            if (m0 >> k & 1) {
 #pragma unroll
-            for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
+              for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
+            }
+            if (m1 >> k & 1) {
+#pragma unroll
+              for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
+            }
           }
           atomicAdd(&dY[(size_t)e * 16 + k], v);  // one add per kernel and address: deterministic
         }
@@ -1245,7 +1285,7 @@ __global__ void __launch_bounds__(kWSThreads, 1)
                     float s, const float* __restrict__ GinA, const float* __restrict__ GinB,
                     float* __restrict__ GoutA, float* __restrict__ GoutB, int first_group, float* __restrict__ dY,
                     float* __restrict__ dz2, int use_bf16, const int* __restrict__ sys_of,
-                    const float2* __restrict__ dws2, int* __restrict__ err) {
+                    const float2* __restrict__ dws2, const uint8_t* __restrict__ epar, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using BL = BwdLayoutWS<L, MODE>;
   static_assert(BL::fits, "shared or tensor memory of the pipelined adjoint kernel exceeds the per-SM limits");
@@ -1275,6 +1315,7 @@ __global__ void __launch_bounds__(kWSThreads, 1)
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 10);
   __shared__ volatile int abort_s;
   __shared__ int abort_p;  // producers' copy, written by the elected producer before their barrier
+  __shared__ int s_lists[2][2 * kNT], s_cnts[2][2], s_owns[2][kNT];  // the warp sets' edges, per buffer
 
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
@@ -1334,12 +1375,15 @@ __global__ void __launch_bounds__(kWSThreads, 1)
         tc::bulk_g2s(sZ2 + b * kTileBytes, z2t + (size_t)tile * kTileBytes, kTileBytes, bar_z2 + b);
         z2_issued[b]++;
       }
-      if (pt < kNT) {
+      if (pt < kNT) {  // one warp: lane = edge slot
         const int e = tile * kNT + pt;
         const bool valid = e >= E0 && e < E1;
         const int r = valid ? recv[e] : -1;
+        const int par = valid ? epar[e] : 0;
         s_recv[pt] = r;
         s_send[pt] = valid ? send[e] : 0;
+        s_owns[b][pt] = valid ? par : -1;
+        build_lists(pt, valid, par, s_lists[b], s_cnts[b]);
         const float2 v = valid ? dws2[sys_of ? sys_of[r] : 0] : make_float2(1.0f, 1.0f);
         s_dws[pt] = v.x;
         s_dws[kNT + pt] = v.y;
@@ -1421,13 +1465,19 @@ __global__ void __launch_bounds__(kWSThreads, 1)
           const int e = tile * kNT + t;
           if (e >= E0 && e < E1 && ((m0 | m1) >> k & 1)) {
             float v = 0.0f;
-            if (m0 >> k & 1) {
+            if (kEdgeSplit) {  // the four warps of the set that owns edge t
+              const int w0 = s_owns[b][t] * 4;
 #pragma unroll
-              for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
-            }
-            if (m1 >> k & 1) {
+              for (int w = 0; w < 4; ++w) v += red[((w0 + w) * kNT + t) * 16 + k];
+            } else {
+              if (m0 >> k & 1) {
 #pragma unroll
-              for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
+                for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
+              }
+              if (m1 >> k & 1) {
+#pragma unroll
+                for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
+              }
             }
             atomicAdd(&dY[(size_t)e * 16 + k], v);  // one add per kernel and address: deterministic
           }
@@ -1520,21 +1570,14 @@ __global__ void __launch_bounds__(kWSThreads, 1)
       float* red = redb + b * 8 * kNT * 16;
       uint8_t* sB2 = sB2base + (BL::NB2 == 2 ? b : 0) * BL::B2_BYTES;
       const uint32_t tw = taddr0 + (b ? wcol1 : wcol0);
-      if (wsid == 0) {
-        if constexpr (heavy0)
-          bwd_tile_ws_roll<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group,
-                                       cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
-        else
-          bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group, cur,
-                                  Gacc, Gt, red, sB2, s, s_dws, use_bf16);
-      } else {
-        if constexpr (heavy1)
-          bwd_tile_ws_roll<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group,
-                                       cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16);
-        else
-          bwd_tile_ws<L, MODE, 1>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group, cur,
-                                  Gacc, Gt, red, sB2, s, s_dws, use_bf16);
-      }
+      const int* lst = s_lists[b] + wsid * kNT;
+      const int cnt = s_cnts[b][wsid];
+      if constexpr (heavy0)
+        bwd_tile_ws_roll<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group,
+                                       cur, Gacc, Gt, red, sB2, s, s_dws, use_bf16, wsid, lst, cnt);
+      else
+        bwd_tile_ws<L, MODE, 0>(i0, i1, s_send, s_recv, sY, cY, tw, hprev, Gm, GinA, GinB, GoutW, first_group, cur,
+                                  Gacc, Gt, red, sB2, s, s_dws, use_bf16, wsid, lst, cnt);
       // dE/dw (for the second product) and the dE/dY partials are written
       tc::fence_proxy_async_smem();
       tc::fence_before_sync();
@@ -1707,15 +1750,15 @@ int resident_ctas(K kernel, size_t smem, int ncols) {
 
 template <int L, int MODE>
 int launch_group(int n, const int* row_ptr, const int* recv, const int* send, const float* Yg, const float* h,
-                 const uint8_t* w3img, const uint8_t* z2t, float s, float* mA, float* mB, int use_bf16, int* err,
-                 int blocks, cudaStream_t st) {  // blocks: SM count
+                 const uint8_t* w3img, const uint8_t* z2t, float s, float* mA, float* mB, int use_bf16,
+                 const uint8_t* epar, int* err, int blocks, cudaStream_t st) {  // blocks: SM count
   const size_t smem = FwdLayout<L, MODE>::bytes;
   MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   blocks = std::min(n, blocks * resident_ctas(tp_fused<L, MODE>, smem, Group<L, MODE>::NCOLS));
   {
     MLIP_PROF("tp_fused", st);
     tp_fused<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, h, w3img, z2t, s, mA, mB, use_bf16,
-                                                      err);
+                                                      epar, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
@@ -1725,8 +1768,8 @@ template <int L, int MODE>
 int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send, const float* Yg,
                      const float* hprev, const float* Gm, const uint8_t* w3img, const uint8_t* z2t, float s,
                      const float* GinA, const float* GinB, float* GoutA, float* GoutB, int first_group, float* dY,
-                     float* dz2, int use_bf16, const int* sys_of, const float2* dws2, int* err, int blocks,
-                     cudaStream_t st) {
+                     float* dz2, int use_bf16, const int* sys_of, const float2* dws2, const uint8_t* epar,
+                     int* err, int blocks, cudaStream_t st) {
   using BL = BwdLayout<L, MODE>;
   if constexpr (ctas_per_sm(BL::bytes) == 1 && BwdLayoutWS<L, MODE>::fits) {  // one CTA per SM: pipelined
     using BW = BwdLayoutWS<L, MODE>;
@@ -1738,7 +1781,7 @@ int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send
       MLIP_PROF("tp_fused_bwd", st);
       tp_fused_bwd_ws<L, MODE><<<blocks, kWSThreads, smem, st>>>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img, z2t,
                                                                   s, GinA, GinB, GoutA, GoutB, first_group, dY, dz2,
-                                                                  use_bf16, sys_of, dws2, err);
+                                                                  use_bf16, sys_of, dws2, epar, err);
     }
     MLIP_LAUNCH_CHECK();
     return MLIP_OK;
@@ -1750,8 +1793,7 @@ int launch_group_bwd(int n, const int* row_ptr, const int* recv, const int* send
     MLIP_PROF("tp_fused_bwd", st);
     tp_fused_bwd<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img, z2t, s, GinA,
                                                           GinB, GoutA, GoutB, first_group, dY, dz2, use_bf16, sys_of,
-                                                          dws2,
-                                                          err);
+                                                          dws2, epar, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
@@ -1815,15 +1857,16 @@ int launch_radial_tiles(int H, int E, int n_tiles, const float4* ev, const float
 // buffer per warp set), every component written.
 int launch_tp_fused(int L, bool first, int n, const int* row_ptr, const int* recv, const int* send,
                     const float* Yg, const float* h, const uint8_t* w3img, const std::vector<size_t>& goff,
-                    const uint8_t* z2t, float s, float* mA, float* mB, int use_bf16, int* err, cudaStream_t st) {
+                    const uint8_t* z2t, float s, float* mA, float* mB, int use_bf16, const uint8_t* epar, int* err,
+                    cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int blocks = sms;
 #define MLIP_G(LL, MM, GI) \
-  MLIP_TRY((launch_group<LL, MM>(n, row_ptr, recv, send, Yg, h, w3img + goff[GI], z2t, s, mA, mB, use_bf16, err, \
-                                 blocks, st)))
+  MLIP_TRY((launch_group<LL, MM>(n, row_ptr, recv, send, Yg, h, w3img + goff[GI], z2t, s, mA, mB, use_bf16, epar, \
+                                 err, blocks, st)))
   if (L == 2) {
     if (first) { MLIP_G(2, -1, 0); }
     else { MLIP_G(2, 0, 0); MLIP_G(2, 1, 1); MLIP_G(2, 2, 2); }
@@ -1844,7 +1887,7 @@ int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int*
                         const float* Yg, const float* hprev, const float* Gm, const uint8_t* w3img,
                         const std::vector<size_t>& goff, const uint8_t* z2t, float s, const float* GinA,
                         const float* GinB, float* GoutA, float* GoutB, float* dY, float* dz2, int use_bf16,
-                        const int* sys_of, const float2* dws2, int* err, cudaStream_t st) {
+                        const int* sys_of, const float2* dws2, const uint8_t* epar, int* err, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -1852,7 +1895,8 @@ int launch_tp_fused_bwd(int L, bool first, int n, const int* row_ptr, const int*
   const int blocks = sms;
 #define MLIP_GB(LL, MM, GI)                                                                                  \
   MLIP_TRY((launch_group_bwd<LL, MM>(n, row_ptr, recv, send, Yg, hprev, Gm, w3img + goff[GI], z2t, s, GinA, GinB, \
-                                     GoutA, GoutB, GI == 0, dY, dz2, use_bf16, sys_of, dws2, err, blocks, st)))
+                                     GoutA, GoutB, GI == 0, dY, dz2, use_bf16, sys_of, dws2, epar, err, blocks, \
+                                     st)))
   if (L == 2) {
     if (first) { MLIP_GB(2, -1, 0); }
     else { MLIP_GB(2, 0, 0); MLIP_GB(2, 1, 1); MLIP_GB(2, 2, 2); }
@@ -1978,10 +2022,14 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
     MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
     MLIP_TRY(ws.get("fz.z2t" + std::to_string(t), (size_t)std::max(n_tiles, 1) * kTileBytes, &z2t[t]));
   }
+  uint8_t* epar = nullptr;
+  MLIP_TRY(ws.get("fz.epar", Ec, &epar));
   MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st));
   if (E > 0) {
     MLIP_PROF("edge_sh", st);
     edge_sh<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, Yg);
+    MLIP_LAUNCH_CHECK();
+    edge_parity<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, nl.row_ptr, nl.recv, epar);
     MLIP_LAUNCH_CHECK();
   }
   MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
@@ -1989,7 +2037,7 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
     MLIP_TRY(launch_radial_tc(H, E, n_tiles, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, use_bf16, z2t[t], flag + 1,
                               st));
     MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], M->d_w3img + M->w3_layer_off[t],
-                             M->w3_goff[t], z2t[t], s, mA, mB, use_bf16, flag + 1, st));
+                             M->w3_goff[t], z2t[t], s, mA, mB, use_bf16, epar, flag + 1, st));
     MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
                            nullptr, flag + 1, st));
   }
@@ -2024,7 +2072,7 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
       }
       MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], Gm,
                                    M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, GaA, GaB, GbA, GbB, dY,
-                                   dz2, use_bf16, b.d_sys_of, dws2, flag + 1, st));
+                                   dz2, use_bf16, b.d_sys_of, dws2, epar, flag + 1, st));
       MLIP_TRY(launch_radial_bwd_tc(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, flag + 1, st));
       std::swap(GaA, GbA);
       std::swap(GaB, GbB);
