@@ -52,7 +52,7 @@ def peaks():
 # capture of the same code (profiles/tp_fused_bwd_water3000.md: mean over the
 # four path-group launches of one evaluation), keyed by (workload, precision,
 # kernel).
-NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): 147.2e6}
+NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): 147.7e6}
 
 # FP32 ALU peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
 # lanes x 2 flop (FMA) x 2.07 GHz.
@@ -507,7 +507,15 @@ def run_md64(args, rank, world):
     pbc = np.stack([r.pbc for r in reps])
     n = int(off[-1])
     stream = torch.cuda.current_stream()
-    model.md_nve_batch(off, pos, vel, sp, cells, pbc, 0.5, args.warmup, stream=stream)
+    skin = args.md_list == "skin"
+
+    def run(steps):
+        if skin:  # candidates within rc + 2 A, rebuilt before every 10-step block, blocks replayed as CUDA graphs
+            return model.md_nve_skin(off, pos, vel, sp, cells, pbc, 0.5, steps, skin=2.0, rebuild_every=10,
+                                     use_graph=True, stream=stream)
+        return model.md_nve_batch(off, pos, vel, sp, cells, pbc, 0.5, steps, stream=stream) + ({},)
+
+    run(args.warmup)
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
@@ -516,7 +524,7 @@ def run_md64(args, rank, world):
     l0 = B.mlip_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    _, _, pe, ke = model.md_nve_batch(off, pos, vel, sp, cells, pbc, 0.5, args.steps, stream=stream)
+    _, _, pe, ke, rep = run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     launches = B.mlip_launch_count() - l0
@@ -531,9 +539,12 @@ def run_md64(args, rank, world):
         "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32", "f16": "f16 tensor-core MLP + f32"}[args.precision],
         "data": "synthetic", "impl": "ours",
         "config": {"workload": "md64", "replicas": R, "atoms": n, "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}",
-                   "precision": args.precision, "dt_fs": 0.5, "neighbour_list": "rebuilt at every force evaluation",
+                   "precision": args.precision, "dt_fs": 0.5,
+                   "neighbour_list": ("skin 2 A, rebuilt every 10 steps, compacted every step; 10-step blocks "
+                                      "replayed as CUDA graphs" if skin else "rebuilt at every force evaluation"),
                    "l2": "working set (1.5 GB per node tensor) exceeds L2; no flush"},
         "drift_eV_per_atom_ps": {"median": float(np.median(drift)), "max_abs": float(np.abs(drift).max())},
+        "skin_report": rep or None,
         "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": None,
     }
     if rank == 0:
@@ -580,6 +591,8 @@ def main():
     ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--md-list", default="skin", choices=["skin", "fresh"],
+                    help="md64: skin list rebuilt every 10 steps with graph replay, or a fresh list every step")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
