@@ -206,6 +206,41 @@ int mlip_md_nve_batch(mlip_model* model, int32_t n_systems, const int64_t* atom_
                       const int32_t* species, const double* cells, const uint8_t* pbc, double dt_fs,
                       int64_t n_steps, double* pe, double* ke, int on_device, void* stream);
 
+/* Options of the skin-list MD driver. */
+typedef struct {
+  double skin;            /* A added to the cutoff for the candidate list (> 0) */
+  int32_t rebuild_every;  /* steps per block: the candidate list is rebuilt before every block (>= 1) */
+  int32_t use_graph;      /* 1: capture the steps of a block as one CUDA graph and replay it for later
+                             blocks; 0: launch them one by one (same kernels, same results) */
+} mlip_md_options;
+
+/* What the skin-list driver did. */
+typedef struct {
+  int64_t builds;          /* candidate-list builds */
+  int64_t redone_blocks;   /* blocks run again with a fresh list at every step (an atom moved > skin/2) */
+  int64_t graph_captures;  /* CUDA graphs captured */
+  int64_t graph_launches;  /* graph replays */
+  int64_t max_candidates;  /* largest candidate count of a build */
+  double max_displacement; /* largest displacement from the positions of the last build (A) */
+} mlip_md_report;
+
+/* mlip_md_nve_batch with a skin neighbour list (the batched MD workload): the
+ * pairs within rc + skin are listed before every block of rebuild_every steps
+ * and compacted at every step to the pairs within rc (in the list's canonical
+ * order), so no cell-list build runs inside a block and a block's launches
+ * have fixed sizes, which lets them be captured as one CUDA graph.  If an atom
+ * moves more than skin/2 from its position at the block's build, the block is
+ * run again from its start with a fresh list at every step, so the trajectory
+ * equals mlip_md_nve_batch's bit for bit in every case.  Needs a 16-bit
+ * (fused) model.  opt NULL: skin 2 A, rebuild every 10 steps, graphs on.
+ * report nullable.  Runs on a stream of its own ordered after `stream`;
+ * returns after the trajectory is complete.  Errors as mlip_md_nve_batch, and
+ * MLIP_ERR_INVALID_ARG for a 32-bit model or bad options. */
+int mlip_md_nve_skin(mlip_model* model, int32_t n_systems, const int64_t* atom_off, double* pos, double* vel,
+                     const int32_t* species, const double* cells, const uint8_t* pbc, double dt_fs,
+                     int64_t n_steps, const mlip_md_options* opt, double* pe, double* ke, mlip_md_report* report,
+                     int on_device, void* stream);
+
 /* ------------------------------------------------------------- serving
  * Continuous batching of independent requests (the paper's batched
  * inference and MD serving, Introduction and "NPT ensemble simulations"):

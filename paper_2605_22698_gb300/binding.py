@@ -46,6 +46,16 @@ class mlip_model_desc(ctypes.Structure):
                 ("avg_num_neighbors", ctypes.c_double), ("masses", ctypes.POINTER(ctypes.c_double))]
 
 
+class mlip_md_options(ctypes.Structure):
+    _fields_ = [("skin", ctypes.c_double), ("rebuild_every", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class mlip_md_report(ctypes.Structure):
+    _fields_ = [("builds", ctypes.c_int64), ("redone_blocks", ctypes.c_int64), ("graph_captures", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64), ("max_candidates", ctypes.c_int64),
+                ("max_displacement", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -68,6 +78,8 @@ def lib():
         L.mlip_neighbors_noalloc.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), P]
         L.mlip_md_nve.argtypes = [P, P, P, P, i64, P, P, f64, i64, P, P, i32, P]
         L.mlip_md_nve_batch.argtypes = [P, i32, P, P, P, P, P, P, f64, i64, P, P, i32, P]
+        L.mlip_md_nve_skin.argtypes = [P, i32, P, P, P, P, P, P, f64, i64, ctypes.POINTER(mlip_md_options), P, P,
+                                       ctypes.POINTER(mlip_md_report), i32, P]
         L.mlip_selftest.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         L.mlip_profile_enable.argtypes = [i32]
         L.mlip_launch_count.restype = ctypes.c_longlong
@@ -280,6 +292,35 @@ def mlip_md_nve_batch(h, atom_off, pos, vel, species, cells, pbc, dt_fs: float, 
     return pos, vel, pe, ke
 
 
+def mlip_md_nve_skin(h, atom_off, pos, vel, species, cells, pbc, dt_fs: float, n_steps: int, skin: float = 2.0,
+                     rebuild_every: int = 10, use_graph: bool = True, stream=None):
+    """mlip_md_nve_batch with a skin neighbour list rebuilt before every block
+    of rebuild_every steps and compacted at every step (blocks replayed as CUDA
+    graphs when use_graph).  Returns (pos, vel, pe, ke, report dict)."""
+    off = np.ascontiguousarray(atom_off, dtype=np.int64)
+    ns = len(off) - 1
+    cells = np.ascontiguousarray(cells, dtype=np.float64).reshape(ns, 9)
+    pbc = np.ascontiguousarray(pbc, dtype=np.uint8).reshape(ns, 3)
+    if isinstance(pos, np.ndarray):
+        pos = np.array(pos, dtype=np.float64, copy=True)
+        vel = np.array(vel, dtype=np.float64, copy=True)
+        species = np.ascontiguousarray(species, dtype=np.int32)
+        pe = np.zeros((n_steps + 1, ns)); ke = np.zeros((n_steps + 1, ns))
+    else:
+        import torch
+        pe = torch.zeros((n_steps + 1, ns), dtype=torch.float64, device=pos.device)
+        ke = torch.zeros_like(pe)
+    opt = mlip_md_options(float(skin), int(rebuild_every), 1 if use_graph else 0)
+    rep = mlip_md_report()
+    pp, dev = _ptr(pos)
+    _check(lib().mlip_md_nve_skin(h, ns, off.ctypes.data_as(ctypes.c_void_p), pp, _ptr(vel)[0], _ptr(species)[0],
+                                  cells.ctypes.data_as(ctypes.c_void_p), pbc.ctypes.data_as(ctypes.c_void_p),
+                                  dt_fs, n_steps, ctypes.byref(opt), _ptr(pe)[0], _ptr(ke)[0], ctypes.byref(rep),
+                                  dev, _stream_ptr(stream)))
+    report = {k: getattr(rep, k) for k, _ in mlip_md_report._fields_}
+    return pos, vel, pe, ke, report
+
+
 def mlip_selftest(which: int) -> float:
     r = ctypes.c_double(0.0)
     _check(lib().mlip_selftest(which, ctypes.byref(r)))
@@ -323,6 +364,11 @@ class Model:
 
     def md_nve_batch(self, atom_off, pos, vel, species, cells, pbc, dt_fs, n_steps, stream=None):
         return mlip_md_nve_batch(self.h, atom_off, pos, vel, species, cells, pbc, dt_fs, n_steps, stream)
+
+    def md_nve_skin(self, atom_off, pos, vel, species, cells, pbc, dt_fs, n_steps, skin=2.0, rebuild_every=10,
+                    use_graph=True, stream=None):
+        return mlip_md_nve_skin(self.h, atom_off, pos, vel, species, cells, pbc, dt_fs, n_steps, skin,
+                                rebuild_every, use_graph, stream)
 
     def close(self):
         if getattr(self, "h", None):

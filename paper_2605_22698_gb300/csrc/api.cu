@@ -32,6 +32,7 @@ int Workspace::get(const std::string& name, size_t bytes, void** out) {
       b.bytes = 0;
     }
     size_t nb = bytes + bytes / 8;
+    ++gen;
     cudaError_t e = cudaMalloc(&b.p, nb);
     if (e != cudaSuccess) {
       cudaGetLastError();

@@ -188,7 +188,8 @@ __device__ __forceinline__ void build_lists(int t, bool valid, int par, int* s_l
 
 // (position of edge e within its receiver's segment) & 1, once per evaluation
 __global__ void edge_parity(int E, const int* __restrict__ row_ptr, const int* __restrict__ recv,
-                            uint8_t* __restrict__ par) {
+                            uint8_t* __restrict__ par, const int* __restrict__ Edev) {
+  if (Edev) E = *Edev;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
     par[e] = (uint8_t)((e - row_ptr[recv[e]]) & 1);
 }
@@ -322,7 +323,8 @@ __device__ __forceinline__ void tile_setup(int tile, int E0, int E1, const int* 
 }
 
 // Real harmonics of every edge direction, Y[e][16] (once per evaluation).
-__global__ void edge_sh(int E, const float4* __restrict__ ev, float* __restrict__ Yg) {
+__global__ void edge_sh(int E, const float4* __restrict__ ev, float* __restrict__ Yg, const int* __restrict__ Edev) {
+  if (Edev) E = *Edev;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
     const float4 v = ev[e];
     const float ir = 1.0f / v.w;
@@ -332,6 +334,15 @@ __global__ void edge_sh(int E, const float4* __restrict__ ev, float* __restrict_
 #pragma unroll
     for (int q = 0; q < 4; ++q) dst[q] = make_float4(Y[4 * q], Y[4 * q + 1], Y[4 * q + 2], Y[4 * q + 3]);
   }
+}
+
+// p[0 .. per * *Edev) = 0 (p 16-byte aligned)
+__global__ void zero_edges(const int* __restrict__ Edev, int per, float* __restrict__ p) {
+  const long long n = (long long)(*Edev) * per, n4 = n >> 2;
+  float4* q = reinterpret_cast<float4*>(p);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n4; k += (long long)gridDim.x * blockDim.x)
+    q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (blockIdx.x == 0 && threadIdx.x < (int)(n & 3)) p[(n4 << 2) + threadIdx.x] = 0.0f;
 }
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
@@ -1990,19 +2001,14 @@ int umma_selftest_mn_run(int variant, double* rel_err) {
   return MLIP_OK;
 }
 
-int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
-                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                         const NeighborList& nl, const int* Edev, int* flag, double* d_energy, double* d_forces,
+                         double* d_stress, cudaStream_t st) {
   Workspace& ws = M->ws;
   const int n = (int)b.n, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H;
   const float s = (float)(1.0 / M->avg_nb);
   const int use_bf16 = M->precision == MLIP_PREC_BF16 ? 1 : 0;
-  int* flag = nullptr;
-  MLIP_TRY(ws.get("chk.flag", 2, &flag));
-  MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
-  MLIP_TRY(launch_check_inputs(n, d_pos, d_species, M->S, flag, st));
-  NeighborList nl;
-  MLIP_TRY(build_neighbors_batch(ws, d_pos, b, M->rc, true, st, &nl));
-  const int E = (int)nl.E;
+  const int E = (int)nl.E;  // the edge count, or with Edev the capacity
   const int n_tiles = (E + kNT - 1) / kNT;
   const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)std::max(n, 1) * D * C;
   CellArg ca{b.d_cell, b.d_sys_of, b.any_pbc() ? 1 : 0};
@@ -2024,18 +2030,38 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
   }
   uint8_t* epar = nullptr;
   MLIP_TRY(ws.get("fz.epar", Ec, &epar));
-  MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st));
+  MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st, Edev));
   if (E > 0) {
-    MLIP_PROF("edge_sh", st);
-    edge_sh<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, Yg);
+    {
+      MLIP_PROF("edge_sh", st);
+      edge_sh<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, Yg, Edev);
+    }
     MLIP_LAUNCH_CHECK();
-    edge_parity<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, nl.row_ptr, nl.recv, epar);
+    {
+      MLIP_PROF("edge_parity", st);
+      edge_parity<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, nl.row_ptr, nl.recv, epar, Edev);
+    }
     MLIP_LAUNCH_CHECK();
   }
+  // zero per-edge adjoint buffers: [E][per] floats
+  auto zero = [&](float* p, int per) -> int {
+    if (E <= 0) return MLIP_OK;
+    if (!Edev) {
+      MLIP_CUDA_TRY(cudaMemsetAsync(p, 0, (size_t)E * per * sizeof(float), st));
+      return MLIP_OK;
+    }
+    const long long n4 = ((long long)E * per + 3) / 4;
+    {
+      MLIP_PROF("zero_edges", st);
+      zero_edges<<<(int)std::min<long long>((n4 + 255) / 256, 8192), 256, 0, st>>>(Edev, per, p);
+    }
+    MLIP_LAUNCH_CHECK();
+    return MLIP_OK;
+  };
   MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
   for (int t = 0; t < T; ++t) {
     MLIP_TRY(launch_radial_tc(H, E, n_tiles, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, use_bf16, z2t[t], flag + 1,
-                              st));
+                              st, Edev));
     MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], M->d_w3img + M->w3_layer_off[t],
                              M->w3_goff[t], z2t[t], s, mA, mB, use_bf16, epar, flag + 1, st));
     MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
@@ -2054,8 +2080,8 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
     MLIP_TRY(ws.get("fz.dz2", Ec * 64, &dz2));
     MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, GaA, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(GaB, 0, ND * sizeof(float), st));
-    MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
-    MLIP_CUDA_TRY(cudaMemsetAsync(dr, 0, Ec * sizeof(float), st));
+    MLIP_TRY(zero(dY, 16));
+    MLIP_TRY(zero(dr, 1));
     float* absmax = nullptr;  // per system: max |h^t|, max |dE/dm|
     float2* dws2 = nullptr;   // per system: scale of dE/dw and its inverse
     MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)b.nsys, &absmax));
@@ -2063,7 +2089,7 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
     for (int t = T - 1; t >= 0; --t) {
       MLIP_TRY(launch_mix_tc(true, n, C, L, GaA, GaB, M->mix_bwd_img[t], M->mix_scale[t], nullptr, Gm, nullptr,
                              u0[t], flag + 1, st));
-      MLIP_CUDA_TRY(cudaMemsetAsync(dz2, 0, Ec * 64 * sizeof(float), st));
+      MLIP_TRY(zero(dz2, 64));
       if (!use_bf16) MLIP_TRY(launch_seg_absmax2(b, D * C, h[t], Gm, absmax, st));
       {
         MLIP_PROF("dw_scales", st);
@@ -2073,15 +2099,20 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
       MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], Gm,
                                    M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, GaA, GaB, GbA, GbB, dY,
                                    dz2, use_bf16, b.d_sys_of, dws2, epar, flag + 1, st));
-      MLIP_TRY(launch_radial_bwd_tc(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, flag + 1, st));
+      MLIP_TRY(launch_radial_bwd_tc(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, flag + 1, st,
+                                        Edev));
       std::swap(GaA, GbA);
       std::swap(GaB, GbB);
     }
-    MLIP_TRY(launch_edge_grad(E, ev, dY, dr, g, st));
+    MLIP_TRY(launch_edge_grad(E, ev, dY, dr, g, st, Edev));
     double* fbuf = d_forces;
     if (!fbuf) MLIP_TRY(ws.get("ef.fscratch", (size_t)3 * std::max(n, 1), &fbuf));
     MLIP_TRY(launch_forces_virial(ws, b, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, st));
   }
+  return MLIP_OK;
+}
+
+int check_eval_flags(const int* flag, cudaStream_t st) {
   int hflag[2] = {0, 0};
   MLIP_CUDA_TRY(cudaMemcpyAsync(hflag, flag, sizeof(hflag), cudaMemcpyDeviceToHost, st));
   MLIP_CUDA_TRY(cudaStreamSynchronize(st));
@@ -2089,6 +2120,19 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
   if (hflag[0] & 2) { set_error("non-finite position"); return MLIP_ERR_INVALID_ARG; }
   if (hflag[1]) { set_error("fused kernel: a bounded wait timed out (code %d)", hflag[1]); return MLIP_ERR_DEVICE_TIMEOUT; }
   return MLIP_OK;
+}
+
+int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+  Workspace& ws = M->ws;
+  int* flag = nullptr;
+  MLIP_TRY(ws.get("chk.flag", 2, &flag));
+  MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
+  MLIP_TRY(launch_check_inputs((int)b.n, d_pos, d_species, M->S, flag, st));
+  NeighborList nl;
+  MLIP_TRY(build_neighbors_batch(ws, d_pos, b, M->rc, true, st, &nl));
+  MLIP_TRY(evaluate_fused_edges(M, d_pos, d_species, b, nl, nullptr, flag, d_energy, d_forces, d_stress, st));
+  return check_eval_flags(flag, st);
 }
 
 }  // namespace mlip

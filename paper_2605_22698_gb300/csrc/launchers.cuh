@@ -5,8 +5,10 @@
 
 namespace mlip {
 
+// Edge kernels take an optional device edge count Edev: when given, the launch
+// is sized for E (a capacity) and the kernel processes *Edev <= E edges.
 int launch_edge_geom(int E, const double* pos, const int* recv, const int* send, const int8_t* shift,
-                     const CellArg& cell, float4* ev, cudaStream_t st);
+                     const CellArg& cell, float4* ev, cudaStream_t st, const int* Edev = nullptr);
 int launch_radial_fwd(int H, int E, const float4* ev, const float* W1, const float* W2, float rc, int p,
                       float* z2T, int ldz, cudaStream_t st);
 int launch_radial_bwd(int H, int E, const float4* ev, const float* W1, const float* W2, float rc, int p,
@@ -27,7 +29,8 @@ int launch_grad_init(int n, int C, int D, const int* species, const float* W_out
 // per-system energies energy[nsys] (FP64)
 int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, const int* species, const float* W_out,
                   const float* E0, const float* h, double* atom_e, double* energy, cudaStream_t st);
-int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, float4* g, cudaStream_t st);
+int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, float4* g, cudaStream_t st,
+                     const int* Edev = nullptr);
 // forces[n][3]; stress[nsys][9] = virial / V per system (zero rows for systems
 // without a fully periodic cell), nullable
 int launch_forces_virial(Workspace& ws, const SystemBatch& b, const int* row_ptr, const int* rev, const float4* g,
@@ -41,9 +44,9 @@ int launch_seg_absmax2(const SystemBatch& b, int row, const float* a, const floa
 // Radial MLP of the fused form on the tensor cores (H = 64): z2 operand tiles,
 // and dE/dr accumulated from dE/dz2.  err receives the bounded-wait flags.
 int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float* W1, const float* W2, float rc,
-                     int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st);
+                     int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st, const int* Edev = nullptr);
 int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const float* W2, float rc, int p,
-                         const float* dz2, float* dr_tot, int* err, cudaStream_t st);
+                         const float* dz2, float* dr_tot, int* err, cudaStream_t st, const int* Edev = nullptr);
 
 // Channel mixes of the fused form on the tensor cores (C = 128): X (+ X2) times
 // the split weight images of one layer (pack_mix_images), forward or adjoint.
@@ -67,6 +70,16 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
 // Fused 16-bit form (tcgen05 radial MLP and path products), same contract.
 int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
                    double* d_energy, double* d_forces, double* d_stress, cudaStream_t st);
+// The fused form's evaluation on a given neighbour list: no build and no
+// synchronisation.  With Edev, nl.E is a capacity and *Edev the edge count on
+// the device (launch sizes then depend on the capacity only, so the work can be
+// captured in a CUDA graph).  Input and bounded-wait errors are flagged in
+// flag[0..1] (check_eval_flags).
+int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                         const NeighborList& nl, const int* Edev, int* flag, double* d_energy, double* d_forces,
+                         double* d_stress, cudaStream_t st);
+// Synchronises st and turns the flags of evaluate_fused_edges into a status.
+int check_eval_flags(const int* flag, cudaStream_t st);
 // The model's form.
 int evaluate(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b, double* d_energy,
              double* d_forces, double* d_stress, cudaStream_t st);

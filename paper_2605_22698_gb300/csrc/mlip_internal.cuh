@@ -45,6 +45,7 @@ struct CGTable;
 struct Workspace {
   struct Buf { void* p = nullptr; size_t bytes = 0; };
   std::map<std::string, Buf> bufs;
+  uint64_t gen = 0;  // bumped whenever a buffer is (re)allocated: device addresses may have changed
   int get(const std::string& name, size_t bytes, void** out);
   template <class T>
   int get(const std::string& name, size_t count, T** out) {
@@ -124,8 +125,35 @@ void single_system(SystemBatch& b, int64_t n, const double* cell, const uint8_t*
 int build_neighbors_batch(Workspace& ws, const double* d_pos, const SystemBatch& b, double rc, bool want_rev,
                           cudaStream_t st, NeighborList* out);
 
+// Skin neighbour list for MD: candidates (recv <- send, S) within rc + skin,
+// in the canonical order, built at the positions pos_ref and kept in buffers
+// of fixed capacity; each step compacts them to the pairs within rc.  While no
+// atom has moved more than skin/2 from pos_ref, the compacted list equals a
+// fresh build at rc element for element (order, shifts and reverse indices).
+struct SkinList {
+  int64_t n = 0, cap = 0, n_cand = 0;  // atoms, edge capacity, candidates of the last build
+  double rc = 0.0, skin = 0.0;
+  int32_t *crow = nullptr, *crecv = nullptr, *csend = nullptr, *crev = nullptr;  // candidates
+  int8_t* cshift = nullptr;
+  double* pos_ref = nullptr;  // [n][3] positions at the build
+  int32_t *deg = nullptr, *newidx = nullptr;
+  uint8_t* keep = nullptr;
+  NeighborList nl;                  // compacted list; nl.E = cap (capacity)
+  int* flags = nullptr;             // [0] an atom moved > skin/2, [1] reverse edge missing
+  unsigned long long* dmax2 = nullptr;  // largest squared displacement (bits of a double)
+  const int* Edev() const { return nl.row_ptr + n; }
+};
+// Candidate build at b's positions (synchronises the stream once).
+int skin_build(Workspace& ws, const double* d_pos, const SystemBatch& b, double rc, double skin, SkinList* sl,
+               cudaStream_t st);
+// Compacts the candidates to the pairs within rc at d_pos and flags atoms that
+// moved more than skin/2; launch sizes depend only on n and the capacity.
+int skin_compact(Workspace& ws, SkinList& sl, const double* d_pos, const SystemBatch& b, cudaStream_t st);
+
 // exclusive scan of n int32 values into out[0..n] (out[n] = total)
-int exclusive_scan_i32(Workspace& ws, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+// (block sums in the workspace buffer named `scratch`)
+int exclusive_scan_i32(Workspace& ws, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st,
+                       const char* scratch = "scan.bsum");
 
 }  // namespace mlip
 

@@ -408,11 +408,12 @@ __global__ void scan_add(int* __restrict__ out, long long n, const int* __restri
 
 }  // namespace
 
-int exclusive_scan_i32(Workspace& ws, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
+int exclusive_scan_i32(Workspace& ws, const int32_t* in, int32_t* out, int64_t n, cudaStream_t st,
+                       const char* scratch) {
   int nb = (int)((n + kScanTile - 1) / kScanTile);
   if (nb < 1) nb = 1;
   int* bsum = nullptr;
-  MLIP_TRY(ws.get("scan.bsum", (size_t)nb, &bsum));
+  MLIP_TRY(ws.get(scratch, (size_t)nb, &bsum));
   { MLIP_PROF("scan_local", st); scan_local<<<nb, kScanThreads, 0, st>>>(in, out, n, bsum); }
   { MLIP_PROF("scan_blocks", st); scan_blocks<<<1, 1024, 0, st>>>(bsum, nb, out + n); }
   { MLIP_PROF("scan_add", st); scan_add<<<nb, kScanThreads, 0, st>>>(out, n, bsum); }

@@ -50,7 +50,8 @@ __global__ void readout(int n, int C, int D, const int* __restrict__ species, co
 
 // g_e = dr r^ + (1/r)(I - r^ r^T) grad(Y . dY)
 __global__ void edge_grad(int E, const float4* __restrict__ ev, const float* __restrict__ dY,
-                          const float* __restrict__ dr, float4* __restrict__ g) {
+                          const float* __restrict__ dr, float4* __restrict__ g, const int* __restrict__ Edev) {
+  if (Edev) E = *Edev;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
     const float4 v = ev[e];
     const float ir = 1.0f / v.w;
@@ -122,9 +123,10 @@ int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, const int* 
   return launch_seg_sum(ws, b, 1, atom_e, false, energy, st);
 }
 
-int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, float4* g, cudaStream_t st) {
+int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, float4* g, cudaStream_t st,
+                     const int* Edev) {
   if (E <= 0) return MLIP_OK;
-  { MLIP_PROF("edge_grad", st); edge_grad<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, dY, dr, g); }
+  { MLIP_PROF("edge_grad", st); edge_grad<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, dY, dr, g, Edev); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }

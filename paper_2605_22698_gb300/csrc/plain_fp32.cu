@@ -32,7 +32,8 @@ constexpr int kNT = 32;  // edges per shared-memory sub-tile
 // Lattice rows of the receiver's system (cells, sys_of: see SystemBatch).
 __global__ void edge_geom(int E, const double* __restrict__ pos, const int* __restrict__ recv,
                           const int* __restrict__ send, const int8_t* __restrict__ shift, CellArg cell,
-                          float4* __restrict__ ev) {
+                          float4* __restrict__ ev, const int* __restrict__ Edev) {
+  if (Edev) E = *Edev;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
     const int i = recv[e], j = send[e];
     const double S0 = shift[3 * e], S1 = shift[3 * e + 1], S2 = shift[3 * e + 2];
@@ -647,9 +648,12 @@ __global__ void mix_bwd(int n, int C, int L, const float* __restrict__ G, const 
 
 // Host-side launchers (declared in plain_fp32.h via extern templates below).
 int launch_edge_geom(int E, const double* pos, const int* recv, const int* send, const int8_t* shift,
-                     const CellArg& cell, float4* ev, cudaStream_t st) {
+                     const CellArg& cell, float4* ev, cudaStream_t st, const int* Edev) {
   if (E <= 0) return MLIP_OK;
-  { MLIP_PROF("edge_geom", st); edge_geom<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, pos, recv, send, shift, cell, ev); }
+  {
+    MLIP_PROF("edge_geom", st);
+    edge_geom<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, pos, recv, send, shift, cell, ev, Edev);
+  }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }

@@ -66,6 +66,10 @@ void prof_end(cudaStream_t st) {
   p.open_events.pop_back();
 }
 
+bool prof_timing_on() { return P().on.load(); }
+long long prof_launches() { return P().launches.load(); }
+void prof_add_launches(long long k) { P().launches.fetch_add(k); }
+
 }  // namespace mlip
 
 extern "C" {

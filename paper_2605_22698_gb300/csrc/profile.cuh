@@ -10,6 +10,12 @@ namespace mlip {
 
 void prof_begin(const char* name, cudaStream_t st);
 void prof_end(cudaStream_t st);
+// Whether per-kernel event timing is on (graph capture is skipped then: the
+// timing events need eager launches).
+bool prof_timing_on();
+// Launch counter: its value, and launches replayed by a CUDA graph.
+long long prof_launches();
+void prof_add_launches(long long k);
 
 struct ProfScope {
   cudaStream_t st;

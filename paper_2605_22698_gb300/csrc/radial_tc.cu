@@ -163,7 +163,11 @@ __device__ __forceinline__ float absmax64(const float* v) {
 __global__ void __launch_bounds__(kRM, 4) radial_tc(int E, int n_tiles32, const float4* __restrict__ ev,
                                                  const float* __restrict__ W1, const float* __restrict__ W2,
                                                  float rc, int p, int use_bf16, uint8_t* __restrict__ z2t,
-                                                 int* __restrict__ err) {
+                                                 const int* __restrict__ Edev, int* __restrict__ err) {
+  if (Edev) {  // edge count on the device (capacity-sized launch)
+    E = *Edev;
+    n_tiles32 = (E + kZ2Tile - 1) / kZ2Tile;
+  }
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sAh = smem;
   uint8_t* sAl = smem + kAOpBytes;
@@ -254,7 +258,9 @@ __global__ void __launch_bounds__(kRM, 4) radial_tc(int E, int n_tiles32, const 
 __global__ void __launch_bounds__(kRM, 3) radial_bwd_tc(int E, const float4* __restrict__ ev,
                                                      const float* __restrict__ W1, const float* __restrict__ W2,
                                                      float rc, int p, const float* __restrict__ dz2,
-                                                     float* __restrict__ dr_tot, int* __restrict__ err) {
+                                                     float* __restrict__ dr_tot, const int* __restrict__ Edev,
+                                                     int* __restrict__ err) {
+  if (Edev) E = *Edev;  // edge count on the device (capacity-sized launch)
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sAh = smem;
   uint8_t* sAl = smem + kAOpBytes;
@@ -393,7 +399,7 @@ static int radial_grid(int tiles, int cols) {
 }
 
 int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float* W1, const float* W2, float rc,
-                     int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st) {
+                     int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st, const int* Edev) {
   if (n_tiles32 <= 0) return MLIP_OK;
   if (H != kRH) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
   const int tiles = (n_tiles32 * kZ2Tile + kRM - 1) / kRM;
@@ -401,14 +407,15 @@ int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float*
   MLIP_CUDA_TRY(cudaFuncSetAttribute(radial_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   {
     MLIP_PROF("radial_tc", st);
-    radial_tc<<<radial_grid(tiles, kRH), kRM, smem, st>>>(E, n_tiles32, ev, W1, W2, rc, p, use_bf16, z2t, err);
+    radial_tc<<<radial_grid(tiles, kRH), kRM, smem, st>>>(E, n_tiles32, ev, W1, W2, rc, p, use_bf16, z2t, Edev,
+                                                                 err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
 int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const float* W2, float rc, int p,
-                         const float* dz2, float* dr_tot, int* err, cudaStream_t st) {
+                         const float* dz2, float* dr_tot, int* err, cudaStream_t st, const int* Edev) {
   if (E <= 0) return MLIP_OK;
   if (H != kRH) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
   const int tiles = (E + kRM - 1) / kRM;
@@ -416,7 +423,7 @@ int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const 
   MLIP_CUDA_TRY(cudaFuncSetAttribute(radial_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   {
     MLIP_PROF("radial_bwd_tc", st);
-    radial_bwd_tc<<<radial_grid(tiles, 2 * kRH), kRM, smem, st>>>(E, ev, W1, W2, rc, p, dz2, dr_tot, err);
+    radial_bwd_tc<<<radial_grid(tiles, 2 * kRH), kRM, smem, st>>>(E, ev, W1, W2, rc, p, dz2, dr_tot, Edev, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
