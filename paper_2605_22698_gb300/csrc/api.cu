@@ -214,6 +214,23 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
         M->mix_scale.push_back(M->d_mixscale + (size_t)t * (M->L + 1));
       }
     }
+    if (M->H == 64) {  // split FP16 images of the radial MLP's hidden layer (the fused form needs H = 64)
+      std::vector<uint8_t> imgs, img1;
+      for (int t = 0; t < M->T; ++t) {
+        float sc = 1.0f;
+        pack_radial_images(M->host_weights.data() + (M->W2[t] - M->d_weights), img1, &sc);
+        imgs.insert(imgs.end(), img1.begin(), img1.end());
+        M->rad_scale.push_back(sc);
+      }
+      cudaError_t e2 = cudaMalloc(&M->d_radimg, imgs.size());
+      if (e2 == cudaSuccess) e2 = cudaMemcpy(M->d_radimg, imgs.data(), imgs.size(), cudaMemcpyHostToDevice);
+      if (e2 != cudaSuccess) {
+        cudaGetLastError();
+        set_error("tensor-core radial weight images: %s", cudaGetErrorString(e2));
+        mlip_model_free(M);
+        return MLIP_ERR_OOM;
+      }
+    }
     e = cudaMalloc(&M->d_w3img, all.size());
     if (e == cudaSuccess) e = cudaMemcpy(M->d_w3img, all.data(), all.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -269,6 +286,7 @@ int mlip_model_free(mlip_model* M) {
   if (M->d_w3img) cudaFree(M->d_w3img);
   if (M->d_wmixT) cudaFree(M->d_wmixT);
   if (M->d_miximg) cudaFree(M->d_miximg);
+  if (M->d_radimg) cudaFree(M->d_radimg);
   if (M->d_mixscale) cudaFree(M->d_mixscale);
   delete M;
   return MLIP_OK;

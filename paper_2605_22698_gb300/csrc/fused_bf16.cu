@@ -2060,8 +2060,9 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
   };
   MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
   for (int t = 0; t < T; ++t) {
-    MLIP_TRY(launch_radial_tc(H, E, n_tiles, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, use_bf16, z2t[t], flag + 1,
-                              st, Edev));
+    if (!M->d_radimg) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
+    MLIP_TRY(launch_radial_tc(H, E, n_tiles, ev, M->W1[t], M->d_radimg + (size_t)t * 32768, M->rad_scale[t],
+                              (float)M->rc, M->p, use_bf16, z2t[t], flag + 1, st, Edev));
     MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], M->d_w3img + M->w3_layer_off[t],
                              M->w3_goff[t], z2t[t], s, mA, mB, use_bf16, epar, flag + 1, st));
     MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
@@ -2099,8 +2100,8 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
       MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], Gm,
                                    M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, GaA, GaB, GbA, GbB, dY,
                                    dz2, use_bf16, b.d_sys_of, dws2, epar, flag + 1, st));
-      MLIP_TRY(launch_radial_bwd_tc(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, flag + 1, st,
-                                        Edev));
+      MLIP_TRY(launch_radial_bwd_tc(H, E, ev, M->W1[t], M->d_radimg + (size_t)t * 32768, M->rad_scale[t],
+                                    (float)M->rc, M->p, dz2, dr, flag + 1, st, Edev));
       std::swap(GaA, GbA);
       std::swap(GaB, GbB);
     }

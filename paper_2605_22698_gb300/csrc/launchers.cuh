@@ -43,10 +43,15 @@ int launch_seg_absmax2(const SystemBatch& b, int row, const float* a, const floa
 
 // Radial MLP of the fused form on the tensor cores (H = 64): z2 operand tiles,
 // and dE/dr accumulated from dE/dz2.  err receives the bounded-wait flags.
-int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float* W1, const float* W2, float rc,
-                     int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st, const int* Edev = nullptr);
-int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const float* W2, float rc, int p,
-                         const float* dz2, float* dr_tot, int* err, cudaStream_t st, const int* Edev = nullptr);
+int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float* W1, const uint8_t* w2img,
+                     float wsc, float rc, int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st,
+                     const int* Edev = nullptr);
+int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const uint8_t* w2img, float wsc, float rc,
+                         int p, const float* dz2, float* dr_tot, int* err, cudaStream_t st,
+                         const int* Edev = nullptr);
+// Split FP16 image of one layer's W2 for the two kernels above (32 KB) and its
+// power-of-two scale.
+void pack_radial_images(const float* W2, std::vector<uint8_t>& img, float* scale);
 
 // Channel mixes of the fused form on the tensor cores (C = 128): X (+ X2) times
 // the split weight images of one layer (pack_mix_images), forward or adjoint.

@@ -178,6 +178,10 @@ struct mlip_model {
   float* d_mixscale = nullptr;
   std::vector<const uint8_t*> mix_fwd_img, mix_bwd_img;
   std::vector<const float*> mix_scale;
+  // fused form: split FP16 images of the radial MLP's W2 per layer (32 KB each)
+  // and their power-of-two scales
+  uint8_t* d_radimg = nullptr;
+  std::vector<float> rad_scale;
   // fused form: W3 of every layer as BF16 tensor-core operands, grouped by path group
   uint8_t* d_w3img = nullptr;
   std::vector<size_t> w3_layer_off;

@@ -72,30 +72,48 @@ __global__ void edge_grad(int E, const float4* __restrict__ ev, const float* __r
 
 // F_i = sum_{e in seg(i)} (g_e - g_rev(e)) in FP64; per-atom virial
 // sum_{e in seg(i)} x_e (x) g_e (FP64) when vir is not null.
+// One warp per atom: lane l sums the atom's edges l, l + 32, ... in order and
+// a fixed butterfly combines the lanes (the order depends only on the edge's
+// position in the receiver's segment, so it is the same in any batch).
 __global__ void forces_virial(int n, const int* __restrict__ row_ptr, const int* __restrict__ rev,
                               const float4* __restrict__ g, const float4* __restrict__ ev,
                               double* __restrict__ forces, double* __restrict__ vir) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
   double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  double f0 = 0, f1 = 0, f2 = 0;
-  for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+  double f[3] = {0, 0, 0};
+  const int end = row_ptr[i + 1];
+  for (int e = row_ptr[i] + lane; e < end; e += 32) {
     const float4 a = g[e], b = g[rev[e]], x = ev[e];
-    f0 += (double)a.x - (double)b.x;
-    f1 += (double)a.y - (double)b.y;
-    f2 += (double)a.z - (double)b.z;
-    const double xe[3] = {x.x, x.y, x.z}, ge[3] = {a.x, a.y, a.z};
+    f[0] += (double)a.x - (double)b.x;
+    f[1] += (double)a.y - (double)b.y;
+    f[2] += (double)a.z - (double)b.z;
+    if (vir) {
+      const double xe[3] = {x.x, x.y, x.z}, ge[3] = {a.x, a.y, a.z};
 #pragma unroll
-    for (int p = 0; p < 3; ++p)
+      for (int p = 0; p < 3; ++p)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) v[3 * p + q] += xe[p] * ge[q];
+        for (int q = 0; q < 3; ++q) v[3 * p + q] += xe[p] * ge[q];
+    }
   }
-  forces[3 * i] = f0;
-  forces[3 * i + 1] = f1;
-  forces[3 * i + 2] = f2;
-  if (vir) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) vir[(size_t)i * 9 + k] = v[k];
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
+    if (vir) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+  }
+  if (lane == 0) {
+    forces[3 * i] = f[0];
+    forces[3 * i + 1] = f[1];
+    forces[3 * i + 2] = f[2];
+    if (vir) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) vir[(size_t)i * 9 + k] = v[k];
+    }
   }
 }
 
@@ -138,7 +156,7 @@ int launch_forces_virial(Workspace& ws, const SystemBatch& b, const int* row_ptr
   if (stress) MLIP_TRY(ws.get("fv.vir", (size_t)std::max(n, 1) * 9, &vir));
   if (n > 0) {
     MLIP_PROF("forces_virial", st);
-    forces_virial<<<(n + 127) / 128, 128, 0, st>>>(n, row_ptr, rev, g, ev, forces, vir);
+    forces_virial<<<(n + 3) / 4, 128, 0, st>>>(n, row_ptr, rev, g, ev, forces, vir);
     MLIP_LAUNCH_CHECK();
   }
   if (stress) MLIP_TRY(launch_seg_sum(ws, b, 9, vir, true, stress, st));

@@ -23,6 +23,9 @@
 // which keeps about 21 significant bits: the layer stays at FP32-level
 // accuracy while its flops run on the tensor pipe.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -40,6 +43,9 @@ constexpr int kRM = 128;         // edges per MMA tile (M)
 constexpr int kZ2Tile = 32;      // edges per z2 operand tile of the message kernels
 constexpr int kAOpBytes = kRM * kRH * 2;   // 16 KB
 constexpr int kBOpBytes = kRH * kRH * 2;   // 8 KB
+// CTAs per SM: forward 4 x (48 KB shared, 64 tensor-memory columns),
+// adjoint 3 x (64 KB, 128 columns)
+constexpr int kFwdCTAs = 4, kBwdCTAs = 3;
 
 __device__ __forceinline__ uint16_t f16_bits(float x) {
   const __half v = __float2half_rn(x);
@@ -83,33 +89,6 @@ __device__ __forceinline__ void put_row(uint8_t* Ahi, uint8_t* Alo, int r, const
     *reinterpret_cast<uint4*>(Ahi + tc::canon_off(r, kg * 8)) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
     *reinterpret_cast<uint4*>(Alo + tc::canon_off(r, kg * 8)) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
   }
-}
-
-// B operand [n][k] = W[k][n] (transpose = true) or W[n][k] times sc, FP16
-// hi and lo tiles, canonical layout.
-__device__ __forceinline__ void load_b(uint8_t* Bhi, uint8_t* Blo, const float* __restrict__ W, bool transpose,
-                                       float sc) {
-  for (int q = threadIdx.x; q < kRH * kRH; q += blockDim.x) {
-    const int n = q / kRH, k = q % kRH;
-    const float w = (transpose ? W[k * kRH + n] : W[n * kRH + k]) * sc;
-    uint16_t h, l;
-    split16(w, h, l);
-    *reinterpret_cast<uint16_t*>(Bhi + tc::canon_off(n, k)) = h;
-    *reinterpret_cast<uint16_t*>(Blo + tc::canon_off(n, k)) = l;
-  }
-}
-
-// Power-of-two scale of W (max |W| * scale in [2^13, 2^14)), all threads.
-__device__ __forceinline__ float weight_scale(const float* __restrict__ W, float* red) {
-  float m = 0.0f;
-  for (int q = threadIdx.x; q < kRH * kRH; q += blockDim.x) m = fmaxf(m, fabsf(W[q]));
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  float t = 0.0f;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
-  __syncthreads();
-  return row_scale(t);
 }
 
 // Issues D = A_hi B_hi + A_lo B_hi + A_hi B_lo over K = 64 (12 MMAs of K = 16)
@@ -160,10 +139,11 @@ __device__ __forceinline__ float absmax64(const float* v) {
 }
 
 // ------------------------------------------------------------- forward
-__global__ void __launch_bounds__(kRM, 4) radial_tc(int E, int n_tiles32, const float4* __restrict__ ev,
-                                                 const float* __restrict__ W1, const float* __restrict__ W2,
-                                                 float rc, int p, int use_bf16, uint8_t* __restrict__ z2t,
-                                                 const int* __restrict__ Edev, int* __restrict__ err) {
+__global__ void __launch_bounds__(kRM, kFwdCTAs) radial_tc(int E, int n_tiles32, const float4* __restrict__ ev,
+                                                 const float* __restrict__ W1, const uint8_t* __restrict__ w2img,
+                                                 float wsc, float rc, int p, int use_bf16,
+                                                 uint8_t* __restrict__ z2t, const int* __restrict__ Edev,
+                                                 int* __restrict__ err) {
   if (Edev) {  // edge count on the device (capacity-sized launch)
     E = *Edev;
     n_tiles32 = (E + kZ2Tile - 1) / kZ2Tile;
@@ -171,11 +151,10 @@ __global__ void __launch_bounds__(kRM, 4) radial_tc(int E, int n_tiles32, const 
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sAh = smem;
   uint8_t* sAl = smem + kAOpBytes;
-  uint8_t* sBh = smem + 2 * kAOpBytes;
+  uint8_t* sBh = smem + 2 * kAOpBytes;  // W2^T image: hi then lo
   uint8_t* sBl = sBh + kBOpBytes;
   __shared__ __align__(16) float sW1[8 * kRH];
-  __shared__ float red[4];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, bar_w;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -183,14 +162,16 @@ __global__ void __launch_bounds__(kRM, 4) radial_tc(int E, int n_tiles32, const 
     tc::tmem_alloc(&tmem_base, kRH);
     tc::tmem_relinquish();
   }
+  bool w_waited = false;  // thread 0: the weight image has landed
   if (tid == 0) {
     tc::mbar_init(&bar, 1);
+    tc::mbar_init(&bar_w, 1);
     tc::fence_mbar_init();
     abort_s = 0;
+    tc::mbar_arrive_expect_tx(&bar_w, 2 * kBOpBytes);
+    tc::bulk_g2s(sBh, w2img, 2 * kBOpBytes, &bar_w);
   }
   for (int q = tid; q < 8 * kRH; q += blockDim.x) sW1[q] = W1[q];
-  const float wsc = weight_scale(W2, red);
-  load_b(sBh, sBl, W2, true, wsc);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -215,9 +196,16 @@ __global__ void __launch_bounds__(kRM, 4) radial_tc(int E, int n_tiles32, const 
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0) {
+      if (!w_waited) w_waited = tc::mbar_wait(&bar_w, 0);
       tc::fence_after_sync();
-      mma_tile(tmem_base, sAh, sAl, sBh, sBl, &bar);
-      ++issued;
+      if (w_waited) {
+        mma_tile(tmem_base, sAh, sAl, sBh, sBl, &bar);
+        ++issued;
+      } else {
+        atomicOr(err, 32);
+        abort_s = 1;
+        tc::mbar_arrive(&bar);  // completes the phase: nobody waits for an MMA that was not issued
+      }
     }
     if (!tc::mbar_wait(&bar, phase)) {
       atomicOr(err, 32);
@@ -248,15 +236,19 @@ __global__ void __launch_bounds__(kRM, 4) radial_tc(int E, int n_tiles32, const 
     tc::fence_after_sync();
     if (abort_s) break;
   }
-  if (tid == 0 && issued > done) tc::mbar_wait(&bar, done & 1, 1LL << 20);  // the product in flight, bounded
+  if (tid == 0) {
+    if (issued > done) tc::mbar_wait(&bar, done & 1, 1LL << 20);  // the product in flight, bounded
+    if (!w_waited) tc::mbar_wait(&bar_w, 0, 1LL << 20);          // the weight copy in flight, bounded
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem_base, kRH);
 }
 
 // ------------------------------------------------------------- adjoint
-__global__ void __launch_bounds__(kRM, 3) radial_bwd_tc(int E, const float4* __restrict__ ev,
-                                                     const float* __restrict__ W1, const float* __restrict__ W2,
+__global__ void __launch_bounds__(kRM, kBwdCTAs) radial_bwd_tc(int E, const float4* __restrict__ ev,
+                                                     const float* __restrict__ W1,
+                                                     const uint8_t* __restrict__ w2img, float wsc,
                                                      float rc, int p, const float* __restrict__ dz2,
                                                      float* __restrict__ dr_tot, const int* __restrict__ Edev,
                                                      int* __restrict__ err) {
@@ -264,13 +256,12 @@ __global__ void __launch_bounds__(kRM, 3) radial_bwd_tc(int E, const float4* __r
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sAh = smem;
   uint8_t* sAl = smem + kAOpBytes;
-  uint8_t* sBth = smem + 2 * kAOpBytes;   // W2^T: a2 = z1 W2
+  uint8_t* sBth = smem + 2 * kAOpBytes;   // W2^T: a2 = z1 W2      (the image: hi, lo,
   uint8_t* sBtl = sBth + kBOpBytes;
-  uint8_t* sBnh = sBtl + kBOpBytes;       // W2:   dz1 = da2 W2^T
+  uint8_t* sBnh = sBtl + kBOpBytes;       // W2:   dz1 = da2 W2^T   then hi, lo)
   uint8_t* sBnl = sBnh + kBOpBytes;
   __shared__ __align__(16) float sW1[8 * kRH];
-  __shared__ float red[4];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar, bar_w;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -278,15 +269,16 @@ __global__ void __launch_bounds__(kRM, 3) radial_bwd_tc(int E, const float4* __r
     tc::tmem_alloc(&tmem_base, 2 * kRH);
     tc::tmem_relinquish();
   }
+  bool w_waited = false;  // thread 0: the weight image has landed
   if (tid == 0) {
     tc::mbar_init(&bar, 1);
+    tc::mbar_init(&bar_w, 1);
     tc::fence_mbar_init();
     abort_s = 0;
+    tc::mbar_arrive_expect_tx(&bar_w, 4 * kBOpBytes);
+    tc::bulk_g2s(sBth, w2img, 4 * kBOpBytes, &bar_w);
   }
   for (int q = tid; q < 8 * kRH; q += blockDim.x) sW1[q] = W1[q];
-  const float wsc = weight_scale(W2, red);
-  load_b(sBth, sBtl, W2, true, wsc);
-  load_b(sBnh, sBnl, W2, false, wsc);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -313,9 +305,16 @@ __global__ void __launch_bounds__(kRM, 3) radial_bwd_tc(int E, const float4* __r
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0) {
+      if (!w_waited) w_waited = tc::mbar_wait(&bar_w, 0);
       tc::fence_after_sync();
-      mma_tile(tmem_base, sAh, sAl, sBth, sBtl, &bar);
-      ++issued;
+      if (w_waited) {
+        mma_tile(tmem_base, sAh, sAl, sBth, sBtl, &bar);
+        ++issued;
+      } else {
+        atomicOr(err, 64);
+        abort_s = 1;
+        tc::mbar_arrive(&bar);  // completes the phase: nobody waits for an MMA that was not issued
+      }
     }
     if (!tc::mbar_wait(&bar, phase)) {
       atomicOr(err, 64);
@@ -351,8 +350,12 @@ __global__ void __launch_bounds__(kRM, 3) radial_bwd_tc(int E, const float4* __r
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      mma_tile(tmem_base + kRH, sAh, sAl, sBnh, sBnl, &bar);
-      ++issued;
+      if (!abort_s) {
+        mma_tile(tmem_base + kRH, sAh, sAl, sBnh, sBnl, &bar);
+        ++issued;
+      } else {
+        tc::mbar_arrive(&bar);
+      }
     }
     if (!tc::mbar_wait(&bar, phase)) {
       atomicOr(err, 64);
@@ -382,7 +385,10 @@ __global__ void __launch_bounds__(kRM, 3) radial_bwd_tc(int E, const float4* __r
     tc::fence_after_sync();
     if (abort_s) break;
   }
-  if (tid == 0 && issued > done) tc::mbar_wait(&bar, done & 1, 1LL << 20);  // the product in flight, bounded
+  if (tid == 0) {
+    if (issued > done) tc::mbar_wait(&bar, done & 1, 1LL << 20);  // the product in flight, bounded
+    if (!w_waited) tc::mbar_wait(&bar_w, 0, 1LL << 20);          // the weight copy in flight, bounded
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem_base, 2 * kRH);
@@ -390,16 +396,41 @@ __global__ void __launch_bounds__(kRM, 3) radial_bwd_tc(int E, const float4* __r
 
 }  // namespace
 
-// Persistent grids: CTAs per SM bounded by tensor memory (512 columns) and 8.
-static int radial_grid(int tiles, int cols) {
+// Split FP16 image of W2 for the radial kernels: the forward operand
+// B[n][k] = W2[k][n] (hi 8 KB, lo 8 KB) then the adjoint's B[n][k] = W2[n][k]
+// (hi, lo), canonical layout, all times the power-of-two *scale with
+// max|W2| * scale in [2^13, 2^14).  32 KB.
+void pack_radial_images(const float* W2, std::vector<uint8_t>& img, float* scale) {
+  float amax = 0.0f;
+  for (int q = 0; q < kRH * kRH; ++q) amax = std::max(amax, std::fabs(W2[q]));
+  const float sc = amax > 0.0f ? std::ldexp(1.0f, std::max(-100, std::min(100, 13 - std::ilogb(amax)))) : 1.0f;
+  *scale = sc;
+  img.assign(4 * kBOpBytes, 0);
+  for (int which = 0; which < 2; ++which)
+    for (int n = 0; n < kRH; ++n)
+      for (int k = 0; k < kRH; ++k) {
+        const float x = (which == 0 ? W2[k * kRH + n] : W2[n * kRH + k]) * sc;
+        const __half h = __float2half_rn(x);
+        const __half lo = __float2half_rn(x - __half2float(h));
+        uint8_t* o = img.data() + (size_t)which * 2 * kBOpBytes + tc::canon_off(n, k);
+        std::memcpy(o, &h, 2);
+        std::memcpy(o + kBOpBytes, &lo, 2);
+      }
+}
+
+// Persistent grids: as many CTAs as fit on the device at once (the launch
+// bounds' CTAs per SM: their registers, shared memory and tensor-memory
+// columns fit together), at most one per tile.
+static int radial_grid(int per_sm, int tiles) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return std::max(1, std::min(tiles, sms * std::min(8, 512 / cols)));
+  return std::max(1, std::min(tiles, sms * per_sm));
 }
 
-int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float* W1, const float* W2, float rc,
-                     int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st, const int* Edev) {
+int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float* W1, const uint8_t* w2img,
+                     float wsc, float rc, int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st,
+                     const int* Edev) {
   if (n_tiles32 <= 0) return MLIP_OK;
   if (H != kRH) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
   const int tiles = (n_tiles32 * kZ2Tile + kRM - 1) / kRM;
@@ -407,15 +438,15 @@ int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float*
   MLIP_CUDA_TRY(cudaFuncSetAttribute(radial_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   {
     MLIP_PROF("radial_tc", st);
-    radial_tc<<<radial_grid(tiles, kRH), kRM, smem, st>>>(E, n_tiles32, ev, W1, W2, rc, p, use_bf16, z2t, Edev,
-                                                                 err);
+    radial_tc<<<radial_grid(kFwdCTAs, tiles), kRM, smem, st>>>(E, n_tiles32, ev, W1, w2img, wsc, rc, p,
+                                                                       use_bf16, z2t, Edev, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
-int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const float* W2, float rc, int p,
-                         const float* dz2, float* dr_tot, int* err, cudaStream_t st, const int* Edev) {
+int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const uint8_t* w2img, float wsc, float rc,
+                         int p, const float* dz2, float* dr_tot, int* err, cudaStream_t st, const int* Edev) {
   if (E <= 0) return MLIP_OK;
   if (H != kRH) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
   const int tiles = (E + kRM - 1) / kRM;
@@ -423,7 +454,8 @@ int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const 
   MLIP_CUDA_TRY(cudaFuncSetAttribute(radial_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   {
     MLIP_PROF("radial_bwd_tc", st);
-    radial_bwd_tc<<<radial_grid(tiles, 2 * kRH), kRM, smem, st>>>(E, ev, W1, W2, rc, p, dz2, dr_tot, Edev, err);
+    radial_bwd_tc<<<radial_grid(kBwdCTAs, tiles), kRM, smem, st>>>(E, ev, W1, w2img, wsc, rc, p, dz2,
+                                                                              dr_tot, Edev, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
