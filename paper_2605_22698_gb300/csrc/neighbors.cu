@@ -38,6 +38,11 @@ struct Grid {
   int max_bins, maxdeg;
   int any_pbc;
   int bin_off;     // first bin of this system in the batch's bin arrays
+  // FP32 pre-test of candidate pairs: bv[a] = Cartesian vector of one bin step
+  // along axis a; pf = 1 when the coordinates involved are small enough for
+  // the pre-test's error bound (nl_setup)
+  float bv[9];
+  int pf;
 };
 
 // Grid of atom i: one per system of a batch (sys_of == nullptr: one system).
@@ -138,6 +143,19 @@ __global__ void nl_setup(Grid* grids, int nsys, const long long* bbox_all) {
     if (!g->pbc[k]) r = min(r, g->nb[k]);
     g->reach[k] = r;
   }
+  // bin step vectors; the pre-test is used while every coordinate it touches
+  // (local offsets within a bin, bin-to-bin shifts within reach) is below 2000 A
+  double span_all = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    double len2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      const double v = g->bsz[a] * (g->any_pbc ? g->h[3 * a + k] : (a == k ? 1.0 : 0.0));
+      g->bv[3 * a + k] = (float)v;
+      len2 += v * v;
+    }
+    span_all += (g->reach[a] + 1.0) * sqrt(len2);
+  }
+  g->pf = span_all < 2000.0 && g->rc < 100.0 ? 1 : 0;
 }
 
 __device__ __forceinline__ void bin_coords(const Grid* g, const double* f, int* b) {
@@ -148,8 +166,11 @@ __device__ __forceinline__ void bin_coords(const Grid* g, const double* f, int* 
   }
 }
 
+// Bin of every atom, and its position relative to the bin's corner (in the
+// atom's own periodic image) rounded to FP32 for the pre-test of nl_pairs_warp.
 __global__ void nl_bin(int n, const Grid* __restrict__ grids, const int* __restrict__ sys_of,
-                       const double* __restrict__ frac, int* __restrict__ bin_of, int* __restrict__ counts) {
+                       const double* __restrict__ pos, const double* __restrict__ frac, const int* __restrict__ img,
+                       int* __restrict__ bin_of, int* __restrict__ counts, float4* __restrict__ loc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Grid* g = grid_of(grids, sys_of, i);
@@ -159,6 +180,14 @@ __global__ void nl_bin(int n, const Grid* __restrict__ grids, const int* __restr
   int bin = g->bin_off + (b[0] * g->nb[1] + b[1]) * g->nb[2] + b[2];
   bin_of[i] = bin;
   atomicAdd(&counts[bin], 1);
+  double u[3];
+  for (int a = 0; a < 3; ++a) u[a] = g->lo[a] + b[a] * g->bsz[a] + img[3 * i + a];
+  double x[3];
+  for (int k = 0; k < 3; ++k) {
+    const double corner = g->any_pbc ? (u[0] * g->h[k] + u[1] * g->h[3 + k]) + u[2] * g->h[6 + k] : u[k];
+    x[k] = pos[3 * i + k] - corner;
+  }
+  loc[i] = make_float4((float)x[0], (float)x[1], (float)x[2], 0.0f);
 }
 
 __global__ void nl_scatter(int n, const int* __restrict__ bin_of, const int* __restrict__ bin_start,
@@ -181,9 +210,14 @@ __device__ __forceinline__ unsigned long long make_key(int j, int s0, int s1, in
 // candidate list walked by all lanes at once (each lane finds its bin by a
 // binary search over the prefix with shuffles).  Matches are compacted with a
 // ballot into the receiver's slab (order irrelevant: nl_sort orders them).
+// Candidates are pre-tested in FP32 from the atoms' offsets within their bins
+// plus the bin-to-bin shift (|error| far below the slack of the test's
+// threshold, rc^2 * 1.02 + 0.01); only the survivors take the exact FP64 test,
+// which alone decides (the FP64 pipe is narrow on this part).
 __global__ void nl_pairs_warp(int n, const Grid* __restrict__ grids, const int* __restrict__ sys_of,
                               const double* __restrict__ pos,
                               const double* __restrict__ frac, const int* __restrict__ img,
+                              const float4* __restrict__ loc,
                               const int* __restrict__ bin_start, const int* __restrict__ bin_atoms,
                               unsigned long long* __restrict__ slab, int* __restrict__ deg, int* __restrict__ flags) {
   const int lane = threadIdx.x & 31;
@@ -198,6 +232,9 @@ __global__ void nl_pairs_warp(int n, const Grid* __restrict__ grids, const int* 
   const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
   const double* h = g->h;
   const double rc2 = g->rc2;
+  const bool pf = g->pf != 0;
+  const float thr = (float)rc2 * 1.02f + 0.01f;
+  const float4 li = loc[i];
   const int r0 = g->reach[0], r1 = g->reach[1], r2 = g->reach[2];
   const int w0 = 2 * r0 + 1, w1 = 2 * r1 + 1, w2 = 2 * r2 + 1;
   const int nbins = w0 * w1 * w2;
@@ -207,8 +244,12 @@ __global__ void nl_pairs_warp(int n, const Grid* __restrict__ grids, const int* 
     // this lane's bin
     const int bidx = base + lane;
     int beg = 0, len = 0, q0 = 0, q1 = 0, q2 = 0;
+    float tx = 0.0f, ty = 0.0f, tz = 0.0f;  // bin shift minus the receiver's offset
     if (bidx < nbins) {
       const int d2 = bidx % w2 - r2, d1 = (bidx / w2) % w1 - r1, d0 = bidx / (w2 * w1) - r0;
+      tx = ((float)d0 * g->bv[0] + (float)d1 * g->bv[3] + (float)d2 * g->bv[6]) - li.x;
+      ty = ((float)d0 * g->bv[1] + (float)d1 * g->bv[4] + (float)d2 * g->bv[7]) - li.y;
+      tz = ((float)d0 * g->bv[2] + (float)d1 * g->bv[5] + (float)d2 * g->bv[8]) - li.z;
       int c0 = b[0] + d0, c1 = b[1] + d1, c2 = b[2] + d2;
       bool ok = true;
       if (g->pbc[0]) { q0 = (int)floor((double)c0 / g->nb[0]); c0 -= q0 * g->nb[0]; } else ok = ok && c0 >= 0 && c0 < g->nb[0];
@@ -243,10 +284,20 @@ __global__ void nl_pairs_warp(int n, const Grid* __restrict__ grids, const int* 
       const int kinc = __shfl_sync(0xffffffffu, incl, k);
       const int kq0 = __shfl_sync(0xffffffffu, q0, k), kq1 = __shfl_sync(0xffffffffu, q1, k),
                 kq2 = __shfl_sync(0xffffffffu, q2, k);
+      const float ktx = __shfl_sync(0xffffffffu, tx, k), kty = __shfl_sync(0xffffffffu, ty, k),
+                  ktz = __shfl_sync(0xffffffffu, tz, k);
       bool hit = false;
       unsigned long long key = 0;
+      int j = 0;
       if (act) {
-        const int j = bin_atoms[kbeg + fidx - (kinc - klen)];
+        j = bin_atoms[kbeg + fidx - (kinc - klen)];
+        if (pf) {
+          const float4 lj = loc[j];
+          const float ex = lj.x + ktx, ey = lj.y + kty, ez = lj.z + ktz;
+          if (ex * ex + ey * ey + ez * ez > thr) j = -1;  // certainly beyond rc
+        }
+      }
+      if (act && j >= 0) {
         const int S0 = kq0 - img[3 * j] + ni0;
         const int S1 = kq1 - img[3 * j + 1] + ni1;
         const int S2 = kq2 - img[3 * j + 2] + ni2;
@@ -507,6 +558,8 @@ int build_neighbors_batch(Workspace& ws, const double* d_pos, const SystemBatch&
   MLIP_TRY(ws.get("nl.deg", (size_t)nn, &deg));
   MLIP_TRY(ws.get("nl.flags", 4, &flags));
   MLIP_TRY(ws.get("nl.bbox", (size_t)6 * nsys, &bbox));
+  float4* loc = nullptr;
+  MLIP_TRY(ws.get("nl.loc", (size_t)nn, &loc));
   MLIP_TRY(ws.get("nl.row_ptr", (size_t)nn + 1, &out->row_ptr));
   std::vector<long long> bb_init(6 * (size_t)nsys);
   for (int s = 0; s < nsys; ++s)
@@ -527,14 +580,14 @@ int build_neighbors_batch(Workspace& ws, const double* d_pos, const SystemBatch&
     MLIP_CUDA_TRY(cudaMemsetAsync(cursor, 0, ((size_t)nbins + 1) * sizeof(int), st));
     if (n > 0) { MLIP_PROF("nl_frac", st); nl_frac<<<blocks, threads, 0, st>>>(d_pos, n, dg, b.d_sys_of, frac, img, bbox); }
     { MLIP_PROF("nl_setup", st); nl_setup<<<(nsys + 127) / 128, 128, 0, st>>>(dg, nsys, bbox); }
-    if (n > 0) { MLIP_PROF("nl_bin", st); nl_bin<<<blocks, threads, 0, st>>>(n, dg, b.d_sys_of, frac, bin_of, counts); }
+    if (n > 0) { MLIP_PROF("nl_bin", st); nl_bin<<<blocks, threads, 0, st>>>(n, dg, b.d_sys_of, d_pos, frac, img, bin_of, counts, loc); }
     MLIP_LAUNCH_CHECK();
     MLIP_TRY(exclusive_scan_i32(ws, counts, bin_start, nbins, st));
     unsigned long long* slab = nullptr;
     MLIP_TRY(ws.get("nl.slab", (size_t)nn * maxdeg, &slab));
     if (n > 0) {
       { MLIP_PROF("nl_scatter", st); nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms); }
-      { MLIP_PROF("nl_pairs", st); nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, b.d_sys_of, d_pos, frac, img, bin_start, bin_atoms, slab, deg, flags); }
+      { MLIP_PROF("nl_pairs", st); nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, b.d_sys_of, d_pos, frac, img, loc, bin_start, bin_atoms, slab, deg, flags); }
       MLIP_LAUNCH_CHECK();
     }
     MLIP_TRY(exclusive_scan_i32(ws, deg, out->row_ptr, n, st));
@@ -726,6 +779,7 @@ extern "C" int mlip_neighbors_noalloc(const double* pos, int64_t n64, const doub
   Grid* dg = cv.take<Grid>(1);
   double* frac = cv.take<double>(3 * nn);
   int* img = cv.take<int>(3 * nn);
+  float4* loc = cv.take<float4>(nn);
   int* bin_of = cv.take<int>(nn);
   int* counts = cv.take<int>((size_t)hg.max_bins + 1);
   int* bin_start = cv.take<int>((size_t)hg.max_bins + 1);
@@ -750,7 +804,7 @@ extern "C" int mlip_neighbors_noalloc(const double* pos, int64_t n64, const doub
   if (n > 0) {
     nl_frac<<<blocks, threads, 0, st>>>(pos, n, dg, nullptr, frac, img, bbox);
     nl_setup<<<1, 32, 0, st>>>(dg, 1, bbox);
-    nl_bin<<<blocks, threads, 0, st>>>(n, dg, nullptr, frac, bin_of, counts);
+    nl_bin<<<blocks, threads, 0, st>>>(n, dg, nullptr, pos, frac, img, bin_of, counts, loc);
   } else {
     nl_setup<<<1, 32, 0, st>>>(dg, 1, bbox);
   }
@@ -758,8 +812,8 @@ extern "C" int mlip_neighbors_noalloc(const double* pos, int64_t n64, const doub
   MLIP_TRY(scan_fixed(counts, bin_start, hg.max_bins, bsum, st));
   if (n > 0) {
     nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms);
-    nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, nullptr, pos, frac, img, bin_start, bin_atoms, slab, deg,
-                                               flags);
+    nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, nullptr, pos, frac, img, loc, bin_start, bin_atoms, slab,
+                                               deg, flags);
     MLIP_LAUNCH_CHECK();
   }
   MLIP_TRY(scan_fixed(deg, row_ptr, n, bsum, st));
