@@ -365,6 +365,7 @@ def run_ours(args, rank, world):
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (512 MB write)", "stress": stress},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernel_share": share,
+        "kernel_ms_per_step": round(tot_all / args.steps, 4),
         "plain_fp32": plain,
         "cpu_baseline": cpu, "clocks": clocks, "wall_s": round(t_wall, 3),
         "peaks": peaks(),

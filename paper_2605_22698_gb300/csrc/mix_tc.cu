@@ -11,8 +11,10 @@
 // B operand is the model's pre-split image of W_l^T (forward) or W_l
 // (adjoint), bulk-copied once per CTA; the product A_hi B_hi + A_lo B_hi +
 // A_hi B_lo (three tcgen05 MMA chains, FP32 accumulation, N = 128) keeps about
-// 21 significant bits.  Thread r then reads its accumulator row back from
-// tensor memory, removes both scales exactly and applies the update.
+// 21 significant bits.  Two threads share a row (64 channels each; 8 warps per
+// CTA): they load and split their halves, read their halves of the
+// accumulator row back from tensor memory, remove both scales exactly and
+// apply the update.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -49,7 +51,7 @@ __device__ __forceinline__ float pow2_scale(float amax) {
 
 // smem: A_hi, A_lo, B_hi, B_lo (32 KB each), then the barriers
 template <bool BWD>
-__global__ void __launch_bounds__(kMM) mix_tc(int n, int L, const float* __restrict__ X, const float* __restrict__ X2,
+__global__ void __launch_bounds__(2 * kMM) mix_tc(int n, int L, const float* __restrict__ X, const float* __restrict__ X2,
                                               const uint8_t* __restrict__ wimg, const float* __restrict__ wscale,
                                               const float* __restrict__ hin, float* __restrict__ out,
                                               float* __restrict__ u0, const float* __restrict__ u0_in,
@@ -62,10 +64,13 @@ __global__ void __launch_bounds__(kMM) mix_tc(int n, int L, const float* __restr
   __shared__ __align__(8) uint64_t bar_w, bar_mma;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
+  __shared__ float s_amax[2 * kMM];
   const int l = blockIdx.y, R = 2 * l + 1, D = (L + 1) * (L + 1);
   const int rows = n * R, row0 = blockIdx.x * kMM;
   if (row0 >= rows) return;  // uniform over the CTA
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int rt = tid & (kMM - 1), half = tid >> 7;  // row of the tile, half of the channels
+  constexpr int HC = kMC / 2;
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, kMC);
     tc::tmem_relinquish();
@@ -84,44 +89,48 @@ __global__ void __launch_bounds__(kMM) mix_tc(int n, int L, const float* __restr
     tc::bulk_g2s(sBh, wl, kMOp, &bar_w);
     tc::bulk_g2s(sBl, wl + kMOp, kMOp, &bar_w);
   }
-  // this thread's row, scaled and split
-  const int r = row0 + tid;
+  // this thread's half row, scaled (by the row's power of two) and split
+  const int r = row0 + rt;
   const bool live = r < rows;
   const int nd = live ? r / R : 0, mm = live ? r % R : 0;
   const size_t base = ((size_t)nd * D + l * l + mm) * kMC;
-  float v[kMC];
+  const int cq = half * (HC / 4);  // first float4 of this half
+  float v[HC];
   if (live) {
     const float4* x4 = reinterpret_cast<const float4*>(X + base);
 #pragma unroll
-    for (int q = 0; q < kMC / 4; ++q) {
-      float4 a = x4[q];
+    for (int q = 0; q < HC / 4; ++q) {
+      float4 a = x4[cq + q];
       if (X2) {
-        const float4 b = reinterpret_cast<const float4*>(X2 + base)[q];
+        const float4 b = reinterpret_cast<const float4*>(X2 + base)[cq + q];
         a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
       }
       if (BWD && l == 0) {
-        const float4 u = reinterpret_cast<const float4*>(u0_in + (size_t)nd * kMC)[q];
+        const float4 u = reinterpret_cast<const float4*>(u0_in + (size_t)nd * kMC)[cq + q];
         a.x *= silu_grad_f(u.x); a.y *= silu_grad_f(u.y); a.z *= silu_grad_f(u.z); a.w *= silu_grad_f(u.w);
       }
       v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < kMC; ++k) v[k] = 0.0f;
+    for (int k = 0; k < HC; ++k) v[k] = 0.0f;
   }
   float amax = 0.0f;
 #pragma unroll
-  for (int k = 0; k < kMC; ++k) amax = fmaxf(amax, fabsf(v[k]));
-  const float sc = pow2_scale(amax);
+  for (int k = 0; k < HC; ++k) amax = fmaxf(amax, fabsf(v[k]));
+  s_amax[tid] = amax;
+  __syncthreads();
+  const float sc = pow2_scale(fmaxf(s_amax[rt], s_amax[rt + kMM]));
 #pragma unroll
-  for (int kg = 0; kg < kMC / 8; ++kg) {
+  for (int kh = 0; kh < HC / 8; ++kh) {
+    const int kg = half * (HC / 8) + kh;
     uint32_t ph[4], pl[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint16_t hh[2], ll[2];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const float x = v[kg * 8 + 2 * q + j] * sc;
+        const float x = v[kh * 8 + 2 * q + j] * sc;
         const __half h = __float2half_rn(x);
         hh[j] = *reinterpret_cast<const uint16_t*>(&h);
         ll[j] = h16(x - __half2float(h));
@@ -129,8 +138,8 @@ __global__ void __launch_bounds__(kMM) mix_tc(int n, int L, const float* __restr
       ph[q] = (uint32_t)hh[0] | ((uint32_t)hh[1] << 16);
       pl[q] = (uint32_t)ll[0] | ((uint32_t)ll[1] << 16);
     }
-    *reinterpret_cast<uint4*>(sAh + canon128(tid, kg * 8)) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-    *reinterpret_cast<uint4*>(sAl + canon128(tid, kg * 8)) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    *reinterpret_cast<uint4*>(sAh + canon128(rt, kg * 8)) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    *reinterpret_cast<uint4*>(sAl + canon128(rt, kg * 8)) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
   }
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
@@ -168,12 +177,12 @@ __global__ void __launch_bounds__(kMM) mix_tc(int n, int L, const float* __restr
   tc::fence_after_sync();
   if (!abort_s) {  // every warp reads its lanes (tcgen05.ld is warp-collective)
     const float inv = 1.0f / (sc * wscale[l]);
-    const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16);
+    const uint32_t taddr = tmem_base + ((uint32_t)((warp & 3) * 32) << 16);
     float4* o4 = reinterpret_cast<float4*>(out + base);
     const float4* h4 = reinterpret_cast<const float4*>(hin + base);
     float4* u4 = reinterpret_cast<float4*>(u0 + (size_t)nd * kMC);
 #pragma unroll 1
-    for (int c0 = 0; c0 < kMC; c0 += 32) {
+    for (int c0 = half * HC; c0 < (half + 1) * HC; c0 += 32) {
       float w[32];
 #pragma unroll
       for (int c = 0; c < 32; c += 8) tc::tmem_ld8(taddr + c0 + c, w + c);
@@ -249,11 +258,11 @@ int launch_mix_tc(bool bwd, int n, int C, int L, const float* X, const float* X2
   if (bwd) {
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     MLIP_PROF("mix_tc_bwd", st);
-    mix_tc<true><<<grid, kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err);
+    mix_tc<true><<<grid, 2 * kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err);
   } else {
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     MLIP_PROF("mix_tc", st);
-    mix_tc<false><<<grid, kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err);
+    mix_tc<false><<<grid, 2 * kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
