@@ -281,6 +281,8 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
 int mlip_model_free(mlip_model* M) {
   if (!M) return MLIP_OK;
   cudaDeviceSynchronize();
+  free_eval_graph(M->egraph);
+  M->egraph = nullptr;
   M->ws.release();
   if (M->d_weights) cudaFree(M->d_weights);
   if (M->d_w3img) cudaFree(M->d_w3img);
@@ -421,8 +423,9 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
 }
 
 int evaluate(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b, double* d_energy,
-             double* d_forces, double* d_stress, cudaStream_t st) {
+             double* d_forces, double* d_stress, cudaStream_t st, bool graph) {
   if (M->precision == MLIP_PREC_FP32) return evaluate_plain(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st);
+  if (graph) return evaluate_fused_graph(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st);
   return evaluate_fused(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st);
 }
 
@@ -462,7 +465,7 @@ extern "C" int mlip_energy_forces(mlip_model* M, const double* pos, const int32_
   SystemBatch b;
   single_system(b, n, cell, pbc);
   MLIP_TRY(upload_batch(ws, M->stage, b, st));
-  MLIP_TRY(evaluate(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st));
+  MLIP_TRY(evaluate(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st, true));
   if (!on_device) {
     MLIP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (forces) MLIP_CUDA_TRY(cudaMemcpyAsync(forces, d_forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
@@ -520,7 +523,7 @@ extern "C" int mlip_energy_forces_batch(mlip_model* M, int32_t n_systems, const 
   b.cell.assign(cells, cells + 9 * (size_t)n_systems);
   b.pbc.assign(pbc, pbc + 3 * (size_t)n_systems);
   MLIP_TRY(upload_batch(ws, M->stage, b, st));
-  MLIP_TRY(evaluate(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st));
+  MLIP_TRY(evaluate(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st, true));
   if (!on_device) {
     MLIP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double) * n_systems, cudaMemcpyDeviceToHost, st));
     if (forces) MLIP_CUDA_TRY(cudaMemcpyAsync(forces, d_forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));

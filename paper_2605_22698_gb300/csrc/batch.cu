@@ -150,15 +150,24 @@ int upload_batch(Workspace& ws, HostStage& stage, SystemBatch& b, cudaStream_t s
   std::copy(b.sys_chunk_off.begin(), b.sys_chunk_off.end(), hi + nsys + 1 + 3 * nch);
   unsigned char* dblob = nullptr;
   MLIP_TRY(ws.get("batch.blob", bytes, &dblob));
-  MLIP_CUDA_TRY(cudaMemcpyAsync(dblob, hp, bytes, cudaMemcpyHostToDevice, st));
+  b.d_sys_of = nullptr;
+  if (nsys > 1 && b.n > 0) MLIP_TRY(ws.get("batch.sys_of", (size_t)b.n, &b.d_sys_of));
   b.d_cell = reinterpret_cast<double*>(dblob);
   b.d_inv_vol = b.d_cell + 9 * nsys;
   b.d_atom_off = reinterpret_cast<int*>(b.d_cell + nd);
   b.d_chunk = b.d_atom_off + nsys + 1;
   b.d_sys_chunk_off = b.d_chunk + 3 * nch;
-  b.d_sys_of = nullptr;
-  if (nsys > 1 && b.n > 0) {
-    MLIP_TRY(ws.get("batch.sys_of", (size_t)b.n, &b.d_sys_of));
+  // the same tables as the last upload into unchanged buffers: nothing to copy
+  std::vector<double> sig;
+  sig.reserve(1 + (size_t)(nsys + 1) + 12 * (size_t)nsys);
+  sig.push_back((double)nsys);
+  for (int s = 0; s <= nsys; ++s) sig.push_back((double)b.atom_off[s]);
+  sig.insert(sig.end(), b.cell.begin(), b.cell.end());
+  for (uint8_t v : b.pbc) sig.push_back(v);
+  if (sig == ws.batch_sig && ws.batch_gen == ws.gen) return MLIP_OK;
+  ws.batch_sig.clear();
+  MLIP_CUDA_TRY(cudaMemcpyAsync(dblob, hp, bytes, cudaMemcpyHostToDevice, st));
+  if (b.d_sys_of) {
     const int n = (int)b.n;
     MLIP_PROF("fill_sys_of", st);
     fill_sys_of<<<std::min((n + 255) / 256, 4096), 256, 0, st>>>(n, nsys, b.d_atom_off, b.d_sys_of);
@@ -166,6 +175,8 @@ int upload_batch(Workspace& ws, HostStage& stage, SystemBatch& b, cudaStream_t s
   }
   // the pinned blob is reused by the next upload: wait for this copy
   MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  ws.batch_sig = sig;
+  ws.batch_gen = ws.gen;
   return MLIP_OK;
 }
 

@@ -2123,8 +2123,10 @@ int check_eval_flags(const int* flag, cudaStream_t st) {
   return MLIP_OK;
 }
 
-int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
-                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+// evaluate_fused; reports the edge count and the degree capacity of its build
+static int evaluate_fused_exact(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                                double* d_energy, double* d_forces, double* d_stress, cudaStream_t st,
+                                int64_t* E_out, int* maxdeg_out) {
   Workspace& ws = M->ws;
   int* flag = nullptr;
   MLIP_TRY(ws.get("chk.flag", 2, &flag));
@@ -2132,8 +2134,158 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
   MLIP_TRY(launch_check_inputs((int)b.n, d_pos, d_species, M->S, flag, st));
   NeighborList nl;
   MLIP_TRY(build_neighbors_batch(ws, d_pos, b, M->rc, true, st, &nl));
+  if (E_out) *E_out = nl.E;
+  if (maxdeg_out) *maxdeg_out = nl.maxdeg;
   MLIP_TRY(evaluate_fused_edges(M, d_pos, d_species, b, nl, nullptr, flag, d_energy, d_forces, d_stress, st));
   return check_eval_flags(flag, st);
+}
+
+int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+  return evaluate_fused_exact(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st, nullptr, nullptr);
+}
+
+// ------------------------------------------------ graph-replayed evaluation
+struct EvalGraph {
+  // the layout and outputs the graph serves
+  int64_t n = -1;
+  int nsys = -1;
+  bool forces = false, stress = false, prof = false;
+  std::vector<int64_t> atom_off;
+  std::vector<uint8_t> pbc;
+  // capacities: from the last exact build (edge count with 25 % headroom)
+  int64_t E_exact = -1, Ecap = 0;
+  int maxdeg = 0;
+  NlPlan plan;
+  uint64_t warm_gen = ~0ULL;  // workspace generation of the last eager run of the graph's launches
+  uint64_t graph_gen = ~0ULL;
+  bool broken = false;        // a capture failed: this layout runs eagerly
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+  std::vector<ProfEvent> events;
+  void drop_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    prof_events_free(events);
+    graph_gen = ~0ULL;
+  }
+  ~EvalGraph() {
+    drop_graph();
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+void free_eval_graph(EvalGraph* g) { delete g; }
+
+int evaluate_fused_graph(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                         double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+  if (!M->egraph) M->egraph = new EvalGraph();
+  EvalGraph& G = *M->egraph;
+  Workspace& ws = M->ws;
+  const int64_t n = b.n;
+  const int nsys = b.nsys;
+  const bool prof = prof_timing_on();
+  const bool same = G.n == n && G.nsys == nsys && G.forces == (d_forces != nullptr) &&
+                    G.stress == (d_stress != nullptr) && G.prof == prof && G.atom_off == b.atom_off && G.pbc == b.pbc;
+  if (!same) {
+    G.drop_graph();
+    G.n = n;
+    G.nsys = nsys;
+    G.forces = d_forces != nullptr;
+    G.stress = d_stress != nullptr;
+    G.prof = prof;
+    G.atom_off = b.atom_off;
+    G.pbc = b.pbc;
+    G.E_exact = -1;
+    G.warm_gen = ~0ULL;
+    G.broken = false;
+  }
+  auto exact = [&]() -> int {
+    int64_t E = 0;
+    int md = 0;
+    G.drop_graph();
+    G.warm_gen = ~0ULL;
+    MLIP_TRY(evaluate_fused_exact(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st, &E, &md));
+    G.E_exact = E;
+    G.Ecap = E + E / 4 + 4096;
+    G.maxdeg = md;
+    return MLIP_OK;
+  };
+  if (G.broken || G.E_exact < 0) return exact();
+
+  // graph-owned inputs, outputs and flags (eval [0..1], neighbours [2..5])
+  double *gpos = nullptr, *gE = nullptr, *gF = nullptr, *gS = nullptr;
+  int *gsp = nullptr, *gflags = nullptr;
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  MLIP_TRY(ws.get("eg.pos", 3 * nn, &gpos));
+  MLIP_TRY(ws.get("eg.sp", nn, &gsp));
+  MLIP_TRY(ws.get("eg.E", (size_t)nsys, &gE));
+  MLIP_TRY(ws.get("eg.F", 3 * nn, &gF));
+  MLIP_TRY(ws.get("eg.S", 9 * (size_t)nsys, &gS));
+  MLIP_TRY(ws.get("eg.flags", 8, &gflags));
+  MLIP_TRY(nl_plan(ws, M->stage, b, M->rc, G.maxdeg, G.Ecap, st, &G.plan));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(gpos, d_pos, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(gsp, d_species, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+  auto body = [&](cudaStream_t s) -> int {
+    MLIP_CUDA_TRY(cudaMemsetAsync(gflags, 0, 8 * sizeof(int), s));
+    MLIP_TRY(launch_check_inputs((int)n, gpos, gsp, M->S, gflags, s));
+    NeighborList nl;
+    MLIP_TRY(build_neighbors_nosync(ws, gpos, b, G.plan, s, &nl, gflags + 2));
+    return evaluate_fused_edges(M, gpos, gsp, b, nl, nl.row_ptr + n, gflags, gE, G.forces ? gF : nullptr,
+                                G.stress ? gS : nullptr, s);
+  };
+  bool replayed = false;
+  if (G.exec && G.graph_gen == ws.gen) {
+    MLIP_CUDA_TRY(cudaGraphLaunch(G.exec, st));
+    prof_add_launches(G.kernels);
+    replayed = true;
+  } else if (G.warm_gen == ws.gen) {
+    // capture on the graph's own stream (capture needs a stream other than the legacy one)
+    G.drop_graph();
+    if (!G.cap) MLIP_CUDA_TRY(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+    const long long l0 = prof_launches();
+    cudaError_t ce = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeRelaxed);
+    int rc = MLIP_ERR_CUDA;
+    if (ce == cudaSuccess) {
+      if (prof) prof_capture_begin(&G.events);
+      rc = body(G.cap);
+      if (prof) prof_capture_end();
+      cudaGraph_t g = nullptr;
+      ce = cudaStreamEndCapture(G.cap, &g);
+      G.graph = g;
+    }
+    if (rc == MLIP_OK && ce == cudaSuccess && G.graph)
+      ce = cudaGraphInstantiate(&G.exec, G.graph, 0);
+    if (rc != MLIP_OK || ce != cudaSuccess || !G.exec) {
+      cudaGetLastError();  // a capture that cannot be made: this layout runs without a graph
+      G.drop_graph();
+      G.broken = true;
+      return exact();
+    }
+    G.kernels = prof_launches() - l0;
+    G.graph_gen = ws.gen;
+    MLIP_CUDA_TRY(cudaGraphLaunch(G.exec, st));
+    replayed = true;
+  } else {
+    MLIP_TRY(body(st));
+    G.warm_gen = ws.gen;
+  }
+  int hf[8];
+  MLIP_CUDA_TRY(cudaMemcpyAsync(hf, gflags, sizeof(hf), cudaMemcpyDeviceToHost, st));
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (replayed && prof) prof_graph_collect(G.events);
+  if (hf[0] & 1) { set_error("species index out of range"); return MLIP_ERR_INVALID_ARG; }
+  if (hf[0] & 2) { set_error("non-finite position"); return MLIP_ERR_INVALID_ARG; }
+  if (hf[1]) { set_error("fused kernel: a bounded wait timed out (code %d)", hf[1]); return MLIP_ERR_DEVICE_TIMEOUT; }
+  if (hf[2] > G.maxdeg || hf[5] || hf[3] || hf[4]) return exact();  // out of room (or an unusual list): exactly
+  MLIP_CUDA_TRY(cudaMemcpyAsync(d_energy, gE, sizeof(double) * nsys, cudaMemcpyDeviceToDevice, st));
+  if (d_forces) MLIP_CUDA_TRY(cudaMemcpyAsync(d_forces, gF, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+  if (d_stress) MLIP_CUDA_TRY(cudaMemcpyAsync(d_stress, gS, sizeof(double) * 9 * nsys, cudaMemcpyDeviceToDevice, st));
+  return MLIP_OK;
 }
 
 }  // namespace mlip

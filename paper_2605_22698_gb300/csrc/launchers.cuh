@@ -85,9 +85,19 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
                          double* d_stress, cudaStream_t st);
 // Synchronises st and turns the flags of evaluate_fused_edges into a status.
 int check_eval_flags(const int* flag, cudaStream_t st);
-// The model's form.
+// evaluate_fused for callers that repeat the same batch layout (one system
+// evaluated again and again, MD steps): the evaluation, neighbour build
+// included, runs without host synchronisation and is captured once as a CUDA
+// graph, replayed while the layout, the requested outputs and the workspace
+// stay the same.  The first call of a layout runs evaluate_fused (to learn
+// the edge count), the second runs the same launches eagerly, the third
+// captures.  Results equal evaluate_fused's bit for bit; capacity overflows
+// are detected after the replay and the call is redone by evaluate_fused.
+int evaluate_fused_graph(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                         double* d_energy, double* d_forces, double* d_stress, cudaStream_t st);
+// The model's form; graph: allow evaluate_fused_graph (fused forms).
 int evaluate(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b, double* d_energy,
-             double* d_forces, double* d_stress, cudaStream_t st);
+             double* d_forces, double* d_stress, cudaStream_t st, bool graph = false);
 
 // Velocity Verlet on a batch: systems with active[s] != 0 move with their own
 // time step dt[s] (fs); the others are left as they are.

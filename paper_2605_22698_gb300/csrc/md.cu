@@ -119,12 +119,12 @@ extern "C" int mlip_md_nve(mlip_model* M, double* pos, double* vel, const int32_
   SystemBatch b;
   single_system(b, n, cell, pbc);
   MLIP_TRY(upload_batch(ws, M->stage, b, st));
-  MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe, d_F, nullptr, st));
+  MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe, d_F, nullptr, st, true));
   MLIP_TRY(launch_kinetic(ws, b, d_sp, d_mass, d_vel, d_ke, st));
   for (int64_t s = 0; s < n_steps; ++s) {
     MLIP_TRY(launch_vv_kick(b, d_sp, d_mass, d_dt, nullptr, d_F, d_vel, st));
     MLIP_TRY(launch_vv_drift(b, d_dt, nullptr, d_vel, d_pos, st));
-    MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe + s + 1, d_F, nullptr, st));
+    MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe + s + 1, d_F, nullptr, st, true));
     MLIP_TRY(launch_vv_kick(b, d_sp, d_mass, d_dt, nullptr, d_F, d_vel, st));
     MLIP_TRY(launch_kinetic(ws, b, d_sp, d_mass, d_vel, d_ke + s + 1, st));
   }
@@ -183,12 +183,12 @@ extern "C" int mlip_md_nve_batch(mlip_model* M, int32_t n_systems, const int64_t
   b.cell.assign(cells, cells + 9 * (size_t)n_systems);
   b.pbc.assign(pbc, pbc + 3 * (size_t)n_systems);
   MLIP_TRY(upload_batch(ws, M->stage, b, st));
-  MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe, d_F, nullptr, st));
+  MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe, d_F, nullptr, st, true));
   MLIP_TRY(launch_kinetic(ws, b, d_sp, d_mass, d_vel, d_ke, st));
   for (int64_t s = 0; s < n_steps; ++s) {
     MLIP_TRY(launch_vv_kick(b, d_sp, d_mass, d_dt, nullptr, d_F, d_vel, st));
     MLIP_TRY(launch_vv_drift(b, d_dt, nullptr, d_vel, d_pos, st));
-    MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe + (s + 1) * n_systems, d_F, nullptr, st));
+    MLIP_TRY(evaluate(M, d_pos, d_sp, b, d_pe + (s + 1) * n_systems, d_F, nullptr, st, true));
     MLIP_TRY(launch_vv_kick(b, d_sp, d_mass, d_dt, nullptr, d_F, d_vel, st));
     MLIP_TRY(launch_kinetic(ws, b, d_sp, d_mass, d_vel, d_ke + (s + 1) * n_systems, st));
   }

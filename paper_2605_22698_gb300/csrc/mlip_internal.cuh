@@ -46,6 +46,9 @@ struct Workspace {
   struct Buf { void* p = nullptr; size_t bytes = 0; };
   std::map<std::string, Buf> bufs;
   uint64_t gen = 0;  // bumped whenever a buffer is (re)allocated: device addresses may have changed
+  // the batch tables last uploaded into this workspace (upload_batch skips an identical upload)
+  std::vector<double> batch_sig;
+  uint64_t batch_gen = ~0ULL;
   int get(const std::string& name, size_t bytes, void** out);
   template <class T>
   int get(const std::string& name, size_t count, T** out) {
@@ -77,11 +80,38 @@ struct NeighborList {
   int8_t* shift = nullptr;      // [E * 3]
   int32_t* rev = nullptr;       // [E] index of the reverse edge (j <- i, -S)
   unsigned long long* keys = nullptr;  // [E] sorted (send, S) keys per segment
+  int maxdeg = 0;                      // per-receiver slab capacity the build used
 };
 
 // Builds the sorted list on the device.  Synchronises `st` once to read E.
 int build_neighbors(Workspace& ws, const double* d_pos, int64_t n, const double* cell,
                     const uint8_t* pbc, double rc, bool want_rev, cudaStream_t st, NeighborList* out);
+
+struct EvalGraph;
+void free_eval_graph(EvalGraph* g);
+
+// Neighbour build without host synchronisation (the launches can be captured
+// in a CUDA graph): the grids of a batch are made on the host and uploaded by
+// nl_plan (skipped when the batch, cell and cutoff are those of the last plan);
+// build_neighbors_nosync then only launches device work, with a per-receiver
+// slab of maxdeg entries and edge arrays of capacity Ecap (out->E = Ecap, the
+// count is row_ptr[n] on the device).  Overflows are flagged, never written
+// past: flags[0] = a receiver's count when above maxdeg (its list is cut),
+// flags[1] an image index beyond +-127, flags[2] a missing reverse edge,
+// flags[3] more than Ecap edges (the list is then emptied).
+struct NlPlan {
+  double rc = 0.0;
+  int maxdeg = 0, nbins = 0, nsys = 0;
+  int64_t n = -1, Ecap = 0;
+  void* d_grid0 = nullptr;       // grids as made on the host (nl_setup completes a copy)
+  long long* d_bbox0 = nullptr;  // initial bounding boxes [nsys][6]
+  std::vector<double> sig;       // what the uploaded grids were made from
+};
+struct SystemBatch;
+int nl_plan(Workspace& ws, HostStage& stage, const SystemBatch& b, double rc, int maxdeg, int64_t Ecap,
+            cudaStream_t st, NlPlan* plan);
+int build_neighbors_nosync(Workspace& ws, const double* d_pos, const SystemBatch& b, const NlPlan& plan,
+                           cudaStream_t st, NeighborList* out, int* flags);
 
 // ----------------------------------------------------- batches of systems
 // Independent systems evaluated together as one graph: the disjoint union of
@@ -189,4 +219,5 @@ struct mlip_model {
   int device = 0;
   mlip::Workspace ws;
   mlip::HostStage stage;
+  mlip::EvalGraph* egraph = nullptr;  // cached CUDA graph of the fused evaluation (fused_bf16.cu)
 };

@@ -20,6 +20,7 @@
 //   nl_rev      per edge: binary search of (i, -S) in the sender's segment
 #include <climits>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 
 #include "mlip_internal.cuh"
@@ -328,20 +329,26 @@ __global__ void nl_pairs_warp(int n, const Grid* __restrict__ grids, const int* 
     }
   }
   if (lane == 0) {
-    deg[i] = cnt;
+    deg[i] = min(cnt, maxdeg);  // the slab holds maxdeg; a larger count is flagged and the build redone
     if (cnt > maxdeg) atomicMax(&flags[0], cnt);
   }
   if (__any_sync(0xffffffffu, bad_shift) && lane == 0) atomicOr(&flags[1], 1);
 }
 
 // One warp per receiver; dynamic shared memory: warps_per_block * cap keys.
+// Edges beyond the output capacity Ecap are not written; flags[3] records it.
 __global__ void nl_sort(int n, int cap, const unsigned long long* __restrict__ slab, int maxdeg,
                         const int* __restrict__ row_ptr, unsigned long long* __restrict__ keys,
-                        int* __restrict__ recv, int* __restrict__ send, int8_t* __restrict__ shift) {
+                        int* __restrict__ recv, int* __restrict__ send, int8_t* __restrict__ shift,
+                        long long Ecap, int* __restrict__ flags) {
   extern __shared__ unsigned long long sk[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int i = blockIdx.x * (blockDim.x >> 5) + wib;
   if (i >= n) return;
+  if ((long long)row_ptr[i + 1] > Ecap) {  // uniform over the warp
+    if (lane == 0) atomicOr(&flags[3], 1);
+    return;
+  }
   unsigned long long* s = sk + (size_t)wib * cap;
   const int beg = row_ptr[i], d = row_ptr[i + 1] - beg;
   int m = 1;
@@ -388,6 +395,20 @@ __global__ void nl_rev(const int* __restrict__ E_ptr, const int* __restrict__ ro
     if (lo < row_ptr[j + 1] && keys[lo] == want) rev[e] = lo;
     else { rev[e] = e; atomicOr(&flags[2], 1); }
   }
+}
+
+// One block: if the edge count exceeds the capacity, flag it (flags[3]) and
+// empty the list (every row_ptr entry 0), so that no later kernel indexes
+// beyond the capacity; the host sees the flag and builds again with room.
+__global__ void nl_cap_guard(int n, int* __restrict__ row_ptr, long long Ecap, int* __restrict__ flags) {
+  __shared__ int over;
+  if (threadIdx.x == 0) {
+    over = (long long)row_ptr[n] > Ecap ? 1 : 0;
+    if (over) atomicOr(&flags[3], 1);
+  }
+  __syncthreads();
+  if (!over) return;
+  for (int i = threadIdx.x; i <= n; i += blockDim.x) row_ptr[i] = 0;
 }
 
 // ------------------------------------------------------------ scan
@@ -606,6 +627,7 @@ int build_neighbors_batch(Workspace& ws, const double* d_pos, const SystemBatch&
       continue;
     }
     out->E = E32;
+    out->maxdeg = maxdeg;
     const size_t Ecap = (size_t)std::max(E32, 1);
     MLIP_TRY(ws.get("nl.keys", Ecap, &out->keys));
     MLIP_TRY(ws.get("nl.recv", Ecap, &out->recv));
@@ -618,8 +640,11 @@ int build_neighbors_batch(Workspace& ws, const double* d_pos, const SystemBatch&
       size_t smem = (size_t)wpb * cap * sizeof(unsigned long long);
       if (smem > 48 * 1024)
         MLIP_CUDA_TRY(cudaFuncSetAttribute(nl_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      { MLIP_PROF("nl_sort", st); nl_sort<<<(n + wpb - 1) / wpb, 32 * wpb, smem, st>>>(n, cap, slab, maxdeg, out->row_ptr, out->keys,
-                                                          out->recv, out->send, out->shift); }
+      {
+        MLIP_PROF("nl_sort", st);
+        nl_sort<<<(n + wpb - 1) / wpb, 32 * wpb, smem, st>>>(n, cap, slab, maxdeg, out->row_ptr, out->keys, out->recv,
+                                                             out->send, out->shift, (long long)E32, flags);
+      }
       MLIP_LAUNCH_CHECK();
     }
     if (want_rev) {
@@ -634,6 +659,143 @@ int build_neighbors_batch(Workspace& ws, const double* d_pos, const SystemBatch&
   }
   set_error("neighbors: degree capacity retries exhausted");
   return MLIP_ERR_CAPACITY;
+}
+
+int nl_plan(Workspace& ws, HostStage& stage, const SystemBatch& b, double rc, int maxdeg, int64_t Ecap,
+            cudaStream_t st, NlPlan* plan) {
+  if (!(rc > 0) || maxdeg < 1 || maxdeg > kMaxDegreeLimit || Ecap < 1 || Ecap > (int64_t)INT32_MAX - 64) {
+    set_error("neighbors: bad plan (cutoff, degree capacity or edge capacity)");
+    return MLIP_ERR_INVALID_ARG;
+  }
+  if (b.nsys < 1 || (b.nsys > 1 && !b.d_sys_of && b.n > 0)) { set_error("neighbors: batch not uploaded"); return MLIP_ERR_INVALID_ARG; }
+  const int nsys = b.nsys;
+  std::vector<double> sig;
+  sig.reserve(4 + 13 * (size_t)nsys);
+  sig.push_back(rc);
+  sig.push_back(maxdeg);
+  sig.push_back((double)nsys);
+  for (int s = 0; s <= nsys; ++s) sig.push_back((double)b.atom_off[s]);
+  sig.insert(sig.end(), b.cell.begin(), b.cell.end());
+  for (uint8_t v : b.pbc) sig.push_back(v);
+  void *g0 = nullptr, *bb0 = nullptr;
+  const uint64_t gen0 = ws.gen;
+  MLIP_TRY(ws.get("nlp.grid0", sizeof(Grid) * nsys, &g0));
+  MLIP_TRY(ws.get("nlp.bbox0", sizeof(long long) * 6 * nsys, &bb0));
+  const bool same = sig == plan->sig && ws.gen == gen0 && plan->d_grid0 == g0 && plan->d_bbox0 == bb0;
+  plan->rc = rc;
+  plan->maxdeg = maxdeg;
+  plan->nsys = nsys;
+  plan->n = b.n;
+  plan->Ecap = Ecap;
+  plan->d_grid0 = g0;
+  plan->d_bbox0 = static_cast<long long*>(bb0);
+  if (same) return MLIP_OK;
+  std::vector<Grid> hg(nsys);
+  int64_t total_bins = 0;
+  for (int s = 0; s < nsys; ++s) {
+    MLIP_TRY(make_grid(&b.cell[9 * s], &b.pbc[3 * s], rc, b.atom_off[s + 1] - b.atom_off[s], &hg[s]));
+    hg[s].bin_off = (int)total_bins;
+    hg[s].maxdeg = maxdeg;
+    total_bins += hg[s].max_bins;
+  }
+  if (total_bins > (1LL << 30)) { set_error("neighbors: batch too large (%lld bins)", (long long)total_bins); return MLIP_ERR_INVALID_ARG; }
+  plan->nbins = (int)total_bins;
+  const size_t gbytes = sizeof(Grid) * nsys, bbytes = sizeof(long long) * 6 * nsys;
+  void* hp = nullptr;
+  MLIP_TRY(stage.get(gbytes + bbytes, &hp));
+  std::memcpy(hp, hg.data(), gbytes);
+  long long* hb = reinterpret_cast<long long*>(static_cast<unsigned char*>(hp) + gbytes);
+  for (int s = 0; s < nsys; ++s)
+    for (int k = 0; k < 3; ++k) {
+      hb[6 * s + 2 * k] = LLONG_MAX;
+      hb[6 * s + 2 * k + 1] = LLONG_MIN;
+    }
+  MLIP_CUDA_TRY(cudaMemcpyAsync(g0, hp, gbytes, cudaMemcpyHostToDevice, st));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(bb0, hb, bbytes, cudaMemcpyHostToDevice, st));
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));  // the staging is reused by the next upload
+  plan->sig = sig;
+  return MLIP_OK;
+}
+
+int build_neighbors_nosync(Workspace& ws, const double* d_pos, const SystemBatch& b, const NlPlan& plan,
+                           cudaStream_t st, NeighborList* out, int* flags) {
+  const int n = (int)b.n, nsys = b.nsys, nbins = plan.nbins, maxdeg = plan.maxdeg;
+  if (n != plan.n || nsys != plan.nsys) { set_error("neighbors: plan made for another batch"); return MLIP_ERR_INVALID_ARG; }
+  const int nn = std::max(n, 1);
+  const size_t Ecap = (size_t)plan.Ecap;
+  Grid* dg = nullptr;
+  double* frac = nullptr;
+  float4* loc = nullptr;
+  int *img = nullptr, *bin_of = nullptr, *counts = nullptr, *bin_start = nullptr, *cursor = nullptr,
+      *bin_atoms = nullptr, *deg = nullptr;
+  long long* bbox = nullptr;
+  unsigned long long* slab = nullptr;
+  MLIP_TRY(ws.get("nlg.grid", (size_t)nsys, &dg));
+  MLIP_TRY(ws.get("nlg.frac", (size_t)3 * nn, &frac));
+  MLIP_TRY(ws.get("nlg.img", (size_t)3 * nn, &img));
+  MLIP_TRY(ws.get("nlg.loc", (size_t)nn, &loc));
+  MLIP_TRY(ws.get("nlg.bin_of", (size_t)nn, &bin_of));
+  MLIP_TRY(ws.get("nlg.counts", (size_t)nbins + 1, &counts));
+  MLIP_TRY(ws.get("nlg.bin_start", (size_t)nbins + 1, &bin_start));
+  MLIP_TRY(ws.get("nlg.cursor", (size_t)nbins + 1, &cursor));
+  MLIP_TRY(ws.get("nlg.bin_atoms", (size_t)nn, &bin_atoms));
+  MLIP_TRY(ws.get("nlg.deg", (size_t)nn, &deg));
+  MLIP_TRY(ws.get("nlg.bbox", (size_t)6 * nsys, &bbox));
+  MLIP_TRY(ws.get("nlg.slab", (size_t)nn * maxdeg, &slab));
+  MLIP_TRY(ws.get("nlg.row_ptr", (size_t)nn + 1, &out->row_ptr));
+  MLIP_TRY(ws.get("nlg.keys", Ecap, &out->keys));
+  MLIP_TRY(ws.get("nlg.recv", Ecap, &out->recv));
+  MLIP_TRY(ws.get("nlg.send", Ecap, &out->send));
+  MLIP_TRY(ws.get("nlg.shift", 3 * Ecap, &out->shift));
+  MLIP_TRY(ws.get("nlg.rev", Ecap, &out->rev));
+  out->n = n;
+  out->E = (int64_t)Ecap;
+  out->maxdeg = maxdeg;
+  MLIP_CUDA_TRY(cudaMemcpyAsync(dg, plan.d_grid0, sizeof(Grid) * nsys, cudaMemcpyDeviceToDevice, st));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(bbox, plan.d_bbox0, sizeof(long long) * 6 * nsys, cudaMemcpyDeviceToDevice, st));
+  MLIP_CUDA_TRY(cudaMemsetAsync(counts, 0, ((size_t)nbins + 1) * sizeof(int), st));
+  MLIP_CUDA_TRY(cudaMemsetAsync(cursor, 0, ((size_t)nbins + 1) * sizeof(int), st));
+  const int threads = 128, blocks = (n + threads - 1) / threads;
+  if (n > 0) { MLIP_PROF("nl_frac", st); nl_frac<<<blocks, threads, 0, st>>>(d_pos, n, dg, b.d_sys_of, frac, img, bbox); }
+  { MLIP_PROF("nl_setup", st); nl_setup<<<(nsys + 127) / 128, 128, 0, st>>>(dg, nsys, bbox); }
+  if (n > 0) {
+    MLIP_PROF("nl_bin", st);
+    nl_bin<<<blocks, threads, 0, st>>>(n, dg, b.d_sys_of, d_pos, frac, img, bin_of, counts, loc);
+  }
+  MLIP_LAUNCH_CHECK();
+  MLIP_TRY(exclusive_scan_i32(ws, counts, bin_start, nbins, st, "nlg.bsum1"));
+  if (n > 0) {
+    { MLIP_PROF("nl_scatter", st); nl_scatter<<<blocks, threads, 0, st>>>(n, bin_of, bin_start, cursor, bin_atoms); }
+    {
+      MLIP_PROF("nl_pairs", st);
+      nl_pairs_warp<<<(n + 3) / 4, 128, 0, st>>>(n, dg, b.d_sys_of, d_pos, frac, img, loc, bin_start, bin_atoms, slab,
+                                                 deg, flags);
+    }
+    MLIP_LAUNCH_CHECK();
+  }
+  MLIP_TRY(exclusive_scan_i32(ws, deg, out->row_ptr, n, st, "nlg.bsum2"));
+  { MLIP_PROF("nl_cap_guard", st); nl_cap_guard<<<1, 1024, 0, st>>>(n, out->row_ptr, (long long)Ecap, flags); }
+  MLIP_LAUNCH_CHECK();
+  if (n > 0) {
+    int cap = 32;
+    while (cap < maxdeg) cap <<= 1;
+    const int wpb = 4;
+    const size_t smem = (size_t)wpb * cap * sizeof(unsigned long long);
+    if (smem > 48 * 1024)
+      MLIP_CUDA_TRY(cudaFuncSetAttribute(nl_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      MLIP_PROF("nl_sort", st);
+      nl_sort<<<(n + wpb - 1) / wpb, 32 * wpb, smem, st>>>(n, cap, slab, maxdeg, out->row_ptr, out->keys, out->recv,
+                                                           out->send, out->shift, (long long)Ecap, flags);
+    }
+    {
+      MLIP_PROF("nl_rev", st);
+      nl_rev<<<(int)std::min<size_t>((Ecap + 255) / 256, 4096), 256, 0, st>>>(
+          out->row_ptr + n, out->row_ptr, out->recv, out->send, out->shift, out->keys, out->rev, flags);
+    }
+    MLIP_LAUNCH_CHECK();
+  }
+  return MLIP_OK;
 }
 
 }  // namespace mlip

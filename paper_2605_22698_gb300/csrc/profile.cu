@@ -21,6 +21,7 @@ struct Profiler {
   std::atomic<bool> on{false};
   std::atomic<long long> launches{0};
   std::vector<Rec> recs;
+  std::map<std::string, std::pair<long long, double>> collected;  // graph replays: launches, ms
   std::vector<cudaEvent_t> pool;
   std::vector<const char*> open_names;
   std::vector<cudaEvent_t> open_events;
@@ -43,10 +44,22 @@ Profiler& P() {
 
 }  // namespace
 
+// The graph being captured on this thread (its timing events), if any.
+thread_local std::vector<ProfEvent>* t_capture = nullptr;
+thread_local std::vector<cudaEvent_t> t_capture_open;
+
 void prof_begin(const char* name, cudaStream_t st) {
   Profiler& p = P();
   p.launches.fetch_add(1);
   if (!p.on.load()) return;
+  if (t_capture) {  // an event-record node of the graph, re-recorded at every replay
+    cudaEvent_t a = nullptr;
+    cudaEventCreate(&a);
+    cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
+    t_capture->push_back({name, a, nullptr});
+    t_capture_open.push_back(a);
+    return;
+  }
   std::lock_guard<std::mutex> g(p.mu);
   cudaEvent_t a = p.take();
   cudaEventRecord(a, st);
@@ -57,6 +70,17 @@ void prof_begin(const char* name, cudaStream_t st) {
 void prof_end(cudaStream_t st) {
   Profiler& p = P();
   if (!p.on.load()) return;
+  if (t_capture) {
+    if (t_capture_open.empty()) return;
+    cudaEvent_t b = nullptr;
+    cudaEventCreate(&b);
+    cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
+    const cudaEvent_t a = t_capture_open.back();
+    t_capture_open.pop_back();
+    for (auto it = t_capture->rbegin(); it != t_capture->rend(); ++it)
+      if (it->a == a) { it->b = b; break; }
+    return;
+  }
   std::lock_guard<std::mutex> g(p.mu);
   if (p.open_events.empty()) return;
   cudaEvent_t b = p.take();
@@ -67,6 +91,35 @@ void prof_end(cudaStream_t st) {
 }
 
 bool prof_timing_on() { return P().on.load(); }
+
+void prof_capture_begin(std::vector<ProfEvent>* events) {
+  t_capture = events;
+  t_capture_open.clear();
+}
+void prof_capture_end() {
+  t_capture = nullptr;
+  t_capture_open.clear();
+}
+void prof_graph_collect(const std::vector<ProfEvent>& events) {
+  Profiler& p = P();
+  if (!p.on.load()) return;
+  std::lock_guard<std::mutex> g(p.mu);
+  for (const auto& e : events) {
+    if (!e.a || !e.b) continue;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) != cudaSuccess) { cudaGetLastError(); continue; }
+    auto& x = p.collected[e.name];
+    x.first += 1;
+    x.second += ms;
+  }
+}
+void prof_events_free(std::vector<ProfEvent>& events) {
+  for (auto& e : events) {
+    if (e.a) cudaEventDestroy(e.a);
+    if (e.b) cudaEventDestroy(e.b);
+  }
+  events.clear();
+}
 long long prof_launches() { return P().launches.load(); }
 void prof_add_launches(long long k) { P().launches.fetch_add(k); }
 
@@ -81,6 +134,7 @@ int mlip_profile_enable(int on) {
   std::lock_guard<std::mutex> g(p.mu);
   for (auto& r : p.recs) { p.pool.push_back(r.a); p.pool.push_back(r.b); }
   p.recs.clear();
+  p.collected.clear();
   p.on.store(on != 0);
   return MLIP_OK;
 }
@@ -93,7 +147,7 @@ int mlip_profile_report(char* buf, long long cap, long long* needed) {
   using namespace mlip;
   Profiler& p = P();
   std::lock_guard<std::mutex> g(p.mu);
-  std::map<std::string, std::pair<long long, double>> agg;
+  std::map<std::string, std::pair<long long, double>> agg = p.collected;
   for (auto& r : p.recs) {
     if (cudaEventSynchronize(r.b) != cudaSuccess) { set_error("profile: event sync failed"); return MLIP_ERR_CUDA; }
     float ms = 0.0f;

@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 namespace mlip {
 
 void prof_begin(const char* name, cudaStream_t st);
@@ -16,6 +18,18 @@ bool prof_timing_on();
 // Launch counter: its value, and launches replayed by a CUDA graph.
 long long prof_launches();
 void prof_add_launches(long long k);
+// Timing inside CUDA graphs: while a capture on this thread is bracketed by
+// prof_capture_begin/end (timing on), every timed launch adds a pair of
+// event-record nodes to the graph; after a replay has completed,
+// prof_graph_collect adds the pairs' durations to the report.
+struct ProfEvent {
+  const char* name;
+  cudaEvent_t a, b;
+};
+void prof_capture_begin(std::vector<ProfEvent>* events);
+void prof_capture_end();
+void prof_graph_collect(const std::vector<ProfEvent>& events);
+void prof_events_free(std::vector<ProfEvent>& events);
 
 struct ProfScope {
   cudaStream_t st;
