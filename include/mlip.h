@@ -362,6 +362,9 @@ int mlip_selftest(int which, double* result);
  * mlip_profile_enable(1): from now on every kernel launch records a pair of
  *   CUDA events on its stream (clears earlier records); 0 stops recording.
  *   Do not enable it while a stream is being captured into a CUDA graph.
+ *   Evaluations replayed as CUDA graphs carry their event pairs as event
+ *   nodes and are timed too (the graph is captured again when the timing
+ *   configuration changes).
  * mlip_profile_report: writes a NUL-terminated JSON object
  *   {"kernels": {"<name>": [launches, total_ms], ...}} for the records since
  *   the last enable into buf (at most cap bytes); *needed receives the full
@@ -369,6 +372,9 @@ int mlip_selftest(int which, double* result);
 int mlip_profile_enable(int on);
 long long mlip_launch_count(void);
 int mlip_profile_report(char* buf, long long cap, long long* needed);
+/* mlip_profile_select("name,name"): time only the kernels with these names
+ * (NULL or "": all); launches are still counted. */
+int mlip_profile_select(const char* names);
 
 #ifdef __cplusplus
 }

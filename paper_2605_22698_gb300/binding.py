@@ -82,6 +82,7 @@ def lib():
                                        ctypes.POINTER(mlip_md_report), i32, P]
         L.mlip_selftest.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         L.mlip_profile_enable.argtypes = [i32]
+        L.mlip_profile_select.argtypes = [ctypes.c_char_p]
         L.mlip_launch_count.restype = ctypes.c_longlong
         L.mlip_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
         _lib = L
@@ -329,6 +330,11 @@ def mlip_selftest(which: int) -> float:
 
 def mlip_profile_enable(on: bool) -> None:
     _check(lib().mlip_profile_enable(1 if on else 0))
+
+
+def mlip_profile_select(names) -> None:
+    """Time only the named kernels (an iterable of names; None: all)."""
+    _check(lib().mlip_profile_select(",".join(names).encode() if names else None))
 
 
 def mlip_launch_count() -> int:

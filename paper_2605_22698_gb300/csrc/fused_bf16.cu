@@ -2150,7 +2150,8 @@ struct EvalGraph {
   // the layout and outputs the graph serves
   int64_t n = -1;
   int nsys = -1;
-  bool forces = false, stress = false, prof = false;
+  bool forces = false, stress = false;
+  long long prof = -1;  // timing configuration at the capture
   std::vector<int64_t> atom_off;
   std::vector<uint8_t> pbc;
   // capacities: from the last exact build (edge count with 25 % headroom)
@@ -2189,15 +2190,16 @@ int evaluate_fused_graph(mlip_model* M, const double* d_pos, const int* d_specie
   const int64_t n = b.n;
   const int nsys = b.nsys;
   const bool prof = prof_timing_on();
+  const long long pcfg = prof_config();
   const bool same = G.n == n && G.nsys == nsys && G.forces == (d_forces != nullptr) &&
-                    G.stress == (d_stress != nullptr) && G.prof == prof && G.atom_off == b.atom_off && G.pbc == b.pbc;
+                    G.stress == (d_stress != nullptr) && G.prof == pcfg && G.atom_off == b.atom_off && G.pbc == b.pbc;
   if (!same) {
     G.drop_graph();
     G.n = n;
     G.nsys = nsys;
     G.forces = d_forces != nullptr;
     G.stress = d_stress != nullptr;
-    G.prof = prof;
+    G.prof = pcfg;
     G.atom_off = b.atom_off;
     G.pbc = b.pbc;
     G.E_exact = -1;

@@ -22,6 +22,8 @@ struct Profiler {
   std::atomic<long long> launches{0};
   std::vector<Rec> recs;
   std::map<std::string, std::pair<long long, double>> collected;  // graph replays: launches, ms
+  std::vector<std::string> select;   // kernels to time (empty: all)
+  std::atomic<long long> config{0};  // changes with the timing switch and the selection
   std::vector<cudaEvent_t> pool;
   std::vector<const char*> open_names;
   std::vector<cudaEvent_t> open_events;
@@ -48,23 +50,35 @@ Profiler& P() {
 thread_local std::vector<ProfEvent>* t_capture = nullptr;
 thread_local std::vector<cudaEvent_t> t_capture_open;
 
-void prof_begin(const char* name, cudaStream_t st) {
+static bool selected(Profiler& p, const char* name) {
+  if (p.select.empty()) return true;
+  for (const auto& s : p.select)
+    if (s == name) return true;
+  return false;
+}
+
+bool prof_begin(const char* name, cudaStream_t st) {
   Profiler& p = P();
   p.launches.fetch_add(1);
-  if (!p.on.load()) return;
+  if (!p.on.load()) return false;
+  {
+    std::lock_guard<std::mutex> g(p.mu);
+    if (!selected(p, name)) return false;
+  }
   if (t_capture) {  // an event-record node of the graph, re-recorded at every replay
     cudaEvent_t a = nullptr;
     cudaEventCreate(&a);
     cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
     t_capture->push_back({name, a, nullptr});
     t_capture_open.push_back(a);
-    return;
+    return true;
   }
   std::lock_guard<std::mutex> g(p.mu);
   cudaEvent_t a = p.take();
   cudaEventRecord(a, st);
   p.open_names.push_back(name);
   p.open_events.push_back(a);
+  return true;
 }
 
 void prof_end(cudaStream_t st) {
@@ -91,6 +105,7 @@ void prof_end(cudaStream_t st) {
 }
 
 bool prof_timing_on() { return P().on.load(); }
+long long prof_config() { return P().config.load(); }
 
 void prof_capture_begin(std::vector<ProfEvent>* events) {
   t_capture = events;
@@ -135,7 +150,31 @@ int mlip_profile_enable(int on) {
   for (auto& r : p.recs) { p.pool.push_back(r.a); p.pool.push_back(r.b); }
   p.recs.clear();
   p.collected.clear();
+  if (p.on.load() != (on != 0)) p.config.fetch_add(1);
   p.on.store(on != 0);
+  return MLIP_OK;
+}
+
+// Time only the kernels named in the comma-separated list (NULL or "": all).
+int mlip_profile_select(const char* names) {
+  using namespace mlip;
+  Profiler& p = P();
+  std::lock_guard<std::mutex> g(p.mu);
+  std::vector<std::string> sel;
+  if (names) {
+    std::string cur;
+    for (const char* c = names;; ++c) {
+      if (*c == ',' || *c == 0) {
+        if (!cur.empty()) sel.push_back(cur);
+        cur.clear();
+        if (*c == 0) break;
+      } else if (*c != ' ') {
+        cur.push_back(*c);
+      }
+    }
+  }
+  if (sel != p.select) p.config.fetch_add(1);
+  p.select = sel;
   return MLIP_OK;
 }
 

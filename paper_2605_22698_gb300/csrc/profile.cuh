@@ -10,11 +10,15 @@
 
 namespace mlip {
 
-void prof_begin(const char* name, cudaStream_t st);
+// prof_begin returns whether the launch is timed (then prof_end closes it).
+bool prof_begin(const char* name, cudaStream_t st);
 void prof_end(cudaStream_t st);
 // Whether per-kernel event timing is on (graph capture is skipped then: the
 // timing events need eager launches).
 bool prof_timing_on();
+// Changes whenever timing is switched or the timed kernels are selected anew
+// (a captured graph holds the timing events of the configuration it saw).
+long long prof_config();
 // Launch counter: its value, and launches replayed by a CUDA graph.
 long long prof_launches();
 void prof_add_launches(long long k);
@@ -33,8 +37,11 @@ void prof_events_free(std::vector<ProfEvent>& events);
 
 struct ProfScope {
   cudaStream_t st;
-  ProfScope(const char* name, cudaStream_t s) : st(s) { prof_begin(name, s); }
-  ~ProfScope() { prof_end(st); }
+  bool timed;
+  ProfScope(const char* name, cudaStream_t s) : st(s), timed(prof_begin(name, s)) {}
+  ~ProfScope() {
+    if (timed) prof_end(st);
+  }
 };
 
 }  // namespace mlip
