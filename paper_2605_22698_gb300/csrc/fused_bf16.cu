@@ -1200,7 +1200,11 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int e = tile * kNT + ch * 8 + j;
-          if (e >= E0 && e < E1) atomicAdd(&dz2[(size_t)e * 64 + tid], v[j] * s_dws[kNT + ch * 8 + j]);
+          if (e >= E0 && e < E1) {
+            const float x = v[j] * s_dws[kNT + ch * 8 + j];
+            if (first_group) dz2[(size_t)e * 64 + tid] = x;  // the layer's first group initialises dE/dz2
+            else atomicAdd(&dz2[(size_t)e * 64 + tid], x);
+          }
         }
       }
     }
@@ -1508,7 +1512,11 @@ __global__ void __launch_bounds__(kWSThreads, 1)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int e = tile * kNT + ch * 8 + j;
-          if (e >= E0 && e < E1) atomicAdd(&dz2[(size_t)e * 64 + pt], v[j] * s_dws[kNT + ch * 8 + j]);
+          if (e >= E0 && e < E1) {
+            const float x = v[j] * s_dws[kNT + ch * 8 + j];
+            if (first_group) dz2[(size_t)e * 64 + pt] = x;  // the layer's first group initialises dE/dz2
+            else atomicAdd(&dz2[(size_t)e * 64 + pt], x);
+          }
         }
       }
       tc::fence_before_sync();
@@ -2081,8 +2089,7 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     MLIP_TRY(ws.get("fz.dz2", Ec * 64, &dz2));
     MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, GaA, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(GaB, 0, ND * sizeof(float), st));
-    MLIP_TRY(zero(dY, 16));
-    MLIP_TRY(zero(dr, 1));
+    MLIP_TRY(zero(dY, 16));  // dE/dz2 and dE/dr are initialised by the first group / layer that writes them
     float* absmax = nullptr;  // per system: max |h^t|, max |dE/dm|
     float2* dws2 = nullptr;   // per system: scale of dE/dw and its inverse
     MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)b.nsys, &absmax));
@@ -2090,7 +2097,6 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     for (int t = T - 1; t >= 0; --t) {
       MLIP_TRY(launch_mix_tc(true, n, C, L, GaA, GaB, M->mix_bwd_img[t], M->mix_scale[t], nullptr, Gm, nullptr,
                              u0[t], flag + 1, st));
-      MLIP_TRY(zero(dz2, 64));
       if (!use_bf16) MLIP_TRY(launch_seg_absmax2(b, D * C, h[t], Gm, absmax, st));
       {
         MLIP_PROF("dw_scales", st);
@@ -2101,7 +2107,7 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
                                    M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, GaA, GaB, GbA, GbB, dY,
                                    dz2, use_bf16, b.d_sys_of, dws2, epar, flag + 1, st));
       MLIP_TRY(launch_radial_bwd_tc(H, E, ev, M->W1[t], M->d_radimg + (size_t)t * 32768, M->rad_scale[t],
-                                    (float)M->rc, M->p, dz2, dr, flag + 1, st, Edev));
+                                    (float)M->rc, M->p, dz2, dr, t == T - 1, flag + 1, st, Edev));
       std::swap(GaA, GbA);
       std::swap(GaB, GbB);
     }

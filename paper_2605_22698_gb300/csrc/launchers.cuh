@@ -46,8 +46,9 @@ int launch_seg_absmax2(const SystemBatch& b, int row, const float* a, const floa
 int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float* W1, const uint8_t* w2img,
                      float wsc, float rc, int p, int use_bf16, uint8_t* z2t, int* err, cudaStream_t st,
                      const int* Edev = nullptr);
+// init: write dE/dr instead of adding to it
 int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const uint8_t* w2img, float wsc, float rc,
-                         int p, const float* dz2, float* dr_tot, int* err, cudaStream_t st,
+                         int p, const float* dz2, float* dr_tot, bool init, int* err, cudaStream_t st,
                          const int* Edev = nullptr);
 // Split FP16 image of one layer's W2 for the two kernels above (32 KB) and its
 // power-of-two scale.

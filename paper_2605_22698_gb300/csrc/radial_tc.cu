@@ -250,8 +250,8 @@ __global__ void __launch_bounds__(kRM, kBwdCTAs) radial_bwd_tc(int E, const floa
                                                      const float* __restrict__ W1,
                                                      const uint8_t* __restrict__ w2img, float wsc,
                                                      float rc, int p, const float* __restrict__ dz2,
-                                                     float* __restrict__ dr_tot, const int* __restrict__ Edev,
-                                                     int* __restrict__ err) {
+                                                     float* __restrict__ dr_tot, int init,
+                                                     const int* __restrict__ Edev, int* __restrict__ err) {
   if (Edev) E = *Edev;  // edge count on the device (capacity-sized launch)
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sAh = smem;
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kRM, kBwdCTAs) radial_bwd_tc(int E, const floa
         }
         dr = fmaf(z[k] * silu_grad_f(a), bd, dr);
       }
-      dr_tot[e] += dr;
+      dr_tot[e] = init ? dr : dr_tot[e] + dr;  // the first layer processed initialises dE/dr
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -446,7 +446,8 @@ int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float*
 }
 
 int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const uint8_t* w2img, float wsc, float rc,
-                         int p, const float* dz2, float* dr_tot, int* err, cudaStream_t st, const int* Edev) {
+                         int p, const float* dz2, float* dr_tot, bool init, int* err, cudaStream_t st,
+                         const int* Edev) {
   if (E <= 0) return MLIP_OK;
   if (H != kRH) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
   const int tiles = (E + kRM - 1) / kRM;
@@ -455,7 +456,7 @@ int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const 
   {
     MLIP_PROF("radial_bwd_tc", st);
     radial_bwd_tc<<<radial_grid(kBwdCTAs, tiles), kRM, smem, st>>>(E, ev, W1, w2img, wsc, rc, p, dz2,
-                                                                              dr_tot, Edev, err);
+                                                                              dr_tot, init ? 1 : 0, Edev, err);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
