@@ -52,7 +52,7 @@ def peaks():
 # capture of the same code (profiles/tp_fused_bwd_water3000.md: mean over the
 # four path-group launches of one evaluation), keyed by (workload, precision,
 # kernel).
-NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): 147.7e6}
+NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): 129.7e6}
 
 # FP32 ALU peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
 # lanes x 2 flop (FMA) x 2.07 GHz.
