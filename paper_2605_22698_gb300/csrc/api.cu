@@ -24,16 +24,18 @@ const char* last_error() { return g_err; }
 int Workspace::get(const std::string& name, size_t bytes, void** out) {
   Buf& b = bufs[name];
   if (b.bytes < bytes) {
+    // stream-ordered: the old buffer is released once the work queued before
+    // on this workspace's stream has finished (no device-wide synchronisation,
+    // which would fail while another thread captures a CUDA graph)
     if (b.p) {
-      cudaError_t e = cudaDeviceSynchronize();
-      if (e != cudaSuccess) { set_error("workspace sync: %s", cudaGetErrorString(e)); return MLIP_ERR_CUDA; }
-      cudaFree(b.p);
+      cudaError_t e = cudaFreeAsync(b.p, stream);
+      if (e != cudaSuccess) { set_error("workspace release: %s", cudaGetErrorString(e)); return MLIP_ERR_CUDA; }
       b.p = nullptr;
       b.bytes = 0;
     }
     size_t nb = bytes + bytes / 8;
     ++gen;
-    cudaError_t e = cudaMalloc(&b.p, nb);
+    cudaError_t e = cudaMallocAsync(&b.p, nb, stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
       set_error("workspace '%s': cudaMalloc of %zu bytes failed: %s", name.c_str(), nb, cudaGetErrorString(e));
@@ -47,6 +49,7 @@ int Workspace::get(const std::string& name, size_t bytes, void** out) {
 }
 
 void Workspace::release() {
+  cudaStreamSynchronize(stream);
   for (auto& kv : bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   bufs.clear();
@@ -302,6 +305,7 @@ int mlip_neighbors(const double* pos, int64_t n, const double cell[9], const uin
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   static thread_local Workspace* ws = nullptr;
   if (!ws) ws = new Workspace();
+  WsStream wss(*ws, st);
   const double* d_pos = pos;
   if (!on_device && n > 0) {
     double* dp = nullptr;
@@ -443,6 +447,7 @@ extern "C" int mlip_energy_forces(mlip_model* M, const double* pos, const int32_
   cudaGetDevice(&cur);
   if (cur != M->device) { set_error("model lives on device %d, current device is %d", M->device, cur); return MLIP_ERR_INVALID_ARG; }
   Workspace& ws = M->ws;
+  WsStream wss(ws, st);
   const double* d_pos = pos;
   const int* d_species = species;
   double *d_energy = energy, *d_forces = forces, *d_stress = stress;
@@ -499,6 +504,7 @@ extern "C" int mlip_energy_forces_batch(mlip_model* M, int32_t n_systems, const 
   cudaGetDevice(&cur);
   if (cur != M->device) { set_error("model lives on device %d, current device is %d", M->device, cur); return MLIP_ERR_INVALID_ARG; }
   Workspace& ws = M->ws;
+  WsStream wss(ws, st);
   const double* d_pos = pos;
   const int* d_species = species;
   double *d_energy = energy, *d_forces = forces, *d_stress = stress;

@@ -93,6 +93,7 @@ extern "C" int mlip_md_nve(mlip_model* M, double* pos, double* vel, const int32_
   if ((int)M->masses.size() != M->S) { set_error("the model has no masses (needed for MD)"); return MLIP_ERR_INVALID_ARG; }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Workspace& ws = M->ws;
+  WsStream wss(ws, st);
   double *d_pos = pos, *d_vel = vel, *d_F = nullptr, *d_E = nullptr, *d_mass = nullptr, *d_pe = nullptr, *d_ke = nullptr;
   const int* d_sp = species;
   if (!on_device) {
@@ -153,6 +154,7 @@ extern "C" int mlip_md_nve_batch(mlip_model* M, int32_t n_systems, const int64_t
   if (n > (1LL << 28)) { set_error("atom count %lld out of range", (long long)n); return MLIP_ERR_INVALID_ARG; }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Workspace& ws = M->ws;
+  WsStream wss(ws, st);
   double *d_pos = pos, *d_vel = vel, *d_F = nullptr, *d_mass = nullptr, *d_pe = nullptr, *d_ke = nullptr,
          *d_dt = nullptr;
   const int* d_sp = species;
@@ -257,6 +259,7 @@ extern "C" int mlip_md_nve_skin(mlip_model* M, int32_t n_systems, const int64_t*
   MLIP_CUDA_TRY(cudaStreamWaitEvent(R.st, R.ev, 0));
   cudaStream_t st = R.st;
   Workspace& ws = M->ws;
+  WsStream wss(ws, st);  // restored before the driver's stream is destroyed (declared after R)
   double *d_pos = pos, *d_vel = vel, *d_F = nullptr, *d_mass = nullptr, *d_pe = nullptr, *d_ke = nullptr,
          *d_dt = nullptr;
   const int* d_sp = species;

@@ -46,6 +46,7 @@ struct Workspace {
   struct Buf { void* p = nullptr; size_t bytes = 0; };
   std::map<std::string, Buf> bufs;
   uint64_t gen = 0;  // bumped whenever a buffer is (re)allocated: device addresses may have changed
+  cudaStream_t stream = nullptr;  // the stream of the caller (allocations and releases are ordered on it)
   // the batch tables last uploaded into this workspace (upload_batch skips an identical upload)
   std::vector<double> batch_sig;
   uint64_t batch_gen = ~0ULL;
@@ -59,6 +60,14 @@ struct Workspace {
   }
   void release();
   ~Workspace() { release(); }
+};
+
+// Sets the workspace's stream for the scope of an entry point.
+struct WsStream {
+  Workspace& ws;
+  cudaStream_t prev;
+  WsStream(Workspace& w, cudaStream_t s) : ws(w), prev(w.stream) { w.stream = s; }
+  ~WsStream() { ws.stream = prev; }
 };
 
 // Pinned host staging (grow-only).

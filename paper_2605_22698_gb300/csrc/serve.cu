@@ -258,6 +258,7 @@ int get_arena(mlip_server* S, int which, int64_t n, Arena* a) {
 // the old arena and the new requests' inputs.
 int compact(mlip_server* S, const std::vector<ReqPtr>& cur, size_t n_old_slots, Arena* out) {
   cudaStream_t st = S->st;
+  WsStream wss(S->ws, st);
   const int nslot = (int)cur.size();
   int64_t total = 0, inc_n = 0;
   for (auto& r : cur) total += r->n;
@@ -345,6 +346,7 @@ bool context_broken() { return cudaDeviceSynchronize() != cudaSuccess; }
 int iterate(mlip_server* S, std::vector<ReqPtr>& cur, const Arena& A, std::vector<ReqPtr>& ended) {
   mlip_model* M = S->M;
   cudaStream_t st = S->st;
+  WsStream wss(S->ws, st), wsm(M->ws, st);
   const int nsys = (int)cur.size();
   SystemBatch b;
   b.nsys = nsys;
@@ -390,7 +392,7 @@ int iterate(mlip_server* S, std::vector<ReqPtr>& cur, const Arena& A, std::vecto
     MLIP_TRY(launch_vv_drift(b, d_dt, d_active, A.vel, A.pos, st));
   }
   std::vector<int> slot_rc(nsys, MLIP_OK);
-  int rc = evaluate(M, A.pos, A.species, b, d_E, A.F, d_S, st);
+  int rc = evaluate(M, A.pos, A.species, b, d_E, A.F, d_S, st, true);  // a graph while the membership stays
   if (rc != MLIP_OK) {
     if (context_broken()) return MLIP_ERR_CUDA;
     if (nsys == 1) {
