@@ -52,7 +52,8 @@ __device__ __forceinline__ float silu_grad_f(float x) {
 // evaluated in the algebraically identical factored form
 //   u(x)  = (1-x)^3 sum_{k<p} C(k+2, 2) x^k,   u'(x) = -p(p+1)(p+2)/2 x^{p-1} (1-x)^2,
 // which keeps FP32 accuracy near the cutoff (the expanded form cancels there).
-template <int NB, bool GRAD>
+// (NC functions from n = N0 + 1: e[0..NC) = e_{N0+1..N0+NC}; the full set by default)
+template <int NB, bool GRAD, int N0 = 0, int NC = NB>
 __device__ __forceinline__ void radial_basis(float r, float rc, int p, float* e, float* de) {
   const float x = r / rc;
   float u = 0.0f, du = 0.0f;
@@ -70,15 +71,15 @@ __device__ __forceinline__ void radial_basis(float r, float rc, int p, float* e,
   const float pref = sqrtf(2.0f / rc);
   const float inv_r = 1.0f / r;
 #pragma unroll
-  for (int n = 1; n <= NB; ++n) {
+  for (int n = N0 + 1; n <= N0 + NC; ++n) {
     const float k = (float)n * 3.14159265358979f / rc;
     float sn, cs;
     sincosf(k * r, &sn, &cs);
     const float B = pref * sn * inv_r;
-    e[n - 1] = B * u;
+    e[n - 1 - N0] = B * u;
     if (GRAD) {
       const float dB = pref * (k * cs * inv_r - sn * inv_r * inv_r);
-      de[n - 1] = dB * u + B * du;
+      de[n - 1 - N0] = dB * u + B * du;
     }
   }
 }

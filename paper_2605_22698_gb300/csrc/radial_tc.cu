@@ -3,9 +3,9 @@
 // memory), for H = 64.
 //
 // The radial network of every edge e is  z1 = silu(e_n W1),  z2 = silu(z1 W2)
-// (Bessel basis e_n times the envelope, bias-free layers).  A CTA of 128
-// threads takes 128 edges at a time, one edge per thread (and per tensor-memory
-// lane):
+// (Bessel basis e_n times the envelope, bias-free layers).  A CTA of 256
+// threads takes 128 edges at a time (one tensor-memory lane each), two threads
+// per edge, each with half of the 64 hidden units:
 //   forward  (radial_tc):      z1 in FP32 on the ALUs, each row scaled by a
 //       power of two so that its largest entry lies in [2^13, 2^14) and written
 //       as the FP16 A operand; one MMA chain (M = 128 edges, N = 64, K = 64)
@@ -15,7 +15,8 @@
 //   adjoint  (radial_bwd_tc):  the same product for a2, then
 //       da2 = dE/dz2 * silu'(a2) (scaled per row likewise), a second MMA chain
 //       dz1 = da2 W2^T against W2, and per edge
-//       dE/dr += sum_k dz1_k silu'(a1_k) (W1 de/dr)_k  with a1 recomputed.
+//       dE/dr += sum_k dz1_k silu'(a1_k) (W1 de/dr)_k  (the halves' partial
+//       sums added in a fixed order).
 // The power-of-two row scales keep FP16 away from overflow and underflow and
 // are removed exactly after the product.  Each FP32 operand x is split into
 // x_hi = fp16(x) and x_lo = fp16(x - x_hi) and the product is taken as
@@ -43,9 +44,9 @@ constexpr int kRM = 128;         // edges per MMA tile (M)
 constexpr int kZ2Tile = 32;      // edges per z2 operand tile of the message kernels
 constexpr int kAOpBytes = kRM * kRH * 2;   // 16 KB
 constexpr int kBOpBytes = kRH * kRH * 2;   // 8 KB
-// CTAs per SM: forward 4 x (48 KB shared, 64 tensor-memory columns),
-// adjoint 3 x (64 KB, 128 columns)
-constexpr int kFwdCTAs = 4, kBwdCTAs = 3;
+// CTAs of 256 threads per SM: forward 2 x (48 KB shared, 64 tensor-memory
+// columns), adjoint 2 x (64 KB, 128 columns)
+constexpr int kFwdCTAs = 2, kBwdCTAs = 2;
 
 __device__ __forceinline__ uint16_t f16_bits(float x) {
   const __half v = __float2half_rn(x);
@@ -72,17 +73,24 @@ __device__ __forceinline__ void split16(float x, uint16_t& hi, uint16_t& lo) {
   lo = f16_bits(x - __half2float(h));
 }
 
-// Writes an FP32 row (times sc) as the FP16 A operand row `r` of the hi and lo
-// tiles (canonical layout, K = 64).
-__device__ __forceinline__ void put_row(uint8_t* Ahi, uint8_t* Alo, int r, const float* v, float sc) {
+// Two threads per edge (row r of the tile): half h of the row holds hidden
+// units [32 h, 32 h + 32).  The halves exchange their row maxima (the row's
+// power-of-two scale) and partial sums through shared memory.
+constexpr int kRT = 2 * kRM;  // threads per CTA
+constexpr int kHH = kRH / 2;  // hidden units per thread
+
+// Writes half h of an FP32 row (times sc) into the FP16 hi and lo A operands
+// (canonical layout, K = 64).
+__device__ __forceinline__ void put_half_row(uint8_t* Ahi, uint8_t* Alo, int r, int h, const float* v, float sc) {
 #pragma unroll
-  for (int kg = 0; kg < 8; ++kg) {
+  for (int kq = 0; kq < kHH / 8; ++kq) {
+    const int kg = h * (kHH / 8) + kq;
     uint32_t ph[4], pl[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       uint16_t h0, l0, h1, l1;
-      split16(v[kg * 8 + 2 * q] * sc, h0, l0);
-      split16(v[kg * 8 + 2 * q + 1] * sc, h1, l1);
+      split16(v[kq * 8 + 2 * q] * sc, h0, l0);
+      split16(v[kq * 8 + 2 * q + 1] * sc, h1, l1);
       ph[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
       pl[q] = (uint32_t)l0 | ((uint32_t)l1 << 16);
     }
@@ -109,37 +117,37 @@ __device__ __forceinline__ void mma_tile(uint32_t dtm, const uint8_t* Ahi, const
   tc::mma_commit(bar);
 }
 
-// Reads this thread's 64 accumulator columns (its lane) into v, times inv.
-__device__ __forceinline__ void get_row(uint32_t taddr, float* v, float inv) {
+// Reads this thread's 32 accumulator columns (its lane; columns col0..+31) times inv.
+__device__ __forceinline__ void get_half_row(uint32_t taddr, float* v, float inv) {
 #pragma unroll
-  for (int c = 0; c < kRH / 8; ++c) tc::tmem_ld8(taddr + c * 8, v + c * 8);
+  for (int c = 0; c < kHH / 8; ++c) tc::tmem_ld8(taddr + c * 8, v + c * 8);
   tc::tmem_ld_wait();
 #pragma unroll
-  for (int k = 0; k < kRH; ++k) v[k] *= inv;
+  for (int k = 0; k < kHH; ++k) v[k] *= inv;
 }
 
-__device__ __forceinline__ void z1_row(float r, float rc, int p, const float* sW1, float* z1, float* b, float* db,
-                                       bool grad) {
-  if (grad) radial_basis<8, true>(r, rc, p, b, db);
-  else radial_basis<8, false>(r, rc, p, b, db);
-#pragma unroll
-  for (int k = 0; k < kRH; ++k) {
-    float a = 0.0f;
-#pragma unroll
-    for (int n = 0; n < 8; ++n) a = fmaf(b[n], sW1[n * kRH + k], a);
-    z1[k] = silu_f(a);
-  }
-}
-
-__device__ __forceinline__ float absmax64(const float* v) {
+__device__ __forceinline__ float absmax32(const float* v) {
   float m = 0.0f;
 #pragma unroll
-  for (int k = 0; k < kRH; ++k) m = fmaxf(m, fabsf(v[k]));
+  for (int k = 0; k < kHH; ++k) m = fmaxf(m, fabsf(v[k]));
   return m;
 }
 
+// Half h of the basis functions of edge length r into sb[0..4), sdb[0..4).
+template <bool GRAD>
+__device__ __forceinline__ void basis_half(float r, float rc, int p, int h, float* sb, float* sdb) {
+  float b[4], db[4];
+  if (h == 0) radial_basis<8, GRAD, 0, 4>(r, rc, p, b, db);
+  else radial_basis<8, GRAD, 4, 4>(r, rc, p, b, db);
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    sb[n] = b[n];
+    if (GRAD) sdb[n] = db[n];
+  }
+}
+
 // ------------------------------------------------------------- forward
-__global__ void __launch_bounds__(kRM, kFwdCTAs) radial_tc(int E, int n_tiles32, const float4* __restrict__ ev,
+__global__ void __launch_bounds__(kRT, kFwdCTAs) radial_tc(int E, int n_tiles32, const float4* __restrict__ ev,
                                                  const float* __restrict__ W1, const uint8_t* __restrict__ w2img,
                                                  float wsc, float rc, int p, int use_bf16,
                                                  uint8_t* __restrict__ z2t, const int* __restrict__ Edev,
@@ -154,10 +162,12 @@ __global__ void __launch_bounds__(kRM, kFwdCTAs) radial_tc(int E, int n_tiles32,
   uint8_t* sBh = smem + 2 * kAOpBytes;  // W2^T image: hi then lo
   uint8_t* sBl = sBh + kBOpBytes;
   __shared__ __align__(16) float sW1[8 * kRH];
+  __shared__ float s_b[kRM][8];
+  __shared__ float s_amax[kRT];
   __shared__ __align__(8) uint64_t bar, bar_w;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, rt = tid & (kRM - 1), hf = tid >> 7;
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, kRH);
     tc::tmem_relinquish();
@@ -175,23 +185,37 @@ __global__ void __launch_bounds__(kRM, kFwdCTAs) radial_tc(int E, int n_tiles32,
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16);
+  // tensor-memory lanes of this warp: rows 32 (warp % 4) ..; columns of this half
+  const uint32_t taddr = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + hf * kHH;
   const int n_edges = n_tiles32 * kZ2Tile;  // z2 rows to write (E rounded up to 32)
   uint32_t phase = 0;
-  int issued = 0, done = 0;  // products issued / seen complete (thread 0)
+  int issued = 0, done = 0;  // products issued / phases seen complete (thread 0)
 #pragma unroll 1
   for (int base = blockIdx.x * kRM; base < n_edges; base += gridDim.x * kRM) {
-    const int e = base + tid;
-    float z[kRH], b[8], db[8];
-    float sc = 1.0f;
-    if (e < E) {
-      z1_row(ev[e].w, rc, p, sW1, z, b, db, false);
-      sc = row_scale(absmax64(z));
+    const int e = base + rt;
+    const bool live = e < E;
+    if (live) basis_half<false>(ev[e].w, rc, p, hf, &s_b[rt][4 * hf], nullptr);
+    __syncthreads();
+    float z[kHH];
+    float amax = 0.0f;
+    if (live) {
+#pragma unroll
+      for (int k = 0; k < kHH; ++k) {
+        const int kk = hf * kHH + k;
+        float a = 0.0f;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) a = fmaf(s_b[rt][n], sW1[n * kRH + kk], a);
+        z[k] = silu_f(a);
+      }
+      amax = absmax32(z);
     } else {
 #pragma unroll
-      for (int k = 0; k < kRH; ++k) z[k] = 0.0f;
+      for (int k = 0; k < kHH; ++k) z[k] = 0.0f;
     }
-    put_row(sAh, sAl, tid, z, sc);
+    s_amax[tid] = amax;
+    __syncthreads();
+    const float sc = row_scale(fmaxf(s_amax[rt], s_amax[rt + kRM]));
+    put_half_row(sAh, sAl, rt, hf, z, sc);
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -215,24 +239,25 @@ __global__ void __launch_bounds__(kRM, kFwdCTAs) radial_tc(int E, int n_tiles32,
     }
     phase ^= 1;
     tc::fence_after_sync();
-    get_row(taddr, z, 1.0f / (sc * wsc));
+    get_half_row(taddr, z, 1.0f / (sc * wsc));
     if (e < n_edges) {
       uint8_t* tile = z2t + (size_t)(e / kZ2Tile) * (kZ2Tile * kRH * 2);
       const int t = e % kZ2Tile;
 #pragma unroll
-      for (int kg = 0; kg < 8; ++kg) {
+      for (int kq = 0; kq < kHH / 8; ++kq) {
+        const int kg = hf * (kHH / 8) + kq;
         uint32_t pk[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int k = kg * 8 + 2 * q;
-          const float v0 = e < E ? silu_f(z[k]) : 0.0f, v1 = e < E ? silu_f(z[k + 1]) : 0.0f;
+          const int k = kq * 8 + 2 * q;
+          const float v0 = live ? silu_f(z[k]) : 0.0f, v1 = live ? silu_f(z[k + 1]) : 0.0f;
           pk[q] = (uint32_t)z2_bits(v0, use_bf16) | ((uint32_t)z2_bits(v1, use_bf16) << 16);
         }
         *reinterpret_cast<uint4*>(tile + tc::canon_off(t, kg * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
       }
     }
     tc::fence_before_sync();
-    __syncthreads();  // the next tile rewrites sA and the accumulator
+    __syncthreads();  // the next tile rewrites sA, the basis and the accumulator
     tc::fence_after_sync();
     if (abort_s) break;
   }
@@ -246,7 +271,7 @@ __global__ void __launch_bounds__(kRM, kFwdCTAs) radial_tc(int E, int n_tiles32,
 }
 
 // ------------------------------------------------------------- adjoint
-__global__ void __launch_bounds__(kRM, kBwdCTAs) radial_bwd_tc(int E, const float4* __restrict__ ev,
+__global__ void __launch_bounds__(kRT, kBwdCTAs) radial_bwd_tc(int E, const float4* __restrict__ ev,
                                                      const float* __restrict__ W1,
                                                      const uint8_t* __restrict__ w2img, float wsc,
                                                      float rc, int p, const float* __restrict__ dz2,
@@ -261,10 +286,12 @@ __global__ void __launch_bounds__(kRM, kBwdCTAs) radial_bwd_tc(int E, const floa
   uint8_t* sBnh = sBtl + kBOpBytes;       // W2:   dz1 = da2 W2^T   then hi, lo)
   uint8_t* sBnl = sBnh + kBOpBytes;
   __shared__ __align__(16) float sW1[8 * kRH];
+  __shared__ float s_b[kRM][8], s_db[kRM][8];
+  __shared__ float s_amax[kRT], s_dr[kRT];
   __shared__ __align__(8) uint64_t bar, bar_w;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_s;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, rt = tid & (kRM - 1), hf = tid >> 7;
   if (warp == 0) {
     tc::tmem_alloc(&tmem_base, 2 * kRH);
     tc::tmem_relinquish();
@@ -282,25 +309,37 @@ __global__ void __launch_bounds__(kRM, kBwdCTAs) radial_bwd_tc(int E, const floa
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16);
+  const uint32_t taddr = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + hf * kHH;
   uint32_t phase = 0;
   int issued = 0, done = 0;
 #pragma unroll 1
   for (int base = blockIdx.x * kRM; base < E; base += gridDim.x * kRM) {
-    const int e = base + tid;
+    const int e = base + rt;
     const bool live = e < E;
-    float z[kRH], t[kRH], b[8], db[8];
-    float sc1 = 1.0f;
+    if (live) basis_half<true>(ev[e].w, rc, p, hf, &s_b[rt][4 * hf], &s_db[rt][4 * hf]);
+    __syncthreads();
+    // first layer for this half: pre-activations a1 (kept) and z1 = silu(a1)
+    float a1[kHH], z[kHH];
+    float amax = 0.0f;
     if (live) {
-      z1_row(ev[e].w, rc, p, sW1, z, b, db, true);
-      sc1 = row_scale(absmax64(z));
+#pragma unroll
+      for (int k = 0; k < kHH; ++k) {
+        const int kk = hf * kHH + k;
+        float a = 0.0f;
+#pragma unroll
+        for (int n = 0; n < 8; ++n) a = fmaf(s_b[rt][n], sW1[n * kRH + kk], a);
+        a1[k] = a;
+        z[k] = silu_f(a);
+      }
+      amax = absmax32(z);
     } else {
 #pragma unroll
-      for (int k = 0; k < kRH; ++k) z[k] = 0.0f;
-#pragma unroll
-      for (int n = 0; n < 8; ++n) b[n] = db[n] = 0.0f;
+      for (int k = 0; k < kHH; ++k) a1[k] = z[k] = 0.0f;
     }
-    put_row(sAh, sAl, tid, z, sc1);
+    s_amax[tid] = amax;
+    __syncthreads();
+    const float sc1 = row_scale(fmaxf(s_amax[rt], s_amax[rt + kRM]));
+    put_half_row(sAh, sAl, rt, hf, z, sc1);
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -324,27 +363,26 @@ __global__ void __launch_bounds__(kRM, kBwdCTAs) radial_bwd_tc(int E, const floa
     }
     phase ^= 1;
     tc::fence_after_sync();
-    get_row(taddr, t, 1.0f / (sc1 * wsc));  // a2
+    get_half_row(taddr, z, 1.0f / (sc1 * wsc));  // a2 of this half
     // da2 = dE/dz2 silu'(a2)
     if (live) {
-      const float4* g4 = reinterpret_cast<const float4*>(dz2 + (size_t)e * kRH);
+      const float4* g4 = reinterpret_cast<const float4*>(dz2 + (size_t)e * kRH + hf * kHH);
 #pragma unroll
-      for (int q4 = 0; q4 < kRH / 4; ++q4) {
+      for (int q4 = 0; q4 < kHH / 4; ++q4) {
         const float4 g = g4[q4];
-        t[4 * q4] = g.x * silu_grad_f(t[4 * q4]);
-        t[4 * q4 + 1] = g.y * silu_grad_f(t[4 * q4 + 1]);
-        t[4 * q4 + 2] = g.z * silu_grad_f(t[4 * q4 + 2]);
-        t[4 * q4 + 3] = g.w * silu_grad_f(t[4 * q4 + 3]);
+        z[4 * q4] = g.x * silu_grad_f(z[4 * q4]);
+        z[4 * q4 + 1] = g.y * silu_grad_f(z[4 * q4 + 1]);
+        z[4 * q4 + 2] = g.z * silu_grad_f(z[4 * q4 + 2]);
+        z[4 * q4 + 3] = g.w * silu_grad_f(z[4 * q4 + 3]);
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < kRH; ++k) t[k] = 0.0f;
+      for (int k = 0; k < kHH; ++k) z[k] = 0.0f;
     }
-    const float sc2 = row_scale(absmax64(t));
-    tc::fence_before_sync();
-    __syncthreads();  // every row of the first product is consumed before sA is rewritten
-    tc::fence_after_sync();
-    put_row(sAh, sAl, tid, t, sc2);
+    s_amax[tid] = absmax32(z);
+    __syncthreads();  // both halves' maxima; the first product (complete) no longer reads sA
+    const float sc2 = row_scale(fmaxf(s_amax[rt], s_amax[rt + kRM]));
+    put_half_row(sAh, sAl, rt, hf, z, sc2);
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -365,24 +403,26 @@ __global__ void __launch_bounds__(kRM, kBwdCTAs) radial_bwd_tc(int E, const floa
     }
     phase ^= 1;
     tc::fence_after_sync();
-    get_row(taddr + kRH, z, 1.0f / (sc2 * wsc));  // dz1
+    get_half_row(taddr + kRH, z, 1.0f / (sc2 * wsc));  // dz1 of this half
+    float dr = 0.0f;
     if (live) {
-      float dr = 0.0f;
 #pragma unroll
-      for (int k = 0; k < kRH; ++k) {
-        float a = 0.0f, bd = 0.0f;
+      for (int k = 0; k < kHH; ++k) {
+        const int kk = hf * kHH + k;
+        float bd = 0.0f;
 #pragma unroll
-        for (int n = 0; n < 8; ++n) {
-          a = fmaf(b[n], sW1[n * kRH + k], a);
-          bd = fmaf(sW1[n * kRH + k], db[n], bd);
-        }
-        dr = fmaf(z[k] * silu_grad_f(a), bd, dr);
+        for (int n = 0; n < 8; ++n) bd = fmaf(sW1[n * kRH + kk], s_db[rt][n], bd);
+        dr = fmaf(z[k] * silu_grad_f(a1[k]), bd, dr);
       }
-      dr_tot[e] = init ? dr : dr_tot[e] + dr;  // the first layer processed initialises dE/dr
     }
+    s_dr[tid] = dr;
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    if (hf == 0 && live) {
+      const float d = s_dr[rt] + s_dr[rt + kRM];
+      dr_tot[e] = init ? d : dr_tot[e] + d;  // the first layer processed initialises dE/dr
+    }
     if (abort_s) break;
   }
   if (tid == 0) {
@@ -438,7 +478,7 @@ int launch_radial_tc(int H, int E, int n_tiles32, const float4* ev, const float*
   MLIP_CUDA_TRY(cudaFuncSetAttribute(radial_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   {
     MLIP_PROF("radial_tc", st);
-    radial_tc<<<radial_grid(kFwdCTAs, tiles), kRM, smem, st>>>(E, n_tiles32, ev, W1, w2img, wsc, rc, p,
+    radial_tc<<<radial_grid(kFwdCTAs, tiles), kRT, smem, st>>>(E, n_tiles32, ev, W1, w2img, wsc, rc, p,
                                                                        use_bf16, z2t, Edev, err);
   }
   MLIP_LAUNCH_CHECK();
@@ -455,7 +495,7 @@ int launch_radial_bwd_tc(int H, int E, const float4* ev, const float* W1, const 
   MLIP_CUDA_TRY(cudaFuncSetAttribute(radial_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   {
     MLIP_PROF("radial_bwd_tc", st);
-    radial_bwd_tc<<<radial_grid(kBwdCTAs, tiles), kRM, smem, st>>>(E, ev, W1, w2img, wsc, rc, p, dz2,
+    radial_bwd_tc<<<radial_grid(kBwdCTAs, tiles), kRT, smem, st>>>(E, ev, W1, w2img, wsc, rc, p, dz2,
                                                                               dr_tot, init ? 1 : 0, Edev, err);
   }
   MLIP_LAUNCH_CHECK();
