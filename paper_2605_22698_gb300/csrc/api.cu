@@ -284,7 +284,7 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
 int mlip_model_free(mlip_model* M) {
   if (!M) return MLIP_OK;
   cudaDeviceSynchronize();
-  free_eval_graph(M->egraph);
+  free_eval_graphs(M->egraph);
   M->egraph = nullptr;
   M->ws.release();
   if (M->d_weights) cudaFree(M->d_weights);

@@ -21,6 +21,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <memory>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -2152,6 +2153,7 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
 }
 
 // ------------------------------------------------ graph-replayed evaluation
+// One cached graph per layout, a few per model (a server alternates layouts).
 struct EvalGraph {
   // the layout and outputs the graph serves
   int64_t n = -1;
@@ -2167,7 +2169,7 @@ struct EvalGraph {
   uint64_t warm_gen = ~0ULL;  // workspace generation of the last eager run of the graph's launches
   uint64_t graph_gen = ~0ULL;
   bool broken = false;        // a capture failed: this layout runs eagerly
-  cudaStream_t cap = nullptr;
+  uint64_t last_use = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;
@@ -2180,38 +2182,60 @@ struct EvalGraph {
     prof_events_free(events);
     graph_gen = ~0ULL;
   }
-  ~EvalGraph() {
-    drop_graph();
+  ~EvalGraph() { drop_graph(); }
+};
+
+struct EvalGraphs {
+  std::vector<std::unique_ptr<EvalGraph>> g;
+  cudaStream_t cap = nullptr;  // capture stream (capture needs a stream other than the legacy one)
+  uint64_t clock = 0;
+  ~EvalGraphs() {
+    g.clear();
     if (cap) cudaStreamDestroy(cap);
   }
 };
 
-void free_eval_graph(EvalGraph* g) { delete g; }
+void free_eval_graphs(EvalGraphs* g) { delete g; }
+
+static constexpr size_t kMaxCachedGraphs = 24;
 
 int evaluate_fused_graph(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
                          double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
-  if (!M->egraph) M->egraph = new EvalGraph();
-  EvalGraph& G = *M->egraph;
+  if (!M->egraph) M->egraph = new EvalGraphs();
+  EvalGraphs& GS = *M->egraph;
   Workspace& ws = M->ws;
   const int64_t n = b.n;
   const int nsys = b.nsys;
   const bool prof = prof_timing_on();
   const long long pcfg = prof_config();
-  const bool same = G.n == n && G.nsys == nsys && G.forces == (d_forces != nullptr) &&
-                    G.stress == (d_stress != nullptr) && G.prof == pcfg && G.atom_off == b.atom_off && G.pbc == b.pbc;
-  if (!same) {
-    G.drop_graph();
-    G.n = n;
-    G.nsys = nsys;
-    G.forces = d_forces != nullptr;
-    G.stress = d_stress != nullptr;
-    G.prof = pcfg;
-    G.atom_off = b.atom_off;
-    G.pbc = b.pbc;
-    G.E_exact = -1;
-    G.warm_gen = ~0ULL;
-    G.broken = false;
+  EvalGraph* found = nullptr;
+  for (auto& e : GS.g) {
+    EvalGraph& G = *e;
+    if (G.n == n && G.nsys == nsys && G.forces == (d_forces != nullptr) && G.stress == (d_stress != nullptr) &&
+        G.prof == pcfg && G.atom_off == b.atom_off && G.pbc == b.pbc) {
+      found = &G;
+      break;
+    }
   }
+  if (!found) {
+    if (GS.g.size() >= kMaxCachedGraphs) {  // the least recently used makes room
+      size_t lru = 0;
+      for (size_t k = 1; k < GS.g.size(); ++k)
+        if (GS.g[k]->last_use < GS.g[lru]->last_use) lru = k;
+      GS.g.erase(GS.g.begin() + lru);
+    }
+    GS.g.push_back(std::make_unique<EvalGraph>());
+    found = GS.g.back().get();
+    found->n = n;
+    found->nsys = nsys;
+    found->forces = d_forces != nullptr;
+    found->stress = d_stress != nullptr;
+    found->prof = pcfg;
+    found->atom_off = b.atom_off;
+    found->pbc = b.pbc;
+  }
+  EvalGraph& G = *found;
+  G.last_use = ++GS.clock;
   auto exact = [&]() -> int {
     int64_t E = 0;
     int md = 0;
@@ -2219,8 +2243,8 @@ int evaluate_fused_graph(mlip_model* M, const double* d_pos, const int* d_specie
     G.warm_gen = ~0ULL;
     MLIP_TRY(evaluate_fused_exact(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st, &E, &md));
     G.E_exact = E;
-    G.Ecap = E + E / 4 + 4096;
-    G.maxdeg = md;
+    G.Ecap = std::max<int64_t>(G.Ecap, E + E / 4 + 4096);
+    G.maxdeg = std::max(G.maxdeg, md);
     return MLIP_OK;
   };
   if (G.broken || G.E_exact < 0) return exact();
@@ -2252,18 +2276,17 @@ int evaluate_fused_graph(mlip_model* M, const double* d_pos, const int* d_specie
     prof_add_launches(G.kernels);
     replayed = true;
   } else if (G.warm_gen == ws.gen) {
-    // capture on the graph's own stream (capture needs a stream other than the legacy one)
     G.drop_graph();
-    if (!G.cap) MLIP_CUDA_TRY(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+    if (!GS.cap) MLIP_CUDA_TRY(cudaStreamCreateWithFlags(&GS.cap, cudaStreamNonBlocking));
     const long long l0 = prof_launches();
-    cudaError_t ce = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeRelaxed);
+    cudaError_t ce = cudaStreamBeginCapture(GS.cap, cudaStreamCaptureModeRelaxed);
     int rc = MLIP_ERR_CUDA;
     if (ce == cudaSuccess) {
       if (prof) prof_capture_begin(&G.events);
-      rc = body(G.cap);
+      rc = body(GS.cap);
       if (prof) prof_capture_end();
       cudaGraph_t g = nullptr;
-      ce = cudaStreamEndCapture(G.cap, &g);
+      ce = cudaStreamEndCapture(GS.cap, &g);
       G.graph = g;
     }
     if (rc == MLIP_OK && ce == cudaSuccess && G.graph)

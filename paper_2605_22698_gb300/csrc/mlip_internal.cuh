@@ -96,8 +96,8 @@ struct NeighborList {
 int build_neighbors(Workspace& ws, const double* d_pos, int64_t n, const double* cell,
                     const uint8_t* pbc, double rc, bool want_rev, cudaStream_t st, NeighborList* out);
 
-struct EvalGraph;
-void free_eval_graph(EvalGraph* g);
+struct EvalGraphs;
+void free_eval_graphs(EvalGraphs* g);
 
 // Neighbour build without host synchronisation (the launches can be captured
 // in a CUDA graph): the grids of a batch are made on the host and uploaded by
@@ -228,5 +228,5 @@ struct mlip_model {
   int device = 0;
   mlip::Workspace ws;
   mlip::HostStage stage;
-  mlip::EvalGraph* egraph = nullptr;  // cached CUDA graph of the fused evaluation (fused_bf16.cu)
+  mlip::EvalGraphs* egraph = nullptr;  // cached CUDA graphs of the fused evaluation (fused_bf16.cu)
 };
