@@ -187,13 +187,6 @@ __device__ __forceinline__ void build_lists(int t, bool valid, int par, int* s_l
   }
 }
 
-// (position of edge e within its receiver's segment) & 1, once per evaluation
-__global__ void edge_parity(int E, const int* __restrict__ row_ptr, const int* __restrict__ recv,
-                            uint8_t* __restrict__ par, const int* __restrict__ Edev) {
-  if (Edev) E = *Edev;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
-    par[e] = (uint8_t)((e - row_ptr[recv[e]]) & 1);
-}
 
 template <int L, int MODE, bool BWD>
 struct Split {
@@ -324,9 +317,13 @@ __device__ __forceinline__ void tile_setup(int tile, int E0, int E1, const int* 
 }
 
 // Real harmonics of every edge direction, Y[e][16] (once per evaluation).
-__global__ void edge_sh(int E, const float4* __restrict__ ev, float* __restrict__ Yg, const int* __restrict__ Edev) {
+// Harmonics of every edge, and (par != nullptr) the parity of the edge's
+// position in its receiver's segment (which warp set takes it).
+__global__ void edge_sh(int E, const float4* __restrict__ ev, float* __restrict__ Yg, const int* __restrict__ Edev,
+                        const int* __restrict__ row_ptr, const int* __restrict__ recv, uint8_t* __restrict__ par) {
   if (Edev) E = *Edev;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
+    if (par) par[e] = (uint8_t)((e - row_ptr[recv[e]]) & 1);
     const float4 v = ev[e];
     const float ir = 1.0f / v.w;
     float Y[16];
@@ -2043,12 +2040,7 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
   if (E > 0) {
     {
       MLIP_PROF("edge_sh", st);
-      edge_sh<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, Yg, Edev);
-    }
-    MLIP_LAUNCH_CHECK();
-    {
-      MLIP_PROF("edge_parity", st);
-      edge_parity<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, nl.row_ptr, nl.recv, epar, Edev);
+      edge_sh<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, Yg, Edev, nl.row_ptr, nl.recv, epar);
     }
     MLIP_LAUNCH_CHECK();
   }

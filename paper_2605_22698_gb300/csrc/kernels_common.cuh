@@ -138,6 +138,33 @@ __device__ __forceinline__ float warp_reduce16(const float* v) {
   return u[0];
 }
 
+// FP64 form of warp_reduce16: 16 values summed over the 32 lanes, lane l ends
+// with the total of component l >> 1 (16 additions per lane instead of 80 for
+// 16 separate butterflies; the FP64 pipe is narrow on this part).
+__device__ __forceinline__ double warp_reduce16_f64(const double* v) {
+  const int lane = threadIdx.x & 31;
+  double u[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const bool hi = lane & 16;
+    const double send = hi ? v[k] : v[k + 8];
+    const double keep = hi ? v[k + 8] : v[k];
+    u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int w = 4; w >= 1; w >>= 1) {
+#pragma unroll
+    for (int k = 0; k < w; ++k) {
+      const bool hi = lane & (2 * w);
+      const double send = hi ? u[k] : u[k + w];
+      const double keep = hi ? u[k + w] : u[k];
+      u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * w);
+    }
+  }
+  u[0] += __shfl_xor_sync(0xffffffffu, u[0], 1);
+  return u[0];
+}
+
 // Sum 32 values over the 32 lanes; lane l ends with the total of value l.
 __device__ __forceinline__ float warp_reduce32(const float* v) {
   const int lane = threadIdx.x & 31;

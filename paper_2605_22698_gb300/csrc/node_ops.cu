@@ -97,23 +97,19 @@ __global__ void forces_virial(int n, const int* __restrict__ row_ptr, const int*
         for (int q = 0; q < 3; ++q) v[3 * p + q] += xe[p] * ge[q];
     }
   }
+  // components: 3 forces then 9 virial entries; lane 2c ends with component c
+  double w[16];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int k = 0; k < 3; ++k) w[k] = f[k];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
-    if (vir) {
+  for (int k = 0; k < 9; ++k) w[3 + k] = v[k];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    }
-  }
-  if (lane == 0) {
-    forces[3 * i] = f[0];
-    forces[3 * i + 1] = f[1];
-    forces[3 * i + 2] = f[2];
-    if (vir) {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) vir[(size_t)i * 9 + k] = v[k];
-    }
+  for (int k = 12; k < 16; ++k) w[k] = 0.0;
+  const double tot = warp_reduce16_f64(w);
+  const int comp = lane >> 1;
+  if ((lane & 1) == 0) {
+    if (comp < 3) forces[3 * i + comp] = tot;
+    else if (comp < 12 && vir) vir[(size_t)i * 9 + comp - 3] = tot;
   }
 }
 
