@@ -217,6 +217,20 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
         M->mix_scale.push_back(M->d_mixscale + (size_t)t * (M->L + 1));
       }
     }
+    {  // per-species max |W_emb row|
+      std::vector<float> em(M->S, 0.0f);
+      const float* We = M->host_weights.data() + (M->W_emb - M->d_weights);
+      for (int z = 0; z < M->S; ++z)
+        for (int c = 0; c < M->C; ++c) em[z] = std::max(em[z], std::fabs(We[(size_t)z * M->C + c]));
+      cudaError_t e2 = cudaMalloc(&M->d_embmax, sizeof(float) * std::max(M->S, 1));
+      if (e2 == cudaSuccess) e2 = cudaMemcpy(M->d_embmax, em.data(), sizeof(float) * M->S, cudaMemcpyHostToDevice);
+      if (e2 != cudaSuccess) {
+        cudaGetLastError();
+        set_error("embedding maxima: %s", cudaGetErrorString(e2));
+        mlip_model_free(M);
+        return MLIP_ERR_OOM;
+      }
+    }
     if (M->H == 64) {  // split FP16 images of the radial MLP's hidden layer (the fused form needs H = 64)
       std::vector<uint8_t> imgs, img1;
       for (int t = 0; t < M->T; ++t) {
@@ -292,6 +306,7 @@ int mlip_model_free(mlip_model* M) {
   if (M->d_wmixT) cudaFree(M->d_wmixT);
   if (M->d_miximg) cudaFree(M->d_miximg);
   if (M->d_radimg) cudaFree(M->d_radimg);
+  if (M->d_embmax) cudaFree(M->d_embmax);
   if (M->d_mixscale) cudaFree(M->d_mixscale);
   delete M;
   return MLIP_OK;

@@ -2,8 +2,7 @@
 // of their neighbour graphs), and the per-system reductions that go with it:
 // energies, virials and kinetic energies summed in FP64 over fixed chunks of
 // each system's own atoms (so a system's sums are the same whatever else is in
-// its batch), and the per-system maxima that set the FP16 operand scale of
-// the adjoint.
+// its batch).
 #include <algorithm>
 #include <cmath>
 
@@ -66,34 +65,6 @@ __global__ void seg_finish(int nsys, const int* __restrict__ sys_chunk_off, cons
   out[q] = scale ? acc * scale[s] : acc;
 }
 
-// Per-system max |x| of two node tensors (rows of `row` floats per atom, row
-// a multiple of 4): out[2s] = max |a|, out[2s+1] = max |b| over the system's
-// atoms.  Values are non-negative, so integer atomicMax on their bits is an
-// exact float max.  Grid (chunks, slices): slice y of a chunk takes every
-// gridDim.y-th stride of float4s.
-__global__ void seg_absmax2(const int* __restrict__ chunk, int row, const float* __restrict__ a,
-                            const float* __restrict__ b, float* __restrict__ out) {
-  const int c = blockIdx.x;
-  const int s = chunk[3 * c];
-  const size_t q0 = (size_t)chunk[3 * c + 1] * (row / 4), q1 = (size_t)chunk[3 * c + 2] * (row / 4);
-  const size_t step = (size_t)blockDim.x * gridDim.y;
-  const float4* a4 = reinterpret_cast<const float4*>(a);
-  const float4* b4 = reinterpret_cast<const float4*>(b);
-  float ma = 0.0f, mb = 0.0f;
-  for (size_t q = q0 + (size_t)blockIdx.y * blockDim.x + threadIdx.x; q < q1; q += step) {
-    const float4 u = a4[q], v = b4[q];
-    ma = fmaxf(ma, fmaxf(fmaxf(fabsf(u.x), fabsf(u.y)), fmaxf(fabsf(u.z), fabsf(u.w))));
-    mb = fmaxf(mb, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-    mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMax(reinterpret_cast<int*>(out) + 2 * s, __float_as_int(ma));
-    atomicMax(reinterpret_cast<int*>(out) + 2 * s + 1, __float_as_int(mb));
-  }
-}
 
 double cell_volume3(const double* h) {
   return std::fabs(h[0] * (h[4] * h[8] - h[5] * h[7]) - h[1] * (h[3] * h[8] - h[5] * h[6]) +
@@ -199,18 +170,5 @@ int launch_seg_sum(Workspace& ws, const SystemBatch& b, int K, const double* v, 
   return MLIP_OK;
 }
 
-int launch_seg_absmax2(const SystemBatch& b, int row, const float* a, const float* bb, float* out, cudaStream_t st) {
-  MLIP_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(float) * 2 * b.nsys, st));
-  const int nch = b.nchunk();
-  if (nch > 0) {
-    if (row % 4) { set_error("seg_absmax2: row length %d is not a multiple of 4", row); return MLIP_ERR_INVALID_ARG; }
-    // about four blocks per SM in total, at most one slice per 256 float4s of a chunk
-    const int slices = std::max(1, std::min(kSegChunk * row / 4 / 256, 608 / nch));
-    MLIP_PROF("seg_absmax2", st);
-    seg_absmax2<<<dim3(nch, slices), 256, 0, st>>>(b.d_chunk, row, a, bb, out);
-    MLIP_LAUNCH_CHECK();
-  }
-  return MLIP_OK;
-}
 
 }  // namespace mlip

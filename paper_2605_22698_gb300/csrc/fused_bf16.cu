@@ -2059,7 +2059,13 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     MLIP_LAUNCH_CHECK();
     return MLIP_OK;
   };
-  MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
+  // per layer t and system: max |h^t|, max |dE/dm^t| (FP16 operand scale of the adjoint), accumulated by
+  // the kernels that write those tensors
+  float* absmax = nullptr;
+  MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)T * b.nsys, &absmax));
+  if (!use_bf16) MLIP_CUDA_TRY(cudaMemsetAsync(absmax, 0, sizeof(float) * 2 * T * b.nsys, st));
+  auto amax_h = [&](int t) -> float* { return use_bf16 || t >= T ? nullptr : absmax + 2 * (size_t)t * b.nsys; };
+  MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st, b.d_sys_of, M->d_embmax, amax_h(0)));
   for (int t = 0; t < T; ++t) {
     if (!M->d_radimg) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
     MLIP_TRY(launch_radial_tc(H, E, n_tiles, ev, M->W1[t], M->d_radimg + (size_t)t * 32768, M->rad_scale[t],
@@ -2067,7 +2073,7 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], M->d_w3img + M->w3_layer_off[t],
                              M->w3_goff[t], z2t[t], s, mA, mB, use_bf16, epar, flag + 1, st));
     MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
-                           nullptr, flag + 1, st));
+                           nullptr, flag + 1, st, b.d_sys_of, amax_h(t + 1)));
   }
   MLIP_TRY(launch_energy(ws, b, C, D, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
   if (d_forces || d_stress) {
@@ -2083,17 +2089,15 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, GaA, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(GaB, 0, ND * sizeof(float), st));
     MLIP_TRY(zero(dY, 16));  // dE/dz2 and dE/dr are initialised by the first group / layer that writes them
-    float* absmax = nullptr;  // per system: max |h^t|, max |dE/dm|
-    float2* dws2 = nullptr;   // per system: scale of dE/dw and its inverse
-    MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)b.nsys, &absmax));
+    float2* dws2 = nullptr;  // per system: scale of dE/dw and its inverse
     MLIP_TRY(ws.get("fz.dws2", (size_t)b.nsys, &dws2));
     for (int t = T - 1; t >= 0; --t) {
       MLIP_TRY(launch_mix_tc(true, n, C, L, GaA, GaB, M->mix_bwd_img[t], M->mix_scale[t], nullptr, Gm, nullptr,
-                             u0[t], flag + 1, st));
-      if (!use_bf16) MLIP_TRY(launch_seg_absmax2(b, D * C, h[t], Gm, absmax, st));
+                             u0[t], flag + 1, st, b.d_sys_of, use_bf16 ? nullptr : amax_h(t) + 1));
       {
         MLIP_PROF("dw_scales", st);
-        dw_scales<<<(b.nsys + 127) / 128, 128, 0, st>>>(b.nsys, absmax, s, use_bf16, dws2);
+        dw_scales<<<(b.nsys + 127) / 128, 128, 0, st>>>(b.nsys, absmax + 2 * (size_t)t * b.nsys, s, use_bf16,
+                                                        dws2);
         MLIP_LAUNCH_CHECK();
       }
       MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], Gm,

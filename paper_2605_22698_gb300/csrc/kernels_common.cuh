@@ -138,6 +138,19 @@ __device__ __forceinline__ float warp_reduce16(const float* v) {
   return u[0];
 }
 
+// out[2 sys] = max(out[2 sys], m) for m >= 0 (float bits ordered as integers);
+// one atomic per warp when all its lanes' values belong to one system (sys < 0:
+// nothing to add).  Every lane of the warp calls it.
+__device__ __forceinline__ void warp_sys_max(float* out, int sys, float m) {
+  const int s0 = __shfl_sync(0xffffffffu, sys, 0);
+  if (__all_sync(0xffffffffu, sys == s0)) {
+    const unsigned mm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0 && s0 >= 0) atomicMax(reinterpret_cast<unsigned*>(out) + 2 * s0, mm);
+  } else if (sys >= 0) {
+    atomicMax(reinterpret_cast<unsigned*>(out) + 2 * sys, __float_as_uint(m));
+  }
+}
+
 // FP64 form of warp_reduce16: 16 values summed over the 32 lanes, lane l ends
 // with the total of component l >> 1 (16 additions per lane instead of 80 for
 // 16 separate butterflies; the FP64 pipe is narrow on this part).

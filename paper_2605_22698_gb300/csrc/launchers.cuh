@@ -24,7 +24,10 @@ int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const
                    float* u0, cudaStream_t st);
 int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, const float* WmixT,
                    float* Gm, cudaStream_t st);
-int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st);
+// amax (nullable): per-system max |h| accumulated into amax[2 s] (zeroed by the caller) from the
+// per-species maxima emax[z] = max_c |W_emb[z][c]|
+int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st,
+                 const int* sys_of = nullptr, const float* emax = nullptr, float* amax = nullptr);
 int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st);
 // per-system energies energy[nsys] (FP64)
 int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, const int* species, const float* W_out,
@@ -38,8 +41,6 @@ int launch_forces_virial(Workspace& ws, const SystemBatch& b, const int* row_ptr
 // out[s][k] = sum over the atoms of system s of v[i][k] (K = 1 or 9), times 1/V_s if scale_inv_vol
 int launch_seg_sum(Workspace& ws, const SystemBatch& b, int K, const double* v, bool scale_inv_vol, double* out,
                    cudaStream_t st);
-// out[2s], out[2s+1] = max |a|, max |b| over the rows (row floats per atom) of system s
-int launch_seg_absmax2(const SystemBatch& b, int row, const float* a, const float* bb, float* out, cudaStream_t st);
 
 // Radial MLP of the fused form on the tensor cores (H = 64): z2 operand tiles,
 // and dE/dr accumulated from dE/dz2.  err receives the bounded-wait flags.
@@ -58,9 +59,10 @@ void pack_radial_images(const float* W2, std::vector<uint8_t>& img, float* scale
 // the split weight images of one layer (pack_mix_images), forward or adjoint.
 void pack_mix_images(const float* W, int L, std::vector<uint8_t>& fwd, std::vector<uint8_t>& bwd,
                      std::vector<float>& scale);
+// amax (nullable): per-system max |out| accumulated into amax[2 s] (zeroed by the caller)
 int launch_mix_tc(bool bwd, int n, int C, int L, const float* X, const float* X2, const uint8_t* wimg,
                   const float* wscale, const float* hin, float* out, float* u0, const float* u0_in, int* err,
-                  cudaStream_t st);
+                  cudaStream_t st, const int* sys_of = nullptr, float* amax = nullptr);
 
 int launch_check_inputs(int n, const double* pos, const int* species, int S, int* flag, cudaStream_t st);
 int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::vector<size_t>& group_off);

@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(2 * kMM) mix_tc(int n, int L, const float* __r
                                               const uint8_t* __restrict__ wimg, const float* __restrict__ wscale,
                                               const float* __restrict__ hin, float* __restrict__ out,
                                               float* __restrict__ u0, const float* __restrict__ u0_in,
-                                              int* __restrict__ err) {
+                                              int* __restrict__ err, const int* __restrict__ sys_of,
+                                              float* __restrict__ out_max) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sAh = smem;
   uint8_t* sAl = smem + kMOp;
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(2 * kMM) mix_tc(int n, int L, const float* __r
     float4* o4 = reinterpret_cast<float4*>(out + base);
     const float4* h4 = reinterpret_cast<const float4*>(hin + base);
     float4* u4 = reinterpret_cast<float4*>(u0 + (size_t)nd * kMC);
+    float m = 0.0f;  // max |out| over this thread's half row
 #pragma unroll 1
     for (int c0 = half * HC; c0 < (half + 1) * HC; c0 += 32) {
       float w[32];
@@ -192,19 +194,23 @@ __global__ void __launch_bounds__(2 * kMM) mix_tc(int n, int L, const float* __r
       for (int q = 0; q < 8; ++q) {
         const float4 u = make_float4(w[4 * q] * inv, w[4 * q + 1] * inv, w[4 * q + 2] * inv, w[4 * q + 3] * inv);
         const int i4 = c0 / 4 + q;
+        float4 o;
         if (BWD) {
-          o4[i4] = u;
+          o = u;
         } else {
           const float4 h = h4[i4];
           if (l == 0) {
             u4[i4] = u;
-            o4[i4] = make_float4(h.x + silu_f(u.x), h.y + silu_f(u.y), h.z + silu_f(u.z), h.w + silu_f(u.w));
+            o = make_float4(h.x + silu_f(u.x), h.y + silu_f(u.y), h.z + silu_f(u.z), h.w + silu_f(u.w));
           } else {
-            o4[i4] = make_float4(h.x + u.x, h.y + u.y, h.z + u.z, h.w + u.w);
+            o = make_float4(h.x + u.x, h.y + u.y, h.z + u.z, h.w + u.w);
           }
         }
+        o4[i4] = o;
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fmaxf(fabsf(o.z), fabsf(o.w))));
       }
     }
+    if (out_max) warp_sys_max(out_max, live ? (sys_of ? sys_of[nd] : 0) : -1, m);
   }
   if (tid == 0) {
     if (abort_s && issued) tc::mbar_wait(&bar_mma, 0, 1LL << 20);  // the product in flight, bounded
@@ -250,7 +256,7 @@ void pack_mix_images(const float* W, int L, std::vector<uint8_t>& fwd, std::vect
 
 int launch_mix_tc(bool bwd, int n, int C, int L, const float* X, const float* X2, const uint8_t* wimg,
                   const float* wscale, const float* hin, float* out, float* u0, const float* u0_in, int* err,
-                  cudaStream_t st) {
+                  cudaStream_t st, const int* sys_of, float* amax) {
   if (n <= 0) return MLIP_OK;
   if (C != kMC) { set_error("the fused form needs 128 channels"); return MLIP_ERR_INVALID_ARG; }
   const int smem = 4 * kMOp;
@@ -258,11 +264,13 @@ int launch_mix_tc(bool bwd, int n, int C, int L, const float* X, const float* X2
   if (bwd) {
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     MLIP_PROF("mix_tc_bwd", st);
-    mix_tc<true><<<grid, 2 * kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err);
+    mix_tc<true><<<grid, 2 * kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err, sys_of,
+                                                           amax);
   } else {
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     MLIP_PROF("mix_tc", st);
-    mix_tc<false><<<grid, 2 * kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err);
+    mix_tc<false><<<grid, 2 * kMM, smem, st>>>(n, L, X, X2, wimg, wscale, hin, out, u0, u0_in, err, sys_of,
+                                                           amax);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;

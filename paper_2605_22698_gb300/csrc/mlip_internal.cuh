@@ -217,6 +217,8 @@ struct mlip_model {
   float* d_mixscale = nullptr;
   std::vector<const uint8_t*> mix_fwd_img, mix_bwd_img;
   std::vector<const float*> mix_scale;
+  // fused form: max_c |W_emb[z][c]| per species (the FP16 scale of the first adjoint layer)
+  float* d_embmax = nullptr;
   // fused form: split FP16 images of the radial MLP's W2 per layer (32 KB each)
   // and their power-of-two scales
   uint8_t* d_radimg = nullptr;

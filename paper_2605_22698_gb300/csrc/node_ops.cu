@@ -10,8 +10,11 @@ namespace mlip {
 namespace {
 
 // h^0: scalars from the species embedding, l > 0 zero.
+// amax (nullable): amax[2 s] = max |h| over the atoms of system s, from the
+// per-species maxima emax[z] = max_c |W_emb[z][c]| (one atomic per atom)
 __global__ void embed(int n, int C, int D, const int* __restrict__ species, const float* __restrict__ W_emb,
-                      float* __restrict__ h) {
+                      float* __restrict__ h, const int* __restrict__ sys_of, const float* __restrict__ emax,
+                      float* __restrict__ amax) {
   const size_t total = (size_t)n * D * C;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
     const int c = (int)(k % C);
@@ -19,6 +22,8 @@ __global__ void embed(int n, int C, int D, const int* __restrict__ species, cons
     const int d = (int)(rest % D);
     const int i = (int)(rest / D);
     h[k] = d == 0 ? W_emb[(size_t)species[i] * C + c] : 0.0f;
+    if (amax && c == 0 && d == 0)
+      atomicMax(reinterpret_cast<unsigned*>(amax) + 2 * (sys_of ? sys_of[i] : 0), __float_as_uint(emax[species[i]]));
   }
 }
 
@@ -115,9 +120,15 @@ __global__ void forces_virial(int n, const int* __restrict__ row_ptr, const int*
 
 }  // namespace
 
-int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st) {
+int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st,
+                 const int* sys_of, const float* emax, float* amax) {
   if (n <= 0) return MLIP_OK;
-  { MLIP_PROF("embed", st); embed<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_emb, h); }
+  if (amax && !emax) { set_error("embed: the per-species maxima are missing"); return MLIP_ERR_INVALID_ARG; }
+  {
+    MLIP_PROF("embed", st);
+    embed<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_emb, h,
+                                                                                      sys_of, emax, amax);
+  }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
