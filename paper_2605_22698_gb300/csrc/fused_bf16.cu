@@ -316,9 +316,9 @@ __device__ __forceinline__ void tile_setup(int tile, int E0, int E1, const int* 
   }
 }
 
-// Real harmonics of every edge direction, Y[e][16] (once per evaluation).
-// Harmonics of every edge, and (par != nullptr) the parity of the edge's
-// position in its receiver's segment (which warp set takes it).
+// Real harmonics of every edge direction, Y[e][16] (once per evaluation), and
+// (par != nullptr) the parity of the edge's position in its receiver's
+// segment (which warp set of the message kernels takes it).
 __global__ void edge_sh(int E, const float4* __restrict__ ev, float* __restrict__ Yg, const int* __restrict__ Edev,
                         const int* __restrict__ row_ptr, const int* __restrict__ recv, uint8_t* __restrict__ par) {
   if (Edev) E = *Edev;
