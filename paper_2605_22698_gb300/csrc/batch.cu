@@ -27,29 +27,37 @@ __global__ void fill_sys_of(int n, int nsys, const int* __restrict__ atom_off, i
 constexpr int kSegThreads = 256;
 
 // One block per chunk: partial[c][k] = sum over the chunk's atoms of v[i][k],
-// each thread summing its atoms in order, then a fixed-shape tree.
+// each thread summing its atoms in order, then a fixed tree: a packed warp
+// butterfly (K <= 16 components at once) and the warps' sums in warp order.
 template <int K>
 __global__ void seg_partial(const int* __restrict__ chunk, const double* __restrict__ v,
                             double* __restrict__ partial) {
-  __shared__ double red[kSegThreads];
+  static_assert(K >= 1 && K <= 16, "up to 16 components");
+  __shared__ double wsum[kSegThreads / 32][K];
   const int c = blockIdx.x;
   const int a0 = chunk[3 * c + 1], a1 = chunk[3 * c + 2];
-  double acc[K];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double acc[16];
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 16; ++k) acc[k] = 0.0;
   for (int i = a0 + threadIdx.x; i < a1; i += kSegThreads)
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] += v[(size_t)i * K + k];
-#pragma unroll 1
-  for (int k = 0; k < K; ++k) {
-    red[threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int s = kSegThreads / 2; s > 0; s >>= 1) {
-      if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) partial[(size_t)c * K + k] = red[0];
-    __syncthreads();
+  if constexpr (K == 1) {
+    double t = acc[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) wsum[w][0] = t;
+  } else {
+    const double t = warp_reduce16_f64(acc);  // lane l: component l >> 1
+    if ((lane & 1) == 0 && (lane >> 1) < K) wsum[w][lane >> 1] = t;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < K) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kSegThreads / 32; ++q) t += wsum[q][threadIdx.x];
+    partial[(size_t)c * K + threadIdx.x] = t;
   }
 }
 

@@ -10,33 +10,38 @@ namespace mlip {
 namespace {
 
 // h^0: scalars from the species embedding, l > 0 zero.
+// h[i][d][c] = W_emb[z_i][c] for d = 0, else 0 (float4 stores; C a multiple of 4).
 // amax (nullable): amax[2 s] = max |h| over the atoms of system s, from the
 // per-species maxima emax[z] = max_c |W_emb[z][c]| (one atomic per atom)
 __global__ void embed(int n, int C, int D, const int* __restrict__ species, const float* __restrict__ W_emb,
                       float* __restrict__ h, const int* __restrict__ sys_of, const float* __restrict__ emax,
                       float* __restrict__ amax) {
-  const size_t total = (size_t)n * D * C;
+  const int C4 = C / 4;
+  const size_t total = (size_t)n * D * C4;
+  float4* h4 = reinterpret_cast<float4*>(h);
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(k % C);
-    const size_t rest = k / C;
+    const int c4 = (int)(k % C4);
+    const size_t rest = k / C4;
     const int d = (int)(rest % D);
     const int i = (int)(rest / D);
-    h[k] = d == 0 ? W_emb[(size_t)species[i] * C + c] : 0.0f;
-    if (amax && c == 0 && d == 0)
+    h4[k] = d == 0 ? reinterpret_cast<const float4*>(W_emb + (size_t)species[i] * C)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (amax && c4 == 0 && d == 0)
       atomicMax(reinterpret_cast<unsigned*>(amax) + 2 * (sys_of ? sys_of[i] : 0), __float_as_uint(emax[species[i]]));
   }
 }
 
-// dE/dh^T: W_out[z_i] on the scalars, zero elsewhere.
+// dE/dh^T: W_out[z_i] on the scalars, zero elsewhere (float4 stores).
 __global__ void grad_init(int n, int C, int D, const int* __restrict__ species, const float* __restrict__ W_out,
                           float* __restrict__ G) {
-  const size_t total = (size_t)n * D * C;
+  const int C4 = C / 4;
+  const size_t total = (size_t)n * D * C4;
+  float4* G4 = reinterpret_cast<float4*>(G);
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(k % C);
-    const size_t rest = k / C;
+    const int c4 = (int)(k % C4);
+    const size_t rest = k / C4;
     const int d = (int)(rest % D);
     const int i = (int)(rest / D);
-    G[k] = d == 0 ? W_out[(size_t)species[i] * C + c] : 0.0f;
+    G4[k] = d == 0 ? reinterpret_cast<const float4*>(W_out + (size_t)species[i] * C)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
@@ -124,9 +129,10 @@ int launch_embed(int n, int C, int D, const int* species, const float* W_emb, fl
                  const int* sys_of, const float* emax, float* amax) {
   if (n <= 0) return MLIP_OK;
   if (amax && !emax) { set_error("embed: the per-species maxima are missing"); return MLIP_ERR_INVALID_ARG; }
+  if (C % 4) { set_error("embed: channels must be a multiple of 4"); return MLIP_ERR_INVALID_ARG; }
   {
     MLIP_PROF("embed", st);
-    embed<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_emb, h,
+    embed<<<std::min<int64_t>(((int64_t)n * D * (C / 4) + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_emb, h,
                                                                                       sys_of, emax, amax);
   }
   MLIP_LAUNCH_CHECK();
@@ -135,7 +141,12 @@ int launch_embed(int n, int C, int D, const int* species, const float* W_emb, fl
 
 int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
-  { MLIP_PROF("grad_init", st); grad_init<<<std::min<int64_t>(((int64_t)n * D * C + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_out, G); }
+  if (C % 4) { set_error("grad_init: channels must be a multiple of 4"); return MLIP_ERR_INVALID_ARG; }
+  {
+    MLIP_PROF("grad_init", st);
+    grad_init<<<std::min<int64_t>(((int64_t)n * D * (C / 4) + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species,
+                                                                                               W_out, G);
+  }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
