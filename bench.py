@@ -113,6 +113,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def barrier(world: int) -> None:
+    """Barrier over the ranks (no-op on one rank), with the device idle on both sides."""
+    if world <= 1:
+        return
+    import torch
+    import torch.distributed as dist
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+    dist.barrier()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+
+
+def max_over_ranks(t: float, world: int) -> float:
+    """The largest of the ranks' times (the job's time); t itself on one rank."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([t], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def workload(name: str, rank: int = 0):
     if name == "water3000":
         spec = synth.model_spec("water")
@@ -270,11 +295,7 @@ def run_ours(args, rank, world):
     for _ in range(3):
         step()
     torch.cuda.synchronize()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-    torch.cuda.synchronize()
+    barrier(world)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -289,6 +310,7 @@ def run_ours(args, rank, world):
         step()
         evs[k][1].record(stream)
     torch.cuda.synchronize()
+    barrier(world)
     t_wall = time.perf_counter() - t_wall0
     launches = B.mlip_launch_count() - launches0
     prof = B.mlip_profile_report()
@@ -296,11 +318,7 @@ def run_ours(args, rank, world):
     B.mlip_profile_select(None)
     clocks = sampler.stop() if sampler else None
     ms = [a.elapsed_time(b) for a, b in evs]
-    t_dev = sum(ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
+    t_dev = max_over_ranks(sum(ms) / 1e3, world)
     value = world * s.n * args.steps / t_dev
     # edge count of this structure (for the algorithmic counts)
     r, _, _ = B.mlip_neighbors(np.ascontiguousarray(s.pos), s.cell, s.pbc, spec.rc)
@@ -439,12 +457,15 @@ def run_serve(args, rank, world):
     # phase 1: saturated (every request queued at once)
     reqs, systems = serve_requests(R, 4 + rank, 1.0)
     srv = B.Server(model, bucket_edges=edges)
+    barrier(world)
     l0 = B.mlip_launch_count()
     t0 = time.perf_counter()
     ids = [submit(srv, r, sy) for r, sy in zip(reqs, systems)]
     for i in ids:
         assert srv.wait(i)["status"] == 0
     t_sat = time.perf_counter() - t0
+    barrier(world)
+    t_sat = max_over_ranks(t_sat, world)
     launches = B.mlip_launch_count() - l0
     st_sat = srv.stats()
     srv.close()
@@ -546,15 +567,17 @@ def run_md64(args, rank, world):
     if sampler:
         sampler.start()
         time.sleep(0.3)
+    barrier(world)
     l0 = B.mlip_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     _, _, pe, ke, rep = run(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    barrier(world)
     launches = B.mlip_launch_count() - l0
     clocks = sampler.stop() if sampler else None
-    t = e0.elapsed_time(e1) / 1e3
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
     etot = (pe + ke).cpu().numpy()  # [steps + 1, R]
     drift = (etot[-1] - etot[0]) / np.diff(off) / (args.steps * 0.5e-3)  # eV / atom / ps per replica
     line = {
