@@ -319,12 +319,16 @@ __device__ __forceinline__ void tile_setup(int tile, int E0, int E1, const int* 
 // Real harmonics of every edge direction, Y[e][16] (once per evaluation), and
 // (par != nullptr) the parity of the edge's position in its receiver's
 // segment (which warp set of the message kernels takes it).
-__global__ void edge_sh(int E, const float4* __restrict__ ev, float* __restrict__ Yg, const int* __restrict__ Edev,
-                        const int* __restrict__ row_ptr, const int* __restrict__ recv, uint8_t* __restrict__ par) {
+// The edge vector ev[e] (edge_vector) comes first in the same pass.
+__global__ void edge_sh(int E, const double* __restrict__ pos, const int* __restrict__ send,
+                        const int8_t* __restrict__ shift, CellArg cell, float4* __restrict__ ev,
+                        float* __restrict__ Yg, const int* __restrict__ Edev, const int* __restrict__ row_ptr,
+                        const int* __restrict__ recv, uint8_t* __restrict__ par) {
   if (Edev) E = *Edev;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
     if (par) par[e] = (uint8_t)((e - row_ptr[recv[e]]) & 1);
-    const float4 v = ev[e];
+    const float4 v = edge_vector(e, pos, recv, send, shift, cell);
+    ev[e] = v;
     const float ir = 1.0f / v.w;
     float Y[16];
     sh3<float>(v.x * ir, v.y * ir, v.z * ir, Y);
@@ -2036,11 +2040,11 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
   }
   uint8_t* epar = nullptr;
   MLIP_TRY(ws.get("fz.epar", Ec, &epar));
-  MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st, Edev));
   if (E > 0) {
     {
       MLIP_PROF("edge_sh", st);
-      edge_sh<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, ev, Yg, Edev, nl.row_ptr, nl.recv, epar);
+      edge_sh<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, d_pos, nl.send, nl.shift, ca, ev, Yg, Edev,
+                                                               nl.row_ptr, nl.recv, epar);
     }
     MLIP_LAUNCH_CHECK();
   }

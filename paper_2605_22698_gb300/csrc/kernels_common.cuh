@@ -211,4 +211,24 @@ struct CellArg {
   int any_pbc;
 };
 
+// x_e = (r_j - r_i) + S.h in FP64 (same operation order as the neighbour test),
+// rounded to FP32; (x, y, z, |x|).  Lattice rows of the receiver's system.
+__device__ __forceinline__ float4 edge_vector(int e, const double* __restrict__ pos, const int* __restrict__ recv,
+                                              const int* __restrict__ send, const int8_t* __restrict__ shift,
+                                              const CellArg& cell) {
+  const int i = recv[e], j = send[e];
+  const double S0 = shift[3 * e], S1 = shift[3 * e + 1], S2 = shift[3 * e + 2];
+  const double* h = cell.cells + (cell.sys_of ? 9 * cell.sys_of[i] : 0);
+  double x[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double sk = 0.0;
+    if (cell.any_pbc)
+      sk = __dadd_rn(__dadd_rn(__dmul_rn(S0, h[k]), __dmul_rn(S1, h[3 + k])), __dmul_rn(S2, h[6 + k]));
+    x[k] = __dadd_rn(__dsub_rn(pos[3 * j + k], pos[3 * i + k]), sk);
+  }
+  const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x[0], x[0]), __dmul_rn(x[1], x[1])), __dmul_rn(x[2], x[2])));
+  return make_float4((float)x[0], (float)x[1], (float)x[2], (float)r);
+}
+
 }  // namespace mlip

@@ -27,28 +27,13 @@ namespace {
 constexpr int kNT = 32;  // edges per shared-memory sub-tile
 
 // ------------------------------------------------------------ edge geometry
-// x_e = (r_j - r_i) + S.h in FP64 (same operation order as the neighbour test),
-// rounded to FP32; ev = (x, y, z, |x|).
-// Lattice rows of the receiver's system (cells, sys_of: see SystemBatch).
+// ev[e] = edge_vector(e) (kernels_common.cuh)
 __global__ void edge_geom(int E, const double* __restrict__ pos, const int* __restrict__ recv,
                           const int* __restrict__ send, const int8_t* __restrict__ shift, CellArg cell,
                           float4* __restrict__ ev, const int* __restrict__ Edev) {
   if (Edev) E = *Edev;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x) {
-    const int i = recv[e], j = send[e];
-    const double S0 = shift[3 * e], S1 = shift[3 * e + 1], S2 = shift[3 * e + 2];
-    const double* h = cell.cells + (cell.sys_of ? 9 * cell.sys_of[i] : 0);
-    double x[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      double sk = 0.0;
-      if (cell.any_pbc)
-        sk = __dadd_rn(__dadd_rn(__dmul_rn(S0, h[k]), __dmul_rn(S1, h[3 + k])), __dmul_rn(S2, h[6 + k]));
-      x[k] = __dadd_rn(__dsub_rn(pos[3 * j + k], pos[3 * i + k]), sk);
-    }
-    const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-    ev[e] = make_float4((float)x[0], (float)x[1], (float)x[2], (float)r);
-  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < E; e += gridDim.x * blockDim.x)
+    ev[e] = edge_vector(e, pos, recv, send, shift, cell);
 }
 
 // --------------------------------------------------------------- radial MLP
