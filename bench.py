@@ -472,27 +472,53 @@ def run_serve(args, rank, world):
     ae = atom_evals(reqs)
     sat_rps = R / t_sat
 
-    # phase 2: open loop at 0.7x the saturated request rate
-    lam = 0.7 * sat_rps
-    reqs2, systems2 = serve_requests(R, 5 + rank, lam)
-    srv = B.Server(model, bucket_edges=edges)
+    def open_loop(factor, seed, sampler=None):
+        """Poisson arrivals at factor x the saturated request rate, submitted at
+        their arrival times; the server's statistics and the served atom-steps/s."""
+        lam = factor * sat_rps
+        rq, sy_list = serve_requests(R, seed, lam)
+        srv = B.Server(model, bucket_edges=edges)
+        if sampler:
+            sampler.start()
+        ids = []
+        t0 = time.perf_counter()
+        for r, sy in zip(rq, sy_list):
+            dt = r.t_arrive - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(submit(srv, r, sy))
+        res = [srv.wait(i) for i in ids]
+        t_run = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        clk = sampler.stop() if sampler else None
+        assert all(r["status"] == 0 for r in res)
+        return lam, st, atom_evals(rq) / t_run, clk
+
+    # phase 2: open loop at 0.7x the saturated request rate (the headline latency)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    if sampler:
-        sampler.start()
-    ids2 = []
-    t0 = time.perf_counter()
-    for r, sy in zip(reqs2, systems2):
-        dt = r.t_arrive - (time.perf_counter() - t0)
-        if dt > 0:
-            time.sleep(dt)
-        ids2.append(submit(srv, r, sy))
-    res2 = [srv.wait(i) for i in ids2]
-    t_open = time.perf_counter() - t0
-    st = srv.stats()
+    lam, st, thr2, clocks = open_loop(0.7, 5 + rank, sampler)
+    # phase 3: the other arrival rates of the sweep
+    sweep = []
+    for k, f in enumerate(args.rate_sweep):
+        lam_f, st_f, thr_f, _ = open_loop(f, 6 + k + rank)
+        sweep.append({"factor": f, "rate_per_s": round(lam_f, 2), "p50_ms": round(st_f["p50_ms"], 2),
+                      "p99_ms": round(st_f["p99_ms"], 2), "throughput_atom_steps_per_s": round(thr_f, 1),
+                      "mean_batch_requests": round(st_f["mean_batch_requests"], 2)})
+    # phase 4: single requests on an idle server (latency alone, against the mix's buckets)
+    alone = []
+    srv = B.Server(model, bucket_edges=edges)
+    for n_at, kind in ((50, 0), (200, 0), (2000, 0), (200, 1)):
+        sy = synth.cluster(n_at, 77 + n_at)
+        r = synth.RequestSpec(0.0, n_at, kind, 77 + n_at, 100 if kind else 0)
+        lat = []
+        for _ in range(4):
+            t0 = time.perf_counter()
+            assert srv.wait(submit(srv, r, sy))["status"] == 0
+            lat.append(1e3 * (time.perf_counter() - t0))
+        alone.append({"atoms": n_at, "kind": "nve100" if kind else "energy_forces",
+                      "ms": round(float(np.median(lat[1:])), 2)})
     srv.close()
-    clocks = sampler.stop() if sampler else None
-    assert all(r["status"] == 0 for r in res2)
-    ae2 = atom_evals(reqs2)
     line = {
         "metric": METRIC, "value": round(world * ae / t_sat, 1), "unit": UNIT, "n_gpus": world, "steps": R,
         "warmup": 16, "ms_per_step": round(1e3 * t_sat / R, 4), "higher_is_better": True, "scaling": "weak",
@@ -505,12 +531,14 @@ def run_serve(args, rank, world):
                    "l2": "inputs change every iteration (no flush)"},
         "latency": {"rate_per_s": round(lam, 2), "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
                     "mean_ms": round(st["mean_ms"], 2), "max_ms": round(st["max_ms"], 2),
-                    "throughput_atom_steps_per_s": round(ae2 / t_open, 1),
+                    "throughput_atom_steps_per_s": round(thr2, 1),
                     "buckets_atoms": ["<=100", "101-1000", ">1000"],
                     "bucket_p50_ms": [round(x, 2) for x in st["bucket_p50_ms"]],
                     "bucket_p99_ms": [round(x, 2) for x in st["bucket_p99_ms"]],
                     "mean_batch_atoms": round(st["mean_batch_atoms"], 1),
                     "mean_batch_requests": round(st["mean_batch_requests"], 2)},
+        "rate_sweep": sweep,
+        "alone_ms": alone,
         "saturated": {"requests_per_s": round(sat_rps, 2), "p50_ms": round(st_sat["p50_ms"], 2),
                       "p99_ms": round(st_sat["p99_ms"], 2), "busy_atom_steps_per_s": round(st_sat["atom_steps_per_s"], 1),
                       "iterations": st_sat["iterations"], "mean_batch_atoms": round(st_sat["mean_batch_atoms"], 1)},
@@ -637,6 +665,8 @@ def main():
     ap.add_argument("--precision", default="f16", choices=["fp32", "bf16", "f16"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form beside the headline")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")
+    ap.add_argument("--rate-sweep", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.5, 0.9, 1.1],
+                    help="serve: further open-loop arrival rates, as factors of the saturated rate")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--md-list", default="skin", choices=["skin", "fresh"],

@@ -62,6 +62,9 @@ def lib():
         L.oracle_energy.argtypes = [P, P, P, i64, P, P, P, P]
         L.oracle_energy_dual.argtypes = [P, P, P, i64, P, P, i64, i32, P, P]
         L.oracle_tp.argtypes = [i32, i32, i32, P, P, P, P]
+        L.oracle_sc_paths.argtypes = [i32, P]
+        L.oracle_sym_contract.argtypes = [i32, i32, P, P, P, P]
+        L.oracle_sym_contract_adjoint.argtypes = [i32, i32, P, P, P, P, P]
         L.oracle_vv_nve.argtypes = [P, P, P, P, P, i64, P, P, f64, i64, P, P]
         L.oracle_set_threads.argtypes = [i32]
         L.oracle_max_threads.restype = i32
@@ -147,6 +150,29 @@ def tp(L: int, Lsh: int, h: np.ndarray, v, w: np.ndarray) -> np.ndarray:
     return out
 
 
+def sc_paths(L: int) -> list:
+    """Couplings (l1 <= l2, l3) of the symmetric contraction of order 2."""
+    n = lib().oracle_sc_paths(L, None)
+    out = np.zeros(3 * n, dtype=np.int32)
+    lib().oracle_sc_paths(L, _p(out))
+    return [tuple(int(x) for x in out[3 * k:3 * k + 3]) for k in range(n)]
+
+
+def sym_contract(L: int, A: np.ndarray, w1: np.ndarray, w2: np.ndarray) -> np.ndarray:
+    """Symmetric contraction of one node; A [(L+1)^2, C], w1 [L+1, C], w2 [Q, C]."""
+    A = _c(A, np.float64); w1 = _c(w1, np.float64); w2 = _c(w2, np.float64)
+    out = np.zeros_like(A)
+    lib().oracle_sym_contract(L, A.shape[1], _p(A), _p(w1), _p(w2), _p(out))
+    return out
+
+
+def sym_contract_adjoint(L: int, A, w1, w2, GB) -> np.ndarray:
+    A = _c(A, np.float64); w1 = _c(w1, np.float64); w2 = _c(w2, np.float64); GB = _c(GB, np.float64)
+    out = np.zeros_like(A)
+    lib().oracle_sym_contract_adjoint(L, A.shape[1], _p(A), _p(w1), _p(w2), _p(GB), _p(out))
+    return out
+
+
 def neighbors(pos, cell, pbc, rc: float):
     """Brute-force neighbour list sorted by (recv, send, shift)."""
     pos = _c(pos, np.float64); cell = _c(cell, np.float64); pbc = _c(pbc, np.uint8)
@@ -168,7 +194,7 @@ class Model:
 
     def __init__(self, spec, weights: np.ndarray):
         self.spec = spec
-        self._hyper = _c(spec.hyper, np.int32)
+        self._hyper = _c(np.append(spec.hyper, getattr(spec, "correlation", 0)), np.int32)
         self._dhyper = _c(spec.dhyper, np.float64)
         nw = lib().oracle_num_weights(_p(self._hyper))
         w = _c(weights, np.float32)

@@ -288,6 +288,22 @@ std::vector<Path> build_paths(int L, int Lsh) {
 
 inline int lm(int l, int m) { return l * l + m + l; }
 
+// Couplings of the symmetric contraction of correlation order 2 (MACE's
+// product basis, Sec. "Background and related work" and the MACE table's
+// "correlation 2"): the node's aggregated features A of orders l1 <= l2 <= L
+// are coupled with themselves into order l3 <= L.  Only l1 <= l2 is kept: the
+// (l2, l1) coupling of the same A is the same quadratic form (the real CG
+// tensor of a natural-parity triple is symmetric under swapping its two
+// inputs), and for l1 = l2 natural parity leaves only even l3, whose coupling
+// is symmetric, so no kept path vanishes identically.  Lexicographic in
+// (l1, l2, l3).
+std::vector<Path> build_sc_paths(int L) {
+  std::vector<Path> ps;
+  for (const Path& p : build_paths(L, L))
+    if (p.l1 <= p.l2) ps.push_back(p);
+  return ps;
+}
+
 // --------------------------------------------------------------- radial part
 // Bessel basis B_n(r) = sqrt(2/rc) sin(n pi r / rc) / r and the polynomial
 // envelope u(x) = 1 - (p+1)(p+2)/2 x^p + p(p+2) x^{p+1} - p(p+1)/2 x^{p+2}
@@ -315,21 +331,63 @@ double silu_grad(double x) {
 struct Hyper {
   int S, T, C, L, Lsh, NB, H, p;
   double rc, avg_nb;
+  int corr;  // 0: no symmetric contraction; 2: correlation order 2
 };
 
 struct Model {
   Hyper hp;
   int D, DY, P;
-  std::vector<Path> paths;
+  std::vector<Path> paths, sc;
   std::vector<double> W_emb, W_out, E0;
-  std::vector<std::vector<double>> W1, W2, W3, Wmix;
+  std::vector<std::vector<double>> W1, W2, W3, Wmix, Wsc1, Wsc2;
 };
 
 int64_t num_weights(const Hyper& h, int P) {
+  const int64_t Q = h.corr == 2 ? (int64_t)build_sc_paths(h.L).size() : 0;
+  const int64_t sc = h.corr == 2 ? int64_t(h.S) * (h.L + 1 + Q) * h.C : 0;
   return int64_t(h.S) * h.C +
          int64_t(h.T) * (int64_t(h.NB) * h.H + int64_t(h.H) * h.H + int64_t(h.H) * P * h.C +
-                         int64_t(h.L + 1) * h.C * h.C) +
+                         int64_t(h.L + 1) * h.C * h.C + sc) +
          int64_t(h.S) * h.C + h.S;
+}
+
+// Symmetric contraction of one node (correlation order 2), species z:
+//   B[l3 m3][c] = w1[z][l3][c] A[l3 m3][c]
+//               + sum_q w2[z][q][c] sum C^q[m3][m1][m2] A[l1 m1][c] A[l2 m2][c]
+// over the couplings q = (l1 <= l2, l3) of build_sc_paths.  A, B: [D][C].
+template <class T>
+void sym_contract(const std::vector<Path>& sc, int L, int C, const T* A, const double* w1, const double* w2, T* B) {
+  for (int l = 0; l <= L; ++l)
+    for (int mm = -l; mm <= l; ++mm)
+      for (int c = 0; c < C; ++c) B[(size_t)lm(l, mm) * C + c] = T(w1[(size_t)l * C + c]) * A[(size_t)lm(l, mm) * C + c];
+  for (size_t q = 0; q < sc.size(); ++q) {
+    const Path& pa = sc[q];
+    for (const CGEntry& ce : pa.nz) {
+      const int i3 = lm(pa.l3, ce.m3), i1 = lm(pa.l1, ce.m1), i2 = lm(pa.l2, ce.m2);
+      for (int c = 0; c < C; ++c)
+        B[(size_t)i3 * C + c] += T(w2[q * C + c] * ce.c) * A[(size_t)i1 * C + c] * A[(size_t)i2 * C + c];
+    }
+  }
+}
+
+// Its adjoint: GA = dE/dA from GB = dE/dB at the node's A (the product rule on
+// both factors of every coupling).
+void sym_contract_adjoint(const std::vector<Path>& sc, int L, int C, const double* A, const double* w1,
+                          const double* w2, const double* GB, double* GA) {
+  for (int l = 0; l <= L; ++l)
+    for (int mm = -l; mm <= l; ++mm)
+      for (int c = 0; c < C; ++c) GA[(size_t)lm(l, mm) * C + c] = w1[(size_t)l * C + c] * GB[(size_t)lm(l, mm) * C + c];
+  for (size_t q = 0; q < sc.size(); ++q) {
+    const Path& pa = sc[q];
+    for (const CGEntry& ce : pa.nz) {
+      const int i3 = lm(pa.l3, ce.m3), i1 = lm(pa.l1, ce.m1), i2 = lm(pa.l2, ce.m2);
+      for (int c = 0; c < C; ++c) {
+        const double g = w2[q * C + c] * ce.c * GB[(size_t)i3 * C + c];
+        GA[(size_t)i1 * C + c] += g * A[(size_t)i2 * C + c];
+        GA[(size_t)i2 * C + c] += g * A[(size_t)i1 * C + c];
+      }
+    }
+  }
 }
 
 struct Edge { int i, j; int s0, s1, s2; };
@@ -426,13 +484,15 @@ int brute_neighbors(const double* pos, int n, const double* cell, const uint8_t*
 //   Y_e   = Y_{l2 m2}(x_e / |x_e|),  b_e[n] = B_n(|x_e|) u(|x_e|/rc)
 //   w_e   = W3^T silu(W2^T silu(W1^T b_e))              [P][C], no biases
 //   m_i   = s sum_{e: recv=i} sum_p w_e[p][c] sum C^p[m3][m1][m2] h_j[l1 m1][c] Y_e[l2 m2]
+//   m_i  <- sym_contract(m_i)   (only with correlation order 2)
 //   u_i,l = m_i,l W_l   (u[c'] = sum_c m[c] W_l[c][c'])
 //   h_i,0 += silu(u_i,0);  h_i,l>0 += u_i,l
 // and E = sum_i (sum_c W_out[z_i][c] h_i,0[c] + E0[z_i]).
 template <class T>
 T model_energy(const Model& M, const std::vector<Edge>& edges, const std::vector<int>& row_ptr,
                const T* pos, const int* species, int n, const double* cell, double* atom_e,
-               std::vector<std::vector<double>>* h_store, std::vector<std::vector<double>>* u_store) {
+               std::vector<std::vector<double>>* h_store, std::vector<std::vector<double>>* u_store,
+               std::vector<std::vector<double>>* a_store = nullptr) {
   const Hyper& hp = M.hp;
   const int D = M.D, C = hp.C, H = hp.H, P = M.P, NB = hp.NB, DY = M.DY;
   const double s = 1.0 / hp.avg_nb;
@@ -486,6 +546,15 @@ T model_energy(const Model& M, const std::vector<Edge>& edges, const std::vector
         }
       }
     }
+    if (hp.corr == 2) {
+      if (a_store) { (*a_store)[t].resize(m.size()); for (size_t k = 0; k < m.size(); ++k) (*a_store)[t][k] = val(m[k]); }
+      std::vector<T> B(m.size());
+#pragma omp parallel for schedule(static)
+      for (int i = 0; i < n; ++i)
+        sym_contract<T>(M.sc, hp.L, C, &m[(size_t)i * D * C], &M.Wsc1[t][(size_t)species[i] * (hp.L + 1) * C],
+                        &M.Wsc2[t][(size_t)species[i] * M.sc.size() * C], &B[(size_t)i * D * C]);
+      m.swap(B);
+    }
     const std::vector<double>& Wm = M.Wmix[t];
     std::vector<T> hn(h);
     if (u_store) (*u_store)[t].assign((size_t)n * D * C, 0.0);
@@ -536,8 +605,8 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
   const double s = 1.0 / hp.avg_nb;
   const int E = (int)edges.size();
   std::vector<int> rp = receiver_row_ptr(edges, n);
-  std::vector<std::vector<double>> hs(hp.T + 1), us(hp.T);
-  double energy = model_energy<double>(M, edges, rp, pos, species, n, cell, atom_e, &hs, &us);
+  std::vector<std::vector<double>> hs(hp.T + 1), us(hp.T), as(hp.T);
+  double energy = model_energy<double>(M, edges, rp, pos, species, n, cell, atom_e, &hs, &us, &as);
 
   // sender-sorted index of edges
   std::vector<int> sp(n + 1, 0), sidx(E);
@@ -594,6 +663,15 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
             Gm[((size_t)i * D + ci) * C + c1] = acc;
           }
         }
+    if (hp.corr == 2) {  // through the symmetric contraction: Gm = dE/dB -> dE/dA
+      std::vector<double> GA(Gm.size());
+#pragma omp parallel for schedule(static)
+      for (int i = 0; i < n; ++i)
+        sym_contract_adjoint(M.sc, hp.L, C, &as[t][(size_t)i * D * C], &M.Wsc1[t][(size_t)species[i] * (hp.L + 1) * C],
+                             &M.Wsc2[t][(size_t)species[i] * M.sc.size() * C], &Gm[(size_t)i * D * C],
+                             &GA[(size_t)i * D * C]);
+      Gm.swap(GA);
+    }
     std::vector<double> Gprev(G);  // residual path
     const std::vector<double>& W1 = M.W1[t];
     const std::vector<double>& W2 = M.W2[t];
@@ -771,9 +849,9 @@ int oracle_paths(int L, int Lsh, int* out) {
 double oracle_bessel(int n, double r, double rc) { return bessel<double>(n, r, rc); }
 double oracle_envelope(double x, int p) { return envelope<double>(x, p); }
 
-// hyper = {S, T, C, L, Lsh, NB, H, p}, dhyper = {rc, avg_num_neighbors}
+// hyper = {S, T, C, L, Lsh, NB, H, p, correlation}, dhyper = {rc, avg_num_neighbors}
 int64_t oracle_num_weights(const int* hyper) {
-  Hyper h{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], 0, 0};
+  Hyper h{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], 0, 0, hyper[8]};
   int P = (int)build_paths(h.L, h.Lsh).size();
   return num_weights(h, P);
 }
@@ -781,8 +859,10 @@ int64_t oracle_num_weights(const int* hyper) {
 void* oracle_model_create(const int* hyper, const double* dhyper, const float* wts) {
   Model* M = new Model();
   Hyper& h = M->hp;
-  h = Hyper{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dhyper[0], dhyper[1]};
+  h = Hyper{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dhyper[0], dhyper[1],
+            hyper[8]};
   M->paths = build_paths(h.L, h.Lsh);
+  if (h.corr == 2) M->sc = build_sc_paths(h.L);
   M->P = (int)M->paths.size();
   M->D = (h.L + 1) * (h.L + 1);
   M->DY = (h.Lsh + 1) * (h.Lsh + 1);
@@ -794,11 +874,16 @@ void* oracle_model_create(const int* hyper, const double* dhyper, const float* w
   };
   take(M->W_emb, (size_t)h.S * h.C);
   M->W1.resize(h.T); M->W2.resize(h.T); M->W3.resize(h.T); M->Wmix.resize(h.T);
+  M->Wsc1.resize(h.T); M->Wsc2.resize(h.T);
   for (int t = 0; t < h.T; ++t) {
     take(M->W1[t], (size_t)h.NB * h.H);
     take(M->W2[t], (size_t)h.H * h.H);
     take(M->W3[t], (size_t)h.H * M->P * h.C);
     take(M->Wmix[t], (size_t)(h.L + 1) * h.C * h.C);
+    if (h.corr == 2) {
+      take(M->Wsc1[t], (size_t)h.S * (h.L + 1) * h.C);
+      take(M->Wsc2[t], (size_t)h.S * M->sc.size() * h.C);
+    }
   }
   take(M->W_out, (size_t)h.S * h.C);
   take(M->E0, (size_t)h.S);
@@ -904,6 +989,32 @@ int oracle_tp(int L, int Lsh, int C, const double* h, const double* v, const dou
       int i3 = lm(ps[p].l3, ce.m3), i1 = lm(ps[p].l1, ce.m1), i2 = lm(ps[p].l2, ce.m2);
       for (int c = 0; c < C; ++c) t[(size_t)i3 * C + c] += w[p * C + c] * ce.c * h[(size_t)i1 * C + c] * Y[i2];
     }
+  return 0;
+}
+
+// Couplings (l1, l2, l3) of the symmetric contraction for node order L;
+// returns their count, writes 3 ints each if out != NULL.
+int oracle_sc_paths(int L, int* out) {
+  std::vector<Path> ps = build_sc_paths(L);
+  if (out)
+    for (size_t k = 0; k < ps.size(); ++k) {
+      out[3 * k] = ps[k].l1; out[3 * k + 1] = ps[k].l2; out[3 * k + 2] = ps[k].l3;
+    }
+  return (int)ps.size();
+}
+
+// Symmetric contraction of one node: A, B [(L+1)^2][C]; w1 [L+1][C]; w2 [Q][C].
+int oracle_sym_contract(int L, int C, const double* A, const double* w1, const double* w2, double* B) {
+  std::vector<Path> ps = build_sc_paths(L);
+  sym_contract<double>(ps, L, C, A, w1, w2, B);
+  return 0;
+}
+
+// Its adjoint: GA = dE/dA for GB = dE/dB at A.
+int oracle_sym_contract_adjoint(int L, int C, const double* A, const double* w1, const double* w2,
+                                const double* GB, double* GA) {
+  std::vector<Path> ps = build_sc_paths(L);
+  sym_contract_adjoint(ps, L, C, A, w1, w2, GB, GA);
   return 0;
 }
 

@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import math
 import struct
+import dataclasses
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -79,6 +80,7 @@ class ModelSpec:
     NB: int = 8
     p: int = 6
     masses: tuple = (1.008, 12.011, 14.007, 15.999)
+    correlation: int = 0  # 0: no symmetric contraction; 2: MACE's of correlation order 2
 
     @property
     def hyper(self) -> np.ndarray:
@@ -100,6 +102,18 @@ class ModelSpec:
                         n += 1
         return n
 
+    @property
+    def n_sc_paths(self) -> int:
+        """Number of (l1 <= l2, l3) triples with l1, l2, l3 <= L, triangle rule
+        and even l1 + l2 + l3 (a count, not part of the method's arithmetic)."""
+        n = 0
+        for l1 in range(self.L + 1):
+            for l2 in range(l1, self.L + 1):
+                for l3 in range(self.L + 1):
+                    if abs(l1 - l2) <= l3 <= l1 + l2 and (l1 + l2 + l3) % 2 == 0:
+                        n += 1
+        return n
+
     def weight_shapes(self):
         """(name, shape, fan_in) in the flat parameter order."""
         P = self.n_paths
@@ -111,6 +125,10 @@ class ModelSpec:
                 (f"W3.{t}", (self.H, P, self.C), self.H),
                 (f"Wmix.{t}", (self.L + 1, self.C, self.C), self.C),
             ]
+            if self.correlation == 2:
+                Q = self.n_sc_paths
+                out += [(f"Wsc1.{t}", (self.S, self.L + 1, self.C), 1),
+                        (f"Wsc2.{t}", (self.S, Q, self.C), Q)]
         out += [("W_out", (self.S, self.C), self.C), ("E0", (self.S,), 0)]
         return out
 
@@ -124,6 +142,8 @@ def model_spec(name: str) -> ModelSpec:
     small   1 layer, 16 channels, l <= 2 features, MLP 8 -> 32 -> 32 -> paths*C
     water   2 layers, 128 channels, l <= 2, hidden 64 (Table tbl:nequip_params)
     fcc     2 layers, 128 channels, l <= 3, hidden 64, 2 species
+    <name>_mace  the same with the symmetric contraction of correlation order 2
+                 after every scatter-sum (Table tbl:mace_params: correlation 2)
     """
     if name == "small":
         return ModelSpec(S=4, T=1, C=16, L=2, H=32, avg_nb=20.0)
@@ -131,6 +151,8 @@ def model_spec(name: str) -> ModelSpec:
         return ModelSpec(S=4, T=2, C=128, L=2, H=64, avg_nb=52.0)
     if name == "fcc":
         return ModelSpec(S=2, T=2, C=128, L=3, H=64, avg_nb=42.0, masses=(63.546, 58.693))
+    if name.endswith("_mace"):  # the same model with the symmetric contraction of correlation order 2
+        return dataclasses.replace(model_spec(name[:-5]), correlation=2)
     raise ValueError(name)
 
 
@@ -160,14 +182,18 @@ PARAMS_MAGIC = b"MLIPPRM1"
 
 
 def write_params(path: str, spec: ModelSpec, w: np.ndarray) -> None:
-    """Parameter file: magic, u32 version=1, 8 x i32 hyper, 2 x f64 (rc, avg_nb),
-    S x f64 masses, i64 count, count x f32 weights; little-endian."""
+    """Parameter file: magic, u32 version, 8 x i32 hyper, (version 2: i32
+    correlation), 2 x f64 (rc, avg_nb), S x f64 masses, i64 count, count x f32
+    weights; little-endian.  Version 1 for models without the symmetric
+    contraction."""
     w = np.ascontiguousarray(w, dtype=np.float32)
     assert w.size == spec.n_weights()
     with open(path, "wb") as f:
         f.write(PARAMS_MAGIC)
-        f.write(struct.pack("<I", 1))
+        f.write(struct.pack("<I", 2 if spec.correlation else 1))
         f.write(spec.hyper.astype("<i4").tobytes())
+        if spec.correlation:
+            f.write(struct.pack("<i", spec.correlation))
         f.write(spec.dhyper.astype("<f8").tobytes())
         f.write(np.asarray(spec.masses, dtype="<f8").tobytes())
         f.write(struct.pack("<q", w.size))
