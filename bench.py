@@ -138,7 +138,21 @@ def max_over_ranks(t: float, world: int) -> float:
     return float(tt.item())
 
 
+def _with_contraction(spec_w_s, name):
+    """The same workload on the model with the symmetric contraction of
+    correlation order 2 after every scatter-sum (suffix _mace)."""
+    import dataclasses
+    if not name.endswith("_mace"):
+        return spec_w_s
+    spec, _, *rest = spec_w_s
+    spec = dataclasses.replace(spec, correlation=2)
+    seed = {"water3000": 21, "fcc108k": 31}[name[:-5]]
+    return (spec, synth.make_weights(spec, seed), *rest)
+
+
 def workload(name: str, rank: int = 0):
+    if name.endswith("_mace"):
+        return _with_contraction(workload(name[:-5], rank), name)
     if name == "water3000":
         spec = synth.model_spec("water")
         sysm = synth.water_box(1000, 31.0, seed=2 + 1000 * rank)
@@ -154,6 +168,8 @@ def workload(name: str, rank: int = 0):
 
 def sample_workload(name: str):
     """Bounded CPU sample of the same workload for the oracle baseline."""
+    if name.endswith("_mace"):
+        return _with_contraction(sample_workload(name[:-5]), name)
     if name == "water3000":
         spec = synth.model_spec("water")
         return spec, synth.make_weights(spec, 21), synth.water_box(100, synth.water_side_for(100), seed=2), \
@@ -365,6 +381,20 @@ def run_ours(args, rank, world):
             roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": round(FP32_ALU_TFLOPS, 1),
                     "unit": "TFLOP/s", "frac": None, "traffic": None, "launches": nl,
                     "avg_launch_ms": round(tot_ms / nl, 5)}
+    # the symmetric contraction's kernels (node-wise, bound by memory): algorithmic bytes per launch
+    # over their mean launch time in the shares pass
+    sc_roof = None
+    if "sym_contract" in share_rep:
+        nodes = s.n * (spec.L + 1) ** 2 * spec.C * 4
+        n_in = 2 if args.precision != "fp32" else 1  # the fused form's two partial message buffers
+        sc_roof = {}
+        for kname, nbytes in (("sym_contract", (n_in + 2) * nodes), ("sym_contract_bwd", 3 * nodes)):
+            nl_, tot_ = share_rep.get(kname, (0, 0.0))
+            if nl_:
+                gbs = nbytes / (tot_ / nl_ / 1e3) / 1e9
+                sc_roof[kname] = {"bound": "hbm", "bytes_per_launch": int(nbytes), "avg_launch_ms": round(tot_ / nl_, 5),
+                                  "achieved": round(gbs, 1), "peak": peaks()["hbm_gbs"], "unit": "GB/s",
+                                  "frac": round(gbs / peaks()["hbm_gbs"], 4)}
     share = {}
     tot_all = sum(v[1] for v in share_rep.values()) or 1.0
     for k_, v in sorted(share_rep.items(), key=lambda kv: -kv[1][1])[:8]:
@@ -401,11 +431,13 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32", "f16": "f16 tensor-core MLP + f32"}[args.precision],
         "data": "synthetic", "impl": "ours",
-        "config": {"workload": args.workload, "atoms": s.n, "edges": E_edges, "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}",
+        "config": {"workload": args.workload, "atoms": s.n, "edges": E_edges,
+                   "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}" + (" SC2" if spec.correlation else ""),
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (512 MB write)", "stress": stress},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernel_share": share,
         "kernel_ms_per_step": round(tot_all / n_share, 4),
+        "sym_contract_roofline": sc_roof,
         "timing": "timed steps: CUDA events around the dominant kernel's launches only (graph event nodes); "
                   "kernel_share from 4 steps with every kernel timed, outside the timed region",
         "plain_fp32": plain,
@@ -661,7 +693,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="water3000", choices=["water3000", "fcc108k", "cluster64", "serve", "md64"])
+    ap.add_argument("--workload", default="water3000", choices=["water3000", "fcc108k", "cluster64", "serve", "md64",
+                                                                 "water3000_mace", "fcc108k_mace"])
     ap.add_argument("--precision", default="f16", choices=["fp32", "bf16", "f16"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form beside the headline")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")

@@ -81,12 +81,21 @@ typedef struct mlip_model mlip_model;
 /* Hyperparameters.  Defaults of the paper's tables: n_basis 8 (num_rbf),
  * hidden 64 (radial_net_n_hidden), two hidden layers, envelope p = 6,
  * cutoff 5 A (graph_cutoff_angstrom).  Supported: channels 16 or 128 (BF16
- * form: 128), l_max 2 or 3, sh_l_max 3, n_basis 8, hidden 32 or 64. */
+ * form: 128), l_max 2 or 3, sh_l_max 3, n_basis 8, hidden 32 or 64.
+ * correlation: 0 = the scatter-summed messages go straight to the channel
+ * mix (NequIP-style layer); 2 = MACE's symmetric contraction of correlation
+ * order 2 (MACE table: correlation 2) is applied to them first, per node and
+ * channel with species-dependent weights:
+ *   B[l3 m3] = w1[z][l3] A[l3 m3]
+ *            + sum_q w2[z][q] sum C^q[m3][m1][m2] A[l1 m1] A[l2 m2]
+ * over the Q couplings q = (l1 <= l2 <= l_max, l3 <= l_max), triangle rule,
+ * l1 + l2 + l3 even, lexicographic (Q = 8 for l_max 2, 15 for l_max 3). */
 typedef struct {
   int32_t n_species, n_layers, channels, l_max, sh_l_max, n_basis, hidden, envelope_p;
   double cutoff;             /* rc, A */
   double avg_num_neighbors;  /* message scale s = 1/avg_num_neighbors */
   const double* masses;      /* n_species masses (amu), host; may be NULL (no MD) */
+  int32_t correlation;       /* 0 or 2 (see above) */
 } mlip_model_desc;
 
 /* Thread-local text of the last error (never NULL). */
@@ -94,8 +103,8 @@ const char* mlip_last_error(void);
 int mlip_version(void);
 
 /* Number of float32 weights a model with this description takes, in the order
- *   W_emb [S][C]; per layer: W1 [8][H], W2 [H][H], W3 [H][P][C], W_mix [L+1][C][C];
- *   W_out [S][C]; E0 [S]
+ *   W_emb [S][C]; per layer: W1 [8][H], W2 [H][H], W3 [H][P][C], W_mix [L+1][C][C]
+ *   (with correlation 2 also w1 [S][L+1][C], w2 [S][Q][C]); W_out [S][C]; E0 [S]
  * (P = number of coupling paths (l1 <= L, l2 <= 3, l3 <= L, triangle rule,
  * l1 + l2 + l3 even, lexicographic).  Errors: MLIP_ERR_INVALID_ARG. */
 int mlip_model_num_weights(const mlip_model_desc* desc, int64_t* n_weights);
@@ -106,8 +115,9 @@ int mlip_model_num_weights(const mlip_model_desc* desc, int64_t* n_weights);
 int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t n_weights,
                       int precision, mlip_model** out);
 
-/* Load a parameter file: "MLIPPRM1", u32 version 1, 8 x i32 (S, T, C, L, Lsh,
- * NB, H, p), 2 x f64 (rc, avg_num_neighbors), S x f64 masses, i64 count,
+/* Load a parameter file: "MLIPPRM1", u32 version (1 or 2), 8 x i32 (S, T, C,
+ * L, Lsh, NB, H, p), version 2 only: i32 correlation, 2 x f64 (rc,
+ * avg_num_neighbors), S x f64 masses, i64 count,
  * count x f32 weights; little-endian.  Errors as mlip_model_create plus
  * MLIP_ERR_NOT_FOUND (unreadable file). */
 int mlip_model_load(const char* params_path, int precision, mlip_model** out);

@@ -43,7 +43,8 @@ class mlip_model_desc(ctypes.Structure):
     _fields_ = [("n_species", ctypes.c_int32), ("n_layers", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("l_max", ctypes.c_int32), ("sh_l_max", ctypes.c_int32), ("n_basis", ctypes.c_int32),
                 ("hidden", ctypes.c_int32), ("envelope_p", ctypes.c_int32), ("cutoff", ctypes.c_double),
-                ("avg_num_neighbors", ctypes.c_double), ("masses", ctypes.POINTER(ctypes.c_double))]
+                ("avg_num_neighbors", ctypes.c_double), ("masses", ctypes.POINTER(ctypes.c_double)),
+                ("correlation", ctypes.c_int32)]
 
 
 class mlip_md_options(ctypes.Structure):
@@ -120,7 +121,7 @@ def _stream_ptr(stream):
 def make_desc(spec, masses=None):
     m = np.ascontiguousarray(masses if masses is not None else spec.masses, dtype=np.float64)
     d = mlip_model_desc(spec.S, spec.T, spec.C, spec.L, spec.Lsh, spec.NB, spec.H, spec.p, spec.rc, spec.avg_nb,
-                        m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                        m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), getattr(spec, "correlation", 0))
     d._keep = m
     return d
 

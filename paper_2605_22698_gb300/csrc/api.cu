@@ -86,7 +86,8 @@ static int count_paths(int L, int Lsh, int* P0) {
 
 static int64_t weights_for(const mlip_model_desc& d, int P) {
   const int64_t S = d.n_species, C = d.channels, H = d.hidden, NB = d.n_basis, L = d.l_max;
-  return S * C + d.n_layers * (NB * H + H * H + H * P * C + (L + 1) * C * C) + S * C + S;
+  const int64_t sc = d.correlation == 2 ? S * (L + 1 + sc_num_paths(d.l_max)) * C : 0;
+  return S * C + d.n_layers * (NB * H + H * H + H * P * C + (L + 1) * C * C + sc) + S * C + S;
 }
 
 static int validate_desc(const mlip_model_desc* d, int precision) {
@@ -102,6 +103,10 @@ static int validate_desc(const mlip_model_desc* d, int precision) {
   if (d->n_basis != 8) { set_error("n_basis must be 8"); return MLIP_ERR_INVALID_ARG; }
   if (d->hidden != 32 && d->hidden != 64) { set_error("hidden %d unsupported (32, 64)", d->hidden); return MLIP_ERR_INVALID_ARG; }
   if (d->envelope_p < 1 || d->envelope_p > 16) { set_error("envelope_p %d out of range", d->envelope_p); return MLIP_ERR_INVALID_ARG; }
+  if (d->correlation != 0 && d->correlation != 2) {
+    set_error("correlation %d unsupported (0: none, 2: symmetric contraction of order 2)", d->correlation);
+    return MLIP_ERR_INVALID_ARG;
+  }
   if (!(d->cutoff > 0) || !(d->avg_num_neighbors > 0)) { set_error("cutoff and avg_num_neighbors must be positive"); return MLIP_ERR_INVALID_ARG; }
   if (precision != MLIP_PREC_FP32 && precision != MLIP_PREC_BF16 && precision != MLIP_PREC_F16) {
     set_error("unknown precision %d", precision);
@@ -143,6 +148,8 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
   M->Lsh = desc->sh_l_max; M->NB = desc->n_basis; M->H = desc->hidden; M->p = desc->envelope_p;
   M->rc = desc->cutoff; M->avg_nb = desc->avg_num_neighbors;
   M->P = P; M->P0 = P0; M->D = (M->L + 1) * (M->L + 1);
+  M->corr = desc->correlation;
+  M->Q = M->corr == 2 ? sc_num_paths(M->L) : 0;
   M->precision = precision;
   if (desc->masses) M->masses.assign(desc->masses, desc->masses + M->S);
   M->host_weights.assign(weights, weights + n_weights);
@@ -159,6 +166,10 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
     M->W2.push_back(q); q += H * H;
     M->W3.push_back(q); q += H * P * C;
     M->Wmix.push_back(q); q += (int64_t)(M->L + 1) * C * C;
+    if (M->corr == 2) {
+      M->Wsc1.push_back(q); q += S * (M->L + 1) * C;
+      M->Wsc2.push_back(q); q += S * M->Q * C;
+    }
   }
   M->W_out = q; q += S * C;
   M->E0 = q; q += S;
@@ -275,13 +286,14 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
   if (!f) { set_error("cannot open '%s'", path); return MLIP_ERR_NOT_FOUND; }
   char magic[8];
   uint32_t version = 0;
-  int32_t hyper[8];
+  int32_t hyper[8], corr = 0;
   double dh[2];
   f.read(magic, 8);
   f.read(reinterpret_cast<char*>(&version), 4);
   f.read(reinterpret_cast<char*>(hyper), sizeof(hyper));
+  if (version == 2) f.read(reinterpret_cast<char*>(&corr), 4);
   f.read(reinterpret_cast<char*>(dh), sizeof(dh));
-  if (!f || std::memcmp(magic, "MLIPPRM1", 8) != 0 || version != 1) { set_error("'%s' is not a parameter file", path); return MLIP_ERR_INVALID_ARG; }
+  if (!f || std::memcmp(magic, "MLIPPRM1", 8) != 0 || (version != 1 && version != 2)) { set_error("'%s' is not a parameter file", path); return MLIP_ERR_INVALID_ARG; }
   if (hyper[0] < 1 || hyper[0] > 128) { set_error("bad species count"); return MLIP_ERR_INVALID_ARG; }
   std::vector<double> masses(hyper[0]);
   f.read(reinterpret_cast<char*>(masses.data()), sizeof(double) * masses.size());
@@ -291,7 +303,7 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
   std::vector<float> w(count);
   f.read(reinterpret_cast<char*>(w.data()), sizeof(float) * count);
   if (!f) { set_error("truncated parameter file"); return MLIP_ERR_INVALID_ARG; }
-  mlip_model_desc d{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dh[0], dh[1], masses.data()};
+  mlip_model_desc d{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dh[0], dh[1], masses.data(), corr};
   return mlip_model_create(&d, w.data(), count, precision, out);
 }
 
@@ -401,33 +413,39 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
   MLIP_TRY(ws.get("ef.dY", Ec * 16, &dY));
   MLIP_TRY(ws.get("ef.dr", Ec, &dr));
   MLIP_TRY(ws.get("ef.atom_e", (size_t)std::max(n, 1), &atom_e));
-  std::vector<float*> h(T + 1), u0(T), w(T);
+  std::vector<float*> h(T + 1), u0(T), w(T), A(T, nullptr);
   for (int t = 0; t <= T; ++t) MLIP_TRY(ws.get("ef.h" + std::to_string(t), ND, &h[t]));
   for (int t = 0; t < T; ++t) {
     MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
     MLIP_TRY(ws.get("ef.w" + std::to_string(t), Ec * (t == 0 ? P0 : P) * C, &w[t]));
+    if (M->corr == 2) MLIP_TRY(ws.get("ef.A" + std::to_string(t), ND, &A[t]));
   }
   double* energy = d_energy;
 
   MLIP_TRY(launch_edge_geom(E, d_pos, nl.recv, nl.send, nl.shift, ca, ev, st));
-  MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st));
+  MLIP_TRY(launch_embed(n, C, D, M->S, d_species, M->W_emb, h[0], st));
   for (int t = 0; t < T; ++t) {
     const bool first = t == 0;
     const int PW = first ? P0 : P;
     MLIP_TRY(launch_radial_fwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, z2T, E, st));
     MLIP_TRY(launch_sgemm(true, false, E, PW * C, H, z2T, E, M->W3[t], P * C, w[t], PW * C, st));
     MLIP_TRY(launch_tp_fwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], w[t], PW, s, m, st));
+    if (M->corr == 2)
+      MLIP_TRY(launch_sym_contract(L, n, C, M->S, m, nullptr, d_species, M->Wsc1[t], M->Wsc2[t], A[t], m, st));
     MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
   }
-  MLIP_TRY(launch_energy(ws, b, C, D, d_species, M->W_out, M->E0, h[T], atom_e, energy, st));
+  MLIP_TRY(launch_energy(ws, b, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, energy, st));
   if (d_forces || d_stress) {
-    MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, Ga, st));
+    MLIP_TRY(launch_grad_init(n, C, D, M->S, d_species, M->W_out, Ga, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dr, 0, Ec * sizeof(float), st));
     for (int t = T - 1; t >= 0; --t) {
       const bool first = t == 0;
       const int PW = first ? P0 : P;
       MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], M->WmixT[t], Gm, st));
+      if (M->corr == 2)
+        MLIP_TRY(launch_sym_contract_bwd(L, n, C, M->S, Gm, A[t], d_species, M->Wsc1[t], M->Wsc2[t], Gm, nullptr, nullptr,
+                                         st));
       MLIP_TRY(launch_tp_bwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], Gm, w[t], PW, s, Ga, Gb, dw, dY, st));
       MLIP_TRY(launch_sgemm(false, true, E, H, PW * C, dw, PW * C, M->W3[t], P * C, dz2, H, st));
       MLIP_TRY(launch_radial_bwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, st));

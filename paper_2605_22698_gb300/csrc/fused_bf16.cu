@@ -2031,11 +2031,12 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
   MLIP_TRY(ws.get("ef.m", ND, &mA));
   MLIP_TRY(ws.get("fz.m2", ND, &mB));
   MLIP_TRY(ws.get("ef.atom_e", (size_t)std::max(n, 1), &atom_e));
-  std::vector<float*> h(T + 1), u0(T);
+  std::vector<float*> h(T + 1), u0(T), A(T, nullptr);
   std::vector<uint8_t*> z2t(T);
   for (int t = 0; t <= T; ++t) MLIP_TRY(ws.get("ef.h" + std::to_string(t), ND, &h[t]));
   for (int t = 0; t < T; ++t) {
     MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
+    if (M->corr == 2) MLIP_TRY(ws.get("ef.A" + std::to_string(t), ND, &A[t]));
     MLIP_TRY(ws.get("fz.z2t" + std::to_string(t), (size_t)std::max(n_tiles, 1) * kTileBytes, &z2t[t]));
   }
   uint8_t* epar = nullptr;
@@ -2069,17 +2070,22 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
   MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)T * b.nsys, &absmax));
   if (!use_bf16) MLIP_CUDA_TRY(cudaMemsetAsync(absmax, 0, sizeof(float) * 2 * T * b.nsys, st));
   auto amax_h = [&](int t) -> float* { return use_bf16 || t >= T ? nullptr : absmax + 2 * (size_t)t * b.nsys; };
-  MLIP_TRY(launch_embed(n, C, D, d_species, M->W_emb, h[0], st, b.d_sys_of, M->d_embmax, amax_h(0)));
+  MLIP_TRY(launch_embed(n, C, D, M->S, d_species, M->W_emb, h[0], st, b.d_sys_of, M->d_embmax, amax_h(0)));
   for (int t = 0; t < T; ++t) {
     if (!M->d_radimg) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
     MLIP_TRY(launch_radial_tc(H, E, n_tiles, ev, M->W1[t], M->d_radimg + (size_t)t * 32768, M->rad_scale[t],
                               (float)M->rc, M->p, use_bf16, z2t[t], flag + 1, st, Edev));
     MLIP_TRY(launch_tp_fused(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], M->d_w3img + M->w3_layer_off[t],
                              M->w3_goff[t], z2t[t], s, mA, mB, use_bf16, epar, flag + 1, st));
-    MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
+    float* mB_mix = mB;
+    if (M->corr == 2) {  // B(mA + mB) into mA; the mix reads it alone
+      MLIP_TRY(launch_sym_contract(L, n, C, M->S, mA, mB, d_species, M->Wsc1[t], M->Wsc2[t], A[t], mA, st));
+      mB_mix = nullptr;
+    }
+    MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB_mix, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
                            nullptr, flag + 1, st, b.d_sys_of, amax_h(t + 1)));
   }
-  MLIP_TRY(launch_energy(ws, b, C, D, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
+  MLIP_TRY(launch_energy(ws, b, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
   if (d_forces || d_stress) {
     MLIP_TRY(ws.get("ef.g", Ec, &g));
     MLIP_TRY(ws.get("ef.Gm", ND, &Gm));
@@ -2090,14 +2096,19 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     MLIP_TRY(ws.get("ef.dY", Ec * 16, &dY));
     MLIP_TRY(ws.get("ef.dr", Ec, &dr));
     MLIP_TRY(ws.get("fz.dz2", Ec * 64, &dz2));
-    MLIP_TRY(launch_grad_init(n, C, D, d_species, M->W_out, GaA, st));
+    MLIP_TRY(launch_grad_init(n, C, D, M->S, d_species, M->W_out, GaA, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(GaB, 0, ND * sizeof(float), st));
     MLIP_TRY(zero(dY, 16));  // dE/dz2 and dE/dr are initialised by the first group / layer that writes them
     float2* dws2 = nullptr;  // per system: scale of dE/dw and its inverse
     MLIP_TRY(ws.get("fz.dws2", (size_t)b.nsys, &dws2));
     for (int t = T - 1; t >= 0; --t) {
+      // max |dE/dm| of the message adjoint's input: from the mix, or from the contraction's adjoint
+      float* gmax = use_bf16 ? nullptr : amax_h(t) + 1;
       MLIP_TRY(launch_mix_tc(true, n, C, L, GaA, GaB, M->mix_bwd_img[t], M->mix_scale[t], nullptr, Gm, nullptr,
-                             u0[t], flag + 1, st, b.d_sys_of, use_bf16 ? nullptr : amax_h(t) + 1));
+                             u0[t], flag + 1, st, b.d_sys_of, M->corr == 2 ? nullptr : gmax));
+      if (M->corr == 2)
+        MLIP_TRY(launch_sym_contract_bwd(L, n, C, M->S, Gm, A[t], d_species, M->Wsc1[t], M->Wsc2[t], Gm, b.d_sys_of, gmax,
+                                         st));
       {
         MLIP_PROF("dw_scales", st);
         dw_scales<<<(b.nsys + 127) / 128, 128, 0, st>>>(b.nsys, absmax + 2 * (size_t)t * b.nsys, s, use_bf16,

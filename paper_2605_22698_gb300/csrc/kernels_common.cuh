@@ -138,6 +138,11 @@ __device__ __forceinline__ float warp_reduce16(const float* v) {
   return u[0];
 }
 
+// Species index for reading per-species weights: an index outside [0, S) is
+// reported by the input check and the call fails, but it must never address
+// outside the weights meanwhile.
+__device__ __forceinline__ int clamp_species(int z, int S) { return min(max(z, 0), S - 1); }
+
 // out[2 sys] = max(out[2 sys], m) for m >= 0 (float bits ordered as integers);
 // one atomic per warp when all its lanes' values belong to one system (sys < 0:
 // nothing to add).  Every lane of the warp calls it.

@@ -26,11 +26,11 @@ int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const f
                    float* Gm, cudaStream_t st);
 // amax (nullable): per-system max |h| accumulated into amax[2 s] (zeroed by the caller) from the
 // per-species maxima emax[z] = max_c |W_emb[z][c]|
-int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st,
+int launch_embed(int n, int C, int D, int S, const int* species, const float* W_emb, float* h, cudaStream_t st,
                  const int* sys_of = nullptr, const float* emax = nullptr, float* amax = nullptr);
-int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st);
+int launch_grad_init(int n, int C, int D, int S, const int* species, const float* W_out, float* G, cudaStream_t st);
 // per-system energies energy[nsys] (FP64)
-int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, const int* species, const float* W_out,
+int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, int S, const int* species, const float* W_out,
                   const float* E0, const float* h, double* atom_e, double* energy, cudaStream_t st);
 int launch_edge_grad(int E, const float4* ev, const float* dY, const float* dr, float4* g, cudaStream_t st,
                      const int* Edev = nullptr);
@@ -111,5 +111,15 @@ int launch_vv_drift(const SystemBatch& b, const double* dt, const int* active, c
 // ke[s] = sum over system s of m v^2 / (2 kappa)  (eV)
 int launch_kinetic(Workspace& ws, const SystemBatch& b, const int* species, const double* mass, const double* vel,
                    double* ke, cudaStream_t st);
+
+// Symmetric contraction of correlation order 2 (sym_contract.cu): out = B(A)
+// with A = X (+ X2), A also written to Asave; its adjoint GA from GB at A
+// (out_max: per-system max |GA| at out_max[2 sys], nullable).  In place allowed.
+int sc_num_paths(int L);
+int launch_sym_contract(int L, int n, int C, int S, const float* X, const float* X2, const int* species, const float* w1,
+                        const float* w2, float* Asave, float* out, cudaStream_t st);
+int launch_sym_contract_bwd(int L, int n, int C, int S, const float* GB, const float* A, const int* species,
+                            const float* w1, const float* w2, float* GA, const int* sys_of, float* out_max,
+                            cudaStream_t st);
 
 }  // namespace mlip

@@ -209,6 +209,9 @@ struct mlip_model {
   const float* W_out = nullptr;
   const float* E0 = nullptr;
   std::vector<const float*> W1, W2, W3, Wmix;
+  // symmetric contraction (correlation 2; empty otherwise): w1 [S][L+1][C], w2 [S][Q][C] per layer
+  int corr = 0, Q = 0;
+  std::vector<const float*> Wsc1, Wsc2;
   float* d_wmixT = nullptr;            // channel-mix weights transposed, per layer and order
   std::vector<const float*> WmixT;
   // fused form: split FP16 tensor-core images of the mix weights per layer

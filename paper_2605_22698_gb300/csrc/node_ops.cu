@@ -13,7 +13,7 @@ namespace {
 // h[i][d][c] = W_emb[z_i][c] for d = 0, else 0 (float4 stores; C a multiple of 4).
 // amax (nullable): amax[2 s] = max |h| over the atoms of system s, from the
 // per-species maxima emax[z] = max_c |W_emb[z][c]| (one atomic per atom)
-__global__ void embed(int n, int C, int D, const int* __restrict__ species, const float* __restrict__ W_emb,
+__global__ void embed(int n, int C, int D, int S, const int* __restrict__ species, const float* __restrict__ W_emb,
                       float* __restrict__ h, const int* __restrict__ sys_of, const float* __restrict__ emax,
                       float* __restrict__ amax) {
   const int C4 = C / 4;
@@ -24,14 +24,15 @@ __global__ void embed(int n, int C, int D, const int* __restrict__ species, cons
     const size_t rest = k / C4;
     const int d = (int)(rest % D);
     const int i = (int)(rest / D);
-    h4[k] = d == 0 ? reinterpret_cast<const float4*>(W_emb + (size_t)species[i] * C)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int z = clamp_species(species[i], S);
+    h4[k] = d == 0 ? reinterpret_cast<const float4*>(W_emb + (size_t)z * C)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
     if (amax && c4 == 0 && d == 0)
-      atomicMax(reinterpret_cast<unsigned*>(amax) + 2 * (sys_of ? sys_of[i] : 0), __float_as_uint(emax[species[i]]));
+      atomicMax(reinterpret_cast<unsigned*>(amax) + 2 * (sys_of ? sys_of[i] : 0), __float_as_uint(emax[z]));
   }
 }
 
 // dE/dh^T: W_out[z_i] on the scalars, zero elsewhere (float4 stores).
-__global__ void grad_init(int n, int C, int D, const int* __restrict__ species, const float* __restrict__ W_out,
+__global__ void grad_init(int n, int C, int D, int S, const int* __restrict__ species, const float* __restrict__ W_out,
                           float* __restrict__ G) {
   const int C4 = C / 4;
   const size_t total = (size_t)n * D * C4;
@@ -41,17 +42,18 @@ __global__ void grad_init(int n, int C, int D, const int* __restrict__ species, 
     const size_t rest = k / C4;
     const int d = (int)(rest % D);
     const int i = (int)(rest / D);
-    G4[k] = d == 0 ? reinterpret_cast<const float4*>(W_out + (size_t)species[i] * C)[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    G4[k] = d == 0 ? reinterpret_cast<const float4*>(W_out + (size_t)clamp_species(species[i], S) * C)[c4]
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
 
 // E_i = sum_c W_out[z_i][c] h_i,0[c] + E0[z_i]  (one warp per atom, FP32 dot, FP64 result)
-__global__ void readout(int n, int C, int D, const int* __restrict__ species, const float* __restrict__ W_out,
+__global__ void readout(int n, int C, int D, int S, const int* __restrict__ species, const float* __restrict__ W_out,
                         const float* __restrict__ E0, const float* __restrict__ h, double* __restrict__ atom_e) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (i >= n) return;
-  const int z = species[i];
+  const int z = clamp_species(species[i], S);
   float acc = 0.0f;
   for (int c = lane; c < C; c += 32) acc = fmaf(W_out[(size_t)z * C + c], h[(size_t)i * D * C + c], acc);
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -125,36 +127,36 @@ __global__ void forces_virial(int n, const int* __restrict__ row_ptr, const int*
 
 }  // namespace
 
-int launch_embed(int n, int C, int D, const int* species, const float* W_emb, float* h, cudaStream_t st,
+int launch_embed(int n, int C, int D, int S, const int* species, const float* W_emb, float* h, cudaStream_t st,
                  const int* sys_of, const float* emax, float* amax) {
   if (n <= 0) return MLIP_OK;
   if (amax && !emax) { set_error("embed: the per-species maxima are missing"); return MLIP_ERR_INVALID_ARG; }
   if (C % 4) { set_error("embed: channels must be a multiple of 4"); return MLIP_ERR_INVALID_ARG; }
   {
     MLIP_PROF("embed", st);
-    embed<<<std::min<int64_t>(((int64_t)n * D * (C / 4) + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species, W_emb, h,
+    embed<<<std::min<int64_t>(((int64_t)n * D * (C / 4) + 255) / 256, 16384), 256, 0, st>>>(n, C, D, S, species, W_emb, h,
                                                                                       sys_of, emax, amax);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
-int launch_grad_init(int n, int C, int D, const int* species, const float* W_out, float* G, cudaStream_t st) {
+int launch_grad_init(int n, int C, int D, int S, const int* species, const float* W_out, float* G, cudaStream_t st) {
   if (n <= 0) return MLIP_OK;
   if (C % 4) { set_error("grad_init: channels must be a multiple of 4"); return MLIP_ERR_INVALID_ARG; }
   {
     MLIP_PROF("grad_init", st);
-    grad_init<<<std::min<int64_t>(((int64_t)n * D * (C / 4) + 255) / 256, 16384), 256, 0, st>>>(n, C, D, species,
+    grad_init<<<std::min<int64_t>(((int64_t)n * D * (C / 4) + 255) / 256, 16384), 256, 0, st>>>(n, C, D, S, species,
                                                                                                W_out, G);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
-int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, const int* species, const float* W_out,
+int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, int S, const int* species, const float* W_out,
                   const float* E0, const float* h, double* atom_e, double* energy, cudaStream_t st) {
   const int n = (int)b.n;
-  if (n > 0) { MLIP_PROF("readout", st); readout<<<(n + 7) / 8, 256, 0, st>>>(n, C, D, species, W_out, E0, h, atom_e); }
+  if (n > 0) { MLIP_PROF("readout", st); readout<<<(n + 7) / 8, 256, 0, st>>>(n, C, D, S, species, W_out, E0, h, atom_e); }
   MLIP_LAUNCH_CHECK();
   return launch_seg_sum(ws, b, 1, atom_e, false, energy, st);
 }
