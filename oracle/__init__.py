@@ -63,6 +63,11 @@ def lib():
         L.oracle_energy_dual.argtypes = [P, P, P, i64, P, P, i64, i32, P, P]
         L.oracle_tp.argtypes = [i32, i32, i32, P, P, P, P]
         L.oracle_sc_paths.argtypes = [i32, P]
+        L.oracle_model_set_total_charge.argtypes = [P, f64]
+        L.oracle_charges.argtypes = [P, P, P, i64, P]
+        L.oracle_coulomb.argtypes = [P, P, i64, f64, P, P, P]
+        L.oracle_inv_chi.argtypes = [f64, f64]
+        L.oracle_inv_chi.restype = f64
         L.oracle_sym_contract.argtypes = [i32, i32, P, P, P, P]
         L.oracle_sym_contract_adjoint.argtypes = [i32, i32, P, P, P, P, P]
         L.oracle_vv_nve.argtypes = [P, P, P, P, P, i64, P, P, f64, i64, P, P]
@@ -173,6 +178,20 @@ def sym_contract_adjoint(L: int, A, w1, w2, GB) -> np.ndarray:
     return out
 
 
+def inv_chi(r: float, r0: float) -> float:
+    """Soft-core pair function 1/chi(r) of the Coulomb term."""
+    return float(lib().oracle_inv_chi(r, r0))
+
+
+def coulomb(pos, qt, r0: float):
+    """The Coulomb term alone: (E, dE/dqt [n], forces [n, 3]) for corrected charges qt."""
+    pos = _c(pos, np.float64); qt = _c(qt, np.float64)
+    n = pos.shape[0]
+    E = np.zeros(1); g = np.zeros(n); F = np.zeros((n, 3))
+    lib().oracle_coulomb(_p(pos), _p(qt), n, r0, _p(E), _p(g), _p(F))
+    return float(E[0]), g, F
+
+
 def neighbors(pos, cell, pbc, rc: float):
     """Brute-force neighbour list sorted by (recv, send, shift)."""
     pos = _c(pos, np.float64); cell = _c(cell, np.float64); pbc = _c(pbc, np.uint8)
@@ -194,8 +213,9 @@ class Model:
 
     def __init__(self, spec, weights: np.ndarray):
         self.spec = spec
-        self._hyper = _c(np.append(spec.hyper, getattr(spec, "correlation", 0)), np.int32)
-        self._dhyper = _c(spec.dhyper, np.float64)
+        self._hyper = _c(np.append(spec.hyper, [getattr(spec, "correlation", 0), getattr(spec, "charges", 0)]),
+                         np.int32)
+        self._dhyper = _c(np.append(spec.dhyper, getattr(spec, "coulomb_r0", 0.0)), np.float64)
         nw = lib().oracle_num_weights(_p(self._hyper))
         w = _c(weights, np.float32)
         if w.size != nw:
@@ -208,6 +228,18 @@ class Model:
         if h and _lib is not None:
             _lib.oracle_model_free(h)
             self._h = None
+
+    def set_total_charge(self, Q: float) -> None:
+        """Total charge of the systems evaluated next (models with the charge head)."""
+        lib().oracle_model_set_total_charge(self._h, float(Q))
+
+    def charges(self, pos, species) -> np.ndarray:
+        """Corrected charges of an open system."""
+        pos = _c(pos, np.float64); species = _c(species, np.int32)
+        q = np.zeros(pos.shape[0])
+        if lib().oracle_charges(self._h, _p(pos), _p(species), pos.shape[0], _p(q)) != 0:
+            raise ValueError("oracle_charges failed")
+        return q
 
     def energy_forces(self, pos, species, cell, pbc, stress: bool = False, atom_energies: bool = False):
         pos = _c(pos, np.float64); species = _c(species, np.int32)

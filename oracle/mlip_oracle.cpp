@@ -332,13 +332,16 @@ struct Hyper {
   int S, T, C, L, Lsh, NB, H, p;
   double rc, avg_nb;
   int corr;  // 0: no symmetric contraction; 2: correlation order 2
+  int charges;  // 1: charge head, charge correction and Coulomb term (open systems)
+  double r0;    // soft-core radius of the Coulomb term, A
 };
 
 struct Model {
   Hyper hp;
   int D, DY, P;
   std::vector<Path> paths, sc;
-  std::vector<double> W_emb, W_out, E0;
+  std::vector<double> W_emb, W_out, E0, W_q, q0;
+  double qtot = 0.0;  // total charge of the system being evaluated
   std::vector<std::vector<double>> W1, W2, W3, Wmix, Wsc1, Wsc2;
 };
 
@@ -348,7 +351,64 @@ int64_t num_weights(const Hyper& h, int P) {
   return int64_t(h.S) * h.C +
          int64_t(h.T) * (int64_t(h.NB) * h.H + int64_t(h.H) * h.H + int64_t(h.H) * P * h.C +
                          int64_t(h.L + 1) * h.C * h.C + sc) +
-         int64_t(h.S) * h.C + h.S;
+         int64_t(h.S) * h.C + h.S + (h.charges ? int64_t(h.S) * h.C + h.S : 0);
+}
+
+// ------------------------------------------------------------ electrostatics
+// Coulomb's constant e^2 / (4 pi eps0) in eV A.
+constexpr double kCoulomb = 14.3996454784;
+
+// Soft-core pair function 1/chi(r) of the long-range term (Eq.
+// long_range_interaction; chi follows PhysNet: equal to r beyond r0, smoothly
+// regularised below):
+//   1/chi(r) = phi(r/r0) / sqrt(r^2 + 1) + (1 - phi(r/r0)) / r,
+//   phi(x) = 1 - 6 x^5 + 15 x^4 - 10 x^3 for x < 1, 0 otherwise.
+template <class T>
+T inv_chi(T r, double r0) {
+  const T x = r / T(r0);
+  if (val(x) >= 1.0) return T(1.0) / r;
+  const T x3 = x * x * x;
+  const T phi = T(1.0) - T(6.0) * x3 * x * x + T(15.0) * x3 * x - T(10.0) * x3;
+  return phi / sqrt(r * r + T(1.0)) + (T(1.0) - phi) / r;
+}
+// d(1/chi)/dr, written out for the reverse pass
+double inv_chi_grad(double r, double r0) {
+  const double x = r / r0;
+  if (x >= 1.0) return -1.0 / (r * r);
+  const double x2 = x * x, x3 = x2 * x;
+  const double phi = 1.0 - 6.0 * x3 * x2 + 15.0 * x3 * x - 10.0 * x3;
+  const double dphi = (-30.0 * x2 * x2 + 60.0 * x3 - 30.0 * x2) / r0;
+  const double s = std::sqrt(r * r + 1.0);
+  return dphi * (1.0 / s - 1.0 / r) - phi * r / (s * s * s) - (1.0 - phi) / (r * r);
+}
+
+// Charge correction (Eq. charge_correction): qt_i = q_i - (sum_j q_j - Q) / N.
+template <class T>
+void correct_charges(std::vector<T>& q, double Q) {
+  T sum = T(0.0);
+  for (const T& v : q) sum += v;
+  const T shift = (sum - T(Q)) / T((double)q.size());
+  for (T& v : q) v = v - shift;
+}
+
+// E_LR = k sum_{i<j} qt_i qt_j / chi(r_ij) over all pairs of an open system
+// (Eq. long_range_interaction, each unordered pair once).  atom_e (nullable)
+// receives the half-pair shares k qt_i / 2 sum_{j != i} qt_j / chi(r_ij).
+template <class T>
+T coulomb_energy(const T* pos, const std::vector<T>& qt, int n, double r0, T* atom_e) {
+  T E = T(0.0);
+  for (int i = 0; i < n; ++i) {
+    T ei = T(0.0);
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      const T dx = pos[3 * j] - pos[3 * i], dy = pos[3 * j + 1] - pos[3 * i + 1], dz = pos[3 * j + 2] - pos[3 * i + 2];
+      ei += qt[j] * inv_chi(sqrt(dx * dx + dy * dy + dz * dz), r0);
+    }
+    ei = T(0.5 * kCoulomb) * qt[i] * ei;
+    if (atom_e) atom_e[i] = ei;
+    E += ei;
+  }
+  return E;
 }
 
 // Symmetric contraction of one node (correlation order 2), species z:
@@ -581,6 +641,20 @@ T model_energy(const Model& M, const std::vector<Edge>& edges, const std::vector
     if (atom_e) atom_e[i] = val(ei);
     E += ei;
   }
+  if (hp.charges) {
+    // charge head q_i = W_q[z_i] . h_i,0 + q0[z_i], corrected to the total charge, and the Coulomb term
+    std::vector<T> q(n);
+    for (int i = 0; i < n; ++i) {
+      T qi = T(M.q0[species[i]]);
+      for (int c = 0; c < C; ++c) qi += T(M.W_q[(size_t)species[i] * C + c]) * h[((size_t)i * D) * C + c];
+      q[i] = qi;
+    }
+    correct_charges(q, M.qtot);
+    std::vector<T> ae(n);
+    E += coulomb_energy<T>(pos, q, n, hp.r0, ae.data());
+    if (atom_e)
+      for (int i = 0; i < n; ++i) atom_e[i] += val(ae[i]);
+  }
   return E;
 }
 
@@ -641,6 +715,37 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
   std::vector<double> G((size_t)n * D * C, 0.0);
   for (int i = 0; i < n; ++i)
     for (int c = 0; c < C; ++c) G[((size_t)i * D) * C + c] = M.W_out[(size_t)species[i] * C + c];
+  std::vector<double> qt, Fc;  // corrected charges and the Coulomb term's direct forces
+  if (hp.charges) {
+    const std::vector<double>& hT = hs[hp.T];
+    qt.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      double qi = M.q0[species[i]];
+      for (int c = 0; c < C; ++c) qi += M.W_q[(size_t)species[i] * C + c] * hT[((size_t)i * D) * C + c];
+      qt[i] = qi;
+    }
+    correct_charges(qt, M.qtot);
+    // gt_i = dE/dqt_i = k sum_{j != i} qt_j / chi(r_ij); direct force -dE/dr_i at fixed charges
+    std::vector<double> gt(n, 0.0);
+    Fc.assign(3 * (size_t)n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        if (j == i) continue;
+        const double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1], pos[3 * j + 2] - pos[3 * i + 2]};
+        const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        gt[i] += kCoulomb * qt[j] * inv_chi(r, hp.r0);
+        // E contains k qt_i qt_j f(r_ij) once per pair; d/dr_i of it is -k qt_i qt_j f'(r) d / r
+        const double fr = kCoulomb * qt[i] * qt[j] * inv_chi_grad(r, hp.r0) / r;
+        for (int a = 0; a < 3; ++a) Fc[3 * (size_t)i + a] += fr * d[a];
+      }
+    // through the correction: dE/dq_i = gt_i - mean(gt)
+    double mean = 0.0;
+    for (int i = 0; i < n; ++i) mean += gt[i];
+    mean /= n;
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < C; ++c)
+        G[((size_t)i * D) * C + c] += (gt[i] - mean) * M.W_q[(size_t)species[i] * C + c];
+  }
   for (int t = hp.T - 1; t >= 0; --t) {
     const std::vector<double>& hprev = hs[t];
     const std::vector<double>& u = us[t];
@@ -755,6 +860,8 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
         forces[3 * edges[e].i + a] += g[(size_t)e * 3 + a];
         forces[3 * edges[e].j + a] -= g[(size_t)e * 3 + a];
       }
+    if (hp.charges)
+      for (size_t k = 0; k < 3 * (size_t)n; ++k) forces[k] += Fc[k];
   }
   if (virial) {
     for (int k = 0; k < 9; ++k) virial[k] = 0.0;
@@ -849,9 +956,9 @@ int oracle_paths(int L, int Lsh, int* out) {
 double oracle_bessel(int n, double r, double rc) { return bessel<double>(n, r, rc); }
 double oracle_envelope(double x, int p) { return envelope<double>(x, p); }
 
-// hyper = {S, T, C, L, Lsh, NB, H, p, correlation}, dhyper = {rc, avg_num_neighbors}
+// hyper = {S, T, C, L, Lsh, NB, H, p, correlation, charges}, dhyper = {rc, avg_num_neighbors, r0}
 int64_t oracle_num_weights(const int* hyper) {
-  Hyper h{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], 0, 0, hyper[8]};
+  Hyper h{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], 0, 0, hyper[8], hyper[9], 0};
   int P = (int)build_paths(h.L, h.Lsh).size();
   return num_weights(h, P);
 }
@@ -860,7 +967,7 @@ void* oracle_model_create(const int* hyper, const double* dhyper, const float* w
   Model* M = new Model();
   Hyper& h = M->hp;
   h = Hyper{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dhyper[0], dhyper[1],
-            hyper[8]};
+            hyper[8], hyper[9], dhyper[2]};
   M->paths = build_paths(h.L, h.Lsh);
   if (h.corr == 2) M->sc = build_sc_paths(h.L);
   M->P = (int)M->paths.size();
@@ -887,10 +994,64 @@ void* oracle_model_create(const int* hyper, const double* dhyper, const float* w
   }
   take(M->W_out, (size_t)h.S * h.C);
   take(M->E0, (size_t)h.S);
+  if (h.charges) {
+    take(M->W_q, (size_t)h.S * h.C);
+    take(M->q0, (size_t)h.S);
+  }
   return M;
 }
 
 void oracle_model_free(void* m) { delete static_cast<Model*>(m); }
+
+// Total charge Q of the systems evaluated next (models with the charge head).
+void oracle_model_set_total_charge(void* m, double Q) { static_cast<Model*>(m)->qtot = Q; }
+
+// Corrected charges of the charge head for one system (n values).
+int oracle_charges(void* model, const double* pos, const int32_t* species, int64_t n, double* q_out) {
+  const Model& M = *static_cast<Model*>(model);
+  if (!M.hp.charges) return -4;
+  std::vector<Edge> edges;
+  double zero[9] = {0};
+  uint8_t np[3] = {0, 0, 0};
+  if (brute_neighbors(pos, (int)n, zero, np, M.hp.rc, edges) != 0) return -1;
+  std::vector<int> rp = receiver_row_ptr(edges, (int)n);
+  std::vector<int> sp(species, species + n);
+  std::vector<std::vector<double>> hs(M.hp.T + 1);
+  model_energy<double>(M, edges, rp, pos, sp.data(), (int)n, zero, nullptr, &hs, nullptr);
+  const int D = M.D, C = M.hp.C;
+  std::vector<double> q(n);
+  for (int64_t i = 0; i < n; ++i) {
+    double qi = M.q0[sp[i]];
+    for (int c = 0; c < C; ++c) qi += M.W_q[(size_t)sp[i] * C + c] * hs[M.hp.T][((size_t)i * D) * C + c];
+    q[i] = qi;
+  }
+  correct_charges(q, M.qtot);
+  for (int64_t i = 0; i < n; ++i) q_out[i] = q[i];
+  return 0;
+}
+
+// The Coulomb term alone for given corrected charges: E, dE/dqt [n], forces [n][3].
+int oracle_coulomb(const double* pos, const double* qt, int64_t n, double r0, double* E, double* dEdq,
+                   double* forces) {
+  std::vector<double> q(qt, qt + n);
+  *E = coulomb_energy<double>(pos, q, (int)n, r0, nullptr);
+  for (int64_t i = 0; i < n; ++i) {
+    double g = 0.0, F[3] = {0.0, 0.0, 0.0};
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      const double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1], pos[3 * j + 2] - pos[3 * i + 2]};
+      const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      g += kCoulomb * q[j] * inv_chi(r, r0);
+      const double fr = kCoulomb * q[i] * q[j] * inv_chi_grad(r, r0) / r;
+      for (int a = 0; a < 3; ++a) F[a] += fr * d[a];
+    }
+    dEdq[i] = g;
+    for (int a = 0; a < 3; ++a) forces[3 * i + a] = F[a];
+  }
+  return 0;
+}
+
+double oracle_inv_chi(double r, double r0) { return inv_chi<double>(r, r0); }
 
 // Brute-force neighbour list, sorted by (recv, send, S).  Returns the number of
 // edges (writing at most cap of them), -1 for a singular periodic cell.
@@ -920,6 +1081,7 @@ int oracle_energy_forces(void* model, const double* pos, const int32_t* species,
                          double* stress, double* atom_e) {
   const Model& M = *static_cast<Model*>(model);
   bool anyp = pbc[0] || pbc[1] || pbc[2];
+  if (M.hp.charges && anyp) return -3;  // the Coulomb term is defined for open systems
   double zero[9] = {0};
   uint8_t np[3] = {0, 0, 0};
   const double* cl = anyp ? cell : zero;
@@ -942,6 +1104,7 @@ int oracle_energy(void* model, const double* pos, const int32_t* species, int64_
                   const double* cell, const uint8_t* pbc, double* energy, double* atom_e) {
   const Model& M = *static_cast<Model*>(model);
   bool anyp = pbc[0] || pbc[1] || pbc[2];
+  if (M.hp.charges && anyp) return -3;  // the Coulomb term is defined for open systems
   double zero[9] = {0};
   uint8_t np[3] = {0, 0, 0};
   const double* cl = anyp ? cell : zero;
@@ -960,6 +1123,7 @@ int oracle_energy_dual(void* model, const double* pos, const int32_t* species, i
                        double* dE) {
   const Model& M = *static_cast<Model*>(model);
   bool anyp = pbc[0] || pbc[1] || pbc[2];
+  if (M.hp.charges && anyp) return -3;  // the Coulomb term is defined for open systems
   double zero[9] = {0};
   uint8_t np[3] = {0, 0, 0};
   const double* cl = anyp ? cell : zero;

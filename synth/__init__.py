@@ -81,6 +81,8 @@ class ModelSpec:
     p: int = 6
     masses: tuple = (1.008, 12.011, 14.007, 15.999)
     correlation: int = 0  # 0: no symmetric contraction; 2: MACE's of correlation order 2
+    charges: int = 0      # 1: charge head + charge correction + Coulomb term (open systems)
+    coulomb_r0: float = 0.0  # soft-core radius of the Coulomb term, A (charges = 1)
 
     @property
     def hyper(self) -> np.ndarray:
@@ -130,6 +132,8 @@ class ModelSpec:
                 out += [(f"Wsc1.{t}", (self.S, self.L + 1, self.C), 1),
                         (f"Wsc2.{t}", (self.S, Q, self.C), Q)]
         out += [("W_out", (self.S, self.C), self.C), ("E0", (self.S,), 0)]
+        if self.charges:
+            out += [("W_q", (self.S, self.C), self.C), ("q0", (self.S,), 0)]
         return out
 
     def n_weights(self) -> int:
@@ -144,6 +148,8 @@ def model_spec(name: str) -> ModelSpec:
     fcc     2 layers, 128 channels, l <= 3, hidden 64, 2 species
     <name>_mace  the same with the symmetric contraction of correlation order 2
                  after every scatter-sum (Table tbl:mace_params: correlation 2)
+    <name>_charged  the same with a charge head, the charge correction and the
+                 soft-core Coulomb term (Eqs. charge_correction, long_range_interaction)
     """
     if name == "small":
         return ModelSpec(S=4, T=1, C=16, L=2, H=32, avg_nb=20.0)
@@ -153,6 +159,9 @@ def model_spec(name: str) -> ModelSpec:
         return ModelSpec(S=2, T=2, C=128, L=3, H=64, avg_nb=42.0, masses=(63.546, 58.693))
     if name.endswith("_mace"):  # the same model with the symmetric contraction of correlation order 2
         return dataclasses.replace(model_spec(name[:-5]), correlation=2)
+    if name.endswith("_charged"):  # the same model with the charge head and the Coulomb term (r0 = rc / 2)
+        base = model_spec(name[:-8])
+        return dataclasses.replace(base, charges=1, coulomb_r0=0.5 * base.rc)
     raise ValueError(name)
 
 
@@ -182,18 +191,19 @@ PARAMS_MAGIC = b"MLIPPRM1"
 
 
 def write_params(path: str, spec: ModelSpec, w: np.ndarray) -> None:
-    """Parameter file: magic, u32 version, 8 x i32 hyper, (version 2: i32
-    correlation), 2 x f64 (rc, avg_nb), S x f64 masses, i64 count, count x f32
-    weights; little-endian.  Version 1 for models without the symmetric
-    contraction."""
+    """Parameter file: magic, u32 version, 8 x i32 hyper, (version 2 only:
+    i32 correlation, i32 charges, f64 coulomb_r0), 2 x f64 (rc, avg_nb),
+    S x f64 masses, i64 count, count x f32 weights; little-endian.  Version 1
+    for models with neither the symmetric contraction nor the charge head."""
     w = np.ascontiguousarray(w, dtype=np.float32)
     assert w.size == spec.n_weights()
+    v2 = bool(spec.correlation or spec.charges)
     with open(path, "wb") as f:
         f.write(PARAMS_MAGIC)
-        f.write(struct.pack("<I", 2 if spec.correlation else 1))
+        f.write(struct.pack("<I", 2 if v2 else 1))
         f.write(spec.hyper.astype("<i4").tobytes())
-        if spec.correlation:
-            f.write(struct.pack("<i", spec.correlation))
+        if v2:
+            f.write(struct.pack("<iid", spec.correlation, spec.charges, spec.coulomb_r0))
         f.write(spec.dhyper.astype("<f8").tobytes())
         f.write(np.asarray(spec.masses, dtype="<f8").tobytes())
         f.write(struct.pack("<q", w.size))
