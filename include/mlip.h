@@ -96,7 +96,20 @@ typedef struct {
   double avg_num_neighbors;  /* message scale s = 1/avg_num_neighbors */
   const double* masses;      /* n_species masses (amu), host; may be NULL (no MD) */
   int32_t correlation;       /* 0 or 2 (see above) */
+  int32_t charges;           /* 1: charge head, charge correction and Coulomb term (below) */
+  double coulomb_r0;         /* soft-core radius r0 of the Coulomb term, A (charges = 1) */
 } mlip_model_desc;
+
+/* charges = 1 (Sec. "Treatment of electrostatics and long-range
+ * interactions"): per-atom charges q_i = W_q[z_i] . h^T_i,0 + q0[z_i] (weights
+ * W_q [S][C], q0 [S] after E0), corrected to the system's total charge Q
+ * (Eq. charge_correction: qt_i = q_i - (sum_j q_j - Q) / N), and the energy
+ * gains E_LR = k sum_{i<j} qt_i qt_j / chi(r_ij) over all pairs of the system
+ * (Eq. long_range_interaction; k = 14.3996454784 eV A / e^2; PhysNet's
+ * surrogate distance 1/chi(r) = phi(r/r0) / sqrt(r^2 + 1) + (1 - phi(r/r0)) / r,
+ * phi(x) = 1 - 10 x^3 + 15 x^4 - 6 x^5 for x < 1, else 0).  Open systems only:
+ * every entry point returns MLIP_ERR_CELL for a periodic system; Q = 0 except
+ * through mlip_energy_forces_charged. */
 
 /* Thread-local text of the last error (never NULL). */
 const char* mlip_last_error(void);
@@ -172,6 +185,16 @@ int mlip_neighbors_noalloc(const double* pos, int64_t n, const double cell[9], c
 int mlip_energy_forces(mlip_model* model, const double* pos, const int32_t* species, int64_t n,
                        const double cell[9], const uint8_t pbc[3], double* energy, double* forces,
                        double* stress, int on_device, void* stream);
+
+/* Energy, forces and the corrected charges of one open system of total
+ * charge total_charge (e) with a model built with charges = 1 (see
+ * mlip_model_desc).  pos double[n][3], species int32[n]; energy double[1];
+ * forces double[n][3] or NULL; charges double[n] or NULL.  Host or device
+ * arrays as for mlip_energy_forces.  Errors: MLIP_ERR_INVALID_ARG (model
+ * without charges, null or out-of-range inputs), MLIP_ERR_CUDA. */
+int mlip_energy_forces_charged(mlip_model* model, const double* pos, const int32_t* species, int64_t n,
+                               double total_charge, double* energy, double* forces, double* charges,
+                               int on_device, void* stream);
 
 /* Energy, forces and stress of a batch of independent systems in one call
  * (the batched inference of the Introduction): the systems are evaluated

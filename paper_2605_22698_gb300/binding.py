@@ -44,7 +44,7 @@ class mlip_model_desc(ctypes.Structure):
                 ("l_max", ctypes.c_int32), ("sh_l_max", ctypes.c_int32), ("n_basis", ctypes.c_int32),
                 ("hidden", ctypes.c_int32), ("envelope_p", ctypes.c_int32), ("cutoff", ctypes.c_double),
                 ("avg_num_neighbors", ctypes.c_double), ("masses", ctypes.POINTER(ctypes.c_double)),
-                ("correlation", ctypes.c_int32)]
+                ("correlation", ctypes.c_int32), ("charges", ctypes.c_int32), ("coulomb_r0", ctypes.c_double)]
 
 
 class mlip_md_options(ctypes.Structure):
@@ -75,6 +75,7 @@ def lib():
         L.mlip_model_free.argtypes = [P]
         L.mlip_neighbors.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), i32, P]
         L.mlip_energy_forces.argtypes = [P, P, P, i64, P, P, P, P, P, i32, P]
+        L.mlip_energy_forces_charged.argtypes = [P, P, P, i64, ctypes.c_double, P, P, P, i32, P]
         L.mlip_energy_forces_batch.argtypes = [P, i32, P, P, P, P, P, P, P, P, i32, P]
         L.mlip_neighbors_noalloc.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), P]
         L.mlip_md_nve.argtypes = [P, P, P, P, i64, P, P, f64, i64, P, P, i32, P]
@@ -121,7 +122,8 @@ def _stream_ptr(stream):
 def make_desc(spec, masses=None):
     m = np.ascontiguousarray(masses if masses is not None else spec.masses, dtype=np.float64)
     d = mlip_model_desc(spec.S, spec.T, spec.C, spec.L, spec.Lsh, spec.NB, spec.H, spec.p, spec.rc, spec.avg_nb,
-                        m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), getattr(spec, "correlation", 0))
+                        m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), getattr(spec, "correlation", 0),
+                        getattr(spec, "charges", 0), getattr(spec, "coulomb_r0", 0.0))
     d._keep = m
     return d
 
@@ -222,6 +224,31 @@ def mlip_energy_forces(h, pos, species, cell, pbc, forces: bool = True, stress: 
                                     pbc.ctypes.data_as(ctypes.c_void_p), _ptr(out["energy"])[0],
                                     _ptr(out["forces"])[0] if forces else None,
                                     _ptr(out["stress"])[0] if stress else None, dev, _stream_ptr(stream)))
+    return out
+
+
+def mlip_energy_forces_charged(h, pos, species, total_charge: float = 0.0, forces: bool = True, stream=None):
+    """One open system of the given total charge with a model with charges:
+    energy, forces and the corrected charges (host or device arrays, as
+    mlip_energy_forces)."""
+    n = int(pos.shape[0])
+    pp, dev = _ptr(pos)
+    sp, dev2 = _ptr(species)
+    if dev != dev2:
+        raise ValueError("positions and species must both be host or both be device arrays")
+    if dev:
+        import torch
+        out = {"energy": torch.zeros(1, dtype=torch.float64, device=pos.device),
+               "charges": torch.zeros(n, dtype=torch.float64, device=pos.device)}
+        if forces:
+            out["forces"] = torch.zeros((n, 3), dtype=torch.float64, device=pos.device)
+    else:
+        out = {"energy": np.zeros(1), "charges": np.zeros(n)}
+        if forces:
+            out["forces"] = np.zeros((n, 3))
+    _check(lib().mlip_energy_forces_charged(h, pp, sp, n, float(total_charge), _ptr(out["energy"])[0],
+                                            _ptr(out["forces"])[0] if forces else None, _ptr(out["charges"])[0],
+                                            dev, _stream_ptr(stream)))
     return out
 
 
@@ -362,6 +389,9 @@ class Model:
 
     def energy_forces(self, pos, species, cell, pbc, forces=True, stress=False, stream=None, out=None):
         return mlip_energy_forces(self.h, pos, species, cell, pbc, forces, stress, stream, out)
+
+    def energy_forces_charged(self, pos, species, total_charge=0.0, forces=True, stream=None):
+        return mlip_energy_forces_charged(self.h, pos, species, total_charge, forces, stream)
 
     def energy_forces_batch(self, systems, forces=True, stress=False, stream=None):
         return mlip_energy_forces_batch(self.h, systems, forces, stress, stream)

@@ -87,7 +87,8 @@ static int count_paths(int L, int Lsh, int* P0) {
 static int64_t weights_for(const mlip_model_desc& d, int P) {
   const int64_t S = d.n_species, C = d.channels, H = d.hidden, NB = d.n_basis, L = d.l_max;
   const int64_t sc = d.correlation == 2 ? S * (L + 1 + sc_num_paths(d.l_max)) * C : 0;
-  return S * C + d.n_layers * (NB * H + H * H + H * P * C + (L + 1) * C * C + sc) + S * C + S;
+  return S * C + d.n_layers * (NB * H + H * H + H * P * C + (L + 1) * C * C + sc) + S * C + S +
+         (d.charges ? S * C + S : 0);
 }
 
 static int validate_desc(const mlip_model_desc* d, int precision) {
@@ -105,6 +106,11 @@ static int validate_desc(const mlip_model_desc* d, int precision) {
   if (d->envelope_p < 1 || d->envelope_p > 16) { set_error("envelope_p %d out of range", d->envelope_p); return MLIP_ERR_INVALID_ARG; }
   if (d->correlation != 0 && d->correlation != 2) {
     set_error("correlation %d unsupported (0: none, 2: symmetric contraction of order 2)", d->correlation);
+    return MLIP_ERR_INVALID_ARG;
+  }
+  if (d->charges != 0 && d->charges != 1) { set_error("charges must be 0 or 1"); return MLIP_ERR_INVALID_ARG; }
+  if (d->charges && !(d->coulomb_r0 > 0.0 && d->coulomb_r0 < 1e3)) {
+    set_error("coulomb_r0 %g out of range (0, 1000)", d->coulomb_r0);
     return MLIP_ERR_INVALID_ARG;
   }
   if (!(d->cutoff > 0) || !(d->avg_num_neighbors > 0)) { set_error("cutoff and avg_num_neighbors must be positive"); return MLIP_ERR_INVALID_ARG; }
@@ -149,6 +155,8 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
   M->rc = desc->cutoff; M->avg_nb = desc->avg_num_neighbors;
   M->P = P; M->P0 = P0; M->D = (M->L + 1) * (M->L + 1);
   M->corr = desc->correlation;
+  M->charges = desc->charges;
+  M->r0 = desc->coulomb_r0;
   M->Q = M->corr == 2 ? sc_num_paths(M->L) : 0;
   M->precision = precision;
   if (desc->masses) M->masses.assign(desc->masses, desc->masses + M->S);
@@ -173,6 +181,10 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
   }
   M->W_out = q; q += S * C;
   M->E0 = q; q += S;
+  if (M->charges) {
+    M->W_q = q; q += S * C;
+    M->q0 = q; q += S;
+  }
   {  // W_l^T of every layer and order, for the adjoint of the mixes
     const size_t per = (size_t)(M->L + 1) * C * C;
     std::vector<float> wt(per * M->T);
@@ -286,12 +298,16 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
   if (!f) { set_error("cannot open '%s'", path); return MLIP_ERR_NOT_FOUND; }
   char magic[8];
   uint32_t version = 0;
-  int32_t hyper[8], corr = 0;
-  double dh[2];
+  int32_t hyper[8], corr = 0, charges = 0;
+  double dh[2], r0 = 0.0;
   f.read(magic, 8);
   f.read(reinterpret_cast<char*>(&version), 4);
   f.read(reinterpret_cast<char*>(hyper), sizeof(hyper));
-  if (version == 2) f.read(reinterpret_cast<char*>(&corr), 4);
+  if (version == 2) {
+    f.read(reinterpret_cast<char*>(&corr), 4);
+    f.read(reinterpret_cast<char*>(&charges), 4);
+    f.read(reinterpret_cast<char*>(&r0), 8);
+  }
   f.read(reinterpret_cast<char*>(dh), sizeof(dh));
   if (!f || std::memcmp(magic, "MLIPPRM1", 8) != 0 || (version != 1 && version != 2)) { set_error("'%s' is not a parameter file", path); return MLIP_ERR_INVALID_ARG; }
   if (hyper[0] < 1 || hyper[0] > 128) { set_error("bad species count"); return MLIP_ERR_INVALID_ARG; }
@@ -303,7 +319,7 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
   std::vector<float> w(count);
   f.read(reinterpret_cast<char*>(w.data()), sizeof(float) * count);
   if (!f) { set_error("truncated parameter file"); return MLIP_ERR_INVALID_ARG; }
-  mlip_model_desc d{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dh[0], dh[1], masses.data(), corr};
+  mlip_model_desc d{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dh[0], dh[1], masses.data(), corr, charges, r0};
   return mlip_model_create(&d, w.data(), count, precision, out);
 }
 
@@ -434,9 +450,16 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
       MLIP_TRY(launch_sym_contract(L, n, C, M->S, m, nullptr, d_species, M->Wsc1[t], M->Wsc2[t], A[t], m, st));
     MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
   }
-  MLIP_TRY(launch_energy(ws, b, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, energy, st));
+  if (M->charges) {  // readout, charge head and Coulomb term, then the per-system sums
+    MLIP_TRY(launch_readout(n, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, st));
+    MLIP_TRY(coulomb_forward(ws, b, M, d_pos, d_species, h[T], atom_e, st));
+    MLIP_TRY(launch_seg_sum(ws, b, 1, atom_e, false, energy, st));
+  } else {
+    MLIP_TRY(launch_energy(ws, b, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, energy, st));
+  }
   if (d_forces || d_stress) {
     MLIP_TRY(launch_grad_init(n, C, D, M->S, d_species, M->W_out, Ga, st));
+    if (M->charges) MLIP_TRY(coulomb_adjoint(ws, b, M, d_species, Ga, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dr, 0, Ec * sizeof(float), st));
     for (int t = T - 1; t >= 0; --t) {
@@ -455,12 +478,17 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
     double* fbuf = d_forces;
     if (!fbuf) MLIP_TRY(ws.get("ef.fscratch", (size_t)3 * std::max(n, 1), &fbuf));
     MLIP_TRY(launch_forces_virial(ws, b, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, st));
+    if (M->charges) MLIP_TRY(coulomb_add_forces(ws, b, fbuf, st));
   }
   return MLIP_OK;
 }
 
 int evaluate(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b, double* d_energy,
              double* d_forces, double* d_stress, cudaStream_t st, bool graph) {
+  if (M->charges && b.any_pbc()) {
+    set_error("a model with charges evaluates open systems only (the Coulomb term has no periodic images)");
+    return MLIP_ERR_CELL;
+  }
   if (M->precision == MLIP_PREC_FP32) return evaluate_plain(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st);
   if (graph) return evaluate_fused_graph(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st);
   return evaluate_fused(M, d_pos, d_species, b, d_energy, d_forces, d_stress, st);
@@ -508,6 +536,58 @@ extern "C" int mlip_energy_forces(mlip_model* M, const double* pos, const int32_
     MLIP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (forces) MLIP_CUDA_TRY(cudaMemcpyAsync(forces, d_forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     if (stress) MLIP_CUDA_TRY(cudaMemcpyAsync(stress, d_stress, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+    MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  } else {
+    MLIP_CUDA_TRY(cudaGetLastError());
+  }
+  return MLIP_OK;
+}
+
+extern "C" int mlip_energy_forces_charged(mlip_model* M, const double* pos, const int32_t* species, int64_t n,
+                                          double total_charge, double* energy, double* forces, double* charges,
+                                          int on_device, void* stream) {
+  using namespace mlip;
+  if (!M || !pos || !species || !energy) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  if (!M->charges) { set_error("the model has no charge head (charges = 0)"); return MLIP_ERR_INVALID_ARG; }
+  if (n < 1 || n > (1LL << 28)) { set_error("atom count %lld out of range", (long long)n); return MLIP_ERR_INVALID_ARG; }
+  if (!std::isfinite(total_charge)) { set_error("total charge is not finite"); return MLIP_ERR_INVALID_ARG; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != M->device) { set_error("model lives on device %d, current device is %d", M->device, cur); return MLIP_ERR_INVALID_ARG; }
+  Workspace& ws = M->ws;
+  WsStream wss(ws, st);
+  const double* d_pos = pos;
+  const int* d_species = species;
+  double *d_energy = energy, *d_forces = forces;
+  if (!on_device) {
+    for (int64_t i = 0; i < n; ++i)
+      if (species[i] < 0 || species[i] >= M->S) { set_error("species[%lld] = %d out of range", (long long)i, species[i]); return MLIP_ERR_INVALID_ARG; }
+    double* dp = nullptr;
+    int* dz = nullptr;
+    MLIP_TRY(ws.get("in.pos", (size_t)3 * n, &dp));
+    MLIP_TRY(ws.get("in.species", (size_t)n, &dz));
+    MLIP_TRY(ws.get("out.energy", 1, &d_energy));
+    if (forces) MLIP_TRY(ws.get("out.forces", (size_t)3 * n, &d_forces));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dp, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(dz, species, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    d_pos = dp;
+    d_species = dz;
+  }
+  const double cell[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  const uint8_t pbc[3] = {0, 0, 0};
+  SystemBatch b;
+  single_system(b, n, cell, pbc);
+  b.qtot.assign(1, total_charge);
+  MLIP_TRY(upload_batch(ws, M->stage, b, st));
+  MLIP_TRY(evaluate(M, d_pos, d_species, b, d_energy, d_forces, nullptr, st, true));
+  double* d_q = nullptr;
+  MLIP_TRY(coulomb_charges(ws, b, &d_q));
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (charges) MLIP_CUDA_TRY(cudaMemcpyAsync(charges, d_q, sizeof(double) * n, k, st));
+  if (!on_device) {
+    MLIP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (forces) MLIP_CUDA_TRY(cudaMemcpyAsync(forces, d_forces, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     MLIP_CUDA_TRY(cudaStreamSynchronize(st));
   } else {
     MLIP_CUDA_TRY(cudaGetLastError());

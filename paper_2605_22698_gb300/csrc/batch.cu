@@ -87,12 +87,13 @@ void single_system(SystemBatch& b, int64_t n, const double* cell, const uint8_t*
   b.atom_off = {0, n};
   b.cell.assign(cell, cell + 9);
   b.pbc.assign(pbc, pbc + 3);
+  b.qtot.clear();
 }
 
 int upload_batch(Workspace& ws, HostStage& stage, SystemBatch& b, cudaStream_t st) {
   const int nsys = b.nsys;
   if (nsys < 1 || (int)b.atom_off.size() != nsys + 1 || (int)b.cell.size() != 9 * nsys ||
-      (int)b.pbc.size() != 3 * nsys) {
+      (int)b.pbc.size() != 3 * nsys || (!b.qtot.empty() && (int)b.qtot.size() != nsys)) {
     set_error("batch: inconsistent system tables");
     return MLIP_ERR_INVALID_ARG;
   }
@@ -110,8 +111,8 @@ int upload_batch(Workspace& ws, HostStage& stage, SystemBatch& b, cudaStream_t s
   }
   b.sys_chunk_off[nsys] = (int)(b.chunk.size() / 3);
   const int nch = b.nchunk();
-  // one pinned blob: doubles (cells, 1/V), then ints (offsets, chunks, chunk offsets)
-  const size_t nd = (size_t)10 * nsys, ni = (size_t)(nsys + 1) + 3 * (size_t)nch + (size_t)(nsys + 1);
+  // one pinned blob: doubles (cells, 1/V, total charges), then ints (offsets, chunks, chunk offsets)
+  const size_t nd = (size_t)11 * nsys, ni = (size_t)(nsys + 1) + 3 * (size_t)nch + (size_t)(nsys + 1);
   const size_t bytes = nd * sizeof(double) + ni * sizeof(int);
   void* hp = nullptr;
   MLIP_TRY(stage.get(bytes, &hp));
@@ -122,6 +123,7 @@ int upload_batch(Workspace& ws, HostStage& stage, SystemBatch& b, cudaStream_t s
     for (int k = 0; k < 9; ++k) hd[9 * s + k] = any ? b.cell[9 * s + k] : 0.0;
     const double vol = all ? cell_volume3(&b.cell[9 * s]) : 0.0;
     hd[9 * nsys + s] = vol > 0.0 ? 1.0 / vol : 0.0;
+    hd[10 * nsys + s] = b.qtot.empty() ? 0.0 : b.qtot[s];
   }
   int* hi = reinterpret_cast<int*>(hd + nd);
   for (int s = 0; s <= nsys; ++s) hi[s] = (int)b.atom_off[s];
@@ -133,16 +135,18 @@ int upload_batch(Workspace& ws, HostStage& stage, SystemBatch& b, cudaStream_t s
   if (nsys > 1 && b.n > 0) MLIP_TRY(ws.get("batch.sys_of", (size_t)b.n, &b.d_sys_of));
   b.d_cell = reinterpret_cast<double*>(dblob);
   b.d_inv_vol = b.d_cell + 9 * nsys;
+  b.d_qtot = b.d_cell + 10 * nsys;
   b.d_atom_off = reinterpret_cast<int*>(b.d_cell + nd);
   b.d_chunk = b.d_atom_off + nsys + 1;
   b.d_sys_chunk_off = b.d_chunk + 3 * nch;
   // the same tables as the last upload into unchanged buffers: nothing to copy
   std::vector<double> sig;
-  sig.reserve(1 + (size_t)(nsys + 1) + 12 * (size_t)nsys);
+  sig.reserve(1 + (size_t)(nsys + 1) + 13 * (size_t)nsys);
   sig.push_back((double)nsys);
   for (int s = 0; s <= nsys; ++s) sig.push_back((double)b.atom_off[s]);
   sig.insert(sig.end(), b.cell.begin(), b.cell.end());
   for (uint8_t v : b.pbc) sig.push_back(v);
+  for (int s = 0; s < nsys; ++s) sig.push_back(b.qtot.empty() ? 0.0 : b.qtot[s]);
   if (sig == ws.batch_sig && ws.batch_gen == ws.gen) return MLIP_OK;
   ws.batch_sig.clear();
   MLIP_CUDA_TRY(cudaMemcpyAsync(dblob, hp, bytes, cudaMemcpyHostToDevice, st));

@@ -2085,7 +2085,13 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB_mix, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
                            nullptr, flag + 1, st, b.d_sys_of, amax_h(t + 1)));
   }
-  MLIP_TRY(launch_energy(ws, b, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
+  if (M->charges) {  // readout, charge head and Coulomb term, then the per-system sums
+    MLIP_TRY(launch_readout(n, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, st));
+    MLIP_TRY(coulomb_forward(ws, b, M, d_pos, d_species, h[T], atom_e, st));
+    MLIP_TRY(launch_seg_sum(ws, b, 1, atom_e, false, d_energy, st));
+  } else {
+    MLIP_TRY(launch_energy(ws, b, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
+  }
   if (d_forces || d_stress) {
     MLIP_TRY(ws.get("ef.g", Ec, &g));
     MLIP_TRY(ws.get("ef.Gm", ND, &Gm));
@@ -2097,6 +2103,7 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     MLIP_TRY(ws.get("ef.dr", Ec, &dr));
     MLIP_TRY(ws.get("fz.dz2", Ec * 64, &dz2));
     MLIP_TRY(launch_grad_init(n, C, D, M->S, d_species, M->W_out, GaA, st));
+    if (M->charges) MLIP_TRY(coulomb_adjoint(ws, b, M, d_species, GaA, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(GaB, 0, ND * sizeof(float), st));
     MLIP_TRY(zero(dY, 16));  // dE/dz2 and dE/dr are initialised by the first group / layer that writes them
     float2* dws2 = nullptr;  // per system: scale of dE/dw and its inverse
@@ -2127,6 +2134,7 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     double* fbuf = d_forces;
     if (!fbuf) MLIP_TRY(ws.get("ef.fscratch", (size_t)3 * std::max(n, 1), &fbuf));
     MLIP_TRY(launch_forces_virial(ws, b, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, st));
+    if (M->charges) MLIP_TRY(coulomb_add_forces(ws, b, fbuf, st));
   }
   return MLIP_OK;
 }

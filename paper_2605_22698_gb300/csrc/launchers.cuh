@@ -29,6 +29,9 @@ int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const f
 int launch_embed(int n, int C, int D, int S, const int* species, const float* W_emb, float* h, cudaStream_t st,
                  const int* sys_of = nullptr, const float* emax = nullptr, float* amax = nullptr);
 int launch_grad_init(int n, int C, int D, int S, const int* species, const float* W_out, float* G, cudaStream_t st);
+// out_i = W[z_i] . h_i,0 + b0[z_i] (FP32 dot, FP64 result)
+int launch_readout(int n, int C, int D, int S, const int* species, const float* W, const float* b0, const float* h,
+                   double* out, cudaStream_t st);
 // per-system energies energy[nsys] (FP64)
 int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, int S, const int* species, const float* W_out,
                   const float* E0, const float* h, double* atom_e, double* energy, cudaStream_t st);
@@ -121,5 +124,19 @@ int launch_sym_contract(int L, int n, int C, int S, const float* X, const float*
 int launch_sym_contract_bwd(int L, int n, int C, int S, const float* GB, const float* A, const int* species,
                             const float* w1, const float* w2, float* GA, const int* sys_of, float* out_max,
                             cudaStream_t st);
+
+// Charge head, charge correction and Coulomb term (coulomb.cu), for models
+// with charges = 1 and open systems.  Forward: from h^T and the per-atom
+// readout energies in atom_e, adds the Coulomb shares to atom_e and keeps
+// the corrected charges, dE/dqt and the direct forces in the workspace.
+// Adjoint: adds dE/dq_i W_q[z_i] to the scalar rows of G and the direct
+// forces to forces.
+int coulomb_forward(Workspace& ws, const SystemBatch& b, const mlip_model* M, const double* d_pos,
+                    const int* species, const float* hT, double* atom_e, cudaStream_t st);
+int coulomb_adjoint(Workspace& ws, const SystemBatch& b, const mlip_model* M, const int* species, float* G,
+                    cudaStream_t st);
+int coulomb_add_forces(Workspace& ws, const SystemBatch& b, double* forces, cudaStream_t st);
+// the corrected charges of the last coulomb_forward ([n] FP64, device)
+int coulomb_charges(Workspace& ws, const SystemBatch& b, double** q);
 
 }  // namespace mlip

@@ -137,6 +137,7 @@ struct SystemBatch {
   std::vector<int64_t> atom_off;      // [nsys + 1]
   std::vector<double> cell;           // [nsys * 9] lattice rows
   std::vector<uint8_t> pbc;           // [nsys * 3]
+  std::vector<double> qtot;           // [nsys] total charges (empty: all zero; models with the charge head)
   std::vector<int> chunk;             // [nchunk * 3]: system, first atom, end atom
   std::vector<int> sys_chunk_off;     // [nsys + 1]: chunks of system s
   // device copies (upload_batch)
@@ -144,6 +145,7 @@ struct SystemBatch {
   int* d_atom_off = nullptr;          // [nsys + 1]
   double* d_cell = nullptr;           // [nsys * 9], zero rows for systems with no periodic axis
   double* d_inv_vol = nullptr;        // [nsys], 1/V for fully periodic systems, else 0
+  double* d_qtot = nullptr;           // [nsys] total charges
   int* d_chunk = nullptr;             // [nchunk * 3]
   int* d_sys_chunk_off = nullptr;     // [nsys + 1]
   int nchunk() const { return (int)(chunk.size() / 3); }
@@ -212,6 +214,11 @@ struct mlip_model {
   // symmetric contraction (correlation 2; empty otherwise): w1 [S][L+1][C], w2 [S][Q][C] per layer
   int corr = 0, Q = 0;
   std::vector<const float*> Wsc1, Wsc2;
+  // charge head and Coulomb term (charges = 1): q_i = W_q[z] . h_i,0 + q0[z]; soft-core radius r0
+  int charges = 0;
+  double r0 = 0.0;
+  const float* W_q = nullptr;
+  const float* q0 = nullptr;
   float* d_wmixT = nullptr;            // channel-mix weights transposed, per layer and order
   std::vector<const float*> WmixT;
   // fused form: split FP16 tensor-core images of the mix weights per layer

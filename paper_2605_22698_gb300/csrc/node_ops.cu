@@ -153,11 +153,16 @@ int launch_grad_init(int n, int C, int D, int S, const int* species, const float
   return MLIP_OK;
 }
 
+int launch_readout(int n, int C, int D, int S, const int* species, const float* W, const float* b0, const float* h,
+                   double* out, cudaStream_t st) {
+  if (n > 0) { MLIP_PROF("readout", st); readout<<<(n + 7) / 8, 256, 0, st>>>(n, C, D, S, species, W, b0, h, out); }
+  MLIP_LAUNCH_CHECK();
+  return MLIP_OK;
+}
+
 int launch_energy(Workspace& ws, const SystemBatch& b, int C, int D, int S, const int* species, const float* W_out,
                   const float* E0, const float* h, double* atom_e, double* energy, cudaStream_t st) {
-  const int n = (int)b.n;
-  if (n > 0) { MLIP_PROF("readout", st); readout<<<(n + 7) / 8, 256, 0, st>>>(n, C, D, S, species, W_out, E0, h, atom_e); }
-  MLIP_LAUNCH_CHECK();
+  MLIP_TRY(launch_readout((int)b.n, C, D, S, species, W_out, E0, h, atom_e, st));
   return launch_seg_sum(ws, b, 1, atom_e, false, energy, st);
 }
 
