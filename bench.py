@@ -163,6 +163,9 @@ def workload(name: str, rank: int = 0):
     if name == "cluster64":
         spec = synth.model_spec("small")
         return spec, synth.make_weights(spec, 7), synth.cluster64(1 + rank)
+    if name == "cluster5000_charged":  # the largest serving request, model with charges and the Coulomb term
+        spec = synth.model_spec("water_charged")
+        return spec, synth.make_weights(spec, 21), synth.cluster(5000, seed=7 + 1000 * rank)
     raise ValueError(name)
 
 
@@ -182,6 +185,10 @@ def sample_workload(name: str):
         spec = synth.model_spec("water")
         return spec, synth.make_weights(spec, 21), synth.water_box(100, synth.water_side_for(100), seed=500), \
             "one 100 H2O (300 atoms) periodic box at the replicas' density, same model"
+    if name == "cluster5000_charged":
+        spec = synth.model_spec("water_charged")
+        return spec, synth.make_weights(spec, 21), synth.cluster(200, seed=7), \
+            "one 200-atom open cluster, same model with charges"
     if name == "serve":
         spec = synth.model_spec("water")
         return spec, synth.make_weights(spec, 21), synth.cluster(200, seed=4), \
@@ -395,6 +402,14 @@ def run_ours(args, rank, world):
                 sc_roof[kname] = {"bound": "hbm", "bytes_per_launch": int(nbytes), "avg_launch_ms": round(tot_ / nl_, 5),
                                   "achieved": round(gbs, 1), "peak": peaks()["hbm_gbs"], "unit": "GB/s",
                                   "frac": round(gbs / peaks()["hbm_gbs"], 4)}
+    # the Coulomb term (models with charges): pair evaluations per second of its all-pairs kernel
+    coul = None
+    if "coulomb_pairs" in share_rep:
+        nl_, tot_ = share_rep["coulomb_pairs"]
+        pairs = s.n * (s.n - 1)  # ordered pairs: every atom's sum runs over all others
+        gps = pairs / (tot_ / nl_ / 1e3) / 1e9
+        coul = {"kernel": "coulomb_pairs", "pairs_per_launch": int(pairs), "avg_launch_ms": round(tot_ / nl_, 5),
+                "gpairs_per_s": round(gps, 2)}
     share = {}
     tot_all = sum(v[1] for v in share_rep.values()) or 1.0
     for k_, v in sorted(share_rep.items(), key=lambda kv: -kv[1][1])[:8]:
@@ -438,6 +453,7 @@ def run_ours(args, rank, world):
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernel_share": share,
         "kernel_ms_per_step": round(tot_all / n_share, 4),
         "sym_contract_roofline": sc_roof,
+        "coulomb": coul,
         "timing": "timed steps: CUDA events around the dominant kernel's launches only (graph event nodes); "
                   "kernel_share from 4 steps with every kernel timed, outside the timed region",
         "plain_fp32": plain,
@@ -694,7 +710,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water3000", choices=["water3000", "fcc108k", "cluster64", "serve", "md64",
-                                                                 "water3000_mace", "fcc108k_mace"])
+                                                                 "water3000_mace", "fcc108k_mace",
+                                                                 "cluster5000_charged"])
     ap.add_argument("--precision", default="f16", choices=["fp32", "bf16", "f16"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form beside the headline")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")
