@@ -13,10 +13,13 @@
 // which enters the network's adjoint as dE/dh^T_i,0 += dE/dq_i W_q[z_i]; the
 // direct forces at fixed charges are added to the network's forces.
 //
-// coulomb_pairs: one warp per atom i, lanes over the atoms j of its system
-// (lane j - first = lane mod 32, so a system's sums do not depend on its
-// batch); pair terms in FP32 from FP64 coordinate differences, folded into
-// FP64 every 16 terms per lane, FP64 warp reduction.
+// coulomb_prep writes every atom's corrected charge and its coordinates as
+// FP32 pairs hi + lo (hi = fp32(x), lo = fp32(x - hi)), so that the pair loop
+// forms d = (hi_j - hi_i) + (lo_j - lo_i) in FP32 to within an FP32 rounding
+// of the exact difference without the narrow FP64 pipe.  coulomb_pairs: one
+// warp per atom i, lanes over the atoms j of its system (j - first = lane mod
+// 32, so a system's sums do not depend on its batch); pair terms in FP32,
+// folded into FP64 every 16 terms per lane, FP64 warp reduction.
 #include <algorithm>
 
 #include "kernels_common.cuh"
@@ -52,32 +55,53 @@ __device__ __forceinline__ void inv_chi(float r, float r0, float& f, float& fpr)
 
 constexpr int kCWarps = 8;
 
-// qt, gt, e (added to atom_e), Fc [n][3] for every atom
-__global__ void __launch_bounds__(32 * kCWarps) coulomb_pairs(int n, const double* __restrict__ pos,
-                                                              const double* __restrict__ q,
-                                                              const double* __restrict__ qsum,
-                                                              const double* __restrict__ qtot,
+// qt_i = q_i - (qsum_s - Q_s) / N_s; hi/lo coordinates with the FP32 charge in hi.w
+__global__ void coulomb_prep(int n, const double* __restrict__ pos, const double* __restrict__ q,
+                             const double* __restrict__ qsum, const double* __restrict__ qtot,
+                             const int* __restrict__ atom_off, const int* __restrict__ sys_of,
+                             double* __restrict__ qt_out, float4* __restrict__ phi, float4* __restrict__ plo) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int s = sys_of ? sys_of[i] : 0;
+    const double qt = q[i] - (qsum[s] - qtot[s]) / (double)(atom_off[s + 1] - atom_off[s]);
+    qt_out[i] = qt;
+    float h[3], l[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double x = pos[3 * i + k];
+      h[k] = (float)x;
+      l[k] = (float)(x - (double)h[k]);
+    }
+    phi[i] = make_float4(h[0], h[1], h[2], (float)qt);
+    plo[i] = make_float4(l[0], l[1], l[2], 0.0f);
+  }
+}
+
+// gt, e (added to atom_e), Fc [n][3] for every atom
+__global__ void __launch_bounds__(32 * kCWarps) coulomb_pairs(int n, const float4* __restrict__ phi,
+                                                              const float4* __restrict__ plo,
+                                                              const double* __restrict__ qt,
                                                               const int* __restrict__ atom_off,
                                                               const int* __restrict__ sys_of, float r0,
-                                                              double* __restrict__ qt_out, double* __restrict__ gt_out,
-                                                              double* __restrict__ atom_e, double* __restrict__ Fc) {
+                                                              double* __restrict__ gt_out, double* __restrict__ atom_e,
+                                                              double* __restrict__ Fc) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * kCWarps + (threadIdx.x >> 5);
   if (i >= n) return;  // uniform over the warp
   const int s = sys_of ? sys_of[i] : 0;
   const int j0 = atom_off[s], j1 = atom_off[s + 1];
-  const double shift = (qsum[s] - qtot[s]) / (double)(j1 - j0);
-  const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+  const float4 hi = phi[i], lo = plo[i];
   double g = 0.0, fx = 0.0, fy = 0.0, fz = 0.0;
   float g32 = 0.0f, fx32 = 0.0f, fy32 = 0.0f, fz32 = 0.0f;
   int cnt = 0;
   for (int j = j0 + lane; j < j1; j += 32) {
     if (j != i) {
-      const float dx = (float)(pos[3 * j] - xi), dy = (float)(pos[3 * j + 1] - yi), dz = (float)(pos[3 * j + 2] - zi);
+      const float4 hj = phi[j], lj = plo[j];
+      const float dx = (hj.x - hi.x) + (lj.x - lo.x), dy = (hj.y - hi.y) + (lj.y - lo.y),
+                  dz = (hj.z - hi.z) + (lj.z - lo.z);
       const float r = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
       float f, fpr;
       inv_chi(r, r0, f, fpr);
-      const float qj = (float)(q[j] - shift);
+      const float qj = hj.w;
       g32 = fmaf(qj, f, g32);
       const float a = qj * fpr;
       fx32 = fmaf(a, dx, fx32);
@@ -99,9 +123,8 @@ __global__ void __launch_bounds__(32 * kCWarps) coulomb_pairs(int n, const doubl
     fz += __shfl_xor_sync(0xffffffffu, fz, o);
   }
   if (lane == 0) {
-    const double qi = q[i] - shift;
+    const double qi = qt[i];
     const double gt = kCoulombK * g;
-    qt_out[i] = qi;
     gt_out[i] = gt;
     atom_e[i] += 0.5 * qi * gt;
     // F_i = -dE/dr_i = k qt_i sum_j qt_j (1/chi)'(r) / r (r_j - r_i)
@@ -131,6 +154,7 @@ __global__ void add_f64(long long m, const double* __restrict__ a, double* __res
 
 struct Bufs {
   double *q, *qt, *gt, *Fc, *qsum, *gsum;
+  float4 *phi, *plo;
 };
 
 int get_bufs(Workspace& ws, const SystemBatch& b, Bufs* B) {
@@ -141,6 +165,8 @@ int get_bufs(Workspace& ws, const SystemBatch& b, Bufs* B) {
   MLIP_TRY(ws.get("cq.Fc", 3 * n, &B->Fc));
   MLIP_TRY(ws.get("cq.qsum", ns, &B->qsum));
   MLIP_TRY(ws.get("cq.gsum", ns, &B->gsum));
+  MLIP_TRY(ws.get("cq.phi", n, &B->phi));
+  MLIP_TRY(ws.get("cq.plo", n, &B->plo));
   return MLIP_OK;
 }
 
@@ -155,9 +181,15 @@ int coulomb_forward(Workspace& ws, const SystemBatch& b, const mlip_model* M, co
   MLIP_TRY(launch_readout(n, M->C, M->D, M->S, species, M->W_q, M->q0, hT, B.q, st));
   MLIP_TRY(launch_seg_sum(ws, b, 1, B.q, false, B.qsum, st));
   if (n > 0) {
+    {
+      MLIP_PROF("coulomb_prep", st);
+      coulomb_prep<<<std::min((n + 255) / 256, 4096), 256, 0, st>>>(n, d_pos, B.q, B.qsum, b.d_qtot, b.d_atom_off,
+                                                                      b.d_sys_of, B.qt, B.phi, B.plo);
+    }
+    MLIP_LAUNCH_CHECK();
     MLIP_PROF("coulomb_pairs", st);
-    coulomb_pairs<<<(n + kCWarps - 1) / kCWarps, 32 * kCWarps, 0, st>>>(
-        n, d_pos, B.q, B.qsum, b.d_qtot, b.d_atom_off, b.d_sys_of, (float)M->r0, B.qt, B.gt, atom_e, B.Fc);
+    coulomb_pairs<<<(n + kCWarps - 1) / kCWarps, 32 * kCWarps, 0, st>>>(n, B.phi, B.plo, B.qt, b.d_atom_off,
+                                                                        b.d_sys_of, (float)M->r0, B.gt, atom_e, B.Fc);
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
