@@ -150,16 +150,17 @@ def _with_contraction(spec_w_s, name):
     return (spec, synth.make_weights(spec, seed), *rest)
 
 
-def workload(name: str, rank: int = 0):
+def workload(name: str, rank: int = 0, fcc_cells: int = 30):
     if name.endswith("_mace"):
-        return _with_contraction(workload(name[:-5], rank), name)
+        return _with_contraction(workload(name[:-5], rank, fcc_cells), name)
     if name == "water3000":
         spec = synth.model_spec("water")
         sysm = synth.water_box(1000, 31.0, seed=2 + 1000 * rank)
         return spec, synth.make_weights(spec, 21), sysm
     if name == "fcc108k":
         spec = synth.model_spec("fcc")
-        return spec, synth.make_weights(spec, 31), synth.fcc((30, 30, 30), seed=3 + 1000 * rank)
+        nc = (fcc_cells,) * 3  # 30^3 cells = 108,000 atoms; fewer only for small profiling captures
+        return spec, synth.make_weights(spec, 31), synth.fcc(nc, seed=3 + 1000 * rank)
     if name == "cluster64":
         spec = synth.model_spec("small")
         return spec, synth.make_weights(spec, 7), synth.cluster64(1 + rank)
@@ -278,7 +279,7 @@ def run_ours(args, rank, world):
     from paper_2605_22698_gb300 import binding as B
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda", torch.cuda.current_device())
-    spec, w, s = workload(args.workload, rank)
+    spec, w, s = workload(args.workload, rank, args.fcc_cells)
     if spec.C != 128 or spec.H != 64:
         args.precision = "fp32"  # the fused 16-bit form serves 128-channel, hidden-64 models only
     prec = {"fp32": B.MLIP_PREC_FP32, "bf16": B.MLIP_PREC_BF16, "f16": B.MLIP_PREC_F16}[args.precision]
@@ -717,6 +718,8 @@ def main():
     ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")
     ap.add_argument("--rate-sweep", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.5, 0.9, 1.1],
                     help="serve: further open-loop arrival rates, as factors of the saturated rate")
+    ap.add_argument("--fcc-cells", type=int, default=30,
+                    help="FCC workloads: conventional cells per edge (30 = 108,000 atoms; smaller for ncu captures)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--md-list", default="skin", choices=["skin", "fresh"],
