@@ -53,6 +53,11 @@ def peaks():
 # four path-group launches of one evaluation), keyed by (workload, precision,
 # kernel).
 NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): 129.7e6}
+# DRAM bytes per launch of the symmetric contraction's kernels at fcc108k: captured on the
+# 20^3-cell FCC (32,000 atoms; the full workload is too large for a capture) and scaled by the
+# atom count (traffic grows in proportion: per-node tensors)
+NCU_TRAFFIC_SC = {("fcc108k_mace", "f16", "sym_contract"): 991.3e6 * 108000 / 32000,
+                  ("fcc108k_mace", "f16", "sym_contract_bwd"): 741.2e6 * 108000 / 32000}
 
 # FP32 ALU peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
 # lanes x 2 flop (FMA) x 2.07 GHz.
@@ -402,7 +407,8 @@ def run_ours(args, rank, world):
                 gbs = nbytes / (tot_ / nl_ / 1e3) / 1e9
                 sc_roof[kname] = {"bound": "hbm", "bytes_per_launch": int(nbytes), "avg_launch_ms": round(tot_ / nl_, 5),
                                   "achieved": round(gbs, 1), "peak": peaks()["hbm_gbs"], "unit": "GB/s",
-                                  "frac": round(gbs / peaks()["hbm_gbs"], 4)}
+                                  "frac": round(gbs / peaks()["hbm_gbs"], 4),
+                                  "traffic": NCU_TRAFFIC_SC.get((args.workload, args.precision, kname))}
     # the Coulomb term (models with charges): pair evaluations per second of its all-pairs kernel
     coul = None
     if "coulomb_pairs" in share_rep:
