@@ -408,7 +408,8 @@ def run_ours(args, rank, world):
                 sc_roof[kname] = {"bound": "hbm", "bytes_per_launch": int(nbytes), "avg_launch_ms": round(tot_ / nl_, 5),
                                   "achieved": round(gbs, 1), "peak": peaks()["hbm_gbs"], "unit": "GB/s",
                                   "frac": round(gbs / peaks()["hbm_gbs"], 4),
-                                  "traffic": NCU_TRAFFIC_SC.get((args.workload, args.precision, kname))}
+                                  "traffic": NCU_TRAFFIC_SC.get((args.workload, args.precision, kname))
+                                  if args.fcc_cells == 30 else None}
     # the Coulomb term (models with charges): pair evaluations per second of its all-pairs kernel
     coul = None
     if "coulomb_pairs" in share_rep:
