@@ -208,7 +208,7 @@ extern "C" int mlip_md_nve_batch(mlip_model* M, int32_t n_systems, const int64_t
 // ------------------------------------------------------- skin-list driver
 namespace {
 
-// The driver's own stream (graph capture needs a stream other than the legacy
+// The skin-list MD run's own stream (graph capture needs a stream other than the legacy
 // default one), its graph, and the event that orders it after the caller's.
 struct SkinRun {
   cudaStream_t st = nullptr;
@@ -259,7 +259,7 @@ extern "C" int mlip_md_nve_skin(mlip_model* M, int32_t n_systems, const int64_t*
   MLIP_CUDA_TRY(cudaStreamWaitEvent(R.st, R.ev, 0));
   cudaStream_t st = R.st;
   Workspace& ws = M->ws;
-  WsStream wss(ws, st);  // restored before the driver's stream is destroyed (declared after R)
+  WsStream wss(ws, st);  // restored before the run's stream is destroyed (declared after R)
   double *d_pos = pos, *d_vel = vel, *d_F = nullptr, *d_mass = nullptr, *d_pe = nullptr, *d_ke = nullptr,
          *d_dt = nullptr;
   const int* d_sp = species;
