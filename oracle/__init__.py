@@ -213,8 +213,8 @@ class Model:
 
     def __init__(self, spec, weights: np.ndarray):
         self.spec = spec
-        self._hyper = _c(np.append(spec.hyper, [getattr(spec, "correlation", 0), getattr(spec, "charges", 0)]),
-                         np.int32)
+        self._hyper = _c(np.append(spec.hyper, [getattr(spec, "correlation", 0), getattr(spec, "charges", 0),
+                                                getattr(spec, "gate", 0)]), np.int32)
         self._dhyper = _c(np.append(spec.dhyper, getattr(spec, "coulomb_r0", 0.0)), np.float64)
         nw = lib().oracle_num_weights(_p(self._hyper))
         w = _c(weights, np.float32)

@@ -322,6 +322,8 @@ T envelope(T x, int p) {
 }
 template <class T>
 T silu(T x) { return x / (T(1.0) + exp(-x)); }
+template <class T>
+T sigmoid(T x) { return T(1.0) / (T(1.0) + exp(-x)); }
 double silu_grad(double x) {
   double s = 1.0 / (1.0 + std::exp(-x));
   return s * (1.0 + x * (1.0 - s));
@@ -334,6 +336,7 @@ struct Hyper {
   int corr;  // 0: no symmetric contraction; 2: correlation order 2
   int charges;  // 1: charge head, charge correction and Coulomb term (open systems)
   double r0;    // soft-core radius of the Coulomb term, A
+  int gate;     // 1: species self-connection and gated update of the l > 0 features
 };
 
 struct Model {
@@ -343,14 +346,19 @@ struct Model {
   std::vector<double> W_emb, W_out, E0, W_q, q0;
   double qtot = 0.0;  // total charge of the system being evaluated
   std::vector<std::vector<double>> W1, W2, W3, Wmix, Wsc1, Wsc2;
+  // gated update: Wself [S][L+1][C][C], Wgate [C][L C], Wselfgate [S][C][L C] per layer
+  std::vector<std::vector<double>> Wself, Wgate, Wselfgate;
 };
 
 int64_t num_weights(const Hyper& h, int P) {
   const int64_t Q = h.corr == 2 ? (int64_t)build_sc_paths(h.L).size() : 0;
   const int64_t sc = h.corr == 2 ? int64_t(h.S) * (h.L + 1 + Q) * h.C : 0;
+  const int64_t gt = h.gate ? int64_t(h.S) * (h.L + 1) * h.C * h.C + int64_t(h.C) * h.L * h.C +
+                                  int64_t(h.S) * h.C * h.L * h.C
+                           : 0;
   return int64_t(h.S) * h.C +
          int64_t(h.T) * (int64_t(h.NB) * h.H + int64_t(h.H) * h.H + int64_t(h.H) * P * h.C +
-                         int64_t(h.L + 1) * h.C * h.C + sc) +
+                         int64_t(h.L + 1) * h.C * h.C + sc + gt) +
          int64_t(h.S) * h.C + h.S + (h.charges ? int64_t(h.S) * h.C + h.S : 0);
 }
 
@@ -552,7 +560,8 @@ template <class T>
 T model_energy(const Model& M, const std::vector<Edge>& edges, const std::vector<int>& row_ptr,
                const T* pos, const int* species, int n, const double* cell, double* atom_e,
                std::vector<std::vector<double>>* h_store, std::vector<std::vector<double>>* u_store,
-               std::vector<std::vector<double>>* a_store = nullptr) {
+               std::vector<std::vector<double>>* a_store = nullptr,
+               std::vector<std::vector<double>>* g_store = nullptr) {
   const Hyper& hp = M.hp;
   const int D = M.D, C = hp.C, H = hp.H, P = M.P, NB = hp.NB, DY = M.DY;
   const double s = 1.0 / hp.avg_nb;
@@ -618,6 +627,41 @@ T model_energy(const Model& M, const std::vector<Edge>& edges, const std::vector
     const std::vector<double>& Wm = M.Wmix[t];
     std::vector<T> hn(h);
     if (u_store) (*u_store)[t].assign((size_t)n * D * C, 0.0);
+    if (hp.gate) {
+      // pre_l = m_l W_l + h_l Wself[z][l];  g_l = m_0 Wgate_l + h_0 Wselfgate[z]_l (l >= 1, per channel)
+      // h_0 += silu(pre_0);  h_l += sigmoid(g_l) pre_l
+      const int LC = hp.L * C;
+      if (g_store) (*g_store)[t].assign((size_t)n * LC, 0.0);
+#pragma omp parallel for schedule(static)
+      for (int i = 0; i < n; ++i) {
+        const int z = species[i];
+        const double* Ws = &M.Wself[t][(size_t)z * (hp.L + 1) * C * C];
+        const double* Wsg = &M.Wselfgate[t][(size_t)z * C * LC];
+        std::vector<T> g(LC);
+        for (int q = 0; q < LC; ++q) {
+          T acc = T(0.0);
+          for (int c1 = 0; c1 < C; ++c1)
+            acc += m[((size_t)i * D) * C + c1] * T(M.Wgate[t][(size_t)c1 * LC + q]) +
+                   h[((size_t)i * D) * C + c1] * T(Wsg[(size_t)c1 * LC + q]);
+          g[q] = acc;
+          if (g_store) (*g_store)[t][(size_t)i * LC + q] = val(acc);
+        }
+        for (int l = 0; l <= hp.L; ++l)
+          for (int mm = -l; mm <= l; ++mm) {
+            const int ci = lm(l, mm);
+            for (int c2 = 0; c2 < C; ++c2) {
+              T acc = T(0.0);
+              for (int c1 = 0; c1 < C; ++c1)
+                acc += m[((size_t)i * D + ci) * C + c1] * T(Wm[((size_t)l * C + c1) * C + c2]) +
+                       h[((size_t)i * D + ci) * C + c1] * T(Ws[((size_t)l * C + c1) * C + c2]);
+              if (u_store) (*u_store)[t][((size_t)i * D + ci) * C + c2] = val(acc);
+              hn[((size_t)i * D + ci) * C + c2] += (l == 0) ? silu(acc) : sigmoid(g[(l - 1) * C + c2]) * acc;
+            }
+          }
+      }
+      h.swap(hn);
+      continue;
+    }
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i)
       for (int l = 0; l <= hp.L; ++l)
@@ -679,8 +723,8 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
   const double s = 1.0 / hp.avg_nb;
   const int E = (int)edges.size();
   std::vector<int> rp = receiver_row_ptr(edges, n);
-  std::vector<std::vector<double>> hs(hp.T + 1), us(hp.T), as(hp.T);
-  double energy = model_energy<double>(M, edges, rp, pos, species, n, cell, atom_e, &hs, &us, &as);
+  std::vector<std::vector<double>> hs(hp.T + 1), us(hp.T), as(hp.T), gs(hp.T);
+  double energy = model_energy<double>(M, edges, rp, pos, species, n, cell, atom_e, &hs, &us, &as, &gs);
 
   // sender-sorted index of edges
   std::vector<int> sp(n + 1, 0), sidx(E);
@@ -752,6 +796,52 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
     const std::vector<double>& Wm = M.Wmix[t];
     // through the residual update and the channel mix
     std::vector<double> Gm((size_t)n * D * C, 0.0);
+    std::vector<double> Gself;  // gated update: the self-connection's share of dE/dh^t
+    if (hp.gate) {
+      const int LC = hp.L * C;
+      Gself.assign((size_t)n * D * C, 0.0);
+#pragma omp parallel for schedule(static)
+      for (int i = 0; i < n; ++i) {
+        const int z = species[i];
+        const double* Ws = &M.Wself[t][(size_t)z * (hp.L + 1) * C * C];
+        const double* Wsg = &M.Wselfgate[t][(size_t)z * C * LC];
+        const double* g = &gs[t][(size_t)i * LC];
+        // dE/dpre and dE/dg
+        std::vector<double> dpre((size_t)D * C), dg(LC, 0.0);
+        for (int l = 0; l <= hp.L; ++l)
+          for (int mm = -l; mm <= l; ++mm) {
+            const int ci = lm(l, mm);
+            for (int c2 = 0; c2 < C; ++c2) {
+              const size_t k = ((size_t)i * D + ci) * C + c2;
+              if (l == 0) {
+                dpre[(size_t)ci * C + c2] = G[k] * silu_grad(u[k]);
+              } else {
+                const double sg = 1.0 / (1.0 + std::exp(-g[(l - 1) * C + c2]));
+                dpre[(size_t)ci * C + c2] = G[k] * sg;
+                dg[(l - 1) * C + c2] += G[k] * u[k] * sg * (1.0 - sg);
+              }
+            }
+          }
+        for (int l = 0; l <= hp.L; ++l)
+          for (int mm = -l; mm <= l; ++mm) {
+            const int ci = lm(l, mm);
+            for (int c1 = 0; c1 < C; ++c1) {
+              double am = 0.0, ah = 0.0;
+              for (int c2 = 0; c2 < C; ++c2) {
+                am += Wm[((size_t)l * C + c1) * C + c2] * dpre[(size_t)ci * C + c2];
+                ah += Ws[((size_t)l * C + c1) * C + c2] * dpre[(size_t)ci * C + c2];
+              }
+              if (l == 0)
+                for (int q = 0; q < LC; ++q) {
+                  am += M.Wgate[t][(size_t)c1 * LC + q] * dg[q];
+                  ah += Wsg[(size_t)c1 * LC + q] * dg[q];
+                }
+              Gm[((size_t)i * D + ci) * C + c1] = am;
+              Gself[((size_t)i * D + ci) * C + c1] = ah;
+            }
+          }
+      }
+    } else {
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i)
       for (int l = 0; l <= hp.L; ++l)
@@ -768,6 +858,7 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
             Gm[((size_t)i * D + ci) * C + c1] = acc;
           }
         }
+    }
     if (hp.corr == 2) {  // through the symmetric contraction: Gm = dE/dB -> dE/dA
       std::vector<double> GA(Gm.size());
 #pragma omp parallel for schedule(static)
@@ -778,6 +869,8 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
       Gm.swap(GA);
     }
     std::vector<double> Gprev(G);  // residual path
+    if (hp.gate)
+      for (size_t k = 0; k < Gprev.size(); ++k) Gprev[k] += Gself[k];
     const std::vector<double>& W1 = M.W1[t];
     const std::vector<double>& W2 = M.W2[t];
     const std::vector<double>& W3 = M.W3[t];
@@ -956,9 +1049,10 @@ int oracle_paths(int L, int Lsh, int* out) {
 double oracle_bessel(int n, double r, double rc) { return bessel<double>(n, r, rc); }
 double oracle_envelope(double x, int p) { return envelope<double>(x, p); }
 
-// hyper = {S, T, C, L, Lsh, NB, H, p, correlation, charges}, dhyper = {rc, avg_num_neighbors, r0}
+// hyper = {S, T, C, L, Lsh, NB, H, p, correlation, charges, gate}, dhyper = {rc, avg_num_neighbors, r0}
 int64_t oracle_num_weights(const int* hyper) {
-  Hyper h{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], 0, 0, hyper[8], hyper[9], 0};
+  Hyper h{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], 0, 0, hyper[8], hyper[9], 0,
+          hyper[10]};
   int P = (int)build_paths(h.L, h.Lsh).size();
   return num_weights(h, P);
 }
@@ -967,7 +1061,7 @@ void* oracle_model_create(const int* hyper, const double* dhyper, const float* w
   Model* M = new Model();
   Hyper& h = M->hp;
   h = Hyper{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dhyper[0], dhyper[1],
-            hyper[8], hyper[9], dhyper[2]};
+            hyper[8], hyper[9], dhyper[2], hyper[10]};
   M->paths = build_paths(h.L, h.Lsh);
   if (h.corr == 2) M->sc = build_sc_paths(h.L);
   M->P = (int)M->paths.size();
@@ -982,6 +1076,7 @@ void* oracle_model_create(const int* hyper, const double* dhyper, const float* w
   take(M->W_emb, (size_t)h.S * h.C);
   M->W1.resize(h.T); M->W2.resize(h.T); M->W3.resize(h.T); M->Wmix.resize(h.T);
   M->Wsc1.resize(h.T); M->Wsc2.resize(h.T);
+  M->Wself.resize(h.T); M->Wgate.resize(h.T); M->Wselfgate.resize(h.T);
   for (int t = 0; t < h.T; ++t) {
     take(M->W1[t], (size_t)h.NB * h.H);
     take(M->W2[t], (size_t)h.H * h.H);
@@ -990,6 +1085,11 @@ void* oracle_model_create(const int* hyper, const double* dhyper, const float* w
     if (h.corr == 2) {
       take(M->Wsc1[t], (size_t)h.S * (h.L + 1) * h.C);
       take(M->Wsc2[t], (size_t)h.S * M->sc.size() * h.C);
+    }
+    if (h.gate) {
+      take(M->Wself[t], (size_t)h.S * (h.L + 1) * h.C * h.C);
+      take(M->Wgate[t], (size_t)h.C * h.L * h.C);
+      take(M->Wselfgate[t], (size_t)h.S * h.C * h.L * h.C);
     }
   }
   take(M->W_out, (size_t)h.S * h.C);

@@ -83,6 +83,7 @@ class ModelSpec:
     correlation: int = 0  # 0: no symmetric contraction; 2: MACE's of correlation order 2
     charges: int = 0      # 1: charge head + charge correction + Coulomb term (open systems)
     coulomb_r0: float = 0.0  # soft-core radius of the Coulomb term, A (charges = 1)
+    gate: int = 0         # 1: species self-connection and gated update of the l > 0 features (oracle only)
 
     @property
     def hyper(self) -> np.ndarray:
@@ -131,6 +132,11 @@ class ModelSpec:
                 Q = self.n_sc_paths
                 out += [(f"Wsc1.{t}", (self.S, self.L + 1, self.C), 1),
                         (f"Wsc2.{t}", (self.S, Q, self.C), Q)]
+            if self.gate:
+                LC = self.L * self.C
+                out += [(f"Wself.{t}", (self.S, self.L + 1, self.C, self.C), self.C),
+                        (f"Wgate.{t}", (self.C, LC), self.C),
+                        (f"Wselfgate.{t}", (self.S, self.C, LC), self.C)]
         out += [("W_out", (self.S, self.C), self.C), ("E0", (self.S,), 0)]
         if self.charges:
             out += [("W_q", (self.S, self.C), self.C), ("q0", (self.S,), 0)]

@@ -16,8 +16,8 @@ import oracle
 import synth
 
 
-def tiny_spec(L=2, T=2, C=8, H=16, avg_nb=10.0, correlation=0):
-    return synth.ModelSpec(S=4, T=T, C=C, L=L, H=H, avg_nb=avg_nb, correlation=correlation)
+def tiny_spec(L=2, T=2, C=8, H=16, avg_nb=10.0, correlation=0, gate=0):
+    return synth.ModelSpec(S=4, T=T, C=C, L=L, H=H, avg_nb=avg_nb, correlation=correlation, gate=gate)
 
 
 def _rot(seed, proper=True):
@@ -33,13 +33,14 @@ def small_water(n_mol=8, seed=11):
     return synth.water_box(n_mol, synth.water_side_for(n_mol) * 1.0, seed=seed, d_oo=2.5)
 
 
-@pytest.fixture(scope="module", params=[0, 2], ids=["plain", "symcontract2"])
+@pytest.fixture(scope="module", params=[(0, 0), (2, 0), (0, 1)], ids=["plain", "symcontract2", "gated"])
 def models(request):
-    """Models of both node orders, without and with the symmetric contraction
-    of correlation order 2 after every scatter-sum."""
+    """Models of both node orders: the plain layer, with the symmetric
+    contraction of correlation order 2 after every scatter-sum, and with the
+    species self-connection and gated update."""
     out = {}
     for L in (2, 3):
-        spec = tiny_spec(L=L, correlation=request.param)
+        spec = tiny_spec(L=L, correlation=request.param[0], gate=request.param[1])
         out[L] = (spec, oracle.Model(spec, synth.make_weights(spec, 100 + L)))
     return out
 
