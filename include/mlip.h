@@ -98,7 +98,16 @@ typedef struct {
   int32_t correlation;       /* 0 or 2 (see above) */
   int32_t charges;           /* 1: charge head, charge correction and Coulomb term (below) */
   double coulomb_r0;         /* soft-core radius r0 of the Coulomb term, A (charges = 1) */
+  int32_t gate;              /* 1: gated update with a species self-connection (below) */
 } mlip_model_desc;
+
+/* gate = 1 (NequIP's gate nonlinearity and self-connection, on the uniform
+ * natural-parity irreps of this layer; 32, 64 or 128 channels): the channel
+ * mix and residual update become, per node of species z and channel,
+ *   pre_l = m_l W_l + h_l Wself[z][l],   g_l = m_0 Wgate_l + h_0 Wselfgate[z]_l (l >= 1)
+ *   h_0 += silu(pre_0),   h_l += sigmoid(g_l) pre_l   (one gate per channel and l, shared over m)
+ * with weights Wself [S][L+1][C][C], Wgate [C][L C], Wselfgate [S][C][L C]
+ * after each layer's W_mix (and the contraction's weights). */
 
 /* charges = 1 (Sec. "Treatment of electrostatics and long-range
  * interactions"): per-atom charges q_i = W_q[z_i] . h^T_i,0 + q0[z_i] (weights
@@ -117,7 +126,8 @@ int mlip_version(void);
 
 /* Number of float32 weights a model with this description takes, in the order
  *   W_emb [S][C]; per layer: W1 [8][H], W2 [H][H], W3 [H][P][C], W_mix [L+1][C][C]
- *   (with correlation 2 also w1 [S][L+1][C], w2 [S][Q][C]); W_out [S][C]; E0 [S]
+ *   (with correlation 2 also w1 [S][L+1][C], w2 [S][Q][C]; with gate also Wself,
+ *   Wgate, Wselfgate); W_out [S][C]; E0 [S] (with charges also W_q [S][C], q0 [S])
  * (P = number of coupling paths (l1 <= L, l2 <= 3, l3 <= L, triangle rule,
  * l1 + l2 + l3 even, lexicographic).  Errors: MLIP_ERR_INVALID_ARG. */
 int mlip_model_num_weights(const mlip_model_desc* desc, int64_t* n_weights);
@@ -129,8 +139,9 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
                       int precision, mlip_model** out);
 
 /* Load a parameter file: "MLIPPRM1", u32 version (1 or 2), 8 x i32 (S, T, C,
- * L, Lsh, NB, H, p), version 2 only: i32 correlation, 2 x f64 (rc,
- * avg_num_neighbors), S x f64 masses, i64 count,
+ * L, Lsh, NB, H, p), version 2 only: i32 correlation, i32 charges, f64
+ * coulomb_r0, i32 gate; then 2 x f64 (rc, avg_num_neighbors), S x f64
+ * masses, i64 count,
  * count x f32 weights; little-endian.  Errors as mlip_model_create plus
  * MLIP_ERR_NOT_FOUND (unreadable file). */
 int mlip_model_load(const char* params_path, int precision, mlip_model** out);

@@ -87,7 +87,8 @@ static int count_paths(int L, int Lsh, int* P0) {
 static int64_t weights_for(const mlip_model_desc& d, int P) {
   const int64_t S = d.n_species, C = d.channels, H = d.hidden, NB = d.n_basis, L = d.l_max;
   const int64_t sc = d.correlation == 2 ? S * (L + 1 + sc_num_paths(d.l_max)) * C : 0;
-  return S * C + d.n_layers * (NB * H + H * H + H * P * C + (L + 1) * C * C + sc) + S * C + S +
+  const int64_t gt = d.gate ? S * (L + 1) * C * C + C * L * C + S * C * L * C : 0;
+  return S * C + d.n_layers * (NB * H + H * H + H * P * C + (L + 1) * C * C + sc + gt) + S * C + S +
          (d.charges ? S * C + S : 0);
 }
 
@@ -109,6 +110,8 @@ static int validate_desc(const mlip_model_desc* d, int precision) {
     return MLIP_ERR_INVALID_ARG;
   }
   if (d->charges != 0 && d->charges != 1) { set_error("charges must be 0 or 1"); return MLIP_ERR_INVALID_ARG; }
+  if (d->gate != 0 && d->gate != 1) { set_error("gate must be 0 or 1"); return MLIP_ERR_INVALID_ARG; }
+  if (d->gate && d->channels < 32) { set_error("the gated update needs 32, 64 or 128 channels"); return MLIP_ERR_INVALID_ARG; }
   if (d->charges && !(d->coulomb_r0 > 0.0 && d->coulomb_r0 < 1e3)) {
     set_error("coulomb_r0 %g out of range (0, 1000)", d->coulomb_r0);
     return MLIP_ERR_INVALID_ARG;
@@ -156,6 +159,7 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
   M->P = P; M->P0 = P0; M->D = (M->L + 1) * (M->L + 1);
   M->corr = desc->correlation;
   M->charges = desc->charges;
+  M->gate = desc->gate;
   M->r0 = desc->coulomb_r0;
   M->Q = M->corr == 2 ? sc_num_paths(M->L) : 0;
   M->precision = precision;
@@ -177,6 +181,12 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
     if (M->corr == 2) {
       M->Wsc1.push_back(q); q += S * (M->L + 1) * C;
       M->Wsc2.push_back(q); q += S * M->Q * C;
+    }
+    if (M->gate) {
+      const int64_t LC = (int64_t)M->L * C;
+      M->Wself.push_back(q); q += S * (M->L + 1) * C * C;
+      M->Wgate.push_back(q); q += C * LC;
+      M->Wselfgate.push_back(q); q += S * C * LC;
     }
   }
   M->W_out = q; q += S * C;
@@ -203,6 +213,43 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
       return MLIP_ERR_OOM;
     }
     for (int t = 0; t < M->T; ++t) M->WmixT.push_back(M->d_wmixT + t * per);
+  }
+  if (M->gate) {  // transposed gate and self-connection weights for the adjoint; kernel limits
+    const int64_t LC = (int64_t)M->L * C, L1 = M->L + 1;
+    const size_t per = (size_t)(S * L1 * C * C + LC * C + S * LC * C);
+    std::vector<float> wt(per * M->T);
+    for (int t = 0; t < M->T; ++t) {
+      float* o = wt.data() + t * per;
+      const float* ws = M->host_weights.data() + (M->Wself[t] - M->d_weights);
+      const float* wg = M->host_weights.data() + (M->Wgate[t] - M->d_weights);
+      const float* wsg = M->host_weights.data() + (M->Wselfgate[t] - M->d_weights);
+      for (int64_t zl = 0; zl < S * L1; ++zl)
+        for (int64_t a = 0; a < C; ++a)
+          for (int64_t b = 0; b < C; ++b) o[zl * C * C + b * C + a] = ws[zl * C * C + a * C + b];
+      o += S * L1 * C * C;
+      for (int64_t a = 0; a < C; ++a)
+        for (int64_t b = 0; b < LC; ++b) o[b * C + a] = wg[a * LC + b];
+      o += LC * C;
+      for (int64_t z = 0; z < S; ++z)
+        for (int64_t a = 0; a < C; ++a)
+          for (int64_t b = 0; b < LC; ++b) o[z * LC * C + b * C + a] = wsg[z * C * LC + a * LC + b];
+    }
+    e = cudaMalloc(&M->d_gateT, sizeof(float) * wt.size());
+    if (e == cudaSuccess) e = cudaMemcpy(M->d_gateT, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("transposed gate weights: %s", cudaGetErrorString(e));
+      mlip_model_free(M);
+      return MLIP_ERR_OOM;
+    }
+    for (int t = 0; t < M->T; ++t) {
+      const float* base = M->d_gateT + t * per;
+      M->WselfT.push_back(base);
+      M->WgateT.push_back(base + S * L1 * C * C);
+      M->WselfgateT.push_back(base + S * L1 * C * C + LC * C);
+    }
+    const int rc = gate_prepare(M->L, C);
+    if (rc != MLIP_OK) { mlip_model_free(M); return rc; }
   }
   if (precision != MLIP_PREC_FP32) {
     std::vector<uint8_t> all, img;
@@ -298,7 +345,7 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
   if (!f) { set_error("cannot open '%s'", path); return MLIP_ERR_NOT_FOUND; }
   char magic[8];
   uint32_t version = 0;
-  int32_t hyper[8], corr = 0, charges = 0;
+  int32_t hyper[8], corr = 0, charges = 0, gate = 0;
   double dh[2], r0 = 0.0;
   f.read(magic, 8);
   f.read(reinterpret_cast<char*>(&version), 4);
@@ -307,6 +354,7 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
     f.read(reinterpret_cast<char*>(&corr), 4);
     f.read(reinterpret_cast<char*>(&charges), 4);
     f.read(reinterpret_cast<char*>(&r0), 8);
+    f.read(reinterpret_cast<char*>(&gate), 4);
   }
   f.read(reinterpret_cast<char*>(dh), sizeof(dh));
   if (!f || std::memcmp(magic, "MLIPPRM1", 8) != 0 || (version != 1 && version != 2)) { set_error("'%s' is not a parameter file", path); return MLIP_ERR_INVALID_ARG; }
@@ -319,7 +367,7 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
   std::vector<float> w(count);
   f.read(reinterpret_cast<char*>(w.data()), sizeof(float) * count);
   if (!f) { set_error("truncated parameter file"); return MLIP_ERR_INVALID_ARG; }
-  mlip_model_desc d{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dh[0], dh[1], masses.data(), corr, charges, r0};
+  mlip_model_desc d{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dh[0], dh[1], masses.data(), corr, charges, r0, gate};
   return mlip_model_create(&d, w.data(), count, precision, out);
 }
 
@@ -332,6 +380,7 @@ int mlip_model_free(mlip_model* M) {
   if (M->d_weights) cudaFree(M->d_weights);
   if (M->d_w3img) cudaFree(M->d_w3img);
   if (M->d_wmixT) cudaFree(M->d_wmixT);
+  if (M->d_gateT) cudaFree(M->d_gateT);
   if (M->d_miximg) cudaFree(M->d_miximg);
   if (M->d_radimg) cudaFree(M->d_radimg);
   if (M->d_embmax) cudaFree(M->d_embmax);
@@ -429,12 +478,16 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
   MLIP_TRY(ws.get("ef.dY", Ec * 16, &dY));
   MLIP_TRY(ws.get("ef.dr", Ec, &dr));
   MLIP_TRY(ws.get("ef.atom_e", (size_t)std::max(n, 1), &atom_e));
-  std::vector<float*> h(T + 1), u0(T), w(T), A(T, nullptr);
+  std::vector<float*> h(T + 1), u0(T), w(T), A(T, nullptr), gpre(T, nullptr), gg(T, nullptr);
   for (int t = 0; t <= T; ++t) MLIP_TRY(ws.get("ef.h" + std::to_string(t), ND, &h[t]));
   for (int t = 0; t < T; ++t) {
     MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
     MLIP_TRY(ws.get("ef.w" + std::to_string(t), Ec * (t == 0 ? P0 : P) * C, &w[t]));
     if (M->corr == 2) MLIP_TRY(ws.get("ef.A" + std::to_string(t), ND, &A[t]));
+    if (M->gate) {
+      MLIP_TRY(ws.get("ef.gpre" + std::to_string(t), ND, &gpre[t]));
+      MLIP_TRY(ws.get("ef.gg" + std::to_string(t), (size_t)std::max(n, 1) * L * C, &gg[t]));
+    }
   }
   double* energy = d_energy;
 
@@ -448,7 +501,11 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
     MLIP_TRY(launch_tp_fwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], w[t], PW, s, m, st));
     if (M->corr == 2)
       MLIP_TRY(launch_sym_contract(L, n, C, M->S, m, nullptr, d_species, M->Wsc1[t], M->Wsc2[t], A[t], m, st));
-    MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
+    if (M->gate)
+      MLIP_TRY(launch_gate_fwd(L, n, C, M->S, d_species, m, nullptr, h[t], M->Wmix[t], M->Wself[t], M->Wgate[t],
+                               M->Wselfgate[t], h[t + 1], gpre[t], gg[t], nullptr, nullptr, st));
+    else
+      MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
   }
   if (M->charges) {  // readout, charge head and Coulomb term, then the per-system sums
     MLIP_TRY(launch_readout(n, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, st));
@@ -465,7 +522,11 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
     for (int t = T - 1; t >= 0; --t) {
       const bool first = t == 0;
       const int PW = first ? P0 : P;
-      MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], M->WmixT[t], Gm, st));
+      if (M->gate)  // Gm = dE/dm; Ga becomes dE/dh^t's residual part (with the self-connection)
+        MLIP_TRY(launch_gate_bwd(L, n, C, M->S, d_species, Ga, nullptr, gpre[t], gg[t], M->WmixT[t], M->WselfT[t],
+                                 M->WgateT[t], M->WselfgateT[t], Gm, nullptr, nullptr, st));
+      else
+        MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], M->WmixT[t], Gm, st));
       if (M->corr == 2)
         MLIP_TRY(launch_sym_contract_bwd(L, n, C, M->S, Gm, A[t], d_species, M->Wsc1[t], M->Wsc2[t], Gm, nullptr, nullptr,
                                          st));

@@ -2031,12 +2031,16 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
   MLIP_TRY(ws.get("ef.m", ND, &mA));
   MLIP_TRY(ws.get("fz.m2", ND, &mB));
   MLIP_TRY(ws.get("ef.atom_e", (size_t)std::max(n, 1), &atom_e));
-  std::vector<float*> h(T + 1), u0(T), A(T, nullptr);
+  std::vector<float*> h(T + 1), u0(T), A(T, nullptr), gpre(T, nullptr), gg(T, nullptr);
   std::vector<uint8_t*> z2t(T);
   for (int t = 0; t <= T; ++t) MLIP_TRY(ws.get("ef.h" + std::to_string(t), ND, &h[t]));
   for (int t = 0; t < T; ++t) {
     MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
     if (M->corr == 2) MLIP_TRY(ws.get("ef.A" + std::to_string(t), ND, &A[t]));
+    if (M->gate) {
+      MLIP_TRY(ws.get("ef.gpre" + std::to_string(t), ND, &gpre[t]));
+      MLIP_TRY(ws.get("ef.gg" + std::to_string(t), (size_t)std::max(n, 1) * L * C, &gg[t]));
+    }
     MLIP_TRY(ws.get("fz.z2t" + std::to_string(t), (size_t)std::max(n_tiles, 1) * kTileBytes, &z2t[t]));
   }
   uint8_t* epar = nullptr;
@@ -2082,8 +2086,12 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
       MLIP_TRY(launch_sym_contract(L, n, C, M->S, mA, mB, d_species, M->Wsc1[t], M->Wsc2[t], A[t], mA, st));
       mB_mix = nullptr;
     }
-    MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB_mix, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
-                           nullptr, flag + 1, st, b.d_sys_of, amax_h(t + 1)));
+    if (M->gate)  // gated update with the species self-connection in place of the mix
+      MLIP_TRY(launch_gate_fwd(L, n, C, M->S, d_species, mA, mB_mix, h[t], M->Wmix[t], M->Wself[t], M->Wgate[t],
+                               M->Wselfgate[t], h[t + 1], gpre[t], gg[t], b.d_sys_of, amax_h(t + 1), st));
+    else
+      MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB_mix, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
+                             nullptr, flag + 1, st, b.d_sys_of, amax_h(t + 1)));
   }
   if (M->charges) {  // readout, charge head and Coulomb term, then the per-system sums
     MLIP_TRY(launch_readout(n, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, st));
@@ -2111,8 +2119,12 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     for (int t = T - 1; t >= 0; --t) {
       // max |dE/dm| of the message adjoint's input: from the mix, or from the contraction's adjoint
       float* gmax = use_bf16 ? nullptr : amax_h(t) + 1;
-      MLIP_TRY(launch_mix_tc(true, n, C, L, GaA, GaB, M->mix_bwd_img[t], M->mix_scale[t], nullptr, Gm, nullptr,
-                             u0[t], flag + 1, st, b.d_sys_of, M->corr == 2 ? nullptr : gmax));
+      if (M->gate)  // Gm = dE/dm; GaA <- dE/dh^t's residual part (with the self-connection), GaB <- 0
+        MLIP_TRY(launch_gate_bwd(L, n, C, M->S, d_species, GaA, GaB, gpre[t], gg[t], M->WmixT[t], M->WselfT[t],
+                                 M->WgateT[t], M->WselfgateT[t], Gm, b.d_sys_of, M->corr == 2 ? nullptr : gmax, st));
+      else
+        MLIP_TRY(launch_mix_tc(true, n, C, L, GaA, GaB, M->mix_bwd_img[t], M->mix_scale[t], nullptr, Gm, nullptr,
+                               u0[t], flag + 1, st, b.d_sys_of, M->corr == 2 ? nullptr : gmax));
       if (M->corr == 2)
         MLIP_TRY(launch_sym_contract_bwd(L, n, C, M->S, Gm, A[t], d_species, M->Wsc1[t], M->Wsc2[t], Gm, b.d_sys_of, gmax,
                                          st));

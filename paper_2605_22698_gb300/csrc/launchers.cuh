@@ -139,4 +139,17 @@ int coulomb_add_forces(Workspace& ws, const SystemBatch& b, double* forces, cuda
 // the corrected charges of the last coulomb_forward ([n] FP64, device)
 int coulomb_charges(Workspace& ws, const SystemBatch& b, double** q);
 
+// Gated update with the species self-connection (gate.cu), replacing the
+// channel mix for models with gate = 1: forward h_out from the messages
+// X (+ X2) and h_in, keeping pre [n][D][C] and the gate pre-activations
+// g [n][L C]; adjoint from G (+ G2) = dE/dh': Gm = dE/dm, and in place
+// G <- dE/dh (G2 <- 0).  out_max (nullable): per-system max |h_out| or |Gm|.
+int gate_prepare(int L, int C);
+int launch_gate_fwd(int L, int n, int C, int S, const int* species, const float* X, const float* X2,
+                    const float* hin, const float* Wm, const float* Ws, const float* Wg, const float* Wsg,
+                    float* hout, float* pre, float* g, const int* sys_of, float* out_max, cudaStream_t st);
+int launch_gate_bwd(int L, int n, int C, int S, const int* species, float* G, float* G2, const float* pre,
+                    const float* g, const float* WmT, const float* WsT, const float* WgT, const float* WsgT,
+                    float* Gm, const int* sys_of, float* out_max, cudaStream_t st);
+
 }  // namespace mlip

@@ -219,6 +219,11 @@ struct mlip_model {
   double r0 = 0.0;
   const float* W_q = nullptr;
   const float* q0 = nullptr;
+  // gated update (gate = 1): Wself [S][L+1][C][C], Wgate [C][L C], Wselfgate [S][C][L C] per layer,
+  // and their transposes for the adjoint ([S][L+1][c2][c1], [L C][C], [S][L C][C])
+  int gate = 0;
+  std::vector<const float*> Wself, Wgate, Wselfgate, WselfT, WgateT, WselfgateT;
+  float* d_gateT = nullptr;
   float* d_wmixT = nullptr;            // channel-mix weights transposed, per layer and order
   std::vector<const float*> WmixT;
   // fused form: split FP16 tensor-core images of the mix weights per layer

@@ -83,7 +83,7 @@ class ModelSpec:
     correlation: int = 0  # 0: no symmetric contraction; 2: MACE's of correlation order 2
     charges: int = 0      # 1: charge head + charge correction + Coulomb term (open systems)
     coulomb_r0: float = 0.0  # soft-core radius of the Coulomb term, A (charges = 1)
-    gate: int = 0         # 1: species self-connection and gated update of the l > 0 features (oracle only)
+    gate: int = 0         # 1: species self-connection and gated update of the l > 0 features
 
     @property
     def hyper(self) -> np.ndarray:
@@ -154,6 +154,7 @@ def model_spec(name: str) -> ModelSpec:
     fcc     2 layers, 128 channels, l <= 3, hidden 64, 2 species
     <name>_mace  the same with the symmetric contraction of correlation order 2
                  after every scatter-sum (Table tbl:mace_params: correlation 2)
+    <name>_gated  the same with the gated update and the species self-connection
     <name>_charged  the same with a charge head, the charge correction and the
                  soft-core Coulomb term (Eqs. charge_correction, long_range_interaction)
     """
@@ -165,6 +166,8 @@ def model_spec(name: str) -> ModelSpec:
         return ModelSpec(S=2, T=2, C=128, L=3, H=64, avg_nb=42.0, masses=(63.546, 58.693))
     if name.endswith("_mace"):  # the same model with the symmetric contraction of correlation order 2
         return dataclasses.replace(model_spec(name[:-5]), correlation=2)
+    if name.endswith("_gated"):  # the same model with the gated update and the species self-connection
+        return dataclasses.replace(model_spec(name[:-6]), gate=1)
     if name.endswith("_charged"):  # the same model with the charge head and the Coulomb term (r0 = rc / 2)
         base = model_spec(name[:-8])
         return dataclasses.replace(base, charges=1, coulomb_r0=0.5 * base.rc)
@@ -198,18 +201,18 @@ PARAMS_MAGIC = b"MLIPPRM1"
 
 def write_params(path: str, spec: ModelSpec, w: np.ndarray) -> None:
     """Parameter file: magic, u32 version, 8 x i32 hyper, (version 2 only:
-    i32 correlation, i32 charges, f64 coulomb_r0), 2 x f64 (rc, avg_nb),
-    S x f64 masses, i64 count, count x f32 weights; little-endian.  Version 1
-    for models with neither the symmetric contraction nor the charge head."""
+    i32 correlation, i32 charges, f64 coulomb_r0, i32 gate), 2 x f64 (rc,
+    avg_nb), S x f64 masses, i64 count, count x f32 weights; little-endian.
+    Version 1 for models with none of the contraction, charge head or gate."""
     w = np.ascontiguousarray(w, dtype=np.float32)
     assert w.size == spec.n_weights()
-    v2 = bool(spec.correlation or spec.charges)
+    v2 = bool(spec.correlation or spec.charges or spec.gate)
     with open(path, "wb") as f:
         f.write(PARAMS_MAGIC)
         f.write(struct.pack("<I", 2 if v2 else 1))
         f.write(spec.hyper.astype("<i4").tobytes())
         if v2:
-            f.write(struct.pack("<iid", spec.correlation, spec.charges, spec.coulomb_r0))
+            f.write(struct.pack("<iidi", spec.correlation, spec.charges, spec.coulomb_r0, spec.gate))
         f.write(spec.dhyper.astype("<f8").tobytes())
         f.write(np.asarray(spec.masses, dtype="<f8").tobytes())
         f.write(struct.pack("<q", w.size))

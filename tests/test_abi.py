@@ -27,7 +27,7 @@ def test_exports_every_declared_symbol(lib):
 
 def test_num_weights_matches_generator(lib):
     for name in ("small", "water", "fcc", "small_mace", "water_mace", "fcc_mace", "small_charged", "water_charged",
-                 "water_mace_charged"):
+                 "water_mace_charged", "water_gated", "fcc_gated", "water_mace_gated"):
         spec = synth.model_spec(name)
         assert lib.mlip_model_num_weights(lib.make_desc(spec)) == spec.n_weights()
 
@@ -61,7 +61,7 @@ _LAYOUT_C = r"""
 #define Z(T) printf(#T " sizeof %zu\n", sizeof(T));
 int main(void) {
   F(mlip_model_desc, cutoff) F(mlip_model_desc, masses) F(mlip_model_desc, correlation)
-  F(mlip_model_desc, charges) F(mlip_model_desc, coulomb_r0) Z(mlip_model_desc)
+  F(mlip_model_desc, charges) F(mlip_model_desc, coulomb_r0) F(mlip_model_desc, gate) Z(mlip_model_desc)
   F(mlip_serve_config, max_slots) F(mlip_serve_config, bucket_edges) F(mlip_serve_config, device_poll_limit_us)
   Z(mlip_serve_config)
   F(mlip_request, n) F(mlip_request, pos) F(mlip_request, cell) F(mlip_request, pbc) F(mlip_request, vel)
