@@ -143,21 +143,21 @@ def max_over_ranks(t: float, world: int) -> float:
     return float(tt.item())
 
 
-def _with_contraction(spec_w_s, name):
+def _with_option(spec_w_s, name):
     """The same workload on the model with the symmetric contraction of
-    correlation order 2 after every scatter-sum (suffix _mace)."""
+    correlation order 2 after every scatter-sum (suffix _mace) or with the
+    gated update and species self-connection (suffix _gated)."""
     import dataclasses
-    if not name.endswith("_mace"):
-        return spec_w_s
+    base, opt = name.rsplit("_", 1)
     spec, _, *rest = spec_w_s
-    spec = dataclasses.replace(spec, correlation=2)
-    seed = {"water3000": 21, "fcc108k": 31}[name[:-5]]
+    spec = dataclasses.replace(spec, **({"correlation": 2} if opt == "mace" else {"gate": 1}))
+    seed = {"water3000": 21, "fcc108k": 31}[base]
     return (spec, synth.make_weights(spec, seed), *rest)
 
 
 def workload(name: str, rank: int = 0, fcc_cells: int = 30):
-    if name.endswith("_mace"):
-        return _with_contraction(workload(name[:-5], rank, fcc_cells), name)
+    if name.endswith(("_mace", "_gated")):
+        return _with_option(workload(name.rsplit("_", 1)[0], rank, fcc_cells), name)
     if name == "water3000":
         spec = synth.model_spec("water")
         sysm = synth.water_box(1000, 31.0, seed=2 + 1000 * rank)
@@ -177,8 +177,8 @@ def workload(name: str, rank: int = 0, fcc_cells: int = 30):
 
 def sample_workload(name: str):
     """Bounded CPU sample of the same workload for the oracle baseline."""
-    if name.endswith("_mace"):
-        return _with_contraction(sample_workload(name[:-5]), name)
+    if name.endswith(("_mace", "_gated")):
+        return _with_option(sample_workload(name.rsplit("_", 1)[0]), name)
     if name == "water3000":
         spec = synth.model_spec("water")
         return spec, synth.make_weights(spec, 21), synth.water_box(100, synth.water_side_for(100), seed=2), \
@@ -410,6 +410,19 @@ def run_ours(args, rank, world):
                                   "frac": round(gbs / peaks()["hbm_gbs"], 4),
                                   "traffic": NCU_TRAFFIC_SC.get((args.workload, args.precision, kname))
                                   if args.fcc_cells == 30 else None}
+    # the gated update's kernels (FP32 ALUs): 4 C^2 (D + L) flops per node and launch, each direction
+    gate_roof = None
+    if "gate_fwd" in share_rep:
+        D_ = (spec.L + 1) ** 2
+        flop = 4.0 * spec.C * spec.C * (D_ + spec.L) * s.n
+        gate_roof = {}
+        for kname in ("gate_fwd", "gate_bwd"):
+            nl_, tot_ = share_rep.get(kname, (0, 0.0))
+            if nl_:
+                tf = flop / (tot_ / nl_ / 1e3) / 1e12
+                gate_roof[kname] = {"bound": "alu", "flops_per_launch": flop, "avg_launch_ms": round(tot_ / nl_, 5),
+                                    "achieved": round(tf, 2), "peak": round(FP32_ALU_TFLOPS, 1), "unit": "TFLOP/s",
+                                    "frac": round(tf / FP32_ALU_TFLOPS, 4)}
     # the Coulomb term (models with charges): pair evaluations per second of its all-pairs kernel
     coul = None
     if "coulomb_pairs" in share_rep:
@@ -455,13 +468,15 @@ def run_ours(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32", "f16": "f16 tensor-core MLP + f32"}[args.precision],
         "data": "synthetic", "impl": "ours",
         "config": {"workload": args.workload, "atoms": s.n, "edges": E_edges,
-                   "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}" + (" SC2" if spec.correlation else ""),
+                   "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}" + (" SC2" if spec.correlation else "")
+                   + (" gated" if spec.gate else ""),
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (512 MB write)", "stress": stress},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernel_share": share,
         "kernel_ms_per_step": round(tot_all / n_share, 4),
         "sym_contract_roofline": sc_roof,
         "coulomb": coul,
+        "gate_roofline": gate_roof,
         "timing": "timed steps: CUDA events around the dominant kernel's launches only (graph event nodes); "
                   "kernel_share from 4 steps with every kernel timed, outside the timed region",
         "plain_fp32": plain,
@@ -719,7 +734,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water3000", choices=["water3000", "fcc108k", "cluster64", "serve", "md64",
                                                                  "water3000_mace", "fcc108k_mace",
-                                                                 "cluster5000_charged"])
+                                                                 "cluster5000_charged", "water3000_gated", "fcc108k_gated"])
     ap.add_argument("--precision", default="f16", choices=["fp32", "bf16", "f16"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form beside the headline")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")
