@@ -67,6 +67,7 @@ def lib():
         L.oracle_charges.argtypes = [P, P, P, i64, P]
         L.oracle_coulomb.argtypes = [P, P, i64, f64, P, P, P]
         L.oracle_inv_chi.argtypes = [f64, f64]
+        L.oracle_hessian_row.argtypes = [P, P, P, i64, P, P, i64, i32, P]
         L.oracle_inv_chi.restype = f64
         L.oracle_sym_contract.argtypes = [i32, i32, P, P, P, P]
         L.oracle_sym_contract_adjoint.argtypes = [i32, i32, P, P, P, P, P]
@@ -280,6 +281,17 @@ class Model:
         if rc != 0:
             raise ValueError("oracle_energy_dual failed")
         return float(E[0]), float(dE[0])
+
+    def hessian_row(self, pos, species, cell, pbc, atom: int, axis: int) -> np.ndarray:
+        """d2E / dr_{atom,axis} dr_{j,b} for every atom j and axis b: [n, 3]."""
+        pos = _c(pos, np.float64); species = _c(species, np.int32)
+        cell = _c(cell, np.float64); pbc = _c(pbc, np.uint8)
+        out = np.zeros((pos.shape[0], 3))
+        rc = lib().oracle_hessian_row(self._h, _p(pos), _p(species), pos.shape[0], _p(cell), _p(pbc), atom, axis,
+                                      _p(out))
+        if rc != 0:
+            raise ValueError("oracle_hessian_row failed")
+        return out
 
     def vv_nve(self, pos, vel, species, masses, cell, pbc, dt: float, n_steps: int):
         pos = np.array(pos, dtype=np.float64, copy=True); vel = np.array(vel, dtype=np.float64, copy=True)

@@ -63,6 +63,37 @@ inline double val(double x) { return x; }
 inline double val(Dual x) { return x.v; }
 using std::sqrt; using std::sin; using std::exp;
 
+// Hyper-dual numbers v + a e1 + b e2 + ab e1 e2 (e1^2 = e2^2 = 0): one pass of
+// the templated energy with e1 on coordinate x and e2 on coordinate y gives
+// d2E / dx dy exactly in the ab part (forward-over-forward, for the Hessian).
+struct HDual {
+  double v, a, b, ab;
+  HDual() : v(0), a(0), b(0), ab(0) {}
+  HDual(double x) : v(x), a(0), b(0), ab(0) {}
+  HDual(double x, double da, double db, double dab) : v(x), a(da), b(db), ab(dab) {}
+};
+// f(x) for a unary function with value f0 and derivatives f1, f2 at x.v
+inline HDual chain(const HDual& x, double f0, double f1, double f2) {
+  return {f0, f1 * x.a, f1 * x.b, f1 * x.ab + f2 * x.a * x.b};
+}
+inline HDual operator+(HDual x, HDual y) { return {x.v + y.v, x.a + y.a, x.b + y.b, x.ab + y.ab}; }
+inline HDual operator-(HDual x, HDual y) { return {x.v - y.v, x.a - y.a, x.b - y.b, x.ab - y.ab}; }
+inline HDual operator-(HDual x) { return {-x.v, -x.a, -x.b, -x.ab}; }
+inline HDual operator*(HDual x, HDual y) {
+  return {x.v * y.v, x.a * y.v + x.v * y.a, x.b * y.v + x.v * y.b, x.ab * y.v + x.a * y.b + x.b * y.a + x.v * y.ab};
+}
+inline HDual operator/(HDual x, HDual y) {
+  const double iv = 1.0 / y.v;
+  return x * chain(y, iv, -iv * iv, 2.0 * iv * iv * iv);
+}
+inline HDual& operator+=(HDual& x, HDual y) { x = x + y; return x; }
+inline HDual& operator-=(HDual& x, HDual y) { x = x - y; return x; }
+inline HDual& operator*=(HDual& x, HDual y) { x = x * y; return x; }
+inline HDual sqrt(HDual x) { const double s = std::sqrt(x.v); return chain(x, s, 0.5 / s, -0.25 / (s * x.v)); }
+inline HDual sin(HDual x) { return chain(x, std::sin(x.v), std::cos(x.v), -std::sin(x.v)); }
+inline HDual exp(HDual x) { const double e = std::exp(x.v); return chain(x, e, e, e); }
+inline double val(HDual x) { return x.v; }
+
 double factorial(int n) {
   double f = 1.0;
   for (int k = 2; k <= n; ++k) f *= k;
@@ -1236,6 +1267,33 @@ int oracle_energy_dual(void* model, const double* pos, const int32_t* species, i
   Dual E = model_energy<Dual>(M, edges, rp, p.data(), sp.data(), (int)n, cl, nullptr, nullptr, nullptr);
   *energy = E.v;
   *dE = E.d;
+  return 0;
+}
+
+// Row (atom, axis) of the Hessian d2E / dr_{atom,axis} dr_{j,b} for every j, b
+// (out [n][3]), one hyper-dual pass per column; the edge set is fixed at the
+// given positions.  -dF_j,b / dr_atom,axis by symmetry: the subsampled Hessian
+// rows of Eq. sampled_hessian2 for one graph.
+int oracle_hessian_row(void* model, const double* pos, const int32_t* species, int64_t n, const double* cell,
+                       const uint8_t* pbc, int64_t atom, int axis, double* out) {
+  const Model& M = *static_cast<Model*>(model);
+  bool anyp = pbc[0] || pbc[1] || pbc[2];
+  if (M.hp.charges && anyp) return -3;
+  double zero[9] = {0};
+  uint8_t np[3] = {0, 0, 0};
+  const double* cl = anyp ? cell : zero;
+  std::vector<Edge> edges;
+  if (brute_neighbors(pos, (int)n, cl, anyp ? pbc : np, M.hp.rc, edges) != 0) return -1;
+  std::vector<int> rp = receiver_row_ptr(edges, (int)n);
+  std::vector<int> sp(species, species + n);
+  const int64_t row = 3 * atom + axis;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t col = 0; col < 3 * n; ++col) {
+    std::vector<HDual> p(3 * n);
+    for (int64_t k = 0; k < 3 * n; ++k) p[k] = HDual(pos[k], k == row ? 1.0 : 0.0, k == col ? 1.0 : 0.0, 0.0);
+    HDual E = model_energy<HDual>(M, edges, rp, p.data(), sp.data(), (int)n, cl, nullptr, nullptr, nullptr);
+    out[col] = E.ab;
+  }
   return 0;
 }
 
