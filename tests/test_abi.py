@@ -93,3 +93,29 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
         T = getattr(lib, tname)
         got = ctypes.sizeof(T) if field == "sizeof" else getattr(T, field).offset
         assert got == int(val), (tname, field, got, val)
+
+
+def test_params_file_version_2_header(tmp_path):
+    """Models with the contraction, the charge head or the gate are written as
+    version 2: after the 8 hyperparameters, i32 correlation, i32 charges,
+    f64 coulomb_r0, i32 gate, then rc and avg_nb as in version 1."""
+    import struct
+    spec = synth.model_spec("water_mace_charged")
+    import dataclasses
+    spec = dataclasses.replace(spec, gate=1)
+    w = synth.make_weights(spec, 2)
+    p = tmp_path / "v2.bin"
+    synth.write_params(str(p), spec, w)
+    raw = p.read_bytes()
+    assert raw[:8] == b"MLIPPRM1" and struct.unpack_from("<I", raw, 8)[0] == 2
+    assert list(struct.unpack_from("<8i", raw, 12)) == list(spec.hyper)
+    corr, charges, r0, gate = struct.unpack_from("<iidi", raw, 44)
+    assert (corr, charges, r0, gate) == (2, 1, 2.5, 1)
+    rc, avg = struct.unpack_from("<2d", raw, 64)
+    assert (rc, avg) == (spec.rc, spec.avg_nb)
+    assert struct.unpack_from("<q", raw, 80 + 8 * spec.S)[0] == w.size == spec.n_weights()
+    # version 1 for the plain model
+    plain = synth.model_spec("small")
+    q = tmp_path / "v1.bin"
+    synth.write_params(str(q), plain, synth.make_weights(plain, 1))
+    assert struct.unpack_from("<I", q.read_bytes(), 8)[0] == 1
