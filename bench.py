@@ -1,19 +1,26 @@
 #!/usr/bin/env python
 """Benchmark: energy+force atom-steps/s of the equivariant interaction layer.
 
-Workload (default): a periodic water-like box, 1000 H2O = 3000 atoms in a
-31.0 A cube (random orientations, O-O >= 2.5 A), the two-layer, 128-channel,
-l <= 2 model with l <= 3 edge harmonics and a 64-wide radial MLP (random
-weights).  One step = one full evaluation through the library's C ABI with the
-positions resident on the GPU: neighbour list (cell list), edge geometry,
-harmonics, radial basis and MLP, tensor product and segmented sum, channel
-mixes, readout and FP64 energy, then the adjoint: forces and virial stress.
-The synthetic box stands in for the paper's MD benchmark systems (Table
+Default workload (the metric's configuration): a periodic FCC cell of
+30 x 30 x 30 conventional cells (108,000 atoms, a = 3.6 A, Gaussian
+displacements of 0.1 A, two species 50/50), the two-layer, 128-channel,
+l <= 3 model with l <= 3 edge harmonics and a 64-wide radial MLP (random
+weights), in the FP16-operand tensor-core form, with the plain FP32 GPU form
+timed beside it.  One step = one full evaluation through the library's C ABI
+with the positions resident on the GPU: neighbour list (cell list), edge
+geometry, harmonics, radial basis and MLP, tensor product and segmented sum,
+channel mixes, readout and FP64 energy, then the adjoint: forces and virial
+stress.  The same line carries the 3000-atom water box (1000 H2O in a 31.0 A
+cube) and a bounded serving phase (requests of 8-5000 atoms, 70 % energy+forces
+and 30 % 100-step NVE, Poisson arrivals; p50/p99 latency) as sub-objects.
+The synthetic systems stand in for the paper's MD benchmark systems (Table
 tbl:performance), which are not available here.
 
 Between timed steps L2 is flushed by writing a 512 MB buffer (outside the
 per-step CUDA-event pairs).  --impl reference times the FP64 CPU oracle on a
-bounded sample of the same workload on the host cores.
+bounded sample of the same workload on the host cores.  --gpus N runs N
+independent replicas, one process per GPU (launched through
+torch.distributed.run when the environment holds no rank).
 """
 from __future__ import annotations
 
@@ -48,16 +55,37 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of the same code (profiles/tp_fused_bwd_water3000.md: mean over the
-# four path-group launches of one evaluation), keyed by (workload, precision,
-# kernel).
-NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): 129.7e6}
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture, keyed by
+# (workload, precision, kernel), with the SHA-256 prefix of the source file the
+# kernel was built from at capture time.  When the file has changed since, the
+# counters no longer describe the running kernel and the roofline reports no
+# traffic.
+NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): (129.7e6, "fused_bf16.cu", None)}
 # DRAM bytes per launch of the symmetric contraction's kernels at fcc108k: captured on the
 # 20^3-cell FCC (32,000 atoms; the full workload is too large for a capture) and scaled by the
 # atom count (traffic grows in proportion: per-node tensors)
-NCU_TRAFFIC_SC = {("fcc108k_mace", "f16", "sym_contract"): 991.3e6 * 108000 / 32000,
-                  ("fcc108k_mace", "f16", "sym_contract_bwd"): 741.2e6 * 108000 / 32000}
+NCU_TRAFFIC_SC = {("fcc108k_mace", "f16", "sym_contract"): (991.3e6 * 108000 / 32000, "sym_contract.cu", None),
+                  ("fcc108k_mace", "f16", "sym_contract_bwd"): (741.2e6 * 108000 / 32000, "sym_contract.cu", None)}
+
+
+def _src_digest(fname: str) -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2605_22698_gb300", "csrc", fname), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_of(table, key):
+    """Captured DRAM bytes per launch, or None when unknown or when the kernel's
+    source changed since the capture (digest None: captured before digests were
+    recorded, so it cannot be shown to describe this build)."""
+    ent = table.get(key)
+    if not ent:
+        return None
+    nbytes, fname, digest = ent
+    if digest is None or _src_digest(fname) != digest:
+        return None
+    return nbytes
+
 
 # FP32 ALU peak from unit counts and the maximum SM clock: 152 SMs x 128 FP32
 # lanes x 2 flop (FMA) x 2.07 GHz.
@@ -279,15 +307,40 @@ def algorithmic_flops(spec, E: int, n: int):
     }
 
 
-def run_ours(args, rank, world):
+def measure_fp32_peak():
+    """FP32 FMA rate measured on this GPU by the library's microbenchmark, with
+    the SM clock sampled while it runs; the derived figure if it fails."""
     import torch
     from paper_2605_22698_gb300 import binding as B
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    try:
+        B.mlip_fp32_fma_rate(2000)  # warm-up
+        runs = [B.mlip_fp32_fma_rate(20000) for _ in range(5)]
+    except Exception as e:  # noqa: BLE001
+        sampler.stop()
+        return {"tflops": FP32_ALU_TFLOPS, "src": f"derived (measurement failed: {e})"}
+    clocks = sampler.stop()
+    best = max(runs, key=lambda r: r["tflops"])
+    return {"tflops": round(best["tflops"], 2), "sms": best["sms"], "ms": round(best["ms"], 3),
+            "src": (f"measured: FP32 FMA microbenchmark (independent FMA chains filling all {best['sms']} SMs), "
+                    "best of 5 launches, CUDA events"),
+            "clocks": clocks, "derived_at_max_clock": round(FP32_ALU_TFLOPS, 1)}
+
+
+def measure(args, rank, world, name, steps, warmup, fp32_peak, plain=True, cpu=True, fcc_cells=30):
+    """One workload through mlip_energy_forces: the timed device steps, the
+    end-to-end steps with host arrays, the dominant kernel's roofline, the
+    kernel shares and (optionally) the plain FP32 form and the oracle."""
+    import torch
+    from paper_2605_22698_gb300 import binding as B
     dev = torch.device("cuda", torch.cuda.current_device())
-    spec, w, s = workload(args.workload, rank, args.fcc_cells)
+    spec, w, s = workload(name, rank, fcc_cells)
+    precision = args.precision
     if spec.C != 128 or spec.H != 64:
-        args.precision = "fp32"  # the fused 16-bit form serves 128-channel, hidden-64 models only
-    prec = {"fp32": B.MLIP_PREC_FP32, "bf16": B.MLIP_PREC_BF16, "f16": B.MLIP_PREC_F16}[args.precision]
+        precision = "fp32"  # the fused 16-bit form serves 128-channel, hidden-64 models only
+    prec = {"fp32": B.MLIP_PREC_FP32, "bf16": B.MLIP_PREC_BF16, "f16": B.MLIP_PREC_F16}[precision]
     model = B.Model(spec, w, prec)
     pos = torch.tensor(s.pos, device=dev)
     sp = torch.tensor(s.species, device=dev)
@@ -302,7 +355,7 @@ def run_ours(args, rank, world):
     def step():
         model.energy_forces(pos, sp, s.cell, s.pbc, forces=True, stress=stress, stream=stream, out=out)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     # kernel shares: every kernel timed, on steps outside the timed region (the
     # evaluation is a replayed CUDA graph after three calls with one layout and
@@ -331,9 +384,9 @@ def run_ours(args, rank, world):
         time.sleep(0.3)
     B.mlip_profile_enable(True)  # clears the records
     launches0 = B.mlip_launch_count()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     t_wall0 = time.perf_counter()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         evs[k][0].record(stream)
         step()
@@ -348,10 +401,11 @@ def run_ours(args, rank, world):
     clocks = sampler.stop() if sampler else None
     ms = [a.elapsed_time(b) for a, b in evs]
     t_dev = max_over_ranks(sum(ms) / 1e3, world)
-    value = world * s.n * args.steps / t_dev
+    value = world * s.n * steps / t_dev
     # edge count of this structure (for the algorithmic counts)
     r, _, _ = B.mlip_neighbors(np.ascontiguousarray(s.pos), s.cell, s.pbc, spec.rc)
     E_edges = len(r)
+    del r
 
     # end-to-end: host arrays in pinned memory, copies inside the timed region
     pin_pos = torch.empty((s.n, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -360,46 +414,46 @@ def run_ours(args, rank, world):
     pin_sp[:] = s.species
     for _ in range(4):  # past the graph capture
         model.energy_forces(pin_pos, pin_sp, s.cell, s.pbc, forces=True, stress=stress)
-    k_e2e = max(3, args.steps // 2)
+    k_e2e = max(3, steps // 2)
+    barrier(world)
     t0 = time.perf_counter()
     for _ in range(k_e2e):
         res = model.energy_forces(pin_pos, pin_sp, s.cell, s.pbc, forces=True, stress=stress)
         _ = float(res["energy"][0])
-    t_e2e = time.perf_counter() - t0
-    e2e = {"value": world * s.n * k_e2e / t_e2e, "unit": UNIT,
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": round(world * s.n * k_e2e / t_e2e, 1), "unit": UNIT,
            "h2d_bytes_per_step": int(pin_pos.nbytes + pin_sp.nbytes),
-           "d2h_bytes_per_step": int(8 + s.n * 3 * 8 + (72 if stress else 0))}
+           "d2h_bytes_per_step": int(8 + s.n * 3 * 8 + (72 if stress else 0)), "steps": k_e2e}
 
     # roofline of the dominant kernel
+    peak = fp32_peak["tflops"]
     kern = prof.get("kernels", {})
     roof = None
     if kern:
         top = max(kern.items(), key=lambda kv: kv[1][1])
-        name, (nl, tot_ms) = top
+        kname, (nl, tot_ms) = top
         flops = algorithmic_flops(spec, E_edges, s.n)
-        if name in flops:
-            per_step = flops[name]
-            achieved = per_step * args.steps / (tot_ms / 1e3) / 1e12
-            roof = {"kernel": name, "bound": "alu", "achieved": round(achieved, 3), "peak": round(FP32_ALU_TFLOPS, 1),
-                    "unit": "TFLOP/s", "frac": round(achieved / FP32_ALU_TFLOPS, 4),
-                    "traffic": NCU_TRAFFIC.get((args.workload, args.precision, name)),
-                    "launches": nl, "avg_launch_ms": round(tot_ms / nl, 5),
-                    "peak_src": "FP32 ALU: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived, not measured)"}
-            if name in ("tp_fused", "tp_fused_bwd"):
-                tk = "tensor_" + name[3:]
-                tens = flops[tk] * args.steps / (tot_ms / 1e3) / 1e12
+        roof = {"kernel": kname, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "launches": nl, "avg_launch_ms": round(tot_ms / nl, 5),
+                "peak_src": fp32_peak["src"] + " (of measured)"}
+        if kname in flops:
+            per_step = flops[kname]
+            achieved = per_step * steps / (tot_ms / 1e3) / 1e12
+            nl_step = max(1, round(nl / steps))
+            roof.update({"achieved": round(achieved, 3), "frac": round(achieved / peak, 4),
+                         "flops_per_launch": round(per_step / nl_step),
+                         "traffic": traffic_of(NCU_TRAFFIC, (name, precision, kname))})
+            if kname in ("tp_fused", "tp_fused_bwd"):
+                tk = "tensor_" + kname[3:]
+                tens = flops[tk] * steps / (tot_ms / 1e3) / 1e12
                 roof["tensor_pipe"] = {"achieved": round(tens, 2), "peak": peaks()["bf16_tflops"],
                                        "frac": round(tens / peaks()["bf16_tflops"], 4), "unit": "TFLOP/s"}
-        else:
-            roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": round(FP32_ALU_TFLOPS, 1),
-                    "unit": "TFLOP/s", "frac": None, "traffic": None, "launches": nl,
-                    "avg_launch_ms": round(tot_ms / nl, 5)}
     # the symmetric contraction's kernels (node-wise, bound by memory): algorithmic bytes per launch
     # over their mean launch time in the shares pass
     sc_roof = None
     if "sym_contract" in share_rep:
         nodes = s.n * (spec.L + 1) ** 2 * spec.C * 4
-        n_in = 2 if args.precision != "fp32" else 1  # the fused form's two partial message buffers
+        n_in = 2 if precision != "fp32" else 1  # the fused form's two partial message buffers
         sc_roof = {}
         for kname, nbytes in (("sym_contract", (n_in + 2) * nodes), ("sym_contract_bwd", 3 * nodes)):
             nl_, tot_ = share_rep.get(kname, (0, 0.0))
@@ -408,8 +462,8 @@ def run_ours(args, rank, world):
                 sc_roof[kname] = {"bound": "hbm", "bytes_per_launch": int(nbytes), "avg_launch_ms": round(tot_ / nl_, 5),
                                   "achieved": round(gbs, 1), "peak": peaks()["hbm_gbs"], "unit": "GB/s",
                                   "frac": round(gbs / peaks()["hbm_gbs"], 4),
-                                  "traffic": NCU_TRAFFIC_SC.get((args.workload, args.precision, kname))
-                                  if args.fcc_cells == 30 else None}
+                                  "traffic": traffic_of(NCU_TRAFFIC_SC, (name, precision, kname))
+                                  if fcc_cells == 30 else None}
     # the gated update's kernels (FP32 ALUs): 4 C^2 (D + L) flops per node and launch, each direction
     gate_roof = None
     if "gate_fwd" in share_rep:
@@ -421,8 +475,8 @@ def run_ours(args, rank, world):
             if nl_:
                 tf = flop / (tot_ / nl_ / 1e3) / 1e12
                 gate_roof[kname] = {"bound": "alu", "flops_per_launch": flop, "avg_launch_ms": round(tot_ / nl_, 5),
-                                    "achieved": round(tf, 2), "peak": round(FP32_ALU_TFLOPS, 1), "unit": "TFLOP/s",
-                                    "frac": round(tf / FP32_ALU_TFLOPS, 4)}
+                                    "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
+                                    "frac": round(tf / peak, 4)}
     # the Coulomb term (models with charges): pair evaluations per second of its all-pairs kernel
     coul = None
     if "coulomb_pairs" in share_rep:
@@ -435,42 +489,49 @@ def run_ours(args, rank, world):
     tot_all = sum(v[1] for v in share_rep.values()) or 1.0
     for k_, v in sorted(share_rep.items(), key=lambda kv: -kv[1][1])[:8]:
         share[k_] = round(v[1] / tot_all, 4)
+    model.close()
+    del model
 
     # the plain FP32 form on the same workload, reported beside the headline form
-    plain = None
-    if args.precision != "fp32" and not args.no_plain:
+    plain_line = None
+    if plain and precision != "fp32":
         pm = B.Model(spec, w, B.MLIP_PREC_FP32)
 
         def pstep():
             pm.energy_forces(pos, sp, s.cell, s.pbc, forces=True, stress=stress, stream=stream, out=out)
         for _ in range(3):
             pstep()
-        kp = max(5, args.steps // 4)
+        kp = max(5, steps // 4)
         pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kp)]
+        barrier(world)
         for k in range(kp):
             flush.zero_()
             pev[k][0].record(stream)
             pstep()
             pev[k][1].record(stream)
         torch.cuda.synchronize()
-        tp = sum(a.elapsed_time(b) for a, b in pev) / 1e3
-        plain = {"precision": "fp32", "value": round(world * s.n * kp / tp, 1), "unit": UNIT, "steps": kp,
-                 "ms_per_step": round(1e3 * tp / kp, 4)}
+        tp = max_over_ranks(sum(a.elapsed_time(b) for a, b in pev) / 1e3, world)
+        plain_line = {"precision": "fp32", "value": round(world * s.n * kp / tp, 1), "unit": UNIT, "steps": kp,
+                      "ms_per_step": round(1e3 * tp / kp, 4), "speedup_of_headline_form": round(value / (world * s.n * kp / tp), 3)}
         pm.close()
+        del pm
+    del flush
+    torch.cuda.empty_cache()
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = time_oracle(args.workload, args.cpu_seconds)
+    cpu_line = None
+    if cpu and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_line = time_oracle(name, args.cpu_seconds)
 
-    line = {
-        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(1e3 * t_dev / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32", "f16": "f16 tensor-core MLP + f32"}[args.precision],
+    return {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": round(1e3 * t_dev / steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32", "f16": "f16 tensor-core MLP + f32"}[precision],
         "data": "synthetic", "impl": "ours",
-        "config": {"workload": args.workload, "atoms": s.n, "edges": E_edges,
+        "config": {"workload": name, "atoms": s.n, "edges": E_edges,
                    "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}" + (" SC2" if spec.correlation else "")
                    + (" gated" if spec.gate else ""),
-                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "single",
+                   "precision": precision, "parallelism": f"replicas x{world}" if world > 1 else "single",
                    "l2": "flushed between steps (512 MB write)", "stress": stress},
         "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "kernel_share": share,
         "kernel_ms_per_step": round(tot_all / n_share, 4),
@@ -479,10 +540,25 @@ def run_ours(args, rank, world):
         "gate_roofline": gate_roof,
         "timing": "timed steps: CUDA events around the dominant kernel's launches only (graph event nodes); "
                   "kernel_share from 4 steps with every kernel timed, outside the timed region",
-        "plain_fp32": plain,
-        "cpu_baseline": cpu, "clocks": clocks, "wall_s": round(t_wall, 3),
-        "peaks": peaks(),
+        "plain_fp32": plain_line,
+        "cpu_baseline": cpu_line, "clocks": clocks, "wall_s": round(t_wall, 3),
     }
+
+
+def run_ours(args, rank, world):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    fp32_peak = measure_fp32_peak()
+    line = measure(args, rank, world, args.workload, args.steps, args.warmup, fp32_peak,
+                   plain=not args.no_plain, cpu=True, fcc_cells=args.fcc_cells)
+    if args.workload == "fcc108k" and args.fcc_cells == 30 and not args.no_extras:
+        # the smaller periodic box of the same metric (water, l <= 2) and a bounded serving phase
+        wl = measure(args, rank, world, "water3000", 20, 3, fp32_peak, plain=not args.no_plain, cpu=False)
+        line["water3000"] = {k: wl[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "e2e", "roofline",
+                                                "kernel_share", "plain_fp32", "clocks")}
+        line["serving"] = serve_phase(args, rank, world, args.serve_requests, sweep=[], alone=False)
+    line["fp32_peak"] = fp32_peak
+    line["peaks"] = peaks()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -498,15 +574,17 @@ def serve_requests(n_requests: int, seed: int, rate: float):
     return reqs, systems
 
 
-def run_serve(args, rank, world):
+def serve_phase(args, rank, world, R, sweep, alone):
+    """The serving workload: a warm-up, every request queued at once
+    (saturated throughput), then Poisson arrivals at 0.7x the saturated request
+    rate (the headline p50/p99), optionally further arrival rates and single
+    requests on an idle server.  Returns the measurements as a dict."""
     import torch
     from paper_2605_22698_gb300 import binding as B
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     spec = synth.model_spec("water")
     w = synth.make_weights(spec, 21)
     prec = {"fp32": B.MLIP_PREC_FP32, "bf16": B.MLIP_PREC_BF16, "f16": B.MLIP_PREC_F16}[args.precision]
     model = B.Model(spec, w, prec)
-    R = args.requests
     edges = (100, 1000)
 
     def submit(srv, r, sy):
@@ -570,36 +648,33 @@ def run_serve(args, rank, world):
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     lam, st, thr2, clocks = open_loop(0.7, 5 + rank, sampler)
     # phase 3: the other arrival rates of the sweep
-    sweep = []
-    for k, f in enumerate(args.rate_sweep):
+    sw = []
+    for k, f in enumerate(sweep):
         lam_f, st_f, thr_f, _ = open_loop(f, 6 + k + rank)
-        sweep.append({"factor": f, "rate_per_s": round(lam_f, 2), "p50_ms": round(st_f["p50_ms"], 2),
-                      "p99_ms": round(st_f["p99_ms"], 2), "throughput_atom_steps_per_s": round(thr_f, 1),
-                      "mean_batch_requests": round(st_f["mean_batch_requests"], 2)})
+        sw.append({"factor": f, "rate_per_s": round(lam_f, 2), "p50_ms": round(st_f["p50_ms"], 2),
+                   "p99_ms": round(st_f["p99_ms"], 2), "throughput_atom_steps_per_s": round(thr_f, 1),
+                   "mean_batch_requests": round(st_f["mean_batch_requests"], 2)})
     # phase 4: single requests on an idle server (latency alone, against the mix's buckets)
-    alone = []
-    srv = B.Server(model, bucket_edges=edges)
-    for n_at, kind in ((50, 0), (200, 0), (2000, 0), (200, 1)):
-        sy = synth.cluster(n_at, 77 + n_at)
-        r = synth.RequestSpec(0.0, n_at, kind, 77 + n_at, 100 if kind else 0)
-        lat = []
-        for _ in range(4):
-            t0 = time.perf_counter()
-            assert srv.wait(submit(srv, r, sy))["status"] == 0
-            lat.append(1e3 * (time.perf_counter() - t0))
-        alone.append({"atoms": n_at, "kind": "nve100" if kind else "energy_forces",
-                      "ms": round(float(np.median(lat[1:])), 2)})
-    srv.close()
-    line = {
-        "metric": METRIC, "value": round(world * ae / t_sat, 1), "unit": UNIT, "n_gpus": world, "steps": R,
-        "warmup": 16, "ms_per_step": round(1e3 * t_sat / R, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32",
-                                       "f16": "f16 tensor-core MLP + f32"}[args.precision],
-        "data": "synthetic", "impl": "ours",
-        "config": {"workload": "serve", "requests": R, "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}",
-                   "precision": args.precision, "mix": "70% E+F, 30% 100-step NVE; N = exp U(ln 8, ln 5000)",
-                   "step": "one request (value: atom-evaluations/s with every request queued at once)",
-                   "l2": "inputs change every iteration (no flush)"},
+    alone_ms = []
+    if alone:
+        srv = B.Server(model, bucket_edges=edges)
+        for n_at, kind in ((50, 0), (200, 0), (2000, 0), (200, 1)):
+            sy = synth.cluster(n_at, 77 + n_at)
+            r = synth.RequestSpec(0.0, n_at, kind, 77 + n_at, 100 if kind else 0)
+            lat = []
+            for _ in range(4):
+                t0 = time.perf_counter()
+                assert srv.wait(submit(srv, r, sy))["status"] == 0
+                lat.append(1e3 * (time.perf_counter() - t0))
+            alone_ms.append({"atoms": n_at, "kind": "nve100" if kind else "energy_forces",
+                             "ms": round(float(np.median(lat[1:])), 2)})
+        srv.close()
+    model.close()
+    return {
+        "requests": R, "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}", "precision": args.precision,
+        "mix": "70% E+F, 30% 100-step NVE at 0.5 fs; N = exp U(ln 8, ln 5000) atoms, open clusters at 0.1 /A^3",
+        "saturated_atom_steps_per_s": round(world * ae / t_sat, 1), "saturated_ms_per_request": round(1e3 * t_sat / R, 4),
+        "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
         "latency": {"rate_per_s": round(lam, 2), "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
                     "mean_ms": round(st["mean_ms"], 2), "max_ms": round(st["max_ms"], 2),
                     "throughput_atom_steps_per_s": round(thr2, 1),
@@ -608,8 +683,8 @@ def run_serve(args, rank, world):
                     "bucket_p99_ms": [round(x, 2) for x in st["bucket_p99_ms"]],
                     "mean_batch_atoms": round(st["mean_batch_atoms"], 1),
                     "mean_batch_requests": round(st["mean_batch_requests"], 2)},
-        "rate_sweep": sweep,
-        "alone_ms": alone,
+        "rate_sweep": sw,
+        "alone_ms": alone_ms,
         "saturated": {"requests_per_s": round(sat_rps, 2), "p50_ms": round(st_sat["p50_ms"], 2),
                       "p99_ms": round(st_sat["p99_ms"], 2), "busy_atom_steps_per_s": round(st_sat["atom_steps_per_s"], 1),
                       "iterations": st_sat["iterations"], "mean_batch_atoms": round(st_sat["mean_batch_atoms"], 1)},
@@ -617,7 +692,28 @@ def run_serve(args, rank, world):
                 "h2d_bytes_per_step": int(sum(sy.n * 28 for sy in systems) / R),
                 "d2h_bytes_per_step": int(sum(sy.n * 24 * (3 if r.kind == 1 else 1) + 16 * (r.n_steps + 1)
                                               for r, sy in zip(reqs, systems)) / R)},
-        "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": None,
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+
+
+def run_serve(args, rank, world):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    R = args.requests
+    sv = serve_phase(args, rank, world, R, args.rate_sweep, alone=True)
+    line = {
+        "metric": METRIC, "value": sv["saturated_atom_steps_per_s"], "unit": UNIT, "n_gpus": world, "steps": R,
+        "warmup": 16, "ms_per_step": sv["saturated_ms_per_request"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32",
+                                       "f16": "f16 tensor-core MLP + f32"}[args.precision],
+        "data": "synthetic", "impl": "ours",
+        "config": {"workload": "serve", "requests": R, "model": sv["model"],
+                   "precision": args.precision, "mix": sv["mix"],
+                   "step": "one request (value: atom-evaluations/s with every request queued at once)",
+                   "l2": "inputs change every iteration (no flush)"},
+        "latency": sv["latency"], "rate_sweep": sv["rate_sweep"], "alone_ms": sv["alone_ms"],
+        "saturated": sv["saturated"], "e2e": sv["e2e"], "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"],
+        "cpu_baseline": None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -726,18 +822,33 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _relaunch(args_gpus: int) -> int:
+    """Run this script under torch.distributed.run with one process per GPU."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args_gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="water3000", choices=["water3000", "fcc108k", "cluster64", "serve", "md64",
-                                                                 "water3000_mace", "fcc108k_mace",
-                                                                 "cluster5000_charged", "water3000_gated", "fcc108k_gated"])
+    ap.add_argument("--workload", default="fcc108k", choices=["water3000", "fcc108k", "cluster64", "serve", "md64",
+                                                               "water3000_mace", "fcc108k_mace",
+                                                               "cluster5000_charged", "water3000_gated", "fcc108k_gated"])
     ap.add_argument("--precision", default="f16", choices=["fp32", "bf16", "f16"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP32 form beside the headline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="fcc108k: skip the water3000 and serving sub-objects of the default line")
     ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests per phase of the serving sub-object of the default line")
     ap.add_argument("--rate-sweep", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.5, 0.9, 1.1],
                     help="serve: further open-loop arrival rates, as factors of the saturated rate")
     ap.add_argument("--fcc-cells", type=int, default=30,
@@ -747,8 +858,16 @@ def main():
     ap.add_argument("--md-list", default="skin", choices=["skin", "fresh"],
                     help="md64: skin list rebuilt every 10 steps with graph replay, or a fresh list every step")
     args = ap.parse_args()
+    if args.gpus < 1:
+        print("bench.py: --gpus must be at least 1", file=sys.stderr)
+        sys.exit(2)
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        sys.exit(_relaunch(args.gpus))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}", file=sys.stderr)
+        sys.exit(2)
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

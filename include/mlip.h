@@ -420,6 +420,17 @@ int mlip_profile_report(char* buf, long long cap, long long* needed);
  * (NULL or "": all); launches are still counted. */
 int mlip_profile_select(const char* names);
 
+/* Measured FP32 FMA throughput of the current device (no counterpart in the
+ * paper; the denominator of the FP32-ALU roofline the benchmark reports).
+ * Launches one grid of independent FMA chains filling every SM (the SM count
+ * is read from the device) after one shorter warm-up launch, and times it with
+ * CUDA events on the default stream.  iters: loop trips per thread (each 256
+ * FMAs); 20000 runs for about 50 ms on a GB300.  *tflops receives 2 x FMAs /
+ * seconds / 1e12; *ms (nullable) the timed duration; *sms (nullable) the SM
+ * count.  It allocates and frees a small sink buffer and synchronises the
+ * device's default stream.  Errors: MLIP_ERR_INVALID_ARG, MLIP_ERR_CUDA. */
+int mlip_fp32_fma_rate(int iters, double* tflops, double* ms, int* sms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,8 @@ def lib():
         L.mlip_profile_select.argtypes = [ctypes.c_char_p]
         L.mlip_launch_count.restype = ctypes.c_longlong
         L.mlip_profile_report.argtypes = [ctypes.c_char_p, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+        L.mlip_fp32_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -355,6 +357,14 @@ def mlip_selftest(which: int) -> float:
     r = ctypes.c_double(0.0)
     _check(lib().mlip_selftest(which, ctypes.byref(r)))
     return float(r.value)
+
+
+def mlip_fp32_fma_rate(iters: int = 20000) -> dict:
+    """Measured FP32 FMA throughput of the current device: TFLOP/s, the timed
+    milliseconds and the SM count."""
+    tf, ms, sms = ctypes.c_double(0.0), ctypes.c_double(0.0), ctypes.c_int(0)
+    _check(lib().mlip_fp32_fma_rate(int(iters), ctypes.byref(tf), ctypes.byref(ms), ctypes.byref(sms)))
+    return {"tflops": float(tf.value), "ms": float(ms.value), "sms": int(sms.value)}
 
 
 def mlip_profile_enable(on: bool) -> None:

@@ -850,18 +850,40 @@ int noalloc_scratch(void** out) {
 }
 
 // Bump allocator over the scratch array (256-byte aligned pieces).
+// Consecutive 256-byte-aligned pieces of the scratch array.  A failed take
+// marks the carve failed, and every later take then fails too, so one check of
+// `failed` after the last take covers the whole layout.
 struct Carve {
   unsigned char* base;
   size_t off, cap;
+  bool failed = false;
+  static constexpr size_t rounded(size_t bytes) { return (bytes + 255) & ~(size_t)255; }
   template <class T>
   T* take(size_t count) {
-    const size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
-    if (off + bytes > cap) return nullptr;
+    const size_t bytes = rounded(count * sizeof(T));
+    if (failed || off + bytes > cap) {
+      failed = true;
+      return nullptr;
+    }
     T* p = reinterpret_cast<T*>(base + off);
     off += bytes;
     return p;
   }
 };
+
+// Bytes the layout of mlip_neighbors_noalloc takes for nn atoms (the takes in
+// the order the entry point makes them); at the limits it must fit the array.
+constexpr size_t noalloc_layout_bytes(size_t nn) {
+  const size_t bins = (nn * 4 > 64 ? nn * 4 : 64) + 1;
+  const size_t scan = ((bins - 1 > nn ? bins - 1 : nn) / kScanTile + 2) * sizeof(int);
+  return Carve::rounded(sizeof(Grid)) + Carve::rounded(3 * nn * sizeof(double)) + Carve::rounded(3 * nn * sizeof(int)) +
+         Carve::rounded(nn * sizeof(float4)) + Carve::rounded(nn * sizeof(int)) + 3 * Carve::rounded(bins * sizeof(int)) +
+         2 * Carve::rounded(nn * sizeof(int)) + Carve::rounded(4 * sizeof(int)) + Carve::rounded(6 * sizeof(long long)) +
+         Carve::rounded((nn + 1) * sizeof(int)) + Carve::rounded(scan) +
+         Carve::rounded(nn * kNoAllocMaxDegree * sizeof(unsigned long long));
+}
+static_assert(noalloc_layout_bytes(kNoAllocMaxAtoms) <= kNoAllocScratchBytes,
+              "the allocation-free neighbour layout at its atom and degree limits exceeds the scratch array");
 
 // nl_sort without the key output (the caller's edge arrays only).
 __global__ void nl_sort_out(int n, int cap, const unsigned long long* __restrict__ slab, int maxdeg,
@@ -953,7 +975,10 @@ extern "C" int mlip_neighbors_noalloc(const double* pos, int64_t n64, const doub
   int* row_ptr = cv.take<int>(nn + 1);
   int* bsum = cv.take<int>((size_t)std::max<int64_t>(hg.max_bins, nn) / kScanTile + 2);
   unsigned long long* slab = cv.take<unsigned long long>(nn * kNoAllocMaxDegree);
-  if (!slab) { set_error("neighbors (no-alloc): scratch layout exceeds %zu bytes", kNoAllocScratchBytes); return MLIP_ERR_CAPACITY; }
+  if (cv.failed || !slab) {
+    set_error("neighbors (no-alloc): scratch layout exceeds %zu bytes", kNoAllocScratchBytes);
+    return MLIP_ERR_CAPACITY;
+  }
 
   // the array keeps the last call's contents: clear what must start at zero
   const long long bb_init[6] = {LLONG_MAX, LLONG_MIN, LLONG_MAX, LLONG_MIN, LLONG_MAX, LLONG_MIN};

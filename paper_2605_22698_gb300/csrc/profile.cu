@@ -138,6 +138,27 @@ void prof_events_free(std::vector<ProfEvent>& events) {
 long long prof_launches() { return P().launches.load(); }
 void prof_add_launches(long long k) { P().launches.fetch_add(k); }
 
+// FP32 FMA throughput: every thread runs kFmaChains independent chains
+// a <- a * m + c (m, c kernel arguments, so nothing folds), kFmaUnroll FMAs per
+// chain per iteration; the sum is stored only when it equals a sentinel that
+// the chains never reach, which keeps the work alive.
+constexpr int kFmaChains = 8, kFmaUnroll = 16, kFmaThreads = 512;
+__global__ void __launch_bounds__(kFmaThreads) fma_rate(int iters, float m, float c, float* __restrict__ sink) {
+  float a[kFmaChains];
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < kFmaUnroll; ++u)
+#pragma unroll
+      for (int k = 0; k < kFmaChains; ++k) a[k] = fmaf(a[k], m, c);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) s += a[k];
+  if (s == -1.2345e30f) sink[blockIdx.x] = s;
+}
+
 }  // namespace mlip
 
 extern "C" {
@@ -179,6 +200,42 @@ int mlip_profile_select(const char* names) {
 }
 
 long long mlip_launch_count(void) { return mlip::P().launches.load(); }
+
+int mlip_fp32_fma_rate(int iters, double* tflops, double* ms, int* sms) {
+  using namespace mlip;
+  if (!tflops || iters < 1) { set_error("fp32 rate: null result or iters < 1"); return MLIP_ERR_INVALID_ARG; }
+  int dev = 0, nsm = 0;
+  MLIP_CUDA_TRY(cudaGetDevice(&dev));
+  MLIP_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int per_sm = 0;
+  MLIP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_rate, kFmaThreads, 0));
+  if (per_sm < 1) per_sm = 1;
+  const int blocks = nsm * per_sm;
+  float* sink = nullptr;
+  MLIP_CUDA_TRY(cudaMalloc(&sink, sizeof(float) * blocks));
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  fma_rate<<<blocks, kFmaThreads>>>(iters / 8 + 1, 0.999999f, 1e-6f, sink);  // warm-up (clocks, code)
+  cudaEventRecord(a);
+  fma_rate<<<blocks, kFmaThreads>>>(iters, 0.999999f, 1e-6f, sink);
+  cudaEventRecord(b);
+  const cudaError_t e = cudaEventSynchronize(b);
+  float t = 0.0f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&t, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess || t <= 0.0f) {
+    set_error("fp32 rate: kernel failed: %s", cudaGetErrorString(e));
+    return MLIP_ERR_CUDA;
+  }
+  const double flop = 2.0 * kFmaChains * kFmaUnroll * (double)iters * blocks * kFmaThreads;
+  *tflops = flop / (t * 1e-3) / 1e12;
+  if (ms) *ms = t;
+  if (sms) *sms = nsm;
+  return MLIP_OK;
+}
 
 // JSON {"kernels": {"name": [launches, total_ms], ...}} of the records since
 // the last mlip_profile_enable; synchronises on the recorded events.

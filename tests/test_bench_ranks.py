@@ -1,6 +1,8 @@
 """The multi-rank path of bench.py on CPU (world size 2, gloo): the job's time
-is the largest rank's time, and under torchrun-style launches the reference
-arm prints one line from rank 0 only."""
+is the largest rank's time; under torchrun-style launches the reference arm
+prints one line from rank 0 only; --gpus N with no rank in the environment
+starts N processes through torch.distributed.run, and a rank count that
+disagrees with --gpus is refused."""
 import json
 import os
 import socket
@@ -48,7 +50,8 @@ def test_reference_arm_prints_from_rank_zero_only():
     lines = {}
     for rank in (1, 0):
         env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank))
-        r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+        r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--workload", "cluster64",
+                            "--steps", "1", "--warmup", "0"],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode == 0, r.stderr[-2000:]
         lines[rank] = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
@@ -56,3 +59,33 @@ def test_reference_arm_prints_from_rank_zero_only():
     assert len(lines[0]) == 1
     rec = json.loads(lines[0][0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def _clean_env():
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT", "LOCAL_WORLD_SIZE"):
+        env.pop(k, None)
+    return env
+
+
+def test_gpus_flag_starts_one_process_per_rank():
+    """bench.py --gpus 2 run bare: two ranks through torch.distributed.run, one
+    JSON line (rank 0), n_gpus 2; a replica workload (the oracle's arm, which
+    needs no GPU) runs on rank 0 and the other rank exits without work."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--workload", "cluster64",
+                        "--steps", "1", "--warmup", "0"],
+                       cwd=ROOT, env=_clean_env(), capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["n_gpus"] == 2 and rec["impl"] == "reference"
+
+
+def test_gpus_flag_disagreeing_with_the_rank_count_is_refused():
+    env = dict(_clean_env(), RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--workload", "cluster64",
+                        "--steps", "1", "--warmup", "0"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0
+    assert "WORLD_SIZE" in r.stderr

@@ -57,3 +57,21 @@ def test_noalloc_rejects_oversized_input(B):
         B.mlip_neighbors_noalloc(pos, s.cell, s.pbc, 5.0, out, out, sh)
     assert e.value.code == B.MLIP_ERR_INVALID_ARG
     assert "12288" in str(e.value)
+
+
+def test_noalloc_rejects_a_receiver_above_the_degree_limit(B):
+    """A dense open FCC cluster (a = 1.2 A, 864 atoms): its central atoms
+    have far more than 256 neighbours within 5 A.  The call must return
+    MLIP_ERR_CAPACITY naming the limit, and a following ordinary call must
+    still match the allocating entry point."""
+    import torch
+    s = synth.fcc((6, 6, 6), seed=3)
+    pos_h = s.pos * (1.2 / 3.6)
+    pos = torch.tensor(pos_h, device="cuda")
+    out = torch.zeros(8, dtype=torch.int32, device="cuda")
+    sh = torch.zeros((8, 3), dtype=torch.int8, device="cuda")
+    with pytest.raises(B.MlipError) as e:
+        B.mlip_neighbors_noalloc(pos, np.eye(3), np.zeros(3, np.uint8), 5.0, out, out, sh)
+    assert e.value.code == B.MLIP_ERR_CAPACITY
+    assert "256" in str(e.value)
+    _run(B, synth.cluster(300, seed=6))
