@@ -197,6 +197,35 @@ int mlip_energy_forces(mlip_model* model, const double* pos, const int32_t* spec
                        const double cell[9], const uint8_t pbc[3], double* energy, double* forces,
                        double* stress, int on_device, void* stream);
 
+/* Separate forward and backward of one system's energy, for automatic
+ * differentiation frameworks (the library's torch.autograd.Function uses them).
+ * The paper differentiates its energy for forces (Eq. full_hessian, first
+ * derivative, F = -dE/dr); this pair splits that differentiation in two calls.
+ *
+ * mlip_energy_forward: the energy of one system (arguments as in
+ *   mlip_energy_forces; energy: one double, on the device when on_device).  It
+ *   runs no adjoint kernel.  It keeps, in the model's workspace, its own copy of
+ *   the positions and species, the neighbour list and the node features (and
+ *   mix pre-activations) of every layer; nothing per edge is kept for the
+ *   backward.  Synchronises the stream (input check, edge count).
+ * mlip_energy_backward: the gradient of g E with respect to the positions of
+ *   the last forward, grad_pos[i][a] = g dE/dr_ia = -g F_ia (double[n][3]),
+ *   and optionally g times the stress (double[9], fully periodic cells only,
+ *   else MLIP_ERR_CELL).  grad_energy points to g (one double; on the device
+ *   when on_device, like grad_pos and stress).  The fused forms compute the
+ *   edge geometry, harmonics and each layer's radial weights again from the
+ *   saved positions and run the adjoint kernels; the plain FP32 form reads the
+ *   radial weights its forward stored.  It may be called more than once for one
+ *   forward.  Any other evaluation of the model after the forward (any entry
+ *   point, the server, MD) overwrites what the forward kept: the backward then
+ *   returns MLIP_ERR_INVALID_ARG.  Other errors: MLIP_ERR_CUDA,
+ *   MLIP_ERR_DEVICE_TIMEOUT.  With on_device the backward does not synchronise
+ *   (except to read the fused kernels' error flags). */
+int mlip_energy_forward(mlip_model* model, const double* pos, const int32_t* species, int64_t n,
+                        const double cell[9], const uint8_t pbc[3], double* energy, int on_device, void* stream);
+int mlip_energy_backward(mlip_model* model, const double* grad_energy, double* grad_pos, double* stress,
+                         int on_device, void* stream);
+
 /* Energy, forces and the corrected charges of one open system of total
  * charge total_charge (e) with a model built with charges = 1 (see
  * mlip_model_desc).  pos double[n][3], species int32[n]; energy double[1];

@@ -77,6 +77,8 @@ def lib():
         L.mlip_neighbors.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), i32, P]
         L.mlip_energy_forces.argtypes = [P, P, P, i64, P, P, P, P, P, i32, P]
         L.mlip_energy_forces_charged.argtypes = [P, P, P, i64, ctypes.c_double, P, P, P, i32, P]
+        L.mlip_energy_forward.argtypes = [P, P, P, i64, P, P, P, i32, P]
+        L.mlip_energy_backward.argtypes = [P, P, P, P, i32, P]
         L.mlip_energy_forces_batch.argtypes = [P, i32, P, P, P, P, P, P, P, P, i32, P]
         L.mlip_neighbors_noalloc.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), P]
         L.mlip_md_nve.argtypes = [P, P, P, P, i64, P, P, f64, i64, P, P, i32, P]
@@ -228,6 +230,45 @@ def mlip_energy_forces(h, pos, species, cell, pbc, forces: bool = True, stress: 
                                     _ptr(out["forces"])[0] if forces else None,
                                     _ptr(out["stress"])[0] if stress else None, dev, _stream_ptr(stream)))
     return out
+
+
+def mlip_energy_forward(h, pos, species, cell, pbc, stream=None):
+    """Energy of one system with no adjoint (host arrays in: a float; CUDA
+    tensors in: a one-element float64 CUDA tensor); the model keeps what
+    mlip_energy_backward needs."""
+    cell = np.ascontiguousarray(cell, dtype=np.float64).reshape(9)
+    pbc = np.ascontiguousarray(pbc, dtype=np.uint8).reshape(3)
+    pp, dev = _ptr(pos)
+    sp, dev2 = _ptr(species)
+    if dev != dev2:
+        raise ValueError("positions and species must both be host or both be device arrays")
+    if dev:
+        import torch
+        e = torch.zeros(1, dtype=torch.float64, device=pos.device)
+    else:
+        e = np.zeros(1)
+    _check(lib().mlip_energy_forward(h, pp, sp, int(pos.shape[0]), cell.ctypes.data_as(ctypes.c_void_p),
+                                     pbc.ctypes.data_as(ctypes.c_void_p), _ptr(e)[0], dev, _stream_ptr(stream)))
+    return e if dev else float(e[0])
+
+
+def mlip_energy_backward(h, n: int, grad_energy, stress: bool = False, stream=None):
+    """Gradient of g E with respect to the positions of the last forward
+    (g = grad_energy: a float for host output, a one-element float64 CUDA
+    tensor for device output); with stress also g times the stress."""
+    if isinstance(grad_energy, (float, int)):
+        g = np.array([float(grad_energy)])
+        out, so = np.zeros((n, 3)), (np.zeros((3, 3)) if stress else None)
+        dev = 0
+    else:
+        import torch
+        g = grad_energy.reshape(1).to(torch.float64).contiguous()
+        out = torch.zeros((n, 3), dtype=torch.float64, device=g.device)
+        so = torch.zeros((3, 3), dtype=torch.float64, device=g.device) if stress else None
+        dev = 1
+    _check(lib().mlip_energy_backward(h, _ptr(g)[0], _ptr(out)[0], _ptr(so)[0] if stress else None, dev,
+                                      _stream_ptr(stream)))
+    return (out, so) if stress else out
 
 
 def mlip_energy_forces_charged(h, pos, species, total_charge: float = 0.0, forces: bool = True, stream=None):
@@ -400,6 +441,12 @@ class Model:
 
     def energy_forces(self, pos, species, cell, pbc, forces=True, stress=False, stream=None, out=None):
         return mlip_energy_forces(self.h, pos, species, cell, pbc, forces, stress, stream, out)
+
+    def energy_forward(self, pos, species, cell, pbc, stream=None):
+        return mlip_energy_forward(self.h, pos, species, cell, pbc, stream)
+
+    def energy_backward(self, n, grad_energy, stress=False, stream=None):
+        return mlip_energy_backward(self.h, n, grad_energy, stress, stream)
 
     def energy_forces_charged(self, pos, species, total_charge=0.0, forces=True, stream=None):
         return mlip_energy_forces_charged(self.h, pos, species, total_charge, forces, stream)

@@ -441,22 +441,11 @@ int launch_check_inputs(int n, const double* pos, const int* species, int S, int
 }
 
 
-int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
-                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+int plain_forward_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                        const NeighborList& nl, double* d_energy, cudaStream_t st) {
   Workspace& ws = M->ws;
   const int n = (int)b.n, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H, P = M->P, P0 = M->P0;
   const float s = (float)(1.0 / M->avg_nb);
-  int* flag = nullptr;
-  MLIP_TRY(ws.get("chk.flag", 1, &flag));
-  MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
-  MLIP_TRY(launch_check_inputs(n, d_pos, d_species, M->S, flag, st));
-  NeighborList nl;
-  MLIP_TRY(build_neighbors_batch(ws, d_pos, b, M->rc, true, st, &nl));
-  int hflag = 0;
-  MLIP_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
-  if (hflag & 1) { set_error("species index out of range"); return MLIP_ERR_INVALID_ARG; }
-  if (hflag & 2) { set_error("non-finite position"); return MLIP_ERR_INVALID_ARG; }
   const int E = (int)nl.E;
   const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)std::max(n, 1) * D * C;
 
@@ -514,7 +503,47 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
   } else {
     MLIP_TRY(launch_energy(ws, b, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, energy, st));
   }
-  if (d_forces || d_stress) {
+  return MLIP_OK;
+}
+
+int plain_adjoint_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                        const NeighborList& nl, double* d_forces, double* d_stress, cudaStream_t st) {
+  Workspace& ws = M->ws;
+  const int n = (int)b.n, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H, P = M->P, P0 = M->P0;
+  const float s = (float)(1.0 / M->avg_nb);
+  const int E = (int)nl.E;
+  const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)std::max(n, 1) * D * C;
+
+  CellArg ca{b.d_cell, b.d_sys_of, b.any_pbc() ? 1 : 0};
+
+  float4 *ev = nullptr, *g = nullptr;
+  float *z2T = nullptr, *m = nullptr, *Gm = nullptr, *Ga = nullptr, *Gb = nullptr, *dw = nullptr, *dz2 = nullptr,
+        *dY = nullptr, *dr = nullptr;
+  double* atom_e = nullptr;
+  MLIP_TRY(ws.get("ef.ev", Ec, &ev));
+  MLIP_TRY(ws.get("ef.g", Ec, &g));
+  MLIP_TRY(ws.get("ef.z2T", Ec * H, &z2T));
+  MLIP_TRY(ws.get("ef.m", ND, &m));
+  MLIP_TRY(ws.get("ef.Gm", ND, &Gm));
+  MLIP_TRY(ws.get("ef.Ga", ND, &Ga));
+  MLIP_TRY(ws.get("ef.Gb", ND, &Gb));
+  MLIP_TRY(ws.get("ef.dw", Ec * P * C, &dw));
+  MLIP_TRY(ws.get("ef.dz2", Ec * H, &dz2));
+  MLIP_TRY(ws.get("ef.dY", Ec * 16, &dY));
+  MLIP_TRY(ws.get("ef.dr", Ec, &dr));
+  MLIP_TRY(ws.get("ef.atom_e", (size_t)std::max(n, 1), &atom_e));
+  std::vector<float*> h(T + 1), u0(T), w(T), A(T, nullptr), gpre(T, nullptr), gg(T, nullptr);
+  for (int t = 0; t <= T; ++t) MLIP_TRY(ws.get("ef.h" + std::to_string(t), ND, &h[t]));
+  for (int t = 0; t < T; ++t) {
+    MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
+    MLIP_TRY(ws.get("ef.w" + std::to_string(t), Ec * (t == 0 ? P0 : P) * C, &w[t]));
+    if (M->corr == 2) MLIP_TRY(ws.get("ef.A" + std::to_string(t), ND, &A[t]));
+    if (M->gate) {
+      MLIP_TRY(ws.get("ef.gpre" + std::to_string(t), ND, &gpre[t]));
+      MLIP_TRY(ws.get("ef.gg" + std::to_string(t), (size_t)std::max(n, 1) * L * C, &gg[t]));
+    }
+  }
+  {
     MLIP_TRY(launch_grad_init(n, C, D, M->S, d_species, M->W_out, Ga, st));
     if (M->charges) MLIP_TRY(coulomb_adjoint(ws, b, M, d_species, Ga, st));
     MLIP_CUDA_TRY(cudaMemsetAsync(dY, 0, Ec * 16 * sizeof(float), st));
@@ -544,8 +573,28 @@ int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, con
   return MLIP_OK;
 }
 
+int evaluate_plain(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                   double* d_energy, double* d_forces, double* d_stress, cudaStream_t st) {
+  Workspace& ws = M->ws;
+  int* flag = nullptr;
+  MLIP_TRY(ws.get("chk.flag", 1, &flag));
+  MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  MLIP_TRY(launch_check_inputs((int)b.n, d_pos, d_species, M->S, flag, st));
+  NeighborList nl;
+  MLIP_TRY(build_neighbors_batch(ws, d_pos, b, M->rc, true, st, &nl));
+  int hflag = 0;
+  MLIP_CUDA_TRY(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hflag & 1) { set_error("species index out of range"); return MLIP_ERR_INVALID_ARG; }
+  if (hflag & 2) { set_error("non-finite position"); return MLIP_ERR_INVALID_ARG; }
+  MLIP_TRY(plain_forward_edges(M, d_pos, d_species, b, nl, d_energy, st));
+  if (d_forces || d_stress) MLIP_TRY(plain_adjoint_edges(M, d_pos, d_species, b, nl, d_forces, d_stress, st));
+  return MLIP_OK;
+}
+
 int evaluate(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b, double* d_energy,
              double* d_forces, double* d_stress, cudaStream_t st, bool graph) {
+  ++M->eval_gen;  // the workspace is written: a saved separate forward is no longer usable
   if (M->charges && b.any_pbc()) {
     set_error("a model with charges evaluates open systems only (the Coulomb term has no periodic images)");
     return MLIP_ERR_CELL;
@@ -600,6 +649,133 @@ extern "C" int mlip_energy_forces(mlip_model* M, const double* pos, const int32_
     MLIP_CUDA_TRY(cudaStreamSynchronize(st));
   } else {
     MLIP_CUDA_TRY(cudaGetLastError());
+  }
+  return MLIP_OK;
+}
+
+namespace mlip {
+// out[k] = -g F[k] = g dE/dr_k (the gradient of g E with respect to the positions)
+__global__ void grad_from_forces(int64_t n3, const double* __restrict__ F, const double* __restrict__ g,
+                                 double* __restrict__ out) {
+  const double gv = *g;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n3; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = -gv * F[k];
+}
+// out[k] = g s[k] (9 stress components)
+__global__ void scale_stress(const double* __restrict__ S, const double* __restrict__ g, double* __restrict__ out) {
+  if (threadIdx.x < 9) out[threadIdx.x] = *g * S[threadIdx.x];
+}
+}  // namespace mlip
+
+extern "C" int mlip_energy_forward(mlip_model* M, const double* pos, const int32_t* species, int64_t n,
+                                   const double cell[9], const uint8_t pbc[3], double* energy, int on_device,
+                                   void* stream) {
+  using namespace mlip;
+  if (!M || !pos || !species || !energy || !cell || !pbc) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  if (n < 1 || n > (1LL << 28)) { set_error("atom count %lld out of range", (long long)n); return MLIP_ERR_INVALID_ARG; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != M->device) { set_error("model lives on device %d, current device is %d", M->device, cur); return MLIP_ERR_INVALID_ARG; }
+  Workspace& ws = M->ws;
+  WsStream wss(ws, st);
+  ++M->eval_gen;
+  M->tape_gen = 0;
+  // the library's own copies of the inputs, which the backward reads
+  double* d_pos = nullptr;
+  int* d_sp = nullptr;
+  double* d_energy = nullptr;
+  int* flag = nullptr;
+  MLIP_TRY(ws.get("tape.pos", (size_t)3 * n, &d_pos));
+  MLIP_TRY(ws.get("tape.species", (size_t)n, &d_sp));
+  MLIP_TRY(ws.get("tape.energy", 1, &d_energy));
+  MLIP_TRY(ws.get("chk.flag", 2, &flag));
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  MLIP_CUDA_TRY(cudaMemcpyAsync(d_pos, pos, sizeof(double) * 3 * n, k, st));
+  MLIP_CUDA_TRY(cudaMemcpyAsync(d_sp, species, sizeof(int) * n, k, st));
+  SystemBatch& b = M->tape_batch;
+  b = SystemBatch();
+  single_system(b, n, cell, pbc);
+  MLIP_TRY(upload_batch(ws, M->stage, b, st));
+  // inputs are checked before any kernel reads a weight row by species
+  MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
+  MLIP_TRY(launch_check_inputs((int)n, d_pos, d_sp, M->S, flag, st));
+  NeighborList nl;
+  MLIP_TRY(build_neighbors_batch(ws, d_pos, b, M->rc, true, st, &nl));
+  MLIP_TRY(check_eval_flags(flag, st));
+  if (M->charges && b.any_pbc()) {
+    set_error("a model with charges evaluates open systems only (the Coulomb term has no periodic images)");
+    return MLIP_ERR_CELL;
+  }
+  if (M->precision == MLIP_PREC_FP32) {
+    MLIP_TRY(plain_forward_edges(M, d_pos, d_sp, b, nl, d_energy, st));
+  } else {
+    MLIP_TRY(fused_forward_edges(M, d_pos, d_sp, b, nl, nullptr, flag, d_energy, st));
+    MLIP_TRY(check_eval_flags(flag, st));
+  }
+  M->tape_nl = nl;
+  M->tape_gen = M->eval_gen;
+  MLIP_CUDA_TRY(cudaMemcpyAsync(energy, d_energy, sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (!on_device) MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  return MLIP_OK;
+}
+
+extern "C" int mlip_energy_backward(mlip_model* M, const double* grad_energy, double* grad_pos, double* stress,
+                                    int on_device, void* stream) {
+  using namespace mlip;
+  if (!M || !grad_energy || !grad_pos) { set_error("null argument"); return MLIP_ERR_INVALID_ARG; }
+  if (M->tape_gen == 0 || M->tape_gen != M->eval_gen) {
+    set_error("no saved forward to differentiate: call mlip_energy_forward first (any other evaluation of the "
+              "model in between overwrites it)");
+    return MLIP_ERR_INVALID_ARG;
+  }
+  const SystemBatch& b = M->tape_batch;
+  const int64_t n = b.n;
+  if (stress && !(b.pbc[0] && b.pbc[1] && b.pbc[2])) { set_error("stress needs a fully periodic cell"); return MLIP_ERR_CELL; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != M->device) { set_error("model lives on device %d, current device is %d", M->device, cur); return MLIP_ERR_INVALID_ARG; }
+  Workspace& ws = M->ws;
+  WsStream wss(ws, st);
+  double *d_pos = nullptr, *d_F = nullptr, *d_S = nullptr, *d_g = nullptr, *d_out = grad_pos, *d_sout = stress;
+  int* d_sp = nullptr;
+  int* flag = nullptr;
+  MLIP_TRY(ws.get("tape.pos", (size_t)3 * n, &d_pos));
+  MLIP_TRY(ws.get("tape.species", (size_t)n, &d_sp));
+  MLIP_TRY(ws.get("tape.forces", (size_t)3 * n, &d_F));
+  if (stress) MLIP_TRY(ws.get("tape.stress", 9, &d_S));
+  MLIP_TRY(ws.get("chk.flag", 2, &flag));
+  if (on_device) {
+    d_g = const_cast<double*>(grad_energy);
+  } else {
+    MLIP_TRY(ws.get("tape.grad", 1, &d_g));
+    MLIP_TRY(ws.get("tape.grad_pos", (size_t)3 * n, &d_out));
+    if (stress) MLIP_TRY(ws.get("tape.grad_stress", 9, &d_sout));
+    MLIP_CUDA_TRY(cudaMemcpyAsync(d_g, grad_energy, sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  if (M->precision == MLIP_PREC_FP32) {
+    MLIP_TRY(plain_adjoint_edges(M, d_pos, d_sp, b, M->tape_nl, d_F, d_S, st));
+  } else {
+    MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
+    MLIP_TRY(fused_adjoint_edges(M, d_pos, d_sp, b, M->tape_nl, nullptr, flag, d_F, d_S, true, st));
+  }
+  {
+    MLIP_PROF("grad_from_forces", st);
+    const int64_t n3 = 3 * n;
+    grad_from_forces<<<(int)std::min<int64_t>((n3 + 255) / 256, 4096), 256, 0, st>>>(n3, d_F, d_g, d_out);
+  }
+  if (stress) {
+    MLIP_PROF("scale_stress", st);
+    scale_stress<<<1, 32, 0, st>>>(d_S, d_g, d_sout);
+  }
+  MLIP_LAUNCH_CHECK();
+  if (M->precision != MLIP_PREC_FP32) MLIP_TRY(check_eval_flags(flag, st));
+  if (!on_device) {
+    MLIP_CUDA_TRY(cudaMemcpyAsync(grad_pos, d_out, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (stress) MLIP_CUDA_TRY(cudaMemcpyAsync(stress, d_sout, sizeof(double) * 9, cudaMemcpyDeviceToHost, st));
+    MLIP_CUDA_TRY(cudaStreamSynchronize(st));
   }
   return MLIP_OK;
 }

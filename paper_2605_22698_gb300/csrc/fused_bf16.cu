@@ -2,7 +2,7 @@
 // FP16 for the tighter error bar, with FP32 accumulation in tensor memory).
 //
 // Per layer:
-//   radial_tiles  one thread per edge: r -> Bessel x envelope -> z1 -> z2 (FP32),
+//   radial_tc     (radial_tc.cu) r -> Bessel x envelope -> z1 -> z2 per edge,
 //                 z2 written as BF16 or FP16 in the tcgen05 canonical K-major layout,
 //                 one 4 KB tile per kNT = 32 consecutive (receiver-sorted) edges
 //   tp_fused      one launch per path group (all l1 = 0 paths for the first
@@ -44,6 +44,16 @@ __host__ __device__ inline uint16_t to16(float x, bool bf16) {
   }
   const __half v = __float2half_rn(x);
   return *reinterpret_cast<const uint16_t*>(&v);
+}
+// Two FP32 values as 16-bit operands (a in the low half, b in the high half),
+// round to nearest, one packed conversion.
+__device__ __forceinline__ uint32_t pack16x2(float a, float b, bool bf16) {
+  if (bf16) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  }
+  const __half2 v = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
 }
 constexpr int kTileBytes = kNT * 64 * 2;
 constexpr int kW3PathBytes = 128 * 64 * 2;
@@ -97,64 +107,6 @@ struct Group {
     return (size_t)NP * kW3PathBytes + 2 * kTileBytes + (size_t)kNT * NZP * 4 + 2 * kNT * 4 + 64;
   }
 };
-
-// ------------------------------------------------------------- radial tiles
-template <int H>
-__global__ void radial_tiles(int E, int n_tiles, const float4* __restrict__ ev, const float* __restrict__ W1,
-                             const float* __restrict__ W2, float rc, int p, int use_bf16, uint8_t* __restrict__ z2t) {
-  static_assert(H == 64, "tile layout assumes K = 64");
-  __shared__ __align__(16) float sW1[8 * H], sW2[H * H];
-  for (int k = threadIdx.x; k < 8 * H; k += blockDim.x) sW1[k] = W1[k];
-  for (int k = threadIdx.x; k < H * H; k += blockDim.x) sW2[k] = W2[k];
-  __syncthreads();
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n_tiles * kNT) return;
-  uint8_t* tile = z2t + (size_t)(e / kNT) * kTileBytes;
-  const int t = e % kNT;
-  if (e >= E) {
-    const uint4 z = make_uint4(0, 0, 0, 0);
-#pragma unroll
-    for (int kg = 0; kg < 8; ++kg) *reinterpret_cast<uint4*>(tile + tc::canon_off(t, kg * 8)) = z;
-    return;
-  }
-  float b[8], db[8];
-  radial_basis<8, false>(ev[e].w, rc, p, b, db);
-  float z1[H];
-#pragma unroll
-  for (int k = 0; k < H; ++k) {
-    float a = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) a = fmaf(b[q], sW1[q * H + k], a);
-    z1[k] = silu_f(a);
-  }
-  // z2 = silu(z1 W2): all H outputs at once, one 16-byte load of a W2 row feeds four FMAs
-  float a2[H];
-#pragma unroll
-  for (int k = 0; k < H; ++k) a2[k] = 0.0f;
-#pragma unroll 4
-  for (int q = 0; q < H; ++q) {
-    const float zq = z1[q];
-    const float4* w4 = reinterpret_cast<const float4*>(sW2 + q * H);
-#pragma unroll
-    for (int k4 = 0; k4 < H / 4; ++k4) {
-      const float4 w = w4[k4];
-      a2[4 * k4] = fmaf(zq, w.x, a2[4 * k4]);
-      a2[4 * k4 + 1] = fmaf(zq, w.y, a2[4 * k4 + 1]);
-      a2[4 * k4 + 2] = fmaf(zq, w.z, a2[4 * k4 + 2]);
-      a2[4 * k4 + 3] = fmaf(zq, w.w, a2[4 * k4 + 3]);
-    }
-  }
-#pragma unroll
-  for (int kg = 0; kg < 8; ++kg) {
-    uint32_t pk[4];
-#pragma unroll
-    for (int h2 = 0; h2 < 4; ++h2) {
-      const int k = kg * 8 + h2 * 2;
-      pk[h2] = (uint32_t)to16(silu_f(a2[k]), use_bf16) | ((uint32_t)to16(silu_f(a2[k + 1]), use_bf16) << 16);
-    }
-    *reinterpret_cast<uint4*>(tile + tc::canon_off(t, kg * 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-  }
-}
 
 // ------------------------------------------------------------ warp sets
 // A CTA runs kWS warp sets of 4 warps (128 threads, one per channel and TMEM
@@ -667,13 +619,19 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(FwdLayout<L, MODE>::byte
 // set), the first group initialising them from G^t.
 constexpr bool kMnLboIsK = true;  // descriptor assignment checked by mlip_selftest(2 / 3)
 
-template <int L, int MODE>
-struct BwdLayout {
+// dE/dw of a tile for the second product: one 16-bit tile (B2H bytes), or with
+// SPLIT a hi tile rn16(x) followed by a lo tile rn16(x - hi), so that the
+// product carries no rounding of dE/dw (about 22 significant bits with FP16
+// operands, 16 with BF16): W3's own 16-bit rounding is then the only one left
+// in the per-path weights and their adjoint.
+template <int L, int MODE, bool SPLIT>
+struct BwdLayoutT {
   using G = Group<L, MODE>;
   static constexpr int NP = G::NP;
   static constexpr bool FIRST = MODE < 0;
   static constexpr int D = NodeDims<L>::D;
-  static constexpr int B2_BYTES = kNT * NP * 128 * 2;
+  static constexpr int B2H = kNT * NP * 128 * 2;
+  static constexpr int B2_BYTES = (SPLIT ? 2 : 1) * B2H;
   static constexpr int NZ = FIRST ? 0 : G::NZ;
   static constexpr int NZP = FIRST ? 4 : G::NZP;
   static constexpr int tmem_cols() {
@@ -692,8 +650,60 @@ struct BwdLayout {
   static constexpr size_t off_idx = off_taby + (((size_t)NZP + 15) & ~(size_t)15);
   static constexpr size_t off_bar = off_idx + 2 * kNT * 4;
   static constexpr size_t bytes = off_bar + 64;
-  static_assert(bytes <= 232448 - 1024, "shared memory of the adjoint kernel exceeds the per-block limit");
+  static constexpr bool fits = bytes <= 232448 - 1024;
 };
+
+
+// Pipelined form's buffers (see tp_fused_bwd_ws below).
+constexpr int kWSConsumers = 256, kWSProducers = 64, kWSThreads = kWSConsumers + kWSProducers;
+
+template <int L, int MODE, bool SPLIT>
+struct BwdLayoutWST {
+  using G = Group<L, MODE>;
+  static constexpr int NP = G::NP;
+  static constexpr bool FIRST = MODE < 0;
+  static constexpr int B2H = kNT * NP * 128 * 2;
+  static constexpr int B2_BYTES = (SPLIT ? 2 : 1) * B2H;
+  static constexpr int NZ = FIRST ? 0 : G::NZ;
+  static constexpr int NZP = FIRST ? 4 : G::NZP;
+  static constexpr int tmem_cols() {
+    int need = 2 * (NP + 1) * kNT, c = 32;
+    while (c < need) c <<= 1;
+    return c;
+  }
+  static constexpr int NCOLS = tmem_cols();
+  static constexpr size_t rest = 2 * kTileBytes + (size_t)2 * kNT * NZP * 4 + 2 * kNT * 16 * 4 + 16 * kNT * 16 * 4 +
+                                 (size_t)NZP * 4 + (((size_t)NZP + 15) & ~(size_t)15) + 4 * kNT * 4 + 4 * kNT * 4 + 128;
+  static constexpr int NB2 = (size_t)NP * kW3PathBytes + rest + 2 * (size_t)B2_BYTES <= 231424 ? 2 : 1;
+  static constexpr size_t off_z2 = (size_t)NP * kW3PathBytes;
+  static constexpr size_t off_b2 = off_z2 + 2 * kTileBytes;
+  static constexpr size_t off_cy = off_b2 + (size_t)NB2 * B2_BYTES;   // [2][kNT][NZP]
+  static constexpr size_t off_y = off_cy + (size_t)2 * kNT * NZP * 4; // [2][kNT][16]
+  static constexpr size_t off_red = off_y + 2 * kNT * 16 * 4;         // [2][8 warps][kNT][16]
+  static constexpr size_t off_tab = off_red + 16 * kNT * 16 * 4;
+  static constexpr size_t off_taby = off_tab + (size_t)NZP * 4;
+  static constexpr size_t off_idx = off_taby + (((size_t)NZP + 15) & ~(size_t)15);  // [2][send kNT, recv kNT]
+  static constexpr size_t off_dws = off_idx + 4 * kNT * 4;                          // [2][scale kNT, inverse kNT]
+  static constexpr size_t off_bar = off_dws + 4 * kNT * 4;
+  static constexpr size_t bytes = off_bar + 128;
+  // groups whose buffers do not fit keep the single-role kernel
+  static constexpr bool fits = bytes <= 232448 - 1024 && NCOLS <= 512;
+};
+
+// dE/dw is split into hi and lo tiles in every group whose adjoint buffers
+// still fit: the single-role kernel's, and the pipelined kernel's where that
+// kernel is used (one CTA per SM and its unsplit buffers fit).  At l <= 2 that
+// is every group; at l <= 3 the groups of up to four paths.
+template <int L, int MODE>
+struct DwSplit {
+  using N1 = BwdLayoutT<L, MODE, true>;
+  static constexpr bool ws_used = ctas_per_sm(N1::bytes) == 1 && BwdLayoutWST<L, MODE, false>::fits;
+  static constexpr bool value = N1::fits && (!ws_used || BwdLayoutWST<L, MODE, true>::fits);
+};
+template <int L, int MODE>
+using BwdLayout = BwdLayoutT<L, MODE, DwSplit<L, MODE>::value>;
+template <int L, int MODE>
+using BwdLayoutWS = BwdLayoutWST<L, MODE, DwSplit<L, MODE>::value>;
 
 template <int L, int MODE, int W>
 __device__ __forceinline__ void bwd_edge(const float* wv, int t, const float* hi, const float* Gi, const float* Gt,
@@ -740,8 +750,21 @@ __device__ __forceinline__ void bwd_edge(const float* wv, int t, const float* hi
         dYp[l2 * l2 + q] = fmaf(wp, Tp[q], dYp[l2 * l2 + q]);
       }
       const int kidx = sl * 128 + c;
-      *reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 + (kidx & 7) * 2) =
-          to16(dwp * dw_scale, use_bf16);
+      uint16_t* dst = reinterpret_cast<uint16_t*>(sB2 + (t >> 3) * SBO2 + (kidx >> 3) * 128 + (t & 7) * 16 +
+                                                  (kidx & 7) * 2);
+      const float x = dwp * dw_scale;
+      if constexpr (BwdLayout<L, MODE>::B2_BYTES > BwdLayout<L, MODE>::B2H) {
+        // hi and lo by Veltkamp's splitting (multiplier 2^s + 1, s = 24 - the format's significand
+        // bits): hi has the format's precision, so it is exact in it, and hi + lo = x exactly; one
+        // packed conversion then gives both 16-bit values, the lo tile following the hi tile
+        const float t = __fmul_rn(x, use_bf16 ? 65537.0f : 8193.0f);
+        const float hi = __fsub_rn(t, __fsub_rn(t, x));
+        const uint32_t pk = pack16x2(hi, __fsub_rn(x, hi), use_bf16);
+        dst[0] = (uint16_t)(pk & 0xFFFFu);
+        dst[BwdLayout<L, MODE>::B2H / 2] = (uint16_t)(pk >> 16);
+      } else {
+        dst[0] = to16(x, use_bf16);
+      }
     }
   });
 }
@@ -1013,6 +1036,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
                                                          const uint8_t* __restrict__ epar, int* __restrict__ err) {
   using G = Group<L, MODE>;
   using BL = BwdLayout<L, MODE>;
+  static_assert(BL::fits, "shared memory of the adjoint kernel exceeds the per-block limit");
   constexpr int D = NodeDims<L>::D;
   constexpr int NP = G::NP;
   constexpr bool FIRST = BL::FIRST;
@@ -1151,14 +1175,17 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
       const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sB2);
       const uint32_t kstride = 1024, mstride = 128;
       const uint32_t lbo = kMnLboIsK ? kstride : mstride, sbo = kMnLboIsK ? mstride : kstride;
+      constexpr int NH = BL::B2_BYTES / BL::B2H;  // dE/dw tiles: hi, and lo when split
 #pragma unroll 1
-      for (int sl = 0; sl < NP; ++sl)
+      for (int q = 0; q < NH * NP; ++q) {
+        const int sl = q % NP, half = q / NP;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 2 * kstride, lbo, sbo);
-          const uint64_t bd = tc::desc_noswizzle(b0 + sl * 2048 + kk * 256, 128, SBO2);
-          tc::mma_bf16(tbase + dcol, ad, bd, idesc2, (sl | kk) ? 1u : 0u);
+          const uint64_t bd = tc::desc_noswizzle(b0 + half * BL::B2H + sl * 2048 + kk * 256, 128, SBO2);
+          tc::mma_bf16(tbase + dcol, ad, bd, idesc2, (q | kk) ? 1u : 0u);
         }
+      }
       tc::mma_commit(bar_mma2);
     }
     // channel sums of dE/dY while the product runs
@@ -1260,39 +1287,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
 // buffer only after finishing the tile that last used it.  Long waits of the
 // producers sleep between polls so that they leave the issue slots to the
 // consumers.
-constexpr int kWSConsumers = 256, kWSProducers = 64, kWSThreads = kWSConsumers + kWSProducers;
 
-template <int L, int MODE>
-struct BwdLayoutWS {
-  using G = Group<L, MODE>;
-  static constexpr int NP = G::NP;
-  static constexpr bool FIRST = MODE < 0;
-  static constexpr int B2_BYTES = kNT * NP * 128 * 2;
-  static constexpr int NZ = FIRST ? 0 : G::NZ;
-  static constexpr int NZP = FIRST ? 4 : G::NZP;
-  static constexpr int tmem_cols() {
-    int need = 2 * (NP + 1) * kNT, c = 32;
-    while (c < need) c <<= 1;
-    return c;
-  }
-  static constexpr int NCOLS = tmem_cols();
-  static constexpr size_t rest = 2 * kTileBytes + (size_t)2 * kNT * NZP * 4 + 2 * kNT * 16 * 4 + 16 * kNT * 16 * 4 +
-                                 (size_t)NZP * 4 + (((size_t)NZP + 15) & ~(size_t)15) + 4 * kNT * 4 + 4 * kNT * 4 + 128;
-  static constexpr int NB2 = (size_t)NP * kW3PathBytes + rest + 2 * (size_t)B2_BYTES <= 231424 ? 2 : 1;
-  static constexpr size_t off_z2 = (size_t)NP * kW3PathBytes;
-  static constexpr size_t off_b2 = off_z2 + 2 * kTileBytes;
-  static constexpr size_t off_cy = off_b2 + (size_t)NB2 * B2_BYTES;   // [2][kNT][NZP]
-  static constexpr size_t off_y = off_cy + (size_t)2 * kNT * NZP * 4; // [2][kNT][16]
-  static constexpr size_t off_red = off_y + 2 * kNT * 16 * 4;         // [2][8 warps][kNT][16]
-  static constexpr size_t off_tab = off_red + 16 * kNT * 16 * 4;
-  static constexpr size_t off_taby = off_tab + (size_t)NZP * 4;
-  static constexpr size_t off_idx = off_taby + (((size_t)NZP + 15) & ~(size_t)15);  // [2][send kNT, recv kNT]
-  static constexpr size_t off_dws = off_idx + 4 * kNT * 4;                          // [2][scale kNT, inverse kNT]
-  static constexpr size_t off_bar = off_dws + 4 * kNT * 4;
-  static constexpr size_t bytes = off_bar + 128;
-  // groups whose buffers do not fit keep the single-role kernel
-  static constexpr bool fits = bytes <= 232448 - 1024 && NCOLS <= 512;
-};
 
 template <int L, int MODE>
 __global__ void __launch_bounds__(kWSThreads, 1)
@@ -1464,14 +1459,17 @@ __global__ void __launch_bounds__(kWSThreads, 1)
         const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sB2);
         const uint32_t kstride = 1024, mstride = 128;
         const uint32_t lbo = kMnLboIsK ? kstride : mstride, sbo = kMnLboIsK ? mstride : kstride;
+        constexpr int NH = BL::B2_BYTES / BL::B2H;  // dE/dw tiles: hi, and lo when split
 #pragma unroll 1
-        for (int sl = 0; sl < NP; ++sl)
+        for (int q = 0; q < NH * NP; ++q) {
+          const int sl = q % NP, half = q / NP;
 #pragma unroll
           for (int kk = 0; kk < 8; ++kk) {
             const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 2 * kstride, lbo, sbo);
-            const uint64_t bd = tc::desc_noswizzle(b0 + sl * 2048 + kk * 256, 128, SBO2);
-            tc::mma_bf16(tbase + dcol, ad, bd, idesc2, (sl | kk) ? 1u : 0u);
+            const uint64_t bd = tc::desc_noswizzle(b0 + half * BL::B2H + sl * 2048 + kk * 256, 128, SBO2);
+            tc::mma_bf16(tbase + dcol, ad, bd, idesc2, (q | kk) ? 1u : 0u);
           }
+        }
         tc::mma_commit(bar_mma2 + b);
       }
       {  // channel sums of dE/dY while the product runs
@@ -1864,16 +1862,6 @@ int pack_w3_groups(const mlip_model* M, int t, std::vector<uint8_t>& img, std::v
   return MLIP_OK;
 }
 
-int launch_radial_tiles(int H, int E, int n_tiles, const float4* ev, const float* W1, const float* W2, float rc,
-                        int p, int use_bf16, uint8_t* z2t, cudaStream_t st) {
-  if (n_tiles <= 0) return MLIP_OK;
-  if (H != 64) { set_error("the fused form needs hidden = 64"); return MLIP_ERR_INVALID_ARG; }
-  const int threads = 128, blocks = (n_tiles * kNT + threads - 1) / threads;
-  { MLIP_PROF("radial_tiles", st); radial_tiles<64><<<blocks, threads, 0, st>>>(E, n_tiles, ev, W1, W2, rc, p, use_bf16, z2t); }
-  MLIP_LAUNCH_CHECK();
-  return MLIP_OK;
-}
-
 // Forward message pass of one layer with the fused kernels: m = mA + mB (one
 // buffer per warp set), every component written.
 int launch_tp_fused(int L, bool first, int n, const int* row_ptr, const int* recv, const int* send,
@@ -2011,9 +1999,13 @@ int umma_selftest_mn_run(int variant, double* rel_err) {
   return MLIP_OK;
 }
 
-int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
-                         const NeighborList& nl, const int* Edev, int* flag, double* d_energy, double* d_forces,
-                         double* d_stress, cudaStream_t st) {
+// Forward half of one evaluation: edge geometry and harmonics, the layers, the
+// readout and the per-system energies.  What the adjoint half reads stays in
+// the model's workspace: the node features and mix pre-activations of every
+// layer (the contraction's inputs and the gate's pre-activations for those
+// options) and the per-system maxima that scale the adjoint's FP16 operand.
+int fused_forward_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                        const NeighborList& nl, const int* Edev, int* flag, double* d_energy, cudaStream_t st) {
   Workspace& ws = M->ws;
   const int n = (int)b.n, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H;
   const float s = (float)(1.0 / M->avg_nb);
@@ -2022,9 +2014,8 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
   const int n_tiles = (E + kNT - 1) / kNT;
   const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)std::max(n, 1) * D * C;
   CellArg ca{b.d_cell, b.d_sys_of, b.any_pbc() ? 1 : 0};
-  float4 *ev = nullptr, *g = nullptr;
-  float *mA = nullptr, *mB = nullptr, *Yg = nullptr, *Gm = nullptr, *dY = nullptr, *dr = nullptr, *dz2 = nullptr;
-  float *GaA = nullptr, *GaB = nullptr, *GbA = nullptr, *GbB = nullptr;
+  float4* ev = nullptr;
+  float *mA = nullptr, *mB = nullptr, *Yg = nullptr;
   double* atom_e = nullptr;
   MLIP_TRY(ws.get("ef.ev", Ec, &ev));
   MLIP_TRY(ws.get("fz.Y", Ec * 16, &Yg));
@@ -2053,21 +2044,6 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     }
     MLIP_LAUNCH_CHECK();
   }
-  // zero per-edge adjoint buffers: [E][per] floats
-  auto zero = [&](float* p, int per) -> int {
-    if (E <= 0) return MLIP_OK;
-    if (!Edev) {
-      MLIP_CUDA_TRY(cudaMemsetAsync(p, 0, (size_t)E * per * sizeof(float), st));
-      return MLIP_OK;
-    }
-    const long long n4 = ((long long)E * per + 3) / 4;
-    {
-      MLIP_PROF("zero_edges", st);
-      zero_edges<<<(int)std::min<long long>((n4 + 255) / 256, 8192), 256, 0, st>>>(Edev, per, p);
-    }
-    MLIP_LAUNCH_CHECK();
-    return MLIP_OK;
-  };
   // per layer t and system: max |h^t|, max |dE/dm^t| (FP16 operand scale of the adjoint), accumulated by
   // the kernels that write those tensors
   float* absmax = nullptr;
@@ -2100,7 +2076,69 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
   } else {
     MLIP_TRY(launch_energy(ws, b, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, d_energy, st));
   }
-  if (d_forces || d_stress) {
+  return MLIP_OK;
+}
+
+// Adjoint half: forces and stress from the workspace the forward half left.
+// With recompute (a separate forward call came before) the edge geometry, the
+// harmonics and every layer's radial MLP output z2 are computed again from the
+// positions instead of being read from the forward's per-edge buffers.
+int fused_adjoint_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                         const NeighborList& nl, const int* Edev, int* flag, double* d_forces, double* d_stress,
+                         bool recompute, cudaStream_t st) {
+  Workspace& ws = M->ws;
+  const int n = (int)b.n, C = M->C, D = M->D, T = M->T, L = M->L, H = M->H;
+  const float s = (float)(1.0 / M->avg_nb);
+  const int use_bf16 = M->precision == MLIP_PREC_BF16 ? 1 : 0;
+  const int E = (int)nl.E;
+  const int n_tiles = (E + kNT - 1) / kNT;
+  const size_t Ec = (size_t)std::max(E, 1), ND = (size_t)std::max(n, 1) * D * C;
+  CellArg ca{b.d_cell, b.d_sys_of, b.any_pbc() ? 1 : 0};
+  float4 *ev = nullptr, *g = nullptr;
+  float *Yg = nullptr, *Gm = nullptr, *dY = nullptr, *dr = nullptr, *dz2 = nullptr;
+  float *GaA = nullptr, *GaB = nullptr, *GbA = nullptr, *GbB = nullptr;
+  MLIP_TRY(ws.get("ef.ev", Ec, &ev));
+  MLIP_TRY(ws.get("fz.Y", Ec * 16, &Yg));
+  std::vector<float*> h(T + 1), u0(T), A(T, nullptr), gpre(T, nullptr), gg(T, nullptr);
+  std::vector<uint8_t*> z2t(T);
+  for (int t = 0; t <= T; ++t) MLIP_TRY(ws.get("ef.h" + std::to_string(t), ND, &h[t]));
+  for (int t = 0; t < T; ++t) {
+    MLIP_TRY(ws.get("ef.u" + std::to_string(t), (size_t)n * C, &u0[t]));
+    if (M->corr == 2) MLIP_TRY(ws.get("ef.A" + std::to_string(t), ND, &A[t]));
+    if (M->gate) {
+      MLIP_TRY(ws.get("ef.gpre" + std::to_string(t), ND, &gpre[t]));
+      MLIP_TRY(ws.get("ef.gg" + std::to_string(t), (size_t)std::max(n, 1) * L * C, &gg[t]));
+    }
+    MLIP_TRY(ws.get("fz.z2t" + std::to_string(t), (size_t)std::max(n_tiles, 1) * kTileBytes, &z2t[t]));
+  }
+  uint8_t* epar = nullptr;
+  MLIP_TRY(ws.get("fz.epar", Ec, &epar));
+  if (recompute && E > 0) {
+    {
+      MLIP_PROF("edge_sh", st);
+      edge_sh<<<std::min((E + 255) / 256, 8192), 256, 0, st>>>(E, d_pos, nl.send, nl.shift, ca, ev, Yg, Edev,
+                                                               nl.row_ptr, nl.recv, epar);
+    }
+    MLIP_LAUNCH_CHECK();
+  }
+  auto zero = [&](float* p, int per) -> int {
+    if (E <= 0) return MLIP_OK;
+    if (!Edev) {
+      MLIP_CUDA_TRY(cudaMemsetAsync(p, 0, (size_t)E * per * sizeof(float), st));
+      return MLIP_OK;
+    }
+    const long long n4 = ((long long)E * per + 3) / 4;
+    {
+      MLIP_PROF("zero_edges", st);
+      zero_edges<<<(int)std::min<long long>((n4 + 255) / 256, 8192), 256, 0, st>>>(Edev, per, p);
+    }
+    MLIP_LAUNCH_CHECK();
+    return MLIP_OK;
+  };
+  float* absmax = nullptr;
+  MLIP_TRY(ws.get("fz.absmax", 2 * (size_t)T * b.nsys, &absmax));
+  auto amax_h = [&](int t) -> float* { return use_bf16 || t >= T ? nullptr : absmax + 2 * (size_t)t * b.nsys; };
+  {
     MLIP_TRY(ws.get("ef.g", Ec, &g));
     MLIP_TRY(ws.get("ef.Gm", ND, &Gm));
     MLIP_TRY(ws.get("ef.Ga", ND, &GaA));
@@ -2134,6 +2172,9 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
                                                         dws2);
         MLIP_LAUNCH_CHECK();
       }
+      if (recompute)  // the radial weights of this layer, again from the edge lengths
+        MLIP_TRY(launch_radial_tc(H, E, n_tiles, ev, M->W1[t], M->d_radimg + (size_t)t * 32768, M->rad_scale[t],
+                                  (float)M->rc, M->p, use_bf16, z2t[t], flag + 1, st, Edev));
       MLIP_TRY(launch_tp_fused_bwd(L, t == 0, n, nl.row_ptr, nl.recv, nl.send, Yg, h[t], Gm,
                                    M->d_w3img + M->w3_layer_off[t], M->w3_goff[t], z2t[t], s, GaA, GaB, GbA, GbB, dY,
                                    dz2, use_bf16, b.d_sys_of, dws2, epar, flag + 1, st));
@@ -2148,6 +2189,15 @@ int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_specie
     MLIP_TRY(launch_forces_virial(ws, b, nl.row_ptr, nl.rev, g, ev, fbuf, d_stress, st));
     if (M->charges) MLIP_TRY(coulomb_add_forces(ws, b, fbuf, st));
   }
+  return MLIP_OK;
+}
+
+int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                         const NeighborList& nl, const int* Edev, int* flag, double* d_energy, double* d_forces,
+                         double* d_stress, cudaStream_t st) {
+  MLIP_TRY(fused_forward_edges(M, d_pos, d_species, b, nl, Edev, flag, d_energy, st));
+  if (d_forces || d_stress)
+    MLIP_TRY(fused_adjoint_edges(M, d_pos, d_species, b, nl, Edev, flag, d_forces, d_stress, false, st));
   return MLIP_OK;
 }
 

@@ -89,6 +89,23 @@ int evaluate_fused(mlip_model* M, const double* d_pos, const int* d_species, con
 int evaluate_fused_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
                          const NeighborList& nl, const int* Edev, int* flag, double* d_energy, double* d_forces,
                          double* d_stress, cudaStream_t st);
+// The two halves of evaluate_fused_edges, for the separate forward and
+// backward entry points.  The forward leaves in the workspace what the adjoint
+// reads (node features and pre-activations of every layer, the FP16 operand
+// scales); the adjoint with recompute first computes the edge geometry, the
+// harmonics and, layer by layer, the radial weights again from the positions.
+int fused_forward_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                        const NeighborList& nl, const int* Edev, int* flag, double* d_energy, cudaStream_t st);
+int fused_adjoint_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                        const NeighborList& nl, const int* Edev, int* flag, double* d_forces, double* d_stress,
+                        bool recompute, cudaStream_t st);
+// The plain form's halves on a given neighbour list (its adjoint reads the
+// per-edge radial weights the forward stored: the stored-intermediate design
+// of the comparator form).
+int plain_forward_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                        const NeighborList& nl, double* d_energy, cudaStream_t st);
+int plain_adjoint_edges(mlip_model* M, const double* d_pos, const int* d_species, const SystemBatch& b,
+                        const NeighborList& nl, double* d_forces, double* d_stress, cudaStream_t st);
 // Synchronises st and turns the flags of evaluate_fused_edges into a status.
 int check_eval_flags(const int* flag, cudaStream_t st);
 // evaluate_fused for callers that repeat the same batch layout (one system

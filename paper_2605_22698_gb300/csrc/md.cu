@@ -260,6 +260,7 @@ extern "C" int mlip_md_nve_skin(mlip_model* M, int32_t n_systems, const int64_t*
   cudaStream_t st = R.st;
   Workspace& ws = M->ws;
   WsStream wss(ws, st);  // restored before the run's stream is destroyed (declared after R)
+  ++M->eval_gen;         // the run writes the workspace: a saved separate forward is no longer usable
   double *d_pos = pos, *d_vel = vel, *d_F = nullptr, *d_mass = nullptr, *d_pe = nullptr, *d_ke = nullptr,
          *d_dt = nullptr;
   const int* d_sp = species;

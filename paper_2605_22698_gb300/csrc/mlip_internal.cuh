@@ -246,4 +246,11 @@ struct mlip_model {
   mlip::Workspace ws;
   mlip::HostStage stage;
   mlip::EvalGraphs* egraph = nullptr;  // cached CUDA graphs of the fused evaluation (fused_bf16.cu)
+  // The last separate forward evaluation (mlip_energy_forward), which
+  // mlip_energy_backward differentiates: its batch and neighbour list (device
+  // tables in the workspace).  Every evaluation that writes the workspace bumps
+  // eval_gen; the saved forward is usable while tape_gen == eval_gen.
+  uint64_t eval_gen = 0, tape_gen = 0;
+  mlip::SystemBatch tape_batch;
+  mlip::NeighborList tape_nl;
 };

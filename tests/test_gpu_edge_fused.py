@@ -3,14 +3,12 @@ one atom, pairs beyond the cutoff (no edges), a handful of edges (one partial
 tile), pairs just inside the cutoff; repeated calls through the replayed
 graph; the Coulomb term acting beyond the cutoff with no edges at all.
 
-Bar of the F16 form here: 2e-3 of max|F_ref| (energy: of max(|E|, sum|E_i|)),
-or 4x the oracle's own change when W3 alone is rounded to FP16, whichever is
-larger.  The form rounds W3 and z2 to FP16 for the per-path weights; on a few
-isolated pairs whose forces are far below the size of the per-edge terms
-(cancelling paths and layers) that rounding alone moves the oracle's forces
-by more than 2e-3 of max|F| (1.6e-3 for W3 on the two-far-pairs system,
-against 3.9e-4 on the 300-atom water box), so no FP16-operand product meets
-the relative bar there; the second factor is the same rounding applied to z2.
+Bar of the F16 form: 2e-3 of max|F_ref| (energy: of max(|E|, sum|E_i|)), the
+same as on the large systems.  On two isolated pairs the forces are far below
+the size of the per-edge terms (cancelling paths and layers), so W3's own FP16
+rounding moves the oracle's forces by 1.6e-3 of max|F| there (3.9e-4 on the
+300-atom water box); the form's other products carry no 16-bit rounding, and
+each check prints the measured error.
 """
 import numpy as np
 import pytest
@@ -41,45 +39,26 @@ def B():
     return binding
 
 
-def _assert_close(out, ref, tol, sens=None):
-    """sens: (|dE|, max|dF|) of the oracle with W3 rounded to FP16 (16-bit forms)."""
+def _assert_close(out, ref, tol, label=""):
     scale = max(abs(ref["energy"]), float(np.abs(ref["atom_energies"]).sum()))
     ebar, fbar = tol * scale, tol * np.abs(ref["forces"]).max()
-    if sens is not None:
-        ebar, fbar = max(ebar, 4.0 * sens[0]), max(fbar, 4.0 * sens[1])
     assert abs(float(np.asarray(out["energy"]).reshape(-1)[0]) - ref["energy"]) <= max(ebar, 1e-12)
     err = np.abs(np.asarray(out["forces"]) - ref["forces"]).max()
+    print(f" {label}: max|dF|/max|F| = {err / max(np.abs(ref['forces']).max(), 1e-300):.2e} (bar {tol:g})", end="")
     assert err <= max(fbar, 1e-12), (err, fbar)
-
-
-def _w3_fp16(spec, w):
-    """The weights with every layer's W3 rounded to FP16 (nothing else changed)."""
-    w2 = w.copy()
-    off = 0
-    for name, shape, _ in spec.weight_shapes():
-        k = int(np.prod(shape))
-        if name.startswith("W3."):
-            w2[off:off + k] = w2[off:off + k].astype(np.float16).astype(np.float32)
-        off += k
-    return w2
-
-
-def _sens(om16, pos, z, ref):
-    r = om16.energy_forces(pos, z, np.eye(3), np.zeros(3, np.uint8))
-    return abs(r["energy"] - ref["energy"]), float(np.abs(r["forces"] - ref["forces"]).max())
 
 
 @pytest.mark.parametrize("name", ["water", "water_mace"])
 def test_fused_degenerate_systems(B, name):
     spec = synth.model_spec(name)
     w = synth.make_weights(spec, 21)
-    om, om16 = oracle.Model(spec, w), oracle.Model(spec, _w3_fp16(spec, w))
+    om = oracle.Model(spec, w)
     cell, pbc = np.eye(3), np.zeros(3, np.uint8)
     for label, pos, z in SYSTEMS:
         ref = om.energy_forces(pos, z, cell, pbc, atom_energies=True)
         m = B.Model(spec, w, B.MLIP_PREC_F16)
         first = m.energy_forces(pos, z, cell, pbc)
-        _assert_close(first, ref, 2e-3, _sens(om16, pos, z, ref))
+        _assert_close(first, ref, 2e-3, label)
         for _ in range(4):  # eager, capture, replays: the same numbers
             r = m.energy_forces(pos, z, cell, pbc)
             assert all(np.array_equal(r[k], first[k]) for k in first), label
@@ -92,16 +71,15 @@ def test_charged_degenerate_systems(B, prec, tol):
     edges or not: two atoms beyond the cutoff still attract or repel."""
     spec = synth.model_spec("water_charged")
     w = synth.make_weights(spec, 21)
-    om, om16 = oracle.Model(spec, w), oracle.Model(spec, _w3_fp16(spec, w))
+    om = oracle.Model(spec, w)
     p = {"fp32": B.MLIP_PREC_FP32, "f16": B.MLIP_PREC_F16}[prec]
     for Q in (0.0, 1.0):
         om.set_total_charge(Q)
-        om16.set_total_charge(Q)
         for label, pos, z in SYSTEMS:
             ref = om.energy_forces(pos, z, np.eye(3), np.zeros(3, np.uint8), atom_energies=True)
             m = B.Model(spec, w, p)
             out = m.energy_forces_charged(pos, z, Q)
-            _assert_close(out, ref, tol, _sens(om16, pos, z, ref) if prec == "f16" else None)
+            _assert_close(out, ref, tol, label)
             np.testing.assert_allclose(out["charges"], om.charges(pos, z), rtol=0,
                                        atol=tol * max(1.0, np.abs(om.charges(pos, z)).max()))
             if label == "beyond the cutoff" and Q == 0.0:

@@ -1,11 +1,13 @@
 """GPU checks of the fused tensor-core form (tcgen05 radial MLP) against the FP64 oracle.
 
-Tolerance of the 16-bit forms (radial MLP operands rounded to 16 bits, FP32
-accumulation): energy |E - E_ref| <= 2e-3 max(|E_ref|, sum_i |E_i,ref|),
-forces max |F - F_ref| <= 2e-3 max |F_ref|, stress likewise.  The FP16-operand
-form meets it everywhere; the BF16-operand form is held to 5e-3 (its 8-bit
-significand alone gives 1.5e-3 on the water box from rounding W3, measured
-with the oracle on BF16-rounded weights).
+Tolerance of the 16-bit forms: energy |E - E_ref| <= 2e-3 max(|E_ref|,
+sum_i |E_i,ref|), forces max |F - F_ref| <= 2e-3 max |F_ref|, stress
+max |s - s_ref| <= 2e-3 max |s_ref|.  The FP16-operand form meets all three;
+the BF16-operand form meets them for energy and forces, and its stress is held
+to 5e-3 max |s_ref|: rounding W3 alone to BF16 moves the oracle's own stress by
+2.8e-3 (300 atoms) and 3.5e-3 (3000 atoms) of max |s_ref|, and the form's
+other products carry no 16-bit rounding (dE/dw is split into hi and lo).
+Every check prints the measured error next to its bar.
 """
 import numpy as np
 import pytest
@@ -39,7 +41,7 @@ def test_tensor_core_transposed_operand_selftest(B):
     assert B.mlip_selftest(2) < 1e-5
 
 
-def _check(out, ref, stress=False, tol=TOL, cell=None, n_edges=0):
+def _check(out, ref, stress=False, tol=TOL, stol=None):
     scale = max(abs(ref["energy"]), float(np.abs(ref["atom_energies"]).sum()))
     E = float(np.asarray(out["energy"]).reshape(-1)[0])
     assert abs(E - ref["energy"]) <= tol * scale, (E, ref["energy"])
@@ -47,16 +49,16 @@ def _check(out, ref, stress=False, tol=TOL, cell=None, n_edges=0):
     err = np.abs(np.asarray(out["forces"]) - ref["forces"]).max()
     assert err <= tol * fmax, (err, fmax)
     if stress:
-        # the stress is a sum of E virial terms x_e (x) g_e / V that largely
-        # cancel; its error scale is that of a random sum of E terms of size
-        # rc max|F|, so the bar is tol * max(max|s_ref|, rc max|F| sqrt(E) / V)
-        V = abs(np.linalg.det(cell))
-        sscale = max(np.abs(ref["stress"]).max(), 5.0 * fmax * np.sqrt(n_edges) / V)
-        assert np.abs(np.asarray(out["stress"]) - ref["stress"]).max() <= tol * sscale
+        smax = np.abs(ref["stress"]).max()
+        serr = np.abs(np.asarray(out["stress"]) - ref["stress"]).max()
+        stol = tol if stol is None else stol
+        print(f" stress: max|ds|/max|s_ref| = {serr / smax:.2e} (bar {stol:g})", end="")
+        assert serr <= stol * smax, (serr, smax)
     return err / fmax
 
 
-PRECS = [("f16", 2e-3), ("bf16", 5e-3)]
+PRECS = [("f16", 2e-3), ("bf16", 2e-3)]
+STRESS_TOL = {"f16": 2e-3, "bf16": 5e-3}
 
 
 def _prec(B, name):
@@ -81,10 +83,9 @@ def test_fused_forces_stress_water(B, nmol, prec, tol):
     s = synth.water_box(nmol, synth.water_side_for(nmol), seed=2)
     ref = _oracle(("water", nmol), spec, w, s, True)
     m = B.Model(spec, w, _prec(B, prec))
-    ne = len(oracle.neighbors(s.pos, s.cell, s.pbc, 5.0)[0])
     rel = _check(m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=True), ref, stress=True, tol=tol,
-                 cell=s.cell, n_edges=ne)
-    print(f"water{3 * nmol} {prec}: max|dF|/max|F| = {rel:.2e}")
+                 stol=STRESS_TOL[prec])
+    print(f" water{3 * nmol} {prec}: max|dF|/max|F| = {rel:.2e} (bar {tol:g})")
 
 
 @pytest.mark.parametrize("prec,tol", PRECS)
@@ -94,10 +95,9 @@ def test_fused_forces_stress_fcc_l3(B, prec, tol):
     s = synth.fcc((5, 10, 10), seed=3)
     ref = _oracle(("fcc", 2000), spec, w, s, True)
     m = B.Model(spec, w, _prec(B, prec))
-    ne = len(oracle.neighbors(s.pos, s.cell, s.pbc, 5.0)[0])
     rel = _check(m.energy_forces(s.pos, s.species, s.cell, s.pbc, stress=True), ref, stress=True, tol=tol,
-                 cell=s.cell, n_edges=ne)
-    print(f"fcc2000 {prec}: max|dF|/max|F| = {rel:.2e}")
+                 stol=STRESS_TOL[prec])
+    print(f" fcc2000 {prec}: max|dF|/max|F| = {rel:.2e} (bar {tol:g})")
 
 
 @pytest.mark.parametrize("prec,tol", PRECS)
@@ -108,7 +108,7 @@ def test_fused_forces_open_cluster(B, prec, tol):
     ref = _oracle(("cluster", 500), spec, w, s, False)
     m = B.Model(spec, w, _prec(B, prec))
     rel = _check(m.energy_forces(s.pos, s.species, s.cell, s.pbc), ref, tol=tol)
-    print(f"cluster500 {prec}: max|dF|/max|F| = {rel:.2e}")
+    print(f" cluster500 {prec}: max|dF|/max|F| = {rel:.2e} (bar {tol:g})")
 
 
 @pytest.mark.parametrize("name,nmol", [("water", 100), ("water", 1000)])
