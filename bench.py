@@ -682,7 +682,8 @@ def serve_phase(args, rank, world, R, sweep, alone):
                     "bucket_p50_ms": [round(x, 2) for x in st["bucket_p50_ms"]],
                     "bucket_p99_ms": [round(x, 2) for x in st["bucket_p99_ms"]],
                     "mean_batch_atoms": round(st["mean_batch_atoms"], 1),
-                    "mean_batch_requests": round(st["mean_batch_requests"], 2)},
+                    "mean_batch_requests": round(st["mean_batch_requests"], 2),
+                    "skin_steps": int(st["skin_steps"]), "skin_builds": int(st["skin_builds"])},
         "rate_sweep": sw,
         "alone_ms": alone_ms,
         "saturated": {"requests_per_s": round(sat_rps, 2), "p50_ms": round(st_sat["p50_ms"], 2),

@@ -393,6 +393,8 @@ typedef struct {
   int32_t n_buckets;
   int64_t bucket_count[9];
   double bucket_p50_ms[9], bucket_p99_ms[9];
+  int64_t skin_steps;         /* MD steps evaluated on the resident skin neighbour list (no rebuild) */
+  int64_t skin_builds;        /* skin list builds: a batch of NVE requests kept its members, or an atom left its skin */
 } mlip_serve_statistics;
 
 /* Starts the worker.  Errors: MLIP_ERR_INVALID_ARG (bad config: max_slots < 0,

@@ -512,7 +512,8 @@ class mlip_serve_statistics(ctypes.Structure):
                 ("mean_batch_atoms", ctypes.c_double), ("mean_batch_requests", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("n_buckets", ctypes.c_int32),
                 ("bucket_count", ctypes.c_int64 * 9), ("bucket_p50_ms", ctypes.c_double * 9),
-                ("bucket_p99_ms", ctypes.c_double * 9)]
+                ("bucket_p99_ms", ctypes.c_double * 9), ("skin_steps", ctypes.c_int64),
+                ("skin_builds", ctypes.c_int64)]
 
 
 def _serve_lib():

@@ -8,7 +8,9 @@
 //   2. applies the first half kick and the drift to the NVE requests past
 //      their first evaluation;
 //   3. evaluates every running request as one graph (the disjoint union of
-//      the systems' neighbour graphs);
+//      the systems' neighbour graphs); a batch of NVE requests whose members
+//      stay the same keeps a skin neighbour list on the device between
+//      iterations (compacted every step, rebuilt when an atom leaves its skin);
 //   4. applies the second half kick, sums per-system kinetic energies, copies
 //      back per-system energies and the outputs of the requests that end;
 //   5. ends finished requests (t_done) and wakes their waiters.
@@ -175,6 +177,28 @@ struct mlip_server {
   int64_t arena_n = 0;
   double per_atom_bytes = 0.0;
   int64_t held_bytes = 0;
+  // Skin neighbour list of the running batch, kept on the device between
+  // iterations while the membership stays the same (an NVE-only batch): built
+  // at r_c + skin, compacted to r_c at every step, rebuilt when an atom moves
+  // more than skin/2; the compaction and evaluation of a step are captured as
+  // one CUDA graph and replayed.  skin_ok: the list belongs to the current
+  // arena and batch.
+  mlip::SkinList sl;
+  bool skin_ok = false;
+  std::atomic<int64_t> skin_reuses{0}, skin_builds{0};  // read by mlip_serve_stats
+  cudaGraph_t sgraph = nullptr;
+  cudaGraphExec_t sexec = nullptr;
+  uint64_t swarm_gen = ~0ULL, sgraph_gen = ~0ULL;
+  int64_t swarm_cap = -1, sgraph_cap = -1;
+  long long sgraph_kernels = 0;
+  void drop_skin_graph() {
+    if (sexec) cudaGraphExecDestroy(sexec);
+    if (sgraph) cudaGraphDestroy(sgraph);
+    sexec = nullptr;
+    sgraph = nullptr;
+    swarm_gen = sgraph_gen = ~0ULL;
+    swarm_cap = sgraph_cap = -1;
+  }
 };
 
 namespace mlip {
@@ -340,10 +364,84 @@ namespace {
 // A failure is fatal for the server when the CUDA context no longer works.
 bool context_broken() { return cudaDeviceSynchronize() != cudaSuccess; }
 
+constexpr double kServeSkin = 2.0;  // A: candidates within r_c + skin
+
+// Forces and energies of the batch at the arena's current positions from the
+// resident skin list: compaction to r_c and the evaluation (a replayed graph
+// after one eager run at the same workspace and capacity), then the skin check;
+// if an atom left its skin the list is rebuilt at the current positions and
+// the step evaluated again (its forces overwritten).  The results equal a
+// fresh list's bit for bit.
+int skin_evaluate(mlip_server* S, const SystemBatch& b, const Arena& A, double* d_E, double* d_S) {
+  mlip_model* M = S->M;
+  cudaStream_t st = S->st;
+  Workspace& ws = M->ws;
+  SkinList& sl = S->sl;
+  ++M->eval_gen;
+  int* flag = nullptr;
+  MLIP_TRY(ws.get("chk.flag", 2, &flag));
+  auto once = [&]() -> int {
+    MLIP_TRY(launch_check_inputs((int)b.n, A.pos, A.species, M->S, flag, st));
+    MLIP_TRY(skin_compact(ws, sl, A.pos, b, st));
+    return evaluate_fused_edges(M, A.pos, A.species, b, sl.nl, sl.Edev(), flag, d_E, A.F, d_S, st);
+  };
+  auto reset = [&]() -> int {
+    MLIP_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
+    MLIP_CUDA_TRY(cudaMemsetAsync(sl.flags, 0, 2 * sizeof(int), st));
+    return MLIP_OK;
+  };
+  MLIP_TRY(reset());
+  const bool graphs = !prof_timing_on();
+  if (graphs && S->sexec && S->sgraph_gen == ws.gen && S->sgraph_cap == sl.cap) {
+    MLIP_CUDA_TRY(cudaGraphLaunch(S->sexec, st));
+    prof_add_launches(S->sgraph_kernels);
+  } else if (graphs && S->swarm_gen == ws.gen && S->swarm_cap == sl.cap) {
+    if (S->sexec) cudaGraphExecDestroy(S->sexec);
+    if (S->sgraph) cudaGraphDestroy(S->sgraph);
+    S->sexec = nullptr;
+    S->sgraph = nullptr;
+    const long long l0 = prof_launches();
+    MLIP_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    const int rc = once();
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (rc != MLIP_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (rc != MLIP_OK) return rc;
+      set_error("serve: graph capture failed: %s", cudaGetErrorString(ce));
+      return MLIP_ERR_CUDA;
+    }
+    S->sgraph = g;
+    MLIP_CUDA_TRY(cudaGraphInstantiate(&S->sexec, S->sgraph, 0));
+    S->sgraph_kernels = prof_launches() - l0;
+    S->sgraph_gen = ws.gen;
+    S->sgraph_cap = sl.cap;
+    MLIP_CUDA_TRY(cudaGraphLaunch(S->sexec, st));
+  } else {
+    MLIP_TRY(once());
+    S->swarm_gen = ws.gen;
+    S->swarm_cap = sl.cap;
+  }
+  MLIP_TRY(check_eval_flags(flag, st));
+  int hs[2] = {0, 0};
+  MLIP_CUDA_TRY(cudaMemcpyAsync(hs, sl.flags, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  MLIP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hs[1]) { set_error("serve: skin list: a kept edge has no kept reverse edge"); return MLIP_ERR_INVALID_ARG; }
+  if (hs[0]) {  // an atom left its skin: a fresh list at the current positions, the step again
+    MLIP_TRY(skin_build(ws, A.pos, b, M->rc, kServeSkin, &sl, st));
+    ++S->skin_builds;
+    MLIP_TRY(reset());
+    MLIP_TRY(once());
+    MLIP_TRY(check_eval_flags(flag, st));
+  }
+  ++S->skin_reuses;
+  return MLIP_OK;
+}
+
 // One batched force evaluation over `cur` (arena A).  Per-request failures end
 // those requests (status in the request); the return value is an error only
 // when the server cannot go on (broken context, device timeout).
-int iterate(mlip_server* S, std::vector<ReqPtr>& cur, const Arena& A, std::vector<ReqPtr>& ended) {
+int iterate(mlip_server* S, std::vector<ReqPtr>& cur, const Arena& A, bool same_members, std::vector<ReqPtr>& ended) {
   mlip_model* M = S->M;
   cudaStream_t st = S->st;
   WsStream wss(S->ws, st), wsm(M->ws, st);
@@ -392,7 +490,14 @@ int iterate(mlip_server* S, std::vector<ReqPtr>& cur, const Arena& A, std::vecto
     MLIP_TRY(launch_vv_drift(b, d_dt, d_active, A.vel, A.pos, st));
   }
   std::vector<int> slot_rc(nsys, MLIP_OK);
-  int rc = evaluate(M, A.pos, A.species, b, d_E, A.F, d_S, st, true);  // a graph while the membership stays
+  if (!same_members) S->skin_ok = false;  // the arena was rebuilt: the list's atom order is gone
+  const bool fused = M->precision != MLIP_PREC_FP32;
+  int rc = MLIP_OK;
+  if (fused && S->skin_ok && any_active)
+    rc = skin_evaluate(S, b, A, d_E, d_S);  // the resident list, compacted to this step's positions
+  else
+    rc = evaluate(M, A.pos, A.species, b, d_E, A.F, d_S, st, true);  // a graph while the membership stays
+  if (rc != MLIP_OK) S->skin_ok = false;
   if (rc != MLIP_OK) {
     if (context_broken()) return MLIP_ERR_CUDA;
     if (nsys == 1) {
@@ -443,6 +548,22 @@ int iterate(mlip_server* S, std::vector<ReqPtr>& cur, const Arena& A, std::vecto
       MLIP_CUDA_TRY(cudaMemcpyAsync(hx, A.pos + 3 * r.off, bytes, cudaMemcpyDeviceToHost, st));
       MLIP_CUDA_TRY(cudaMemcpyAsync(hx + 3 * r.n, A.vel + 3 * r.off, bytes, cudaMemcpyDeviceToHost, st));
       hx += 6 * r.n;
+    }
+  }
+  // an NVE-only batch whose requests all go on keeps its members unless new
+  // requests arrive: its skin list is built now, at the positions of the next
+  // step's start, if it has none
+  bool keep_members = fused;
+  for (int s = 0; s < nsys && keep_members; ++s) keep_members = !ends[s] && cur[s]->kind == MLIP_REQ_NVE;
+  if (keep_members && !S->skin_ok) {
+    S->drop_skin_graph();
+    const int brc = skin_build(M->ws, A.pos, b, M->rc, kServeSkin, &S->sl, st);
+    if (brc != MLIP_OK) {
+      if (context_broken()) return MLIP_ERR_CUDA;
+      cudaGetLastError();
+    } else {
+      S->skin_ok = true;
+      ++S->skin_builds;
     }
   }
   cudaEvent_t ev;
@@ -531,7 +652,7 @@ void worker_main(mlip_server* S) {
     if (changed || !fresh.empty()) rc = compact(S, cur, n_old, &A);
     else rc = get_arena(S, S->arena, S->arena_n, &A);
     std::vector<ReqPtr> ended;
-    if (rc == MLIP_OK) rc = iterate(S, cur, A, ended);
+    if (rc == MLIP_OK) rc = iterate(S, cur, A, !(changed || !fresh.empty()), ended);
     const double dt_it = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_it).count();
     std::lock_guard<std::mutex> lk(S->mu);
     S->running = cur;
@@ -777,6 +898,8 @@ extern "C" int mlip_serve_stats(mlip_server* S, mlip_serve_statistics* out) {
     out->bucket_p50_ms[b] = pct(per[b], 0.50);
     out->bucket_p99_ms[b] = pct(per[b], 0.99);
   }
+  out->skin_steps = S->skin_reuses.load();
+  out->skin_builds = S->skin_builds.load();
   return MLIP_OK;
 }
 
@@ -789,6 +912,7 @@ extern "C" int mlip_serve_destroy(mlip_server* S) {
   S->cv_work.notify_all();
   if (S->worker.joinable()) S->worker.join();
   cudaStreamSynchronize(S->st);
+  S->drop_skin_graph();
   cudaStreamDestroy(S->st);
   cudaGetLastError();
   delete S;

@@ -69,7 +69,8 @@ int main(void) {
   F(mlip_result, energy) F(mlip_result, stress) F(mlip_result, forces) F(mlip_result, ke) F(mlip_result, t_done)
   Z(mlip_result)
   F(mlip_serve_statistics, elapsed_s) F(mlip_serve_statistics, device_bytes) F(mlip_serve_statistics, n_buckets)
-  F(mlip_serve_statistics, bucket_count) F(mlip_serve_statistics, bucket_p99_ms) Z(mlip_serve_statistics)
+  F(mlip_serve_statistics, bucket_count) F(mlip_serve_statistics, bucket_p99_ms) F(mlip_serve_statistics, skin_steps)
+  F(mlip_serve_statistics, skin_builds) Z(mlip_serve_statistics)
   F(mlip_md_options, rebuild_every) F(mlip_md_options, use_graph) Z(mlip_md_options)
   F(mlip_md_report, redone_blocks) F(mlip_md_report, max_candidates) F(mlip_md_report, max_displacement)
   Z(mlip_md_report)

@@ -2,11 +2,15 @@
 
 Every request's result must equal the single-system call on its own (alone vs
 in a mix), bit for bit: the batch evaluation is independent of the other
-systems in it, and the velocity-Verlet updates are per atom.
+systems in it, and the velocity-Verlet updates are per atom.  NVE batches that
+keep their members step on a skin neighbour list kept on the device (equal to
+fresh lists bit for bit, rebuilt when an atom leaves its skin), and served
+results of both kinds agree with the FP64 oracle within the form's tolerance.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -185,3 +189,60 @@ def test_host_wait_limit_stops_the_server(B):
     # the model is usable again once the server is gone
     out = m.energy_forces(s.pos, s.species, s.cell, s.pbc)
     assert np.isfinite(out["energy"][0])
+
+
+def test_nve_batch_on_the_resident_skin_list(B):
+    """Two NVE requests admitted together and nothing else: after the first
+    iteration the batch keeps its members, so its steps run on the resident
+    skin list (skin_steps counts them).  One request drifts as a whole at
+    0.05 A/fs, so it moves more than skin/2 = 1 A within 40 steps and the list
+    is rebuilt mid-run.  Both trajectories equal mlip_md_nve's (a fresh list
+    at every step) bit for bit."""
+    m, spec = _model(B, "f16")
+    ref_model, _ = _model(B, "f16")
+    masses = np.asarray(spec.masses)
+    a, b = synth.cluster(300, seed=21), synth.cluster(120, seed=22)
+    va = synth.maxwell_boltzmann(masses[a.species], 300.0, seed=31)
+    vb = synth.maxwell_boltzmann(masses[b.species], 300.0, seed=32) + np.array([0.05, 0.0, 0.0])
+    srv = B.Server(m, max_slots=8)
+    ids = [srv.submit(B.MLIP_REQ_NVE, a.pos, a.species, vel=va, n_steps=60, dt_fs=0.5),
+           srv.submit(B.MLIP_REQ_NVE, b.pos, b.species, vel=vb, n_steps=60, dt_fs=0.5)]
+    res = [srv.wait(i, 120000) for i in ids]
+    st = srv.stats()
+    srv.close()
+    for (s, v), r in zip(((a, va), (b, vb)), res):
+        assert r["status"] == 0
+        pos, vel, pe, ke = ref_model.md_nve(s.pos, v, s.species, s.cell, s.pbc, 0.5, 60)
+        assert np.array_equal(r["pos"], pos) and np.array_equal(r["vel"], vel)
+        assert np.array_equal(r["pe"], pe) and np.array_equal(r["ke"], ke)
+    assert st["skin_steps"] >= 50, st["skin_steps"]  # steps 1..60, all but the first iteration or two
+    assert st["skin_builds"] >= 2  # the first build, and at least one after the drift
+
+
+def test_served_results_against_the_oracle(B):
+    """One served energy+forces request and one served 10-step NVE request
+    against the FP64 oracle: forces within 2e-3 of max|F| (FP16 form), the NVE
+    trajectory's positions within 1e-6 A and its energies within 2e-3 of
+    their scale (the bars of the single-call tests)."""
+    m, spec = _model(B, "f16")
+    w = synth.make_weights(spec, 21)
+    om = oracle.Model(spec, w)
+    masses = np.asarray(spec.masses)
+    s1, s2 = synth.cluster(200, seed=41), synth.cluster(150, seed=42)
+    v2 = synth.maxwell_boltzmann(masses[s2.species], 300.0, seed=43)
+    srv = B.Server(m, max_slots=8)
+    i1 = srv.submit(B.MLIP_REQ_ENERGY_FORCES, s1.pos, s1.species)
+    i2 = srv.submit(B.MLIP_REQ_NVE, s2.pos, s2.species, vel=v2, n_steps=10, dt_fs=0.5)
+    r1, r2 = srv.wait(i1, 60000), srv.wait(i2, 60000)
+    srv.close()
+    ref = om.energy_forces(s1.pos, s1.species, s1.cell, s1.pbc, atom_energies=True)
+    scale = max(abs(ref["energy"]), float(np.abs(ref["atom_energies"]).sum()))
+    assert abs(r1["energy"] - ref["energy"]) <= 2e-3 * scale
+    err = np.abs(r1["forces"] - ref["forces"]).max() / np.abs(ref["forces"]).max()
+    print(f" served E+F: max|dF|/max|F| = {err:.2e} (bar 0.002)", end="")
+    assert err <= 2e-3
+    rp, rv, rpe, rke = om.vv_nve(s2.pos, v2, s2.species, masses, s2.cell, s2.pbc, 0.5, 10)
+    assert np.abs(r2["pos"] - rp).max() < 1e-6
+    esc = np.abs(rpe).max() + np.abs(rke).max()
+    assert np.abs(r2["pe"] - rpe).max() < 2e-3 * esc
+    assert np.abs(r2["ke"] - rke).max() < 2e-3 * esc
