@@ -226,6 +226,29 @@ int mlip_energy_forward(mlip_model* model, const double* pos, const int32_t* spe
 int mlip_energy_backward(mlip_model* model, const double* grad_energy, double* grad_pos, double* stress,
                          int on_device, void* stream);
 
+/* Subsampled Hessian rows of a batch of systems (Sec. "Training with Hessian
+ * labels": Eq. full_hessian, H_ij = d2E/dr_i dr_j = -dF_i/dr_j, and the rows of
+ * Eq. sampled_hessian2).  For every row index rho = 0..R-1 and every system g
+ * the row atom is row_atoms[g * R + rho] (an index within system g); the
+ * summed force F_rho = sum_g F_{atom(g, rho)} is differentiated with respect to
+ * all positions:
+ *   rows[rho][a][j][b] = -dF_rho,a / dr_jb,   a, b = x, y, z, j = 0..n-1
+ * (double[R][3][n][3], n the batch's total atom count).  Systems do not
+ * interact, so each row is the concatenation of the systems' own rows (zero
+ * outside system g for the part of g).  Computed on the GPU by
+ * forward-over-reverse differentiation of the energy and its adjoint in FP32
+ * dual numbers (the model's FP32 weights, whatever its precision form).
+ *   atom_off [n_systems + 1], cells [n_systems][9], pbc [n_systems][3],
+ *   row_atoms [n_systems][R]: host arrays; pos [n][3], species [n] and rows:
+ *   host or device (on_device).
+ * Errors: MLIP_ERR_INVALID_ARG (bad sizes, a row atom outside its system,
+ * species out of range, a model with the symmetric contraction, gate or
+ * charges, hidden width other than 64, more than 128 channels), MLIP_ERR_CELL,
+ * MLIP_ERR_OOM, MLIP_ERR_CUDA.  Synchronises the stream. */
+int mlip_hessian_rows(mlip_model* model, int32_t n_systems, const int64_t* atom_off, const double* pos,
+                      const int32_t* species, const double* cells, const uint8_t* pbc, int32_t R,
+                      const int32_t* row_atoms, double* rows, int on_device, void* stream);
+
 /* Energy, forces and the corrected charges of one open system of total
  * charge total_charge (e) with a model built with charges = 1 (see
  * mlip_model_desc).  pos double[n][3], species int32[n]; energy double[1];

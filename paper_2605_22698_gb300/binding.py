@@ -78,6 +78,7 @@ def lib():
         L.mlip_energy_forces.argtypes = [P, P, P, i64, P, P, P, P, P, i32, P]
         L.mlip_energy_forces_charged.argtypes = [P, P, P, i64, ctypes.c_double, P, P, P, i32, P]
         L.mlip_energy_forward.argtypes = [P, P, P, i64, P, P, P, i32, P]
+        L.mlip_hessian_rows.argtypes = [P, i32, P, P, P, P, P, i32, P, P, i32, P]
         L.mlip_energy_backward.argtypes = [P, P, P, P, i32, P]
         L.mlip_energy_forces_batch.argtypes = [P, i32, P, P, P, P, P, P, P, P, i32, P]
         L.mlip_neighbors_noalloc.argtypes = [P, i64, P, P, f64, P, P, P, i64, ctypes.POINTER(ctypes.c_int64), P]
@@ -271,6 +272,31 @@ def mlip_energy_backward(h, n: int, grad_energy, stress: bool = False, stream=No
     return (out, so) if stress else out
 
 
+def mlip_hessian_rows(h, systems, row_atoms, stream=None):
+    """Subsampled Hessian rows of a batch: systems = [(pos, species, cell, pbc)]
+    (numpy host arrays), row_atoms int [n_systems][R] (indices within each
+    system).  Returns float64 [R][3][n][3], n the total atom count:
+    rows[rho][a][j][b] = -dF_rho,a/dr_jb with F_rho the sum over systems of the
+    force on each system's row atom rho."""
+    ns = len(systems)
+    off = np.zeros(ns + 1, np.int64)
+    for k, (p, _, _, _) in enumerate(systems):
+        off[k + 1] = off[k] + len(p)
+    n = int(off[-1])
+    pos = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64).reshape(-1, 3) for p, _, _, _ in systems]))
+    sp = np.ascontiguousarray(np.concatenate([np.asarray(z, np.int32) for _, z, _, _ in systems]))
+    cells = np.ascontiguousarray(np.stack([np.asarray(c, np.float64).reshape(9) for _, _, c, _ in systems]))
+    pbc = np.ascontiguousarray(np.stack([np.asarray(b, np.uint8).reshape(3) for _, _, _, b in systems]))
+    ra = np.ascontiguousarray(np.asarray(row_atoms, np.int32).reshape(ns, -1))
+    R = int(ra.shape[1])
+    out = np.zeros((R, 3, n, 3))
+    _check(lib().mlip_hessian_rows(h, ns, off.ctypes.data_as(ctypes.c_void_p), pos.ctypes.data_as(ctypes.c_void_p),
+                                   sp.ctypes.data_as(ctypes.c_void_p), cells.ctypes.data_as(ctypes.c_void_p),
+                                   pbc.ctypes.data_as(ctypes.c_void_p), R, ra.ctypes.data_as(ctypes.c_void_p),
+                                   out.ctypes.data_as(ctypes.c_void_p), 0, _stream_ptr(stream)))
+    return out
+
+
 def mlip_energy_forces_charged(h, pos, species, total_charge: float = 0.0, forces: bool = True, stream=None):
     """One open system of the given total charge with a model with charges:
     energy, forces and the corrected charges (host or device arrays, as
@@ -447,6 +473,9 @@ class Model:
 
     def energy_backward(self, n, grad_energy, stress=False, stream=None):
         return mlip_energy_backward(self.h, n, grad_energy, stress, stream)
+
+    def hessian_rows(self, systems, row_atoms, stream=None):
+        return mlip_hessian_rows(self.h, systems, row_atoms, stream)
 
     def energy_forces_charged(self, pos, species, total_charge=0.0, forces=True, stream=None):
         return mlip_energy_forces_charged(self.h, pos, species, total_charge, forces, stream)
