@@ -545,6 +545,35 @@ def measure(args, rank, world, name, steps, warmup, fp32_peak, plain=True, cpu=T
     }
 
 
+def hessian_phase(n_graphs: int = 128, atoms: int = 24, R: int = 8, reps: int = 3):
+    """Subsampled Hessian rows (Eq. sampled_hessian2) of a batch of small open
+    clusters (the paper's Hessian-labelled molecules have at most 31 atoms and
+    8 rows are sampled per graph): host arrays in, rows out, timed on the host
+    around mlip_hessian_rows (it synchronises)."""
+    from paper_2605_22698_gb300 import binding as B
+    spec = synth.model_spec("water")
+    w = synth.make_weights(spec, 21)
+    m = B.Model(spec, w, B.MLIP_PREC_F16)
+    systems = []
+    for g in range(n_graphs):
+        c = synth.cluster(atoms, seed=7000 + g, side=6.0)
+        systems.append((c.pos, c.species, c.cell, c.pbc))
+    rng = np.random.default_rng(5)
+    rows = np.stack([rng.choice(atoms, size=R, replace=False) for _ in range(n_graphs)]).astype(np.int32)
+    m.hessian_rows(systems, rows)  # warm-up (workspace)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        out = m.hessian_rows(systems, rows)
+    dt = (time.perf_counter() - t0) / reps
+    m.close()
+    n_rows = n_graphs * R * 3
+    return {"graphs": n_graphs, "atoms_per_graph": atoms, "rows_per_graph": R * 3, "model": "T2 C128 L2 H64",
+            "rows_per_s": round(n_rows / dt, 1), "ms_per_batch": round(1e3 * dt, 3),
+            "row_length": int(out.shape[2] * 3),
+            "note": "rows of length 3n (n = all atoms of the batch: each graph's part of its rows, zero elsewhere); "
+                    "host arrays in and out, timed on the host"}
+
+
 def run_ours(args, rank, world):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -557,6 +586,7 @@ def run_ours(args, rank, world):
         line["water3000"] = {k: wl[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "e2e", "roofline",
                                                 "kernel_share", "plain_fp32", "clocks")}
         line["serving"] = serve_phase(args, rank, world, args.serve_requests, sweep=[], alone=False)
+        line["hessian_rows"] = hessian_phase()
     line["fp32_peak"] = fp32_peak
     line["peaks"] = peaks()
     if rank == 0:

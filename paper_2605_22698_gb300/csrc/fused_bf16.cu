@@ -123,6 +123,7 @@ constexpr int kThreads = 128 * kWS;
 // order in which it is summed, do not depend on where tile boundaries fall
 // (a system's results do not depend on the other systems of its batch).
 constexpr bool kEdgeSplit = true;
+static_assert(kEdgeSplit, "the adjoint's dE/dY partial buffers hold one warp set per edge");
 
 // Per-tile edge lists of the two sets, built by one warp (lane t = edge slot t).
 __device__ __forceinline__ void build_lists(int t, bool valid, int par, int* s_list, int* s_cnt) {
@@ -645,7 +646,8 @@ struct BwdLayoutT {
   static constexpr size_t off_cy = off_b2 + B2_BYTES;
   static constexpr size_t off_y = off_cy + (size_t)kNT * NZP * 4;
   static constexpr size_t off_red = off_y + kNT * 16 * 4;
-  static constexpr size_t off_tab = off_red + (size_t)(4 * kWS) * kNT * 16 * 4;
+  // dE/dY partials [4 warps of the owning set][kNT][16]: every edge belongs to one warp set
+  static constexpr size_t off_tab = off_red + (size_t)4 * kNT * 16 * 4;
   static constexpr size_t off_taby = off_tab + (size_t)NZP * 4;
   static constexpr size_t off_idx = off_taby + (((size_t)NZP + 15) & ~(size_t)15);
   static constexpr size_t off_bar = off_idx + 2 * kNT * 4;
@@ -672,15 +674,15 @@ struct BwdLayoutWST {
     return c;
   }
   static constexpr int NCOLS = tmem_cols();
-  static constexpr size_t rest = 2 * kTileBytes + (size_t)2 * kNT * NZP * 4 + 2 * kNT * 16 * 4 + 16 * kNT * 16 * 4 +
+  static constexpr size_t rest = 2 * kTileBytes + (size_t)2 * kNT * NZP * 4 + 2 * kNT * 16 * 4 + 8 * kNT * 16 * 4 +
                                  (size_t)NZP * 4 + (((size_t)NZP + 15) & ~(size_t)15) + 4 * kNT * 4 + 4 * kNT * 4 + 128;
   static constexpr int NB2 = (size_t)NP * kW3PathBytes + rest + 2 * (size_t)B2_BYTES <= 231424 ? 2 : 1;
   static constexpr size_t off_z2 = (size_t)NP * kW3PathBytes;
   static constexpr size_t off_b2 = off_z2 + 2 * kTileBytes;
   static constexpr size_t off_cy = off_b2 + (size_t)NB2 * B2_BYTES;   // [2][kNT][NZP]
   static constexpr size_t off_y = off_cy + (size_t)2 * kNT * NZP * 4; // [2][kNT][16]
-  static constexpr size_t off_red = off_y + 2 * kNT * 16 * 4;         // [2][8 warps][kNT][16]
-  static constexpr size_t off_tab = off_red + 16 * kNT * 16 * 4;
+  static constexpr size_t off_red = off_y + 2 * kNT * 16 * 4;         // [2][4 warps of the owning set][kNT][16]
+  static constexpr size_t off_tab = off_red + 8 * kNT * 16 * 4;
   static constexpr size_t off_taby = off_tab + (size_t)NZP * 4;
   static constexpr size_t off_idx = off_taby + (((size_t)NZP + 15) & ~(size_t)15);  // [2][send kNT, recv kNT]
   static constexpr size_t off_dws = off_idx + 4 * kNT * 4;                          // [2][scale kNT, inverse kNT]
@@ -893,7 +895,7 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
       if constexpr (slot == PK - 1) {
         const float tot = warp_reduce16(pv);
         const int ie = base + j - (PK - 1) + (lane >> 1) / NVP;  // list entry of this lane pair's value
-        if ((lane & 1) == 0 && my_comp >= 0 && ie < cnt) red[(warp * kNT + list[ie]) * 16 + my_comp] = tot;
+        if ((lane & 1) == 0 && my_comp >= 0 && ie < cnt) red[((warp & 3) * kNT + list[ie]) * 16 + my_comp] = tot;
       }
     });
   }
@@ -986,7 +988,7 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
       // lane v holds the total of value v: list entry i - (PK - 1) + v / NV, component v % NV;
       // entries older than this group's first were written by the previous group
       const int ie = i - (PK - 1) + lane / NV;
-      if (lane < PK * NV && ie >= i - slot) red[(warp * kNT + list[ie]) * 16 + yl_rt[lane % NV]] = tot;
+      if (lane < PK * NV && ie >= i - slot) red[((warp & 3) * kNT + list[ie]) * 16 + yl_rt[lane % NV]] = tot;
     }
   };
   // list entries in pairs with two register buffers: the sender rows of the
@@ -1047,7 +1049,7 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
   uint8_t* sB2 = smem + BL::off_b2;
   float* cY = reinterpret_cast<float*>(smem + BL::off_cy);
   float* sY = reinterpret_cast<float*>(smem + BL::off_y);
-  float* red = reinterpret_cast<float*>(smem + BL::off_red);  // [4 kWS][kNT][16]
+  float* red = reinterpret_cast<float*>(smem + BL::off_red);  // [4][kNT][16]
   float* tab_c = reinterpret_cast<float*>(smem + BL::off_tab);
   uint8_t* tab_y = smem + BL::off_taby;
   int* s_send = reinterpret_cast<int*>(smem + BL::off_idx);
@@ -1196,21 +1198,9 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(BwdLayout<L, MODE>::byte
         const int t = q >> 4, k = q & 15;
         const int e = tile * kNT + t;
         if (e >= E0 && e < E1 && ((m0 | m1) >> k & 1)) {
-          float v = 0.0f;
-          if (kEdgeSplit) {  // the four warps of the set that owns edge t
-            const int w0 = s_own[t] * 4;
+          float v = 0.0f;  // the four warps of the set that owns edge t
 #pragma unroll
-            for (int w = 0; w < 4; ++w) v += red[((w0 + w) * kNT + t) * 16 + k];
-          } else {
-            if (m0 >> k & 1) {
-#pragma unroll
-              for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
-            }
-            if (m1 >> k & 1) {
-#pragma unroll
-              for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
-            }
-          }
+          for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
           atomicAdd(&dY[(size_t)e * 16 + k], v);  // one add per kernel and address: deterministic
         }
       }
@@ -1447,7 +1437,7 @@ __global__ void __launch_bounds__(kWSThreads, 1)
     auto drain = [&](int it) {
       const int b = it & 1, tile = t_begin + it;
       const float* s_dws = dwsb + b * 2 * kNT;
-      const float* red = redb + b * 8 * kNT * 16;
+      const float* red = redb + b * 4 * kNT * 16;
       const uint32_t dcol = b ? dcol1 : dcol0;
       if (!tc::mbar_wait_sleep(bar_done + b, (uint32_t)((it >> 1) & 1))) {
         atomicOr(err, 8);
@@ -1479,21 +1469,9 @@ __global__ void __launch_bounds__(kWSThreads, 1)
           const int t = q >> 4, k = q & 15;
           const int e = tile * kNT + t;
           if (e >= E0 && e < E1 && ((m0 | m1) >> k & 1)) {
-            float v = 0.0f;
-            if (kEdgeSplit) {  // the four warps of the set that owns edge t
-              const int w0 = s_owns[b][t] * 4;
+            float v = 0.0f;  // the four warps of the set that owns edge t
 #pragma unroll
-              for (int w = 0; w < 4; ++w) v += red[((w0 + w) * kNT + t) * 16 + k];
-            } else {
-              if (m0 >> k & 1) {
-#pragma unroll
-                for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
-              }
-              if (m1 >> k & 1) {
-#pragma unroll
-                for (int w = 4; w < 8; ++w) v += red[(w * kNT + t) * 16 + k];
-              }
-            }
+            for (int w = 0; w < 4; ++w) v += red[(w * kNT + t) * 16 + k];
             atomicAdd(&dY[(size_t)e * 16 + k], v);  // one add per kernel and address: deterministic
           }
         }
@@ -1586,7 +1564,7 @@ __global__ void __launch_bounds__(kWSThreads, 1)
       const float* sY = sYb + b * kNT * 16;
       const float* cY = cYb + b * kNT * NZP;
       const float* s_dws = dwsb + b * 2 * kNT;
-      float* red = redb + b * 8 * kNT * 16;
+      float* red = redb + b * 4 * kNT * 16;
       uint8_t* sB2 = sB2base + (BL::NB2 == 2 ? b : 0) * BL::B2_BYTES;
       const uint32_t tw = taddr0 + (b ? wcol1 : wcol0);
       const int* lst = s_lists[b] + wsid * kNT;
