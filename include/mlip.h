@@ -99,7 +99,21 @@ typedef struct {
   int32_t charges;           /* 1: charge head, charge correction and Coulomb term (below) */
   double coulomb_r0;         /* soft-core radius r0 of the Coulomb term, A (charges = 1) */
   int32_t gate;              /* 1: gated update with a species self-connection (below) */
+  int32_t parity;            /* 1: mixed-parity features (below) */
 } mlip_model_desc;
+
+/* parity = 1 (the mixed-parity irreps of the paper's NequIP table,
+ * "0e + 0o + 1o + 1e + 2e + 2o", here with C/2 channels of each order and
+ * parity): channels c < C/2 of every order form the even-parity block, c >= C/2
+ * the odd block.  The paths are every triangle-valid (l1, l2, l3) in
+ * lexicographic order, odd l1 + l2 + l3 (pseudotensor couplings) included
+ * (18 for l_max 2, 34 for l_max 3); a path with odd l2 couples each channel to
+ * the same channel of the other block (output parity = input parity x
+ * (-1)^l2).  The embedding and the readout use the even scalars only, the
+ * channel mixes keep the blocks (block-diagonal W_l), and the scalar update is
+ * h_0 += silu(u) on even channels and tanh(u) on odd ones: the weights outside
+ * those blocks are ignored (zeroed at creation).  Plain FP32 form only, without
+ * correlation, charges or gate; an even channel count. */
 
 /* gate = 1 (NequIP's gate nonlinearity and self-connection, on the uniform
  * natural-parity irreps of this layer; 32, 64 or 128 channels): the channel
@@ -138,10 +152,10 @@ int mlip_model_num_weights(const mlip_model_desc* desc, int64_t* n_weights);
 int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t n_weights,
                       int precision, mlip_model** out);
 
-/* Load a parameter file: "MLIPPRM1", u32 version (1 or 2), 8 x i32 (S, T, C,
- * L, Lsh, NB, H, p), version 2 only: i32 correlation, i32 charges, f64
- * coulomb_r0, i32 gate; then 2 x f64 (rc, avg_num_neighbors), S x f64
- * masses, i64 count,
+/* Load a parameter file: "MLIPPRM1", u32 version (1, 2 or 3), 8 x i32 (S, T,
+ * C, L, Lsh, NB, H, p), versions 2 and 3: i32 correlation, i32 charges, f64
+ * coulomb_r0, i32 gate; version 3: i32 parity; then 2 x f64 (rc,
+ * avg_num_neighbors), S x f64 masses, i64 count,
  * count x f32 weights; little-endian.  Errors as mlip_model_create plus
  * MLIP_ERR_NOT_FOUND (unreadable file). */
 int mlip_model_load(const char* params_path, int precision, mlip_model** out);

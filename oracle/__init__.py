@@ -47,6 +47,8 @@ def lib():
         L.oracle_real_basis_U.argtypes = [i32, P, P]
         L.oracle_real_cg.argtypes = [i32, i32, i32, P]
         L.oracle_paths.argtypes = [i32, i32, P]
+        L.oracle_paths_all.argtypes = [i32, i32, P]
+        L.oracle_node_features.argtypes = [P, P, P, i64, P, P, i32, P]
         L.oracle_bessel.argtypes = [i32, f64, f64]
         L.oracle_bessel.restype = f64
         L.oracle_envelope.argtypes = [f64, i32]
@@ -132,10 +134,13 @@ def real_cg(l1: int, l2: int, l3: int) -> np.ndarray:
     return out.reshape(2 * l3 + 1, 2 * l1 + 1, 2 * l2 + 1)
 
 
-def paths(L: int, Lsh: int = 3) -> list:
-    n = lib().oracle_paths(L, Lsh, None)
+def paths(L: int, Lsh: int = 3, all_parities: bool = False) -> list:
+    """Coupling paths (l1, l2, l3): natural parity, or every triangle-valid
+    triple (the mixed-parity model's paths)."""
+    f = lib().oracle_paths_all if all_parities else lib().oracle_paths
+    n = f(L, Lsh, None)
     out = np.zeros(3 * n, dtype=np.int32)
-    lib().oracle_paths(L, Lsh, _p(out))
+    f(L, Lsh, _p(out))
     return [tuple(int(x) for x in out[3 * k:3 * k + 3]) for k in range(n)]
 
 
@@ -215,7 +220,7 @@ class Model:
     def __init__(self, spec, weights: np.ndarray):
         self.spec = spec
         self._hyper = _c(np.append(spec.hyper, [getattr(spec, "correlation", 0), getattr(spec, "charges", 0),
-                                                getattr(spec, "gate", 0)]), np.int32)
+                                                getattr(spec, "gate", 0), getattr(spec, "parity", 0)]), np.int32)
         self._dhyper = _c(np.append(spec.dhyper, getattr(spec, "coulomb_r0", 0.0)), np.float64)
         nw = lib().oracle_num_weights(_p(self._hyper))
         w = _c(weights, np.float32)
@@ -223,6 +228,8 @@ class Model:
             raise ValueError(f"expected {nw} weights, got {w.size}")
         self._w = w
         self._h = lib().oracle_model_create(_p(self._hyper), _p(self._dhyper), _p(w))
+        if not self._h:
+            raise ValueError("unsupported model options")
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -281,6 +288,18 @@ class Model:
         if rc != 0:
             raise ValueError("oracle_energy_dual failed")
         return float(E[0]), float(dE[0])
+
+    def node_features(self, pos, species, cell, pbc, layer: int) -> np.ndarray:
+        """Node features after `layer` interaction layers, [n][(L+1)^2][C]."""
+        pos = _c(pos, np.float64)
+        n = pos.shape[0]
+        D = (self.spec.L + 1) ** 2
+        out = np.zeros((n, D, self.spec.C))
+        rc = lib().oracle_node_features(self._h, _p(pos), _p(_c(species, np.int32)), n, _p(_c(cell, np.float64)),
+                                        _p(_c(pbc, np.uint8)), int(layer), _p(out))
+        if rc != 0:
+            raise ValueError("oracle_node_features failed")
+        return out
 
     def hessian_row(self, pos, species, cell, pbc, atom: int, axis: int) -> np.ndarray:
         """d2E / dr_{atom,axis} dr_{j,b} for every atom j and axis b: [n, 3]."""

@@ -245,9 +245,11 @@ double cg_complex(int l1, int m1, int l2, int m2, int l3, int m3) {
   return pre * sum;
 }
 
-// Real CG tensor C[m3][m1][m2] (each index -l..l, row-major) for natural
-// parity paths: C^r = U_l3 C^c (U_l1^* (x) U_l2^*).  The result is real up to
-// one global phase, which is removed; then the overall sign is fixed so that
+// Real CG tensor C[m3][m1][m2] (each index -l..l, row-major) of a
+// triangle-valid triple: C^r = U_l3 C^c (U_l1^* (x) U_l2^*).  The result is
+// real up to one global phase (a power of i: imaginary for odd l1 + l2 + l3,
+// the pseudotensor couplings of mixed-parity models), which is removed; then
+// the overall sign is fixed so that
 // the first entry (lexicographic in m3, m1, m2) with |c| > 1e-8 is positive.
 // Entries below 1e-14 in magnitude are set to zero.
 void real_cg(int l1, int l2, int l3, double* out) {
@@ -290,18 +292,20 @@ void real_cg(int l1, int l2, int l3, double* out) {
 }
 
 // ------------------------------------------------------------------ paths
-// Every (l1 <= L, l2 <= Lsh, l3 <= L) with |l1-l2| <= l3 <= l1+l2 and
-// l1+l2+l3 even, in lexicographic order of (l1, l2, l3).
+// Every (l1 <= L, l2 <= Lsh, l3 <= L) with |l1-l2| <= l3 <= l1+l2, in
+// lexicographic order of (l1, l2, l3): with l1+l2+l3 even only (natural
+// parity), or all of them (all_parities: the mixed-parity model, whose odd
+// paths couple features into the opposite parity block).
 struct CGEntry { int m3, m1, m2; double c; };
 struct Path { int l1, l2, l3; std::vector<CGEntry> nz; };
 
-std::vector<Path> build_paths(int L, int Lsh) {
+std::vector<Path> build_paths(int L, int Lsh, bool all_parities = false) {
   std::vector<Path> ps;
   for (int l1 = 0; l1 <= L; ++l1)
     for (int l2 = 0; l2 <= Lsh; ++l2)
       for (int l3 = 0; l3 <= L; ++l3) {
         if (l3 < std::abs(l1 - l2) || l3 > l1 + l2) continue;
-        if ((l1 + l2 + l3) % 2) continue;
+        if (!all_parities && (l1 + l2 + l3) % 2) continue;
         Path p{l1, l2, l3, {}};
         int n1 = 2 * l1 + 1, n2 = 2 * l2 + 1, n3 = 2 * l3 + 1;
         std::vector<double> C(n3 * n1 * n2);
@@ -360,6 +364,23 @@ double silu_grad(double x) {
   return s * (1.0 + x * (1.0 - s));
 }
 
+// tanh through the exponential, tanh(x) = 1 - 2 / (exp(2x) + 1): odd, so it
+// keeps the parity of an odd scalar (mixed-parity models' 0o channels)
+template <class T>
+T tanh_t(T x) { return T(1.0) - T(2.0) / (exp(T(2.0) * x) + T(1.0)); }
+double tanh_grad(double x) { const double t = std::tanh(x); return 1.0 - t * t; }
+
+// Mixed-parity models (parity = 1): channel c < C/2 is the even-parity block,
+// c >= C/2 the odd block.  A path with odd l2 (odd harmonics) takes its input
+// from the other block (the output parity is the input parity times (-1)^l2).
+inline int src_channel(int c, int C, int l2, int parity) { return (parity && (l2 & 1)) ? (c + C / 2) % C : c; }
+// The scalar update's activation: SiLU on even scalars, tanh on odd ones.
+template <class T>
+T scalar_act(T x, int c, int C, int parity) { return (parity && c >= C / 2) ? tanh_t(x) : silu(x); }
+inline double scalar_act_grad(double x, int c, int C, int parity) {
+  return (parity && c >= C / 2) ? tanh_grad(x) : silu_grad(x);
+}
+
 // ------------------------------------------------------------------ model
 struct Hyper {
   int S, T, C, L, Lsh, NB, H, p;
@@ -368,6 +389,7 @@ struct Hyper {
   int charges;  // 1: charge head, charge correction and Coulomb term (open systems)
   double r0;    // soft-core radius of the Coulomb term, A
   int gate;     // 1: species self-connection and gated update of the l > 0 features
+  int parity;   // 1: mixed-parity features (channel blocks of even and odd parity; pseudotensor paths)
 };
 
 struct Model {
@@ -640,8 +662,9 @@ T model_energy(const Model& M, const std::vector<Edge>& edges, const std::vector
           for (const CGEntry& ce : pa.nz) {
             const int i3 = lm(pa.l3, ce.m3), i1 = lm(pa.l1, ce.m1), i2 = lm(pa.l2, ce.m2);
             for (int c = 0; c < C; ++c)
-              m[((size_t)i * D + i3) * C + c] +=
-                  T(s) * w[(size_t)p * C + c] * T(ce.c) * h[((size_t)j * D + i1) * C + c] * Y[i2];
+              m[((size_t)i * D + i3) * C + c] += T(s) * w[(size_t)p * C + c] * T(ce.c) *
+                                                   h[((size_t)j * D + i1) * C + src_channel(c, C, pa.l2, hp.parity)] *
+                                                   Y[i2];
           }
         }
       }
@@ -703,7 +726,7 @@ T model_energy(const Model& M, const std::vector<Edge>& edges, const std::vector
             for (int c1 = 0; c1 < C; ++c1)
               acc += m[((size_t)i * D + ci) * C + c1] * T(Wm[((size_t)l * C + c1) * C + c2]);
             if (u_store) (*u_store)[t][((size_t)i * D + ci) * C + c2] = val(acc);
-            hn[((size_t)i * D + ci) * C + c2] += (l == 0) ? silu(acc) : acc;
+            hn[((size_t)i * D + ci) * C + c2] += (l == 0) ? scalar_act(acc, c2, C, hp.parity) : acc;
           }
         }
     h.swap(hn);
@@ -881,7 +904,7 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
           std::vector<double> gu(C);
           for (int c2 = 0; c2 < C; ++c2) {
             size_t k = ((size_t)i * D + ci) * C + c2;
-            gu[c2] = (l == 0) ? G[k] * silu_grad(u[k]) : G[k];
+            gu[c2] = (l == 0) ? G[k] * scalar_act_grad(u[k], c2, C, hp.parity) : G[k];
           }
           for (int c1 = 0; c1 < C; ++c1) {
             double acc = 0.0;
@@ -940,10 +963,11 @@ double model_energy_forces(const Model& M, const std::vector<Edge>& edges, const
           for (const CGEntry& ce : pa.nz) {
             const int i3 = lm(pa.l3, ce.m3), i1 = lm(pa.l1, ce.m1), i2 = lm(pa.l2, ce.m2);
             for (int c = 0; c < C; ++c) {
+              const int cs = src_channel(c, C, pa.l2, hp.parity);
               const double gt = s * Gm[((size_t)i * D + i3) * C + c];
-              const double hj = hprev[((size_t)j * D + i1) * C + c];
+              const double hj = hprev[((size_t)j * D + i1) * C + cs];
               const double wp = w[(size_t)p * C + c];
-              Gprev[((size_t)j * D + i1) * C + c] += wp * ce.c * Y[i2] * gt;
+              Gprev[((size_t)j * D + i1) * C + cs] += wp * ce.c * Y[i2] * gt;
               dYe[i2] += wp * ce.c * hj * gt;
               dw[(size_t)p * C + c] += ce.c * hj * Y[i2] * gt;
             }
@@ -1062,7 +1086,7 @@ int oracle_real_basis_U(int l, double* re, double* im) {
 }
 
 int oracle_real_cg(int l1, int l2, int l3, double* out) {
-  if (l3 < std::abs(l1 - l2) || l3 > l1 + l2 || (l1 + l2 + l3) % 2) return -1;
+  if (l3 < std::abs(l1 - l2) || l3 > l1 + l2) return -1;
   real_cg(l1, l2, l3, out);
   return 0;
 }
@@ -1077,14 +1101,24 @@ int oracle_paths(int L, int Lsh, int* out) {
   return (int)ps.size();
 }
 
+// Paths of the mixed-parity model: every triangle-valid (l1, l2, l3), both parities.
+int oracle_paths_all(int L, int Lsh, int* out) {
+  std::vector<Path> ps = build_paths(L, Lsh, true);
+  if (out)
+    for (size_t k = 0; k < ps.size(); ++k) {
+      out[3 * k] = ps[k].l1; out[3 * k + 1] = ps[k].l2; out[3 * k + 2] = ps[k].l3;
+    }
+  return (int)ps.size();
+}
+
 double oracle_bessel(int n, double r, double rc) { return bessel<double>(n, r, rc); }
 double oracle_envelope(double x, int p) { return envelope<double>(x, p); }
 
 // hyper = {S, T, C, L, Lsh, NB, H, p, correlation, charges, gate}, dhyper = {rc, avg_num_neighbors, r0}
 int64_t oracle_num_weights(const int* hyper) {
   Hyper h{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], 0, 0, hyper[8], hyper[9], 0,
-          hyper[10]};
-  int P = (int)build_paths(h.L, h.Lsh).size();
+          hyper[10], hyper[11]};
+  int P = (int)build_paths(h.L, h.Lsh, h.parity != 0).size();
   return num_weights(h, P);
 }
 
@@ -1092,8 +1126,9 @@ void* oracle_model_create(const int* hyper, const double* dhyper, const float* w
   Model* M = new Model();
   Hyper& h = M->hp;
   h = Hyper{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dhyper[0], dhyper[1],
-            hyper[8], hyper[9], dhyper[2], hyper[10]};
-  M->paths = build_paths(h.L, h.Lsh);
+            hyper[8], hyper[9], dhyper[2], hyper[10], hyper[11]};
+  if (h.parity && (h.corr || h.gate || h.charges || h.C % 2)) { delete M; return nullptr; }
+  M->paths = build_paths(h.L, h.Lsh, h.parity != 0);
   if (h.corr == 2) M->sc = build_sc_paths(h.L);
   M->P = (int)M->paths.size();
   M->D = (h.L + 1) * (h.L + 1);
@@ -1125,6 +1160,20 @@ void* oracle_model_create(const int* hyper, const double* dhyper, const float* w
   }
   take(M->W_out, (size_t)h.S * h.C);
   take(M->E0, (size_t)h.S);
+  if (h.parity) {
+    // the definition of the mixed-parity model: the embedding and the readout
+    // act on even scalars only (the energy is a true scalar), and the channel
+    // mixes keep each parity block (block-diagonal W_l): the weights outside
+    // those blocks are ignored
+    const int Ch = h.C / 2;
+    for (int z = 0; z < h.S; ++z)
+      for (int c = Ch; c < h.C; ++c) M->W_emb[(size_t)z * h.C + c] = M->W_out[(size_t)z * h.C + c] = 0.0;
+    for (int t = 0; t < h.T; ++t)
+      for (int l = 0; l <= h.L; ++l)
+        for (int c1 = 0; c1 < h.C; ++c1)
+          for (int c2 = 0; c2 < h.C; ++c2)
+            if ((c1 < Ch) != (c2 < Ch)) M->Wmix[t][((size_t)l * h.C + c1) * h.C + c2] = 0.0;
+  }
   if (h.charges) {
     take(M->W_q, (size_t)h.S * h.C);
     take(M->q0, (size_t)h.S);
@@ -1267,6 +1316,25 @@ int oracle_energy_dual(void* model, const double* pos, const int32_t* species, i
   Dual E = model_energy<Dual>(M, edges, rp, p.data(), sp.data(), (int)n, cl, nullptr, nullptr, nullptr);
   *energy = E.v;
   *dE = E.d;
+  return 0;
+}
+
+// Node features h^layer [n][(L+1)^2][C] (layer 0: the embedding; layer t:
+// after t interaction layers), for feature-level equivariance pins.
+int oracle_node_features(void* model, const double* pos, const int32_t* species, int64_t n, const double* cell,
+                         const uint8_t* pbc, int layer, double* out) {
+  const Model& M = *static_cast<Model*>(model);
+  if (layer < 0 || layer > M.hp.T) return -2;
+  bool anyp = pbc[0] || pbc[1] || pbc[2];
+  double zero[9] = {0};
+  uint8_t np[3] = {0, 0, 0};
+  const double* cl = anyp ? cell : zero;
+  std::vector<Edge> edges;
+  if (brute_neighbors(pos, (int)n, cl, anyp ? pbc : np, M.hp.rc, edges) != 0) return -1;
+  std::vector<int> rp = receiver_row_ptr(edges, (int)n);
+  std::vector<std::vector<double>> hs(M.hp.T + 1), us(M.hp.T), as(M.hp.T), gs(M.hp.T);
+  model_energy<double>(M, edges, rp, pos, species, (int)n, cl, nullptr, &hs, &us, &as, &gs);
+  std::copy(hs[layer].begin(), hs[layer].end(), out);
   return 0;
 }
 

@@ -45,7 +45,7 @@ class mlip_model_desc(ctypes.Structure):
                 ("hidden", ctypes.c_int32), ("envelope_p", ctypes.c_int32), ("cutoff", ctypes.c_double),
                 ("avg_num_neighbors", ctypes.c_double), ("masses", ctypes.POINTER(ctypes.c_double)),
                 ("correlation", ctypes.c_int32), ("charges", ctypes.c_int32), ("coulomb_r0", ctypes.c_double),
-                ("gate", ctypes.c_int32)]
+                ("gate", ctypes.c_int32), ("parity", ctypes.c_int32)]
 
 
 class mlip_md_options(ctypes.Structure):
@@ -129,7 +129,8 @@ def make_desc(spec, masses=None):
     m = np.ascontiguousarray(masses if masses is not None else spec.masses, dtype=np.float64)
     d = mlip_model_desc(spec.S, spec.T, spec.C, spec.L, spec.Lsh, spec.NB, spec.H, spec.p, spec.rc, spec.avg_nb,
                         m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), getattr(spec, "correlation", 0),
-                        getattr(spec, "charges", 0), getattr(spec, "coulomb_r0", 0.0), getattr(spec, "gate", 0))
+                        getattr(spec, "charges", 0), getattr(spec, "coulomb_r0", 0.0), getattr(spec, "gate", 0),
+                        getattr(spec, "parity", 0))
     d._keep = m
     return d
 

@@ -71,12 +71,12 @@ HostStage::~HostStage() {
   if (p) cudaFreeHost(p);
 }
 
-static int count_paths(int L, int Lsh, int* P0) {
+static int count_paths(int L, int Lsh, int* P0, bool all_parities = false) {
   int P = 0, p0 = 0;
   for (int l1 = 0; l1 <= L; ++l1)
     for (int l2 = 0; l2 <= Lsh; ++l2)
       for (int l3 = 0; l3 <= L; ++l3)
-        if (l3 >= std::abs(l1 - l2) && l3 <= l1 + l2 && (l1 + l2 + l3) % 2 == 0) {
+        if (l3 >= std::abs(l1 - l2) && l3 <= l1 + l2 && (all_parities || (l1 + l2 + l3) % 2 == 0)) {
           ++P;
           if (l1 == 0) ++p0;
         }
@@ -112,6 +112,15 @@ static int validate_desc(const mlip_model_desc* d, int precision) {
   if (d->charges != 0 && d->charges != 1) { set_error("charges must be 0 or 1"); return MLIP_ERR_INVALID_ARG; }
   if (d->gate != 0 && d->gate != 1) { set_error("gate must be 0 or 1"); return MLIP_ERR_INVALID_ARG; }
   if (d->gate && d->channels < 32) { set_error("the gated update needs 32, 64 or 128 channels"); return MLIP_ERR_INVALID_ARG; }
+  if (d->parity != 0 && d->parity != 1) { set_error("parity must be 0 or 1"); return MLIP_ERR_INVALID_ARG; }
+  if (d->parity && (d->correlation || d->charges || d->gate)) {
+    set_error("mixed parity (parity = 1) is built without the contraction, the charge head and the gate");
+    return MLIP_ERR_INVALID_ARG;
+  }
+  if (d->parity && precision != MLIP_PREC_FP32) {
+    set_error("mixed parity (parity = 1) runs in the plain FP32 form");
+    return MLIP_ERR_INVALID_ARG;
+  }
   if (d->charges && !(d->coulomb_r0 > 0.0 && d->coulomb_r0 < 1e3)) {
     set_error("coulomb_r0 %g out of range (0, 1000)", d->coulomb_r0);
     return MLIP_ERR_INVALID_ARG;
@@ -149,7 +158,7 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
   *out = nullptr;
   MLIP_TRY(validate_desc(desc, precision));
   int P0 = 0;
-  const int P = count_paths(desc->l_max, desc->sh_l_max, &P0);
+  const int P = count_paths(desc->l_max, desc->sh_l_max, &P0, desc->parity != 0);
   const int64_t need = weights_for(*desc, P);
   if (n_weights != need) { set_error("expected %lld weights, got %lld", (long long)need, (long long)n_weights); return MLIP_ERR_INVALID_ARG; }
   mlip_model* M = new mlip_model();
@@ -160,11 +169,33 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
   M->corr = desc->correlation;
   M->charges = desc->charges;
   M->gate = desc->gate;
+  M->parity = desc->parity;
   M->r0 = desc->coulomb_r0;
   M->Q = M->corr == 2 ? sc_num_paths(M->L) : 0;
   M->precision = precision;
   if (desc->masses) M->masses.assign(desc->masses, desc->masses + M->S);
   M->host_weights.assign(weights, weights + n_weights);
+  if (M->parity) {
+    // the mixed-parity model's definition: embedding and readout on the even
+    // scalars only, block-diagonal channel mixes; the other weights are zeroed
+    float* w = M->host_weights.data();
+    const int64_t S = M->S, C = M->C, H = M->H, NB = M->NB, Ch = C / 2;
+    int64_t off = 0;
+    for (int64_t z = 0; z < S; ++z)
+      for (int64_t c = Ch; c < C; ++c) w[z * C + c] = 0.0f;
+    off += S * C;
+    for (int t = 0; t < M->T; ++t) {
+      off += NB * H + H * H + H * (int64_t)P * C;
+      for (int l = 0; l <= M->L; ++l)
+        for (int64_t c1 = 0; c1 < C; ++c1)
+          for (int64_t c2 = 0; c2 < C; ++c2)
+            if ((c1 < Ch) != (c2 < Ch)) w[off + ((int64_t)l * C + c1) * C + c2] = 0.0f;
+      off += (int64_t)(M->L + 1) * C * C;
+    }
+    for (int64_t z = 0; z < S; ++z)
+      for (int64_t c = Ch; c < C; ++c) w[off + z * C + c] = 0.0f;
+    weights = w;
+  }
   cudaGetDevice(&M->device);
   cudaError_t e = cudaMalloc(&M->d_weights, sizeof(float) * n_weights);
   if (e != cudaSuccess) { cudaGetLastError(); delete M; set_error("cudaMalloc weights: %s", cudaGetErrorString(e)); return MLIP_ERR_OOM; }
@@ -345,19 +376,20 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
   if (!f) { set_error("cannot open '%s'", path); return MLIP_ERR_NOT_FOUND; }
   char magic[8];
   uint32_t version = 0;
-  int32_t hyper[8], corr = 0, charges = 0, gate = 0;
+  int32_t hyper[8], corr = 0, charges = 0, gate = 0, parity = 0;
   double dh[2], r0 = 0.0;
   f.read(magic, 8);
   f.read(reinterpret_cast<char*>(&version), 4);
   f.read(reinterpret_cast<char*>(hyper), sizeof(hyper));
-  if (version == 2) {
+  if (version >= 2) {
     f.read(reinterpret_cast<char*>(&corr), 4);
     f.read(reinterpret_cast<char*>(&charges), 4);
     f.read(reinterpret_cast<char*>(&r0), 8);
     f.read(reinterpret_cast<char*>(&gate), 4);
   }
+  if (version >= 3) f.read(reinterpret_cast<char*>(&parity), 4);
   f.read(reinterpret_cast<char*>(dh), sizeof(dh));
-  if (!f || std::memcmp(magic, "MLIPPRM1", 8) != 0 || (version != 1 && version != 2)) { set_error("'%s' is not a parameter file", path); return MLIP_ERR_INVALID_ARG; }
+  if (!f || std::memcmp(magic, "MLIPPRM1", 8) != 0 || version < 1 || version > 3) { set_error("'%s' is not a parameter file", path); return MLIP_ERR_INVALID_ARG; }
   if (hyper[0] < 1 || hyper[0] > 128) { set_error("bad species count"); return MLIP_ERR_INVALID_ARG; }
   std::vector<double> masses(hyper[0]);
   f.read(reinterpret_cast<char*>(masses.data()), sizeof(double) * masses.size());
@@ -367,7 +399,7 @@ int mlip_model_load(const char* path, int precision, mlip_model** out) {
   std::vector<float> w(count);
   f.read(reinterpret_cast<char*>(w.data()), sizeof(float) * count);
   if (!f) { set_error("truncated parameter file"); return MLIP_ERR_INVALID_ARG; }
-  mlip_model_desc d{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dh[0], dh[1], masses.data(), corr, charges, r0, gate};
+  mlip_model_desc d{hyper[0], hyper[1], hyper[2], hyper[3], hyper[4], hyper[5], hyper[6], hyper[7], dh[0], dh[1], masses.data(), corr, charges, r0, gate, parity};
   return mlip_model_create(&d, w.data(), count, precision, out);
 }
 
@@ -487,14 +519,14 @@ int plain_forward_edges(mlip_model* M, const double* d_pos, const int* d_species
     const int PW = first ? P0 : P;
     MLIP_TRY(launch_radial_fwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, z2T, E, st));
     MLIP_TRY(launch_sgemm(true, false, E, PW * C, H, z2T, E, M->W3[t], P * C, w[t], PW * C, st));
-    MLIP_TRY(launch_tp_fwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], w[t], PW, s, m, st));
+    MLIP_TRY(launch_tp_fwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], w[t], PW, s, m, st, M->parity != 0));
     if (M->corr == 2)
       MLIP_TRY(launch_sym_contract(L, n, C, M->S, m, nullptr, d_species, M->Wsc1[t], M->Wsc2[t], A[t], m, st));
     if (M->gate)
       MLIP_TRY(launch_gate_fwd(L, n, C, M->S, d_species, m, nullptr, h[t], M->Wmix[t], M->Wself[t], M->Wgate[t],
                                M->Wselfgate[t], h[t + 1], gpre[t], gg[t], nullptr, nullptr, st));
     else
-      MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st));
+      MLIP_TRY(launch_mix_fwd(n, C, L, m, M->Wmix[t], h[t], h[t + 1], u0[t], st, M->parity));
   }
   if (M->charges) {  // readout, charge head and Coulomb term, then the per-system sums
     MLIP_TRY(launch_readout(n, C, D, M->S, d_species, M->W_out, M->E0, h[T], atom_e, st));
@@ -555,11 +587,12 @@ int plain_adjoint_edges(mlip_model* M, const double* d_pos, const int* d_species
         MLIP_TRY(launch_gate_bwd(L, n, C, M->S, d_species, Ga, nullptr, gpre[t], gg[t], M->WmixT[t], M->WselfT[t],
                                  M->WgateT[t], M->WselfgateT[t], Gm, nullptr, nullptr, st));
       else
-        MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], M->WmixT[t], Gm, st));
+        MLIP_TRY(launch_mix_bwd(n, C, L, Ga, u0[t], M->Wmix[t], M->WmixT[t], Gm, st, M->parity));
       if (M->corr == 2)
         MLIP_TRY(launch_sym_contract_bwd(L, n, C, M->S, Gm, A[t], d_species, M->Wsc1[t], M->Wsc2[t], Gm, nullptr, nullptr,
                                          st));
-      MLIP_TRY(launch_tp_bwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], Gm, w[t], PW, s, Ga, Gb, dw, dY, st));
+      MLIP_TRY(launch_tp_bwd(L, first, n, C, nl.row_ptr, nl.recv, nl.send, ev, h[t], Gm, w[t], PW, s, Ga, Gb, dw, dY, st,
+                             M->parity != 0));
       MLIP_TRY(launch_sgemm(false, true, E, H, PW * C, dw, PW * C, M->W3[t], P * C, dz2, H, st));
       MLIP_TRY(launch_radial_bwd(H, E, ev, M->W1[t], M->W2[t], (float)M->rc, M->p, dz2, dr, st));
       std::swap(Ga, Gb);

@@ -604,8 +604,8 @@ extern "C" int mlip_hessian_rows(mlip_model* M, int32_t n_systems, const int64_t
   }
   if (n_systems < 1 || n_systems > (1 << 20)) { set_error("system count %d out of range", n_systems); return MLIP_ERR_INVALID_ARG; }
   if (R < 1 || R > 4096) { set_error("row count %d out of range", R); return MLIP_ERR_INVALID_ARG; }
-  if (M->corr || M->gate || M->charges) {
-    set_error("Hessian rows: the GPU path serves the base layer (no symmetric contraction, gate or charges)");
+  if (M->corr || M->gate || M->charges || M->parity) {
+    set_error("Hessian rows: the GPU path serves the base layer (no symmetric contraction, gate, charges or mixed parity)");
     return MLIP_ERR_INVALID_ARG;
   }
   if (M->H != 64 || (M->L != 2 && M->L != 3) || M->C > 128) {

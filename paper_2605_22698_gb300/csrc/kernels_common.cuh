@@ -41,6 +41,10 @@ struct PathInfo {
 // infinity gives sigmoid 0, as it should.
 __device__ __forceinline__ float sigmoid_f(float x) { return __fdividef(1.0f, 1.0f + expf(-x)); }
 __device__ __forceinline__ float silu_f(float x) { return x * sigmoid_f(x); }
+__device__ __forceinline__ float tanh_grad_f(float x) {
+  const float t = tanhf(x);
+  return 1.0f - t * t;
+}
 __device__ __forceinline__ float silu_grad_f(float x) {
   const float s = sigmoid_f(x);
   return s * (1.0f + x * (1.0f - s));

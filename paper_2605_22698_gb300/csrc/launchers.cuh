@@ -15,15 +15,18 @@ int launch_radial_bwd(int H, int E, const float4* ev, const float* W1, const flo
                       const float* dz2, float* dr_tot, cudaStream_t st);
 int launch_sgemm(bool a_km, bool b_nk, int M, int N, int K, const float* A, int lda, const float* B, int ldb,
                  float* C, int ldc, cudaStream_t st);
+// par: mixed-parity models (every path; odd-l2 paths couple the other parity block)
 int launch_tp_fwd(int L, bool first, int n, int C, const int* row_ptr, const int* recv, const int* send,
-                  const float4* ev, const float* h, const float* w, int PW, float s, float* m, cudaStream_t st);
+                  const float4* ev, const float* h, const float* w, int PW, float s, float* m, cudaStream_t st,
+                  bool par = false);
 int launch_tp_bwd(int L, bool first, int n, int C, const int* row_ptr, const int* recv, const int* send,
                   const float4* ev, const float* hprev, const float* Gm, const float* w, int PW, float s,
-                  const float* Gin, float* Gout, float* dw, float* dY, cudaStream_t st);
+                  const float* Gin, float* Gout, float* dw, float* dY, cudaStream_t st, bool par = false);
+// parity: tanh instead of SiLU on the odd scalar block (channels >= C/2) of mixed-parity models
 int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const float* hin, float* hout,
-                   float* u0, cudaStream_t st);
+                   float* u0, cudaStream_t st, int parity = 0);
 int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, const float* WmixT,
-                   float* Gm, cudaStream_t st);
+                   float* Gm, cudaStream_t st, int parity = 0);
 // amax (nullable): per-system max |h| accumulated into amax[2 s] (zeroed by the caller) from the
 // per-species maxima emax[z] = max_c |W_emb[z][c]|
 int launch_embed(int n, int C, int D, int S, const int* species, const float* W_emb, float* h, cudaStream_t st,

@@ -38,6 +38,8 @@ const char* last_error();
 // ------------------------------------------------------- coupling tables
 template <int L>
 struct CGTable;
+template <int L>
+struct CGTableP;  // every triangle-valid path, both parities (mixed-parity models)
 #include "cg_tables.inc"
 
 // ------------------------------------------------------------ workspace
@@ -223,6 +225,8 @@ struct mlip_model {
   // and their transposes for the adjoint ([S][L+1][c2][c1], [L C][C], [S][L C][C])
   int gate = 0;
   std::vector<const float*> Wself, Wgate, Wselfgate, WselfT, WgateT, WselfgateT;
+  // mixed parity (parity = 1): channel blocks of even and odd parity, every triangle-valid path
+  int parity = 0;
   float* d_gateT = nullptr;
   float* d_wmixT = nullptr;            // channel-mix weights transposed, per layer and order
   std::vector<const float*> WmixT;

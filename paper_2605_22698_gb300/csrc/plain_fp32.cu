@@ -17,6 +17,7 @@
 // then g_e = dE/dr r^ + (1/r)(I - r^ r^T) grad_Y . dE/dY, F_i = sum_{recv=i}
 // (g_e - g_rev(e)) and the virial sum_e x_e (x) g_e in FP64.
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels_common.cuh"
 #include "profile.cuh"
@@ -205,15 +206,17 @@ __global__ void __launch_bounds__(256) sgemm(int M, const int* M_dev, int N, int
 // order, gathers the sender's features for its channel, and accumulates the
 // receiver's message in registers, flushed (times s) at segment ends.
 // FIRST: only the l1 = 0 paths (input features are scalars).
-template <int L, bool FIRST>
+// PAR (mixed-parity models): every triangle-valid path (CGTableP); a path with
+// odd l2 reads the sender's channel of the other parity block, cx = (c + C/2) % C.
+template <int L, bool FIRST, bool PAR = false>
 __global__ void tp_fwd(int n, int C, const int* __restrict__ row_ptr, const int* __restrict__ recv,
                        const int* __restrict__ send, const float4* __restrict__ ev, const float* __restrict__ h,
                        const float* __restrict__ w, int PW, float s, float* __restrict__ m) {
-  using Tab = CGTable<L>;
+  using Tab = std::conditional_t<PAR, CGTableP<L>, CGTable<L>>;
   using PI = PathInfo<L>;
   constexpr int D = NodeDims<L>::D;
-  constexpr int NP = FIRST ? PI::P0 : PI::P;
-  constexpr int NZ = FIRST ? PI::NNZ0 : PI::NNZ;
+  constexpr int NP = FIRST ? PI::P0 : Tab::P;
+  constexpr int NZ = FIRST ? Tab::off[PI::P0] : Tab::NNZ;
   constexpr int NZP = (NZ + 3) & ~3;
   constexpr int DH = FIRST ? 1 : D;  // sender components read
   __shared__ __align__(16) float cY[kNT * NZP];
@@ -260,9 +263,14 @@ __global__ void tp_fwd(int n, int C, const int* __restrict__ row_ptr, const int*
       const int r = s_recv[t];
       while (cur < r) { flush(cur); ++cur; }
       const int j = s_send[t];
-      float hj[DH], wp[NP];
+      float hj[DH], hx[PAR ? DH : 1], wp[NP];
 #pragma unroll
       for (int d = 0; d < DH; ++d) hj[d] = active ? h[((size_t)j * D + d) * C + c] : 0.0f;
+      if constexpr (PAR) {
+        const int cx = (c + C / 2) % C;
+#pragma unroll
+        for (int d = 0; d < DH; ++d) hx[d] = active ? h[((size_t)j * D + d) * C + cx] : 0.0f;
+      }
       const float* wrow = w + (size_t)(e0 + t) * PW * C;
 #pragma unroll
       for (int p = 0; p < NP; ++p) wp[p] = active ? wrow[p * C + c] : 0.0f;
@@ -270,10 +278,11 @@ __global__ void tp_fwd(int n, int C, const int* __restrict__ row_ptr, const int*
       static_for<0, NP>([&](auto pc) {
         constexpr int p = decltype(pc)::value;
         constexpr int l1 = Tab::l1[p];
+        constexpr bool swap = PAR && (Tab::l2[p] & 1);
         constexpr int kb = Tab::off[p], ke = Tab::off[p + 1];
         float wh[2 * l1 + 1];
 #pragma unroll
-        for (int q = 0; q < 2 * l1 + 1; ++q) wh[q] = wp[p] * hj[l1 * l1 + q];
+        for (int q = 0; q < 2 * l1 + 1; ++q) wh[q] = wp[p] * (swap ? hx[l1 * l1 + q] : hj[l1 * l1 + q]);
         static_for<kb, ke>([&](auto kc) {
           constexpr int k = decltype(kc)::value;
           constexpr int i3 = Tab::e3[k], j1 = Tab::e1[k] - l1 * l1;
@@ -291,17 +300,21 @@ __global__ void tp_fwd(int n, int C, const int* __restrict__ row_ptr, const int*
 //   G^{t-1}_j[l1 m1] += s w_e[p] (-1)^{l2} C^p[m3][m1][m2] Y_e[l2 m2] Gm_i[l3 m3]   (not FIRST)
 //   with Gt = s Gm_j:  T_p[m2] = sum_entries C h_i[l1 m1] Gt[l3 m3]
 //   dE/dw_e[p] = sum_m2 Y_e[l2 m2] T_p[m2];   dE/dY_e[l2 m2] += sum_c w_e[p] T_p[m2]
-template <int L, bool FIRST>
+// PAR: for a path with odd l2 the forward coupled output channel c to input
+// channel cx = (c + C/2) % C, so thread c's dE/dw and dE/dY read the sender's
+// cx, and its reverse-edge term for the receiver's channel c takes w and Gm of
+// channel cx (the channel whose input c was).
+template <int L, bool FIRST, bool PAR = false>
 __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int* __restrict__ recv,
                        const int* __restrict__ send, const float4* __restrict__ ev,
                        const float* __restrict__ hprev, const float* __restrict__ Gm,
                        const float* __restrict__ w, int PW, float s, const float* __restrict__ Gin,
                        float* __restrict__ Gout, float* __restrict__ dw, float* __restrict__ dY) {
-  using Tab = CGTable<L>;
+  using Tab = std::conditional_t<PAR, CGTableP<L>, CGTable<L>>;
   using PI = PathInfo<L>;
   constexpr int D = NodeDims<L>::D;
-  constexpr int NP = FIRST ? PI::P0 : PI::P;
-  constexpr int NZ = FIRST ? PI::NNZ0 : PI::NNZ;
+  constexpr int NP = FIRST ? PI::P0 : Tab::P;
+  constexpr int NZ = FIRST ? Tab::off[PI::P0] : Tab::NNZ;
   constexpr int NZP = (NZ + 3) & ~3;
   constexpr int DH = FIRST ? 1 : D;
   __shared__ __align__(16) float cY[kNT * NZP];
@@ -370,12 +383,19 @@ __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int*
     for (int t = 0; t < nt; ++t) {
       advance(s_recv[t]);
       const int i = s_send[t];
-      float hi[DH], wp[NP], Y[16];
+      const int cx = PAR ? (c + C / 2) % C : c;
+      float hi[DH], hix[PAR ? DH : 1], wp[NP], wpx[PAR ? NP : 1], Y[16];
 #pragma unroll
       for (int d = 0; d < DH; ++d) hi[d] = active ? hprev[((size_t)i * D + d) * C + c] : 0.0f;
       const float* wrow = w + (size_t)(e0 + t) * PW * C;
 #pragma unroll
       for (int p = 0; p < NP; ++p) wp[p] = active ? wrow[p * C + c] : 0.0f;
+      if constexpr (PAR) {
+#pragma unroll
+        for (int d = 0; d < DH; ++d) hix[d] = active ? hprev[((size_t)i * D + d) * C + cx] : 0.0f;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) wpx[p] = active ? wrow[p * C + cx] : 0.0f;
+      }
 #pragma unroll
       for (int k = 0; k < 16; ++k) Y[k] = sY[t * 16 + k];
       float dYp[16];
@@ -383,17 +403,23 @@ __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int*
       for (int k = 0; k < 16; ++k) dYp[k] = 0.0f;
       float* dwrow = dw + (size_t)(e0 + t) * PW * C;
       if (!FIRST) {
-        float Gi[D];
+        float Gi[D], Gix[PAR ? D : 1];
 #pragma unroll
         for (int d = 0; d < D; ++d) Gi[d] = active ? Gm[((size_t)i * D + d) * C + c] : 0.0f;
+        if constexpr (PAR) {
+#pragma unroll
+          for (int d = 0; d < D; ++d) Gix[d] = active ? Gm[((size_t)i * D + d) * C + cx] : 0.0f;
+        }
         const float* cy = cY + t * NZP;
         static_for<0, NP>([&](auto pc) {
           constexpr int p = decltype(pc)::value;
           constexpr int l3 = Tab::l3[p];
+          constexpr bool swap = PAR && (Tab::l2[p] & 1);
           constexpr int kb = Tab::off[p], ke = Tab::off[p + 1];
           float wg[2 * l3 + 1];
 #pragma unroll
-          for (int q = 0; q < 2 * l3 + 1; ++q) wg[q] = s * wp[p] * Gi[l3 * l3 + q];
+          for (int q = 0; q < 2 * l3 + 1; ++q)
+            wg[q] = swap ? s * wpx[p] * Gix[l3 * l3 + q] : s * wp[p] * Gi[l3 * l3 + q];
           static_for<kb, ke>([&](auto kc) {
             constexpr int k = decltype(kc)::value;
             constexpr int i1 = Tab::e1[k], j3 = Tab::e3[k] - l3 * l3;
@@ -404,6 +430,7 @@ __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int*
       static_for<0, NP>([&](auto pc) {
         constexpr int p = decltype(pc)::value;
         constexpr int l2 = Tab::l2[p];
+        constexpr bool swap = PAR && (l2 & 1);
         constexpr int kb = Tab::off[p], ke = Tab::off[p + 1];
         float Tp[2 * l2 + 1];
 #pragma unroll
@@ -412,7 +439,7 @@ __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int*
           constexpr int k = decltype(kc)::value;
           constexpr int j2 = Tab::e2[k] - l2 * l2, i1 = FIRST ? 0 : Tab::e1[k], i3 = Tab::e3[k];
           constexpr float cv = Tab::ec[k];
-          Tp[j2] = fmaf(cv, hi[i1] * Gt[i3], Tp[j2]);
+          Tp[j2] = fmaf(cv, (swap ? hix[i1] : hi[i1]) * Gt[i3], Tp[j2]);
         });
         float dwp = 0.0f;
 #pragma unroll
@@ -450,12 +477,14 @@ __global__ void tp_bwd(int n, int C, const int* __restrict__ row_ptr, const int*
 // floats) and read four k at a time.
 constexpr int kMixRows = 64;
 constexpr int kMixAS = 132;  // A tile row stride (floats)
+// parity (mixed-parity models): the scalar activation of the odd block (channels
+// >= 64) is tanh instead of SiLU.
 template <bool BWD>
 __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __restrict__ X,
                                                 const float* __restrict__ X2, const float* __restrict__ Wg,
                                                 const float* __restrict__ hin,
                                                 float* __restrict__ out, float* __restrict__ u0,
-                                                const float* __restrict__ u0_in) {
+                                                const float* __restrict__ u0_in, int parity) {
   constexpr int C = 128, C4 = C / 4;
   extern __shared__ __align__(16) float sm[];
   float* Ws = sm;                   // [k][n]
@@ -485,7 +514,11 @@ __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __res
       }
       if (BWD && l == 0) {
         const float4 uu = U4[(size_t)nd * C4 + c4];
-        v.x *= silu_grad_f(uu.x); v.y *= silu_grad_f(uu.y); v.z *= silu_grad_f(uu.z); v.w *= silu_grad_f(uu.w);
+        if (parity && c4 >= C4 / 2) {
+          v.x *= tanh_grad_f(uu.x); v.y *= tanh_grad_f(uu.y); v.z *= tanh_grad_f(uu.z); v.w *= tanh_grad_f(uu.w);
+        } else {
+          v.x *= silu_grad_f(uu.x); v.y *= silu_grad_f(uu.y); v.z *= silu_grad_f(uu.z); v.w *= silu_grad_f(uu.w);
+        }
       }
     }
     va[u] = v;
@@ -551,7 +584,10 @@ __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __res
       } else if (l == 0) {
         reinterpret_cast<float4*>(u0 + (size_t)nd * C)[16 * g + tx] = u;
         const float4 h = hv[i][g];
-        o4[16 * g + tx] = make_float4(h.x + silu_f(u.x), h.y + silu_f(u.y), h.z + silu_f(u.z), h.w + silu_f(u.w));
+        if (parity && g == 1)
+          o4[16 * g + tx] = make_float4(h.x + tanhf(u.x), h.y + tanhf(u.y), h.z + tanhf(u.z), h.w + tanhf(u.w));
+        else
+          o4[16 * g + tx] = make_float4(h.x + silu_f(u.x), h.y + silu_f(u.y), h.z + silu_f(u.z), h.w + silu_f(u.w));
       } else {
         const float4 h = hv[i][g];
         o4[16 * g + tx] = make_float4(h.x + u.x, h.y + u.y, h.z + u.z, h.w + u.w);
@@ -564,7 +600,8 @@ __global__ void __launch_bounds__(128) mix_gemm(int n, int L, const float* __res
 // channel, W_l in shared memory.
 constexpr int kMixNodes = 8;
 __global__ void mix_fwd(int n, int C, int L, const float* __restrict__ m, const float* __restrict__ Wmix,
-                        const float* __restrict__ hin, float* __restrict__ hout, float* __restrict__ u0) {
+                        const float* __restrict__ hin, float* __restrict__ hout, float* __restrict__ u0,
+                        int parity) {
   extern __shared__ float smem[];
   const int l = blockIdx.y, D = (L + 1) * (L + 1), R = 2 * l + 1;
   float* W = smem;                 // [C][C]
@@ -588,7 +625,7 @@ __global__ void mix_fwd(int n, int C, int L, const float* __restrict__ m, const 
     const size_t o = ((size_t)nd * D + l * l + mm) * C + c2;
     if (l == 0) {
       u0[(size_t)nd * C + c2] = u;
-      hout[o] = hin[o] + silu_f(u);
+      hout[o] = hin[o] + ((parity && c2 >= C / 2) ? tanhf(u) : silu_f(u));
     } else {
       hout[o] = hin[o] + u;
     }
@@ -596,7 +633,7 @@ __global__ void mix_fwd(int n, int C, int L, const float* __restrict__ m, const 
 }
 
 __global__ void mix_bwd(int n, int C, int L, const float* __restrict__ G, const float* __restrict__ u0,
-                        const float* __restrict__ Wmix, float* __restrict__ Gm) {
+                        const float* __restrict__ Wmix, float* __restrict__ Gm, int parity) {
   extern __shared__ float smem[];
   const int l = blockIdx.y, D = (L + 1) * (L + 1), R = 2 * l + 1;
   float* Wt = smem;                // Wt[c'][c] = W[c][c']
@@ -612,7 +649,10 @@ __global__ void mix_bwd(int n, int C, int L, const float* __restrict__ G, const 
     float v = 0.0f;
     if (nd < n) {
       v = G[((size_t)nd * D + l * l + mm) * C + cc];
-      if (l == 0) v *= silu_grad_f(u0[(size_t)nd * C + cc]);
+      if (l == 0) {
+        const float uu = u0[(size_t)nd * C + cc];
+        v *= (parity && cc >= C / 2) ? tanh_grad_f(uu) : silu_grad_f(uu);
+      }
     }
     rows[k] = v;
   }
@@ -685,33 +725,40 @@ static int tp_blocks(int n) {
 }
 
 int launch_tp_fwd(int L, bool first, int n, int C, const int* row_ptr, const int* recv, const int* send,
-                  const float4* ev, const float* h, const float* w, int PW, float s, float* m, cudaStream_t st) {
+                  const float4* ev, const float* h, const float* w, int PW, float s, float* m, cudaStream_t st,
+                  bool par) {
   if (n <= 0) return MLIP_OK;
   const int G = tp_blocks(n), threads = std::max(C, 32);
-  if (L == 2 && first) { MLIP_PROF("tp_fwd", st); tp_fwd<2, true><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m); }
-  else if (L == 2) { MLIP_PROF("tp_fwd", st); tp_fwd<2, false><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m); }
-  else if (L == 3 && first) { MLIP_PROF("tp_fwd", st); tp_fwd<3, true><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m); }
-  else if (L == 3) { MLIP_PROF("tp_fwd", st); tp_fwd<3, false><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m); }
+#define MLIP_TPF(LL, FF, PP)                                                                         \
+  {                                                                                                  \
+    MLIP_PROF("tp_fwd", st);                                                                         \
+    tp_fwd<LL, FF, PP><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, h, w, PW, s, m);        \
+  }
+  if (L == 2 && first) { if (par) MLIP_TPF(2, true, true) else MLIP_TPF(2, true, false) }
+  else if (L == 2) { if (par) MLIP_TPF(2, false, true) else MLIP_TPF(2, false, false) }
+  else if (L == 3 && first) { if (par) MLIP_TPF(3, true, true) else MLIP_TPF(3, true, false) }
+  else if (L == 3) { if (par) MLIP_TPF(3, false, true) else MLIP_TPF(3, false, false) }
   else { set_error("l_max %d unsupported", L); return MLIP_ERR_INVALID_ARG; }
+#undef MLIP_TPF
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
 int launch_tp_bwd(int L, bool first, int n, int C, const int* row_ptr, const int* recv, const int* send,
                   const float4* ev, const float* hprev, const float* Gm, const float* w, int PW, float s,
-                  const float* Gin, float* Gout, float* dw, float* dY, cudaStream_t st) {
+                  const float* Gin, float* Gout, float* dw, float* dY, cudaStream_t st, bool par) {
   if (n <= 0) return MLIP_OK;
   const int G = tp_blocks(n), threads = std::max(C, 32);
   if (threads > 128) { set_error("channels %d unsupported", C); return MLIP_ERR_INVALID_ARG; }
-#define MLIP_TPB(LL, FF)                                                                                \
+#define MLIP_TPB(LL, FF, PP)                                                                            \
   {                                                                                                     \
     MLIP_PROF("tp_bwd", st);                                                                            \
-    tp_bwd<LL, FF><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, hprev, Gm, w, PW, s, Gin, Gout, dw, dY); \
+    tp_bwd<LL, FF, PP><<<G, threads, 0, st>>>(n, C, row_ptr, recv, send, ev, hprev, Gm, w, PW, s, Gin, Gout, dw, dY); \
   }
-  if (L == 2 && first) MLIP_TPB(2, true)
-  else if (L == 2) MLIP_TPB(2, false)
-  else if (L == 3 && first) MLIP_TPB(3, true)
-  else if (L == 3) MLIP_TPB(3, false)
+  if (L == 2 && first) { if (par) MLIP_TPB(2, true, true) else MLIP_TPB(2, true, false) }
+  else if (L == 2) { if (par) MLIP_TPB(2, false, true) else MLIP_TPB(2, false, false) }
+  else if (L == 3 && first) { if (par) MLIP_TPB(3, true, true) else MLIP_TPB(3, true, false) }
+  else if (L == 3) { if (par) MLIP_TPB(3, false, true) else MLIP_TPB(3, false, false) }
   else { set_error("l_max %d unsupported", L); return MLIP_ERR_INVALID_ARG; }
 #undef MLIP_TPB
   MLIP_LAUNCH_CHECK();
@@ -719,39 +766,39 @@ int launch_tp_bwd(int L, bool first, int n, int C, const int* row_ptr, const int
 }
 
 int launch_mix_fwd(int n, int C, int L, const float* m, const float* Wmix, const float* hin, float* hout,
-                   float* u0, cudaStream_t st) {
+                   float* u0, cudaStream_t st, int parity) {
   if (n <= 0) return MLIP_OK;
   if (C == 128) {
     const size_t smem = (size_t)(128 * 128 + kMixRows * kMixAS) * sizeof(float);
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
-    { MLIP_PROF("mix_fwd", st); mix_gemm<false><<<grid, 128, smem, st>>>(n, L, m, nullptr, Wmix, hin, hout, u0, nullptr); }
+    { MLIP_PROF("mix_fwd", st); mix_gemm<false><<<grid, 128, smem, st>>>(n, L, m, nullptr, Wmix, hin, hout, u0, nullptr, parity); }
     MLIP_LAUNCH_CHECK();
     return MLIP_OK;
   }
   const size_t smem = ((size_t)C * C + (size_t)kMixNodes * (2 * L + 1) * C) * sizeof(float);
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n + kMixNodes - 1) / kMixNodes, L + 1);
-  { MLIP_PROF("mix_fwd", st); mix_fwd<<<grid, std::max(C, 32), smem, st>>>(n, C, L, m, Wmix, hin, hout, u0); }
+  { MLIP_PROF("mix_fwd", st); mix_fwd<<<grid, std::max(C, 32), smem, st>>>(n, C, L, m, Wmix, hin, hout, u0, parity); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }
 
 int launch_mix_bwd(int n, int C, int L, const float* G, const float* u0, const float* Wmix, const float* WmixT,
-                   float* Gm, cudaStream_t st) {
+                   float* Gm, cudaStream_t st, int parity) {
   if (n <= 0) return MLIP_OK;
   if (C == 128) {
     const size_t smem = (size_t)(128 * 128 + kMixRows * kMixAS) * sizeof(float);
     MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((n * (2 * L + 1) + kMixRows - 1) / kMixRows, L + 1);
-    { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, G, nullptr, WmixT, nullptr, Gm, nullptr, u0); }
+    { MLIP_PROF("mix_bwd", st); mix_gemm<true><<<grid, 128, smem, st>>>(n, L, G, nullptr, WmixT, nullptr, Gm, nullptr, u0, parity); }
     MLIP_LAUNCH_CHECK();
     return MLIP_OK;
   }
   const size_t smem = ((size_t)C * C + (size_t)kMixNodes * (2 * L + 1) * C) * sizeof(float);
   MLIP_CUDA_TRY(cudaFuncSetAttribute(mix_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((n + kMixNodes - 1) / kMixNodes, L + 1);
-  { MLIP_PROF("mix_bwd", st); mix_bwd<<<grid, std::max(C, 32), smem, st>>>(n, C, L, G, u0, Wmix, Gm); }
+  { MLIP_PROF("mix_bwd", st); mix_bwd<<<grid, std::max(C, 32), smem, st>>>(n, C, L, G, u0, Wmix, Gm, parity); }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;
 }

@@ -84,6 +84,7 @@ class ModelSpec:
     charges: int = 0      # 1: charge head + charge correction + Coulomb term (open systems)
     coulomb_r0: float = 0.0  # soft-core radius of the Coulomb term, A (charges = 1)
     gate: int = 0         # 1: species self-connection and gated update of the l > 0 features
+    parity: int = 0       # 1: mixed-parity features (even and odd channel blocks, pseudotensor paths)
 
     @property
     def hyper(self) -> np.ndarray:
@@ -96,12 +97,13 @@ class ModelSpec:
     @property
     def n_paths(self) -> int:
         """Number of (l1, l2, l3) triples with l1, l3 <= L, l2 <= Lsh, triangle
-        rule and even l1 + l2 + l3 (a count, not part of the method's arithmetic)."""
+        rule and even l1 + l2 + l3 (any parity for mixed-parity models; a count,
+        not part of the method's arithmetic)."""
         n = 0
         for l1 in range(self.L + 1):
             for l2 in range(self.Lsh + 1):
                 for l3 in range(self.L + 1):
-                    if abs(l1 - l2) <= l3 <= l1 + l2 and (l1 + l2 + l3) % 2 == 0:
+                    if abs(l1 - l2) <= l3 <= l1 + l2 and (self.parity or (l1 + l2 + l3) % 2 == 0):
                         n += 1
         return n
 
@@ -157,6 +159,8 @@ def model_spec(name: str) -> ModelSpec:
     <name>_gated  the same with the gated update and the species self-connection
     <name>_charged  the same with a charge head, the charge correction and the
                  soft-core Coulomb term (Eqs. charge_correction, long_range_interaction)
+    <name>_parity  the same with mixed-parity features, the irreps of Table
+                 tbl:nequip_params (0e + 0o + 1o + 1e + 2e + 2o) with C/2 channels each
     """
     if name == "small":
         return ModelSpec(S=4, T=1, C=16, L=2, H=32, avg_nb=20.0)
@@ -168,6 +172,8 @@ def model_spec(name: str) -> ModelSpec:
         return dataclasses.replace(model_spec(name[:-5]), correlation=2)
     if name.endswith("_gated"):  # the same model with the gated update and the species self-connection
         return dataclasses.replace(model_spec(name[:-6]), gate=1)
+    if name.endswith("_parity"):  # the same model with mixed-parity features (C/2 channels of each parity)
+        return dataclasses.replace(model_spec(name[:-7]), parity=1)
     if name.endswith("_charged"):  # the same model with the charge head and the Coulomb term (r0 = rc / 2)
         base = model_spec(name[:-8])
         return dataclasses.replace(base, charges=1, coulomb_r0=0.5 * base.rc)
@@ -200,19 +206,23 @@ PARAMS_MAGIC = b"MLIPPRM1"
 
 
 def write_params(path: str, spec: ModelSpec, w: np.ndarray) -> None:
-    """Parameter file: magic, u32 version, 8 x i32 hyper, (version 2 only:
-    i32 correlation, i32 charges, f64 coulomb_r0, i32 gate), 2 x f64 (rc,
-    avg_nb), S x f64 masses, i64 count, count x f32 weights; little-endian.
-    Version 1 for models with none of the contraction, charge head or gate."""
+    """Parameter file: magic, u32 version, 8 x i32 hyper, (versions 2 and 3:
+    i32 correlation, i32 charges, f64 coulomb_r0, i32 gate; version 3: i32
+    parity), 2 x f64 (rc, avg_nb), S x f64 masses, i64 count, count x f32
+    weights; little-endian.  Version 1 for models with none of the options,
+    3 for mixed-parity models, else 2."""
     w = np.ascontiguousarray(w, dtype=np.float32)
     assert w.size == spec.n_weights()
-    v2 = bool(spec.correlation or spec.charges or spec.gate)
+    parity = getattr(spec, "parity", 0)
+    v2 = bool(spec.correlation or spec.charges or spec.gate or parity)
     with open(path, "wb") as f:
         f.write(PARAMS_MAGIC)
-        f.write(struct.pack("<I", 2 if v2 else 1))
+        f.write(struct.pack("<I", 3 if parity else (2 if v2 else 1)))
         f.write(spec.hyper.astype("<i4").tobytes())
         if v2:
             f.write(struct.pack("<iidi", spec.correlation, spec.charges, spec.coulomb_r0, spec.gate))
+        if parity:
+            f.write(struct.pack("<i", parity))
         f.write(spec.dhyper.astype("<f8").tobytes())
         f.write(np.asarray(spec.masses, dtype="<f8").tobytes())
         f.write(struct.pack("<q", w.size))

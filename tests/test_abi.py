@@ -61,7 +61,8 @@ _LAYOUT_C = r"""
 #define Z(T) printf(#T " sizeof %zu\n", sizeof(T));
 int main(void) {
   F(mlip_model_desc, cutoff) F(mlip_model_desc, masses) F(mlip_model_desc, correlation)
-  F(mlip_model_desc, charges) F(mlip_model_desc, coulomb_r0) F(mlip_model_desc, gate) Z(mlip_model_desc)
+  F(mlip_model_desc, charges) F(mlip_model_desc, coulomb_r0) F(mlip_model_desc, gate) F(mlip_model_desc, parity)
+  Z(mlip_model_desc)
   F(mlip_serve_config, max_slots) F(mlip_serve_config, bucket_edges) F(mlip_serve_config, device_poll_limit_us)
   Z(mlip_serve_config)
   F(mlip_request, n) F(mlip_request, pos) F(mlip_request, cell) F(mlip_request, pbc) F(mlip_request, vel)

@@ -25,28 +25,34 @@ def tables(tmp_path_factory):
     subprocess.run([exe, inc], check=True)
     text = open(inc).read()
     out = {}
-    for m in re.finditer(r"struct CGTable<(\d)> \{(.*?)\n\};", text, re.S):
-        L, body = int(m.group(1)), m.group(2)
+    for m in re.finditer(r"struct CGTable(P?)<(\d)> \{(.*?)\n\};", text, re.S):
+        key, body = (int(m.group(2)), m.group(1) == "P"), m.group(3)
         arrs = {}
         for a in re.finditer(r"static constexpr (?:int|float|double) (\w+)\[\d+\] = \{([^}]*)\};", body):
             arrs[a.group(1)] = np.array([float(x.rstrip("f")) for x in a.group(2).split(",")])
-        out[L] = arrs
-    assert set(out) == {2, 3}
+        out[key] = arrs
+    assert set(out) == {(2, False), (3, False), (2, True), (3, True)}
     return out
 
 
-@pytest.mark.parametrize("L", [2, 3])
-def test_paths_match_the_oracle(tables, L):
-    t = tables[L]
+VARIANTS = [(2, False), (3, False), (2, True), (3, True)]  # (l_max, every parity)
+
+
+@pytest.mark.parametrize("L,allp", VARIANTS)
+def test_paths_match_the_oracle(tables, L, allp):
+    t = tables[(L, allp)]
     got = list(zip(t["l1"].astype(int), t["l2"].astype(int), t["l3"].astype(int)))
-    assert got == oracle.paths(L, 3)
+    assert got == oracle.paths(L, 3, all_parities=allp)
 
 
-@pytest.mark.parametrize("L", [2, 3])
-def test_entries_match_the_oracle(tables, L):
-    t = tables[L]
+@pytest.mark.parametrize("L,allp", VARIANTS)
+def test_entries_match_the_oracle(tables, L, allp):
+    """Natural-parity paths: Gaunt integrals; odd l1 + l2 + l3 (the mixed-parity
+    table): integrals of Y_l3 r.(grad Y_l1 x grad Y_l2); both against the
+    oracle's Racah-based real tensors."""
+    t = tables[(L, allp)]
     off = t["off"].astype(int)
-    for p, (l1, l2, l3) in enumerate(oracle.paths(L, 3)):
+    for p, (l1, l2, l3) in enumerate(oracle.paths(L, 3, all_parities=allp)):
         C = oracle.real_cg(l1, l2, l3)  # [m3][m1][m2]
         dense = np.zeros_like(C)
         for k in range(off[p], off[p + 1]):
@@ -62,6 +68,6 @@ def test_entries_match_the_oracle(tables, L):
 
 @pytest.mark.parametrize("L", [2, 3])
 def test_contraction_couplings_are_the_table_paths_with_l1_le_l2(tables, L):
-    t = tables[L]
+    t = tables[(L, False)]
     sub = [(int(a), int(b), int(c)) for a, b, c in zip(t["l1"], t["l2"], t["l3"]) if a <= b <= L]
     assert sub == oracle.sc_paths(L)
