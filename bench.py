@@ -60,7 +60,12 @@ def peaks():
 # kernel was built from at capture time.  When the file has changed since, the
 # counters no longer describe the running kernel and the roofline reports no
 # traffic.
-NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): (129.7e6, "fused_bf16.cu", None)}
+# fcc108k: captured on the 20^3-cell FCC (32,000 atoms, 1,439,826 edges; the full cell is
+# too large for a capture), mean of the five adjoint launches of one evaluation, scaled by
+# the edge count (the sender gathers are per edge)
+NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): (129.7e6, "fused_bf16.cu", None),
+               ("fcc108k", "f16", "tp_fused_bwd"): (25.754369e9 / 5 * 4860690 / 1439826, "fused_bf16.cu",
+                                                    "01672288c574048f")}
 # DRAM bytes per launch of the symmetric contraction's kernels at fcc108k: captured on the
 # 20^3-cell FCC (32,000 atoms; the full workload is too large for a capture) and scaled by the
 # atom count (traffic grows in proportion: per-node tensors)
@@ -442,7 +447,8 @@ def measure(args, rank, world, name, steps, warmup, fp32_peak, plain=True, cpu=T
             nl_step = max(1, round(nl / steps))
             roof.update({"achieved": round(achieved, 3), "frac": round(achieved / peak, 4),
                          "flops_per_launch": round(per_step / nl_step),
-                         "traffic": traffic_of(NCU_TRAFFIC, (name, precision, kname))})
+                         "traffic": traffic_of(NCU_TRAFFIC, (name, precision, kname))
+                         if (name != "fcc108k" or fcc_cells == 30) else None})
             if kname in ("tp_fused", "tp_fused_bwd"):
                 tk = "tensor_" + kname[3:]
                 tens = flops[tk] * steps / (tot_ms / 1e3) / 1e12
