@@ -591,7 +591,8 @@ def run_ours(args, rank, world):
         wl = measure(args, rank, world, "water3000", 20, 3, fp32_peak, plain=not args.no_plain, cpu=False)
         line["water3000"] = {k: wl[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "e2e", "roofline",
                                                 "kernel_share", "plain_fp32", "clocks")}
-        line["serving"] = serve_phase(args, rank, world, args.serve_requests, sweep=[], alone=False)
+        line["serving"] = serve_phase(args, rank, world, args.serve_requests, sweep=[], alone=False,
+                                      fixed_rate=args.serve_fixed_rate)
         line["hessian_rows"] = hessian_phase()
     line["fp32_peak"] = fp32_peak
     line["peaks"] = peaks()
@@ -610,7 +611,7 @@ def serve_requests(n_requests: int, seed: int, rate: float):
     return reqs, systems
 
 
-def serve_phase(args, rank, world, R, sweep, alone):
+def serve_phase(args, rank, world, R, sweep, alone, fixed_rate=None):
     """The serving workload: a warm-up, every request queued at once
     (saturated throughput), then Poisson arrivals at 0.7x the saturated request
     rate (the headline p50/p99), optionally further arrival rates and single
@@ -657,10 +658,11 @@ def serve_phase(args, rank, world, R, sweep, alone):
     ae = atom_evals(reqs)
     sat_rps = R / t_sat
 
-    def open_loop(factor, seed, sampler=None):
-        """Poisson arrivals at factor x the saturated request rate, submitted at
-        their arrival times; the server's statistics and the served atom-steps/s."""
-        lam = factor * sat_rps
+    def open_loop(factor, seed, sampler=None, rate=None):
+        """Poisson arrivals at factor x the saturated request rate (or at a fixed
+        rate per second), submitted at their arrival times; the server's
+        statistics and the served atom-steps/s."""
+        lam = rate if rate else factor * sat_rps
         rq, sy_list = serve_requests(R, seed, lam)
         srv = B.Server(model, bucket_edges=edges)
         if sampler:
@@ -690,6 +692,15 @@ def serve_phase(args, rank, world, R, sweep, alone):
         sw.append({"factor": f, "rate_per_s": round(lam_f, 2), "p50_ms": round(st_f["p50_ms"], 2),
                    "p99_ms": round(st_f["p99_ms"], 2), "throughput_atom_steps_per_s": round(thr_f, 1),
                    "mean_batch_requests": round(st_f["mean_batch_requests"], 2)})
+    # phase 3b: a fixed arrival rate, independent of the saturated rate (which
+    # moves with every change of the kernels), so that builds compare at the same load
+    fixed = None
+    if fixed_rate:
+        lam_x, st_x, thr_x, _ = open_loop(0.0, 9 + rank, rate=fixed_rate)
+        fixed = {"rate_per_s": round(lam_x, 2), "p50_ms": round(st_x["p50_ms"], 2), "p99_ms": round(st_x["p99_ms"], 2),
+                 "mean_ms": round(st_x["mean_ms"], 2), "throughput_atom_steps_per_s": round(thr_x, 1),
+                 "mean_batch_requests": round(st_x["mean_batch_requests"], 2),
+                 "bucket_p99_ms": [round(x, 2) for x in st_x["bucket_p99_ms"]]}
     # phase 4: single requests on an idle server (latency alone, against the mix's buckets)
     alone_ms = []
     if alone:
@@ -721,6 +732,7 @@ def serve_phase(args, rank, world, R, sweep, alone):
                     "mean_batch_requests": round(st["mean_batch_requests"], 2),
                     "skin_steps": int(st["skin_steps"]), "skin_builds": int(st["skin_builds"])},
         "rate_sweep": sw,
+        "fixed_rate": fixed,
         "alone_ms": alone_ms,
         "saturated": {"requests_per_s": round(sat_rps, 2), "p50_ms": round(st_sat["p50_ms"], 2),
                       "p99_ms": round(st_sat["p99_ms"], 2), "busy_atom_steps_per_s": round(st_sat["atom_steps_per_s"], 1),
@@ -737,7 +749,7 @@ def run_serve(args, rank, world):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     R = args.requests
-    sv = serve_phase(args, rank, world, R, args.rate_sweep, alone=True)
+    sv = serve_phase(args, rank, world, R, args.rate_sweep, alone=True, fixed_rate=args.serve_fixed_rate)
     line = {
         "metric": METRIC, "value": sv["saturated_atom_steps_per_s"], "unit": UNIT, "n_gpus": world, "steps": R,
         "warmup": 16, "ms_per_step": sv["saturated_ms_per_request"], "higher_is_better": True, "scaling": "weak",
@@ -748,7 +760,8 @@ def run_serve(args, rank, world):
                    "precision": args.precision, "mix": sv["mix"],
                    "step": "one request (value: atom-evaluations/s with every request queued at once)",
                    "l2": "inputs change every iteration (no flush)"},
-        "latency": sv["latency"], "rate_sweep": sv["rate_sweep"], "alone_ms": sv["alone_ms"],
+        "latency": sv["latency"], "rate_sweep": sv["rate_sweep"], "fixed_rate": sv["fixed_rate"],
+        "alone_ms": sv["alone_ms"],
         "saturated": sv["saturated"], "e2e": sv["e2e"], "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"],
         "cpu_baseline": None,
     }
@@ -756,44 +769,85 @@ def run_serve(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def _oracle_vv(spec_name, w, pos, vel, species, cell, pbc, dt, steps, threads):
+    """The FP64 oracle's velocity-Verlet trajectory (pe, ke per step) of one
+    replica, on `threads` host threads (0: all)."""
+    import oracle
+    if threads > 0:
+        oracle.set_threads(threads)
+    spec = synth.model_spec(spec_name)
+    t0 = time.perf_counter()
+    _, _, pe, ke = oracle.Model(spec, w).vv_nve(pos, vel, species, np.asarray(spec.masses), cell, pbc, dt, steps)
+    return pe, ke, time.perf_counter() - t0, oracle.max_threads()
+
+
 def run_md64(args, rank, world):
     """Batched MD: 64 replicas of 1667 H2O (5001 atoms) in 36.76 A periodic
     cells, different seeds, velocity Verlet at dt 0.5 fs from Maxwell-Boltzmann
     velocities at 300 K; every step evaluates all replicas as one graph.  One
     step = one MD step of all replicas (320,064 atoms).  The node tensors
-    (1.5 GB per layer tensor) exceed L2, so no flush is needed."""
-    R, nmol, side = 64, 1667, 36.76
+    (1.5 GB per layer tensor) exceed L2, so no flush is needed.
+
+    The timed run starts from the initial state (the warm-up run is undone).
+    After the GPU work the FP64 oracle integrates replica 0 from the same
+    state for the first --md-oracle-steps steps; the line reports both
+    total-energy trajectories' drift and their largest gap."""
+    R, nmol, side, dt = 64, 1667, 36.76, 0.5
+    steps = args.steps
     # the replicas are generated by a spawned process pool before any CUDA call
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(min(R, os.cpu_count() or 1)) as pool:
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(R, os.cpu_count() or 1)) as pool:
         reps = pool.starmap(synth.water_box, [(nmol, side, 500 + 64 * rank + k) for k in range(R)])
+    spec = synth.model_spec("water")
+    w = synth.make_weights(spec, 21)
+    masses = np.asarray(spec.masses)
+    vels = [synth.maxwell_boltzmann(masses[r.species], 300.0, seed=900 + 64 * rank + k) for k, r in enumerate(reps)]
+    k_or = min(args.md_oracle_steps, steps) if rank == 0 else 0
     import torch
     from paper_2605_22698_gb300 import binding as B
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda", torch.cuda.current_device())
-    spec = synth.model_spec("water")
-    w = synth.make_weights(spec, 21)
     prec = {"fp32": B.MLIP_PREC_FP32, "bf16": B.MLIP_PREC_BF16, "f16": B.MLIP_PREC_F16}[args.precision]
     model = B.Model(spec, w, prec)
-    masses = np.asarray(spec.masses)
-    vels = [synth.maxwell_boltzmann(masses[r.species], 300.0, seed=900 + 64 * rank + k) for k, r in enumerate(reps)]
     off = np.cumsum([0] + [r.n for r in reps]).astype(np.int64)
-    pos = torch.tensor(np.concatenate([r.pos for r in reps]), device=dev)
-    vel = torch.tensor(np.concatenate(vels), device=dev)
-    sp = torch.tensor(np.concatenate([r.species for r in reps]), device=dev)
+    pos0 = np.concatenate([r.pos for r in reps])
+    vel0 = np.concatenate(vels)
+    sp0 = np.concatenate([r.species for r in reps])
+    pos = torch.tensor(pos0, device=dev)
+    vel = torch.tensor(vel0, device=dev)
+    sp = torch.tensor(sp0, device=dev)
     cells = np.stack([r.cell for r in reps])
     pbc = np.stack([r.pbc for r in reps])
     n = int(off[-1])
     stream = torch.cuda.current_stream()
     skin = args.md_list == "skin"
 
-    def run(steps):
+    def run(k, p=pos, v=vel):
         if skin:  # candidates within rc + 2 A, rebuilt before every 10-step block, blocks replayed as CUDA graphs
-            return model.md_nve_skin(off, pos, vel, sp, cells, pbc, 0.5, steps, skin=2.0, rebuild_every=10,
-                                     use_graph=True, stream=stream)
-        return model.md_nve_batch(off, pos, vel, sp, cells, pbc, 0.5, steps, stream=stream) + ({},)
+            return model.md_nve_skin(off, p, v, sp if isinstance(p, torch.Tensor) else sp0, cells, pbc, dt, k,
+                                     skin=2.0, rebuild_every=10, use_graph=True, stream=stream)
+        return model.md_nve_batch(off, p, v, sp if isinstance(p, torch.Tensor) else sp0, cells, pbc, dt, k,
+                                  stream=stream) + ({},)
 
+    def reset():
+        pos.copy_(torch.from_numpy(pos0))
+        vel.copy_(torch.from_numpy(vel0))
+
+    # kernel shares and the dominant kernel's launch time: a profiled run outside
+    # the timed region (the MD driver runs eagerly while kernels are timed)
     run(args.warmup)
+    reset()
+    B.mlip_profile_select(None)
+    B.mlip_profile_enable(True)
+    k_prof = min(20, steps)
+    run(k_prof)
+    torch.cuda.synchronize()
+    share_rep = B.mlip_profile_report().get("kernels", {})
+    B.mlip_profile_enable(False)
+    reset()
+    run(args.warmup)  # graphs again, past their capture
+    reset()
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
@@ -803,7 +857,7 @@ def run_md64(args, rank, world):
     l0 = B.mlip_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    _, _, pe, ke, rep = run(args.steps)
+    _, _, pe, ke, rep = run(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -811,21 +865,79 @@ def run_md64(args, rank, world):
     clocks = sampler.stop() if sampler else None
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
     etot = (pe + ke).cpu().numpy()  # [steps + 1, R]
-    drift = (etot[-1] - etot[0]) / np.diff(off) / (args.steps * 0.5e-3)  # eV / atom / ps per replica
+    nat = np.diff(off).astype(np.float64)
+    drift = (etot[-1] - etot[0]) / nat / (steps * dt * 1e-3)  # eV / atom / ps per replica
+    # edge count at the initial state (for the algorithmic flop count)
+    E_edges = 0
+    for r in reps:
+        rr, _, _ = B.mlip_neighbors(np.ascontiguousarray(r.pos), r.cell, r.pbc, spec.rc)
+        E_edges += len(rr)
+    roof = None
+    share = {}
+    if share_rep:
+        tot_all = sum(v[1] for v in share_rep.values()) or 1.0
+        for k_, v in sorted(share_rep.items(), key=lambda kv: -kv[1][1])[:8]:
+            share[k_] = round(v[1] / tot_all, 4)
+        kname, (nl, tot_ms) = max(share_rep.items(), key=lambda kv: kv[1][1])
+        flops = algorithmic_flops(spec, E_edges, n)
+        fp32_peak = measure_fp32_peak()
+        peak = fp32_peak["tflops"]
+        roof = {"kernel": kname, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "launches": nl, "avg_launch_ms": round(tot_ms / nl, 5),
+                "peak_src": fp32_peak["src"] + " (of measured)",
+                "timing": f"CUDA events around every launch of {k_prof} MD steps outside the timed region "
+                          "(the MD driver runs without graphs while kernels are timed)"}
+        if kname in flops:
+            nl_step = max(1, round(nl / k_prof))
+            achieved = flops[kname] / nl_step / (tot_ms / nl / 1e3) / 1e12
+            roof.update({"achieved": round(achieved, 3), "frac": round(achieved / peak, 4),
+                         "flops_per_launch": round(flops[kname] / nl_step)})
+    # end to end: host arrays through the public call (copies of positions,
+    # velocities and species in, positions, velocities and energies out)
+    k_e2e = max(10, steps // 10)
+    barrier(world)
+    t0 = time.perf_counter()
+    p_h, v_h, pe_h, _, _ = run(k_e2e, pos0, vel0)
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": round(world * n * k_e2e / t_e2e, 1), "unit": UNIT,
+           "h2d_bytes_per_step": int((pos0.nbytes + vel0.nbytes + sp0.nbytes) / k_e2e),
+           "d2h_bytes_per_step": int((pos0.nbytes + vel0.nbytes + 2 * 8 * R * (k_e2e + 1)) / k_e2e),
+           "steps": k_e2e, "note": "one call of k steps with host arrays; bytes per step = the call's copies / k"}
+    model.close()
+    oracle_cmp = None
+    if k_or > 0:  # the oracle's replica-0 trajectory from the same state, after the GPU work
+        ope, oke, o_s, o_threads = _oracle_vv("water", w, reps[0].pos, vels[0], reps[0].species, reps[0].cell,
+                                              reps[0].pbc, dt, k_or, 0)
+        eo = ope + oke
+        eg = etot[: k_or + 1, 0]
+        oracle_cmp = {
+            "replica": 0, "atoms": int(nat[0]), "steps": k_or,
+            "drift_eV_per_atom_ps": {"gpu": float((eg[-1] - eg[0]) / nat[0] / (k_or * dt * 1e-3)),
+                                     "oracle": float((eo[-1] - eo[0]) / nat[0] / (k_or * dt * 1e-3))},
+            "max_abs_dE_total_eV_per_atom": float(np.abs(eg - eo).max() / nat[0]),
+            "max_abs_dE_potential_eV_per_atom": float(np.abs(pe.cpu().numpy()[: k_or + 1, 0] - ope).max() / nat[0]),
+            "oracle_seconds": round(o_s, 1), "oracle_threads": o_threads}
+    cpu_line = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_line = time_oracle("md64", args.cpu_seconds)
     line = {
-        "metric": METRIC, "value": round(world * n * args.steps / t, 1), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 3),
+        "metric": METRIC, "value": round(world * n * steps / t, 1), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t / steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "bf16": "bf16 tensor-core MLP + f32", "f16": "f16 tensor-core MLP + f32"}[args.precision],
         "data": "synthetic", "impl": "ours",
-        "config": {"workload": "md64", "replicas": R, "atoms": n, "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}",
-                   "precision": args.precision, "dt_fs": 0.5,
+        "config": {"workload": "md64", "replicas": R, "atoms": n, "edges_at_start": E_edges,
+                   "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}",
+                   "precision": args.precision, "dt_fs": dt,
                    "neighbour_list": ("skin 2 A, rebuilt every 10 steps, compacted every step; 10-step blocks "
                                       "replayed as CUDA graphs" if skin else "rebuilt at every force evaluation"),
                    "l2": "working set (1.5 GB per node tensor) exceeds L2; no flush"},
-        "drift_eV_per_atom_ps": {"median": float(np.median(drift)), "max_abs": float(np.abs(drift).max())},
-        "skin_report": rep or None,
-        "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": None,
+        "drift_eV_per_atom_ps": {"median": float(np.median(drift)), "max_abs": float(np.abs(drift).max()),
+                                 "over_steps": steps},
+        "energy_fluctuation_eV_per_atom": float(np.median(etot.std(axis=0) / nat)),
+        "oracle_first_steps": oracle_cmp,
+        "skin_report": rep or None, "e2e": e2e, "roofline": roof, "kernel_share": share,
+        "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu_line,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -873,7 +985,7 @@ def _relaunch(args_gpus: int) -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default 20; md64: 1000)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fcc108k", choices=["water3000", "fcc108k", "cluster64", "serve", "md64",
@@ -886,15 +998,21 @@ def main():
     ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests per phase of the serving sub-object of the default line")
+    ap.add_argument("--serve-fixed-rate", type=float, default=41.7,
+                    help="serving: one more open-loop phase at this absolute arrival rate (requests/s; 0: none)")
     ap.add_argument("--rate-sweep", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.5, 0.9, 1.1],
                     help="serve: further open-loop arrival rates, as factors of the saturated rate")
     ap.add_argument("--fcc-cells", type=int, default=30,
                     help="FCC workloads: conventional cells per edge (30 = 108,000 atoms; smaller for ncu captures)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--md-oracle-steps", type=int, default=20,
+                    help="md64: steps of replica 0 integrated by the FP64 oracle beside the GPU run (0: none)")
     ap.add_argument("--md-list", default="skin", choices=["skin", "fresh"],
                     help="md64: skin list rebuilt every 10 steps with graph replay, or a fresh list every step")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 1000 if (args.workload == "md64" and args.impl == "ours") else 20
     if args.gpus < 1:
         print("bench.py: --gpus must be at least 1", file=sys.stderr)
         sys.exit(2)

@@ -391,6 +391,11 @@ __device__ __forceinline__ void fwd_edge(const float* wv, const float* hj, const
   });
 }
 
+// Hint: the 128-byte line at p into L1 (no register written).
+__device__ __forceinline__ void prefetch_l1(const float* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // One warp set over one tile: 2-edge chunks, sender features prefetched one
 // chunk ahead, partial messages flushed (times s) into this warp set's buffer.
 template <int L, int MODE, int W>
@@ -903,9 +908,9 @@ __device__ __forceinline__ void bwd_tile_ws(int i0, int i1, const int* s_send, c
 
 
 // Heavy groups: one copy of the per-edge body in a runtime loop over the
-// tile's edges (keeps the hot loop inside the instruction cache); the sender
-// gathers run kPF edges ahead in a rotating register window.
-constexpr int kPF = 4;
+// tile's edges, taken in pairs (keeps the hot loop inside the instruction
+// cache); the sender rows of an edge are loaded into one of two register
+// buffers an edge ahead of their use, after an L1 prefetch a pair ahead.
 template <int L, int MODE, int W>
 __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_send, const int* s_recv,
                                                  const float* sY, const float* cY, uint32_t taddr0,
@@ -1003,6 +1008,20 @@ __device__ __forceinline__ void bwd_tile_ws_roll(int i0, int i1, const int* s_se
 #pragma unroll 1
   for (int i = 0; i < cnt; i += 2) {
     const int tA = list[i], tB = lslot(i + 1);
+    {  // the next pair's sender rows into L1 (one line per lane: a warp's 32 channels of a
+       // component), so that their register loads, issued after this pair's first edge, hit L1
+      const int lane = threadIdx.x & 31;
+#pragma unroll
+      for (int q0 = 0; q0 < 2 * (DH + NG); q0 += 32) {
+        const int q = q0 + lane;
+        const int e = i + 2 + q / (DH + NG), d = q % (DH + NG);
+        if (q < 2 * (DH + NG) && e < cnt && (!FIRST || d < DH)) {
+          const int si = s_send[list[e]];
+          prefetch_l1((d < DH ? hprev + ((size_t)si * D + d) * C : Gm + ((size_t)si * D + G::comp0 + d - DH) * C) +
+                      (c & ~31));
+        }
+      }
+    }
     float wA[G::NP], wB[G::NP];
     static_for<0, G::NP>([&](auto sc) {
       constexpr int sl = decltype(sc)::value;
