@@ -635,14 +635,14 @@ def serve_phase(args, rank, world, R, sweep, alone, fixed_rate=None):
 
     # warm-up: a few requests through a throw-away server (workspace growth)
     reqs, systems = serve_requests(min(R, 16), 100 + rank, 1.0)
-    srv = B.Server(model, bucket_edges=edges)
+    srv = B.Server(model, bucket_edges=edges, resident_after=args.serve_resident_after)
     for i in [submit(srv, r, sy) for r, sy in zip(reqs, systems)]:
         srv.wait(i)
     srv.close()
 
     # phase 1: saturated (every request queued at once)
     reqs, systems = serve_requests(R, 4 + rank, 1.0)
-    srv = B.Server(model, bucket_edges=edges)
+    srv = B.Server(model, bucket_edges=edges, resident_after=args.serve_resident_after)
     barrier(world)
     l0 = B.mlip_launch_count()
     t0 = time.perf_counter()
@@ -658,13 +658,21 @@ def serve_phase(args, rank, world, R, sweep, alone, fixed_rate=None):
     ae = atom_evals(reqs)
     sat_rps = R / t_sat
 
+    def iter_ms(st):
+        """Mean worker time per iteration, split by whether the membership changed."""
+        it, ci = st["iterations"], st["changed_iterations"]
+        same = (st["busy_s"] - st["changed_busy_s"]) / (it - ci) * 1e3 if it > ci else None
+        chg = st["changed_busy_s"] / ci * 1e3 if ci else None
+        return {"iterations": int(it), "changed": int(ci), "ms_changed": round(chg, 3) if chg else None,
+                "ms_same": round(same, 3) if same else None}
+
     def open_loop(factor, seed, sampler=None, rate=None):
         """Poisson arrivals at factor x the saturated request rate (or at a fixed
         rate per second), submitted at their arrival times; the server's
         statistics and the served atom-steps/s."""
         lam = rate if rate else factor * sat_rps
         rq, sy_list = serve_requests(R, seed, lam)
-        srv = B.Server(model, bucket_edges=edges)
+        srv = B.Server(model, bucket_edges=edges, resident_after=args.serve_resident_after)
         if sampler:
             sampler.start()
         ids = []
@@ -696,15 +704,15 @@ def serve_phase(args, rank, world, R, sweep, alone, fixed_rate=None):
     # moves with every change of the kernels), so that builds compare at the same load
     fixed = None
     if fixed_rate:
-        lam_x, st_x, thr_x, _ = open_loop(0.0, 9 + rank, rate=fixed_rate)
+        lam_x, st_x, thr_x, _ = open_loop(0.0, 5 + rank, rate=fixed_rate)  # the headline phase's stream
         fixed = {"rate_per_s": round(lam_x, 2), "p50_ms": round(st_x["p50_ms"], 2), "p99_ms": round(st_x["p99_ms"], 2),
                  "mean_ms": round(st_x["mean_ms"], 2), "throughput_atom_steps_per_s": round(thr_x, 1),
                  "mean_batch_requests": round(st_x["mean_batch_requests"], 2),
-                 "bucket_p99_ms": [round(x, 2) for x in st_x["bucket_p99_ms"]]}
+                 "bucket_p99_ms": [round(x, 2) for x in st_x["bucket_p99_ms"]], "iterations": iter_ms(st_x)}
     # phase 4: single requests on an idle server (latency alone, against the mix's buckets)
     alone_ms = []
     if alone:
-        srv = B.Server(model, bucket_edges=edges)
+        srv = B.Server(model, bucket_edges=edges, resident_after=args.serve_resident_after)
         for n_at, kind in ((50, 0), (200, 0), (2000, 0), (200, 1)):
             sy = synth.cluster(n_at, 77 + n_at)
             r = synth.RequestSpec(0.0, n_at, kind, 77 + n_at, 100 if kind else 0)
@@ -730,7 +738,8 @@ def serve_phase(args, rank, world, R, sweep, alone, fixed_rate=None):
                     "bucket_p99_ms": [round(x, 2) for x in st["bucket_p99_ms"]],
                     "mean_batch_atoms": round(st["mean_batch_atoms"], 1),
                     "mean_batch_requests": round(st["mean_batch_requests"], 2),
-                    "skin_steps": int(st["skin_steps"]), "skin_builds": int(st["skin_builds"])},
+                    "skin_steps": int(st["skin_steps"]), "skin_builds": int(st["skin_builds"]),
+                    "iterations": iter_ms(st)},
         "rate_sweep": sw,
         "fixed_rate": fixed,
         "alone_ms": alone_ms,
@@ -998,6 +1007,9 @@ def main():
     ap.add_argument("--requests", type=int, default=300, help="serve: requests per phase")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests per phase of the serving sub-object of the default line")
+    ap.add_argument("--serve-resident-after", type=int, default=0,
+                    help="serving: iterations of unchanged NVE-only membership before a resident neighbour list "
+                         "(0: the server's default; negative: never)")
     ap.add_argument("--serve-fixed-rate", type=float, default=41.7,
                     help="serving: one more open-loop phase at this absolute arrival rate (requests/s; 0: none)")
     ap.add_argument("--rate-sweep", type=lambda v: [float(x) for x in v.split(",") if x], default=[0.5, 0.9, 1.1],

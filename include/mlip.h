@@ -384,6 +384,11 @@ typedef struct {
                                  iteration's results; exceeded: the batch's
                                  requests fail with MLIP_ERR_DEVICE_TIMEOUT and
                                  the server admits nothing more.  0: no limit */
+  int32_t resident_after;     /* a batch of NVE requests keeps a skin neighbour
+                                 list on the device once its members have stayed
+                                 the same for this many iterations (0: 3;
+                                 negative: never, a fresh list every iteration) */
+  int32_t reserved;           /* 0 */
 } mlip_serve_config;
 
 typedef struct {
@@ -432,6 +437,8 @@ typedef struct {
   double bucket_p50_ms[9], bucket_p99_ms[9];
   int64_t skin_steps;         /* MD steps evaluated on the resident skin neighbour list (no rebuild) */
   int64_t skin_builds;        /* skin list builds: a batch of NVE requests kept its members, or an atom left its skin */
+  int64_t changed_iterations; /* iterations whose membership differed from the previous one's (compaction, new layout) */
+  double changed_busy_s;      /* worker time inside those iterations (busy_s includes it) */
 } mlip_serve_statistics;
 
 /* Starts the worker.  Errors: MLIP_ERR_INVALID_ARG (bad config: max_slots < 0,

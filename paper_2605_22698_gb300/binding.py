@@ -514,7 +514,8 @@ MLIP_REQ_NVE = 1
 
 class mlip_serve_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("n_buckets", ctypes.c_int32),
-                ("bucket_edges", ctypes.c_int64 * 8), ("device_poll_limit_us", ctypes.c_int64)]
+                ("bucket_edges", ctypes.c_int64 * 8), ("device_poll_limit_us", ctypes.c_int64),
+                ("resident_after", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class mlip_request(ctypes.Structure):
@@ -543,7 +544,8 @@ class mlip_serve_statistics(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("n_buckets", ctypes.c_int32),
                 ("bucket_count", ctypes.c_int64 * 9), ("bucket_p50_ms", ctypes.c_double * 9),
                 ("bucket_p99_ms", ctypes.c_double * 9), ("skin_steps", ctypes.c_int64),
-                ("skin_builds", ctypes.c_int64)]
+                ("skin_builds", ctypes.c_int64), ("changed_iterations", ctypes.c_int64),
+                ("changed_busy_s", ctypes.c_double)]
 
 
 def _serve_lib():
@@ -562,8 +564,9 @@ def _serve_lib():
 
 
 def mlip_serve_create(h, hbm_budget_bytes: int = 0, max_slots: int = 0, bucket_edges=(),
-                      device_poll_limit_us: int = 0):
+                      device_poll_limit_us: int = 0, resident_after: int = 0):
     c = mlip_serve_config()
+    c.resident_after = int(resident_after)
     c.hbm_budget_bytes = int(hbm_budget_bytes)
     c.max_slots = int(max_slots)
     c.n_buckets = len(bucket_edges)

@@ -398,7 +398,7 @@ __device__ __forceinline__ void prefetch_l1(const float* p) {
 
 // One warp set over one tile: 2-edge chunks, sender features prefetched one
 // chunk ahead, partial messages flushed (times s) into this warp set's buffer.
-template <int L, int MODE, int W>
+template <int L, int MODE, int W, int CHO = 0>
 __device__ __forceinline__ void fwd_tile_ws(const int* s_send, const int* s_recv, const float* cY, uint32_t taddr0,
                                             const float* __restrict__ h, int& cur, float* acc,
                                             float* __restrict__ mW, float s, const int* list, int cnt) {
@@ -407,7 +407,7 @@ __device__ __forceinline__ void fwd_tile_ws(const int* s_send, const int* s_recv
   constexpr int D = NodeDims<L>::D;
   constexpr int C = 128;
   constexpr int DH = S::dh(W);
-  constexpr int CH = chunk_edges<DH>();
+  constexpr int CH = CHO > 0 ? CHO : chunk_edges<DH>();  // edges per chunk (CHO: set by the caller)
   const int c = threadIdx.x & 127;
   if (cnt <= 0) return;  // uniform over the warp set
   auto slot = [&](int i) { return list[i < cnt ? i : cnt - 1]; };
@@ -609,6 +609,251 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(FwdLayout<L, MODE>::byte
   if (warp == 0) tc::tmem_dealloc(tbase, G::NCOLS);
 }
 
+// Pipelined forward for the groups that fit one CTA per SM: two producer warps
+// prepare tile it + 1 (ids, edge lists, harmonics, c.Y products, the z2 copy
+// and the product w = W3^T z2 into the other of two tensor-memory buffers)
+// while the eight consumer warps run tile it; mbarriers full / done per buffer
+// order them, so the consumers never wait at a CTA-wide barrier.
+// Pipelined kernels (forward and adjoint): two warp sets of consumers, two producer warps.
+constexpr int kWSConsumers = 256, kWSProducers = 64, kWSThreads = kWSConsumers + kWSProducers;
+constexpr int kWSFChunk = 2;  // consumers' edges per chunk (register budget of 10 warps per SM)
+
+template <int L, int MODE>
+struct FwdLayoutWS {
+  using G = Group<L, MODE>;
+  static constexpr int NP = G::NP;
+  static constexpr int tmem_cols() {
+    int need = 2 * NP * kNT, c = 32;
+    while (c < need) c <<= 1;
+    return c;
+  }
+  static constexpr int NCOLS = tmem_cols();
+  static constexpr size_t off_z2 = (size_t)NP * kW3PathBytes;
+  static constexpr size_t off_cy = off_z2 + 2 * kTileBytes;
+  static constexpr size_t off_y = off_cy + 2 * (size_t)kNT * G::NZP * 4;
+  static constexpr size_t off_tab = off_y + 2 * kNT * 16 * 4;
+  static constexpr size_t off_taby = off_tab + (size_t)G::NZP * 4;
+  static constexpr size_t off_idx = off_taby + (((size_t)G::NZP + 15) & ~(size_t)15);
+  static constexpr size_t off_bar = off_idx + 2 * 2 * kNT * 4;
+  static constexpr size_t bytes = off_bar + 128;
+  static constexpr bool fits = bytes <= 232448 - 1024 && NCOLS <= 512;
+};
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(kWSThreads, 1)
+    tp_fused_ws(int n, const int* __restrict__ row_ptr, const int* __restrict__ recv, const int* __restrict__ send,
+                const float* __restrict__ Yg, const float* __restrict__ h, const uint8_t* __restrict__ w3img,
+                const uint8_t* __restrict__ z2t, float s, float* __restrict__ mA, float* __restrict__ mB,
+                int use_bf16, const uint8_t* __restrict__ epar, int* __restrict__ err) {
+  using G = Group<L, MODE>;
+  using FL = FwdLayoutWS<L, MODE>;
+  static_assert(FL::fits, "shared or tensor memory of the pipelined forward kernel exceeds the per-SM limits");
+  constexpr int D = NodeDims<L>::D;
+  constexpr int C = 128;
+  constexpr int NP = G::NP;
+  constexpr int NZ = G::NZ, NZP = G::NZP;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sW3 = smem;
+  uint8_t* sZ2 = smem + FL::off_z2;
+  float* cYb = reinterpret_cast<float*>(smem + FL::off_cy);
+  float* sYb = reinterpret_cast<float*>(smem + FL::off_y);
+  float* tab_c = reinterpret_cast<float*>(smem + FL::off_tab);
+  uint8_t* tab_y = smem + FL::off_taby;
+  int* idxb = reinterpret_cast<int*>(smem + FL::off_idx);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + FL::off_bar);
+  uint64_t* bar_w3 = bars;
+  uint64_t* bar_z2 = bars + 1;    // [2]
+  uint64_t* bar_full = bars + 3;  // [2]
+  uint64_t* bar_done = bars + 5;  // [2]
+  uint64_t* bar_fin = bars + 7;
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 8);
+  __shared__ volatile int abort_s;
+  __shared__ int abort_p;
+  __shared__ int s_lists[2][2 * kNT], s_cnts[2][2];
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(tmem_holder, FL::NCOLS);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(bar_w3, 1);
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(bar_z2 + b, 1);
+      tc::mbar_init(bar_full + b, kWSProducers + 1);
+      tc::mbar_init(bar_done + b, kWSConsumers);
+    }
+    tc::mbar_init(bar_fin, 1);
+    tc::fence_mbar_init();
+    abort_s = 0;
+    abort_p = 0;
+  }
+  load_group_table<L, MODE, false>(tab_c, tab_y);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tmem_holder;
+  const uint32_t wcol0 = 0, wcol1 = NP * kNT;
+
+  int i0, i1;
+  block_receivers(row_ptr, n, blockIdx.x, gridDim.x, &i0, &i1);
+  const int E0 = row_ptr[i0], E1 = row_ptr[i1];
+  const int t_begin = E0 / kNT, t_end = (E1 > E0) ? (E1 + kNT - 1) / kNT : t_begin;
+  const int n_tiles = t_end - t_begin;
+  const uint32_t idesc = tc::idesc_16bit(128, kNT, use_bf16 != 0);
+
+  if (warp >= 8) {
+    // ---------------------------------------------------------- producers
+    const int pt = tid - kWSConsumers;  // 0..63
+    const bool elect = pt == 0;
+    int z2_issued[2] = {0, 0}, z2_waited[2] = {0, 0};
+    bool w3_waited = false;
+    if (elect && n_tiles > 0) {
+      tc::mbar_arrive_expect_tx(bar_w3, NP * kW3PathBytes);
+#pragma unroll 1
+      for (int sl = 0; sl < NP; ++sl)
+        tc::bulk_g2s(sW3 + sl * kW3PathBytes, w3img + (size_t)sl * kW3PathBytes, kW3PathBytes, bar_w3);
+    }
+    auto setup = [&](int it) {  // tile it into buffer b = it & 1
+      const int b = it & 1, tile = t_begin + it;
+      int* s_send = idxb + b * 2 * kNT;
+      int* s_recv = s_send + kNT;
+      float* sY = sYb + b * kNT * 16;
+      float* cY = cYb + b * kNT * NZP;
+      if (elect) {
+        tc::mbar_arrive_expect_tx(bar_z2 + b, kTileBytes);
+        tc::bulk_g2s(sZ2 + b * kTileBytes, z2t + (size_t)tile * kTileBytes, kTileBytes, bar_z2 + b);
+        z2_issued[b]++;
+      }
+      if (pt < kNT) {  // one warp: lane = edge slot
+        const int e = tile * kNT + pt;
+        const bool valid = e >= E0 && e < E1;
+        s_recv[pt] = valid ? recv[e] : -1;
+        s_send[pt] = valid ? send[e] : 0;
+        build_lists(pt, valid, valid ? epar[e] : 0, s_lists[b], s_cnts[b]);
+      }
+      for (int q = pt; q < kNT * 4; q += kWSProducers) {
+        const int t = q >> 2, e = tile * kNT + t;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e >= E0 && e < E1) v = reinterpret_cast<const float4*>(Yg)[(size_t)e * 4 + (q & 3)];
+        reinterpret_cast<float4*>(sY)[q] = v;
+      }
+      tc::named_bar(1, kWSProducers);
+      for (int q = pt; q < kNT * NZ; q += kWSProducers) {
+        const int t = q / NZ, k = q - t * NZ;
+        cY[t * NZP + k] = tab_c[k] * sY[t * 16 + tab_y[k]];
+      }
+      if (elect) {
+        bool ok = true;
+        if (!w3_waited) ok = w3_waited = tc::mbar_wait(bar_w3, 0);
+        ok = ok && tc::mbar_wait(bar_z2 + b, (uint32_t)(z2_waited[b] & 1));
+        if (ok) {
+          z2_waited[b]++;
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_u32(sW3), b0 = tc::smem_u32(sZ2 + b * kTileBytes);
+          const uint32_t wcol = b ? wcol1 : wcol0;
+#pragma unroll 1
+          for (int sl = 0; sl < NP; ++sl)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad = tc::desc_noswizzle(a0 + sl * kW3PathBytes + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+              const uint64_t bd = tc::desc_noswizzle(b0 + kk * 256, tc::kCanonLBO, tc::kCanonSBO);
+              tc::mma_bf16(tbase + wcol + sl * kNT, ad, bd, idesc, kk > 0 ? 1u : 0u);
+            }
+          tc::mma_commit(bar_full + b);
+        } else {
+          atomicOr(err, 1);
+          abort_s = 1;
+          tc::mbar_arrive(bar_full + b);  // completes the phase so the consumers see the abort
+        }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(bar_full + b);
+    };
+    auto stop = [&]() -> bool {  // one decision for all producer threads (named barriers must not diverge)
+      if (elect) abort_p = abort_s;
+      tc::named_bar(1, kWSProducers);
+      const bool st = abort_p != 0;
+      tc::named_bar(1, kWSProducers);
+      return st;
+    };
+    if (n_tiles > 0) setup(0);
+#pragma unroll 1
+    for (int it = 0; it + 1 < n_tiles; ++it) {
+      if (stop()) break;
+      // buffer (it + 1) & 1 was last read by the consumers' tile it - 1
+      if (it >= 1 && !tc::mbar_wait_sleep(bar_done + ((it + 1) & 1), (uint32_t)(((it - 1) >> 1) & 1))) {
+        atomicOr(err, 2);
+        abort_s = 1;
+      }
+      if (stop()) break;
+      tc::fence_after_sync();
+      setup(it + 1);
+    }
+    if (elect) {
+      for (int b = 0; b < 2; ++b)
+        while (z2_waited[b] < z2_issued[b]) {
+          if (!tc::mbar_wait(bar_z2 + b, (uint32_t)(z2_waited[b] & 1), 1LL << 20)) break;
+          z2_waited[b]++;
+        }
+      if (n_tiles > 0 && !w3_waited) tc::mbar_wait(bar_w3, 0, 1LL << 20);
+      tc::mma_commit(bar_fin);  // every product issued by this thread
+    }
+  } else {
+    // ---------------------------------------------------------- consumers
+    const int wsid = warp >> 2, c = tid & 127;
+    float* mW = wsid == 0 ? mA : mB;
+    const uint32_t taddr0 = tbase + ((uint32_t)((warp & 3) * 32) << 16);
+    float acc[G::NOUT];
+#pragma unroll
+    for (int q = 0; q < G::NOUT; ++q) acc[q] = 0.0f;
+    int cur = i0;
+    bool aborted = false;
+#pragma unroll 1
+    for (int it = 0; it < n_tiles; ++it) {
+      const int b = it & 1;
+      if (abort_s) {
+        aborted = true;
+        break;
+      }
+      if (!tc::mbar_wait(bar_full + b, (uint32_t)((it >> 1) & 1))) {
+        atomicOr(err, 2);
+        abort_s = 1;
+        aborted = true;
+        break;
+      }
+      if (abort_s) {  // the producers failed on this tile: its buffers are not valid
+        aborted = true;
+        break;
+      }
+      tc::fence_after_sync();
+      const int* s_send = idxb + b * 2 * kNT;
+      const int* s_recv = s_send + kNT;
+      const float* cY = cYb + b * kNT * NZP;
+      fwd_tile_ws<L, MODE, 0, kWSFChunk>(s_send, s_recv, cY, taddr0 + (b ? wcol1 : wcol0), h, cur, acc, mW, s,
+                                          s_lists[b] + wsid * kNT, s_cnts[b][wsid]);
+      tc::fence_before_sync();
+      tc::mbar_arrive(bar_done + b);
+    }
+    if (!aborted) {
+      while (cur < i1) {
+#pragma unroll
+        for (int q = 0; q < G::NOUT; ++q) {
+          mW[((size_t)cur * D + G::comp0 + q) * C + c] = s * acc[q];
+          acc[q] = 0.0f;
+        }
+        ++cur;
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (tid == 0) tc::mbar_wait(bar_fin, 0, 1LL << 20);  // no product in flight, bounded
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tbase, FL::NCOLS);
+}
+
 // ------------------------------------------------------------ tp_fused_bwd
 // Adjoint of one layer for one path group.  Per tile of kNT receiver-sorted
 // edges: (1) w = W3_p^T z2 recomputed on the tensor cores into tensor memory;
@@ -662,7 +907,6 @@ struct BwdLayoutT {
 
 
 // Pipelined form's buffers (see tp_fused_bwd_ws below).
-constexpr int kWSConsumers = 256, kWSProducers = 64, kWSThreads = kWSConsumers + kWSProducers;
 
 template <int L, int MODE, bool SPLIT>
 struct BwdLayoutWST {
@@ -1768,13 +2012,24 @@ template <int L, int MODE>
 int launch_group(int n, const int* row_ptr, const int* recv, const int* send, const float* Yg, const float* h,
                  const uint8_t* w3img, const uint8_t* z2t, float s, float* mA, float* mB, int use_bf16,
                  const uint8_t* epar, int* err, int blocks, cudaStream_t st) {  // blocks: SM count
-  const size_t smem = FwdLayout<L, MODE>::bytes;
-  MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  blocks = std::min(n, blocks * resident_ctas(tp_fused<L, MODE>, smem, Group<L, MODE>::NCOLS));
-  {
-    MLIP_PROF("tp_fused", st);
-    tp_fused<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, h, w3img, z2t, s, mA, mB, use_bf16,
-                                                      epar, err);
+  if constexpr (ctas_per_sm(FwdLayout<L, MODE>::bytes) == 1 && FwdLayoutWS<L, MODE>::fits) {  // pipelined
+    const size_t smem = FwdLayoutWS<L, MODE>::bytes;
+    MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused_ws<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    blocks = std::min(n, blocks);
+    {
+      MLIP_PROF("tp_fused", st);
+      tp_fused_ws<L, MODE><<<blocks, kWSThreads, smem, st>>>(n, row_ptr, recv, send, Yg, h, w3img, z2t, s, mA, mB,
+                                                            use_bf16, epar, err);
+    }
+  } else {
+    const size_t smem = FwdLayout<L, MODE>::bytes;
+    MLIP_CUDA_TRY(cudaFuncSetAttribute(tp_fused<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    blocks = std::min(n, blocks * resident_ctas(tp_fused<L, MODE>, smem, Group<L, MODE>::NCOLS));
+    {
+      MLIP_PROF("tp_fused", st);
+      tp_fused<L, MODE><<<blocks, kThreads, smem, st>>>(n, row_ptr, recv, send, Yg, h, w3img, z2t, s, mA, mB,
+                                                        use_bf16, epar, err);
+    }
   }
   MLIP_LAUNCH_CHECK();
   return MLIP_OK;

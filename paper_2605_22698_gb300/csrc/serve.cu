@@ -164,7 +164,8 @@ struct mlip_server {
   std::unordered_map<uint64_t, std::shared_ptr<mlip::Request>> table;
   // statistics
   int64_t submitted = 0, completed = 0, failed = 0, rejected = 0;
-  int64_t iterations = 0, atom_evals = 0, batch_req_sum = 0;
+  int64_t iterations = 0, atom_evals = 0, batch_req_sum = 0, changed_iterations = 0;
+  double changed_busy_s = 0.0;
   double busy_s = 0.0;
   std::vector<double> lat_ms;
   std::vector<int64_t> lat_n;
@@ -185,6 +186,7 @@ struct mlip_server {
   // arena and batch.
   mlip::SkinList sl;
   bool skin_ok = false;
+  int same_run = 0;  // consecutive iterations (this one included) with the same members
   std::atomic<int64_t> skin_reuses{0}, skin_builds{0};  // read by mlip_serve_stats
   cudaGraph_t sgraph = nullptr;
   cudaGraphExec_t sexec = nullptr;
@@ -491,6 +493,7 @@ int iterate(mlip_server* S, std::vector<ReqPtr>& cur, const Arena& A, bool same_
   }
   std::vector<int> slot_rc(nsys, MLIP_OK);
   if (!same_members) S->skin_ok = false;  // the arena was rebuilt: the list's atom order is gone
+  S->same_run = same_members ? S->same_run + 1 : 1;
   const bool fused = M->precision != MLIP_PREC_FP32;
   int rc = MLIP_OK;
   if (fused && S->skin_ok && any_active)
@@ -555,6 +558,9 @@ int iterate(mlip_server* S, std::vector<ReqPtr>& cur, const Arena& A, bool same_
   // step's start, if it has none
   bool keep_members = fused;
   for (int s = 0; s < nsys && keep_members; ++s) keep_members = !ends[s] && cur[s]->kind == MLIP_REQ_NVE;
+  // (only once the members have stayed for resident_after iterations: a list
+  // built for a batch that changes again a step later costs more than it saves)
+  keep_members = keep_members && S->cfg.resident_after > 0 && S->same_run >= S->cfg.resident_after;
   if (keep_members && !S->skin_ok) {
     S->drop_skin_graph();
     const int brc = skin_build(M->ws, A.pos, b, M->rc, kServeSkin, &S->sl, st);
@@ -649,10 +655,11 @@ void worker_main(mlip_server* S) {
     if (cur.empty()) continue;
     Arena A;
     int rc = MLIP_OK;
-    if (changed || !fresh.empty()) rc = compact(S, cur, n_old, &A);
+    const bool moved = changed || !fresh.empty();
+    if (moved) rc = compact(S, cur, n_old, &A);
     else rc = get_arena(S, S->arena, S->arena_n, &A);
     std::vector<ReqPtr> ended;
-    if (rc == MLIP_OK) rc = iterate(S, cur, A, !(changed || !fresh.empty()), ended);
+    if (rc == MLIP_OK) rc = iterate(S, cur, A, !moved, ended);
     const double dt_it = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_it).count();
     std::lock_guard<std::mutex> lk(S->mu);
     S->running = cur;
@@ -675,6 +682,10 @@ void worker_main(mlip_server* S) {
     S->atom_evals += cur.back()->off + cur.back()->n;
     S->batch_req_sum += (int64_t)cur.size();
     S->busy_s += dt_it;
+    if (moved) {
+      ++S->changed_iterations;
+      S->changed_busy_s += dt_it;
+    }
     changed = !ended.empty();
     if (changed) {
       for (auto& r : ended) {
@@ -733,7 +744,9 @@ extern "C" int mlip_serve_create(mlip_model* M, const mlip_serve_config* cfg, ml
   }
   for (int b = 1; b < c.n_buckets; ++b)
     if (c.bucket_edges[b] <= c.bucket_edges[b - 1]) { set_error("serve: bucket edges must ascend"); return MLIP_ERR_INVALID_ARG; }
+  if (c.reserved != 0) { set_error("serve: reserved configuration field must be 0"); return MLIP_ERR_INVALID_ARG; }
   if (c.max_slots == 0) c.max_slots = 512;
+  if (c.resident_after == 0) c.resident_after = 3;
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != M->device) { set_error("model lives on device %d, current device is %d", M->device, cur); return MLIP_ERR_INVALID_ARG; }
@@ -877,6 +890,8 @@ extern "C" int mlip_serve_stats(mlip_server* S, mlip_serve_statistics* out) {
   out->queued = (int64_t)S->queue.size();
   out->running = (int64_t)S->running.size();
   out->iterations = S->iterations;
+  out->changed_iterations = S->changed_iterations;
+  out->changed_busy_s = S->changed_busy_s;
   out->atom_evals = S->atom_evals;
   out->elapsed_s = now_s(S->t0);
   out->busy_s = S->busy_s;

@@ -64,6 +64,7 @@ int main(void) {
   F(mlip_model_desc, charges) F(mlip_model_desc, coulomb_r0) F(mlip_model_desc, gate) F(mlip_model_desc, parity)
   Z(mlip_model_desc)
   F(mlip_serve_config, max_slots) F(mlip_serve_config, bucket_edges) F(mlip_serve_config, device_poll_limit_us)
+  F(mlip_serve_config, resident_after)
   Z(mlip_serve_config)
   F(mlip_request, n) F(mlip_request, pos) F(mlip_request, cell) F(mlip_request, pbc) F(mlip_request, vel)
   F(mlip_request, seed) F(mlip_request, dt_fs) Z(mlip_request)
@@ -71,7 +72,8 @@ int main(void) {
   Z(mlip_result)
   F(mlip_serve_statistics, elapsed_s) F(mlip_serve_statistics, device_bytes) F(mlip_serve_statistics, n_buckets)
   F(mlip_serve_statistics, bucket_count) F(mlip_serve_statistics, bucket_p99_ms) F(mlip_serve_statistics, skin_steps)
-  F(mlip_serve_statistics, skin_builds) Z(mlip_serve_statistics)
+  F(mlip_serve_statistics, skin_builds) F(mlip_serve_statistics, changed_iterations)
+  F(mlip_serve_statistics, changed_busy_s) Z(mlip_serve_statistics)
   F(mlip_md_options, rebuild_every) F(mlip_md_options, use_graph) Z(mlip_md_options)
   F(mlip_md_report, redone_blocks) F(mlip_md_report, max_candidates) F(mlip_md_report, max_displacement)
   Z(mlip_md_report)
