@@ -581,7 +581,10 @@ __global__ void __launch_bounds__(kThreads, ctas_per_sm(FwdLayout<L, MODE>::byte
       abort_s = 1;
     }
     tc::fence_after_sync();
-    fwd_tile_ws<L, MODE, 0>(s_send, s_recv, cY, taddr0, h, cur, acc, mW, s, s_list + wsid * kNT, s_cnt[wsid]);
+    // two CTAs per SM leave 128 registers a thread: 2-edge chunks when an edge carries the 16 sender
+    // components of l1 <= 3 (4-edge chunks of them spill)
+    constexpr int CHO = (ctas_per_sm(FwdLayout<L, MODE>::bytes) == 2 && Split<L, MODE, false>::dh(0) > 12) ? 2 : 0;
+    fwd_tile_ws<L, MODE, 0, CHO>(s_send, s_recv, cY, taddr0, h, cur, acc, mW, s, s_list + wsid * kNT, s_cnt[wsid]);
     tc::fence_before_sync();
     __syncthreads();
     if (abort_s) break;
