@@ -470,19 +470,33 @@ def measure(args, rank, world, name, steps, warmup, fp32_peak, plain=True, cpu=T
                                   "frac": round(gbs / peaks()["hbm_gbs"], 4),
                                   "traffic": traffic_of(NCU_TRAFFIC_SC, (name, precision, kname))
                                   if fcc_cells == 30 else None}
-    # the gated update's kernels (FP32 ALUs): 4 C^2 (D + L) flops per node and launch, each direction
+    # the gated update's kernels, per step over all layers, each direction: 4 C^2 (D + L) algorithmic
+    # flops per node and layer; algorithmic bytes per node and layer (FP32): forward reads the two
+    # message buffers and h, writes pre and h' (D rows each) and the gates (L rows), the adjoint reads
+    # and writes dE/dh' (two buffers), reads pre and the gates, writes dE/dpre, dE/dg, dE/dm and dE/dh.
+    # The fused form runs them on the tensor cores (split FP16, three products per term; latency-bound
+    # at these sizes, so the HBM figure is reported beside the flop rate); the plain form on the ALUs.
     gate_roof = None
     if "gate_fwd" in share_rep:
         D_ = (spec.L + 1) ** 2
-        flop = 4.0 * spec.C * spec.C * (D_ + spec.L) * s.n
+        flop = 4.0 * spec.C * spec.C * (D_ + spec.L) * s.n * spec.T
+        nbytes = {"fwd": (5 * D_ + spec.L) * spec.C * 4.0 * s.n * spec.T,
+                  "bwd": (10 * D_ + 3 * spec.L) * spec.C * 4.0 * s.n * spec.T}
+        tensor = precision != "fp32"
+        tpk = peaks()["bf16_tflops"] if tensor else peak
         gate_roof = {}
-        for kname in ("gate_fwd", "gate_bwd"):
-            nl_, tot_ = share_rep.get(kname, (0, 0.0))
-            if nl_:
-                tf = flop / (tot_ / nl_ / 1e3) / 1e12
-                gate_roof[kname] = {"bound": "alu", "flops_per_launch": flop, "avg_launch_ms": round(tot_ / nl_, 5),
-                                    "achieved": round(tf, 2), "peak": peak, "unit": "TFLOP/s",
-                                    "frac": round(tf / peak, 4)}
+        for key, names in (("fwd", ("gate_fwd",)), ("bwd", ("gate_prep", "gate_bwd"))):
+            ms = sum(share_rep.get(k_, (0, 0.0))[1] for k_ in names) / n_share
+            if ms <= 0:
+                continue
+            tf = flop / (ms / 1e3) / 1e12
+            gbs = nbytes[key] / (ms / 1e3) / 1e9
+            gate_roof[key] = {"kernels": list(names), "ms_per_step": round(ms, 4), "flops_per_step": flop,
+                              "bound": "tensor" if tensor else "alu", "achieved": round(tf, 2), "peak": tpk,
+                              "unit": "TFLOP/s", "frac": round(tf / tpk, 4),
+                              "hbm": {"bytes_per_step": nbytes[key], "achieved": round(gbs, 1),
+                                      "peak": peaks()["hbm_gbs"], "unit": "GB/s",
+                                      "frac": round(gbs / peaks()["hbm_gbs"], 4)}}
     # the Coulomb term (models with charges): pair evaluations per second of its all-pairs kernel
     coul = None
     if "coulomb_pairs" in share_rep:

@@ -318,6 +318,44 @@ int mlip_model_create(const mlip_model_desc* desc, const float* weights, int64_t
         M->mix_scale.push_back(M->d_mixscale + (size_t)t * (M->L + 1));
       }
     }
+    if (M->gate) {  // split FP16 weight blocks of the tensor-core gate, per layer: forward, then adjoint
+      std::vector<uint8_t> imgs, f, b;
+      std::vector<float> scales, sf, sb;
+      std::vector<size_t> off;
+      for (int t = 0; t < M->T; ++t) {
+        const float* hw = M->host_weights.data();
+        const float *wm = hw + (M->Wmix[t] - M->d_weights), *wsf = hw + (M->Wself[t] - M->d_weights),
+                    *wg = hw + (M->Wgate[t] - M->d_weights), *wsg = hw + (M->Wselfgate[t] - M->d_weights);
+        pack_gate_images(false, wm, wsf, wg, wsg, M->L, M->S, f, sf);
+        pack_gate_images(true, wm, wsf, wg, wsg, M->L, M->S, b, sb);
+        off.push_back(imgs.size());
+        imgs.insert(imgs.end(), f.begin(), f.end());
+        off.push_back(imgs.size());
+        imgs.insert(imgs.end(), b.begin(), b.end());
+        scales.insert(scales.end(), sf.begin(), sf.end());
+        scales.insert(scales.end(), sb.begin(), sb.end());
+      }
+      cudaError_t e2 = cudaMalloc(&M->d_gateimg, imgs.size());
+      if (e2 == cudaSuccess) e2 = cudaMemcpy(M->d_gateimg, imgs.data(), imgs.size(), cudaMemcpyHostToDevice);
+      if (e2 == cudaSuccess) e2 = cudaMalloc(&M->d_gatescale, sizeof(float) * scales.size());
+      if (e2 == cudaSuccess)
+        e2 = cudaMemcpy(M->d_gatescale, scales.data(), sizeof(float) * scales.size(), cudaMemcpyHostToDevice);
+      if (e2 != cudaSuccess) {
+        cudaGetLastError();
+        set_error("tensor-core gate weight images: %s", cudaGetErrorString(e2));
+        mlip_model_free(M);
+        return MLIP_ERR_OOM;
+      }
+      const size_t per = (size_t)(M->L + 1) * 4;
+      for (int t = 0; t < M->T; ++t) {
+        M->gate_fwd_img.push_back(M->d_gateimg + off[2 * t]);
+        M->gate_bwd_img.push_back(M->d_gateimg + off[2 * t + 1]);
+        M->gate_fwd_scale.push_back(M->d_gatescale + (2 * t) * per);
+        M->gate_bwd_scale.push_back(M->d_gatescale + (2 * t + 1) * per);
+      }
+      const int rc = gate_tc_prepare();
+      if (rc != MLIP_OK) { mlip_model_free(M); return rc; }
+    }
     {  // per-species max |W_emb row|
       std::vector<float> em(M->S, 0.0f);
       const float* We = M->host_weights.data() + (M->W_emb - M->d_weights);
@@ -414,6 +452,8 @@ int mlip_model_free(mlip_model* M) {
   if (M->d_wmixT) cudaFree(M->d_wmixT);
   if (M->d_gateT) cudaFree(M->d_gateT);
   if (M->d_miximg) cudaFree(M->d_miximg);
+  if (M->d_gateimg) cudaFree(M->d_gateimg);
+  if (M->d_gatescale) cudaFree(M->d_gatescale);
   if (M->d_radimg) cudaFree(M->d_radimg);
   if (M->d_embmax) cudaFree(M->d_embmax);
   if (M->d_mixscale) cudaFree(M->d_mixscale);

@@ -2317,9 +2317,9 @@ int fused_forward_edges(mlip_model* M, const double* d_pos, const int* d_species
       MLIP_TRY(launch_sym_contract(L, n, C, M->S, mA, mB, d_species, M->Wsc1[t], M->Wsc2[t], A[t], mA, st));
       mB_mix = nullptr;
     }
-    if (M->gate)  // gated update with the species self-connection in place of the mix
-      MLIP_TRY(launch_gate_fwd(L, n, C, M->S, d_species, mA, mB_mix, h[t], M->Wmix[t], M->Wself[t], M->Wgate[t],
-                               M->Wselfgate[t], h[t + 1], gpre[t], gg[t], b.d_sys_of, amax_h(t + 1), st));
+    if (M->gate)  // gated update with the species self-connection in place of the mix (tensor cores)
+      MLIP_TRY(launch_gate_tc_fwd(L, n, M->S, d_species, mA, mB_mix, h[t], M->gate_fwd_img[t], M->gate_fwd_scale[t],
+                                  h[t + 1], gpre[t], gg[t], flag + 1, b.d_sys_of, amax_h(t + 1), st));
     else
       MLIP_TRY(launch_mix_tc(false, n, C, L, mA, mB_mix, M->mix_fwd_img[t], M->mix_scale[t], h[t], h[t + 1], u0[t],
                              nullptr, flag + 1, st, b.d_sys_of, amax_h(t + 1)));
@@ -2365,6 +2365,11 @@ int fused_adjoint_edges(mlip_model* M, const double* d_pos, const int* d_species
       MLIP_TRY(ws.get("ef.gg" + std::to_string(t), (size_t)std::max(n, 1) * L * C, &gg[t]));
     }
     MLIP_TRY(ws.get("fz.z2t" + std::to_string(t), (size_t)std::max(n_tiles, 1) * kTileBytes, &z2t[t]));
+  }
+  float *gdpre = nullptr, *gdg = nullptr;  // the tensor-core gate's adjoint scratch
+  if (M->gate) {
+    MLIP_TRY(ws.get("fz.gdpre", ND, &gdpre));
+    MLIP_TRY(ws.get("fz.gdg", (size_t)std::max(n, 1) * L * C, &gdg));
   }
   uint8_t* epar = nullptr;
   MLIP_TRY(ws.get("fz.epar", Ec, &epar));
@@ -2413,8 +2418,9 @@ int fused_adjoint_edges(mlip_model* M, const double* d_pos, const int* d_species
       // max |dE/dm| of the message adjoint's input: from the mix, or from the contraction's adjoint
       float* gmax = use_bf16 ? nullptr : amax_h(t) + 1;
       if (M->gate)  // Gm = dE/dm; GaA <- dE/dh^t's residual part (with the self-connection), GaB <- 0
-        MLIP_TRY(launch_gate_bwd(L, n, C, M->S, d_species, GaA, GaB, gpre[t], gg[t], M->WmixT[t], M->WselfT[t],
-                                 M->WgateT[t], M->WselfgateT[t], Gm, b.d_sys_of, M->corr == 2 ? nullptr : gmax, st));
+        MLIP_TRY(launch_gate_tc_bwd(L, n, M->S, d_species, GaA, GaB, gpre[t], gg[t], M->gate_bwd_img[t],
+                                    M->gate_bwd_scale[t], Gm, gdpre, gdg, flag + 1, b.d_sys_of,
+                                    M->corr == 2 ? nullptr : gmax, st));
       else
         MLIP_TRY(launch_mix_tc(true, n, C, L, GaA, GaB, M->mix_bwd_img[t], M->mix_scale[t], nullptr, Gm, nullptr,
                                u0[t], flag + 1, st, b.d_sys_of, M->corr == 2 ? nullptr : gmax));

@@ -1,6 +1,9 @@
 // Host launchers of the device kernels (defined in plain_fp32.cu, node_ops.cu).
 #pragma once
 
+#include <cstdint>
+#include <vector>
+
 #include "kernels_common.cuh"
 
 namespace mlip {
@@ -171,5 +174,17 @@ int launch_gate_fwd(int L, int n, int C, int S, const int* species, const float*
 int launch_gate_bwd(int L, int n, int C, int S, const int* species, float* G, float* G2, const float* pre,
                     const float* g, const float* WmT, const float* WsT, const float* WgT, const float* WsgT,
                     float* Gm, const int* sys_of, float* out_max, cudaStream_t st);
+// The same on the tensor cores (gate_tc.cu; fused form, 128 channels): the
+// layer's split FP16 weight blocks and scales from pack_gate_images.  The
+// adjoint needs dpre [n][D][C] and dg [n][L C] as scratch.
+void pack_gate_images(bool bwd, const float* Wm, const float* Ws, const float* Wg, const float* Wsg, int L, int S,
+                      std::vector<uint8_t>& img, std::vector<float>& scale);
+int gate_tc_prepare();
+int launch_gate_tc_fwd(int L, int n, int S, const int* species, const float* X, const float* X2, const float* hin,
+                       const uint8_t* img, const float* wscale, float* hout, float* pre, float* g, int* err,
+                       const int* sys_of, float* out_max, cudaStream_t st);
+int launch_gate_tc_bwd(int L, int n, int S, const int* species, float* G, float* G2, const float* pre, const float* g,
+                       const uint8_t* img, const float* wscale, float* Gm, float* dpre, float* dg, int* err,
+                       const int* sys_of, float* out_max, cudaStream_t st);
 
 }  // namespace mlip

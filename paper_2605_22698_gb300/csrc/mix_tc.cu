@@ -26,28 +26,10 @@
 #include "launchers.cuh"
 #include "profile.cuh"
 #include "sm100_tc.cuh"
+#include "split16.cuh"
 
 namespace mlip {
 namespace {
-
-constexpr int kMC = 128;                      // channels
-constexpr int kMM = 128;                      // rows per CTA (MMA M)
-constexpr int kMOp = kMM * kMC * 2;           // one 16-bit 128 x 128 operand: 32 KB
-constexpr uint32_t kMLBO = 128, kMSBO = 2048; // K-adjacent / row-group-adjacent core matrices
-
-__host__ __device__ constexpr uint32_t canon128(int r, int k) {
-  return (uint32_t)((r >> 3) * kMSBO + (k >> 3) * kMLBO + (r & 7) * 16 + (k & 7) * 2);
-}
-
-__device__ __forceinline__ uint16_t h16(float x) {
-  const __half v = __float2half_rn(x);
-  return *reinterpret_cast<const uint16_t*>(&v);
-}
-
-__device__ __forceinline__ float pow2_scale(float amax) {
-  if (!(amax > 0.0f)) return 1.0f;
-  return exp2f((float)max(-100, min(100, 13 - ilogbf(amax))));
-}
 
 // smem: A_hi, A_lo, B_hi, B_lo (32 KB each), then the barriers
 template <bool BWD>
@@ -125,22 +107,8 @@ __global__ void __launch_bounds__(2 * kMM) mix_tc(int n, int L, const float* __r
 #pragma unroll
   for (int kh = 0; kh < HC / 8; ++kh) {
     const int kg = half * (HC / 8) + kh;
-    uint32_t ph[4], pl[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      uint16_t hh[2], ll[2];
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const float x = v[kh * 8 + 2 * q + j] * sc;
-        const __half h = __float2half_rn(x);
-        hh[j] = *reinterpret_cast<const uint16_t*>(&h);
-        ll[j] = h16(x - __half2float(h));
-      }
-      ph[q] = (uint32_t)hh[0] | ((uint32_t)hh[1] << 16);
-      pl[q] = (uint32_t)ll[0] | ((uint32_t)ll[1] << 16);
-    }
-    *reinterpret_cast<uint4*>(sAh + canon128(rt, kg * 8)) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-    *reinterpret_cast<uint4*>(sAl + canon128(rt, kg * 8)) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    split8(v + kh * 8, sc, reinterpret_cast<uint4*>(sAh + canon128(rt, kg * 8)),
+           reinterpret_cast<uint4*>(sAl + canon128(rt, kg * 8)));
   }
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();

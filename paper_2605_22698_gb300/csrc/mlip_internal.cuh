@@ -236,6 +236,12 @@ struct mlip_model {
   float* d_mixscale = nullptr;
   std::vector<const uint8_t*> mix_fwd_img, mix_bwd_img;
   std::vector<const float*> mix_scale;
+  // fused form with the gated update: split FP16 weight blocks of the
+  // tensor-core gate per layer (forward and adjoint) and their scales [L+1][4]
+  uint8_t* d_gateimg = nullptr;
+  float* d_gatescale = nullptr;
+  std::vector<const uint8_t*> gate_fwd_img, gate_bwd_img;
+  std::vector<const float*> gate_fwd_scale, gate_bwd_scale;
   // fused form: max_c |W_emb[z][c]| per species (the FP16 scale of the first adjoint layer)
   float* d_embmax = nullptr;
   // fused form: split FP16 images of the radial MLP's W2 per layer (32 KB each)
