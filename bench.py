@@ -743,8 +743,13 @@ def serve_phase(args, rank, world, R, sweep, alone, fixed_rate=None):
         "requests": R, "model": f"T{spec.T} C{spec.C} L{spec.L} H{spec.H}", "precision": args.precision,
         "mix": "70% E+F, 30% 100-step NVE at 0.5 fs; N = exp U(ln 8, ln 5000) atoms, open clusters at 0.1 /A^3",
         "saturated_atom_steps_per_s": round(world * ae / t_sat, 1), "saturated_ms_per_request": round(1e3 * t_sat / R, 4),
-        "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
-        "latency": {"rate_per_s": round(lam, 2), "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
+        # the headline p50 / p99: the fixed arrival rate (the same load whatever the kernels' speed;
+        # 0.7x the saturated rate grows with every speed-up, and the saturated rate comes from batches
+        # far larger than the open loop's, so that phase runs near or above capacity)
+        "p50_ms": fixed["p50_ms"] if fixed else round(st["p50_ms"], 2),
+        "p99_ms": fixed["p99_ms"] if fixed else round(st["p99_ms"], 2),
+        "headline_phase": "fixed_rate" if fixed else "latency",
+        "latency": {"rate_per_s": round(lam, 2), "load": "0.7x the saturated request rate", "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
                     "mean_ms": round(st["mean_ms"], 2), "max_ms": round(st["max_ms"], 2),
                     "throughput_atom_steps_per_s": round(thr2, 1),
                     "buckets_atoms": ["<=100", "101-1000", ">1000"],
@@ -783,6 +788,7 @@ def run_serve(args, rank, world):
                    "precision": args.precision, "mix": sv["mix"],
                    "step": "one request (value: atom-evaluations/s with every request queued at once)",
                    "l2": "inputs change every iteration (no flush)"},
+        "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "headline_phase": sv["headline_phase"],
         "latency": sv["latency"], "rate_sweep": sv["rate_sweep"], "fixed_rate": sv["fixed_rate"],
         "alone_ms": sv["alone_ms"],
         "saturated": sv["saturated"], "e2e": sv["e2e"], "gpu_launches": sv["gpu_launches"], "clocks": sv["clocks"],
