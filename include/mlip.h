@@ -193,8 +193,8 @@ int mlip_neighbors(const double* pos, int64_t n, const double cell[9], const uin
  * inputs return MLIP_ERR_INVALID_ARG (atoms) or MLIP_ERR_CAPACITY (degree)
  * with a message naming the limit.  *n_edges and MLIP_ERR_CAPACITY behave as
  * in mlip_neighbors.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) for that device; make that first call before
- * any stream capture.  All calls share the one array: calls that overlap on
+ * address (cudaGetSymbolAddress) for that device.  All calls share the one
+ * array: calls that overlap on
  * the GPU (two streams, two threads) race and must be serialised by the
  * caller.  The call synchronises the stream (to read the edge count). */
 int mlip_neighbors_noalloc(const double* pos, int64_t n, const double cell[9], const uint8_t pbc[3],
