@@ -1792,7 +1792,9 @@ __global__ void __launch_bounds__(kWSThreads, 1)
   } else {
     // ---------------------------------------------------------- consumers
     using S = Split<L, MODE, true>;
-    constexpr bool heavy0 = S::dh(0) + (FIRST ? 0 : G::NOUT) > 8, heavy1 = S::dh(1) + (FIRST ? 0 : G::NOUT) > 8;
+    // the first layer's group (one sender component, every output order) also takes the rolled
+    // per-edge loop: its unrolled 8-edge chunks overflow the instruction cache
+    constexpr bool heavy0 = FIRST || S::dh(0) + (FIRST ? 0 : G::NOUT) > 8, heavy1 = S::dh(1) + (FIRST ? 0 : G::NOUT) > 8;
     const int wsid = warp >> 2, c = tid & 127;
     float* GoutW = wsid == 0 ? GoutA : GoutB;
     const uint32_t taddr0 = tbase + ((uint32_t)((warp & 3) * 32) << 16);
