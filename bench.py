@@ -64,8 +64,8 @@ def peaks():
 # too large for a capture), mean of the five adjoint launches of one evaluation, scaled by
 # the edge count (the sender gathers are per edge)
 NCU_TRAFFIC = {("water3000", "f16", "tp_fused_bwd"): (129.7e6, "fused_bf16.cu", None),
-               ("fcc108k", "f16", "tp_fused_bwd"): (26.011029e9 / 5 * 4860690 / 1439826, "fused_bf16.cu",
-                                                    "64c5ca3d7460cde4")}
+               ("fcc108k", "f16", "tp_fused_bwd"): (26.035007e9 / 5 * 4860690 / 1439826, "fused_bf16.cu",
+                                                    "ce5b70cb78f48cf8")}
 # DRAM bytes per launch of the symmetric contraction's kernels at fcc108k: captured on the
 # 20^3-cell FCC (32,000 atoms; the full workload is too large for a capture) and scaled by the
 # atom count (traffic grows in proportion: per-node tensors)
