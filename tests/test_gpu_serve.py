@@ -219,6 +219,32 @@ def test_nve_batch_on_the_resident_skin_list(B):
     assert st["skin_builds"] >= 2  # the first build, and at least one after the drift
 
 
+def test_resident_list_threshold(B):
+    """resident_after < 0: no resident list at all (every step a fresh list,
+    the same trajectory bit for bit); resident_after = 1: the list from the
+    first unchanged iteration on.  The statistics count the iterations whose
+    membership changed (here only the first)."""
+    spec_m, spec = _model(B, "f16")
+    masses = np.asarray(spec.masses)
+    a = synth.cluster(200, seed=23)
+    va = synth.maxwell_boltzmann(masses[a.species], 300.0, seed=33)
+    out = {}
+    for ra in (-1, 1):
+        srv = B.Server(spec_m, resident_after=ra)
+        r = srv.wait(srv.submit(B.MLIP_REQ_NVE, a.pos, a.species, vel=va, n_steps=20, dt_fs=0.5), 120000)
+        st = srv.stats()
+        srv.close()
+        assert r["status"] == 0
+        out[ra] = (r, st)
+    (r0, s0), (r1, s1) = out[-1], out[1]
+    assert s0["skin_steps"] == 0 and s0["skin_builds"] == 0
+    assert s1["skin_steps"] >= 15 and s1["skin_builds"] >= 1
+    assert np.array_equal(r0["pos"], r1["pos"]) and np.array_equal(r0["pe"], r1["pe"])
+    for st in (s0, s1):
+        assert st["iterations"] == 21 and st["changed_iterations"] == 1
+        assert 0.0 < st["changed_busy_s"] <= st["busy_s"]
+
+
 def test_served_results_against_the_oracle(B):
     """One served energy+forces request and one served 10-step NVE request
     against the FP64 oracle: forces within 2e-3 of max|F| (FP16 form), the NVE
