@@ -18,8 +18,8 @@
 // The species self-connection thus costs S terms whose A rows
 // of the other species are zero: tensor-core work is cheap next to the rows'
 // traffic.  Operands are split FP16 (split16.cuh) with one power-of-two scale
-// per row (over every source of the row) and one per output block of B, so the
-// sums keep about 21 significant bits.  The epilogue applies the update
+// per row (over the sources feeding the CTA's output block) and one per output
+// block of B, so the sums keep about 21 significant bits.  The epilogue applies the update
 // (forward) or writes dE/dm and adds dE/dh (adjoint).  Order 0 runs first in
 // the forward: the later orders read its gates.
 #include <algorithm>
@@ -143,8 +143,9 @@ __host__ __device__ inline size_t gate_block0(bool bwd, int l, int L, int S) {
 namespace {
 
 // One CTA: 128 rows of order l = l_first + blockIdx.y (two threads a row, 64
-// channels each), output block blockIdx.z.  Forward: A0 (+ A0b) = the message buffers, A1 = the input
-// features; writes pre, the gates (order 0) and the updated features.
+// channels each), output block blockIdx.z (ncols: its tensor-memory columns).
+// Forward: A0 (+ A0b) = the message buffers, A1 = the input features; writes
+// pre, the gates (order 0) and the updated features.
 // Adjoint: A0 = dE/dpre, A1 = dE/dg [N][L][C]; writes Gm = dE/dm and adds
 // dE/dh into G (which holds dE/dh').
 template <bool BWD>
