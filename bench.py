@@ -82,7 +82,7 @@ def _src_digest(fname: str) -> str:
 def traffic_of(table, key):
     """Captured DRAM bytes per launch, or None when unknown or when the kernel's
     source changed since the capture (digest None: captured before digests were
-    recorded, so it cannot be shown to describe this build)."""
+    recorded, so it cannot be shown to describe the running kernel)."""
     ent = table.get(key)
     if not ent:
         return None
